@@ -1,0 +1,412 @@
+"""Python face of the serial FP64 CPU oracle (vbd_oracle.c) for Vertex Block Descent.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the
+benchmark's CPU-baseline leg, never by the product package.  It shares no
+code with the CUDA path; both are fed the same seeded inputs.
+
+Besides marshalling, this file holds the two dense FP64 references that need
+a linear-algebra library primitive:
+  * ``newton_solve``: the global implicit-Euler minimiser of Eq. 1 by a dense
+    Newton method with backtracking (the paper's "converges to the same
+    result as backward Euler" claim, Sec. 1 / Sec. 3.1);
+  * ``dense_adjoint``: reverse-mode derivative of converged implicit-Euler
+    steps (implicit function theorem on dG/dx = 0 of Eq. 1; the paper has
+    no adjoint, this is derived from Eqs. 1, 2 and 5).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "vbd_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_up = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C99, -O2, no fast-math)."""
+    hdr = os.path.join(_HERE, "vbd_oracle.h")
+    stale = (not os.path.exists(_LIB) or
+             os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(hdr)))
+    if force or stale:
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-fno-fast-math",
+                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(C.Structure):
+    _fields_ = [("gravity", C.c_double * 3), ("ground_on", C.c_int), ("ground_height", C.c_double),
+                ("ground_normal", C.c_double * 3), ("k_c", C.c_double), ("cheby_rho", C.c_double),
+                ("init_mode", C.c_int), ("det_eps", C.c_double), ("k_d", C.c_double)]
+
+    @classmethod
+    def make(cls, gravity=(0.0, 0.0, -9.8), ground_on=False, ground_height=0.0,
+             ground_normal=(0.0, 0.0, 1.0), k_c=0.0, cheby_rho=0.0, init_mode=3,
+             det_eps=1e-12, k_d=0.0, **_ignored) -> "Params":
+        p = cls()
+        p.gravity[:] = [float(g) for g in gravity]
+        p.ground_on = int(bool(ground_on))
+        p.ground_height = float(ground_height)
+        p.ground_normal[:] = [float(g) for g in ground_normal]
+        p.k_c = float(k_c)
+        p.cheby_rho = float(cheby_rho)
+        p.init_mode = int(init_mode)
+        p.det_eps = float(det_eps)
+        p.k_d = float(k_d)
+        return p
+
+
+class Stats(C.Structure):
+    _fields_ = [("vertex_solves", C.c_longlong), ("det_skips", C.c_longlong), ("contacts", C.c_longlong)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        vp = C.c_void_p
+        sig = {
+            "orc_lame": (None, [C.c_double, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+            "orc_rest_tet": (C.c_int, [_dp, _dp, C.POINTER(C.c_double)]),
+            "orc_tet_F": (None, [_dp, _dp, _dp]),
+            "orc_nh_psi": (C.c_double, [_dp, C.c_double, C.c_double]),
+            "orc_nh_pk1": (None, [_dp, C.c_double, C.c_double, _dp]),
+            "orc_cofactor": (None, [_dp, _dp]),
+            "orc_tet_energy": (C.c_double, [_dp, _dp, C.c_double, C.c_double, C.c_double]),
+            "orc_tet_grad": (None, [_dp, _dp, C.c_double, C.c_double, C.c_double, _dp]),
+            "orc_tet_hess_block": (None, [_dp, _dp, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, _dp]),
+            "orc_tet_hess": (None, [_dp, _dp, C.c_double, C.c_double, C.c_double, _dp]),
+            "orc_color_greedy": (C.c_int, [C.c_int, C.c_int, _ip, _ip]),
+            "orc_color_valid": (C.c_int, [C.c_int, C.c_int, _ip, _ip]),
+            "orc_model_new": (vp, [C.c_int, C.c_int, _dp, _ip, _dp, _dp, _dp, _up, C.POINTER(C.c_int)]),
+            "orc_model_free": (None, [vp]),
+            "orc_model_mass": (None, [vp, _dp]),
+            "orc_model_tet_data": (None, [vp, _dp, _dp, _dp, _dp]),
+            "orc_model_set_log_young": (None, [vp, _dp]),
+            "orc_inertia_target": (None, [vp, C.POINTER(Params), C.c_double, _dp, _dp, _dp]),
+            "orc_initial_guess": (None, [vp, C.POINTER(Params), C.c_double, _dp, _dp, _dp, _dp]),
+            "orc_vertex_solve": (C.c_int, [vp, C.POINTER(Params), C.c_double, C.c_int, _dp, _dp, _dp, _dp,
+                                           C.POINTER(C.c_int)]),
+            "orc_sweep_color": (None, [vp, C.POINTER(Params), C.c_double, _ip, C.c_int, _dp, _dp, _dp, _up,
+                                       C.POINTER(Stats)]),
+            "orc_cheby_omega": (C.c_double, [C.c_int, C.c_double, C.c_double]),
+            "orc_step": (C.c_int, [vp, C.POINTER(Params), _ip, C.c_int, C.c_double, C.c_int, _dp, _dp, _dp,
+                                   C.POINTER(Stats)]),
+            "orc_energy_G": (C.c_double, [vp, C.POINTER(Params), C.c_double, _dp, _dp]),
+            "orc_elastic_grad": (None, [vp, _dp, _dp]),
+            "orc_elastic_hess_triplets": (None, [vp, _dp, _ip, _ip, _dp]),
+            "orc_tet_grads": (None, [vp, _dp, _dp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _d(a, shape=None) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a.reshape(shape) if shape is not None else a
+
+
+# ---------------------------------------------------------------- element --
+
+def lame(E: float, nu: float) -> tuple[float, float]:
+    mu, lam = C.c_double(), C.c_double()
+    lib().orc_lame(E, nu, C.byref(mu), C.byref(lam))
+    return mu.value, lam.value
+
+
+def rest_tet(X: np.ndarray) -> tuple[np.ndarray, float]:
+    B = np.zeros(9)
+    V = C.c_double()
+    if lib().orc_rest_tet(_d(X, 12), B, C.byref(V)):
+        raise ValueError("degenerate rest tet")
+    return B.reshape(3, 3), V.value
+
+
+def tet_F(x, B) -> np.ndarray:
+    F = np.zeros(9)
+    lib().orc_tet_F(_d(x, 12), _d(B, 9), F)
+    return F.reshape(3, 3)
+
+
+def psi(F, mu, lam) -> float:
+    return lib().orc_nh_psi(_d(F, 9), mu, lam)
+
+
+def pk1(F, mu, lam) -> np.ndarray:
+    P = np.zeros(9)
+    lib().orc_nh_pk1(_d(F, 9), mu, lam, P)
+    return P.reshape(3, 3)
+
+
+def cofactor(F) -> np.ndarray:
+    Cm = np.zeros(9)
+    lib().orc_cofactor(_d(F, 9), Cm)
+    return Cm.reshape(3, 3)
+
+
+def tet_energy(x, B, V, mu, lam) -> float:
+    return lib().orc_tet_energy(_d(x, 12), _d(B, 9), V, mu, lam)
+
+
+def tet_grad(x, B, V, mu, lam) -> np.ndarray:
+    g = np.zeros(12)
+    lib().orc_tet_grad(_d(x, 12), _d(B, 9), V, mu, lam, g)
+    return g.reshape(4, 3)
+
+
+def tet_hess(x, B, V, mu, lam) -> np.ndarray:
+    H = np.zeros(144)
+    lib().orc_tet_hess(_d(x, 12), _d(B, 9), V, mu, lam, H)
+    return H.reshape(12, 12)
+
+
+def tet_hess_block(x, B, V, mu, lam, k, l) -> np.ndarray:
+    H = np.zeros(9)
+    lib().orc_tet_hess_block(_d(x, 12), _d(B, 9), V, mu, lam, k, l, H)
+    return H.reshape(3, 3)
+
+
+def cheby_omega(n: int, rho: float, omega_prev: float) -> float:
+    return lib().orc_cheby_omega(n, rho, omega_prev)
+
+
+# --------------------------------------------------------------- colouring --
+
+def color_greedy(n_verts: int, tets: np.ndarray) -> tuple[np.ndarray, int]:
+    t = np.ascontiguousarray(tets, dtype=np.int32)
+    colors = np.zeros(n_verts, np.int32)
+    nc = lib().orc_color_greedy(n_verts, t.shape[0], t.reshape(-1), colors)
+    if nc < 0:
+        raise ValueError("bad tet index")
+    return colors, nc
+
+
+def color_valid(n_verts: int, tets: np.ndarray, colors: np.ndarray) -> bool:
+    t = np.ascontiguousarray(tets, dtype=np.int32)
+    return bool(lib().orc_color_valid(n_verts, t.shape[0], t.reshape(-1),
+                                      np.ascontiguousarray(colors, dtype=np.int32)))
+
+
+# ------------------------------------------------------------------- model --
+
+class Model:
+    """One (or a union of independent) tet mesh(es) with FP64 rest data."""
+
+    def __init__(self, rest, tets, young, poisson, density, pinned):
+        self.n = int(np.asarray(rest).shape[0])
+        self.t = int(np.asarray(tets).shape[0])
+        self.tets = np.ascontiguousarray(tets, dtype=np.int32)
+        self.pinned = np.ascontiguousarray(pinned, dtype=np.uint8)
+        status = C.c_int()
+        self._h = lib().orc_model_new(self.n, self.t, _d(rest).reshape(-1), self.tets.reshape(-1),
+                                      _d(young), _d(poisson), _d(density), self.pinned, C.byref(status))
+        if not self._h:
+            raise ValueError("oracle model rejected mesh (status %d)" % status.value)
+        self.poisson = _d(poisson).copy()
+
+    @classmethod
+    def from_mesh(cls, m) -> "Model":
+        return cls(m.rest, m.tets, m.young, m.poisson, m.density, m.pinned)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.orc_model_free(h)
+            self._h = None
+
+    @property
+    def free(self) -> np.ndarray:
+        return self.pinned == 0
+
+    def mass(self) -> np.ndarray:
+        m = np.zeros(self.n)
+        lib().orc_model_mass(self._h, m)
+        return m
+
+    def tet_data(self):
+        B, V, mu, lam = np.zeros(9 * self.t), np.zeros(self.t), np.zeros(self.t), np.zeros(self.t)
+        lib().orc_model_tet_data(self._h, B, V, mu, lam)
+        return B.reshape(-1, 3, 3), V, mu, lam
+
+    def set_log_young(self, log_young) -> None:
+        lib().orc_model_set_log_young(self._h, _d(log_young))
+
+    # -- Algorithm 1 pieces
+    def inertia_target(self, p: Params, h, xt, vt) -> np.ndarray:
+        y = np.zeros(3 * self.n)
+        lib().orc_inertia_target(self._h, C.byref(p), h, _d(xt).reshape(-1), _d(vt).reshape(-1), y)
+        return y.reshape(-1, 3)
+
+    def initial_guess(self, p: Params, h, xt, vt, vprev) -> np.ndarray:
+        x = np.zeros(3 * self.n)
+        lib().orc_initial_guess(self._h, C.byref(p), h, _d(xt).reshape(-1), _d(vt).reshape(-1),
+                                _d(vprev).reshape(-1), x)
+        return x.reshape(-1, 3)
+
+    def vertex_solve(self, p: Params, h, i, x, y, xt) -> tuple[np.ndarray, int, int]:
+        dx = np.zeros(3)
+        contact = C.c_int()
+        skipped = lib().orc_vertex_solve(self._h, C.byref(p), h, int(i), _d(x).reshape(-1), _d(y).reshape(-1),
+                                         _d(xt).reshape(-1), dx, C.byref(contact))
+        return dx, skipped, contact.value
+
+    def sweep_color(self, p: Params, h, colors, color, x, y, xt, colliding=None) -> Stats:
+        st = Stats()
+        if colliding is None:
+            colliding = np.zeros(self.n, np.uint8)
+        xx = _d(x).reshape(-1)
+        lib().orc_sweep_color(self._h, C.byref(p), h, np.ascontiguousarray(colors, np.int32), int(color),
+                              xx, _d(y).reshape(-1), _d(xt).reshape(-1), colliding, C.byref(st))
+        x[...] = xx.reshape(x.shape)
+        return st
+
+    def step(self, p: Params, colors, n_colors, h, iters, x, v, vprev) -> Stats:
+        """In place: (x, v, vprev) = (x^t, v^t, v^{t-1}) -> (x^{t+1}, v^{t+1}, v^t)."""
+        st = Stats()
+        for a in (x, v, vprev):
+            assert a.dtype == np.float64 and a.flags.c_contiguous
+        lib().orc_step(self._h, C.byref(p), np.ascontiguousarray(colors, np.int32), int(n_colors), h,
+                       int(iters), x.reshape(-1), v.reshape(-1), vprev.reshape(-1), C.byref(st))
+        return st
+
+    def energy_G(self, p: Params, h, x, y) -> float:
+        return lib().orc_energy_G(self._h, C.byref(p), h, _d(x).reshape(-1), _d(y).reshape(-1))
+
+    def elastic_grad(self, x) -> np.ndarray:
+        g = np.zeros(3 * self.n)
+        lib().orc_elastic_grad(self._h, _d(x).reshape(-1), g)
+        return g
+
+    def elastic_hess(self, x) -> np.ndarray:
+        """Dense 3N x 3N elastic Hessian (small meshes only)."""
+        nt = 144 * self.t
+        r, c, v = np.zeros(nt, np.int32), np.zeros(nt, np.int32), np.zeros(nt)
+        lib().orc_elastic_hess_triplets(self._h, _d(x).reshape(-1), r, c, v)
+        H = np.zeros((3 * self.n, 3 * self.n))
+        np.add.at(H, (r, c), v)
+        return H
+
+    def tet_grads(self, x) -> np.ndarray:
+        g = np.zeros(12 * self.t)
+        lib().orc_tet_grads(self._h, _d(x).reshape(-1), g)
+        return g.reshape(self.t, 4, 3)
+
+    # -- dense global references (small meshes only)
+    def _ground_terms(self, p: Params, x):
+        n = np.array(p.ground_normal[:], dtype=np.float64)
+        n /= np.linalg.norm(n)
+        d = p.ground_height - x @ n
+        act = (d > 0) & self.free if p.ground_on else np.zeros(self.n, bool)
+        return n, d, act
+
+    def global_grad_hess(self, p: Params, h, x, y):
+        """dG/dx and d2G/dx2 of Eq. 1 (+ ground penalty), dense, all DoFs."""
+        m = self.mass()
+        M = np.repeat(np.where(self.free, m, 0.0), 3)
+        g = M / h ** 2 * (x - y).reshape(-1) + self.elastic_grad(x)
+        H = self.elastic_hess(x) + np.diag(M / h ** 2)
+        n, d, act = self._ground_terms(p, x)
+        for i in np.nonzero(act)[0]:
+            g[3 * i:3 * i + 3] -= p.k_c * d[i] * n
+            H[3 * i:3 * i + 3, 3 * i:3 * i + 3] += p.k_c * np.outer(n, n)
+        return g, H
+
+    def newton_solve(self, p: Params, h, x0, y, tol=1e-11, max_iter=200) -> np.ndarray:
+        """Global minimiser of G (Eq. 1) over free DoFs: dense Newton with
+        backtracking on G, from x0.  Used as the backward-Euler reference."""
+        x = np.array(x0, dtype=np.float64).reshape(-1, 3)
+        fd = np.repeat(self.free, 3)
+        scale = None
+        for _ in range(max_iter):
+            g, H = self.global_grad_hess(p, h, x, y)
+            gf = g[fd]
+            if scale is None:
+                scale = max(np.abs(gf).max(), 1e-300)
+            if np.abs(gf).max() <= tol * scale:
+                break
+            Hf = H[np.ix_(fd, fd)]
+            try:
+                dxf = -np.linalg.solve(Hf, gf)
+            except np.linalg.LinAlgError:
+                dxf = -gf
+            if dxf @ gf > 0:
+                dxf = -gf
+            dx = np.zeros(3 * self.n)
+            dx[fd] = dxf
+            G0 = self.energy_G(p, h, x, y)
+            a = 1.0
+            while a > 1e-12:
+                xn = x + a * dx.reshape(-1, 3)
+                if self.energy_G(p, h, xn, y) <= G0 + 1e-4 * a * (g @ dx):
+                    break
+                a *= 0.5
+            x = xn
+        return x
+
+
+def dense_adjoint(model: Model, p: Params, h: float, xs: list, dL_dxT: np.ndarray):
+    """Reverse-mode gradients of L(x_T) through T converged implicit-Euler steps.
+
+    xs = [x_0, ..., x_T] (positions after each step).  At a converged step
+    dG/dx(x_{t+1}; x_t, v_t, theta) = 0 on free DoFs, so with
+    H = M/h^2 + d2E/dx2 (+ contact):
+        r = xbar_{t+1} + vbar_{t+1}/h,   H lam = r,
+        xbar_t += M/h^2 lam - vbar_{t+1}/h,   vbar_t = M/h lam,
+        thetabar_j -= sum_{i in tet j} lam_i . dE_j/dx_i   (theta_j = log E_j).
+    Returns (dL/dlogE per tet, dL/dv_0 (N,3), dL/dx_0 (N,3)).
+    """
+    n = model.n
+    fd = np.repeat(model.free, 3)
+    m = np.repeat(model.mass(), 3)
+    xbar = np.asarray(dL_dxT, np.float64).reshape(-1).copy()
+    xbar[~fd] = 0.0
+    vbar = np.zeros(3 * n)
+    theta_bar = np.zeros(model.t)
+    T = len(xs) - 1
+    for t in range(T - 1, -1, -1):
+        x1 = np.asarray(xs[t + 1], np.float64).reshape(-1, 3)
+        H = model.elastic_hess(x1) + np.diag(m / h ** 2)
+        nrm, d, act = model._ground_terms(p, x1)
+        for i in np.nonzero(act)[0]:
+            H[3 * i:3 * i + 3, 3 * i:3 * i + 3] += p.k_c * np.outer(nrm, nrm)
+        r = xbar + vbar / h
+        lam = np.zeros(3 * n)
+        lam[fd] = np.linalg.solve(H[np.ix_(fd, fd)], r[fd])
+        tg = model.tet_grads(x1)  # (T, 4, 3)
+        lam3 = lam.reshape(-1, 3)
+        theta_bar -= np.einsum("tkr,tkr->t", tg, lam3[model.tets])
+        xbar_new = m / h ** 2 * lam - vbar / h
+        vbar = m / h * lam
+        xbar = xbar_new
+        xbar[~fd] = 0.0
+        vbar[~fd] = 0.0
+    return theta_bar, vbar.reshape(-1, 3), xbar.reshape(-1, 3)
+
+
+def run(model: Model, p: Params, colors, n_colors, h, iters, steps, x0, v0,
+        vprev0: Optional[np.ndarray] = None, record: bool = False):
+    """Run `steps` VBD steps from (x0, v0); v^{-1} defaults to v0."""
+    x = np.array(x0, np.float64).reshape(-1, 3).copy()
+    v = np.array(v0, np.float64).reshape(-1, 3).copy()
+    vp = (v.copy() if vprev0 is None else np.array(vprev0, np.float64).reshape(-1, 3).copy())
+    traj = [x.copy()] if record else None
+    for _ in range(steps):
+        model.step(p, colors, n_colors, h, iters, x, v, vp)
+        if record:
+            traj.append(x.copy())
+    return (x, v, vp, traj) if record else (x, v, vp)

@@ -1,0 +1,613 @@
+/*
+ * vbd_oracle.c -- serial FP64 CPU oracle for Vertex Block Descent.
+ *
+ * TEST INFRASTRUCTURE ONLY (see vbd_oracle.h).  Plain loops, FP64, no
+ * blocking, fusion or reordering beyond what the paper states, so each
+ * routine can be read against the paper equation it cites.
+ *
+ * Readings of points the paper leaves open (each pinned by a test):
+ *  - Material (Sec. 5 names "Neo-Hookean [Smith et al. 2018] without the
+ *    logarithmic term" and prints no formula):
+ *        Psi(F) = mu/2 (tr F^T F - 3) + lam/2 (J - alpha)^2,
+ *        alpha  = 1 + mu/lam   (the unique value making F = I stress free).
+ *  - Lame mapping from (E, nu): mu = E/(2(1+nu)),
+ *        lam = E nu/((1+nu)(1-2nu)) + mu, so the small-strain limit of Psi
+ *        is linear elasticity with the textbook Lame pair.
+ *  - Mass: lumped, m_i = sum over tets j containing i of rho_j V_j / 4.
+ *  - Singular-Hessian skip (Sec. 3.2): |det H| <= det_eps * |tr H / 3|^3.
+ *  - Contact (Eq. 11) with a ground half-space: x_b is the projection of
+ *    the vertex on the plane, d = max(0, height - x.n), n held constant.
+ *  - Colouring (Sec. 3.9 gives no algorithm): greedy, vertices visited by
+ *    decreasing number of distinct neighbours, ties by lower id, each
+ *    taking the smallest colour unused by its neighbours.
+ *  - Chebyshev (Eqs. 12-13): x^(0) is the initial guess; a vertex that
+ *    saw contact in any iteration of the step, including the current one,
+ *    keeps its Gauss-Seidel result (Sec. 3.8 collision skip).
+ *  - First step: the caller passes v^{t-1} = v^t, so the adaptive
+ *    acceleration estimate is 0.
+ */
+#include "vbd_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+struct orc_model {
+    int n_verts, n_tets;
+    int *tets;           /* 4T */
+    double *B;           /* 9T: inverse rest edge matrix, row-major */
+    double *V;           /* T : rest volume */
+    double *mu, *lam;    /* T : stable neo-Hookean parameters */
+    double *poisson;     /* T */
+    double *mass;        /* N */
+    unsigned char *pinned;
+    int *inc_off;        /* N+1: vertex -> incident tets */
+    int *inc_tet;        /* 4T */
+    int *inc_loc;        /* 4T: local index (0..3) of the vertex in that tet */
+};
+
+/* ------------------------------------------------------------------ */
+/* small 3x3 helpers (row-major)                                        */
+/* ------------------------------------------------------------------ */
+static double det3(const double A[9]) {
+    return A[0] * (A[4] * A[8] - A[5] * A[7])
+         - A[1] * (A[3] * A[8] - A[5] * A[6])
+         + A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+
+/* adjugate (transpose of the cofactor matrix): A * adj(A) = det(A) I */
+static void adj3(const double A[9], double R[9]) {
+    R[0] = A[4] * A[8] - A[5] * A[7];
+    R[1] = A[2] * A[7] - A[1] * A[8];
+    R[2] = A[1] * A[5] - A[2] * A[4];
+    R[3] = A[5] * A[6] - A[3] * A[8];
+    R[4] = A[0] * A[8] - A[2] * A[6];
+    R[5] = A[2] * A[3] - A[0] * A[5];
+    R[6] = A[3] * A[7] - A[4] * A[6];
+    R[7] = A[1] * A[6] - A[0] * A[7];
+    R[8] = A[0] * A[4] - A[1] * A[3];
+}
+
+static void cross3(const double a[3], const double b[3], double c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double dot3(const double a[3], const double b[3]) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+/* ------------------------------------------------------------------ */
+/* materials and the tetrahedral element                                */
+/* ------------------------------------------------------------------ */
+void orc_lame(double E, double nu, double *mu, double *lam) {
+    *mu = E / (2.0 * (1.0 + nu));
+    *lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)) + *mu;
+}
+
+/* Rest edge matrix Dm = [X1-X0, X2-X0, X3-X0] (columns), B = Dm^{-1},
+ * V = |det Dm| / 6.  Returns 1 for a degenerate rest tet. */
+int orc_rest_tet(const double X[12], double B[9], double *V) {
+    double Dm[9], A[9], L = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double len2 = 0.0;
+        for (int r = 0; r < 3; ++r) {
+            Dm[r * 3 + a] = X[(a + 1) * 3 + r] - X[r];
+            len2 += Dm[r * 3 + a] * Dm[r * 3 + a];
+        }
+        if (len2 > L) L = len2;
+    }
+    L = sqrt(L);
+    double d = det3(Dm);
+    if (!(fabs(d) > 1e-12 * L * L * L)) return 1;
+    adj3(Dm, A);
+    for (int k = 0; k < 9; ++k) B[k] = A[k] / d;
+    *V = fabs(d) / 6.0;
+    return 0;
+}
+
+/* Deformation gradient F = Ds B with Ds = [x1-x0, x2-x0, x3-x0]. */
+void orc_tet_F(const double x[12], const double B[9], double F[9]) {
+    double Ds[9];
+    for (int a = 0; a < 3; ++a)
+        for (int r = 0; r < 3; ++r) Ds[r * 3 + a] = x[(a + 1) * 3 + r] - x[r];
+    for (int r = 0; r < 3; ++r)
+        for (int s = 0; s < 3; ++s) {
+            double acc = 0.0;
+            for (int a = 0; a < 3; ++a) acc += Ds[r * 3 + a] * B[a * 3 + s];
+            F[r * 3 + s] = acc;
+        }
+}
+
+/* cof F = dJ/dF: columns f1 x f2, f2 x f0, f0 x f1 (f_s = column s of F). */
+void orc_cofactor(const double F[9], double C[9]) {
+    double f[3][3], c[3];
+    for (int s = 0; s < 3; ++s)
+        for (int r = 0; r < 3; ++r) f[s][r] = F[r * 3 + s];
+    for (int s = 0; s < 3; ++s) {
+        cross3(f[(s + 1) % 3], f[(s + 2) % 3], c);
+        for (int r = 0; r < 3; ++r) C[r * 3 + s] = c[r];
+    }
+}
+
+double orc_nh_psi(const double F[9], double mu, double lam) {
+    double Ic = 0.0;
+    for (int k = 0; k < 9; ++k) Ic += F[k] * F[k];
+    double alpha = 1.0 + mu / lam;
+    double J = det3(F);
+    return 0.5 * mu * (Ic - 3.0) + 0.5 * lam * (J - alpha) * (J - alpha);
+}
+
+/* First Piola-Kirchhoff stress P = dPsi/dF = mu F + lam (J - alpha) cof F. */
+void orc_nh_pk1(const double F[9], double mu, double lam, double P[9]) {
+    double C[9];
+    orc_cofactor(F, C);
+    double alpha = 1.0 + mu / lam;
+    double J = det3(F);
+    for (int k = 0; k < 9; ++k) P[k] = mu * F[k] + lam * (J - alpha) * C[k];
+}
+
+/* g_k = dF/dx_k (as F = sum_k x_k g_k^T): rows of B, g_0 = -(g_1+g_2+g_3). */
+static void shape_grad(const double B[9], int k, double g[3]) {
+    if (k == 0) {
+        for (int s = 0; s < 3; ++s) g[s] = -(B[s] + B[3 + s] + B[6 + s]);
+    } else {
+        for (int s = 0; s < 3; ++s) g[s] = B[(k - 1) * 3 + s];
+    }
+}
+
+double orc_tet_energy(const double x[12], const double B[9], double V, double mu, double lam) {
+    double F[9];
+    orc_tet_F(x, B, F);
+    return V * orc_nh_psi(F, mu, lam);
+}
+
+/* dE/dx_k = V P g_k */
+void orc_tet_grad(const double x[12], const double B[9], double V, double mu, double lam,
+                  double grad[12]) {
+    double F[9], P[9], g[3];
+    orc_tet_F(x, B, F);
+    orc_nh_pk1(F, mu, lam, P);
+    for (int k = 0; k < 4; ++k) {
+        shape_grad(B, k, g);
+        for (int r = 0; r < 3; ++r)
+            grad[k * 3 + r] = V * (P[r * 3 + 0] * g[0] + P[r * 3 + 1] * g[1] + P[r * 3 + 2] * g[2]);
+    }
+}
+
+/* d^2E/(dx_k dx_l) = V [ mu (g_k.g_l) I + lam c_k c_l^T
+ *                        + lam (J - alpha) [F (g_l x g_k)]_x ],  c = cof(F) g.
+ * The skew term is the derivative of cof(F) g_k along x_l; it vanishes for
+ * k == l because J is affine in any single vertex. */
+void orc_tet_hess_block(const double x[12], const double B[9], double V, double mu, double lam,
+                        int k, int l, double Hkl[9]) {
+    double F[9], C[9], gk[3], gl[3], ck[3], cl[3], gx[3], a[3];
+    orc_tet_F(x, B, F);
+    orc_cofactor(F, C);
+    double alpha = 1.0 + mu / lam;
+    double J = det3(F);
+    shape_grad(B, k, gk);
+    shape_grad(B, l, gl);
+    for (int r = 0; r < 3; ++r) {
+        ck[r] = C[r * 3 + 0] * gk[0] + C[r * 3 + 1] * gk[1] + C[r * 3 + 2] * gk[2];
+        cl[r] = C[r * 3 + 0] * gl[0] + C[r * 3 + 1] * gl[1] + C[r * 3 + 2] * gl[2];
+    }
+    cross3(gl, gk, gx);
+    for (int r = 0; r < 3; ++r) a[r] = F[r * 3 + 0] * gx[0] + F[r * 3 + 1] * gx[1] + F[r * 3 + 2] * gx[2];
+    double skew[9] = {0.0, -a[2], a[1], a[2], 0.0, -a[0], -a[1], a[0], 0.0};
+    double gg = dot3(gk, gl);
+    for (int r = 0; r < 3; ++r)
+        for (int s = 0; s < 3; ++s)
+            Hkl[r * 3 + s] = V * ((r == s ? mu * gg : 0.0) + lam * ck[r] * cl[s]
+                                  + lam * (J - alpha) * skew[r * 3 + s]);
+}
+
+void orc_tet_hess(const double x[12], const double B[9], double V, double mu, double lam,
+                  double H[144]) {
+    double blk[9];
+    for (int k = 0; k < 4; ++k)
+        for (int l = 0; l < 4; ++l) {
+            orc_tet_hess_block(x, B, V, mu, lam, k, l, blk);
+            for (int r = 0; r < 3; ++r)
+                for (int s = 0; s < 3; ++s) H[(k * 3 + r) * 12 + l * 3 + s] = blk[r * 3 + s];
+        }
+}
+
+/* ------------------------------------------------------------------ */
+/* vertex graph colouring (Sec. 3.9)                                    */
+/* ------------------------------------------------------------------ */
+static int cmp_int(const void *a, const void *b) {
+    int x = *(const int *)a, y = *(const int *)b;
+    return (x > y) - (x < y);
+}
+
+static int *g_deg_for_sort;
+static int cmp_visit(const void *a, const void *b) {
+    int i = *(const int *)a, j = *(const int *)b;
+    if (g_deg_for_sort[i] != g_deg_for_sort[j]) return g_deg_for_sort[j] - g_deg_for_sort[i];
+    return (i > j) - (i < j);
+}
+
+/* Returns the number of colours, or -1 on bad input. */
+int orc_color_greedy(int n, int t, const int *tets, int *colors) {
+    for (int k = 0; k < 4 * t; ++k)
+        if (tets[k] < 0 || tets[k] >= n) return -1;
+    int *cnt = (int *)calloc((size_t)n + 1, sizeof(int));
+    for (int j = 0; j < t; ++j)
+        for (int a = 0; a < 4; ++a) cnt[tets[4 * j + a] + 1] += 3;
+    for (int i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+    int *nbr = (int *)malloc(sizeof(int) * (size_t)(cnt[n] > 0 ? cnt[n] : 1));
+    int *fill = (int *)calloc((size_t)n, sizeof(int));
+    for (int j = 0; j < t; ++j)
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b)
+                if (a != b) {
+                    int i = tets[4 * j + a];
+                    nbr[cnt[i] + fill[i]++] = tets[4 * j + b];
+                }
+    /* sort and de-duplicate each list; degree = distinct neighbours */
+    int *deg = (int *)calloc((size_t)n, sizeof(int));
+    for (int i = 0; i < n; ++i) {
+        int *L = nbr + cnt[i];
+        int m = cnt[i + 1] - cnt[i];
+        qsort(L, (size_t)m, sizeof(int), cmp_int);
+        int u = 0;
+        for (int k = 0; k < m; ++k)
+            if (u == 0 || L[k] != L[u - 1]) L[u++] = L[k];
+        deg[i] = u;
+    }
+    int *order = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) order[i] = i;
+    g_deg_for_sort = deg;
+    qsort(order, (size_t)n, sizeof(int), cmp_visit);
+    for (int i = 0; i < n; ++i) colors[i] = -1;
+    int n_colors = 0;
+    unsigned char *used = (unsigned char *)calloc(4096, 1);
+    for (int q = 0; q < n; ++q) {
+        int i = order[q];
+        for (int k = 0; k < deg[i]; ++k) {
+            int c = colors[nbr[cnt[i] + k]];
+            if (c >= 0 && c < 4096) used[c] = 1;
+        }
+        int c = 0;
+        while (used[c]) ++c;
+        colors[i] = c;
+        if (c + 1 > n_colors) n_colors = c + 1;
+        for (int k = 0; k < deg[i]; ++k) {
+            int cc = colors[nbr[cnt[i] + k]];
+            if (cc >= 0 && cc < 4096) used[cc] = 0;
+        }
+    }
+    free(used); free(order); free(deg); free(fill); free(nbr); free(cnt);
+    return n_colors;
+}
+
+/* 1 iff no force element (tet) uses two vertices of the same colour. */
+int orc_color_valid(int n, int t, const int *tets, const int *colors) {
+    for (int i = 0; i < n; ++i)
+        if (colors[i] < 0) return 0;
+    for (int j = 0; j < t; ++j)
+        for (int a = 0; a < 4; ++a)
+            for (int b = a + 1; b < 4; ++b)
+                if (colors[tets[4 * j + a]] == colors[tets[4 * j + b]]) return 0;
+    return 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* model                                                                */
+/* ------------------------------------------------------------------ */
+static void gather_tet(const orc_model *m, int j, const double *x, double out[12]) {
+    for (int a = 0; a < 4; ++a)
+        for (int r = 0; r < 3; ++r) out[a * 3 + r] = x[3 * m->tets[4 * j + a] + r];
+}
+
+/* status: 0 ok, 1 bad index, 2 degenerate rest tet, 3 bad material */
+orc_model *orc_model_new(int n, int t, const double *rest, const int *tets,
+                         const double *young, const double *poisson, const double *density,
+                         const unsigned char *pinned, int *status) {
+    *status = 0;
+    for (int k = 0; k < 4 * t; ++k)
+        if (tets[k] < 0 || tets[k] >= n) { *status = 1; return NULL; }
+    for (int j = 0; j < t; ++j)
+        if (!(young[j] > 0.0) || !(poisson[j] > -1.0 && poisson[j] < 0.5) || !(density[j] > 0.0)) {
+            *status = 3;
+            return NULL;
+        }
+    orc_model *m = (orc_model *)calloc(1, sizeof(orc_model));
+    m->n_verts = n;
+    m->n_tets = t;
+    m->tets = (int *)malloc(sizeof(int) * 4 * (size_t)t + 1);
+    memcpy(m->tets, tets, sizeof(int) * 4 * (size_t)t);
+    m->B = (double *)malloc(sizeof(double) * 9 * (size_t)t + 1);
+    m->V = (double *)malloc(sizeof(double) * (size_t)t + 1);
+    m->mu = (double *)malloc(sizeof(double) * (size_t)t + 1);
+    m->lam = (double *)malloc(sizeof(double) * (size_t)t + 1);
+    m->poisson = (double *)malloc(sizeof(double) * (size_t)t + 1);
+    m->mass = (double *)calloc((size_t)n + 1, sizeof(double));
+    m->pinned = (unsigned char *)malloc((size_t)n + 1);
+    memcpy(m->pinned, pinned, (size_t)n);
+    for (int j = 0; j < t; ++j) {
+        double X[12];
+        gather_tet(m, j, rest, X);
+        if (orc_rest_tet(X, m->B + 9 * (size_t)j, m->V + j)) {
+            *status = 2;
+            orc_model_free(m);
+            return NULL;
+        }
+        orc_lame(young[j], poisson[j], m->mu + j, m->lam + j);
+        m->poisson[j] = poisson[j];
+        for (int a = 0; a < 4; ++a) m->mass[tets[4 * j + a]] += density[j] * m->V[j] / 4.0;
+    }
+    m->inc_off = (int *)calloc((size_t)n + 1, sizeof(int));
+    for (int k = 0; k < 4 * t; ++k) m->inc_off[tets[k] + 1]++;
+    for (int i = 0; i < n; ++i) m->inc_off[i + 1] += m->inc_off[i];
+    m->inc_tet = (int *)malloc(sizeof(int) * 4 * (size_t)t + 1);
+    m->inc_loc = (int *)malloc(sizeof(int) * 4 * (size_t)t + 1);
+    int *fill = (int *)calloc((size_t)n + 1, sizeof(int));
+    for (int j = 0; j < t; ++j)
+        for (int a = 0; a < 4; ++a) {
+            int i = tets[4 * j + a];
+            int s = m->inc_off[i] + fill[i]++;
+            m->inc_tet[s] = j;
+            m->inc_loc[s] = a;
+        }
+    free(fill);
+    return m;
+}
+
+void orc_model_free(orc_model *m) {
+    if (!m) return;
+    free(m->tets); free(m->B); free(m->V); free(m->mu); free(m->lam); free(m->poisson);
+    free(m->mass); free(m->pinned); free(m->inc_off); free(m->inc_tet); free(m->inc_loc);
+    free(m);
+}
+
+int orc_model_n_verts(const orc_model *m) { return m->n_verts; }
+int orc_model_n_tets(const orc_model *m) { return m->n_tets; }
+
+void orc_model_mass(const orc_model *m, double *mass) {
+    memcpy(mass, m->mass, sizeof(double) * (size_t)m->n_verts);
+}
+
+void orc_model_tet_data(const orc_model *m, double *B, double *V, double *mu, double *lam) {
+    memcpy(B, m->B, sizeof(double) * 9 * (size_t)m->n_tets);
+    memcpy(V, m->V, sizeof(double) * (size_t)m->n_tets);
+    memcpy(mu, m->mu, sizeof(double) * (size_t)m->n_tets);
+    memcpy(lam, m->lam, sizeof(double) * (size_t)m->n_tets);
+}
+
+/* Per-tet Young's modulus given as log E (the differentiable parameter). */
+void orc_model_set_log_young(orc_model *m, const double *log_young) {
+    for (int j = 0; j < m->n_tets; ++j) orc_lame(exp(log_young[j]), m->poisson[j], m->mu + j, m->lam + j);
+}
+
+/* ------------------------------------------------------------------ */
+/* time step                                                            */
+/* ------------------------------------------------------------------ */
+
+/* Eq. 2: y = x^t + h v^t + h^2 a_ext */
+void orc_inertia_target(const orc_model *m, const orc_params *p, double h,
+                        const double *xt, const double *vt, double *y) {
+    for (int i = 0; i < m->n_verts; ++i)
+        for (int r = 0; r < 3; ++r) y[3 * i + r] = xt[3 * i + r] + h * vt[3 * i + r] + h * h * p->gravity[r];
+}
+
+/* Sec. 3.7 initialisation options (a)-(d); pinned vertices keep x^t. */
+void orc_initial_guess(const orc_model *m, const orc_params *p, double h,
+                       const double *xt, const double *vt, const double *vprev, double *x) {
+    const double *g = p->gravity;
+    double gnorm = sqrt(dot3(g, g));
+    for (int i = 0; i < m->n_verts; ++i) {
+        const double *xi = xt + 3 * i, *vi = vt + 3 * i, *wi = vprev + 3 * i;
+        double *out = x + 3 * i;
+        if (m->pinned[i]) {
+            for (int r = 0; r < 3; ++r) out[r] = xi[r];
+            continue;
+        }
+        double atil = 0.0; /* factor on a_ext */
+        switch (p->init_mode) {
+        case 0:
+            for (int r = 0; r < 3; ++r) out[r] = xi[r];
+            continue;
+        case 1: atil = 0.0; break;
+        case 2: atil = 1.0; break;
+        default: {
+            /* a^t = (v^t - v^{t-1})/h, its component along a_ext / |a_ext| */
+            if (gnorm > 0.0) {
+                double a_ext_comp = 0.0;
+                for (int r = 0; r < 3; ++r) a_ext_comp += (vi[r] - wi[r]) / h * g[r] / gnorm;
+                if (a_ext_comp > gnorm) atil = 1.0;
+                else if (a_ext_comp < 0.0) atil = 0.0;
+                else atil = a_ext_comp / gnorm;
+            }
+        }
+        }
+        for (int r = 0; r < 3; ++r) out[r] = xi[r] + h * vi[r] + h * h * atil * g[r];
+    }
+}
+
+/* Local Newton step for vertex i (Eqs. 6-8, damping Eqs. 9-10, contact
+ * Eq. 11, analytic 3x3 solve and singular skip of Sec. 3.2).  Returns 1 if
+ * the vertex is skipped (dx = 0). */
+int orc_vertex_solve(const orc_model *m, const orc_params *p, double h, int i,
+                     const double *x, const double *y, const double *xt,
+                     double dx[3], int *in_contact) {
+    double f[3], H[9], Hel[9];
+    double mh2 = m->mass[i] / (h * h);
+    for (int r = 0; r < 3; ++r) f[r] = -mh2 * (x[3 * i + r] - y[3 * i + r]);
+    for (int k = 0; k < 9; ++k) Hel[k] = 0.0;
+    for (int s = m->inc_off[i]; s < m->inc_off[i + 1]; ++s) {
+        int j = m->inc_tet[s], a = m->inc_loc[s];
+        double xs[12], grad[12], Hb[9];
+        gather_tet(m, j, x, xs);
+        orc_tet_grad(xs, m->B + 9 * (size_t)j, m->V[j], m->mu[j], m->lam[j], grad);
+        orc_tet_hess_block(xs, m->B + 9 * (size_t)j, m->V[j], m->mu[j], m->lam[j], a, a, Hb);
+        for (int r = 0; r < 3; ++r) f[r] -= grad[3 * a + r];
+        for (int k = 0; k < 9; ++k) Hel[k] += Hb[k];
+    }
+    for (int k = 0; k < 9; ++k) H[k] = (1.0 + p->k_d / h) * Hel[k];
+    H[0] += mh2; H[4] += mh2; H[8] += mh2;
+    if (p->k_d != 0.0) {
+        for (int r = 0; r < 3; ++r)
+            for (int s = 0; s < 3; ++s) f[r] -= p->k_d / h * Hel[r * 3 + s] * (x[3 * i + s] - xt[3 * i + s]);
+    }
+    *in_contact = 0;
+    if (p->ground_on) {
+        const double *n = p->ground_normal;
+        double nn = sqrt(dot3(n, n));
+        double nh[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
+        double d = p->ground_height - dot3(x + 3 * i, nh);
+        if (d > 0.0) {
+            *in_contact = 1;
+            for (int r = 0; r < 3; ++r) {
+                f[r] += p->k_c * d * nh[r];
+                for (int s = 0; s < 3; ++s) H[r * 3 + s] += p->k_c * nh[r] * nh[s];
+            }
+        }
+    }
+    double det = det3(H);
+    double tr3 = (H[0] + H[4] + H[8]) / 3.0;
+    if (fabs(det) <= p->det_eps * fabs(tr3 * tr3 * tr3)) {
+        dx[0] = dx[1] = dx[2] = 0.0;
+        return 1;
+    }
+    double A[9];
+    adj3(H, A);
+    for (int r = 0; r < 3; ++r) dx[r] = (A[r * 3 + 0] * f[0] + A[r * 3 + 1] * f[1] + A[r * 3 + 2] * f[2]) / det;
+    return 0;
+}
+
+/* One colour pass (Algorithm 1 inner loop).  Vertices of one colour share
+ * no tet, so updating them in place, in any order, equals writing x^new and
+ * copying back after the pass (ground contact couples no two vertices). */
+void orc_sweep_color(const orc_model *m, const orc_params *p, double h, const int *colors,
+                     int color, double *x, const double *y, const double *xt,
+                     unsigned char *colliding, orc_stats *st) {
+    for (int i = 0; i < m->n_verts; ++i) {
+        if (colors[i] != color || m->pinned[i]) continue;
+        double dx[3];
+        int contact;
+        int skipped = orc_vertex_solve(m, p, h, i, x, y, xt, dx, &contact);
+        if (st) {
+            st->vertex_solves++;
+            st->det_skips += skipped;
+            st->contacts += contact;
+        }
+        if (contact && colliding) colliding[i] = 1;
+        for (int r = 0; r < 3; ++r) x[3 * i + r] += dx[r];
+    }
+}
+
+/* Eq. 13: omega_1 = 1, omega_2 = 2/(2 - rho^2), omega_n = 4/(4 - rho^2 omega_{n-1}) */
+double orc_cheby_omega(int n, double rho, double omega_prev) {
+    if (n <= 1) return 1.0;
+    if (n == 2) return 2.0 / (2.0 - rho * rho);
+    return 4.0 / (4.0 - rho * rho * omega_prev);
+}
+
+/* Algorithm 1 for one time step.  In: x = x^t, v = v^t, vprev = v^{t-1}.
+ * Out: x = x^{t+1}, v = v^{t+1}, vprev = v^t.  Returns 0. */
+int orc_step(const orc_model *m, const orc_params *p, const int *colors, int n_colors,
+             double h, int iters, double *x, double *v, double *vprev, orc_stats *st) {
+    size_t n3 = 3 * (size_t)m->n_verts;
+    double *xt = (double *)malloc(sizeof(double) * n3 + 1);
+    double *y = (double *)malloc(sizeof(double) * n3 + 1);
+    double *p1 = (double *)malloc(sizeof(double) * n3 + 1);
+    double *p2 = (double *)malloc(sizeof(double) * n3 + 1);
+    unsigned char *coll = (unsigned char *)calloc((size_t)m->n_verts + 1, 1);
+    memcpy(xt, x, sizeof(double) * n3);
+    orc_inertia_target(m, p, h, xt, v, y);            /* Eq. 2 */
+    orc_initial_guess(m, p, h, xt, v, vprev, x);      /* Sec. 3.7 */
+    memcpy(p1, x, sizeof(double) * n3);               /* x^(0) */
+    double omega = 1.0;
+    for (int n = 1; n <= iters; ++n) {
+        for (int c = 0; c < n_colors; ++c) orc_sweep_color(m, p, h, colors, c, x, y, xt, coll, st);
+        if (p->cheby_rho > 0.0) {
+            omega = orc_cheby_omega(n, p->cheby_rho, omega);   /* Eq. 13 */
+            for (int i = 0; i < m->n_verts; ++i) {
+                for (int r = 0; r < 3; ++r) {
+                    size_t q = 3 * (size_t)i + r;
+                    double xbar = x[q];
+                    double xn = xbar;
+                    if (n >= 2 && !m->pinned[i] && !coll[i]) xn = omega * (xbar - p2[q]) + p2[q]; /* Eq. 12 */
+                    p2[q] = p1[q];
+                    p1[q] = xn;
+                    x[q] = xn;
+                }
+            }
+        }
+    }
+    for (size_t q = 0; q < n3; ++q) {                  /* Eq. 5 */
+        double vn = (x[q] - xt[q]) / h;
+        vprev[q] = v[q];
+        v[q] = vn;
+    }
+    free(xt); free(y); free(p1); free(p2); free(coll);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* diagnostics and assembly                                             */
+/* ------------------------------------------------------------------ */
+
+/* Eq. 1 variational energy G(x) = 1/(2h^2) |x - y|_M^2 + E(x) over the free
+ * vertices, with the ground penalty of Eq. 11 when enabled. */
+double orc_energy_G(const orc_model *m, const orc_params *p, double h,
+                    const double *x, const double *y) {
+    double G = 0.0;
+    for (int i = 0; i < m->n_verts; ++i) {
+        if (m->pinned[i]) continue;
+        double d2 = 0.0;
+        for (int r = 0; r < 3; ++r) d2 += (x[3 * i + r] - y[3 * i + r]) * (x[3 * i + r] - y[3 * i + r]);
+        G += m->mass[i] / (2.0 * h * h) * d2;
+        if (p->ground_on) {
+            const double *n = p->ground_normal;
+            double nn = sqrt(dot3(n, n));
+            double d = p->ground_height - (x[3 * i] * n[0] + x[3 * i + 1] * n[1] + x[3 * i + 2] * n[2]) / nn;
+            if (d > 0.0) G += 0.5 * p->k_c * d * d;
+        }
+    }
+    for (int j = 0; j < m->n_tets; ++j) {
+        double xs[12];
+        gather_tet(m, j, x, xs);
+        G += orc_tet_energy(xs, m->B + 9 * (size_t)j, m->V[j], m->mu[j], m->lam[j]);
+    }
+    return G;
+}
+
+void orc_elastic_grad(const orc_model *m, const double *x, double *grad) {
+    memset(grad, 0, sizeof(double) * 3 * (size_t)m->n_verts);
+    for (int j = 0; j < m->n_tets; ++j) {
+        double xs[12], g[12];
+        gather_tet(m, j, x, xs);
+        orc_tet_grad(xs, m->B + 9 * (size_t)j, m->V[j], m->mu[j], m->lam[j], g);
+        for (int a = 0; a < 4; ++a)
+            for (int r = 0; r < 3; ++r) grad[3 * m->tets[4 * j + a] + r] += g[3 * a + r];
+    }
+}
+
+/* 144 (row, col, value) triplets per tet, global DoF indices 3*i + r. */
+void orc_elastic_hess_triplets(const orc_model *m, const double *x,
+                               int *rows, int *cols, double *vals) {
+    for (int j = 0; j < m->n_tets; ++j) {
+        double xs[12], H[144];
+        gather_tet(m, j, x, xs);
+        orc_tet_hess(xs, m->B + 9 * (size_t)j, m->V[j], m->mu[j], m->lam[j], H);
+        for (int a = 0; a < 12; ++a)
+            for (int b = 0; b < 12; ++b) {
+                size_t q = 144 * (size_t)j + 12 * a + b;
+                rows[q] = 3 * m->tets[4 * j + a / 3] + a % 3;
+                cols[q] = 3 * m->tets[4 * j + b / 3] + b % 3;
+                vals[q] = H[a * 12 + b];
+            }
+    }
+}
+
+void orc_tet_grads(const orc_model *m, const double *x, double *g12) {
+    for (int j = 0; j < m->n_tets; ++j) {
+        double xs[12];
+        gather_tet(m, j, x, xs);
+        orc_tet_grad(xs, m->B + 9 * (size_t)j, m->V[j], m->mu[j], m->lam[j], g12 + 12 * (size_t)j);
+    }
+}

@@ -1,0 +1,103 @@
+/*
+ * vbd_oracle.h -- serial FP64 CPU oracle for Vertex Block Descent
+ * (Chen, Liu, Yang, Yuksel, "Vertex Block Descent", ACM TOG 43(4), 2024).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library includes,
+ * links or calls this code; only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg do.  It shares no header, helper or table
+ * with the CUDA path.
+ *
+ * Every routine is a direct transcription of the paper's definitions
+ * (Sec. 3.1 Eqs. 1-5, Sec. 3.2 Eqs. 6-8, Sec. 3.5 Eq. 11, Sec. 3.7
+ * initialisation (a)-(d), Sec. 3.8 Eqs. 12-13, Algorithm 1), in FP64,
+ * with plain loops and no blocking or reordering.  Where the paper is
+ * silent (material formula, Lame mapping, lumped mass, det threshold,
+ * colouring algorithm) the readings are stated next to the code.
+ *
+ * Pins: every function is checked by tests against finite differences,
+ * invariances, closed forms or brute force (tests/test_oracle_*.py).
+ */
+#ifndef VBD_ORACLE_H
+#define VBD_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct orc_model orc_model;
+
+typedef struct {
+    double gravity[3];      /* a_ext of Eq. 2 */
+    int ground_on;          /* ground half-space penalty of Eq. 11 */
+    double ground_height;   /* plane {x : x.n = ground_height} */
+    double ground_normal[3];
+    double k_c;             /* collision stiffness, Eq. 11 */
+    double cheby_rho;       /* Eq. 12-13 spectral radius; 0 = no acceleration */
+    int init_mode;          /* Sec. 3.7: 0 previous, 1 inertia, 2 inertia+acc, 3 adaptive */
+    double det_eps;         /* relative threshold of the Sec. 3.2 singular-Hessian skip */
+    double k_d;             /* Rayleigh damping coefficient, Eqs. 9-10 (0 = off) */
+} orc_params;
+
+typedef struct {
+    long long vertex_solves;   /* local solves performed */
+    long long det_skips;       /* solves skipped by the |det H| test */
+    long long contacts;        /* solves that saw ground penetration */
+} orc_stats;
+
+/* ---- materials and element (Sec. 5: stable neo-Hookean without log term) -- */
+void orc_lame(double E, double nu, double *mu, double *lam);
+int orc_rest_tet(const double X[12], double B[9], double *V);
+void orc_tet_F(const double x[12], const double B[9], double F[9]);
+double orc_nh_psi(const double F[9], double mu, double lam);
+void orc_nh_pk1(const double F[9], double mu, double lam, double P[9]);
+void orc_cofactor(const double F[9], double C[9]);
+double orc_tet_energy(const double x[12], const double B[9], double V, double mu, double lam);
+void orc_tet_grad(const double x[12], const double B[9], double V, double mu, double lam,
+                  double grad[12]);
+void orc_tet_hess_block(const double x[12], const double B[9], double V, double mu, double lam,
+                        int k, int l, double Hkl[9]);
+void orc_tet_hess(const double x[12], const double B[9], double V, double mu, double lam,
+                  double H[144]);
+
+/* ---- colouring (Sec. 3.9) --------------------------------------------- */
+int orc_color_greedy(int n_verts, int n_tets, const int *tets, int *colors);
+int orc_color_valid(int n_verts, int n_tets, const int *tets, const int *colors);
+
+/* ---- model -------------------------------------------------------------- */
+orc_model *orc_model_new(int n_verts, int n_tets, const double *rest, const int *tets,
+                         const double *young, const double *poisson, const double *density,
+                         const unsigned char *pinned, int *status);
+void orc_model_free(orc_model *m);
+int orc_model_n_verts(const orc_model *m);
+int orc_model_n_tets(const orc_model *m);
+void orc_model_mass(const orc_model *m, double *mass);
+void orc_model_tet_data(const orc_model *m, double *B, double *V, double *mu, double *lam);
+void orc_model_set_log_young(orc_model *m, const double *log_young);
+
+/* ---- one time step (Algorithm 1) --------------------------------------- */
+void orc_inertia_target(const orc_model *m, const orc_params *p, double h,
+                        const double *xt, const double *vt, double *y);
+void orc_initial_guess(const orc_model *m, const orc_params *p, double h,
+                       const double *xt, const double *vt, const double *vprev, double *x);
+int orc_vertex_solve(const orc_model *m, const orc_params *p, double h, int i,
+                     const double *x, const double *y, const double *xt,
+                     double dx[3], int *in_contact);
+void orc_sweep_color(const orc_model *m, const orc_params *p, double h, const int *colors,
+                     int color, double *x, const double *y, const double *xt,
+                     unsigned char *colliding, orc_stats *st);
+double orc_cheby_omega(int n, double rho, double omega_prev);
+int orc_step(const orc_model *m, const orc_params *p, const int *colors, int n_colors,
+             double h, int iters, double *x, double *v, double *vprev, orc_stats *st);
+
+/* ---- diagnostics, assembly for the dense Newton / adjoint pins ---------- */
+double orc_energy_G(const orc_model *m, const orc_params *p, double h,
+                    const double *x, const double *y);
+void orc_elastic_grad(const orc_model *m, const double *x, double *grad);
+void orc_elastic_hess_triplets(const orc_model *m, const double *x,
+                               int *rows, int *cols, double *vals);
+void orc_tet_grads(const orc_model *m, const double *x, double *g12);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
