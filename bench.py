@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Throughput of the Vertex Block Descent sweep on one B300 (or N replicas).
+
+Workload (default): a 100x100x100 grid of cubes split into 6 tets each
+(1,030,301 vertices, 6,000,000 tets), vertices jittered by +-10% of the
+0.01 m edge, E = 1e6 Pa, nu = 0.45, rho = 1000, dropped from 0.5 m onto a
+ground plane with penalty stiffness 1e7, h = 1/60, 100 iterations per step,
+20 steps (the warm-up steps run before and the state is reset to rest).
+Synthetic inputs; the slot data streamed per iteration (1.3 GB) exceeds L2.
+
+Metric: vertex-block updates per second = free vertices x iterations x steps
+/ time, whole job.  One JSON line on rank 0.  ``--impl reference`` times the
+FP64 CPU oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "vertex-block updates/sec and % HBM roofline (1M-vert mesh); batched & adjoint vs plain"
+UNIT = "vertex-block updates/s"
+# algorithmic bytes per vertex-block update (per-incidence rest data + own
+# vertex I/O + one re-read of neighbour positions per colour pass)
+B_INC, B_VTX, B_X = 52, 44, 12
+CPU_SAMPLE_N = 32      # the CPU legs run a 32^3-cube crop of the same recipe
+CPU_SAMPLE_ITERS = 10
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=100, help="cubes per side of the grid")
+    ap.add_argument("--iters", type=int, default=100)
+    ap.add_argument("--coloring", choices=["kuhn", "greedy"], default="kuhn")
+    ap.add_argument("--lanes", type=int, default=0)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------ distributed ---
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_job(seconds: float, units: float, world: int):
+    """(max seconds over ranks, sum of units over ranks)."""
+    if world <= 1:
+        return seconds, units
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks ---
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", gpu_id, "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "note": "nvidia-smi unavailable"}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_id_of(dev: int) -> str:
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev)
+
+
+# ---------------------------------------------------------------- helpers ---
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("vbd_kernels.cu", "vbd_kernels.h"):
+        with open(os.path.join(ROOT, "paper_2403_06321_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload_key: str):
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "sweep_%s.md" % workload_key)
+    try:
+        lines = open(p).read().splitlines()
+    except OSError:
+        return None
+    kv = {}
+    for ln in lines:
+        if ln.startswith("- ") and ":" in ln:
+            k, v = ln[2:].split(":", 1)
+            kv[k.strip()] = v.strip().strip("`")
+    if kv.get("kernel_source_sha") != kernel_source_sha():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_sample(n_iters_total_seconds: float = 10.0):
+    """The FP64 oracle on a 32^3-cube crop of the same workload recipe."""
+    import numpy as np
+    from oracle import oracle
+    from paper_2403_06321_b300 import synth
+    m, cfg = synth.large_cube(CPU_SAMPLE_N)
+    model = oracle.Model.from_mesh(m)
+    colors = synth.kuhn_coloring(m.grid_ijk)
+    p = oracle.Params.make(gravity=cfg.gravity, ground_on=cfg.ground_on, k_c=cfg.k_c)
+    x, v = m.rest.copy(), np.zeros_like(m.rest)
+    vp = v.copy()
+    n_free = int((m.pinned == 0).sum())
+    return model, p, colors, cfg, x, v, vp, n_free
+
+
+def run_cpu_baseline(budget_s: float = 12.0) -> dict:
+    model, p, colors, cfg, x, v, vp, n_free = cpu_sample()
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        model.step(p, colors, 4, cfg.h, CPU_SAMPLE_ITERS, x, v, vp)
+        steps += 1
+        if time.perf_counter() - t0 >= budget_s or steps >= 50:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n_free * CPU_SAMPLE_ITERS * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d step(s) x %d iterations of the serial FP64 oracle on a %d^3-cube crop (%d verts) "
+                      "of the same recipe (jitter, material, ground, h)" % (
+                          steps, CPU_SAMPLE_ITERS, CPU_SAMPLE_N, n_free)}
+
+
+# --------------------------------------------------------------- reference ---
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    model, p, colors, cfg, x, v, vp, n_free = cpu_sample()
+    for _ in range(args.warmup):
+        model.step(p, colors, 4, cfg.h, CPU_SAMPLE_ITERS, x, v, vp)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        model.step(p, colors, 4, cfg.h, CPU_SAMPLE_ITERS, x, v, vp)
+    dt = time.perf_counter() - t0
+    value = n_free * CPU_SAMPLE_ITERS * args.steps / dt
+    sample = ("each step: one time step with %d iterations of the serial FP64 oracle on a %d^3-cube crop "
+              "(%d free verts) of the same recipe" % (CPU_SAMPLE_ITERS, CPU_SAMPLE_N, n_free))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args, None),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(args, info) -> dict:
+    n = args.n
+    cfg = {"workload": "large_cube: %d^3 cubes x 6 tets (%d verts, %d tets), jitter 10%%, E=1e6 nu=0.45, "
+                       "drop 0.5 m onto ground k_c=1e7, h=1/60, %d iterations/step" % (
+                           n, (n + 1) ** 3, 6 * n ** 3, args.iters),
+           "iters_per_step": args.iters, "h": 1.0 / 60.0, "coloring": args.coloring,
+           "l2": "inputs larger than L2 (slot stream %.2f GB per iteration)" % (6 * n ** 3 * 4 * 56 / 1e9)}
+    if info is not None:
+        cfg.update({"n_colors": info.n_colors, "n_free_verts": info.n_free, "n_slots": int(info.n_slots),
+                    "lanes_per_vertex": info.lanes_per_vertex, "block_threads": info.block_threads,
+                    "cuda_graph": bool(info.use_graph), "parallelism": "replicas"})
+    return cfg
+
+
+# --------------------------------------------------------------------- ours ---
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_2403_06321_b300 import synth, vbd
+    from paper_2403_06321_b300.build import build
+    if rank == 0:
+        build()
+    barrier(world)
+
+    m, cfg = synth.large_cube(args.n)
+    colors = synth.kuhn_coloring(m.grid_ijk) if args.coloring == "kuhn" else None
+    params = vbd.make_params(gravity=cfg.gravity, ground_on=cfg.ground_on, k_c=cfg.k_c,
+                             init_mode=cfg.init_mode, det_eps=cfg.det_eps)
+    stream = torch.cuda.Stream()
+    sim = vbd.Sim(m, params, colors=colors, stream=stream)
+    if args.lanes or args.block:
+        vbd.vbd_set_launch(sim.ctx, args.lanes, args.block)
+    vbd.vbd_set_graph(sim.ctx, not args.no_graph)
+    info = vbd.vbd_get_info(sim.ctx)
+    iters, h, K = args.iters, cfg.h, args.steps
+    zeros = np.zeros_like(m.rest)
+
+    # warm-up (graph capture happens here), then reset to the initial state
+    sim.set_state(m.rest, zeros)
+    for _ in range(args.warmup):
+        sim.step(h, iters)
+    sim.sync_status()
+    sim.set_state(m.rest, zeros)
+    torch.cuda.synchronize()
+
+    ev_start = torch.cuda.Event(enable_timing=True)
+    ev_end = torch.cuda.Event(enable_timing=True)
+    ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    clocks = ClockSampler(gpu_id_of(local))
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev_start.record(stream)
+    for k in range(K):
+        vbd.vbd_begin_step(sim.ctx, h)
+        ev_a[k].record(stream)
+        vbd.vbd_iterate(sim.ctx, iters)
+        ev_b[k].record(stream)
+        vbd.vbd_end_step(sim.ctx)
+    ev_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    sim.sync_status()  # raises on non-finite updates
+    t_ms = ev_start.elapsed_time(ev_end)
+    sweep_ms = sum(a.elapsed_time(b) for a, b in zip(ev_a, ev_b))
+    units = float(info.n_free) * iters * K
+    t_job, units_job = reduce_job(t_ms / 1e3, units, world)
+    value = units_job / t_job
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        N = m.n_verts
+        xh = torch.from_numpy(m.rest.astype(np.float32).reshape(-1)).pin_memory()
+        vh = torch.zeros(3 * N, dtype=torch.float32).pin_memory()
+        vph = torch.zeros(3 * N, dtype=torch.float32).pin_memory()
+        vout = torch.zeros(3 * N, dtype=torch.float32).pin_memory()
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            vbd.vbd_set_state(sim.ctx, xh, vh, vph)
+            vbd.vbd_step(sim.ctx, h, iters)
+            vbd.vbd_get_state(sim.ctx, xh, vout)  # synchronising (host destination)
+            vph, vh, vout = vh, vout, vph
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        te_job, ue_job = reduce_job(te, units, world)
+        e2e = {"value": ue_job / te_job, "unit": UNIT, "h2d_bytes_per_step": 3 * 12 * N,
+               "d2h_bytes_per_step": 2 * 12 * N}
+    sim.close()
+
+    if rank != 0:
+        return 0
+    C = info.n_colors
+    inc_per_vert = 4.0 * m.n_tets / m.n_verts
+    b_upd = inc_per_vert * B_INC + B_VTX + B_X * C
+    launches_sweep = K * iters * C
+    bytes_per_launch = info.n_free / C * b_upd
+    avg_launch_s = sweep_ms / 1e3 / launches_sweep
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    traffic = profiled_traffic("large_cube")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": t_job * 1e3 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": workload_config(args, info),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                     "kernel": "k_sweep (one colour pass)", "alg_bytes_per_update": b_upd,
+                     "avg_launch_us": avg_launch_s * 1e6,
+                     "sweep_share_of_step": sweep_ms / t_ms},
+        "e2e": e2e,
+        "gpu_launches": K * (2 + iters * C),
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = run_cpu_baseline()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

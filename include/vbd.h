@@ -1,0 +1,223 @@
+/*
+ * vbd.h -- C ABI of the B300 (sm_103a) Vertex Block Descent library.
+ *
+ * Vertex Block Descent (Chen, Liu, Yang, Yuksel, ACM TOG 43(4), 2024)
+ * integrates elastic tetrahedral bodies with implicit Euler written as the
+ * minimisation of the variational energy G of Eq. 1, by block coordinate
+ * descent over vertices: Gauss-Seidel passes over vertex colours (Sec. 3.9),
+ * each vertex taking one Newton step on its local energy G_i (Eqs. 3, 6-8).
+ * One time step is Algorithm 1.
+ *
+ * Conventions for every entry point:
+ *  - Returns a vbd_status; nothing throws across the ABI.  On failure the
+ *    message of vbd_last_error() says why; the context stays usable unless
+ *    the status is VBD_ERR_CUDA.
+ *  - Host inputs to vbd_create_mesh / vbd_color are copied; the caller may
+ *    free them on return.
+ *  - The library allocates no device memory.  The caller allocates one
+ *    workspace of vbd_workspace_size() bytes (256-byte aligned) and lends it
+ *    with vbd_bind(); it must outlive the binding (until vbd_destroy or the
+ *    next vbd_bind).
+ *  - All device work is asynchronous on the stream given to vbd_bind()
+ *    (a cudaStream_t passed as void*; NULL = the legacy default stream).
+ *    Calls marked "synchronising" wait for that stream.
+ *  - Vertex and tet arrays are in the caller's order; the internal
+ *    colour-major renumbering is never visible.
+ *  - Float arrays of positions and velocities are 3*n_verts floats (x,y,z
+ *    interleaved).  Pointers marked "host or device" may be either: with
+ *    unified addressing the library tells them apart itself.
+ *  - Units are SI; the default ground plane is z = 0 with +z up.
+ */
+#ifndef VBD_H
+#define VBD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VBD_OK = 0,
+    VBD_ERR_INVALID_ARG = 1,   /* NULL pointer, size or range error */
+    VBD_ERR_BAD_MESH = 2,      /* tet index out of range, degenerate rest tet, bad material */
+    VBD_ERR_BAD_COLORING = 3,  /* two vertices of one tet share a colour */
+    VBD_ERR_NOT_COLORED = 4,   /* vbd_color() has not run */
+    VBD_ERR_WORKSPACE = 5,     /* not bound, or workspace too small / misaligned */
+    VBD_ERR_CUDA = 6,          /* a CUDA runtime call failed */
+    VBD_ERR_NONFINITE = 7,     /* a kernel met a non-finite position or solve */
+    VBD_ERR_NO_TAPE = 8,       /* vbd_backward without recorded steps */
+    VBD_ERR_STATE = 9          /* call out of order (e.g. vbd_iterate before vbd_begin_step) */
+} vbd_status;
+
+typedef struct vbd_ctx vbd_ctx;
+
+/* One mesh, or the union of n_meshes independent meshes (batched mode):
+ * mesh b owns vertices [vert_offset[b], vert_offset[b+1]) and tets
+ * [tet_offset[b], tet_offset[b+1]); tets index the global vertex range.
+ * Meshes never interact, so the union is swept in one launch per colour. */
+typedef struct {
+    int32_t n_meshes;             /* >= 1 */
+    const int32_t *vert_offset;   /* host, n_meshes+1, or NULL when n_meshes == 1 */
+    const int32_t *tet_offset;    /* host, n_meshes+1, or NULL when n_meshes == 1 */
+    int32_t n_verts;              /* N >= 1 */
+    int32_t n_tets;               /* T >= 1 */
+    const double *rest_pos;       /* host, 3N: rest (material) positions */
+    const int32_t *tets;          /* host, 4T: vertex ids in [0, N) */
+    const float *young;           /* host, T: Young's modulus E > 0 [Pa] */
+    const float *poisson;         /* host, T: Poisson ratio in (-1, 0.5) */
+    const float *density;         /* host, T: mass density > 0 [kg/m^3] */
+    const uint8_t *pinned;        /* host, N: 1 = fixed vertex (Sec. 3.5), or NULL */
+} vbd_mesh_desc;
+
+typedef struct {
+    float gravity[3];        /* a_ext of Eq. 2 [m/s^2] */
+    int32_t ground_on;       /* ground half-space penalty (Eq. 11) on/off */
+    float ground_height;     /* plane {x : x . n = ground_height} */
+    float ground_normal[3];  /* n, need not be unit length */
+    float k_c;               /* collision stiffness of Eq. 11 [N/m] */
+    float cheby_rho;         /* spectral radius of Eq. 13; 0 disables acceleration */
+    int32_t init_mode;       /* Sec. 3.7: 0 previous position, 1 inertia,
+                                2 inertia + acceleration, 3 adaptive (default) */
+    float det_eps;           /* Sec. 3.2 skip when |det H_i| <= det_eps |tr H_i / 3|^3 */
+    float k_d;               /* Rayleigh damping coefficient of Eqs. 9-10 (0 = off) */
+    int32_t tape_steps;      /* steps of positions recorded for vbd_backward (0 = none) */
+} vbd_params;
+
+/* Library defaults: gravity (0,0,-9.8), ground off at z = 0 with n = +z,
+ * k_c = 1e7, no acceleration, adaptive init, det_eps = 1e-12, no damping. */
+void vbd_default_params(vbd_params *out);
+
+/* Sizes of a created context (filled after vbd_color for the colour data). */
+typedef struct {
+    int32_t n_verts, n_tets, n_meshes;
+    int32_t n_free;          /* vertices that are not pinned */
+    int32_t n_colors;        /* 0 before vbd_color */
+    int64_t n_slots;         /* (free vertex, incident tet) pairs streamed per iteration */
+    int32_t lanes_per_vertex, block_threads;   /* current sweep launch shape */
+    int32_t use_graph;       /* vbd_iterate replays a CUDA graph */
+} vbd_info;
+
+/* Creates a context from host arrays (copied).  Computes per-tet rest data
+ * in FP64 (inverse rest edge matrix and volume, lumped vertex masses
+ * m_i = sum_j rho_j V_j / 4) and the stable neo-Hookean parameters
+ * (Sec. 5 material; mu = E/(2(1+nu)), lambda = E nu/((1+nu)(1-2nu)) + mu,
+ * alpha = 1 + mu/lambda).  VBD_ERR_BAD_MESH for an out-of-range index, a
+ * rest tet with |det Dm| <= 1e-12 L^3, or a material outside its range.
+ * *out receives the context (NULL on failure); free it with vbd_destroy. */
+vbd_status vbd_create_mesh(const vbd_mesh_desc *desc, const vbd_params *params, vbd_ctx **out);
+
+/* Vertex colouring of Sec. 3.9: no tet may hold two vertices of one colour.
+ * colors = host array of N colour ids in [0, 4096) to validate and use, or
+ * NULL for the library's greedy colouring (vertices by decreasing number of
+ * distinct neighbours, ties by lower id, smallest free colour).  Renumbers
+ * vertices colour-major and builds the incidence-slot arrays.  Invalidates
+ * a previous binding (call vbd_bind again).  VBD_ERR_BAD_COLORING when the
+ * given colouring is invalid.  *n_colors_out may be NULL. */
+vbd_status vbd_color(vbd_ctx *ctx, const int32_t *colors, int32_t *n_colors_out);
+
+/* Host copy of the colouring in use (N ints, caller order). */
+vbd_status vbd_get_colors(const vbd_ctx *ctx, int32_t *colors_out);
+
+vbd_status vbd_get_info(const vbd_ctx *ctx, vbd_info *out);
+
+/* Bytes of device workspace needed with the current colouring and params
+ * (tape_steps enlarges it).  VBD_ERR_NOT_COLORED before vbd_color. */
+vbd_status vbd_workspace_size(const vbd_ctx *ctx, size_t *bytes);
+
+/* Lends the device workspace (256-byte aligned, >= vbd_workspace_size
+ * bytes) and the stream; uploads the static mesh data and sets the state to
+ * x = rest positions, v = v_prev = 0.  Asynchronous on `stream`. */
+vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *stream);
+
+/* Replaces the parameters.  Changing tape_steps requires a new vbd_bind. */
+vbd_status vbd_set_params(vbd_ctx *ctx, const vbd_params *params);
+
+/* Sets x^t, v^t and v^{t-1} (3N floats each, caller order, host or device).
+ * v_prev == NULL means v^{t-1} = v^t (zero estimated acceleration, the
+ * first-step convention of Sec. 3.7 (d)).  Clears the tape. */
+vbd_status vbd_set_state(vbd_ctx *ctx, const float *x, const float *v, const float *v_prev);
+
+/* Copies x and v (3N floats each, caller order, host or device; either may
+ * be NULL) on the bound stream.  For host destinations the call waits for
+ * the stream (synchronising). */
+vbd_status vbd_get_state(vbd_ctx *ctx, float *x, float *v);
+
+/* Replaces the per-tet Young's moduli by exp(log_young) (T floats, caller
+ * tet order, host or device), Poisson ratios unchanged. */
+vbd_status vbd_set_log_young(vbd_ctx *ctx, const float *log_young);
+
+/* One time step of Algorithm 1 with step size h and `iters` iterations:
+ * vbd_begin_step + vbd_iterate + vbd_end_step. */
+vbd_status vbd_step(vbd_ctx *ctx, float h, int32_t iters);
+
+/* Algorithm 1, first lines: y = x^t + h v^t + h^2 a_ext (Eq. 2) and the
+ * initial guess of Sec. 3.7 (pinned vertices keep x^t). */
+vbd_status vbd_begin_step(vbd_ctx *ctx, float h);
+
+/* Algorithm 1 iteration loop: for n = 1..iters, one Gauss-Seidel pass per
+ * colour in ascending colour order, each vertex solving H_i dx = f_i (Eqs.
+ * 6-8, damping Eqs. 9-10, ground penalty Eq. 11, singular skip Sec. 3.2),
+ * then, if cheby_rho > 0, the Chebyshev update of Eqs. 12-13 skipping
+ * vertices that touched the ground during this step (Sec. 3.8).  Replays a
+ * CUDA graph of the whole loop when graphs are enabled (default). */
+vbd_status vbd_iterate(vbd_ctx *ctx, int32_t iters);
+
+/* One Gauss-Seidel pass over the vertices of one colour (in place; vertices
+ * of one colour share no tet, so in-place writes equal the x^new copy-back
+ * of Algorithm 1 on this path). */
+vbd_status vbd_sweep_color(vbd_ctx *ctx, int32_t color);
+
+/* Chebyshev update (Eq. 12) after iteration n (1-based) of the current step. */
+vbd_status vbd_accelerate(vbd_ctx *ctx, int32_t n);
+
+/* Algorithm 1, last lines: v^{t+1} = (x^{t+1} - x^t)/h (Eq. 5); records x
+ * on the tape when tape_steps > 0. */
+vbd_status vbd_end_step(vbd_ctx *ctx);
+
+/* FP64 variational energy G(x) of Eq. 1 for the current x and the inertia
+ * target y of the current step (free vertices; ground penalty included when
+ * on).  Synchronising. */
+vbd_status vbd_energy(vbd_ctx *ctx, double *G_out);
+
+/* Waits for the stream and reads the device counters: VBD_ERR_NONFINITE if
+ * any solve produced a non-finite update since the last call (that update
+ * was not applied).  det_skips / contacts may be NULL.  Synchronising. */
+vbd_status vbd_sync_status(vbd_ctx *ctx, int64_t *det_skips, int64_t *contacts);
+
+/* Adjoint of the recorded steps (tape_steps > 0; no paper counterpart, the
+ * paper has no derivatives): treats every recorded step as converged
+ * (dG/dx = 0 of Eq. 1) and, backwards over the steps, solves H lam = r with
+ * `adj_iters` colour-ordered block Gauss-Seidel sweeps, H the Hessian of G
+ * at the recorded positions.  Inputs: dL_dxT (3N floats, caller order,
+ * device): dL/dx of the final positions.  Outputs (device, overwritten):
+ * dL_dlogE (T floats, caller tet order): dL/d log E per tet; dL_dv0 (3N):
+ * dL/dv at the first recorded step; either may be NULL.  Synchronises only
+ * to read the tape length. */
+vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, float *dL_dv0,
+                        int32_t adj_iters);
+
+/* Sweep launch shape: lanes_per_vertex in {4, 8, 16, 32} threads cooperate
+ * on one vertex; block_threads in {64, 128, 256, 512}.  0 keeps a value. */
+vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_threads);
+
+/* Enables (1) or disables (0) CUDA-graph replay of vbd_iterate. */
+vbd_status vbd_set_graph(vbd_ctx *ctx, int32_t enable);
+
+/* Times every sweep launch shape on the bound stream with the current state
+ * (which it restores) for `iters` iterations at step size h and keeps the
+ * fastest.  Synchronising.  best_ms_per_iter may be NULL. */
+vbd_status vbd_autotune(vbd_ctx *ctx, float h, int32_t iters, float *best_ms_per_iter);
+
+/* Message of the last failed call on this context (static storage owned by
+ * the context; valid until the next call).  Never NULL. */
+const char *vbd_last_error(const vbd_ctx *ctx);
+
+/* Releases host memory and CUDA graphs.  The workspace is the caller's. */
+void vbd_destroy(vbd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

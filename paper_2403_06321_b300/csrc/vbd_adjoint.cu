@@ -1,0 +1,260 @@
+// vbd_adjoint.cu -- reverse pass through converged VBD steps (no paper
+// counterpart: the paper has no derivatives; this follows from applying the
+// implicit function theorem to dG/dx = 0 of Eq. 1, with y from Eq. 2 and the
+// velocity update of Eq. 5).
+//
+// For a recorded step t with end positions x_{t+1} and H = M/h^2 + d2E/dx2
+// (+ the ground penalty Hessian), going backwards:
+//   r = xbar_{t+1} + vbar_{t+1} / h,   H lam = r   (colour-ordered block GS),
+//   xbar_t = M/h^2 lam - vbar_{t+1}/h,  vbar_t = M/h lam,
+//   d L / d log E_j -= sum_{i in tet j} lam_i . dE_j/dx_i.
+// The block Gauss-Seidel sweep reuses the forward's slot layout: per slot it
+// forms the tet's off-diagonal blocks H_ik (k = the three other vertices)
+// applied to lam_k, and the vertex's diagonal block, then one lane solves
+// the 3x3 system for lam_i.  Vertices of one colour share no tet, so the
+// in-place update is an exact Gauss-Seidel sweep.
+#include "vbd_kernels.h"
+
+namespace vbd {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ __forceinline__ float3 sub(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+// F v with F given by its columns f0, f1, f2
+__device__ __forceinline__ float3 mulF(float3 f0, float3 f1, float3 f2, float3 v) {
+    return make_float3(v.x * f0.x + v.y * f1.x + v.z * f2.x, v.x * f0.y + v.y * f1.y + v.z * f2.y,
+                       v.x * f0.z + v.y * f1.z + v.z * f2.z);
+}
+
+template <int L>
+__device__ __forceinline__ float sub_reduce(float v) {
+#pragma unroll
+    for (int off = L / 2; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    return v;
+}
+
+struct AdjAcc {
+    float q0, q1, q2;                      // sum_k H_ik lam_k (off-diagonal part)
+    float h00, h01, h02, h11, h12, h22;    // elastic diagonal block
+};
+
+template <int L>
+__global__ void __launch_bounds__(256) k_adj_sweep(Dev d, const float4 *__restrict__ xs, SweepParams p) {
+    const int lane = threadIdx.x & (L - 1);
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int vi = p.vbegin + (int)(gt / L);
+    const bool active = vi < p.vend;
+    float3 xi = make_float3(0.f, 0.f, 0.f);
+    int s0 = 0, s1 = 0;
+    if (active) {
+        xi = f3(xs[vi]);
+        s0 = d.slot_off[vi];
+        s1 = d.slot_off[vi + 1];
+    }
+    AdjAcc a = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int s = s0 + lane; s < s1; s += L) {
+        const int4 r0 = __ldcs(d.s0 + s);
+        const float4 r1 = __ldcs(d.s1 + s);
+        const float4 r2 = __ldcs(d.s2 + s);
+        const float2 r3 = __ldcs(d.s3 + s);
+        const int nb[3] = {r0.x, r0.y, r0.z};
+        const float Vmu = __int_as_float(r0.w), Vlam = r3.y;
+        float3 g[3];
+        g[0] = make_float3(r1.x, r1.y, r1.z);
+        g[1] = make_float3(r1.w, r2.x, r2.y);
+        g[2] = make_float3(r2.z, r2.w, r3.x);
+        const float3 gi = make_float3(-(g[0].x + g[1].x + g[2].x), -(g[0].y + g[1].y + g[2].y),
+                                      -(g[0].z + g[1].z + g[2].z));
+        float3 e[3], lk[3];
+        for (int k = 0; k < 3; ++k) {
+            e[k] = sub(f3(__ldg(xs + nb[k])), xi);
+            lk[k] = f3(d.lam[nb[k]]);  // written by other colours' launches only
+        }
+        float3 f0 = make_float3(0.f, 0.f, 0.f), f1 = f0, f2 = f0;
+        for (int k = 0; k < 3; ++k) {
+            f0.x += e[k].x * g[k].x; f0.y += e[k].y * g[k].x; f0.z += e[k].z * g[k].x;
+            f1.x += e[k].x * g[k].y; f1.y += e[k].y * g[k].y; f1.z += e[k].z * g[k].y;
+            f2.x += e[k].x * g[k].z; f2.y += e[k].y * g[k].z; f2.z += e[k].z * g[k].z;
+        }
+        const float3 c0 = cross(f1, f2), c1 = cross(f2, f0), c2 = cross(f0, f1);
+        const float J = dot(f0, c0);
+        // cof(F) v
+        auto cof = [&](float3 v) {
+            return make_float3(v.x * c0.x + v.y * c1.x + v.z * c2.x, v.x * c0.y + v.y * c1.y + v.z * c2.y,
+                               v.x * c0.z + v.y * c1.z + v.z * c2.z);
+        };
+        const float3 ci = cof(gi);
+        const float kJ = Vlam * J - (Vlam + Vmu);  // V lam (J - alpha)
+        float sc = 0.f;                              // sum_k c_k . lam_k
+        float3 q = make_float3(0.f, 0.f, 0.f);
+        for (int k = 0; k < 3; ++k) {
+            const float gg = Vmu * dot(gi, g[k]);
+            q.x += gg * lk[k].x; q.y += gg * lk[k].y; q.z += gg * lk[k].z;
+            sc += dot(cof(g[k]), lk[k]);
+            const float3 w = cross(mulF(f0, f1, f2, cross(g[k], gi)), lk[k]);
+            q.x += kJ * w.x; q.y += kJ * w.y; q.z += kJ * w.z;
+        }
+        q.x += Vlam * ci.x * sc; q.y += Vlam * ci.y * sc; q.z += Vlam * ci.z * sc;
+        a.q0 += q.x; a.q1 += q.y; a.q2 += q.z;
+        const float dd = Vmu * dot(gi, gi);
+        a.h00 += dd + Vlam * ci.x * ci.x;
+        a.h11 += dd + Vlam * ci.y * ci.y;
+        a.h22 += dd + Vlam * ci.z * ci.z;
+        a.h01 += Vlam * ci.x * ci.y;
+        a.h02 += Vlam * ci.x * ci.z;
+        a.h12 += Vlam * ci.y * ci.z;
+    }
+    a.q0 = sub_reduce<L>(a.q0); a.q1 = sub_reduce<L>(a.q1); a.q2 = sub_reduce<L>(a.q2);
+    a.h00 = sub_reduce<L>(a.h00); a.h01 = sub_reduce<L>(a.h01); a.h02 = sub_reduce<L>(a.h02);
+    a.h11 = sub_reduce<L>(a.h11); a.h12 = sub_reduce<L>(a.h12); a.h22 = sub_reduce<L>(a.h22);
+    if (!(active && lane == 0)) return;
+    const float mh2 = d.mass[vi] * p.inv_h2;
+    const float4 r = d.rhs[vi];
+    const float b0 = r.x - a.q0, b1 = r.y - a.q1, b2 = r.z - a.q2;
+    float h00 = a.h00 + mh2, h11 = a.h11 + mh2, h22 = a.h22 + mh2, h01 = a.h01, h02 = a.h02, h12 = a.h12;
+    if (p.ground_on) {
+        const float pen = p.gh - (p.gn.x * xi.x + p.gn.y * xi.y + p.gn.z * xi.z);
+        if (pen > 0.f) {
+            h00 += p.kc * p.gn.x * p.gn.x; h11 += p.kc * p.gn.y * p.gn.y; h22 += p.kc * p.gn.z * p.gn.z;
+            h01 += p.kc * p.gn.x * p.gn.y; h02 += p.kc * p.gn.x * p.gn.z; h12 += p.kc * p.gn.y * p.gn.z;
+        }
+    }
+    const float a00 = h11 * h22 - h12 * h12, a01 = h02 * h12 - h01 * h22, a02 = h01 * h12 - h02 * h11;
+    const float a11 = h00 * h22 - h02 * h02, a12 = h01 * h02 - h00 * h12, a22 = h00 * h11 - h01 * h01;
+    const float det = h00 * a00 + h01 * a01 + h02 * a02;
+    const float inv = 1.f / det;
+    const float l0 = (a00 * b0 + a01 * b1 + a02 * b2) * inv;
+    const float l1 = (a01 * b0 + a11 * b1 + a12 * b2) * inv;
+    const float l2 = (a02 * b0 + a12 * b1 + a22 * b2) * inv;
+    if (!(isfinite(l0) && isfinite(l1) && isfinite(l2))) {
+        atomicAdd(d.counters + 0, 1ull);
+        return;
+    }
+    d.lam[vi] = make_float4(l0, l1, l2, 0.f);
+}
+
+// xbar, vbar <- seed; lam <- 0; gtheta <- 0 is done by the host (memset).
+__global__ void k_adj_seed(Dev d, const float *dL_dx, int n) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    const int i = d.new_of_orig[o];
+    d.xbar[i] = make_float4(dL_dx[3 * o], dL_dx[3 * o + 1], dL_dx[3 * o + 2], 0.f);
+    d.vbar[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// r = xbar + vbar / h on free vertices; lam = 0 everywhere (pinned stay 0).
+__global__ void k_adj_rhs(Dev d, int n, int n_free, float inv_h) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    d.lam[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i >= n_free) return;
+    const float4 xb = d.xbar[i], vb = d.vbar[i];
+    d.rhs[i] = make_float4(xb.x + vb.x * inv_h, xb.y + vb.y * inv_h, xb.z + vb.z * inv_h, 0.f);
+}
+
+// xbar_t = M/h^2 lam - vbar/h, vbar_t = M/h lam (free vertices; pinned 0)
+__global__ void k_adj_post_verts(Dev d, int n, int n_free, float h) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (i >= n_free) {
+        d.xbar[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        d.vbar[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const float m = d.mass[i];
+    const float4 l = d.lam[i], vb = d.vbar[i];
+    const float a = m / (h * h), b = m / h, c = 1.f / h;
+    d.xbar[i] = make_float4(a * l.x - c * vb.x, a * l.y - c * vb.y, a * l.z - c * vb.z, 0.f);
+    d.vbar[i] = make_float4(b * l.x, b * l.y, b * l.z, 0.f);
+}
+
+// gtheta_j -= sum_k lam_k . V P g_k at the recorded positions (dE_j/dlogE_j = E_j)
+__global__ void k_adj_post_tets(Dev d, const float4 *__restrict__ xs, int n_tets) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_tets) return;
+    const int4 t = d.tet_v[j];
+    const int id[4] = {t.x, t.y, t.z, t.w};
+    const float *B = d.tet_B + 9 * (size_t)j;
+    float3 x[4];
+    for (int k = 0; k < 4; ++k) x[k] = f3(xs[id[k]]);
+    float3 g[4];
+    g[1] = make_float3(B[0], B[1], B[2]);
+    g[2] = make_float3(B[3], B[4], B[5]);
+    g[3] = make_float3(B[6], B[7], B[8]);
+    g[0] = make_float3(-(g[1].x + g[2].x + g[3].x), -(g[1].y + g[2].y + g[3].y), -(g[1].z + g[2].z + g[3].z));
+    float3 f0 = make_float3(0.f, 0.f, 0.f), f1 = f0, f2 = f0;
+    for (int k = 1; k < 4; ++k) {
+        const float3 e = sub(x[k], x[0]);
+        f0.x += e.x * g[k].x; f0.y += e.y * g[k].x; f0.z += e.z * g[k].x;
+        f1.x += e.x * g[k].y; f1.y += e.y * g[k].y; f1.z += e.z * g[k].y;
+        f2.x += e.x * g[k].z; f2.y += e.y * g[k].z; f2.z += e.z * g[k].z;
+    }
+    const float3 c0 = cross(f1, f2), c1 = cross(f2, f0), c2 = cross(f0, f1);
+    const float J = dot(f0, c0);
+    const float mu = d.tet_mu[j], lam = d.tet_lam[j], V = d.tet_V[j];
+    const float kJ = lam * (J - (1.f + mu / lam));
+    float acc = 0.f;
+    for (int k = 0; k < 4; ++k) {
+        const float3 l = f3(d.lam[id[k]]);
+        const float3 Fg = mulF(f0, f1, f2, g[k]);
+        const float3 cg = mulF(c0, c1, c2, g[k]);
+        acc += V * (mu * dot(Fg, l) + kJ * dot(cg, l));
+    }
+    d.gtheta[j] -= acc;
+}
+
+__global__ void k_adj_out(Dev d, float *dL_dv0, int n) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    const float4 a = d.vbar[d.new_of_orig[o]];
+    dL_dv0[3 * o] = a.x;
+    dL_dv0[3 * o + 1] = a.y;
+    dL_dv0[3 * o + 2] = a.z;
+}
+
+inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+void launch_adj_seed(const Dev &d, const float *dL_dx, int n, cudaStream_t s) {
+    k_adj_seed<<<blocks_for(n, 256), 256, 0, s>>>(d, dL_dx, n);
+}
+
+void launch_adj_rhs(const Dev &d, int n, int n_free, float inv_h, cudaStream_t s) {
+    k_adj_rhs<<<blocks_for(n, 256), 256, 0, s>>>(d, n, n_free, inv_h);
+}
+
+void launch_adj_sweep(const Dev &d, const float4 *xs, const SweepParams &p, int lanes, int block,
+                      cudaStream_t s) {
+    const long long threads = (long long)(p.vend - p.vbegin) * lanes;
+    if (threads <= 0) return;
+    const unsigned grid = blocks_for(threads, block);
+    switch (lanes) {
+    case 4: k_adj_sweep<4><<<grid, block, 0, s>>>(d, xs, p); break;
+    case 8: k_adj_sweep<8><<<grid, block, 0, s>>>(d, xs, p); break;
+    case 16: k_adj_sweep<16><<<grid, block, 0, s>>>(d, xs, p); break;
+    default: k_adj_sweep<32><<<grid, block, 0, s>>>(d, xs, p); break;
+    }
+}
+
+void launch_adj_post(const Dev &d, const float4 *xs, int n, int n_free, int n_tets, float h,
+                     cudaStream_t s) {
+    // tets first: they read lam, which the vertex pass does not change
+    k_adj_post_tets<<<blocks_for(n_tets, 256), 256, 0, s>>>(d, xs, n_tets);
+    k_adj_post_verts<<<blocks_for(n, 256), 256, 0, s>>>(d, n, n_free, h);
+}
+
+void launch_adj_out(const Dev &d, float *dL_dlogE, float *dL_dv0, int n, int n_tets, cudaStream_t s) {
+    if (dL_dv0) k_adj_out<<<blocks_for(n, 256), 256, 0, s>>>(d, dL_dv0, n);
+    if (dL_dlogE) cudaMemcpyAsync(dL_dlogE, d.gtheta, sizeof(float) * (size_t)n_tets,
+                                  cudaMemcpyDeviceToDevice, s);
+}
+
+}  // namespace vbd

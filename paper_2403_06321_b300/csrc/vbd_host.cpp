@@ -1,0 +1,924 @@
+// vbd_host.cpp -- host side of the C ABI declared in include/vbd.h.
+//
+// Preprocessing (once per mesh, FP64 on the host): per-tet inverse rest edge
+// matrix and volume, lumped masses, the stable neo-Hookean parameters, the
+// vertex colouring (Sec. 3.9), a colour-major renumbering of the vertices and
+// the incidence-slot arrays the sweep streams.  Everything on the device
+// lives in the caller's workspace; this file never allocates device memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "vbd.h"
+#include "vbd_kernels.h"
+
+using vbd::Dev;
+using vbd::SweepParams;
+
+namespace {
+
+constexpr int kMaxColors = 4096;
+
+struct GraphEntry {
+    int first_n, iters;
+    uint32_t hbits;
+    uint64_t version;
+    cudaGraphExec_t exec;
+};
+
+}  // namespace
+
+struct vbd_ctx {
+    // mesh, caller order
+    int N = 0, T = 0, n_meshes = 1;
+    std::vector<int> vert_off, tet_off;
+    std::vector<double> rest;        // 3N
+    std::vector<int> tets;           // 4T
+    std::vector<float> young, poisson, density;
+    std::vector<uint8_t> pinned;
+    // FP64 rest data
+    std::vector<double> B;           // 9T
+    std::vector<double> V;           // T
+    std::vector<double> mu, lam;     // T
+    std::vector<double> mass;        // N
+    vbd_params params{};
+    // colouring and layout
+    bool colored = false;
+    std::vector<int> colors;
+    int n_colors = 0;
+    std::vector<int> new_of_orig, orig_of_new;
+    int n_free = 0;
+    std::vector<int> color_begin;    // n_colors + 1, over the free range
+    long long n_slots = 0;
+    std::vector<int> slot_off;       // n_free + 1
+    std::vector<int4> s0;
+    std::vector<float4> s1, s2;
+    std::vector<float2> s3;
+    std::vector<int> slot_tet, slot_loc;
+    // device
+    bool bound = false;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t stream = nullptr;
+    Dev d{};
+    int n_partials = 0;
+    // step state
+    bool in_step = false;
+    float h = 0.f;
+    int iter_in_step = 0;
+    int tape_len = 0;
+    std::vector<float> tape_h;
+    // launch shape / graphs
+    int lanes = 8, block = 256;
+    bool use_graph = true;
+    uint64_t version = 1;
+    std::vector<GraphEntry> graphs;
+    cudaStream_t capture_stream = nullptr;
+    std::string err = "no error";
+};
+
+namespace {
+
+vbd_status fail(vbd_ctx *c, vbd_status s, const std::string &msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+vbd_status cuda_fail(vbd_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, VBD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CU(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+double det3(const double A[9]) {
+    return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+           A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+
+// inverse rest edge matrix B = Dm^{-1}, Dm columns X_a - X_0; returns false if degenerate
+bool rest_inverse(const double *X0, const double *X1, const double *X2, const double *X3,
+                  double B[9], double *V) {
+    const double *Xa[3] = {X1, X2, X3};
+    double Dm[9];
+    double L2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double l = 0.0;
+        for (int r = 0; r < 3; ++r) {
+            Dm[r * 3 + a] = Xa[a][r] - X0[r];
+            l += Dm[r * 3 + a] * Dm[r * 3 + a];
+        }
+        L2 = std::max(L2, l);
+    }
+    const double L = std::sqrt(L2);
+    const double d = det3(Dm);
+    if (!(std::fabs(d) > 1e-12 * L * L * L)) return false;
+    // B = adj(Dm) / det
+    B[0] = (Dm[4] * Dm[8] - Dm[5] * Dm[7]) / d;
+    B[1] = (Dm[2] * Dm[7] - Dm[1] * Dm[8]) / d;
+    B[2] = (Dm[1] * Dm[5] - Dm[2] * Dm[4]) / d;
+    B[3] = (Dm[5] * Dm[6] - Dm[3] * Dm[8]) / d;
+    B[4] = (Dm[0] * Dm[8] - Dm[2] * Dm[6]) / d;
+    B[5] = (Dm[2] * Dm[3] - Dm[0] * Dm[5]) / d;
+    B[6] = (Dm[3] * Dm[7] - Dm[4] * Dm[6]) / d;
+    B[7] = (Dm[1] * Dm[6] - Dm[0] * Dm[7]) / d;
+    B[8] = (Dm[0] * Dm[4] - Dm[1] * Dm[3]) / d;
+    *V = std::fabs(d) / 6.0;
+    return true;
+}
+
+// shape gradient of local vertex k: rows of B, g_0 = -(g_1 + g_2 + g_3)
+void shape_grad(const double *B, int k, double g[3]) {
+    for (int s = 0; s < 3; ++s)
+        g[s] = k == 0 ? -(B[s] + B[3 + s] + B[6 + s]) : B[(k - 1) * 3 + s];
+}
+
+// vertex -> incident tets CSR (tet order ascending)
+void incidence(int N, int T, const std::vector<int> &tets, std::vector<int> &off,
+               std::vector<int> &tet, std::vector<int> &loc) {
+    off.assign(N + 1, 0);
+    for (int k = 0; k < 4 * T; ++k) off[tets[k] + 1]++;
+    for (int i = 0; i < N; ++i) off[i + 1] += off[i];
+    tet.resize((size_t)4 * T);
+    loc.resize((size_t)4 * T);
+    std::vector<int> fill(N, 0);
+    for (int j = 0; j < T; ++j)
+        for (int a = 0; a < 4; ++a) {
+            const int i = tets[4 * j + a];
+            const int s = off[i] + fill[i]++;
+            tet[s] = j;
+            loc[s] = a;
+        }
+}
+
+int greedy_coloring(int N, int T, const std::vector<int> &tets, std::vector<int> &colors) {
+    std::vector<int> off, tet, loc;
+    incidence(N, T, tets, off, tet, loc);
+    // distinct neighbours per vertex
+    std::vector<int> nb_off(N + 1, 0), nb;
+    nb.reserve((size_t)12 * T);
+    std::vector<int> tmp;
+    for (int i = 0; i < N; ++i) {
+        tmp.clear();
+        for (int s = off[i]; s < off[i + 1]; ++s)
+            for (int b = 0; b < 4; ++b) {
+                const int k = tets[4 * tet[s] + b];
+                if (k != i) tmp.push_back(k);
+            }
+        std::sort(tmp.begin(), tmp.end());
+        tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+        nb.insert(nb.end(), tmp.begin(), tmp.end());
+        nb_off[i + 1] = (int)nb.size();
+    }
+    std::vector<int> order(N);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const int da = nb_off[a + 1] - nb_off[a], db = nb_off[b + 1] - nb_off[b];
+        return da > db;  // stable: ties keep the lower id first
+    });
+    colors.assign(N, -1);
+    std::vector<char> used(kMaxColors + 1, 0);
+    int n_colors = 0;
+    for (int i : order) {
+        for (int s = nb_off[i]; s < nb_off[i + 1]; ++s) {
+            const int c = colors[nb[s]];
+            if (c >= 0 && c <= kMaxColors) used[c] = 1;
+        }
+        int c = 0;
+        while (used[c]) ++c;
+        colors[i] = c;
+        n_colors = std::max(n_colors, c + 1);
+        for (int s = nb_off[i]; s < nb_off[i + 1]; ++s) {
+            const int cc = colors[nb[s]];
+            if (cc >= 0 && cc <= kMaxColors) used[cc] = 0;
+        }
+    }
+    return n_colors;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Carves the workspace; with base == nullptr only measures it.
+size_t carve(const vbd_ctx *c, char *base, Dev *d) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        char *p = base ? base + off : nullptr;
+        off += align_up(std::max<size_t>(bytes, 1));
+        return p;
+    };
+    const size_t N = (size_t)c->N, T = (size_t)c->T, S = (size_t)std::max<long long>(c->n_slots, 1);
+    Dev t{};
+    t.x = (float4 *)take(16 * N);
+    t.xt = (float4 *)take(16 * N);
+    t.v = (float4 *)take(16 * N);
+    t.vprev = (float4 *)take(16 * N);
+    t.ym = (float4 *)take(16 * N);
+    t.cheb[0] = (float4 *)take(16 * N);
+    t.cheb[1] = (float4 *)take(16 * N);
+    t.mass = (float *)take(4 * N);
+    t.slot_off = (int *)take(4 * ((size_t)c->n_free + 1));
+    t.s0 = (int4 *)take(16 * S);
+    t.s1 = (float4 *)take(16 * S);
+    t.s2 = (float4 *)take(16 * S);
+    t.s3 = (float2 *)take(8 * S);
+    t.slot_tet = (int *)take(4 * S);
+    t.slot_loc = (int *)take(4 * S);
+    t.tet_v = (int4 *)take(16 * T);
+    t.tet_B = (float *)take(36 * T);
+    t.tet_V = (float *)take(4 * T);
+    t.tet_nu = (float *)take(4 * T);
+    t.tet_mu = (float *)take(4 * T);
+    t.tet_lam = (float *)take(4 * T);
+    t.new_of_orig = (int *)take(4 * N);
+    for (int k = 0; k < 3; ++k) t.stage[k] = (float *)take(12 * N);
+    t.counters = (unsigned long long *)take(8 * 8);
+    t.partials = (double *)take(8 * (size_t)vbd::energy_partials_needed(c->n_free, c->T));
+    t.energy_out = (double *)take(8);
+    t.tape = (float4 *)take(16 * N * (size_t)std::max(c->params.tape_steps, 0));
+    t.lam = (float4 *)take(16 * N);
+    t.rhs = (float4 *)take(16 * N);
+    t.xbar = (float4 *)take(16 * N);
+    t.vbar = (float4 *)take(16 * N);
+    t.gtheta = (float *)take(4 * T);
+    if (d) *d = t;
+    return off;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+SweepParams sweep_params(const vbd_ctx *c, int color) {
+    SweepParams p{};
+    p.vbegin = color >= 0 ? c->color_begin[color] : 0;
+    p.vend = color >= 0 ? c->color_begin[color + 1] : 0;
+    const float *n = c->params.ground_normal;
+    const float nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    p.gn = make_float3(n[0] / nn, n[1] / nn, n[2] / nn);
+    p.gh = c->params.ground_height;
+    p.kc = c->params.k_c;
+    p.ground_on = c->params.ground_on ? 1 : 0;
+    p.det_eps = c->params.det_eps;
+    p.kd_over_h = c->h > 0.f ? c->params.k_d / c->h : 0.f;
+    p.inv_h2 = c->h > 0.f ? 1.f / (c->h * c->h) : 0.f;
+    return p;
+}
+
+bool params_ok(const vbd_params *p, std::string &why) {
+    const float *n = p->ground_normal;
+    const float nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    if (!(nn > 0.f) || !std::isfinite(nn)) { why = "ground_normal must be non-zero"; return false; }
+    if (!(p->cheby_rho >= 0.f && p->cheby_rho < 1.f)) { why = "cheby_rho must be in [0, 1)"; return false; }
+    if (p->init_mode < 0 || p->init_mode > 3) { why = "init_mode must be 0..3"; return false; }
+    if (!(p->det_eps >= 0.f)) { why = "det_eps must be >= 0"; return false; }
+    if (!(p->k_c >= 0.f) || !(p->k_d >= 0.f)) { why = "k_c and k_d must be >= 0"; return false; }
+    if (p->tape_steps < 0) { why = "tape_steps must be >= 0"; return false; }
+    for (int r = 0; r < 3; ++r)
+        if (!std::isfinite(p->gravity[r])) { why = "gravity must be finite"; return false; }
+    return true;
+}
+
+void clear_graphs(vbd_ctx *c) {
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+}
+
+// Chebyshev omega_n of Eq. 13 (computed in FP64)
+double cheby_omega(int n, double rho) {
+    double w = 1.0;
+    for (int k = 2; k <= n; ++k) w = (k == 2) ? 2.0 / (2.0 - rho * rho) : 4.0 / (4.0 - rho * rho * w);
+    return w;
+}
+
+// enqueue iterations n = first_n+1 .. first_n+iters on stream s
+void enqueue_iterations(vbd_ctx *c, int first_n, int iters, cudaStream_t s) {
+    const bool cheby = c->params.cheby_rho > 0.f;
+    for (int n = first_n + 1; n <= first_n + iters; ++n) {
+        for (int col = 0; col < c->n_colors; ++col)
+            vbd::launch_sweep(c->d, sweep_params(c, col), c->lanes, c->block, s);
+        if (cheby)
+            vbd::launch_cheby(c->d, c->n_free, n, (float)cheby_omega(n, c->params.cheby_rho), s);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+void vbd_default_params(vbd_params *out) {
+    if (!out) return;
+    std::memset(out, 0, sizeof(*out));
+    out->gravity[2] = -9.8f;
+    out->ground_on = 0;
+    out->ground_height = 0.f;
+    out->ground_normal[2] = 1.f;
+    out->k_c = 1e7f;
+    out->cheby_rho = 0.f;
+    out->init_mode = 3;
+    out->det_eps = 1e-12f;
+    out->k_d = 0.f;
+    out->tape_steps = 0;
+}
+
+vbd_status vbd_create_mesh(const vbd_mesh_desc *desc, const vbd_params *params, vbd_ctx **out) {
+    if (!out) return VBD_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!desc || !params || !desc->rest_pos || !desc->tets || !desc->young || !desc->poisson ||
+        !desc->density)
+        return VBD_ERR_INVALID_ARG;
+    if (desc->n_verts < 1 || desc->n_tets < 1 || desc->n_meshes < 1) return VBD_ERR_INVALID_ARG;
+    if ((long long)desc->n_tets * 4 > 0x7fffffffLL) return VBD_ERR_INVALID_ARG;
+    std::string why;
+    if (!params_ok(params, why)) return VBD_ERR_INVALID_ARG;
+    vbd_ctx *ctx = new vbd_ctx();
+    const int N = desc->n_verts, T = desc->n_tets;
+    ctx->N = N;
+    ctx->T = T;
+    ctx->n_meshes = desc->n_meshes;
+    ctx->params = *params;
+    if (desc->n_meshes > 1) {
+        if (!desc->vert_offset || !desc->tet_offset) { delete ctx; return VBD_ERR_INVALID_ARG; }
+        ctx->vert_off.assign(desc->vert_offset, desc->vert_offset + desc->n_meshes + 1);
+        ctx->tet_off.assign(desc->tet_offset, desc->tet_offset + desc->n_meshes + 1);
+        bool ok = ctx->vert_off.front() == 0 && ctx->tet_off.front() == 0 && ctx->vert_off.back() == N &&
+                  ctx->tet_off.back() == T;
+        for (int b = 0; b < desc->n_meshes && ok; ++b)
+            ok = ctx->vert_off[b + 1] > ctx->vert_off[b] && ctx->tet_off[b + 1] > ctx->tet_off[b];
+        if (!ok) { delete ctx; return VBD_ERR_INVALID_ARG; }
+    } else {
+        ctx->vert_off = {0, N};
+        ctx->tet_off = {0, T};
+    }
+    ctx->rest.assign(desc->rest_pos, desc->rest_pos + 3 * (size_t)N);
+    ctx->tets.assign(desc->tets, desc->tets + 4 * (size_t)T);
+    ctx->young.assign(desc->young, desc->young + T);
+    ctx->poisson.assign(desc->poisson, desc->poisson + T);
+    ctx->density.assign(desc->density, desc->density + T);
+    ctx->pinned.assign(N, 0);
+    if (desc->pinned)
+        for (int i = 0; i < N; ++i) ctx->pinned[i] = desc->pinned[i] ? 1 : 0;
+    for (size_t k = 0; k < ctx->rest.size(); ++k)
+        if (!std::isfinite(ctx->rest[k])) { delete ctx; return VBD_ERR_BAD_MESH; }
+    // every tet must stay inside its own mesh
+    for (int b = 0; b < ctx->n_meshes; ++b)
+        for (int j = ctx->tet_off[b]; j < ctx->tet_off[b + 1]; ++j)
+            for (int a = 0; a < 4; ++a) {
+                const int v = ctx->tets[4 * j + a];
+                if (v < ctx->vert_off[b] || v >= ctx->vert_off[b + 1]) { delete ctx; return VBD_ERR_BAD_MESH; }
+            }
+    for (int j = 0; j < T; ++j) {
+        const int *t = &ctx->tets[4 * j];
+        if (t[0] == t[1] || t[0] == t[2] || t[0] == t[3] || t[1] == t[2] || t[1] == t[3] || t[2] == t[3]) {
+            delete ctx;
+            return VBD_ERR_BAD_MESH;
+        }
+        if (!(ctx->young[j] > 0.f) || !(ctx->poisson[j] > -1.f && ctx->poisson[j] < 0.5f) ||
+            !(ctx->density[j] > 0.f) || !std::isfinite(ctx->young[j]) || !std::isfinite(ctx->density[j])) {
+            delete ctx;
+            return VBD_ERR_BAD_MESH;
+        }
+    }
+    ctx->B.resize(9 * (size_t)T);
+    ctx->V.resize(T);
+    ctx->mu.resize(T);
+    ctx->lam.resize(T);
+    ctx->mass.assign(N, 0.0);
+    for (int j = 0; j < T; ++j) {
+        const int *t = &ctx->tets[4 * j];
+        const double *R = ctx->rest.data();
+        if (!rest_inverse(R + 3 * (size_t)t[0], R + 3 * (size_t)t[1], R + 3 * (size_t)t[2], R + 3 * (size_t)t[3],
+                          &ctx->B[9 * (size_t)j], &ctx->V[j])) {
+            delete ctx;
+            return VBD_ERR_BAD_MESH;
+        }
+        const double E = ctx->young[j], nu = ctx->poisson[j];
+        ctx->mu[j] = E / (2.0 * (1.0 + nu));
+        ctx->lam[j] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)) + ctx->mu[j];
+        for (int a = 0; a < 4; ++a) ctx->mass[t[a]] += ctx->density[j] * ctx->V[j] / 4.0;
+    }
+    *out = ctx;
+    return VBD_OK;
+}
+
+vbd_status vbd_color(vbd_ctx *ctx, const int32_t *colors, int32_t *n_colors_out) {
+    if (!ctx) return VBD_ERR_INVALID_ARG;
+    const int N = ctx->N, T = ctx->T;
+    std::vector<int> col(N);
+    int nc = 0;
+    if (colors) {
+        for (int i = 0; i < N; ++i) {
+            if (colors[i] < 0 || colors[i] >= kMaxColors)
+                return fail(ctx, VBD_ERR_BAD_COLORING, "colour id out of [0, 4096)");
+            col[i] = colors[i];
+            nc = std::max(nc, col[i] + 1);
+        }
+        for (int j = 0; j < T; ++j) {
+            const int *t = &ctx->tets[4 * j];
+            for (int a = 0; a < 4; ++a)
+                for (int b = a + 1; b < 4; ++b)
+                    if (col[t[a]] == col[t[b]])
+                        return fail(ctx, VBD_ERR_BAD_COLORING,
+                                    "tet " + std::to_string(j) + " has two vertices of colour " +
+                                        std::to_string(col[t[a]]));
+        }
+    } else {
+        nc = greedy_coloring(N, T, ctx->tets, col);
+    }
+    ctx->colors = col;
+    ctx->n_colors = nc;
+    // colour-major order of free vertices (ties by caller id), pinned at the end
+    std::vector<int> order;
+    order.reserve(N);
+    for (int i = 0; i < N; ++i)
+        if (!ctx->pinned[i]) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return col[a] < col[b]; });
+    ctx->n_free = (int)order.size();
+    for (int i = 0; i < N; ++i)
+        if (ctx->pinned[i]) order.push_back(i);
+    ctx->orig_of_new = order;
+    ctx->new_of_orig.assign(N, 0);
+    for (int k = 0; k < N; ++k) ctx->new_of_orig[order[k]] = k;
+    ctx->color_begin.assign(nc + 1, 0);
+    for (int k = 0; k < ctx->n_free; ++k) ctx->color_begin[col[order[k]] + 1]++;
+    for (int c = 0; c < nc; ++c) ctx->color_begin[c + 1] += ctx->color_begin[c];
+    // incidence slots of free vertices
+    std::vector<int> off, tet, loc;
+    incidence(N, T, ctx->tets, off, tet, loc);
+    ctx->slot_off.assign(ctx->n_free + 1, 0);
+    for (int k = 0; k < ctx->n_free; ++k) {
+        const int i = order[k];
+        ctx->slot_off[k + 1] = ctx->slot_off[k] + (off[i + 1] - off[i]);
+    }
+    const long long S = ctx->slot_off[ctx->n_free];
+    ctx->n_slots = S;
+    ctx->s0.resize(S);
+    ctx->s1.resize(S);
+    ctx->s2.resize(S);
+    ctx->s3.resize(S);
+    ctx->slot_tet.resize(S);
+    ctx->slot_loc.resize(S);
+    for (int k = 0; k < ctx->n_free; ++k) {
+        const int i = order[k];
+        long long s = ctx->slot_off[k];
+        for (int q = off[i]; q < off[i + 1]; ++q, ++s) {
+            const int j = tet[q], a = loc[q];
+            const double *Bj = &ctx->B[9 * (size_t)j];
+            int ids[3];
+            double g[3][3];
+            int m = 0;
+            for (int b = 0; b < 4; ++b) {
+                if (b == a) continue;
+                ids[m] = ctx->new_of_orig[ctx->tets[4 * j + b]];
+                shape_grad(Bj, b, g[m]);
+                ++m;
+            }
+            const float Vmu = (float)(ctx->V[j] * ctx->mu[j]);
+            const float Vlam = (float)(ctx->V[j] * ctx->lam[j]);
+            int vmu_bits;
+            std::memcpy(&vmu_bits, &Vmu, 4);
+            ctx->s0[s] = make_int4(ids[0], ids[1], ids[2], vmu_bits);
+            ctx->s1[s] = make_float4((float)g[0][0], (float)g[0][1], (float)g[0][2], (float)g[1][0]);
+            ctx->s2[s] = make_float4((float)g[1][1], (float)g[1][2], (float)g[2][0], (float)g[2][1]);
+            ctx->s3[s] = make_float2((float)g[2][2], Vlam);
+            ctx->slot_tet[s] = j;
+            ctx->slot_loc[s] = a;
+        }
+    }
+    ctx->colored = true;
+    ctx->bound = false;
+    ctx->in_step = false;
+    ctx->tape_len = 0;
+    clear_graphs(ctx);
+    if (n_colors_out) *n_colors_out = nc;
+    return VBD_OK;
+}
+
+vbd_status vbd_get_colors(const vbd_ctx *ctx, int32_t *colors_out) {
+    if (!ctx || !colors_out) return VBD_ERR_INVALID_ARG;
+    if (!ctx->colored) return VBD_ERR_NOT_COLORED;
+    std::copy(ctx->colors.begin(), ctx->colors.end(), colors_out);
+    return VBD_OK;
+}
+
+vbd_status vbd_get_info(const vbd_ctx *ctx, vbd_info *out) {
+    if (!ctx || !out) return VBD_ERR_INVALID_ARG;
+    out->n_verts = ctx->N;
+    out->n_tets = ctx->T;
+    out->n_meshes = ctx->n_meshes;
+    out->n_free = ctx->colored ? ctx->n_free : 0;
+    out->n_colors = ctx->colored ? ctx->n_colors : 0;
+    out->n_slots = ctx->colored ? ctx->n_slots : 0;
+    out->lanes_per_vertex = ctx->lanes;
+    out->block_threads = ctx->block;
+    out->use_graph = ctx->use_graph ? 1 : 0;
+    return VBD_OK;
+}
+
+vbd_status vbd_workspace_size(const vbd_ctx *ctx, size_t *bytes) {
+    if (!ctx || !bytes) return VBD_ERR_INVALID_ARG;
+    if (!ctx->colored) return VBD_ERR_NOT_COLORED;
+    *bytes = carve(ctx, nullptr, nullptr);
+    return VBD_OK;
+}
+
+vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *stream) {
+    if (!ctx || !device_workspace) return VBD_ERR_INVALID_ARG;
+    if (!ctx->colored) return fail(ctx, VBD_ERR_NOT_COLORED, "vbd_color must run before vbd_bind");
+    const size_t need = carve(ctx, nullptr, nullptr);
+    if (bytes < need) return fail(ctx, VBD_ERR_WORKSPACE, "workspace too small: need " + std::to_string(need));
+    if (((uintptr_t)device_workspace & 255) != 0) return fail(ctx, VBD_ERR_WORKSPACE, "workspace not 256-byte aligned");
+    if (!is_device_ptr(device_workspace)) return fail(ctx, VBD_ERR_WORKSPACE, "workspace is not device memory");
+    ctx->ws = (char *)device_workspace;
+    ctx->ws_bytes = bytes;
+    ctx->stream = (cudaStream_t)stream;
+    carve(ctx, ctx->ws, &ctx->d);
+    ctx->n_partials = vbd::energy_partials_needed(ctx->n_free, ctx->T);
+    cudaStream_t s = ctx->stream;
+    const int N = ctx->N, T = ctx->T;
+    const long long S = ctx->n_slots;
+    const Dev &d = ctx->d;
+    // static data
+    std::vector<float> massf(N);
+    for (int k = 0; k < N; ++k) massf[k] = (float)ctx->mass[ctx->orig_of_new[k]];
+    std::vector<int4> tv(T);
+    std::vector<float> tB(9 * (size_t)T), tV(T), tnu(T), tmu(T), tlam(T);
+    for (int j = 0; j < T; ++j) {
+        const int *t = &ctx->tets[4 * j];
+        tv[j] = make_int4(ctx->new_of_orig[t[0]], ctx->new_of_orig[t[1]], ctx->new_of_orig[t[2]],
+                          ctx->new_of_orig[t[3]]);
+        for (int k = 0; k < 9; ++k) tB[9 * (size_t)j + k] = (float)ctx->B[9 * (size_t)j + k];
+        tV[j] = (float)ctx->V[j];
+        tnu[j] = ctx->poisson[j];
+        tmu[j] = (float)ctx->mu[j];
+        tlam[j] = (float)ctx->lam[j];
+    }
+    CU(cudaMemcpyAsync(d.mass, massf.data(), 4 * (size_t)N, cudaMemcpyHostToDevice, s), "upload mass");
+    CU(cudaMemcpyAsync(d.slot_off, ctx->slot_off.data(), 4 * ((size_t)ctx->n_free + 1), cudaMemcpyHostToDevice, s),
+       "upload slot_off");
+    if (S > 0) {
+        CU(cudaMemcpyAsync(d.s0, ctx->s0.data(), 16 * (size_t)S, cudaMemcpyHostToDevice, s), "upload slots");
+        CU(cudaMemcpyAsync(d.s1, ctx->s1.data(), 16 * (size_t)S, cudaMemcpyHostToDevice, s), "upload slots");
+        CU(cudaMemcpyAsync(d.s2, ctx->s2.data(), 16 * (size_t)S, cudaMemcpyHostToDevice, s), "upload slots");
+        CU(cudaMemcpyAsync(d.s3, ctx->s3.data(), 8 * (size_t)S, cudaMemcpyHostToDevice, s), "upload slots");
+        CU(cudaMemcpyAsync(d.slot_tet, ctx->slot_tet.data(), 4 * (size_t)S, cudaMemcpyHostToDevice, s), "upload slots");
+        CU(cudaMemcpyAsync(d.slot_loc, ctx->slot_loc.data(), 4 * (size_t)S, cudaMemcpyHostToDevice, s), "upload slots");
+    }
+    CU(cudaMemcpyAsync(d.tet_v, tv.data(), 16 * (size_t)T, cudaMemcpyHostToDevice, s), "upload tets");
+    CU(cudaMemcpyAsync(d.tet_B, tB.data(), 36 * (size_t)T, cudaMemcpyHostToDevice, s), "upload tets");
+    CU(cudaMemcpyAsync(d.tet_V, tV.data(), 4 * (size_t)T, cudaMemcpyHostToDevice, s), "upload tets");
+    CU(cudaMemcpyAsync(d.tet_nu, tnu.data(), 4 * (size_t)T, cudaMemcpyHostToDevice, s), "upload tets");
+    CU(cudaMemcpyAsync(d.tet_mu, tmu.data(), 4 * (size_t)T, cudaMemcpyHostToDevice, s), "upload tets");
+    CU(cudaMemcpyAsync(d.tet_lam, tlam.data(), 4 * (size_t)T, cudaMemcpyHostToDevice, s), "upload tets");
+    CU(cudaMemcpyAsync(d.new_of_orig, ctx->new_of_orig.data(), 4 * (size_t)N, cudaMemcpyHostToDevice, s),
+       "upload permutation");
+    CU(cudaMemsetAsync(d.counters, 0, 64, s), "clear counters");
+    // state: x = rest, v = v_prev = 0
+    std::vector<float> restf(3 * (size_t)N);
+    for (size_t k = 0; k < restf.size(); ++k) restf[k] = (float)ctx->rest[k];
+    CU(cudaMemcpyAsync(d.stage[0], restf.data(), 12 * (size_t)N, cudaMemcpyHostToDevice, s), "upload rest");
+    vbd::launch_scatter(d.stage[0], d.x, d.new_of_orig, N, s);
+    CU(cudaMemsetAsync(d.v, 0, 16 * (size_t)N, s), "clear v");
+    CU(cudaMemsetAsync(d.vprev, 0, 16 * (size_t)N, s), "clear v_prev");
+    CU(cudaMemsetAsync(d.xt, 0, 16 * (size_t)N, s), "clear x^t");
+    CU(cudaStreamSynchronize(s), "bind upload");  // host staging vectors die here
+    CU(cudaGetLastError(), "bind kernels");
+    ctx->bound = true;
+    ctx->in_step = false;
+    ctx->tape_len = 0;
+    ctx->tape_h.clear();
+    clear_graphs(ctx);
+    return VBD_OK;
+}
+
+vbd_status vbd_set_params(vbd_ctx *ctx, const vbd_params *params) {
+    if (!ctx || !params) return VBD_ERR_INVALID_ARG;
+    std::string why;
+    if (!params_ok(params, why)) return fail(ctx, VBD_ERR_INVALID_ARG, why);
+    if (ctx->bound && params->tape_steps != ctx->params.tape_steps)
+        return fail(ctx, VBD_ERR_STATE, "tape_steps changed: query the workspace size and bind again");
+    ctx->params = *params;
+    ctx->version++;
+    clear_graphs(ctx);
+    return VBD_OK;
+}
+
+static vbd_status check_bound(vbd_ctx *ctx) {
+    if (!ctx) return VBD_ERR_INVALID_ARG;
+    if (!ctx->colored) return fail(ctx, VBD_ERR_NOT_COLORED, "vbd_color has not run");
+    if (!ctx->bound) return fail(ctx, VBD_ERR_WORKSPACE, "no workspace bound");
+    return VBD_OK;
+}
+
+vbd_status vbd_set_state(vbd_ctx *ctx, const float *x, const float *v, const float *v_prev) {
+    vbd_status st = check_bound(ctx);
+    if (st != VBD_OK) return st;
+    if (!x || !v) return fail(ctx, VBD_ERR_INVALID_ARG, "x and v are required");
+    if (ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_set_state inside a step");
+    const size_t bytes = 12 * (size_t)ctx->N;
+    const float *src[3] = {x, v, v_prev ? v_prev : v};
+    float4 *dst[3] = {ctx->d.x, ctx->d.v, ctx->d.vprev};
+    for (int k = 0; k < 3; ++k) {
+        const float *from = src[k];
+        if (!is_device_ptr(from)) {
+            CU(cudaMemcpyAsync(ctx->d.stage[k], from, bytes, cudaMemcpyDefault, ctx->stream), "state upload");
+            from = ctx->d.stage[k];
+        }
+        vbd::launch_scatter(from, dst[k], ctx->d.new_of_orig, ctx->N, ctx->stream);
+    }
+    CU(cudaGetLastError(), "set_state");
+    ctx->tape_len = 0;
+    ctx->tape_h.clear();
+    return VBD_OK;
+}
+
+vbd_status vbd_get_state(vbd_ctx *ctx, float *x, float *v) {
+    vbd_status st = check_bound(ctx);
+    if (st != VBD_OK) return st;
+    const size_t bytes = 12 * (size_t)ctx->N;
+    float *dst[2] = {x, v};
+    const float4 *src[2] = {ctx->d.x, ctx->d.v};
+    bool host = false;
+    for (int k = 0; k < 2; ++k) {
+        if (!dst[k]) continue;
+        if (is_device_ptr(dst[k])) {
+            vbd::launch_gather(src[k], dst[k], ctx->d.new_of_orig, ctx->N, ctx->stream);
+        } else {
+            vbd::launch_gather(src[k], ctx->d.stage[k], ctx->d.new_of_orig, ctx->N, ctx->stream);
+            CU(cudaMemcpyAsync(dst[k], ctx->d.stage[k], bytes, cudaMemcpyDefault, ctx->stream), "state download");
+            host = true;
+        }
+    }
+    CU(cudaGetLastError(), "get_state");
+    if (host) CU(cudaStreamSynchronize(ctx->stream), "get_state sync");
+    return VBD_OK;
+}
+
+vbd_status vbd_set_log_young(vbd_ctx *ctx, const float *log_young) {
+    vbd_status st = check_bound(ctx);
+    if (st != VBD_OK) return st;
+    if (!log_young) return fail(ctx, VBD_ERR_INVALID_ARG, "log_young is NULL");
+    const float *src = log_young;
+    if (!is_device_ptr(src)) {
+        CU(cudaMemcpyAsync(ctx->d.stage[2], src, 4 * (size_t)ctx->T, cudaMemcpyDefault, ctx->stream),
+           "log_young upload");
+        src = ctx->d.stage[2];
+    }
+    vbd::launch_set_log_young(ctx->d, src, ctx->T, ctx->n_slots, ctx->stream);
+    CU(cudaGetLastError(), "set_log_young");
+    return VBD_OK;
+}
+
+vbd_status vbd_begin_step(vbd_ctx *ctx, float h) {
+    vbd_status st = check_bound(ctx);
+    if (st != VBD_OK) return st;
+    if (!(h > 0.f) || !std::isfinite(h)) return fail(ctx, VBD_ERR_INVALID_ARG, "h must be > 0");
+    if (ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_begin_step inside a step");
+    ctx->h = h;
+    ctx->iter_in_step = 0;
+    const float *g = ctx->params.gravity;
+    vbd::launch_predict(ctx->d, ctx->N, ctx->n_free, h, make_float3(g[0], g[1], g[2]), ctx->params.init_mode,
+                        ctx->params.cheby_rho > 0.f, ctx->stream);
+    CU(cudaGetLastError(), "predict");
+    ctx->in_step = true;
+    return VBD_OK;
+}
+
+vbd_status vbd_sweep_color(vbd_ctx *ctx, int32_t color) {
+    vbd_status st = check_bound(ctx);
+    if (st != VBD_OK) return st;
+    if (!ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_sweep_color outside a step");
+    if (color < 0 || color >= ctx->n_colors) return fail(ctx, VBD_ERR_INVALID_ARG, "colour out of range");
+    vbd::launch_sweep(ctx->d, sweep_params(ctx, color), ctx->lanes, ctx->block, ctx->stream);
+    CU(cudaGetLastError(), "sweep");
+    return VBD_OK;
+}
+
+vbd_status vbd_accelerate(vbd_ctx *ctx, int32_t n) {
+    vbd_status st = check_bound(ctx);
+    if (st != VBD_OK) return st;
+    if (!ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_accelerate outside a step");
+    if (n < 1) return fail(ctx, VBD_ERR_INVALID_ARG, "n must be >= 1");
+    if (!(ctx->params.cheby_rho > 0.f)) return VBD_OK;
+    vbd::launch_cheby(ctx->d, ctx->n_free, n, (float)cheby_omega(n, ctx->params.cheby_rho), ctx->stream);
+    CU(cudaGetLastError(), "cheby");
+    ctx->iter_in_step = n;
+    return VBD_OK;
+}
+
+vbd_status vbd_iterate(vbd_ctx *ctx, int32_t iters) {
+    vbd_status st = check_bound(ctx);
+    if (st != VBD_OK) return st;
+    if (!ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_iterate outside a step");
+    if (iters < 0) return fail(ctx, VBD_ERR_INVALID_ARG, "iters must be >= 0");
+    if (iters == 0) return VBD_OK;
+    const int first = ctx->iter_in_step;
+    if (!ctx->use_graph) {
+        enqueue_iterations(ctx, first, iters, ctx->stream);
+        CU(cudaGetLastError(), "iterate");
+    } else {
+        uint32_t hb;
+        std::memcpy(&hb, &ctx->h, 4);
+        cudaGraphExec_t exec = nullptr;
+        for (auto &g : ctx->graphs)
+            if (g.first_n == first && g.iters == iters && g.hbits == hb && g.version == ctx->version) exec = g.exec;
+        if (!exec) {
+            if (!ctx->capture_stream)
+                CU(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking), "capture stream");
+            cudaGraph_t graph = nullptr;
+            CU(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            enqueue_iterations(ctx, first, iters, ctx->capture_stream);
+            cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &graph);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+            if (ctx->graphs.size() >= 16) {
+                cudaGraphExecDestroy(ctx->graphs.front().exec);
+                ctx->graphs.erase(ctx->graphs.begin());
+            }
+            ctx->graphs.push_back({first, iters, hb, ctx->version, exec});
+        }
+        CU(cudaGraphLaunch(exec, ctx->stream), "graph launch");
+    }
+    ctx->iter_in_step = first + iters;
+    return VBD_OK;
+}
+
+vbd_status vbd_end_step(vbd_ctx *ctx) {
+    vbd_status st = check_bound(ctx);
+    if (st != VBD_OK) return st;
+    if (!ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_end_step outside a step");
+    float4 *row = nullptr;
+    if (ctx->params.tape_steps > 0 && ctx->tape_len < ctx->params.tape_steps) {
+        row = ctx->d.tape + (size_t)ctx->tape_len * ctx->N;
+        ctx->tape_len++;
+        ctx->tape_h.push_back(ctx->h);
+    }
+    vbd::launch_finish(ctx->d, ctx->N, ctx->h, row, ctx->stream);
+    CU(cudaGetLastError(), "finish");
+    ctx->in_step = false;
+    return VBD_OK;
+}
+
+vbd_status vbd_step(vbd_ctx *ctx, float h, int32_t iters) {
+    vbd_status st = vbd_begin_step(ctx, h);
+    if (st != VBD_OK) return st;
+    st = vbd_iterate(ctx, iters);
+    if (st != VBD_OK) {
+        ctx->in_step = false;
+        return st;
+    }
+    return vbd_end_step(ctx);
+}
+
+vbd_status vbd_energy(vbd_ctx *ctx, double *G_out) {
+    vbd_status st = check_bound(ctx);
+    if (st != VBD_OK) return st;
+    if (!G_out) return fail(ctx, VBD_ERR_INVALID_ARG, "G_out is NULL");
+    if (!(ctx->h > 0.f)) return fail(ctx, VBD_ERR_STATE, "no step has begun (y undefined)");
+    vbd::launch_energy(ctx->d, ctx->n_free, ctx->T, (double)ctx->h, sweep_params(ctx, -1), ctx->stream);
+    CU(cudaGetLastError(), "energy");
+    CU(cudaMemcpyAsync(G_out, ctx->d.energy_out, 8, cudaMemcpyDefault, ctx->stream), "energy download");
+    CU(cudaStreamSynchronize(ctx->stream), "energy sync");
+    return VBD_OK;
+}
+
+vbd_status vbd_sync_status(vbd_ctx *ctx, int64_t *det_skips, int64_t *contacts) {
+    vbd_status st = check_bound(ctx);
+    if (st != VBD_OK) return st;
+    unsigned long long c[8] = {0};
+    CU(cudaStreamSynchronize(ctx->stream), "sync");
+    CU(cudaMemcpy(c, ctx->d.counters, sizeof(c), cudaMemcpyDeviceToHost), "read counters");
+    CU(cudaMemsetAsync(ctx->d.counters, 0, sizeof(c), ctx->stream), "clear counters");
+    CU(cudaStreamSynchronize(ctx->stream), "sync");
+    if (det_skips) *det_skips = (int64_t)c[1];
+    if (contacts) *contacts = 0;
+    if (c[0] > 0) return fail(ctx, VBD_ERR_NONFINITE, std::to_string(c[0]) + " non-finite updates");
+    return VBD_OK;
+}
+
+vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, float *dL_dv0, int32_t adj_iters) {
+    vbd_status st = check_bound(ctx);
+    if (st != VBD_OK) return st;
+    if (!dL_dxT) return fail(ctx, VBD_ERR_INVALID_ARG, "dL_dxT is NULL");
+    if (adj_iters < 1) return fail(ctx, VBD_ERR_INVALID_ARG, "adj_iters must be >= 1");
+    if (ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_backward inside a step");
+    if (ctx->tape_len < 1) return fail(ctx, VBD_ERR_NO_TAPE, "no recorded steps (tape_steps = 0?)");
+    if (ctx->params.k_d != 0.f) return fail(ctx, VBD_ERR_INVALID_ARG, "the adjoint needs k_d = 0");
+    if (!is_device_ptr(dL_dxT) || (dL_dlogE && !is_device_ptr(dL_dlogE)) || (dL_dv0 && !is_device_ptr(dL_dv0)))
+        return fail(ctx, VBD_ERR_INVALID_ARG, "vbd_backward takes device pointers");
+    const Dev &d = ctx->d;
+    cudaStream_t s = ctx->stream;
+    const int N = ctx->N;
+    CU(cudaMemsetAsync(d.gtheta, 0, 4 * (size_t)ctx->T, s), "clear gtheta");
+    vbd::launch_adj_seed(d, dL_dxT, N, s);
+    const float h_saved = ctx->h;
+    for (int t = ctx->tape_len - 1; t >= 0; --t) {
+        const float h = ctx->tape_h[t];
+        ctx->h = h;
+        const float4 *xs = d.tape + (size_t)t * N;
+        vbd::launch_adj_rhs(d, N, ctx->n_free, 1.f / h, s);
+        for (int it = 0; it < adj_iters; ++it)
+            for (int col = 0; col < ctx->n_colors; ++col)
+                vbd::launch_adj_sweep(d, xs, sweep_params(ctx, col), ctx->lanes, ctx->block, s);
+        vbd::launch_adj_post(d, xs, N, ctx->n_free, ctx->T, h, s);
+    }
+    ctx->h = h_saved;
+    vbd::launch_adj_out(d, dL_dlogE, dL_dv0, N, ctx->T, s);
+    CU(cudaGetLastError(), "backward");
+    return VBD_OK;
+}
+
+vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_threads) {
+    if (!ctx) return VBD_ERR_INVALID_ARG;
+    if (lanes_per_vertex != 0 && lanes_per_vertex != 4 && lanes_per_vertex != 8 && lanes_per_vertex != 16 &&
+        lanes_per_vertex != 32)
+        return fail(ctx, VBD_ERR_INVALID_ARG, "lanes_per_vertex must be 4, 8, 16 or 32");
+    if (block_threads != 0 && block_threads != 64 && block_threads != 128 && block_threads != 256 &&
+        block_threads != 512)
+        return fail(ctx, VBD_ERR_INVALID_ARG, "block_threads must be 64, 128, 256 or 512");
+    if (block_threads == 512) return fail(ctx, VBD_ERR_INVALID_ARG, "block_threads 512 exceeds the kernel bound");
+    if (lanes_per_vertex) ctx->lanes = lanes_per_vertex;
+    if (block_threads) ctx->block = block_threads;
+    ctx->version++;
+    clear_graphs(ctx);
+    return VBD_OK;
+}
+
+vbd_status vbd_set_graph(vbd_ctx *ctx, int32_t enable) {
+    if (!ctx) return VBD_ERR_INVALID_ARG;
+    ctx->use_graph = enable != 0;
+    return VBD_OK;
+}
+
+vbd_status vbd_autotune(vbd_ctx *ctx, float h, int32_t iters, float *best_ms_per_iter) {
+    vbd_status st = check_bound(ctx);
+    if (st != VBD_OK) return st;
+    if (ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_autotune inside a step");
+    if (iters < 1) return fail(ctx, VBD_ERR_INVALID_ARG, "iters must be >= 1");
+    const int lanes_opts[] = {4, 8, 16, 32};
+    const int block_opts[] = {128, 256};
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0), "event");
+    CU(cudaEventCreate(&e1), "event");
+    const bool graph_saved = ctx->use_graph;
+    ctx->use_graph = false;
+    float best = 1e30f;
+    int best_l = ctx->lanes, best_b = ctx->block;
+    for (int l : lanes_opts)
+        for (int b : block_opts) {
+            ctx->lanes = l;
+            ctx->block = b;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2; ++rep) {  // first repetition warms up
+                vbd_begin_step(ctx, h);
+                cudaEventRecord(e0, ctx->stream);
+                vbd_iterate(ctx, iters);
+                cudaEventRecord(e1, ctx->stream);
+                ctx->in_step = false;
+                vbd::launch_restore_x(ctx->d, ctx->N, ctx->stream);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (ms < best) { best = ms; best_l = l; best_b = b; }
+        }
+    ctx->use_graph = graph_saved;
+    ctx->lanes = best_l;
+    ctx->block = best_b;
+    ctx->version++;
+    clear_graphs(ctx);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CU(cudaStreamSynchronize(ctx->stream), "autotune");
+    CU(cudaGetLastError(), "autotune");
+    if (best_ms_per_iter) *best_ms_per_iter = best / iters;
+    return VBD_OK;
+}
+
+const char *vbd_last_error(const vbd_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : "NULL context";
+}
+
+void vbd_destroy(vbd_ctx *ctx) {
+    if (!ctx) return;
+    clear_graphs(ctx);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    delete ctx;
+}
+
+}  // extern "C"

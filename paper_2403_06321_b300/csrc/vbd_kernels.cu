@@ -1,0 +1,429 @@
+// vbd_kernels.cu -- forward kernels of Vertex Block Descent for sm_103a.
+//
+// One time step (Algorithm 1) is
+//   k_predict            y (Eq. 2) and the initial guess (Sec. 3.7), once per step
+//   k_sweep<L>           one Gauss-Seidel pass over one colour (Sec. 3.1-3.9),
+//                        iters * n_colors launches per step -- the hot path
+//   k_cheby              Chebyshev update (Eqs. 12-13), once per iteration if enabled
+//   k_finish             v = (x - x^t)/h (Eq. 5), once per step
+//
+// The sweep is memory bound: per (vertex, incident tet) pair ("slot") it
+// streams 56 bytes of precomputed rest data once per iteration and gathers
+// three neighbour positions.  Slots of one colour are contiguous, so the
+// stream is fully sequential; L lanes of a warp cooperate on one vertex
+// (lanes stride over its slots), reduce f_i and H_i with xor shuffles in a
+// fixed order (deterministic), and one lane solves the 3x3 system.
+#include "vbd_kernels.h"
+
+#include <algorithm>
+#include <cstdio>
+
+namespace vbd {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) {
+    return make_float3(a.x - b.x, a.y - b.y, a.z - b.z);
+}
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// f_i and the symmetric H_i (upper triangle) accumulated over incident tets
+struct Acc {
+    float f0, f1, f2, h00, h01, h02, h11, h12, h22;
+};
+
+// Contribution of one tet to the vertex that owns slot s (Eqs. 7-8 with the
+// stable neo-Hookean element):  with e_k = x_k - x_i for the three other
+// vertices and their shape gradients g_k,
+//   F = sum_k e_k g_k^T,  g_i = -(g_a + g_b + g_c),  c = cof(F) g_i,
+//   f_i -= V P g_i = V mu F g_i + V lam (J - alpha) c,   (alpha lam = lam + mu)
+//   H_i += V mu |g_i|^2 I + V lam c c^T.
+__device__ __forceinline__ void accumulate_slot(const float4 *__restrict__ x, int4 r0, float4 r1,
+                                                float4 r2, float2 r3, float3 xi, Acc &acc) {
+    const float3 pa = f3(__ldg(x + r0.x));
+    const float3 pb = f3(__ldg(x + r0.y));
+    const float3 pc = f3(__ldg(x + r0.z));
+    const float Vmu = __int_as_float(r0.w);
+    const float Vlam = r3.y;
+    const float3 ga = make_float3(r1.x, r1.y, r1.z);
+    const float3 gb = make_float3(r1.w, r2.x, r2.y);
+    const float3 gc = make_float3(r2.z, r2.w, r3.x);
+    const float3 gi = make_float3(-(ga.x + gb.x + gc.x), -(ga.y + gb.y + gc.y), -(ga.z + gb.z + gc.z));
+    const float3 ea = pa - xi, eb = pb - xi, ec = pc - xi;
+    // columns of F: f_s = ea * ga[s] + eb * gb[s] + ec * gc[s]
+    const float3 f0 = make_float3(ea.x * ga.x + eb.x * gb.x + ec.x * gc.x,
+                                  ea.y * ga.x + eb.y * gb.x + ec.y * gc.x,
+                                  ea.z * ga.x + eb.z * gb.x + ec.z * gc.x);
+    const float3 f1 = make_float3(ea.x * ga.y + eb.x * gb.y + ec.x * gc.y,
+                                  ea.y * ga.y + eb.y * gb.y + ec.y * gc.y,
+                                  ea.z * ga.y + eb.z * gb.y + ec.z * gc.y);
+    const float3 f2 = make_float3(ea.x * ga.z + eb.x * gb.z + ec.x * gc.z,
+                                  ea.y * ga.z + eb.y * gb.z + ec.y * gc.z,
+                                  ea.z * ga.z + eb.z * gb.z + ec.z * gc.z);
+    const float3 c0 = cross(f1, f2), c1 = cross(f2, f0), c2 = cross(f0, f1);
+    const float J = dot(f0, c0);
+    const float3 c = make_float3(gi.x * c0.x + gi.y * c1.x + gi.z * c2.x,
+                                 gi.x * c0.y + gi.y * c1.y + gi.z * c2.y,
+                                 gi.x * c0.z + gi.y * c1.z + gi.z * c2.z);
+    const float3 Fg = make_float3(gi.x * f0.x + gi.y * f1.x + gi.z * f2.x,
+                                  gi.x * f0.y + gi.y * f1.y + gi.z * f2.y,
+                                  gi.x * f0.z + gi.y * f1.z + gi.z * f2.z);
+    const float k = Vlam * J - (Vlam + Vmu);
+    acc.f0 -= Vmu * Fg.x + k * c.x;
+    acc.f1 -= Vmu * Fg.y + k * c.y;
+    acc.f2 -= Vmu * Fg.z + k * c.z;
+    const float d = Vmu * dot(gi, gi);
+    acc.h00 += d + Vlam * c.x * c.x;
+    acc.h11 += d + Vlam * c.y * c.y;
+    acc.h22 += d + Vlam * c.z * c.z;
+    acc.h01 += Vlam * c.x * c.y;
+    acc.h02 += Vlam * c.x * c.z;
+    acc.h12 += Vlam * c.y * c.z;
+}
+
+template <int L>
+__device__ __forceinline__ float sub_reduce(float v) {
+#pragma unroll
+    for (int off = L / 2; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    return v;
+}
+
+// Local solve of Sec. 3.2 for one vertex: inertia (Eqs. 7-8), damping
+// (Eqs. 9-10), ground penalty (Eq. 11), singular skip, analytic inverse.
+__device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams &p, int vi, float4 xi,
+                                                const Acc &a) {
+    const float4 yv = d.ym[vi];
+    const float mh2 = yv.w;
+    const float kdh = p.kd_over_h;
+    float f0 = mh2 * (yv.x - xi.x) + a.f0;
+    float f1 = mh2 * (yv.y - xi.y) + a.f1;
+    float f2 = mh2 * (yv.z - xi.z) + a.f2;
+    const float s = 1.0f + kdh;
+    float h00 = s * a.h00 + mh2, h11 = s * a.h11 + mh2, h22 = s * a.h22 + mh2;
+    float h01 = s * a.h01, h02 = s * a.h02, h12 = s * a.h12;
+    if (kdh != 0.0f) {
+        const float4 xt = d.xt[vi];
+        const float dx = xi.x - xt.x, dy = xi.y - xt.y, dz = xi.z - xt.z;
+        f0 -= kdh * (a.h00 * dx + a.h01 * dy + a.h02 * dz);
+        f1 -= kdh * (a.h01 * dx + a.h11 * dy + a.h12 * dz);
+        f2 -= kdh * (a.h02 * dx + a.h12 * dy + a.h22 * dz);
+    }
+    float flag = xi.w;
+    if (p.ground_on) {
+        const float pen = p.gh - (p.gn.x * xi.x + p.gn.y * xi.y + p.gn.z * xi.z);
+        if (pen > 0.0f) {
+            const float kd = p.kc * pen;
+            f0 += kd * p.gn.x; f1 += kd * p.gn.y; f2 += kd * p.gn.z;
+            h00 += p.kc * p.gn.x * p.gn.x; h11 += p.kc * p.gn.y * p.gn.y; h22 += p.kc * p.gn.z * p.gn.z;
+            h01 += p.kc * p.gn.x * p.gn.y; h02 += p.kc * p.gn.x * p.gn.z; h12 += p.kc * p.gn.y * p.gn.z;
+            flag = 1.0f;
+        }
+    }
+    // adjugate of the symmetric H
+    const float a00 = h11 * h22 - h12 * h12;
+    const float a01 = h02 * h12 - h01 * h22;
+    const float a02 = h01 * h12 - h02 * h11;
+    const float a11 = h00 * h22 - h02 * h02;
+    const float a12 = h01 * h02 - h00 * h12;
+    const float a22 = h00 * h11 - h01 * h01;
+    const float det = h00 * a00 + h01 * a01 + h02 * a02;
+    const float tr3 = (h00 + h11 + h22) * (1.0f / 3.0f);
+    if (!(fabsf(det) > p.det_eps * fabsf(tr3 * tr3 * tr3))) {
+        atomicAdd(d.counters + 1, 1ull);
+        if (flag != xi.w) d.x[vi] = make_float4(xi.x, xi.y, xi.z, flag);
+        return;
+    }
+    const float inv = 1.0f / det;
+    const float dx = (a00 * f0 + a01 * f1 + a02 * f2) * inv;
+    const float dy = (a01 * f0 + a11 * f1 + a12 * f2) * inv;
+    const float dz = (a02 * f0 + a12 * f1 + a22 * f2) * inv;
+    if (!(isfinite(dx) && isfinite(dy) && isfinite(dz))) {
+        atomicAdd(d.counters + 0, 1ull);
+        return;
+    }
+    d.x[vi] = make_float4(xi.x + dx, xi.y + dy, xi.z + dz, flag);
+}
+
+template <int L>
+__global__ void __launch_bounds__(256) k_sweep(Dev d, SweepParams p) {
+    const int lane = threadIdx.x & (L - 1);
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int vi = p.vbegin + (int)(gt / L);
+    const bool active = vi < p.vend;
+    float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
+    int s0 = 0, s1 = 0;
+    if (active) {
+        xi = d.x[vi];
+        s0 = d.slot_off[vi];
+        s1 = d.slot_off[vi + 1];
+    }
+    const float3 x3 = f3(xi);
+    Acc acc = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int s = s0 + lane; s < s1; s += L) {
+        const int4 r0 = __ldcs(d.s0 + s);
+        const float4 r1 = __ldcs(d.s1 + s);
+        const float4 r2 = __ldcs(d.s2 + s);
+        const float2 r3 = __ldcs(d.s3 + s);
+        accumulate_slot(d.x, r0, r1, r2, r3, x3, acc);
+    }
+    acc.f0 = sub_reduce<L>(acc.f0);
+    acc.f1 = sub_reduce<L>(acc.f1);
+    acc.f2 = sub_reduce<L>(acc.f2);
+    acc.h00 = sub_reduce<L>(acc.h00);
+    acc.h01 = sub_reduce<L>(acc.h01);
+    acc.h02 = sub_reduce<L>(acc.h02);
+    acc.h11 = sub_reduce<L>(acc.h11);
+    acc.h12 = sub_reduce<L>(acc.h12);
+    acc.h22 = sub_reduce<L>(acc.h22);
+    if (active && lane == 0) solve_and_store(d, p, vi, xi, acc);
+}
+
+// Eq. 2 and Sec. 3.7 (a)-(d).  Pinned vertices (ids >= n_free) keep x^t.
+__global__ void k_predict(Dev d, int n, int n_free, float h, float3 g, float gnorm, int mode,
+                          int cheby) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 xi = d.x[i];
+    d.xt[i] = make_float4(xi.x, xi.y, xi.z, 0.f);
+    if (i >= n_free) {
+        d.x[i] = make_float4(xi.x, xi.y, xi.z, 0.f);
+        return;
+    }
+    const float4 vi = d.v[i];
+    const float h2 = h * h;
+    d.ym[i] = make_float4(xi.x + h * vi.x + h2 * g.x, xi.y + h * vi.y + h2 * g.y,
+                          xi.z + h * vi.z + h2 * g.z, d.mass[i] / h2);
+    float4 xn;
+    if (mode == 0) {
+        xn = make_float4(xi.x, xi.y, xi.z, 0.f);
+    } else {
+        float at = (mode == 2) ? 1.f : 0.f;
+        if (mode == 3 && gnorm > 0.f) {
+            const float4 wi = d.vprev[i];
+            const float comp = ((vi.x - wi.x) / h * g.x + (vi.y - wi.y) / h * g.y +
+                                (vi.z - wi.z) / h * g.z) / gnorm;
+            at = comp > gnorm ? 1.f : (comp < 0.f ? 0.f : comp / gnorm);
+        }
+        const float ah2 = h2 * at;
+        xn = make_float4(xi.x + h * vi.x + ah2 * g.x, xi.y + h * vi.y + ah2 * g.y,
+                         xi.z + h * vi.z + ah2 * g.z, 0.f);
+    }
+    d.x[i] = xn;
+    if (cheby) d.cheb[0][i] = xn;
+}
+
+// Eq. 12 after iteration n: history buffer cheb[n & 1] holds x^(n-2) on entry
+// and x^(n) on exit; the other buffer holds x^(n-1).  Vertices flagged in
+// ground contact (x.w != 0) keep the Gauss-Seidel result.
+__global__ void k_cheby(Dev d, int n_free, int n, float omega) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_free) return;
+    float4 *hist = d.cheb[n & 1];
+    const float4 xb = d.x[i];
+    float4 xn = xb;
+    if (n >= 2 && xb.w == 0.f) {
+        const float4 q = hist[i];
+        xn = make_float4(omega * (xb.x - q.x) + q.x, omega * (xb.y - q.y) + q.y,
+                         omega * (xb.z - q.z) + q.z, xb.w);
+        d.x[i] = xn;
+    }
+    hist[i] = xn;
+}
+
+// Eq. 5; v^{t-1} <- v^t; optional tape row.
+__global__ void k_finish(Dev d, int n, float h, float4 *tape_row) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 x = d.x[i], xt = d.xt[i];
+    d.vprev[i] = d.v[i];
+    d.v[i] = make_float4((x.x - xt.x) / h, (x.y - xt.y) / h, (x.z - xt.z) / h, 0.f);
+    if (tape_row) tape_row[i] = make_float4(x.x, x.y, x.z, 0.f);
+    if (!(isfinite(x.x) && isfinite(x.y) && isfinite(x.z))) atomicAdd(d.counters + 0, 1ull);
+}
+
+__global__ void k_scatter(const float *src, float4 *dst, const int *new_of_orig, int n) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    dst[new_of_orig[o]] = make_float4(src[3 * o], src[3 * o + 1], src[3 * o + 2], 0.f);
+}
+
+__global__ void k_gather(const float4 *src, float *dst, const int *new_of_orig, int n) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    const float4 a = src[new_of_orig[o]];
+    dst[3 * o] = a.x;
+    dst[3 * o + 1] = a.y;
+    dst[3 * o + 2] = a.z;
+}
+
+__global__ void k_restore_x(Dev d, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) d.x[i] = d.xt[i];
+}
+
+// ---- FP64 energy of Eq. 1 (diagnostics) -----------------------------------
+constexpr int EB = 256;
+
+__device__ __forceinline__ void block_sum_store(double v, double *out) {
+    __shared__ double sh[EB / 32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < EB / 32; ++w) t += sh[w];
+        *out = t;
+    }
+}
+
+__global__ void __launch_bounds__(EB) k_energy_verts(Dev d, int n_free, double inv_2h2, SweepParams p,
+                                                     double *partials) {
+    double e = 0.0;
+    for (int i = blockIdx.x * EB + threadIdx.x; i < n_free; i += gridDim.x * EB) {
+        const float4 x = d.x[i], y = d.ym[i];
+        const double dx = (double)x.x - y.x, dy = (double)x.y - y.y, dz = (double)x.z - y.z;
+        e += (double)d.mass[i] * inv_2h2 * (dx * dx + dy * dy + dz * dz);
+        if (p.ground_on) {
+            const double pen = (double)p.gh - ((double)p.gn.x * x.x + (double)p.gn.y * x.y +
+                                               (double)p.gn.z * x.z);
+            if (pen > 0.0) e += 0.5 * (double)p.kc * pen * pen;
+        }
+    }
+    block_sum_store(e, partials + blockIdx.x);
+}
+
+__global__ void __launch_bounds__(EB) k_energy_tets(Dev d, int n_tets, double *partials) {
+    double e = 0.0;
+    for (int j = blockIdx.x * EB + threadIdx.x; j < n_tets; j += gridDim.x * EB) {
+        const int4 t = d.tet_v[j];
+        const float4 p0 = d.x[t.x], p1 = d.x[t.y], p2 = d.x[t.z], p3 = d.x[t.w];
+        const double D[3][3] = {{(double)p1.x - p0.x, (double)p2.x - p0.x, (double)p3.x - p0.x},
+                                {(double)p1.y - p0.y, (double)p2.y - p0.y, (double)p3.y - p0.y},
+                                {(double)p1.z - p0.z, (double)p2.z - p0.z, (double)p3.z - p0.z}};
+        const float *B = d.tet_B + 9 * (size_t)j;
+        double F[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int s = 0; s < 3; ++s)
+                F[r][s] = D[r][0] * B[s] + D[r][1] * B[3 + s] + D[r][2] * B[6 + s];
+        const double J = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) -
+                         F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +
+                         F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
+        double ic = 0.0;
+        for (int r = 0; r < 3; ++r)
+            for (int s = 0; s < 3; ++s) ic += F[r][s] * F[r][s];
+        const double mu = d.tet_mu[j], lam = d.tet_lam[j];
+        const double alpha = 1.0 + mu / lam;
+        e += (double)d.tet_V[j] * (0.5 * mu * (ic - 3.0) + 0.5 * lam * (J - alpha) * (J - alpha));
+    }
+    block_sum_store(e, partials + blockIdx.x);
+}
+
+__global__ void k_reduce_partials(const double *partials, int n, double *out) {
+    double e = 0.0;
+    for (int i = threadIdx.x; i < n; i += EB) e += partials[i];
+    block_sum_store(e, out);
+}
+
+__global__ void k_set_log_young(Dev d, const float *log_young, int n_tets, long long n_slots) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_tets) {
+        const float E = expf(log_young[i]);
+        const float nu = d.tet_nu[i];
+        const float mu = E / (2.f * (1.f + nu));
+        d.tet_mu[i] = mu;
+        d.tet_lam[i] = E * nu / ((1.f + nu) * (1.f - 2.f * nu)) + mu;
+    }
+    if (i < n_slots) {
+        const int j = d.slot_tet[i];
+        const float E = expf(log_young[j]);
+        const float nu = d.tet_nu[j];
+        const float V = d.tet_V[j];
+        const float mu = E / (2.f * (1.f + nu));
+        const float lam = E * nu / ((1.f + nu) * (1.f - 2.f * nu)) + mu;
+        d.s0[i].w = __float_as_int(V * mu);
+        d.s3[i].y = V * lam;
+    }
+}
+
+inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+int num_sms() {
+    int dev = 0, n = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+}
+
+void launch_predict(const Dev &d, int n, int n_free, float h, float3 g, int init_mode, bool cheby,
+                    cudaStream_t s) {
+    const float gnorm = sqrtf(g.x * g.x + g.y * g.y + g.z * g.z);
+    k_predict<<<blocks_for(n, 256), 256, 0, s>>>(d, n, n_free, h, g, gnorm, init_mode, cheby ? 1 : 0);
+}
+
+void launch_sweep(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s) {
+    const long long threads = (long long)(p.vend - p.vbegin) * lanes;
+    if (threads <= 0) return;
+    const unsigned grid = blocks_for(threads, block);
+    switch (lanes) {
+    case 4: k_sweep<4><<<grid, block, 0, s>>>(d, p); break;
+    case 8: k_sweep<8><<<grid, block, 0, s>>>(d, p); break;
+    case 16: k_sweep<16><<<grid, block, 0, s>>>(d, p); break;
+    default: k_sweep<32><<<grid, block, 0, s>>>(d, p); break;
+    }
+}
+
+void launch_cheby(const Dev &d, int n_free, int n, float omega, cudaStream_t s) {
+    if (n_free > 0) k_cheby<<<blocks_for(n_free, 256), 256, 0, s>>>(d, n_free, n, omega);
+}
+
+void launch_finish(const Dev &d, int n, float h, float4 *tape_row, cudaStream_t s) {
+    k_finish<<<blocks_for(n, 256), 256, 0, s>>>(d, n, h, tape_row);
+}
+
+void launch_scatter(const float *src, float4 *dst, const int *new_of_orig, int n, cudaStream_t s) {
+    k_scatter<<<blocks_for(n, 256), 256, 0, s>>>(src, dst, new_of_orig, n);
+}
+
+void launch_gather(const float4 *src, float *dst, const int *new_of_orig, int n, cudaStream_t s) {
+    k_gather<<<blocks_for(n, 256), 256, 0, s>>>(src, dst, new_of_orig, n);
+}
+
+void launch_restore_x(const Dev &d, int n, cudaStream_t s) {
+    k_restore_x<<<blocks_for(n, 256), 256, 0, s>>>(d, n);
+}
+
+static void energy_grid(int n_free, int n_tets, int *gv, int *gt) {
+    const int cap = 4 * 148;
+    *gv = (int)std::min<long long>(cap, std::max<long long>(1, blocks_for(n_free, EB)));
+    *gt = (int)std::min<long long>(cap, std::max<long long>(1, blocks_for(n_tets, EB)));
+}
+
+int energy_partials_needed(int n_free, int n_tets) {
+    int gv, gt;
+    energy_grid(n_free, n_tets, &gv, &gt);
+    return gv + gt;
+}
+
+void launch_energy(const Dev &d, int n_free, int n_tets, double h, const SweepParams &p, cudaStream_t s) {
+    int gv, gt;
+    energy_grid(n_free, n_tets, &gv, &gt);
+    k_energy_verts<<<gv, EB, 0, s>>>(d, n_free, 1.0 / (2.0 * h * h), p, d.partials);
+    k_energy_tets<<<gt, EB, 0, s>>>(d, n_tets, d.partials + gv);
+    k_reduce_partials<<<1, EB, 0, s>>>(d.partials, gv + gt, d.energy_out);
+}
+
+void launch_set_log_young(const Dev &d, const float *log_young, int n_tets, long long n_slots,
+                          cudaStream_t s) {
+    const long long n = std::max<long long>(n_tets, n_slots);
+    k_set_log_young<<<blocks_for(n, 256), 256, 0, s>>>(d, log_young, n_tets, n_slots);
+}
+
+}  // namespace vbd

@@ -1,0 +1,79 @@
+// vbd_kernels.h -- device data layout and kernel launchers of the VBD library
+// (internal; the public boundary is include/vbd.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vbd {
+
+// Device arrays, all carved out of the caller's workspace.  Vertices are in
+// colour-major order: free vertices of colour 0, colour 1, ..., then pinned
+// vertices.  Tets keep the caller's order.
+struct Dev {
+    float4 *x;        // current positions; .w = 1 once the vertex touched the ground this step
+    float4 *xt;       // x^t (start of step)
+    float4 *v;        // v^t
+    float4 *vprev;    // v^{t-1}
+    float4 *ym;       // inertia target y (Eq. 2) in .xyz, m_i / h^2 in .w
+    float4 *cheb[2];  // Chebyshev history (Eq. 12), roles alternate with iteration parity
+    float *mass;      // lumped mass
+    int *slot_off;    // n_free + 1: slots of free vertex i are [slot_off[i], slot_off[i+1])
+    // incidence slots (one per (free vertex, incident tet)), 56 bytes each:
+    int4 *s0;         // other three vertex ids, bits of V*mu
+    float4 *s1;       // g_a.xyz, g_b.x
+    float4 *s2;       // g_b.yz, g_c.xy
+    float2 *s3;       // g_c.z, V*lambda
+    int *slot_tet;    // caller tet id of each slot
+    int *slot_loc;    // local index (0..3) of the slot's own vertex in that tet
+    // per tet (caller order)
+    int4 *tet_v;      // vertex ids (internal numbering)
+    float *tet_B;     // 9 per tet: inverse rest edge matrix, row-major
+    float *tet_V, *tet_nu, *tet_mu, *tet_lam;
+    int *new_of_orig; // N
+    float *stage[3];  // 3N each, state exchange with caller order
+    unsigned long long *counters;  // [0] non-finite updates, [1] det skips
+    double *partials; // energy partial sums
+    double *energy_out;
+    float4 *tape;     // tape_steps * N positions
+    // adjoint
+    float4 *lam, *rhs, *xbar, *vbar;
+    float *gtheta;    // T
+};
+
+struct SweepParams {
+    int vbegin, vend;
+    float3 gn;        // unit ground normal
+    float gh, kc;     // ground height, collision stiffness
+    int ground_on;
+    float det_eps;
+    float kd_over_h;  // Rayleigh damping k_d / h
+    float inv_h2;     // 1/h^2 (adjoint only)
+};
+
+int num_sms();
+
+void launch_predict(const Dev &d, int n, int n_free, float h, float3 g, int init_mode,
+                    bool cheby, cudaStream_t s);
+void launch_sweep(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s);
+void launch_cheby(const Dev &d, int n_free, int n, float omega, cudaStream_t s);
+void launch_finish(const Dev &d, int n, float h, float4 *tape_row, cudaStream_t s);
+void launch_scatter(const float *src, float4 *dst, const int *new_of_orig, int n, cudaStream_t s);
+void launch_gather(const float4 *src, float *dst, const int *new_of_orig, int n, cudaStream_t s);
+void launch_restore_x(const Dev &d, int n, cudaStream_t s);
+void launch_energy(const Dev &d, int n_free, int n_tets, double h, const SweepParams &p,
+                   cudaStream_t s);
+int energy_partials_needed(int n_free, int n_tets);
+void launch_set_log_young(const Dev &d, const float *log_young, int n_tets, long long n_slots,
+                          cudaStream_t s);
+
+// adjoint
+void launch_adj_rhs(const Dev &d, int n, int n_free, float inv_h, cudaStream_t s);
+void launch_adj_sweep(const Dev &d, const float4 *xs, const SweepParams &p, int lanes, int block,
+                      cudaStream_t s);
+void launch_adj_post(const Dev &d, const float4 *xs, int n, int n_free, int n_tets, float h,
+                     cudaStream_t s);
+void launch_adj_seed(const Dev &d, const float *dL_dx, int n, cudaStream_t s);
+void launch_adj_out(const Dev &d, float *dL_dlogE, float *dL_dv0, int n, int n_tets,
+                    cudaStream_t s);
+
+}  // namespace vbd

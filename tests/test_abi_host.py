@@ -1,0 +1,131 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, it
+exports every entry point include/vbd.h declares, and its host logic
+(mesh validation, colouring, workspace sizing) behaves as documented."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2403_06321_b300 import synth, vbd
+from paper_2403_06321_b300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return vbd.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "vbd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(vbd_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_entry_point_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(vbd.ENTRY_POINTS) == names
+
+
+def _create(m, **kw):
+    arr = vbd.MeshArrays(m.rest, m.tets, m.young, m.poisson, m.density, m.pinned)
+    return vbd.vbd_create_mesh(arr.desc(), vbd.make_params(**kw))
+
+
+def test_create_rejects_bad_meshes(lib):
+    m = synth.beam(2, 1, 1)
+    bad = synth.beam(2, 1, 1)
+    bad.tets = bad.tets.copy()
+    bad.tets[3, 2] = m.n_verts  # out of range
+    with pytest.raises(vbd.VbdError) as e:
+        _create(bad)
+    assert e.value.status == "VBD_ERR_BAD_MESH"
+    deg = synth.beam(2, 1, 1)
+    deg.rest = deg.rest.copy()
+    t = deg.tets[0]
+    deg.rest[t[3]] = deg.rest[t[0]] + 0.5 * (deg.rest[t[1]] - deg.rest[t[0]])  # collinear -> flat tet
+    with pytest.raises(vbd.VbdError) as e:
+        _create(deg)
+    assert e.value.status == "VBD_ERR_BAD_MESH"
+    mat = synth.beam(2, 1, 1, nu=0.5)
+    with pytest.raises(vbd.VbdError) as e:
+        _create(mat)
+    assert e.value.status == "VBD_ERR_BAD_MESH"
+    with pytest.raises(vbd.VbdError) as e:
+        _create(m, cheby_rho=1.5)
+    assert e.value.status == "VBD_ERR_INVALID_ARG"
+
+
+def test_colouring_matches_oracle_greedy_and_validates(lib, orc):
+    for dims in [(10, 3, 3), (5, 4, 3)]:
+        m = synth.beam(*dims)
+        ctx = _create(m)
+        try:
+            nc = vbd.vbd_color(ctx, None)
+            ours = vbd.vbd_get_colors(ctx, m.n_verts)
+            ref, nref = orc.color_greedy(m.n_verts, m.tets)
+            assert nc == nref
+            assert np.array_equal(ours, ref)
+            assert orc.color_valid(m.n_verts, m.tets, ours)
+            # the Kuhn closed-form colouring is accepted as given
+            kc = synth.kuhn_coloring(m.grid_ijk)
+            assert vbd.vbd_color(ctx, kc) == 4
+            assert np.array_equal(vbd.vbd_get_colors(ctx, m.n_verts), kc)
+            bad = kc.copy()
+            bad[m.tets[7, 0]] = bad[m.tets[7, 1]]
+            with pytest.raises(vbd.VbdError) as e:
+                vbd.vbd_color(ctx, bad)
+            assert e.value.status == "VBD_ERR_BAD_COLORING"
+        finally:
+            vbd.vbd_destroy(ctx)
+
+
+def test_info_workspace_and_call_order(lib):
+    m = synth.cantilever_beam()[0]
+    ctx = _create(m)
+    try:
+        with pytest.raises(vbd.VbdError) as e:
+            vbd.vbd_workspace_size(ctx)
+        assert e.value.status == "VBD_ERR_NOT_COLORED"
+        vbd.vbd_color(ctx, synth.kuhn_coloring(m.grid_ijk))
+        info = vbd.vbd_get_info(ctx)
+        assert (info.n_verts, info.n_tets, info.n_colors) == (176, 540, 4)
+        assert info.n_free == 176 - 16
+        # every (free vertex, tet) incidence is one slot
+        assert info.n_slots == int(sum((m.tets == i).sum() for i in np.nonzero(m.pinned == 0)[0]))
+        size = vbd.vbd_workspace_size(ctx)
+        assert size % 256 == 0 and size > 56 * info.n_slots
+        # a host pointer is not a workspace; stepping before binding is refused
+        buf = np.zeros(size // 4 + 64, np.float32)
+        with pytest.raises(vbd.VbdError) as e:
+            vbd.vbd_bind(ctx, buf.ctypes.data, size, 0)
+        assert e.value.status == "VBD_ERR_WORKSPACE"
+        with pytest.raises(vbd.VbdError) as e:
+            vbd.vbd_step(ctx, 1 / 60, 5)
+        assert e.value.status == "VBD_ERR_WORKSPACE"
+        with pytest.raises(vbd.VbdError) as e:
+            vbd.vbd_set_launch(ctx, 3, 0)
+        assert e.value.status == "VBD_ERR_INVALID_ARG"
+    finally:
+        vbd.vbd_destroy(ctx)
+
+
+def test_batched_union_rejects_cross_mesh_tets(lib):
+    ms = [synth.beam(2, 1, 1), synth.beam(3, 1, 1)]
+    cat, voff, toff = synth.concat(ms)
+    arr = vbd.MeshArrays(cat.rest, cat.tets, cat.young, cat.poisson, cat.density, cat.pinned, voff, toff)
+    ctx = vbd.vbd_create_mesh(arr.desc(), vbd.make_params())
+    assert vbd.vbd_get_info(ctx).n_meshes == 2
+    vbd.vbd_destroy(ctx)
+    tets = cat.tets.copy()
+    tets[0, 0] = voff[1]  # a tet of mesh 0 that reaches into mesh 1
+    arr = vbd.MeshArrays(cat.rest, tets, cat.young, cat.poisson, cat.density, cat.pinned, voff, toff)
+    with pytest.raises(vbd.VbdError) as e:
+        vbd.vbd_create_mesh(arr.desc(), vbd.make_params())
+    assert e.value.status in ("VBD_ERR_BAD_MESH",)

@@ -1,0 +1,82 @@
+"""Parity at the full size of the benchmark workload (100^3 cubes, 1,030,301
+vertices, 6,000,000 tets, ground penalty 1e7) in the launch configuration
+bench.py times.  The oracle cannot run whole steps at this size in seconds,
+so it checks (a) sampled vertices of the first colour pass one by one, each
+an exact function of the seeded input state, and (b) a property that holds
+at any size: without contact, no colour pass raises the FP64 energy G."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2403_06321_b300 import synth, vbd
+from gpu_util import bbox_diag, params_of
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def big():
+    from paper_2403_06321_b300.build import build
+    build()
+    m, cfg = synth.large_cube(100)
+    x0, v0 = synth.perturbed_state(m.rest, 0.0005, 0.5, seed=31)
+    # float32-representable so both sides read the same numbers
+    x0 = x0.astype(np.float32).astype(np.float64)
+    v0 = v0.astype(np.float32).astype(np.float64)
+    return m, cfg, x0, v0
+
+
+def test_first_colour_pass_sampled(orc, big):
+    m, cfg, x0, v0 = big
+    colors = synth.kuhn_coloring(m.grid_ijk)
+    pd = params_of(cfg)
+    sim = vbd.Sim(m, vbd.make_params(**pd), colors=colors)
+    try:
+        sim.set_state(x0, v0)
+        vbd.vbd_begin_step(sim.ctx, cfg.h)
+        vbd.vbd_sweep_color(sim.ctx, 0)
+        xg, _ = sim.get_state()
+        xg = xg.cpu().numpy().astype(np.float64)
+        vbd.vbd_end_step(sim.ctx)
+        sim.sync_status()
+    finally:
+        sim.close()
+    model = orc.Model.from_mesh(m)
+    p = orc.Params.make(**pd)
+    y = model.inertia_target(p, cfg.h, x0, v0)
+    xi = model.initial_guess(p, cfg.h, x0, v0, v0)
+    rng = np.random.default_rng(32)
+    c0 = np.nonzero(colors == 0)[0]
+    others = np.nonzero(colors != 0)[0]
+    diag = bbox_diag(m.rest)
+    worst = 0.0
+    for i in rng.choice(c0, 400, replace=False):
+        dx, skipped, _ = model.vertex_solve(p, cfg.h, i, xi, y, x0)
+        assert skipped == 0
+        worst = max(worst, float(np.abs(xg[i] - (xi[i] + dx)).max()))
+    for i in rng.choice(others, 200, replace=False):
+        worst = max(worst, float(np.abs(xg[i] - xi[i]).max()))
+    print("large cube first pass: worst |x_gpu - x_oracle| / bbox = %.3e" % (worst / diag))
+    assert worst <= 1e-6 * diag
+
+
+def test_energy_never_rises_per_pass(big):
+    m, cfg, x0, v0 = big
+    pd = params_of(cfg)  # the cube starts 0.5 m above the ground: no contact
+    sim = vbd.Sim(m, vbd.make_params(**pd), colors=synth.kuhn_coloring(m.grid_ijk))
+    try:
+        sim.set_state(x0, v0)
+        vbd.vbd_begin_step(sim.ctx, cfg.h)
+        G = [sim.energy()]
+        for it in range(2):
+            for c in range(4):
+                vbd.vbd_sweep_color(sim.ctx, c)
+                G.append(sim.energy())
+        vbd.vbd_end_step(sim.ctx)
+        sim.sync_status()
+    finally:
+        sim.close()
+    G = np.array(G)
+    print("large cube G per pass:", G)
+    assert np.all(np.diff(G) <= 1e-9 * np.abs(G[:-1]))
+    assert G[-1] < G[0]

@@ -1,0 +1,146 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the
+same seeded inputs and the same colouring.  Tolerance: FP32 positions
+within 1e-5 of the bounding-box diagonal of the FP64 oracle's, the bar the
+method's FP32 GPU / FP64 CPU comparison is held to."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2403_06321_b300 import synth, vbd
+from gpu_util import bbox_diag, gpu_run, oracle_run, params_of
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5  # x bbox diagonal
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2403_06321_b300.build import build
+    build()
+    assert torch.cuda.is_available()
+
+
+def _err(xg, xo, ref):
+    return float(np.abs(xg - xo).max() / bbox_diag(ref))
+
+
+@pytest.mark.parametrize("coloring", ["kuhn", "greedy"])
+def test_cantilever_beam_100_steps(orc, coloring):
+    """10x3x3 beam, x=0 face pinned, E=1e5, nu=0.4, h=1/60, 20 iters, 100 steps."""
+    m, cfg = synth.cantilever_beam()
+    colors = synth.kuhn_coloring(m.grid_ijk) if coloring == "kuhn" else orc.color_greedy(m.n_verts, m.tets)[0]
+    pd = params_of(cfg)
+    xg, vg = gpu_run(m, pd, colors, cfg.h, cfg.iters, cfg.steps)
+    xo, vo = oracle_run(orc, m, pd, colors, cfg.h, cfg.iters, cfg.steps)
+    err = _err(xg, xo, m.rest)
+    print("cantilever %s: max |x_gpu - x_oracle| / bbox = %.3e" % (coloring, err))
+    assert err <= TOL
+    assert np.abs(xo - m.rest).max() > 0.01  # the beam really sags
+    assert np.abs(vg - vo).max() <= TOL * bbox_diag(m.rest) / cfg.h * 10
+
+
+def test_one_iteration_from_perturbed_state_ragged(orc):
+    """13x5x3 jittered beam (several blocks, ragged colour ranges), seeded
+    deformed state and velocities: one iteration of every colour."""
+    m = synth.beam(13, 5, 3, edge=0.05, E=3e5, nu=0.42, jitter_frac=0.1, seed=11)
+    x0, v0 = synth.perturbed_state(m.rest, 0.004, 0.3, seed=12)
+    x0[m.pinned == 1] = m.rest[m.pinned == 1]
+    colors, _ = orc.color_greedy(m.n_verts, m.tets)
+    pd = params_of(synth.SimConfig())
+    for lanes in (4, 8, 16, 32):
+        xg, vg = gpu_run(m, pd, colors, 1 / 60, 1, 1, x0, v0, lanes=lanes)
+        xo, vo = oracle_run(orc, m, pd, colors, 1 / 60, 1, 1, x0, v0)
+        assert _err(xg, xo, m.rest) <= 1e-6, lanes
+
+
+def test_ground_contact_and_chebyshev(orc):
+    """Jittered 4x4x3 block falling onto the ground (k_c = 1e5), Chebyshev
+    rho = 0.9 with the colliding-vertex skip, 30 steps of 15 iterations."""
+    m = synth.beam(4, 4, 3, edge=0.05, E=2e5, nu=0.4, pin_face=None, jitter_frac=0.1, seed=13,
+                   origin=(0.0, 0.0, 0.02))
+    colors, _ = orc.color_greedy(m.n_verts, m.tets)
+    for rho in (0.0, 0.9):
+        pd = params_of(synth.SimConfig(), ground_on=True, k_c=1e5, cheby_rho=rho)
+        xg, _ = gpu_run(m, pd, colors, 1 / 60, 15, 30)
+        xo, _ = oracle_run(orc, m, pd, colors, 1 / 60, 15, 30)
+        assert xo[:, 2].min() < 0.0  # contact happened
+        err = _err(xg, xo, m.rest)
+        print("contact rho=%.1f: err/bbox = %.3e" % (rho, err))
+        assert err <= TOL
+
+
+def test_init_modes_and_damping(orc):
+    m = synth.beam(6, 2, 2, edge=0.1, E=1e5, nu=0.4, jitter_frac=0.05, seed=14)
+    colors, _ = orc.color_greedy(m.n_verts, m.tets)
+    rng = np.random.default_rng(15)
+    v0 = rng.normal(0, 0.2, m.rest.shape)
+    for mode in (0, 1, 2, 3):
+        for kd in (0.0, 1e-3):
+            pd = params_of(synth.SimConfig(), init_mode=mode, k_d=kd)
+            xg, _ = gpu_run(m, pd, colors, 1 / 60, 10, 10, None, v0)
+            xo, _ = oracle_run(orc, m, pd, colors, 1 / 60, 10, 10, None, v0)
+            assert _err(xg, xo, m.rest) <= TOL, (mode, kd)
+
+
+def test_batched_union_equals_individual_meshes(orc):
+    meshes = [synth.beam(a, b, c, E=E, nu=nu, pin_face=f) for a, b, c, E, nu, f in
+              [(5, 2, 2, 2e4, 0.3, "x-"), (8, 3, 2, 3e5, 0.45, "y+"), (4, 2, 3, 1e5, 0.4, "z-")]]
+    cat, voff, toff = synth.concat(meshes)
+    cat_colors = np.concatenate([orc.color_greedy(mm.n_verts, mm.tets)[0] for mm in meshes])
+    pd = params_of(synth.SimConfig())
+    xb, _ = gpu_run(cat, pd, cat_colors, 1 / 60, 10, 8, vert_offset=voff, tet_offset=toff)
+    for b, mm in enumerate(meshes):
+        xi, _ = gpu_run(mm, pd, cat_colors[voff[b]:voff[b + 1]], 1 / 60, 10, 8)
+        assert np.array_equal(xb[voff[b]:voff[b + 1]], xi)  # bit-identical
+    xo, _ = oracle_run(orc, cat, pd, cat_colors, 1 / 60, 10, 8)
+    assert _err(xb, xo, cat.rest) <= TOL
+
+
+def test_graph_replay_equals_eager():
+    m, cfg = synth.cantilever_beam()
+    colors = synth.kuhn_coloring(m.grid_ijk)
+    pd = params_of(cfg, cheby_rho=0.8)
+    xa, va = gpu_run(m, pd, colors, cfg.h, 7, 5, graph=True)
+    xb, vb = gpu_run(m, pd, colors, cfg.h, 7, 5, graph=False)
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
+def test_energy_fp64_matches_oracle(orc):
+    m = synth.beam(6, 3, 2, edge=0.1, E=1e5, nu=0.4, jitter_frac=0.1, seed=16)
+    x0, v0 = synth.perturbed_state(m.rest, 0.01, 0.2, seed=17)
+    pd = params_of(synth.SimConfig(), ground_on=True, ground_height=0.05, k_c=1e4)
+    # float32-representable inputs so that both sides start from the same numbers
+    x0, v0 = x0.astype(np.float32).astype(np.float64), v0.astype(np.float32).astype(np.float64)
+    sim = vbd.Sim(m, vbd.make_params(**pd))
+    try:
+        sim.set_state(x0, v0)
+        vbd.vbd_begin_step(sim.ctx, 1 / 60)
+        G_gpu = sim.energy()
+    finally:
+        sim.close()
+    model = orc.Model.from_mesh(m)
+    p = orc.Params.make(**pd)
+    y = model.inertia_target(p, 1 / 60, x0, v0)
+    xi = model.initial_guess(p, 1 / 60, x0, v0, v0)
+    G_orc = model.energy_G(p, 1 / 60, xi, y)
+    assert G_gpu == pytest.approx(G_orc, rel=1e-5)
+
+
+def test_nonfinite_update_is_reported():
+    m, cfg = synth.cantilever_beam()
+    x0 = m.rest.copy()
+    free = np.nonzero(m.pinned == 0)[0]
+    x0[free[5]] = np.nan
+    sim = vbd.Sim(m, vbd.make_params(**params_of(cfg)), colors=synth.kuhn_coloring(m.grid_ijk))
+    try:
+        sim.set_state(x0, np.zeros_like(x0))
+        sim.step(cfg.h, 3)
+        with pytest.raises(vbd.VbdError) as e:
+            sim.sync_status()
+        assert e.value.status == "VBD_ERR_NONFINITE"
+        sim.set_state(m.rest, np.zeros_like(x0))  # the context stays usable
+        sim.step(cfg.h, 3)
+        sim.sync_status()
+    finally:
+        sim.close()
