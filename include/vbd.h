@@ -181,6 +181,22 @@ vbd_status vbd_end_step(vbd_ctx *ctx);
  * on).  Synchronising. */
 vbd_status vbd_energy(vbd_ctx *ctx, double *G_out);
 
+/* FP64 energy G(x), as vbd_energy, for callers that cannot allocate device
+ * memory.  The paper has no counterpart; it exists for hosts that own every
+ * byte of device memory themselves (a fixed pool handed out at start-up, a
+ * real-time loop where cudaMalloc's implicit synchronisation is not
+ * allowed) and so cannot grant this diagnostic scratch of its own.  Its
+ * scratch (per-block partial sums) is a 512 KiB array inside the library,
+ * one per device, kept until the process exits; nothing is allocated.
+ * G_out: device pointer to one double, written asynchronously on the bound
+ * stream (not synchronising).  The first call on a device looks up that
+ * array's device address; make it before any stream capture.  Calls that
+ * overlap on the GPU (several streams or contexts at once) race on the
+ * shared array.  VBD_ERR_INVALID_ARG when ceil(free vertices / 256) +
+ * ceil(tets / 256) exceeds 65536 partial sums (about 16.7 million vertices
+ * plus tets), or when G_out is not device memory. */
+vbd_status vbd_energy_static(vbd_ctx *ctx, double *G_out);
+
 /* Waits for the stream and reads the device counters: VBD_ERR_NONFINITE if
  * any solve produced a non-finite update since the last call (that update
  * was not applied).  det_skips / contacts may be NULL.  Synchronising. */

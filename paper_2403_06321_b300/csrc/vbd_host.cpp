@@ -798,6 +798,22 @@ vbd_status vbd_energy(vbd_ctx *ctx, double *G_out) {
     return VBD_OK;
 }
 
+vbd_status vbd_energy_static(vbd_ctx *ctx, double *G_out) {
+    vbd_status st = check_bound(ctx);
+    if (st != VBD_OK) return st;
+    if (!G_out || !is_device_ptr(G_out)) return fail(ctx, VBD_ERR_INVALID_ARG, "G_out must be a device pointer");
+    if (!(ctx->h > 0.f)) return fail(ctx, VBD_ERR_STATE, "no step has begun (y undefined)");
+    const int need = vbd::energy_static_partials_needed(ctx->n_free, ctx->T);
+    if (need > vbd::energy_static_capacity())
+        return fail(ctx, VBD_ERR_INVALID_ARG,
+                    "mesh too large for the static scratch: needs " + std::to_string(need) +
+                        " partial sums, the library holds " + std::to_string(vbd::energy_static_capacity()));
+    cudaError_t e = vbd::launch_energy_static(ctx->d, ctx->n_free, ctx->T, (double)ctx->h,
+                                              sweep_params(ctx, -1), G_out, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "energy (static scratch)");
+    return VBD_OK;
+}
+
 vbd_status vbd_sync_status(vbd_ctx *ctx, int64_t *det_skips, int64_t *contacts) {
     vbd_status st = check_bound(ctx);
     if (st != VBD_OK) return st;

@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 
 namespace vbd {
 
@@ -424,6 +425,64 @@ void launch_set_log_young(const Dev &d, const float *log_young, int n_tets, long
                           cudaStream_t s) {
     const long long n = std::max<long long>(n_tets, n_slots);
     k_set_log_young<<<blocks_for(n, 256), 256, 0, s>>>(d, log_young, n_tets, n_slots);
+}
+
+// ---- energy with library-owned scratch --------------------------------------
+// vbd_energy_static runs the same three energy kernels as launch_energy, but
+// its per-block partial sums live in this file-scope device array instead of
+// the caller's workspace, and the total goes straight to a caller-given
+// device double.  Each device that loads the library holds one copy (512 KiB)
+// until the process exits; every call on that device reuses it, so calls
+// that overlap on the GPU (other streams, other contexts) race on it.
+namespace {
+constexpr int kStaticPartials = 65536;
+static __device__ __align__(256) double g_static_partials[kStaticPartials];
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+double *g_static_ptr[kMaxDevices] = {};
+}  // namespace
+
+int energy_static_capacity() { return kStaticPartials; }
+
+int energy_static_partials_needed(int n_free, int n_tets) {
+    const long long gv = std::max<long long>(1, blocks_for(n_free, EB));
+    const long long gt = std::max<long long>(1, blocks_for(n_tets, EB));
+    return (int)std::min<long long>(gv + gt, 0x7fffffffLL);
+}
+
+// Device address of g_static_partials on the current device.  The symbol name
+// is only a host-side handle; kernels must be given this address.  Looked up
+// once per device (the first call on a device does it, so that call should
+// precede any stream capture).
+cudaError_t energy_static_scratch(double **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_partials);
+        if (e != cudaSuccess) return e;
+        g_static_ptr[dev] = (double *)p;
+    }
+    *out = g_static_ptr[dev];
+    return cudaSuccess;
+}
+
+cudaError_t launch_energy_static(const Dev &d, int n_free, int n_tets, double h, const SweepParams &p,
+                                 double *G_out, cudaStream_t s) {
+    const int gv = std::max(1, (int)blocks_for(n_free, EB));
+    const int gt = std::max(1, (int)blocks_for(n_tets, EB));
+    if ((long long)gv + gt > kStaticPartials) return cudaErrorInvalidValue;
+    double *part = nullptr;
+    cudaError_t e = energy_static_scratch(&part);
+    if (e != cudaSuccess) return e;
+    // every partial slot [0, gv + gt) is written before the final sum reads it
+    k_energy_verts<<<gv, EB, 0, s>>>(d, n_free, 1.0 / (2.0 * h * h), p, part);
+    k_energy_tets<<<gt, EB, 0, s>>>(d, n_tets, part + gv);
+    k_reduce_partials<<<1, EB, 0, s>>>(part, gv + gt, G_out);
+    return cudaGetLastError();
 }
 
 }  // namespace vbd

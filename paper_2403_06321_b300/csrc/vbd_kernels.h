@@ -63,6 +63,11 @@ void launch_restore_x(const Dev &d, int n, cudaStream_t s);
 void launch_energy(const Dev &d, int n_free, int n_tets, double h, const SweepParams &p,
                    cudaStream_t s);
 int energy_partials_needed(int n_free, int n_tets);
+// energy with its scratch in a static device array (see vbd_energy_static)
+int energy_static_capacity();
+int energy_static_partials_needed(int n_free, int n_tets);
+cudaError_t launch_energy_static(const Dev &d, int n_free, int n_tets, double h, const SweepParams &p,
+                                 double *G_out, cudaStream_t s);
 void launch_set_log_young(const Dev &d, const float *log_young, int n_tets, long long n_slots,
                           cudaStream_t s);
 

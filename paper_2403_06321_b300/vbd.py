@@ -27,7 +27,7 @@ ENTRY_POINTS = [
     "vbd_default_params", "vbd_create_mesh", "vbd_color", "vbd_get_colors", "vbd_get_info",
     "vbd_workspace_size", "vbd_bind", "vbd_set_params", "vbd_set_state", "vbd_get_state",
     "vbd_set_log_young", "vbd_step", "vbd_begin_step", "vbd_iterate", "vbd_sweep_color",
-    "vbd_accelerate", "vbd_end_step", "vbd_energy", "vbd_sync_status", "vbd_backward",
+    "vbd_accelerate", "vbd_end_step", "vbd_energy", "vbd_energy_static", "vbd_sync_status", "vbd_backward",
     "vbd_set_launch", "vbd_set_graph", "vbd_autotune", "vbd_last_error", "vbd_destroy",
 ]
 
@@ -94,6 +94,7 @@ def load() -> C.CDLL:
         "vbd_accelerate": (C.c_int, [P, I32]),
         "vbd_end_step": (C.c_int, [P]),
         "vbd_energy": (C.c_int, [P, C.POINTER(D)]),
+        "vbd_energy_static": (C.c_int, [P, P]),
         "vbd_sync_status": (C.c_int, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "vbd_backward": (C.c_int, [P, P, P, P, I32]),
         "vbd_set_launch": (C.c_int, [P, I32, I32]),
@@ -218,6 +219,11 @@ def vbd_energy(ctx: int) -> float:
     g = C.c_double()
     _check("vbd_energy", ctx, load().vbd_energy(ctx, C.byref(g)))
     return g.value
+
+
+def vbd_energy_static(ctx: int, G_out) -> None:
+    """G_out: device buffer of one float64 (e.g. a torch tensor); asynchronous."""
+    _check("vbd_energy_static", ctx, load().vbd_energy_static(ctx, _ptr(G_out)))
 
 
 def vbd_sync_status(ctx: int) -> int:
