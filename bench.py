@@ -146,10 +146,16 @@ def measured_peak_hbm():
 
 
 def kernel_source_sha() -> str:
+    """Hash of the forward kernels' code with comments and blank space removed,
+    so that a profile stays attached to the code it measured."""
+    import re
     h = hashlib.sha256()
     for f in ("vbd_kernels.cu", "vbd_kernels.h"):
-        with open(os.path.join(ROOT, "paper_2403_06321_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2403_06321_b300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update("".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

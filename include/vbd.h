@@ -3,9 +3,9 @@
  *
  * Vertex Block Descent (Chen, Liu, Yang, Yuksel, ACM TOG 43(4), 2024)
  * integrates elastic tetrahedral bodies with implicit Euler written as the
- * minimisation of the variational energy G of Eq. 1, by block coordinate
+ * minimisation of the variational energy G of Eqs. 1-2, by block coordinate
  * descent over vertices: Gauss-Seidel passes over vertex colours (Sec. 3.9),
- * each vertex taking one Newton step on its local energy G_i (Eqs. 3, 6-8).
+ * each vertex taking one Newton step on its local energy G_i (Eqs. 4-5, 7-9).
  * One time step is Algorithm 1.
  *
  * Conventions for every entry point:
@@ -72,16 +72,16 @@ typedef struct {
 } vbd_mesh_desc;
 
 typedef struct {
-    float gravity[3];        /* a_ext of Eq. 2 [m/s^2] */
-    int32_t ground_on;       /* ground half-space penalty (Eq. 11) on/off */
+    float gravity[3];        /* a_ext of Eq. 3 [m/s^2] */
+    int32_t ground_on;       /* ground half-space penalty (Eq. 12) on/off */
     float ground_height;     /* plane {x : x . n = ground_height} */
     float ground_normal[3];  /* n, need not be unit length */
-    float k_c;               /* collision stiffness of Eq. 11 [N/m] */
-    float cheby_rho;         /* spectral radius of Eq. 13; 0 disables acceleration */
+    float k_c;               /* collision stiffness of Eq. 12 [N/m] */
+    float cheby_rho;         /* spectral radius of Eq. 19; 0 disables acceleration */
     int32_t init_mode;       /* Sec. 3.7: 0 previous position, 1 inertia,
                                 2 inertia + acceleration, 3 adaptive (default) */
     float det_eps;           /* Sec. 3.2 skip when |det H_i| <= det_eps |tr H_i / 3|^3 */
-    float k_d;               /* Rayleigh damping coefficient of Eqs. 9-10 (0 = off) */
+    float k_d;               /* Rayleigh damping coefficient of Eqs. 10-11 (0 = off) */
     int32_t tape_steps;      /* steps of positions recorded for vbd_backward (0 = none) */
 } vbd_params;
 
@@ -152,14 +152,14 @@ vbd_status vbd_set_log_young(vbd_ctx *ctx, const float *log_young);
  * vbd_begin_step + vbd_iterate + vbd_end_step. */
 vbd_status vbd_step(vbd_ctx *ctx, float h, int32_t iters);
 
-/* Algorithm 1, first lines: y = x^t + h v^t + h^2 a_ext (Eq. 2) and the
+/* Start of Algorithm 1: y = x^t + h v^t + h^2 a_ext (Eq. 3) and the
  * initial guess of Sec. 3.7 (pinned vertices keep x^t). */
 vbd_status vbd_begin_step(vbd_ctx *ctx, float h);
 
 /* Algorithm 1 iteration loop: for n = 1..iters, one Gauss-Seidel pass per
  * colour in ascending colour order, each vertex solving H_i dx = f_i (Eqs.
- * 6-8, damping Eqs. 9-10, ground penalty Eq. 11, singular skip Sec. 3.2),
- * then, if cheby_rho > 0, the Chebyshev update of Eqs. 12-13 skipping
+ * 7-9, damping Eqs. 10-11, ground penalty Eq. 12, singular skip Sec. 3.2),
+ * then, if cheby_rho > 0, the Chebyshev update of Eqs. 18-19 skipping
  * vertices that touched the ground during this step (Sec. 3.8).  Replays a
  * CUDA graph of the whole loop when graphs are enabled (default). */
 vbd_status vbd_iterate(vbd_ctx *ctx, int32_t iters);
@@ -169,14 +169,14 @@ vbd_status vbd_iterate(vbd_ctx *ctx, int32_t iters);
  * of Algorithm 1 on this path). */
 vbd_status vbd_sweep_color(vbd_ctx *ctx, int32_t color);
 
-/* Chebyshev update (Eq. 12) after iteration n (1-based) of the current step. */
+/* Chebyshev update (Eq. 18) after iteration n (1-based) of the current step. */
 vbd_status vbd_accelerate(vbd_ctx *ctx, int32_t n);
 
-/* Algorithm 1, last lines: v^{t+1} = (x^{t+1} - x^t)/h (Eq. 5); records x
+/* End of Algorithm 1: v^{t+1} = (x^{t+1} - x^t)/h (Eq. 6); records x
  * on the tape when tape_steps > 0. */
 vbd_status vbd_end_step(vbd_ctx *ctx);
 
-/* FP64 variational energy G(x) of Eq. 1 for the current x and the inertia
+/* FP64 variational energy G(x) of Eq. 2 for the current x and the inertia
  * target y of the current step (free vertices; ground penalty included when
  * on).  Synchronising. */
 vbd_status vbd_energy(vbd_ctx *ctx, double *G_out);
@@ -204,7 +204,7 @@ vbd_status vbd_sync_status(vbd_ctx *ctx, int64_t *det_skips, int64_t *contacts);
 
 /* Adjoint of the recorded steps (tape_steps > 0; no paper counterpart, the
  * paper has no derivatives): treats every recorded step as converged
- * (dG/dx = 0 of Eq. 1) and, backwards over the steps, solves H lam = r with
+ * (dG/dx = 0 of Eq. 2) and, backwards over the steps, solves H lam = r with
  * `adj_iters` colour-ordered block Gauss-Seidel sweeps, H the Hessian of G
  * at the recorded positions.  Inputs: dL_dxT (3N floats, caller order,
  * device): dL/dx of the final positions.  Outputs (device, overwritten):

@@ -6,12 +6,12 @@ code with the CUDA path; both are fed the same seeded inputs.
 
 Besides marshalling, this file holds the two dense FP64 references that need
 a linear-algebra library primitive:
-  * ``newton_solve``: the global implicit-Euler minimiser of Eq. 1 by a dense
-    Newton method with backtracking (the paper's "converges to the same
-    result as backward Euler" claim, Sec. 1 / Sec. 3.1);
+  * ``newton_solve``: the global implicit-Euler minimiser of Eqs. 1-2 by a dense
+    Newton method with backtracking (VBD iterations converge to the
+    implicit-Euler solution, Sec. 1 and Sec. 3.1);
   * ``dense_adjoint``: reverse-mode derivative of converged implicit-Euler
-    steps (implicit function theorem on dG/dx = 0 of Eq. 1; the paper has
-    no adjoint, this is derived from Eqs. 1, 2 and 5).
+    steps (implicit function theorem on dG/dx = 0 of Eq. 2; the paper has
+    no adjoint, this is derived from Eqs. 2, 3 and 6).
 """
 from __future__ import annotations
 
@@ -315,7 +315,7 @@ class Model:
         return n, d, act
 
     def global_grad_hess(self, p: Params, h, x, y):
-        """dG/dx and d2G/dx2 of Eq. 1 (+ ground penalty), dense, all DoFs."""
+        """dG/dx and d2G/dx2 of Eq. 2 (+ ground penalty), dense, all DoFs."""
         m = self.mass()
         M = np.repeat(np.where(self.free, m, 0.0), 3)
         g = M / h ** 2 * (x - y).reshape(-1) + self.elastic_grad(x)
@@ -327,7 +327,7 @@ class Model:
         return g, H
 
     def newton_solve(self, p: Params, h, x0, y, tol=1e-11, max_iter=200) -> np.ndarray:
-        """Global minimiser of G (Eq. 1) over free DoFs: dense Newton with
+        """Global minimiser of G (Eqs. 1-2) over free DoFs: dense Newton with
         backtracking on G, from x0.  Used as the backward-Euler reference."""
         x = np.array(x0, dtype=np.float64).reshape(-1, 3)
         fd = np.repeat(self.free, 3)

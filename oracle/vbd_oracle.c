@@ -6,8 +6,8 @@
  * routine can be read against the paper equation it cites.
  *
  * Readings of points the paper leaves open (each pinned by a test):
- *  - Material (Sec. 5 names "Neo-Hookean [Smith et al. 2018] without the
- *    logarithmic term" and prints no formula):
+ *  - Material: Sec. 5 uses the stable neo-Hookean model of Smith et al.
+ *    (2018) with its logarithmic term dropped, and prints no formula:
  *        Psi(F) = mu/2 (tr F^T F - 3) + lam/2 (J - alpha)^2,
  *        alpha  = 1 + mu/lam   (the unique value making F = I stress free).
  *  - Lame mapping from (E, nu): mu = E/(2(1+nu)),
@@ -15,12 +15,12 @@
  *        is linear elasticity with the textbook Lame pair.
  *  - Mass: lumped, m_i = sum over tets j containing i of rho_j V_j / 4.
  *  - Singular-Hessian skip (Sec. 3.2): |det H| <= det_eps * |tr H / 3|^3.
- *  - Contact (Eq. 11) with a ground half-space: x_b is the projection of
+ *  - Contact (Eq. 12) with a ground half-space: x_b is the projection of
  *    the vertex on the plane, d = max(0, height - x.n), n held constant.
  *  - Colouring (Sec. 3.9 gives no algorithm): greedy, vertices visited by
  *    decreasing number of distinct neighbours, ties by lower id, each
  *    taking the smallest colour unused by its neighbours.
- *  - Chebyshev (Eqs. 12-13): x^(0) is the initial guess; a vertex that
+ *  - Chebyshev (Eqs. 18-19): x^(0) is the initial guess; a vertex that
  *    saw contact in any iteration of the step, including the current one,
  *    keeps its Gauss-Seidel result (Sec. 3.8 collision skip).
  *  - First step: the caller passes v^{t-1} = v^t, so the adaptive
@@ -386,7 +386,7 @@ void orc_model_set_log_young(orc_model *m, const double *log_young) {
 /* time step                                                            */
 /* ------------------------------------------------------------------ */
 
-/* Eq. 2: y = x^t + h v^t + h^2 a_ext */
+/* Eq. 3: y = x^t + h v^t + h^2 a_ext */
 void orc_inertia_target(const orc_model *m, const orc_params *p, double h,
                         const double *xt, const double *vt, double *y) {
     for (int i = 0; i < m->n_verts; ++i)
@@ -427,8 +427,8 @@ void orc_initial_guess(const orc_model *m, const orc_params *p, double h,
     }
 }
 
-/* Local Newton step for vertex i (Eqs. 6-8, damping Eqs. 9-10, contact
- * Eq. 11, analytic 3x3 solve and singular skip of Sec. 3.2).  Returns 1 if
+/* Local Newton step for vertex i (Eqs. 7-9, damping Eqs. 10-11, contact
+ * Eq. 12, analytic 3x3 solve and singular skip of Sec. 3.2).  Returns 1 if
  * the vertex is skipped (dx = 0). */
 int orc_vertex_solve(const orc_model *m, const orc_params *p, double h, int i,
                      const double *x, const double *y, const double *xt,
@@ -499,7 +499,7 @@ void orc_sweep_color(const orc_model *m, const orc_params *p, double h, const in
     }
 }
 
-/* Eq. 13: omega_1 = 1, omega_2 = 2/(2 - rho^2), omega_n = 4/(4 - rho^2 omega_{n-1}) */
+/* Eq. 19: omega_1 = 1, omega_2 = 2/(2 - rho^2), omega_n = 4/(4 - rho^2 omega_{n-1}) */
 double orc_cheby_omega(int n, double rho, double omega_prev) {
     if (n <= 1) return 1.0;
     if (n == 2) return 2.0 / (2.0 - rho * rho);
@@ -517,20 +517,20 @@ int orc_step(const orc_model *m, const orc_params *p, const int *colors, int n_c
     double *p2 = (double *)malloc(sizeof(double) * n3 + 1);
     unsigned char *coll = (unsigned char *)calloc((size_t)m->n_verts + 1, 1);
     memcpy(xt, x, sizeof(double) * n3);
-    orc_inertia_target(m, p, h, xt, v, y);            /* Eq. 2 */
+    orc_inertia_target(m, p, h, xt, v, y);            /* Eq. 3 */
     orc_initial_guess(m, p, h, xt, v, vprev, x);      /* Sec. 3.7 */
     memcpy(p1, x, sizeof(double) * n3);               /* x^(0) */
     double omega = 1.0;
     for (int n = 1; n <= iters; ++n) {
         for (int c = 0; c < n_colors; ++c) orc_sweep_color(m, p, h, colors, c, x, y, xt, coll, st);
         if (p->cheby_rho > 0.0) {
-            omega = orc_cheby_omega(n, p->cheby_rho, omega);   /* Eq. 13 */
+            omega = orc_cheby_omega(n, p->cheby_rho, omega);   /* Eq. 19 */
             for (int i = 0; i < m->n_verts; ++i) {
                 for (int r = 0; r < 3; ++r) {
                     size_t q = 3 * (size_t)i + r;
                     double xbar = x[q];
                     double xn = xbar;
-                    if (n >= 2 && !m->pinned[i] && !coll[i]) xn = omega * (xbar - p2[q]) + p2[q]; /* Eq. 12 */
+                    if (n >= 2 && !m->pinned[i] && !coll[i]) xn = omega * (xbar - p2[q]) + p2[q]; /* Eq. 18 */
                     p2[q] = p1[q];
                     p1[q] = xn;
                     x[q] = xn;
@@ -538,7 +538,7 @@ int orc_step(const orc_model *m, const orc_params *p, const int *colors, int n_c
             }
         }
     }
-    for (size_t q = 0; q < n3; ++q) {                  /* Eq. 5 */
+    for (size_t q = 0; q < n3; ++q) {                  /* Eq. 6 */
         double vn = (x[q] - xt[q]) / h;
         vprev[q] = v[q];
         v[q] = vn;
@@ -551,8 +551,8 @@ int orc_step(const orc_model *m, const orc_params *p, const int *colors, int n_c
 /* diagnostics and assembly                                             */
 /* ------------------------------------------------------------------ */
 
-/* Eq. 1 variational energy G(x) = 1/(2h^2) |x - y|_M^2 + E(x) over the free
- * vertices, with the ground penalty of Eq. 11 when enabled. */
+/* Eq. 2 variational energy G(x) = 1/(2h^2) |x - y|_M^2 + E(x) over the free
+ * vertices, with the ground penalty of Eq. 12 when enabled. */
 double orc_energy_G(const orc_model *m, const orc_params *p, double h,
                     const double *x, const double *y) {
     double G = 0.0;

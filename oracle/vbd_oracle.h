@@ -8,8 +8,9 @@
  * with the CUDA path.
  *
  * Every routine is a direct transcription of the paper's definitions
- * (Sec. 3.1 Eqs. 1-5, Sec. 3.2 Eqs. 6-8, Sec. 3.5 Eq. 11, Sec. 3.7
- * initialisation (a)-(d), Sec. 3.8 Eqs. 12-13, Algorithm 1), in FP64,
+ * (Sec. 3.1 Eqs. 1-6, Sec. 3.2 Eqs. 7-9, Sec. 3.3 Eqs. 10-11, Sec. 3.5
+ * Eq. 12, Sec. 3.7 options (a)-(d) and Eq. 17, Sec. 3.8 Eqs. 18-19,
+ * Algorithm 1), in FP64,
  * with plain loops and no blocking or reordering.  Where the paper is
  * silent (material formula, Lame mapping, lumped mass, det threshold,
  * colouring algorithm) the readings are stated next to the code.
@@ -27,15 +28,15 @@ extern "C" {
 typedef struct orc_model orc_model;
 
 typedef struct {
-    double gravity[3];      /* a_ext of Eq. 2 */
-    int ground_on;          /* ground half-space penalty of Eq. 11 */
+    double gravity[3];      /* a_ext of Eq. 3 */
+    int ground_on;          /* ground half-space penalty of Eq. 12 */
     double ground_height;   /* plane {x : x.n = ground_height} */
     double ground_normal[3];
-    double k_c;             /* collision stiffness, Eq. 11 */
-    double cheby_rho;       /* Eq. 12-13 spectral radius; 0 = no acceleration */
+    double k_c;             /* collision stiffness, Eq. 12 */
+    double cheby_rho;       /* Eqs. 18-19 spectral radius; 0 = no acceleration */
     int init_mode;          /* Sec. 3.7: 0 previous, 1 inertia, 2 inertia+acc, 3 adaptive */
     double det_eps;         /* relative threshold of the Sec. 3.2 singular-Hessian skip */
-    double k_d;             /* Rayleigh damping coefficient, Eqs. 9-10 (0 = off) */
+    double k_d;             /* Rayleigh damping coefficient, Eqs. 10-11 (0 = off) */
 } orc_params;
 
 typedef struct {

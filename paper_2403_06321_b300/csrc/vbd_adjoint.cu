@@ -1,7 +1,7 @@
 // vbd_adjoint.cu -- reverse pass through converged VBD steps (no paper
 // counterpart: the paper has no derivatives; this follows from applying the
-// implicit function theorem to dG/dx = 0 of Eq. 1, with y from Eq. 2 and the
-// velocity update of Eq. 5).
+// implicit function theorem to dG/dx = 0 of Eq. 2, with y from Eq. 3 and the
+// velocity update of Eq. 6).
 //
 // For a recorded step t with end positions x_{t+1} and H = M/h^2 + d2E/dx2
 // (+ the ground penalty Hessian), going backwards:

@@ -298,7 +298,7 @@ void clear_graphs(vbd_ctx *c) {
     c->graphs.clear();
 }
 
-// Chebyshev omega_n of Eq. 13 (computed in FP64)
+// Chebyshev omega_n of Eq. 19 (computed in FP64)
 double cheby_omega(int n, double rho) {
     double w = 1.0;
     for (int k = 2; k <= n; ++k) w = (k == 2) ? 2.0 / (2.0 - rho * rho) : 4.0 / (4.0 - rho * rho * w);

@@ -1,11 +1,11 @@
 // vbd_kernels.cu -- forward kernels of Vertex Block Descent for sm_103a.
 //
 // One time step (Algorithm 1) is
-//   k_predict            y (Eq. 2) and the initial guess (Sec. 3.7), once per step
+//   k_predict            y (Eq. 3) and the initial guess (Sec. 3.7), once per step
 //   k_sweep<L>           one Gauss-Seidel pass over one colour (Sec. 3.1-3.9),
 //                        iters * n_colors launches per step -- the hot path
-//   k_cheby              Chebyshev update (Eqs. 12-13), once per iteration if enabled
-//   k_finish             v = (x - x^t)/h (Eq. 5), once per step
+//   k_cheby              Chebyshev update (Eqs. 18-19), once per iteration if enabled
+//   k_finish             v = (x - x^t)/h (Eq. 6), once per step
 //
 // The sweep is memory bound: per (vertex, incident tet) pair ("slot") it
 // streams 56 bytes of precomputed rest data once per iteration and gathers
@@ -39,7 +39,7 @@ struct Acc {
     float f0, f1, f2, h00, h01, h02, h11, h12, h22;
 };
 
-// Contribution of one tet to the vertex that owns slot s (Eqs. 7-8 with the
+// Contribution of one tet to the vertex that owns slot s (Eqs. 8-9 with the
 // stable neo-Hookean element):  with e_k = x_k - x_i for the three other
 // vertices and their shape gradients g_k,
 //   F = sum_k e_k g_k^T,  g_i = -(g_a + g_b + g_c),  c = cof(F) g_i,
@@ -95,8 +95,9 @@ __device__ __forceinline__ float sub_reduce(float v) {
     return v;
 }
 
-// Local solve of Sec. 3.2 for one vertex: inertia (Eqs. 7-8), damping
-// (Eqs. 9-10), ground penalty (Eq. 11), singular skip, analytic inverse.
+// Local solve of Sec. 3.2 for one vertex: Eq. 7 with the inertia terms of
+// Eqs. 8-9, damping (Eqs. 10-11), ground penalty (Eq. 12), singular skip,
+// analytic inverse.
 __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams &p, int vi, float4 xi,
                                                 const Acc &a) {
     const float4 yv = d.ym[vi];
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, SweepParams p) {
     if (active && lane == 0) solve_and_store(d, p, vi, xi, acc);
 }
 
-// Eq. 2 and Sec. 3.7 (a)-(d).  Pinned vertices (ids >= n_free) keep x^t.
+// Eq. 3 and Sec. 3.7 options (a)-(d), Eq. 17.  Pinned vertices (ids >= n_free) keep x^t.
 __global__ void k_predict(Dev d, int n, int n_free, float h, float3 g, float gnorm, int mode,
                           int cheby) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -219,7 +220,7 @@ __global__ void k_predict(Dev d, int n, int n_free, float h, float3 g, float gno
     if (cheby) d.cheb[0][i] = xn;
 }
 
-// Eq. 12 after iteration n: history buffer cheb[n & 1] holds x^(n-2) on entry
+// Eq. 18 after iteration n: history buffer cheb[n & 1] holds x^(n-2) on entry
 // and x^(n) on exit; the other buffer holds x^(n-1).  Vertices flagged in
 // ground contact (x.w != 0) keep the Gauss-Seidel result.
 __global__ void k_cheby(Dev d, int n_free, int n, float omega) {
@@ -237,7 +238,7 @@ __global__ void k_cheby(Dev d, int n_free, int n, float omega) {
     hist[i] = xn;
 }
 
-// Eq. 5; v^{t-1} <- v^t; optional tape row.
+// Eq. 6; v^{t-1} <- v^t; optional tape row.
 __global__ void k_finish(Dev d, int n, float h, float4 *tape_row) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -268,7 +269,7 @@ __global__ void k_restore_x(Dev d, int n) {
     if (i < n) d.x[i] = d.xt[i];
 }
 
-// ---- FP64 energy of Eq. 1 (diagnostics) -----------------------------------
+// ---- FP64 energy of Eq. 2 (diagnostics) -----------------------------------
 constexpr int EB = 256;
 
 __device__ __forceinline__ void block_sum_store(double v, double *out) {

@@ -14,8 +14,8 @@ struct Dev {
     float4 *xt;       // x^t (start of step)
     float4 *v;        // v^t
     float4 *vprev;    // v^{t-1}
-    float4 *ym;       // inertia target y (Eq. 2) in .xyz, m_i / h^2 in .w
-    float4 *cheb[2];  // Chebyshev history (Eq. 12), roles alternate with iteration parity
+    float4 *ym;       // inertia target y (Eq. 3) in .xyz, m_i / h^2 in .w
+    float4 *cheb[2];  // Chebyshev history (Eq. 18), roles alternate with iteration parity
     float *mass;      // lumped mass
     int *slot_off;    // n_free + 1: slots of free vertex i are [slot_off[i], slot_off[i+1])
     // incidence slots (one per (free vertex, incident tet)), 56 bytes each:

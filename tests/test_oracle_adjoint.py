@@ -1,8 +1,8 @@
 """Pins of the oracle's dense adjoint of converged implicit-Euler steps.
 
 The paper has no adjoint; the reverse recursion follows from the implicit
-function theorem applied to dG/dx = 0 of Eq. 1 with y from Eq. 2 and the
-velocity update of Eq. 5.  It is checked here against central finite
+function theorem applied to dG/dx = 0 of Eq. 2 with y from Eq. 3 and the
+velocity update of Eq. 6.  It is checked here against central finite
 differences of a forward solved to convergence by dense Newton, and against
 the closed form of a body without stiffness.  CPU only."""
 import numpy as np

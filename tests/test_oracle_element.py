@@ -1,5 +1,5 @@
 """Pins of the oracle's element routines (stable neo-Hookean tet, Sec. 5;
-gradient and Hessian blocks entering Eqs. 7-8) against finite differences,
+gradient and Hessian blocks entering Eqs. 8-9) against finite differences,
 invariances and closed forms.  CPU only."""
 import numpy as np
 import pytest

@@ -1,7 +1,7 @@
-"""Pins of the oracle's time step (Algorithm 1): inertia target (Eq. 2),
-initialisation (Sec. 3.7), local solve (Eqs. 6-8), Gauss-Seidel colour
-passes (Sec. 3.1, 3.9), Chebyshev acceleration (Eqs. 12-13), ground
-penalty (Eq. 11) and the velocity update (Eq. 5).  CPU only."""
+"""Pins of the oracle's time step (Algorithm 1): inertia target (Eq. 3),
+initialisation (Sec. 3.7, Eq. 17), local solve (Eqs. 7-9), Gauss-Seidel
+colour passes (Sec. 3.1, 3.9), Chebyshev acceleration (Eqs. 18-19), ground
+penalty (Eq. 12) and the velocity update (Eq. 6).  CPU only."""
 import numpy as np
 import pytest
 
@@ -232,7 +232,7 @@ def test_chebyshev_skips_colliding_vertices(orc):
     v = np.zeros_like(xt)
     iters = 4
     x, _, _ = orc.run(model, p, colors, nc, H, iters, 1, xt, v)
-    # manual Algorithm 1 with Eq. 12 and the skip
+    # manual Algorithm 1 with Eq. 18 and the skip
     y = model.inertia_target(pg, H, xt, v)
     xm = model.initial_guess(pg, H, xt, v, v)
     coll = np.zeros(m.n_verts, np.uint8)
