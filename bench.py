@@ -50,6 +50,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched and adjoint comparisons")
+    ap.add_argument("--batch-meshes", type=int, default=4096)
     return ap.parse_args(argv)
 
 
@@ -251,6 +254,109 @@ def workload_config(args, info) -> dict:
     return cfg
 
 
+# ------------------------------------------------------------------ extras ---
+
+def _timed(stream, fn, reps):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def run_batched(args) -> dict:
+    """4096 independent beams (cube counts U{4..40} x U{2..8} x U{2..8}) swept
+    in one launch per colour, against the same beams each in its own context
+    (its own launches and graph) on the same GPU, both on one stream."""
+    import numpy as np
+    import torch
+    from paper_2403_06321_b300 import synth, vbd
+    meshes, cfg = synth.beam_batch(args.batch_meshes)
+    cat, voff, toff = synth.concat(meshes)
+    colors = np.concatenate([synth.kuhn_coloring(m.grid_ijk) for m in meshes])
+    params = vbd.make_params(gravity=cfg.gravity, init_mode=cfg.init_mode, det_eps=cfg.det_eps)
+    stream = torch.cuda.Stream()
+    sim = vbd.Sim(cat, params, colors=colors, stream=stream, vert_offset=voff, tet_offset=toff)
+    info = vbd.vbd_get_info(sim.ctx)
+    sim.set_state(cat.rest, np.zeros_like(cat.rest))
+    steps = 5
+    h, iters = cfg.h, cfg.iters
+    for _ in range(2):
+        sim.step(h, iters)
+    t_b = _timed(stream, lambda: sim.step(h, iters), steps)
+    sim.sync_status()
+    v_batched = info.n_free * iters * steps / t_b
+    sim.close()
+    # per-mesh contexts
+    sims = []
+    for m in meshes:
+        s_ = vbd.Sim(m, params, colors=synth.kuhn_coloring(m.grid_ijk), stream=stream)
+        s_.set_state(m.rest, np.zeros_like(m.rest))
+        sims.append(s_)
+    n_free = sum(s_.info.n_free for s_ in sims)
+
+    def all_step():
+        for s_ in sims:
+            s_.step(h, iters)
+    all_step()
+    psteps = 2
+    t_p = _timed(stream, all_step, psteps)
+    v_plain = n_free * iters * psteps / t_p
+    for s_ in sims:
+        s_.sync_status()
+        s_.close()
+    return {"workload": "%d beams, %d verts, %d tets, Kuhn 4-colouring, h=1/60, %d iterations/step, "
+                        "one launch per colour for all meshes, CUDA graph per step" % (
+                            len(meshes), cat.n_verts, cat.n_tets, iters),
+            "value": v_batched, "unit": UNIT, "ms_per_step": t_b * 1e3 / steps,
+            "per_mesh_value": v_plain, "per_mesh_ms_per_step": t_p * 1e3 / psteps,
+            "speedup_vs_plain": v_batched / v_plain, "n_free_verts": int(info.n_free)}
+
+
+def run_adjoint(args) -> dict:
+    """Adjoint block-GS sweeps (vbd_backward) on the benchmark cube against
+    the forward sweeps on the same mesh: vertex-block updates per second of
+    each, 2 recorded steps."""
+    import numpy as np
+    import torch
+    from paper_2403_06321_b300 import synth, vbd
+    m, cfg = synth.large_cube(args.n)
+    steps, iters, adj_iters = 2, args.iters, args.iters
+    params = vbd.make_params(gravity=cfg.gravity, ground_on=cfg.ground_on, k_c=cfg.k_c,
+                             init_mode=cfg.init_mode, det_eps=cfg.det_eps, tape_steps=steps)
+    stream = torch.cuda.Stream()
+    sim = vbd.Sim(m, params, colors=synth.kuhn_coloring(m.grid_ijk), stream=stream)
+    n_free = sim.info.n_free
+    zeros = np.zeros_like(m.rest)
+    dev = sim.workspace.device
+    gx = torch.zeros(3 * m.n_verts, dtype=torch.float32, device=dev)
+    gx[2::3] = 1.0 / m.n_verts
+    gE = torch.empty(m.n_tets, dtype=torch.float32, device=dev)
+    gv = torch.empty(3 * m.n_verts, dtype=torch.float32, device=dev)
+
+    def fwd():
+        sim.set_state(m.rest, zeros)
+        for _ in range(steps):
+            sim.step(cfg.h, iters)
+    fwd()
+    vbd.vbd_backward(sim.ctx, gx, gE, gv, adj_iters)  # warm-up
+    sim.set_state(m.rest, zeros)
+    t_f = _timed(stream, lambda: sim.step(cfg.h, iters), steps)
+    t_a = _timed(stream, lambda: vbd.vbd_backward(sim.ctx, gx, gE, gv, adj_iters), 1)
+    sim.sync_status()
+    sim.close()
+    v_f = n_free * iters * steps / t_f
+    v_a = n_free * adj_iters * steps / t_a
+    return {"workload": "large_cube %d^3, %d recorded steps, %d adjoint block-GS iterations per step" % (
+                args.n, steps, adj_iters),
+            "value": v_a, "unit": "adjoint vertex-block updates/s", "forward_value": v_f,
+            "ratio_vs_plain": v_a / v_f, "ms_backward": t_a * 1e3, "ms_forward": t_f * 1e3}
+
+
 # --------------------------------------------------------------------- ours ---
 
 def run_ours(args):
@@ -361,6 +467,9 @@ def run_ours(args):
         "gpu_launches": K * (2 + iters * C),
         "clocks": clk,
     }
+    if not args.no_extras and world == 1:
+        line["batched"] = run_batched(args)
+        line["adjoint"] = run_adjoint(args)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = run_cpu_baseline()
     print(json.dumps(line), flush=True)

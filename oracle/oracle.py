@@ -292,11 +292,14 @@ class Model:
         lib().orc_elastic_grad(self._h, _d(x).reshape(-1), g)
         return g
 
-    def elastic_hess(self, x) -> np.ndarray:
-        """Dense 3N x 3N elastic Hessian (small meshes only)."""
+    def elastic_hess(self, x, sparse: bool = False):
+        """3N x 3N elastic Hessian: dense (small meshes) or scipy CSR."""
         nt = 144 * self.t
         r, c, v = np.zeros(nt, np.int32), np.zeros(nt, np.int32), np.zeros(nt)
         lib().orc_elastic_hess_triplets(self._h, _d(x).reshape(-1), r, c, v)
+        if sparse:
+            import scipy.sparse as sp
+            return sp.csr_matrix((v, (r, c)), shape=(3 * self.n, 3 * self.n))
         H = np.zeros((3 * self.n, 3 * self.n))
         np.add.at(H, (r, c), v)
         return H
@@ -359,7 +362,7 @@ class Model:
         return x
 
 
-def dense_adjoint(model: Model, p: Params, h: float, xs: list, dL_dxT: np.ndarray):
+def dense_adjoint(model: Model, p: Params, h: float, xs: list, dL_dxT: np.ndarray, sparse=None):
     """Reverse-mode gradients of L(x_T) through T converged implicit-Euler steps.
 
     xs = [x_0, ..., x_T] (positions after each step).  At a converged step
@@ -368,7 +371,9 @@ def dense_adjoint(model: Model, p: Params, h: float, xs: list, dL_dxT: np.ndarra
         r = xbar_{t+1} + vbar_{t+1}/h,   H lam = r,
         xbar_t += M/h^2 lam - vbar_{t+1}/h,   vbar_t = M/h lam,
         thetabar_j -= sum_{i in tet j} lam_i . dE_j/dx_i   (theta_j = log E_j).
-    Returns (dL/dlogE per tet, dL/dv_0 (N,3), dL/dx_0 (N,3)).
+    Returns (dL/dlogE per tet, dL/dv_0 (N,3), dL/dx_0 (N,3)).  The linear
+    solve is dense LU for small meshes and a sparse direct solve (scipy) for
+    larger ones (sparse=None picks by size).
     """
     n = model.n
     fd = np.repeat(model.free, 3)
@@ -378,15 +383,33 @@ def dense_adjoint(model: Model, p: Params, h: float, xs: list, dL_dxT: np.ndarra
     vbar = np.zeros(3 * n)
     theta_bar = np.zeros(model.t)
     T = len(xs) - 1
+    if sparse is None:
+        sparse = n > 400
     for t in range(T - 1, -1, -1):
         x1 = np.asarray(xs[t + 1], np.float64).reshape(-1, 3)
-        H = model.elastic_hess(x1) + np.diag(m / h ** 2)
         nrm, d, act = model._ground_terms(p, x1)
-        for i in np.nonzero(act)[0]:
-            H[3 * i:3 * i + 3, 3 * i:3 * i + 3] += p.k_c * np.outer(nrm, nrm)
+        diag = m / h ** 2
         r = xbar + vbar / h
         lam = np.zeros(3 * n)
-        lam[fd] = np.linalg.solve(H[np.ix_(fd, fd)], r[fd])
+        if sparse:
+            import scipy.sparse as sp
+            import scipy.sparse.linalg as spla
+            H = model.elastic_hess(x1, sparse=True) + sp.diags(diag)
+            if act.any():
+                rows, cols, vals = [], [], []
+                for i in np.nonzero(act)[0]:
+                    for a_ in range(3):
+                        for b_ in range(3):
+                            rows.append(3 * i + a_); cols.append(3 * i + b_)
+                            vals.append(p.k_c * nrm[a_] * nrm[b_])
+                H = H + sp.csr_matrix((vals, (rows, cols)), shape=H.shape)
+            idx = np.nonzero(fd)[0]
+            lam[fd] = spla.spsolve(H[idx][:, idx].tocsc(), r[fd])
+        else:
+            H = model.elastic_hess(x1) + np.diag(diag)
+            for i in np.nonzero(act)[0]:
+                H[3 * i:3 * i + 3, 3 * i:3 * i + 3] += p.k_c * np.outer(nrm, nrm)
+            lam[fd] = np.linalg.solve(H[np.ix_(fd, fd)], r[fd])
         tg = model.tet_grads(x1)  # (T, 4, 3)
         lam3 = lam.reshape(-1, 3)
         theta_bar -= np.einsum("tkr,tkr->t", tg, lam3[model.tets])

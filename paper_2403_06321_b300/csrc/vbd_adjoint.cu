@@ -3,6 +3,8 @@
 // implicit function theorem to dG/dx = 0 of Eq. 2, with y from Eq. 3 and the
 // velocity update of Eq. 6).
 //
+// Positions are displacements u = x - X (tape rows included), and the element
+// is evaluated from F = I + D as in the forward sweep.
 // For a recorded step t with end positions x_{t+1} and H = M/h^2 + d2E/dx2
 // (+ the ground penalty Hessian), going backwards:
 //   r = xbar_{t+1} + vbar_{t+1} / h,   H lam = r   (colour-ordered block GS),
@@ -22,7 +24,9 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
-__device__ __forceinline__ float3 sub(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 sub(float3 a, float3 b) {
+    return make_float3(a.x - b.x, a.y - b.y, a.z - b.z);
+}
 __device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 __device__ __forceinline__ float3 cross(float3 a, float3 b) {
     return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
@@ -45,16 +49,51 @@ struct AdjAcc {
     float h00, h01, h02, h11, h12, h22;    // elastic diagonal block
 };
 
+// F = I + D restricted to what the adjoint needs: D from the displacements
+// (columns D0..D2), tr D, cof(D) columns q0..q2 and J - 1.
+struct DForm {
+    float3 D0, D1, D2, q0, q1, q2;
+    float tr, jm1;
+    // cof(F) v = v + (tr D) v - D^T v + cof(D) v
+    __device__ __forceinline__ float3 cof(float3 v) const {
+        return make_float3(v.x + tr * v.x - dot(D0, v) + v.x * q0.x + v.y * q1.x + v.z * q2.x,
+                           v.y + tr * v.y - dot(D1, v) + v.x * q0.y + v.y * q1.y + v.z * q2.y,
+                           v.z + tr * v.z - dot(D2, v) + v.x * q0.z + v.y * q1.z + v.z * q2.z);
+    }
+    // D v
+    __device__ __forceinline__ float3 dmul(float3 v) const { return mulF(D0, D1, D2, v); }
+};
+
+__device__ __forceinline__ DForm make_dform(const float3 d[3], const float3 g[3]) {
+    DForm f;
+    f.D0 = make_float3(0.f, 0.f, 0.f);
+    f.D1 = f.D0;
+    f.D2 = f.D0;
+    for (int k = 0; k < 3; ++k) {
+        f.D0.x += d[k].x * g[k].x; f.D0.y += d[k].y * g[k].x; f.D0.z += d[k].z * g[k].x;
+        f.D1.x += d[k].x * g[k].y; f.D1.y += d[k].y * g[k].y; f.D1.z += d[k].z * g[k].y;
+        f.D2.x += d[k].x * g[k].z; f.D2.y += d[k].y * g[k].z; f.D2.z += d[k].z * g[k].z;
+    }
+    f.tr = f.D0.x + f.D1.y + f.D2.z;
+    const float m2 = (f.D0.x * f.D1.y - f.D1.x * f.D0.y) + (f.D0.x * f.D2.z - f.D2.x * f.D0.z) +
+                     (f.D1.y * f.D2.z - f.D2.y * f.D1.z);
+    f.q0 = cross(f.D1, f.D2);
+    f.q1 = cross(f.D2, f.D0);
+    f.q2 = cross(f.D0, f.D1);
+    f.jm1 = f.tr + m2 + dot(f.D0, f.q0);
+    return f;
+}
+
 template <int L>
 __global__ void __launch_bounds__(256) k_adj_sweep(Dev d, const float4 *__restrict__ xs, SweepParams p) {
     const int lane = threadIdx.x & (L - 1);
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int vi = p.vbegin + (int)(gt / L);
     const bool active = vi < p.vend;
-    float3 xi = make_float3(0.f, 0.f, 0.f);
+    float3 ui = make_float3(0.f, 0.f, 0.f);
     int s0 = 0, s1 = 0;
     if (active) {
-        xi = f3(xs[vi]);
+        ui = f3(xs[vi]);
         s0 = d.slot_off[vi];
         s1 = d.slot_off[vi + 1];
     }
@@ -74,31 +113,21 @@ __global__ void __launch_bounds__(256) k_adj_sweep(Dev d, const float4 *__restri
                                       -(g[0].z + g[1].z + g[2].z));
         float3 e[3], lk[3];
         for (int k = 0; k < 3; ++k) {
-            e[k] = sub(f3(__ldg(xs + nb[k])), xi);
+            e[k] = sub(f3(__ldg(xs + nb[k])), ui);
             lk[k] = f3(d.lam[nb[k]]);  // written by other colours' launches only
         }
-        float3 f0 = make_float3(0.f, 0.f, 0.f), f1 = f0, f2 = f0;
-        for (int k = 0; k < 3; ++k) {
-            f0.x += e[k].x * g[k].x; f0.y += e[k].y * g[k].x; f0.z += e[k].z * g[k].x;
-            f1.x += e[k].x * g[k].y; f1.y += e[k].y * g[k].y; f1.z += e[k].z * g[k].y;
-            f2.x += e[k].x * g[k].z; f2.y += e[k].y * g[k].z; f2.z += e[k].z * g[k].z;
-        }
-        const float3 c0 = cross(f1, f2), c1 = cross(f2, f0), c2 = cross(f0, f1);
-        const float J = dot(f0, c0);
-        // cof(F) v
-        auto cof = [&](float3 v) {
-            return make_float3(v.x * c0.x + v.y * c1.x + v.z * c2.x, v.x * c0.y + v.y * c1.y + v.z * c2.y,
-                               v.x * c0.z + v.y * c1.z + v.z * c2.z);
-        };
-        const float3 ci = cof(gi);
-        const float kJ = Vlam * J - (Vlam + Vmu);  // V lam (J - alpha)
-        float sc = 0.f;                              // sum_k c_k . lam_k
+        const DForm F = make_dform(e, g);
+        const float3 ci = F.cof(gi);
+        const float kJ = Vlam * F.jm1 - Vmu;  // V lam (J - alpha)
+        float sc = 0.f;                         // sum_k c_k . lam_k
         float3 q = make_float3(0.f, 0.f, 0.f);
         for (int k = 0; k < 3; ++k) {
             const float gg = Vmu * dot(gi, g[k]);
             q.x += gg * lk[k].x; q.y += gg * lk[k].y; q.z += gg * lk[k].z;
-            sc += dot(cof(g[k]), lk[k]);
-            const float3 w = cross(mulF(f0, f1, f2, cross(g[k], gi)), lk[k]);
+            sc += dot(F.cof(g[k]), lk[k]);
+            const float3 w0 = cross(g[k], gi);      // F (g_k x g_i) = w0 + D w0
+            const float3 Dw = F.dmul(w0);
+            const float3 w = cross(make_float3(w0.x + Dw.x, w0.y + Dw.y, w0.z + Dw.z), lk[k]);
             q.x += kJ * w.x; q.y += kJ * w.y; q.z += kJ * w.z;
         }
         q.x += Vlam * ci.x * sc; q.y += Vlam * ci.y * sc; q.z += Vlam * ci.z * sc;
@@ -120,7 +149,8 @@ __global__ void __launch_bounds__(256) k_adj_sweep(Dev d, const float4 *__restri
     const float b0 = r.x - a.q0, b1 = r.y - a.q1, b2 = r.z - a.q2;
     float h00 = a.h00 + mh2, h11 = a.h11 + mh2, h22 = a.h22 + mh2, h01 = a.h01, h02 = a.h02, h12 = a.h12;
     if (p.ground_on) {
-        const float pen = p.gh - (p.gn.x * xi.x + p.gn.y * xi.y + p.gn.z * xi.z);
+        const float4 X = d.rest[vi];
+        const float pen = p.gh - (p.gn.x * (X.x + ui.x) + p.gn.y * (X.y + ui.y) + p.gn.z * (X.z + ui.z));
         if (pen > 0.f) {
             h00 += p.kc * p.gn.x * p.gn.x; h11 += p.kc * p.gn.y * p.gn.y; h22 += p.kc * p.gn.z * p.gn.z;
             h01 += p.kc * p.gn.x * p.gn.y; h02 += p.kc * p.gn.x * p.gn.z; h12 += p.kc * p.gn.y * p.gn.z;
@@ -175,37 +205,33 @@ __global__ void k_adj_post_verts(Dev d, int n, int n_free, float h) {
     d.vbar[i] = make_float4(b * l.x, b * l.y, b * l.z, 0.f);
 }
 
-// gtheta_j -= sum_k lam_k . V P g_k at the recorded positions (dE_j/dlogE_j = E_j)
+// gtheta_j -= sum_k lam_k . V P g_k at the recorded positions (dE_j/dlogE_j = E_j),
+// V P g_k = V mu (D g_k - c'_k) + V lam (J - 1) (g_k + c'_k),  c'_k = cof(F) g_k - g_k
 __global__ void k_adj_post_tets(Dev d, const float4 *__restrict__ xs, int n_tets) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_tets) return;
     const int4 t = d.tet_v[j];
     const int id[4] = {t.x, t.y, t.z, t.w};
     const float *B = d.tet_B + 9 * (size_t)j;
-    float3 x[4];
-    for (int k = 0; k < 4; ++k) x[k] = f3(xs[id[k]]);
-    float3 g[4];
-    g[1] = make_float3(B[0], B[1], B[2]);
-    g[2] = make_float3(B[3], B[4], B[5]);
-    g[3] = make_float3(B[6], B[7], B[8]);
-    g[0] = make_float3(-(g[1].x + g[2].x + g[3].x), -(g[1].y + g[2].y + g[3].y), -(g[1].z + g[2].z + g[3].z));
-    float3 f0 = make_float3(0.f, 0.f, 0.f), f1 = f0, f2 = f0;
-    for (int k = 1; k < 4; ++k) {
-        const float3 e = sub(x[k], x[0]);
-        f0.x += e.x * g[k].x; f0.y += e.y * g[k].x; f0.z += e.z * g[k].x;
-        f1.x += e.x * g[k].y; f1.y += e.y * g[k].y; f1.z += e.z * g[k].y;
-        f2.x += e.x * g[k].z; f2.y += e.y * g[k].z; f2.z += e.z * g[k].z;
-    }
-    const float3 c0 = cross(f1, f2), c1 = cross(f2, f0), c2 = cross(f0, f1);
-    const float J = dot(f0, c0);
+    float3 g[3];
+    g[0] = make_float3(B[0], B[1], B[2]);
+    g[1] = make_float3(B[3], B[4], B[5]);
+    g[2] = make_float3(B[6], B[7], B[8]);
+    const float3 g0 = make_float3(-(g[0].x + g[1].x + g[2].x), -(g[0].y + g[1].y + g[2].y),
+                                  -(g[0].z + g[1].z + g[2].z));
+    const float3 u0 = f3(xs[id[0]]);
+    float3 e[3];
+    for (int k = 0; k < 3; ++k) e[k] = sub(f3(xs[id[k + 1]]), u0);
+    const DForm F = make_dform(e, g);
     const float mu = d.tet_mu[j], lam = d.tet_lam[j], V = d.tet_V[j];
-    const float kJ = lam * (J - (1.f + mu / lam));
     float acc = 0.f;
     for (int k = 0; k < 4; ++k) {
+        const float3 gk = k == 0 ? g0 : g[k - 1];
         const float3 l = f3(d.lam[id[k]]);
-        const float3 Fg = mulF(f0, f1, f2, g[k]);
-        const float3 cg = mulF(c0, c1, c2, g[k]);
-        acc += V * (mu * dot(Fg, l) + kJ * dot(cg, l));
+        const float3 c = F.cof(gk);                  // g_k + c'_k
+        const float3 Dg = F.dmul(gk);
+        const float3 cp = make_float3(c.x - gk.x, c.y - gk.y, c.z - gk.z);
+        acc += V * (mu * (dot(Dg, l) - dot(cp, l)) + lam * F.jm1 * dot(c, l));
     }
     d.gtheta[j] -= acc;
 }

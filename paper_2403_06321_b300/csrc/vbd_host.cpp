@@ -218,8 +218,9 @@ size_t carve(const vbd_ctx *c, char *base, Dev *d) {
     };
     const size_t N = (size_t)c->N, T = (size_t)c->T, S = (size_t)std::max<long long>(c->n_slots, 1);
     Dev t{};
-    t.x = (float4 *)take(16 * N);
-    t.xt = (float4 *)take(16 * N);
+    t.u = (float4 *)take(16 * N);
+    t.ut = (float4 *)take(16 * N);
+    t.rest = (float4 *)take(16 * N);
     t.v = (float4 *)take(16 * N);
     t.vprev = (float4 *)take(16 * N);
     t.ym = (float4 *)take(16 * N);
@@ -587,14 +588,17 @@ vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *st
     CU(cudaMemcpyAsync(d.new_of_orig, ctx->new_of_orig.data(), 4 * (size_t)N, cudaMemcpyHostToDevice, s),
        "upload permutation");
     CU(cudaMemsetAsync(d.counters, 0, 64, s), "clear counters");
-    // state: x = rest, v = v_prev = 0
-    std::vector<float> restf(3 * (size_t)N);
-    for (size_t k = 0; k < restf.size(); ++k) restf[k] = (float)ctx->rest[k];
-    CU(cudaMemcpyAsync(d.stage[0], restf.data(), 12 * (size_t)N, cudaMemcpyHostToDevice, s), "upload rest");
-    vbd::launch_scatter(d.stage[0], d.x, d.new_of_orig, N, s);
+    // rest positions (FP32, internal order); state x = rest (u = 0), v = v_prev = 0
+    std::vector<float4> restf(N);
+    for (int k = 0; k < N; ++k) {
+        const double *X = &ctx->rest[3 * (size_t)ctx->orig_of_new[k]];
+        restf[k] = make_float4((float)X[0], (float)X[1], (float)X[2], 0.f);
+    }
+    CU(cudaMemcpyAsync(d.rest, restf.data(), 16 * (size_t)N, cudaMemcpyHostToDevice, s), "upload rest");
+    CU(cudaMemsetAsync(d.u, 0, 16 * (size_t)N, s), "clear u");
     CU(cudaMemsetAsync(d.v, 0, 16 * (size_t)N, s), "clear v");
     CU(cudaMemsetAsync(d.vprev, 0, 16 * (size_t)N, s), "clear v_prev");
-    CU(cudaMemsetAsync(d.xt, 0, 16 * (size_t)N, s), "clear x^t");
+    CU(cudaMemsetAsync(d.ut, 0, 16 * (size_t)N, s), "clear u^t");
     CU(cudaStreamSynchronize(s), "bind upload");  // host staging vectors die here
     CU(cudaGetLastError(), "bind kernels");
     ctx->bound = true;
@@ -631,14 +635,16 @@ vbd_status vbd_set_state(vbd_ctx *ctx, const float *x, const float *v, const flo
     if (ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_set_state inside a step");
     const size_t bytes = 12 * (size_t)ctx->N;
     const float *src[3] = {x, v, v_prev ? v_prev : v};
-    float4 *dst[3] = {ctx->d.x, ctx->d.v, ctx->d.vprev};
+    float4 *dst[3] = {ctx->d.u, ctx->d.v, ctx->d.vprev};
     for (int k = 0; k < 3; ++k) {
         const float *from = src[k];
         if (!is_device_ptr(from)) {
             CU(cudaMemcpyAsync(ctx->d.stage[k], from, bytes, cudaMemcpyDefault, ctx->stream), "state upload");
             from = ctx->d.stage[k];
         }
-        vbd::launch_scatter(from, dst[k], ctx->d.new_of_orig, ctx->N, ctx->stream);
+        // positions become displacements from the rest shape
+        vbd::launch_scatter(from, dst[k], ctx->d.new_of_orig, k == 0 ? ctx->d.rest : nullptr, ctx->N,
+                            ctx->stream);
     }
     CU(cudaGetLastError(), "set_state");
     ctx->tape_len = 0;
@@ -651,14 +657,15 @@ vbd_status vbd_get_state(vbd_ctx *ctx, float *x, float *v) {
     if (st != VBD_OK) return st;
     const size_t bytes = 12 * (size_t)ctx->N;
     float *dst[2] = {x, v};
-    const float4 *src[2] = {ctx->d.x, ctx->d.v};
+    const float4 *src[2] = {ctx->d.u, ctx->d.v};
     bool host = false;
     for (int k = 0; k < 2; ++k) {
         if (!dst[k]) continue;
+        const float4 *rest = k == 0 ? ctx->d.rest : nullptr;  // x = X + u
         if (is_device_ptr(dst[k])) {
-            vbd::launch_gather(src[k], dst[k], ctx->d.new_of_orig, ctx->N, ctx->stream);
+            vbd::launch_gather(src[k], dst[k], ctx->d.new_of_orig, rest, ctx->N, ctx->stream);
         } else {
-            vbd::launch_gather(src[k], ctx->d.stage[k], ctx->d.new_of_orig, ctx->N, ctx->stream);
+            vbd::launch_gather(src[k], ctx->d.stage[k], ctx->d.new_of_orig, rest, ctx->N, ctx->stream);
             CU(cudaMemcpyAsync(dst[k], ctx->d.stage[k], bytes, cudaMemcpyDefault, ctx->stream), "state download");
             host = true;
         }

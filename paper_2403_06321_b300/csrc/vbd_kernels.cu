@@ -39,46 +39,51 @@ struct Acc {
     float f0, f1, f2, h00, h01, h02, h11, h12, h22;
 };
 
-// Contribution of one tet to the vertex that owns slot s (Eqs. 8-9 with the
-// stable neo-Hookean element):  with e_k = x_k - x_i for the three other
-// vertices and their shape gradients g_k,
-//   F = sum_k e_k g_k^T,  g_i = -(g_a + g_b + g_c),  c = cof(F) g_i,
-//   f_i -= V P g_i = V mu F g_i + V lam (J - alpha) c,   (alpha lam = lam + mu)
-//   H_i += V mu |g_i|^2 I + V lam c c^T.
-__device__ __forceinline__ void accumulate_slot(const float4 *__restrict__ x, int4 r0, float4 r1,
-                                                float4 r2, float2 r3, float3 xi, Acc &acc) {
-    const float3 pa = f3(__ldg(x + r0.x));
-    const float3 pb = f3(__ldg(x + r0.y));
-    const float3 pc = f3(__ldg(x + r0.z));
+// Contribution of one tet to the vertex that owns the slot (Eqs. 8-9 with the
+// stable neo-Hookean element), written in terms of displacements so that no
+// step subtracts nearly equal numbers.  With d_k = u_k - u_i for the three
+// other vertices and their shape gradients g_k (g_i = -(g_a + g_b + g_c)):
+//   F = I + D,  D = sum_k d_k g_k^T
+//   J - 1      = tr D + (sum of principal 2x2 minors of D) + det D
+//   c' = cof(F) g_i - g_i = (tr D) g_i - D^T g_i + cof(D) g_i,   c = g_i + c'
+//   V P g_i    = V mu (D g_i - c') + V lam (J - 1) c     (alpha lam = lam + mu)
+//   f_i -= V P g_i,   H_i += V mu |g_i|^2 I + V lam c c^T.
+__device__ __forceinline__ void accumulate_slot(const float4 *__restrict__ u, int4 r0, float4 r1,
+                                                float4 r2, float2 r3, float3 ui, Acc &acc) {
+    const float3 da = f3(__ldg(u + r0.x)) - ui;
+    const float3 db = f3(__ldg(u + r0.y)) - ui;
+    const float3 dc = f3(__ldg(u + r0.z)) - ui;
     const float Vmu = __int_as_float(r0.w);
     const float Vlam = r3.y;
     const float3 ga = make_float3(r1.x, r1.y, r1.z);
     const float3 gb = make_float3(r1.w, r2.x, r2.y);
     const float3 gc = make_float3(r2.z, r2.w, r3.x);
     const float3 gi = make_float3(-(ga.x + gb.x + gc.x), -(ga.y + gb.y + gc.y), -(ga.z + gb.z + gc.z));
-    const float3 ea = pa - xi, eb = pb - xi, ec = pc - xi;
-    // columns of F: f_s = ea * ga[s] + eb * gb[s] + ec * gc[s]
-    const float3 f0 = make_float3(ea.x * ga.x + eb.x * gb.x + ec.x * gc.x,
-                                  ea.y * ga.x + eb.y * gb.x + ec.y * gc.x,
-                                  ea.z * ga.x + eb.z * gb.x + ec.z * gc.x);
-    const float3 f1 = make_float3(ea.x * ga.y + eb.x * gb.y + ec.x * gc.y,
-                                  ea.y * ga.y + eb.y * gb.y + ec.y * gc.y,
-                                  ea.z * ga.y + eb.z * gb.y + ec.z * gc.y);
-    const float3 f2 = make_float3(ea.x * ga.z + eb.x * gb.z + ec.x * gc.z,
-                                  ea.y * ga.z + eb.y * gb.z + ec.y * gc.z,
-                                  ea.z * ga.z + eb.z * gb.z + ec.z * gc.z);
-    const float3 c0 = cross(f1, f2), c1 = cross(f2, f0), c2 = cross(f0, f1);
-    const float J = dot(f0, c0);
-    const float3 c = make_float3(gi.x * c0.x + gi.y * c1.x + gi.z * c2.x,
-                                 gi.x * c0.y + gi.y * c1.y + gi.z * c2.y,
-                                 gi.x * c0.z + gi.y * c1.z + gi.z * c2.z);
-    const float3 Fg = make_float3(gi.x * f0.x + gi.y * f1.x + gi.z * f2.x,
-                                  gi.x * f0.y + gi.y * f1.y + gi.z * f2.y,
-                                  gi.x * f0.z + gi.y * f1.z + gi.z * f2.z);
-    const float k = Vlam * J - (Vlam + Vmu);
-    acc.f0 -= Vmu * Fg.x + k * c.x;
-    acc.f1 -= Vmu * Fg.y + k * c.y;
-    acc.f2 -= Vmu * Fg.z + k * c.z;
+    // columns of D: D_s = da * ga[s] + db * gb[s] + dc * gc[s]
+    const float3 D0 = make_float3(da.x * ga.x + db.x * gb.x + dc.x * gc.x,
+                                  da.y * ga.x + db.y * gb.x + dc.y * gc.x,
+                                  da.z * ga.x + db.z * gb.x + dc.z * gc.x);
+    const float3 D1 = make_float3(da.x * ga.y + db.x * gb.y + dc.x * gc.y,
+                                  da.y * ga.y + db.y * gb.y + dc.y * gc.y,
+                                  da.z * ga.y + db.z * gb.y + dc.z * gc.y);
+    const float3 D2 = make_float3(da.x * ga.z + db.x * gb.z + dc.x * gc.z,
+                                  da.y * ga.z + db.y * gb.z + dc.y * gc.z,
+                                  da.z * ga.z + db.z * gb.z + dc.z * gc.z);
+    const float tr = D0.x + D1.y + D2.z;
+    const float m2 = (D0.x * D1.y - D1.x * D0.y) + (D0.x * D2.z - D2.x * D0.z) + (D1.y * D2.z - D2.y * D1.z);
+    const float3 q0 = cross(D1, D2), q1 = cross(D2, D0), q2 = cross(D0, D1);  // columns of cof(D)
+    const float jm1 = tr + m2 + dot(D0, q0);
+    const float3 cp = make_float3(tr * gi.x - dot(D0, gi) + gi.x * q0.x + gi.y * q1.x + gi.z * q2.x,
+                                  tr * gi.y - dot(D1, gi) + gi.x * q0.y + gi.y * q1.y + gi.z * q2.y,
+                                  tr * gi.z - dot(D2, gi) + gi.x * q0.z + gi.y * q1.z + gi.z * q2.z);
+    const float3 c = make_float3(gi.x + cp.x, gi.y + cp.y, gi.z + cp.z);
+    const float3 Dg = make_float3(gi.x * D0.x + gi.y * D1.x + gi.z * D2.x,
+                                  gi.x * D0.y + gi.y * D1.y + gi.z * D2.y,
+                                  gi.x * D0.z + gi.y * D1.z + gi.z * D2.z);
+    const float k = Vlam * jm1;
+    acc.f0 -= Vmu * (Dg.x - cp.x) + k * c.x;
+    acc.f1 -= Vmu * (Dg.y - cp.y) + k * c.y;
+    acc.f2 -= Vmu * (Dg.z - cp.z) + k * c.z;
     const float d = Vmu * dot(gi, gi);
     acc.h00 += d + Vlam * c.x * c.x;
     acc.h11 += d + Vlam * c.y * c.y;
@@ -100,6 +105,7 @@ __device__ __forceinline__ float sub_reduce(float v) {
 // analytic inverse.
 __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams &p, int vi, float4 xi,
                                                 const Acc &a) {
+    // xi holds the displacement u_i; ym the displacement of the inertia target
     const float4 yv = d.ym[vi];
     const float mh2 = yv.w;
     const float kdh = p.kd_over_h;
@@ -110,7 +116,7 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
     float h00 = s * a.h00 + mh2, h11 = s * a.h11 + mh2, h22 = s * a.h22 + mh2;
     float h01 = s * a.h01, h02 = s * a.h02, h12 = s * a.h12;
     if (kdh != 0.0f) {
-        const float4 xt = d.xt[vi];
+        const float4 xt = d.ut[vi];
         const float dx = xi.x - xt.x, dy = xi.y - xt.y, dz = xi.z - xt.z;
         f0 -= kdh * (a.h00 * dx + a.h01 * dy + a.h02 * dz);
         f1 -= kdh * (a.h01 * dx + a.h11 * dy + a.h12 * dz);
@@ -118,7 +124,8 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
     }
     float flag = xi.w;
     if (p.ground_on) {
-        const float pen = p.gh - (p.gn.x * xi.x + p.gn.y * xi.y + p.gn.z * xi.z);
+        const float4 X = d.rest[vi];
+        const float pen = p.gh - (p.gn.x * (X.x + xi.x) + p.gn.y * (X.y + xi.y) + p.gn.z * (X.z + xi.z));
         if (pen > 0.0f) {
             const float kd = p.kc * pen;
             f0 += kd * p.gn.x; f1 += kd * p.gn.y; f2 += kd * p.gn.z;
@@ -138,7 +145,7 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
     const float tr3 = (h00 + h11 + h22) * (1.0f / 3.0f);
     if (!(fabsf(det) > p.det_eps * fabsf(tr3 * tr3 * tr3))) {
         atomicAdd(d.counters + 1, 1ull);
-        if (flag != xi.w) d.x[vi] = make_float4(xi.x, xi.y, xi.z, flag);
+        if (flag != xi.w) d.u[vi] = make_float4(xi.x, xi.y, xi.z, flag);
         return;
     }
     const float inv = 1.0f / det;
@@ -149,7 +156,7 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
         atomicAdd(d.counters + 0, 1ull);
         return;
     }
-    d.x[vi] = make_float4(xi.x + dx, xi.y + dy, xi.z + dz, flag);
+    d.u[vi] = make_float4(xi.x + dx, xi.y + dy, xi.z + dz, flag);
 }
 
 template <int L>
@@ -161,7 +168,7 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, SweepParams p) {
     float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
     int s0 = 0, s1 = 0;
     if (active) {
-        xi = d.x[vi];
+        xi = d.u[vi];
         s0 = d.slot_off[vi];
         s1 = d.slot_off[vi + 1];
     }
@@ -172,7 +179,7 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, SweepParams p) {
         const float4 r1 = __ldcs(d.s1 + s);
         const float4 r2 = __ldcs(d.s2 + s);
         const float2 r3 = __ldcs(d.s3 + s);
-        accumulate_slot(d.x, r0, r1, r2, r3, x3, acc);
+        accumulate_slot(d.u, r0, r1, r2, r3, x3, acc);
     }
     acc.f0 = sub_reduce<L>(acc.f0);
     acc.f1 = sub_reduce<L>(acc.f1);
@@ -191,10 +198,10 @@ __global__ void k_predict(Dev d, int n, int n_free, float h, float3 g, float gno
                           int cheby) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float4 xi = d.x[i];
-    d.xt[i] = make_float4(xi.x, xi.y, xi.z, 0.f);
+    const float4 xi = d.u[i];
+    d.ut[i] = make_float4(xi.x, xi.y, xi.z, 0.f);
     if (i >= n_free) {
-        d.x[i] = make_float4(xi.x, xi.y, xi.z, 0.f);
+        d.u[i] = make_float4(xi.x, xi.y, xi.z, 0.f);
         return;
     }
     const float4 vi = d.v[i];
@@ -216,7 +223,7 @@ __global__ void k_predict(Dev d, int n, int n_free, float h, float3 g, float gno
         xn = make_float4(xi.x + h * vi.x + ah2 * g.x, xi.y + h * vi.y + ah2 * g.y,
                          xi.z + h * vi.z + ah2 * g.z, 0.f);
     }
-    d.x[i] = xn;
+    d.u[i] = xn;
     if (cheby) d.cheb[0][i] = xn;
 }
 
@@ -227,13 +234,13 @@ __global__ void k_cheby(Dev d, int n_free, int n, float omega) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_free) return;
     float4 *hist = d.cheb[n & 1];
-    const float4 xb = d.x[i];
+    const float4 xb = d.u[i];
     float4 xn = xb;
     if (n >= 2 && xb.w == 0.f) {
         const float4 q = hist[i];
         xn = make_float4(omega * (xb.x - q.x) + q.x, omega * (xb.y - q.y) + q.y,
                          omega * (xb.z - q.z) + q.z, xb.w);
-        d.x[i] = xn;
+        d.u[i] = xn;
     }
     hist[i] = xn;
 }
@@ -242,23 +249,34 @@ __global__ void k_cheby(Dev d, int n_free, int n, float omega) {
 __global__ void k_finish(Dev d, int n, float h, float4 *tape_row) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float4 x = d.x[i], xt = d.xt[i];
+    const float4 x = d.u[i], xt = d.ut[i];
     d.vprev[i] = d.v[i];
     d.v[i] = make_float4((x.x - xt.x) / h, (x.y - xt.y) / h, (x.z - xt.z) / h, 0.f);
     if (tape_row) tape_row[i] = make_float4(x.x, x.y, x.z, 0.f);
     if (!(isfinite(x.x) && isfinite(x.y) && isfinite(x.z))) atomicAdd(d.counters + 0, 1ull);
 }
 
-__global__ void k_scatter(const float *src, float4 *dst, const int *new_of_orig, int n) {
+__global__ void k_scatter(const float *src, float4 *dst, const int *new_of_orig, const float4 *rest, int n) {
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= n) return;
-    dst[new_of_orig[o]] = make_float4(src[3 * o], src[3 * o + 1], src[3 * o + 2], 0.f);
+    const int i = new_of_orig[o];
+    float4 a = make_float4(src[3 * o], src[3 * o + 1], src[3 * o + 2], 0.f);
+    if (rest) {
+        const float4 X = rest[i];
+        a.x -= X.x; a.y -= X.y; a.z -= X.z;
+    }
+    dst[i] = a;
 }
 
-__global__ void k_gather(const float4 *src, float *dst, const int *new_of_orig, int n) {
+__global__ void k_gather(const float4 *src, float *dst, const int *new_of_orig, const float4 *rest, int n) {
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= n) return;
-    const float4 a = src[new_of_orig[o]];
+    const int i = new_of_orig[o];
+    float4 a = src[i];
+    if (rest) {
+        const float4 X = rest[i];
+        a.x += X.x; a.y += X.y; a.z += X.z;
+    }
     dst[3 * o] = a.x;
     dst[3 * o + 1] = a.y;
     dst[3 * o + 2] = a.z;
@@ -266,10 +284,11 @@ __global__ void k_gather(const float4 *src, float *dst, const int *new_of_orig, 
 
 __global__ void k_restore_x(Dev d, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) d.x[i] = d.xt[i];
+    if (i < n) d.u[i] = d.ut[i];
 }
 
 // ---- FP64 energy of Eq. 2 (diagnostics) -----------------------------------
+// Psi = mu/2 (tr F^T F - 3) + lam/2 (J - alpha)^2 evaluated from F = I + D.
 constexpr int EB = 256;
 
 __device__ __forceinline__ void block_sum_store(double v, double *out) {
@@ -289,12 +308,13 @@ __global__ void __launch_bounds__(EB) k_energy_verts(Dev d, int n_free, double i
                                                      double *partials) {
     double e = 0.0;
     for (int i = blockIdx.x * EB + threadIdx.x; i < n_free; i += gridDim.x * EB) {
-        const float4 x = d.x[i], y = d.ym[i];
+        const float4 x = d.u[i], y = d.ym[i], X = d.rest[i];
         const double dx = (double)x.x - y.x, dy = (double)x.y - y.y, dz = (double)x.z - y.z;
         e += (double)d.mass[i] * inv_2h2 * (dx * dx + dy * dy + dz * dz);
         if (p.ground_on) {
-            const double pen = (double)p.gh - ((double)p.gn.x * x.x + (double)p.gn.y * x.y +
-                                               (double)p.gn.z * x.z);
+            const double pen = (double)p.gh - ((double)p.gn.x * ((double)X.x + x.x) +
+                                               (double)p.gn.y * ((double)X.y + x.y) +
+                                               (double)p.gn.z * ((double)X.z + x.z));
             if (pen > 0.0) e += 0.5 * (double)p.kc * pen * pen;
         }
     }
@@ -304,25 +324,30 @@ __global__ void __launch_bounds__(EB) k_energy_verts(Dev d, int n_free, double i
 __global__ void __launch_bounds__(EB) k_energy_tets(Dev d, int n_tets, double *partials) {
     double e = 0.0;
     for (int j = blockIdx.x * EB + threadIdx.x; j < n_tets; j += gridDim.x * EB) {
+        // F = I + D with D from the displacements (rest edges times B give I)
         const int4 t = d.tet_v[j];
-        const float4 p0 = d.x[t.x], p1 = d.x[t.y], p2 = d.x[t.z], p3 = d.x[t.w];
-        const double D[3][3] = {{(double)p1.x - p0.x, (double)p2.x - p0.x, (double)p3.x - p0.x},
+        const float4 p0 = d.u[t.x], p1 = d.u[t.y], p2 = d.u[t.z], p3 = d.u[t.w];
+        const double E[3][3] = {{(double)p1.x - p0.x, (double)p2.x - p0.x, (double)p3.x - p0.x},
                                 {(double)p1.y - p0.y, (double)p2.y - p0.y, (double)p3.y - p0.y},
                                 {(double)p1.z - p0.z, (double)p2.z - p0.z, (double)p3.z - p0.z}};
         const float *B = d.tet_B + 9 * (size_t)j;
-        double F[3][3];
+        double D[3][3];
         for (int r = 0; r < 3; ++r)
             for (int s = 0; s < 3; ++s)
-                F[r][s] = D[r][0] * B[s] + D[r][1] * B[3 + s] + D[r][2] * B[6 + s];
-        const double J = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) -
-                         F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +
-                         F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
-        double ic = 0.0;
+                D[r][s] = E[r][0] * B[s] + E[r][1] * B[3 + s] + E[r][2] * B[6 + s];
+        const double tr = D[0][0] + D[1][1] + D[2][2];
+        const double m2 = (D[0][0] * D[1][1] - D[0][1] * D[1][0]) + (D[0][0] * D[2][2] - D[0][2] * D[2][0]) +
+                          (D[1][1] * D[2][2] - D[1][2] * D[2][1]);
+        const double det = D[0][0] * (D[1][1] * D[2][2] - D[1][2] * D[2][1]) -
+                           D[0][1] * (D[1][0] * D[2][2] - D[1][2] * D[2][0]) +
+                           D[0][2] * (D[1][0] * D[2][1] - D[1][1] * D[2][0]);
+        double dd = 0.0;
         for (int r = 0; r < 3; ++r)
-            for (int s = 0; s < 3; ++s) ic += F[r][s] * F[r][s];
+            for (int s = 0; s < 3; ++s) dd += D[r][s] * D[r][s];
         const double mu = d.tet_mu[j], lam = d.tet_lam[j];
-        const double alpha = 1.0 + mu / lam;
-        e += (double)d.tet_V[j] * (0.5 * mu * (ic - 3.0) + 0.5 * lam * (J - alpha) * (J - alpha));
+        const double jma = tr + m2 + det - mu / lam;  // J - alpha
+        // tr F^T F - 3 = 2 tr D + |D|^2
+        e += (double)d.tet_V[j] * (0.5 * mu * (2.0 * tr + dd) + 0.5 * lam * jma * jma);
     }
     block_sum_store(e, partials + blockIdx.x);
 }
@@ -390,12 +415,14 @@ void launch_finish(const Dev &d, int n, float h, float4 *tape_row, cudaStream_t 
     k_finish<<<blocks_for(n, 256), 256, 0, s>>>(d, n, h, tape_row);
 }
 
-void launch_scatter(const float *src, float4 *dst, const int *new_of_orig, int n, cudaStream_t s) {
-    k_scatter<<<blocks_for(n, 256), 256, 0, s>>>(src, dst, new_of_orig, n);
+void launch_scatter(const float *src, float4 *dst, const int *new_of_orig, const float4 *rest, int n,
+                    cudaStream_t s) {
+    k_scatter<<<blocks_for(n, 256), 256, 0, s>>>(src, dst, new_of_orig, rest, n);
 }
 
-void launch_gather(const float4 *src, float *dst, const int *new_of_orig, int n, cudaStream_t s) {
-    k_gather<<<blocks_for(n, 256), 256, 0, s>>>(src, dst, new_of_orig, n);
+void launch_gather(const float4 *src, float *dst, const int *new_of_orig, const float4 *rest, int n,
+                   cudaStream_t s) {
+    k_gather<<<blocks_for(n, 256), 256, 0, s>>>(src, dst, new_of_orig, rest, n);
 }
 
 void launch_restore_x(const Dev &d, int n, cudaStream_t s) {

@@ -9,12 +9,16 @@ namespace vbd {
 // Device arrays, all carved out of the caller's workspace.  Vertices are in
 // colour-major order: free vertices of colour 0, colour 1, ..., then pinned
 // vertices.  Tets keep the caller's order.
+// Positions are kept as displacements from the rest shape, u = x - X, so
+// that FP32 resolves small strains at any distance from the origin; every
+// quantity below that is a position (u, ut, ym, cheb, tape) is a displacement.
 struct Dev {
-    float4 *x;        // current positions; .w = 1 once the vertex touched the ground this step
-    float4 *xt;       // x^t (start of step)
+    float4 *u;        // current displacement; .w = 1 once the vertex touched the ground this step
+    float4 *ut;       // u^t (start of step)
     float4 *v;        // v^t
     float4 *vprev;    // v^{t-1}
-    float4 *ym;       // inertia target y (Eq. 3) in .xyz, m_i / h^2 in .w
+    float4 *ym;       // inertia target y - X (Eq. 3) in .xyz, m_i / h^2 in .w
+    float4 *rest;     // rest position X (FP32), used to form x = X + u
     float4 *cheb[2];  // Chebyshev history (Eq. 18), roles alternate with iteration parity
     float *mass;      // lumped mass
     int *slot_off;    // n_free + 1: slots of free vertex i are [slot_off[i], slot_off[i+1])
@@ -34,7 +38,7 @@ struct Dev {
     unsigned long long *counters;  // [0] non-finite updates, [1] det skips
     double *partials; // energy partial sums
     double *energy_out;
-    float4 *tape;     // tape_steps * N positions
+    float4 *tape;     // tape_steps * N displacements
     // adjoint
     float4 *lam, *rhs, *xbar, *vbar;
     float *gtheta;    // T
@@ -57,8 +61,12 @@ void launch_predict(const Dev &d, int n, int n_free, float h, float3 g, int init
 void launch_sweep(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s);
 void launch_cheby(const Dev &d, int n_free, int n, float omega, cudaStream_t s);
 void launch_finish(const Dev &d, int n, float h, float4 *tape_row, cudaStream_t s);
-void launch_scatter(const float *src, float4 *dst, const int *new_of_orig, int n, cudaStream_t s);
-void launch_gather(const float4 *src, float *dst, const int *new_of_orig, int n, cudaStream_t s);
+// caller order <-> internal order; with `rest` non-null the caller array holds
+// positions and the internal one displacements (u = x - X)
+void launch_scatter(const float *src, float4 *dst, const int *new_of_orig, const float4 *rest, int n,
+                    cudaStream_t s);
+void launch_gather(const float4 *src, float *dst, const int *new_of_orig, const float4 *rest, int n,
+                   cudaStream_t s);
 void launch_restore_x(const Dev &d, int n, cudaStream_t s);
 void launch_energy(const Dev &d, int n_free, int n_tets, double h, const SweepParams &p,
                    cudaStream_t s);

@@ -318,6 +318,7 @@ class Sim:
                           vert_offset, tet_offset)
         self.n_verts = arrs.rest.shape[0]
         self.n_tets = arrs.tets.shape[0]
+        self.tape_steps = int(params.tape_steps)
         self.ctx = vbd_create_mesh(arrs.desc(), params)
         try:
             self.n_colors = vbd_color(self.ctx, colors)

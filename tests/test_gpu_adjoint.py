@@ -1,0 +1,99 @@
+"""GPU adjoint (vbd_backward, via the torch.autograd wrapper) against the
+oracle's FP64 adjoint of the same steps.  The oracle adjoint is itself
+pinned to central finite differences (tests/test_oracle_adjoint.py).
+Gate: gradients within 1e-3 relative (2-norm) of the oracle's."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2403_06321_b300 import synth, vbd
+from paper_2403_06321_b300.autograd import simulate
+from gpu_util import params_of
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2403_06321_b300.build import build
+    build()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _gpu_grads(m, pd, colors, h, iters, steps, v0, tip, target, adj_iters, logE=None):
+    sim = vbd.Sim(m, vbd.make_params(tape_steps=steps, **pd), colors=colors)
+    try:
+        dev = sim.workspace.device
+        le = torch.tensor(np.log(m.young.astype(np.float64)) if logE is None else logE,
+                          dtype=torch.float32, device=dev, requires_grad=True)
+        vv = torch.tensor(v0, dtype=torch.float32, device=dev, requires_grad=True)
+        x0 = torch.tensor(m.rest, dtype=torch.float32, device=dev)
+        xT = simulate(le, vv, sim, x0, h, iters, steps, adj_iters)
+        tip_t = torch.tensor(tip, device=dev)
+        tgt = torch.tensor(target, dtype=torch.float32, device=dev)
+        loss = ((xT[tip_t] - tgt) ** 2).sum(dim=1).mean()
+        gE, gv = torch.autograd.grad(loss, [le, vv])
+        sim.sync_status()
+        return (gE.cpu().numpy().astype(np.float64), gv.cpu().numpy().astype(np.float64),
+                xT.detach().cpu().numpy().astype(np.float64))
+    finally:
+        sim.close()
+
+
+def _oracle_grads(orc, m, pd, colors, h, iters, steps, v0, tip, target, newton=False):
+    model = orc.Model.from_mesh(m)
+    p = orc.Params.make(**pd)
+    x, v = m.rest.copy(), np.array(v0, np.float64)
+    vp = v.copy()
+    xs = [x.copy()]
+    for _ in range(steps):
+        if newton:
+            y = model.inertia_target(p, h, x, v)
+            xn = model.newton_solve(p, h, x + h * v, y, tol=1e-13)
+            vp, v, x = v, (xn - x) / h, xn
+        else:
+            model.step(p, colors, int(colors.max()) + 1, h, iters, x, v, vp)
+        xs.append(x.copy())
+    g = np.zeros_like(x)
+    g[tip] = 2.0 / len(tip) * (x[tip] - target)
+    gE, gv, _ = orc.dense_adjoint(model, p, h, xs, g)
+    return gE, gv, x
+
+
+def test_adjoint_converged_small_beam(orc):
+    """6x2x2 beam, 4 steps solved to convergence on both sides."""
+    m = synth.beam(6, 2, 2, E=1e5, nu=0.4, jitter_frac=0.05, seed=51)
+    colors, _ = orc.color_greedy(m.n_verts, m.tets)
+    pd = params_of(synth.SimConfig())
+    rng = np.random.default_rng(52)
+    v0 = rng.normal(0, 0.3, m.rest.shape) * (1 - m.pinned[:, None])
+    tip = np.nonzero(m.grid_ijk[:, 0] == 6)[0]
+    target = m.rest[tip] + np.array([0.05, -0.03, 0.08])
+    h, steps = 1 / 60, 4
+    gE, gv, xg = _gpu_grads(m, pd, colors, h, 400, steps, v0, tip, target, adj_iters=300)
+    oE, ov, xo = _oracle_grads(orc, m, pd, colors, h, 0, steps, v0, tip, target, newton=True)
+    print("small beam: |x|err %.2e  dlogE rel %.2e  dv0 rel %.2e" % (
+        np.abs(xg - xo).max(), _rel(gE, oE), _rel(gv, ov)))
+    assert np.abs(xg - xo).max() < 1e-5
+    assert _rel(gE, oE) <= 1e-3 and _rel(gv, ov) <= 1e-3
+    assert np.all(gv[m.pinned == 1] == 0)
+
+
+def test_adjoint_differentiable_beam_full_size(orc):
+    """40x8x8 beam (3,321 verts, 15,360 tets), 30 steps of 50 iterations; both
+    sides run the same fixed-iteration forward and apply the converged-step
+    adjoint at their own recorded positions."""
+    m, cfg, tip, target = synth.differentiable_beam()
+    colors = synth.kuhn_coloring(m.grid_ijk)
+    pd = params_of(cfg)
+    v0 = np.zeros_like(m.rest)
+    gE, gv, xg = _gpu_grads(m, pd, colors, cfg.h, cfg.iters, cfg.steps, v0, tip, target, adj_iters=150)
+    oE, ov, xo = _oracle_grads(orc, m, pd, colors, cfg.h, cfg.iters, cfg.steps, v0, tip, target)
+    diag = float(np.linalg.norm(m.rest.max(0) - m.rest.min(0)))
+    print("differentiable beam: x err/bbox %.2e  dlogE rel %.2e  dv0 rel %.2e" % (
+        np.abs(xg - xo).max() / diag, _rel(gE, oE), _rel(gv, ov)))
+    assert np.abs(xg - xo).max() <= 1e-5 * diag
+    assert _rel(gE, oE) <= 1e-3 and _rel(gv, ov) <= 1e-3

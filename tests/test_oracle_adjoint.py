@@ -88,3 +88,17 @@ def test_dense_adjoint_without_stiffness_is_free_fall(orc):
     assert np.allclose(gv, steps * H * dLdx, rtol=1e-8, atol=1e-12)
     assert np.allclose(gx, dLdx, rtol=1e-8, atol=1e-12)
     assert np.abs(gE).max() < 1e-9
+
+
+def test_sparse_and_dense_adjoint_agree(orc):
+    m = synth.beam(4, 2, 1, E=1e5, nu=0.4, jitter_frac=0.05, seed=22)
+    model = orc.Model.from_mesh(m)
+    p = orc.Params.make(gravity=(0, 0, -9.8), ground_on=True, ground_height=-0.001, k_c=1e5)
+    tip = np.nonzero(m.grid_ijk[:, 0] == 4)[0]
+    target = m.rest[tip] + 0.05
+    xs = _converged_forward(orc, model, p, m.rest, np.zeros_like(m.rest), 3)
+    g = _dloss(xs[-1], tip, target)
+    d = orc.dense_adjoint(model, p, H, xs, g, sparse=False)
+    s = orc.dense_adjoint(model, p, H, xs, g, sparse=True)
+    for a, b in zip(d, s):
+        assert np.allclose(a, b, rtol=1e-9, atol=1e-12 * np.abs(a).max())
