@@ -47,6 +47,7 @@ def parse_args(argv=None):
     ap.add_argument("--coloring", choices=["kuhn", "greedy"], default="kuhn")
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--pipeline", type=int, default=-1, help="1 TMA-staged sweep, 0 plain sweep, -1 library default")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -250,6 +251,8 @@ def workload_config(args, info) -> dict:
     if info is not None:
         cfg.update({"n_colors": info.n_colors, "n_free_verts": info.n_free, "n_slots": int(info.n_slots),
                     "lanes_per_vertex": info.lanes_per_vertex, "block_threads": info.block_threads,
+                    "tma_pipeline": bool(info.pipeline), "stage_slots": info.pipe_stage_slots,
+                    "ctas_per_sm": info.pipe_ctas_per_sm,
                     "cuda_graph": bool(info.use_graph), "parallelism": "replicas"})
     return cfg
 
@@ -379,8 +382,8 @@ def run_ours(args):
                              init_mode=cfg.init_mode, det_eps=cfg.det_eps)
     stream = torch.cuda.Stream()
     sim = vbd.Sim(m, params, colors=colors, stream=stream)
-    if args.lanes or args.block:
-        vbd.vbd_set_launch(sim.ctx, args.lanes, args.block)
+    if args.lanes or args.block or args.pipeline >= 0:
+        vbd.vbd_set_launch(sim.ctx, args.lanes, args.block, args.pipeline)
     vbd.vbd_set_graph(sim.ctx, not args.no_graph)
     info = vbd.vbd_get_info(sim.ctx)
     iters, h, K = args.iters, cfg.h, args.steps
@@ -460,7 +463,7 @@ def run_ours(args):
         "dtype": "f32", "data": "synthetic", "config": workload_config(args, info),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                     "kernel": "k_sweep (one colour pass)", "alg_bytes_per_update": b_upd,
+                     "kernel": ("k_sweep_pipe" if info.pipeline else "k_sweep") + " (one colour pass)", "alg_bytes_per_update": b_upd,
                      "avg_launch_us": avg_launch_s * 1e6,
                      "sweep_share_of_step": sweep_ms / t_ms},
         "e2e": e2e,

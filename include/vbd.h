@@ -48,7 +48,8 @@ typedef enum {
     VBD_ERR_CUDA = 6,          /* a CUDA runtime call failed */
     VBD_ERR_NONFINITE = 7,     /* a kernel met a non-finite position or solve */
     VBD_ERR_NO_TAPE = 8,       /* vbd_backward without recorded steps */
-    VBD_ERR_STATE = 9          /* call out of order (e.g. vbd_iterate before vbd_begin_step) */
+    VBD_ERR_STATE = 9,         /* call out of order (e.g. vbd_iterate before vbd_begin_step) */
+    VBD_ERR_TIMEOUT = 10       /* a bounded wait inside a kernel gave up; results are invalid */
 } vbd_status;
 
 typedef struct vbd_ctx vbd_ctx;
@@ -96,6 +97,9 @@ typedef struct {
     int32_t n_colors;        /* 0 before vbd_color */
     int64_t n_slots;         /* (free vertex, incident tet) pairs streamed per iteration */
     int32_t lanes_per_vertex, block_threads;   /* current sweep launch shape */
+    int32_t pipeline;        /* 1: slot records staged in shared memory by TMA bulk copies */
+    int32_t pipe_stage_slots; /* slot capacity of one pipeline stage */
+    int32_t pipe_ctas_per_sm; /* resident CTAs per SM of the pipelined sweep */
     int32_t use_graph;       /* vbd_iterate replays a CUDA graph */
 } vbd_info;
 
@@ -197,9 +201,11 @@ vbd_status vbd_energy(vbd_ctx *ctx, double *G_out);
  * plus tets), or when G_out is not device memory. */
 vbd_status vbd_energy_static(vbd_ctx *ctx, double *G_out);
 
-/* Waits for the stream and reads the device counters: VBD_ERR_NONFINITE if
- * any solve produced a non-finite update since the last call (that update
- * was not applied).  det_skips / contacts may be NULL.  Synchronising. */
+/* Waits for the stream and reads the device counters: VBD_ERR_TIMEOUT if a
+ * bounded wait inside the pipelined sweep gave up (the step's results are
+ * then invalid), else VBD_ERR_NONFINITE if any solve produced a non-finite
+ * update since the last call (that update was not applied).  det_skips /
+ * contacts may be NULL.  Synchronising. */
 vbd_status vbd_sync_status(vbd_ctx *ctx, int64_t *det_skips, int64_t *contacts);
 
 /* Adjoint of the recorded steps (tape_steps > 0; no paper counterpart, the
@@ -214,9 +220,15 @@ vbd_status vbd_sync_status(vbd_ctx *ctx, int64_t *det_skips, int64_t *contacts);
 vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, float *dL_dv0,
                         int32_t adj_iters);
 
-/* Sweep launch shape: lanes_per_vertex in {4, 8, 16, 32} threads cooperate
- * on one vertex; block_threads in {64, 128, 256, 512}.  0 keeps a value. */
-vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_threads);
+/* Sweep launch shape.  pipeline = 1: persistent CTAs of
+ * block_threads in {128, 256} stage each chunk of block_threads/8 vertices'
+ * slot records in shared memory with TMA bulk copies, two chunks ahead, 8
+ * lanes per vertex (lanes_per_vertex is ignored).  pipeline = 0: one thread
+ * group of lanes_per_vertex in {4, 8, 16, 32} per vertex loading its slots
+ * from global memory, block_threads in {64, 128, 256} (default: pipeline 0,
+ * 8 lanes, 128 threads, the fastest measured on B300).  0 keeps a value
+ * (pipeline < 0 keeps it too).  Must not be called during stream capture. */
+vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_threads, int32_t pipeline);
 
 /* Enables (1) or disables (0) CUDA-graph replay of vbd_iterate. */
 vbd_status vbd_set_graph(vbd_ctx *ctx, int32_t enable);

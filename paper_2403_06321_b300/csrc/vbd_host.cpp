@@ -76,7 +76,12 @@ struct vbd_ctx {
     int tape_len = 0;
     std::vector<float> tape_h;
     // launch shape / graphs
-    int lanes = 8, block = 256;
+    int lanes = 8, block = 128;
+    bool pipeline = false;
+    int pipe_block = 128;
+    int pipe_maxs = 0;          // slot capacity of one stage
+    int pipe_ctas_per_sm = 0;
+    int pipe_grid_cap = 0;
     bool use_graph = true;
     uint64_t version = 1;
     std::vector<GraphEntry> graphs;
@@ -231,7 +236,7 @@ size_t carve(const vbd_ctx *c, char *base, Dev *d) {
     t.s0 = (int4 *)take(16 * S);
     t.s1 = (float4 *)take(16 * S);
     t.s2 = (float4 *)take(16 * S);
-    t.s3 = (float2 *)take(8 * S);
+    t.s3 = (float2 *)take(8 * (S + 2));  // the pipelined sweep copies s3 from/to even slots
     t.slot_tet = (int *)take(4 * S);
     t.slot_loc = (int *)take(4 * S);
     t.tet_v = (int4 *)take(16 * T);
@@ -306,12 +311,46 @@ double cheby_omega(int n, double rho) {
     return w;
 }
 
+// Largest slot count of a chunk of `cv` consecutive vertices of one colour.
+int max_chunk_slots(const vbd_ctx *c, int cv) {
+    int mx = 0;
+    for (int col = 0; col < c->n_colors; ++col)
+        for (int v0 = c->color_begin[col]; v0 < c->color_begin[col + 1]; v0 += cv) {
+            const int v1 = std::min(c->color_begin[col + 1], v0 + cv);
+            mx = std::max(mx, c->slot_off[v1] - c->slot_off[v0]);
+        }
+    return mx;
+}
+
+// Sizes the pipeline stages for the current block and mesh: the largest
+// chunk, capped at 100 KiB of shared memory per CTA (larger chunks are read
+// from global memory by the same kernel).
+vbd_status prepare_pipeline(vbd_ctx *ctx) {
+    const int cv = vbd::sweep_pipe_chunk(ctx->pipe_block);
+    int maxs = std::max(16, max_chunk_slots(ctx, cv));
+    while (maxs > 16 && vbd::sweep_pipe_smem(maxs) > 100 * 1024) maxs = maxs * 7 / 8;
+    int occ = 0;
+    cudaError_t e = vbd::sweep_pipe_prepare(ctx->pipe_block, maxs, &occ);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pipelined sweep set-up");
+    ctx->pipe_maxs = maxs;
+    ctx->pipe_ctas_per_sm = occ;
+    ctx->pipe_grid_cap = vbd::num_sms() * occ;
+    return VBD_OK;
+}
+
+void launch_colour(vbd_ctx *c, int col, cudaStream_t s) {
+    if (c->pipeline)
+        vbd::launch_sweep_pipe(c->d, sweep_params(c, col), c->pipe_block, c->pipe_maxs, c->pipe_grid_cap, s);
+    else
+        vbd::launch_sweep(c->d, sweep_params(c, col), c->lanes, c->block, s);
+}
+
 // enqueue iterations n = first_n+1 .. first_n+iters on stream s
 void enqueue_iterations(vbd_ctx *c, int first_n, int iters, cudaStream_t s) {
     const bool cheby = c->params.cheby_rho > 0.f;
     for (int n = first_n + 1; n <= first_n + iters; ++n) {
         for (int col = 0; col < c->n_colors; ++col)
-            vbd::launch_sweep(c->d, sweep_params(c, col), c->lanes, c->block, s);
+            launch_colour(c, col, s);
         if (cheby)
             vbd::launch_cheby(c->d, c->n_free, n, (float)cheby_omega(n, c->params.cheby_rho), s);
     }
@@ -524,8 +563,11 @@ vbd_status vbd_get_info(const vbd_ctx *ctx, vbd_info *out) {
     out->n_free = ctx->colored ? ctx->n_free : 0;
     out->n_colors = ctx->colored ? ctx->n_colors : 0;
     out->n_slots = ctx->colored ? ctx->n_slots : 0;
-    out->lanes_per_vertex = ctx->lanes;
-    out->block_threads = ctx->block;
+    out->lanes_per_vertex = ctx->pipeline ? 8 : ctx->lanes;
+    out->block_threads = ctx->pipeline ? ctx->pipe_block : ctx->block;
+    out->pipeline = ctx->pipeline ? 1 : 0;
+    out->pipe_stage_slots = ctx->pipe_maxs;
+    out->pipe_ctas_per_sm = ctx->pipe_ctas_per_sm;
     out->use_graph = ctx->use_graph ? 1 : 0;
     return VBD_OK;
 }
@@ -601,6 +643,10 @@ vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *st
     CU(cudaMemsetAsync(d.ut, 0, 16 * (size_t)N, s), "clear u^t");
     CU(cudaStreamSynchronize(s), "bind upload");  // host staging vectors die here
     CU(cudaGetLastError(), "bind kernels");
+    {
+        vbd_status ps = prepare_pipeline(ctx);
+        if (ps != VBD_OK) return ps;
+    }
     ctx->bound = true;
     ctx->in_step = false;
     ctx->tape_len = 0;
@@ -710,7 +756,7 @@ vbd_status vbd_sweep_color(vbd_ctx *ctx, int32_t color) {
     if (st != VBD_OK) return st;
     if (!ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_sweep_color outside a step");
     if (color < 0 || color >= ctx->n_colors) return fail(ctx, VBD_ERR_INVALID_ARG, "colour out of range");
-    vbd::launch_sweep(ctx->d, sweep_params(ctx, color), ctx->lanes, ctx->block, ctx->stream);
+    launch_colour(ctx, color, ctx->stream);
     CU(cudaGetLastError(), "sweep");
     return VBD_OK;
 }
@@ -831,6 +877,7 @@ vbd_status vbd_sync_status(vbd_ctx *ctx, int64_t *det_skips, int64_t *contacts) 
     CU(cudaStreamSynchronize(ctx->stream), "sync");
     if (det_skips) *det_skips = (int64_t)c[1];
     if (contacts) *contacts = 0;
+    if (c[2] > 0) return fail(ctx, VBD_ERR_TIMEOUT, std::to_string(c[2]) + " pipelined-sweep waits timed out");
     if (c[0] > 0) return fail(ctx, VBD_ERR_NONFINITE, std::to_string(c[0]) + " non-finite updates");
     return VBD_OK;
 }
@@ -867,17 +914,30 @@ vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, floa
     return VBD_OK;
 }
 
-vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_threads) {
+vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_threads, int32_t pipeline) {
     if (!ctx) return VBD_ERR_INVALID_ARG;
+    const bool pipe = pipeline < 0 ? ctx->pipeline : pipeline != 0;
     if (lanes_per_vertex != 0 && lanes_per_vertex != 4 && lanes_per_vertex != 8 && lanes_per_vertex != 16 &&
         lanes_per_vertex != 32)
         return fail(ctx, VBD_ERR_INVALID_ARG, "lanes_per_vertex must be 4, 8, 16 or 32");
-    if (block_threads != 0 && block_threads != 64 && block_threads != 128 && block_threads != 256 &&
-        block_threads != 512)
-        return fail(ctx, VBD_ERR_INVALID_ARG, "block_threads must be 64, 128, 256 or 512");
-    if (block_threads == 512) return fail(ctx, VBD_ERR_INVALID_ARG, "block_threads 512 exceeds the kernel bound");
+    if (pipe) {
+        if (block_threads != 0 && block_threads != 128 && block_threads != 256)
+            return fail(ctx, VBD_ERR_INVALID_ARG, "the pipelined sweep takes block_threads 128 or 256");
+    } else if (block_threads != 0 && block_threads != 64 && block_threads != 128 && block_threads != 256) {
+        return fail(ctx, VBD_ERR_INVALID_ARG, "block_threads must be 64, 128 or 256");
+    }
+    ctx->pipeline = pipe;
     if (lanes_per_vertex) ctx->lanes = lanes_per_vertex;
-    if (block_threads) ctx->block = block_threads;
+    if (block_threads) {
+        if (pipe)
+            ctx->pipe_block = block_threads;
+        else
+            ctx->block = block_threads;
+    }
+    if (pipe && ctx->bound) {
+        vbd_status ps = prepare_pipeline(ctx);
+        if (ps != VBD_OK) return ps;
+    }
     ctx->version++;
     clear_graphs(ctx);
     return VBD_OK;
@@ -894,37 +954,32 @@ vbd_status vbd_autotune(vbd_ctx *ctx, float h, int32_t iters, float *best_ms_per
     if (st != VBD_OK) return st;
     if (ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_autotune inside a step");
     if (iters < 1) return fail(ctx, VBD_ERR_INVALID_ARG, "iters must be >= 1");
-    const int lanes_opts[] = {4, 8, 16, 32};
-    const int block_opts[] = {128, 256};
+    struct Shape { int pipe, lanes, block; };
+    const Shape shapes[] = {{1, 8, 128}, {1, 8, 256}, {0, 4, 128}, {0, 8, 128}, {0, 8, 256}, {0, 16, 256}};
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0), "event");
     CU(cudaEventCreate(&e1), "event");
     const bool graph_saved = ctx->use_graph;
     ctx->use_graph = false;
     float best = 1e30f;
-    int best_l = ctx->lanes, best_b = ctx->block;
-    for (int l : lanes_opts)
-        for (int b : block_opts) {
-            ctx->lanes = l;
-            ctx->block = b;
-            float ms = 0.f;
-            for (int rep = 0; rep < 2; ++rep) {  // first repetition warms up
-                vbd_begin_step(ctx, h);
-                cudaEventRecord(e0, ctx->stream);
-                vbd_iterate(ctx, iters);
-                cudaEventRecord(e1, ctx->stream);
-                ctx->in_step = false;
-                vbd::launch_restore_x(ctx->d, ctx->N, ctx->stream);
-                cudaEventSynchronize(e1);
-                cudaEventElapsedTime(&ms, e0, e1);
-            }
-            if (ms < best) { best = ms; best_l = l; best_b = b; }
+    Shape bs = {ctx->pipeline ? 1 : 0, ctx->lanes, ctx->pipeline ? ctx->pipe_block : ctx->block};
+    for (const Shape &sh : shapes) {
+        if (vbd_set_launch(ctx, sh.lanes, sh.block, sh.pipe) != VBD_OK) continue;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {  // first repetition warms up
+            vbd_begin_step(ctx, h);
+            cudaEventRecord(e0, ctx->stream);
+            vbd_iterate(ctx, iters);
+            cudaEventRecord(e1, ctx->stream);
+            ctx->in_step = false;
+            vbd::launch_restore_x(ctx->d, ctx->N, ctx->stream);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms, e0, e1);
         }
+        if (ms < best) { best = ms; bs = sh; }
+    }
     ctx->use_graph = graph_saved;
-    ctx->lanes = best_l;
-    ctx->block = best_b;
-    ctx->version++;
-    clear_graphs(ctx);
+    vbd_set_launch(ctx, bs.lanes, bs.block, bs.pipe);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     CU(cudaStreamSynchronize(ctx->stream), "autotune");

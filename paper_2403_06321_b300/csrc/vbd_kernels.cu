@@ -193,6 +193,185 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, SweepParams p) {
     if (active && lane == 0) solve_and_store(d, p, vi, xi, acc);
 }
 
+// ---- pipelined sweep: slot records staged in shared memory by TMA ----------
+// Persistent CTAs of TT threads walk the colour range in chunks of TT / 8
+// consecutive vertices (8 lanes per vertex as in k_sweep).  A chunk's slot
+// records are contiguous, so one thread copies them global -> shared with
+// four bulk copies (cp.async.bulk, completion counted in bytes on an
+// mbarrier), two chunks ahead of the consumers.  The stream is then in flight
+// without occupying registers, which is what limits k_sweep.  Every wait is
+// bounded: on time-out the CTA records an error (counters[2]), waits (again
+// bounded) for its own copies and returns; the host reports it.
+constexpr int kPipeLanes = 8;
+constexpr int kPipeStages = 2;
+constexpr long long kWaitSpins = 1ll << 22;        // try_wait calls before giving up
+constexpr long long kWaitCycles = 4000000000ll;   // ~2 s of SM clock
+
+struct StageMeta {
+    int a;       // first slot of the chunk
+    int n;       // slot count
+    int a3;      // first slot of the s3 copy (even)
+    int direct;  // 1: consumers read global memory (chunk larger than a stage, or empty)
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+    const unsigned a = smem_addr(bar);
+    const long long t0 = clock64();
+    for (long long i = 0; i < kWaitSpins; ++i) {
+        unsigned ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+// shared-memory image of one stage (maxs slots)
+struct StageView {
+    int4 *s0;
+    float4 *s1, *s2;
+    float2 *s3;
+};
+
+__device__ __forceinline__ StageView stage_view(char *base, int maxs) {
+    StageView v;
+    v.s0 = (int4 *)base;
+    v.s1 = (float4 *)(base + 16 * (size_t)maxs);
+    v.s2 = (float4 *)(base + 32 * (size_t)maxs);
+    v.s3 = (float2 *)(base + 48 * (size_t)maxs);
+    return v;
+}
+
+// Bytes of one stage: three 16-byte arrays and one 8-byte array with two
+// spare entries (the s3 copy starts on an even slot), rounded to 128.
+__host__ __device__ inline size_t pipe_stage_bytes(int maxs) {
+    return ((size_t)48 * maxs + 8 * ((size_t)maxs + 2) + 127) & ~(size_t)127;
+}
+__host__ __device__ inline size_t pipe_smem_bytes(int maxs) {
+    return 128 + kPipeStages * pipe_stage_bytes(maxs);
+}
+
+// issued by one thread: chunk q of the colour range into stage st
+__device__ __forceinline__ void pipe_issue(const Dev &d, const SweepParams &p, int q, int cv, int maxs,
+                                           char *stages, StageMeta *meta, unsigned long long *bar, int st) {
+    const int v0 = p.vbegin + q * cv;
+    const int v1 = min(p.vend, v0 + cv);
+    const int a = d.slot_off[v0], b = d.slot_off[v1];
+    const int n = b - a;
+    StageMeta m;
+    m.a = a;
+    m.n = n;
+    m.a3 = a & ~1;
+    m.direct = (n <= 0 || n > maxs) ? 1 : 0;
+    meta[st] = m;
+    const unsigned ab = smem_addr(bar + st);
+    if (m.direct) {
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(ab) : "memory");
+        return;
+    }
+    const int b3 = (b + 1) & ~1;
+    const unsigned tx = 48u * (unsigned)n + 8u * (unsigned)(b3 - m.a3);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(ab), "r"(tx) : "memory");
+    StageView v = stage_view(stages + st * pipe_stage_bytes(maxs), maxs);
+    bulk_g2s(v.s0, d.s0 + a, 16u * n, bar + st);
+    bulk_g2s(v.s1, d.s1 + a, 16u * n, bar + st);
+    bulk_g2s(v.s2, d.s2 + a, 16u * n, bar + st);
+    bulk_g2s(v.s3, d.s3 + m.a3, 8u * (unsigned)(b3 - m.a3), bar + st);
+}
+
+template <int TT>
+__global__ void __launch_bounds__(TT) k_sweep_pipe(Dev d, SweepParams p, int maxs) {
+    constexpr int L = kPipeLanes;
+    constexpr int CV = TT / L;  // vertices per chunk
+    extern __shared__ __align__(128) char smem[];
+    unsigned long long *bar = (unsigned long long *)smem;     // kPipeStages barriers
+    StageMeta *meta = (StageMeta *)(smem + 64);               // kPipeStages records
+    char *stages = smem + 128;
+    const int n = p.vend - p.vbegin;
+    const int nchunks = (n + CV - 1) / CV;
+    const int first = blockIdx.x, stride = gridDim.x;
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < kPipeStages; ++st)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(bar + st)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int st = 0; st < kPipeStages; ++st)
+            if (first + st * stride < nchunks)
+                pipe_issue(d, p, first + st * stride, CV, maxs, stages, meta, bar, st);
+    const int lane = threadIdx.x & (L - 1);
+    for (int k = 0;; ++k) {
+        const int q = first + k * stride;
+        if (q >= nchunks) break;
+        const int st = k % kPipeStages;
+        const bool ok = mbar_wait(bar + st, (unsigned)((k / kPipeStages) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicAdd(d.counters + 2, 1ull);
+                // drain this CTA's outstanding copies before leaving (bounded):
+                // chunks k .. k+kPipeStages-2 are issued (k .. kPipeStages-1 when k == 0)
+                const int last = (k == 0) ? kPipeStages - 1 : k + kPipeStages - 2;
+                for (int kk = k; kk <= last; ++kk)
+                    if (first + kk * stride < nchunks)
+                        mbar_wait(bar + kk % kPipeStages, (unsigned)((kk / kPipeStages) & 1));
+            }
+            return;
+        }
+        // all threads are past chunk k-1: its stage takes chunk k-1+kPipeStages
+        if (k >= 1 && threadIdx.x == 0) {
+            const int kk = k - 1 + kPipeStages;
+            if (first + kk * stride < nchunks)
+                pipe_issue(d, p, first + kk * stride, CV, maxs, stages, meta, bar, kk % kPipeStages);
+        }
+        const StageMeta m = meta[st];
+        const StageView v = stage_view(stages + st * pipe_stage_bytes(maxs), maxs);
+        const int vi = p.vbegin + q * CV + (int)(threadIdx.x / L);
+        const bool active = vi < p.vend;
+        float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
+        int s0 = 0, s1 = 0;
+        if (active) {
+            xi = d.u[vi];
+            s0 = d.slot_off[vi] - m.a;
+            s1 = d.slot_off[vi + 1] - m.a;
+        }
+        const float3 x3 = f3(xi);
+        Acc acc = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (!m.direct) {
+            const int o3 = m.a - m.a3;
+            for (int s = s0 + lane; s < s1; s += L)
+                accumulate_slot(d.u, v.s0[s], v.s1[s], v.s2[s], v.s3[s + o3], x3, acc);
+        } else {
+            for (int s = s0 + lane + m.a; s < s1 + m.a; s += L)
+                accumulate_slot(d.u, __ldcs(d.s0 + s), __ldcs(d.s1 + s), __ldcs(d.s2 + s), __ldcs(d.s3 + s), x3, acc);
+        }
+        acc.f0 = sub_reduce<L>(acc.f0);
+        acc.f1 = sub_reduce<L>(acc.f1);
+        acc.f2 = sub_reduce<L>(acc.f2);
+        acc.h00 = sub_reduce<L>(acc.h00);
+        acc.h01 = sub_reduce<L>(acc.h01);
+        acc.h02 = sub_reduce<L>(acc.h02);
+        acc.h11 = sub_reduce<L>(acc.h11);
+        acc.h12 = sub_reduce<L>(acc.h12);
+        acc.h22 = sub_reduce<L>(acc.h22);
+        if (active && lane == 0) solve_and_store(d, p, vi, xi, acc);
+    }
+}
+
 // Eq. 3 and Sec. 3.7 options (a)-(d), Eq. 17.  Pinned vertices (ids >= n_free) keep x^t.
 __global__ void k_predict(Dev d, int n, int n_free, float h, float3 g, float gnorm, int mode,
                           int cheby) {
@@ -405,6 +584,41 @@ void launch_sweep(const Dev &d, const SweepParams &p, int lanes, int block, cuda
     case 16: k_sweep<16><<<grid, block, 0, s>>>(d, p); break;
     default: k_sweep<32><<<grid, block, 0, s>>>(d, p); break;
     }
+}
+
+size_t sweep_pipe_smem(int maxs) { return pipe_smem_bytes(maxs); }
+
+int sweep_pipe_chunk(int block) { return block / kPipeLanes; }
+
+cudaError_t sweep_pipe_prepare(int block, int maxs, int *ctas_per_sm) {
+    const size_t smem = pipe_smem_bytes(maxs);
+    cudaError_t e;
+    int occ = 0;
+    if (block == 256) {
+        e = cudaFuncSetAttribute(k_sweep_pipe<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_pipe<256>, 256, smem);
+    } else {
+        e = cudaFuncSetAttribute(k_sweep_pipe<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_pipe<128>, 128, smem);
+    }
+    if (e != cudaSuccess) return e;
+    *ctas_per_sm = occ;
+    return occ > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
+void launch_sweep_pipe(const Dev &d, const SweepParams &p, int block, int maxs, int grid_cap, cudaStream_t s) {
+    const int n = p.vend - p.vbegin;
+    if (n <= 0) return;
+    const int cv = block / kPipeLanes;
+    const int nchunks = (n + cv - 1) / cv;
+    const unsigned grid = (unsigned)std::max(1, std::min(nchunks, grid_cap));
+    const size_t smem = pipe_smem_bytes(maxs);
+    if (block == 256)
+        k_sweep_pipe<256><<<grid, 256, smem, s>>>(d, p, maxs);
+    else
+        k_sweep_pipe<128><<<grid, 128, smem, s>>>(d, p, maxs);
 }
 
 void launch_cheby(const Dev &d, int n_free, int n, float omega, cudaStream_t s) {

@@ -35,7 +35,7 @@ struct Dev {
     float *tet_V, *tet_nu, *tet_mu, *tet_lam;
     int *new_of_orig; // N
     float *stage[3];  // 3N each, state exchange with caller order
-    unsigned long long *counters;  // [0] non-finite updates, [1] det skips
+    unsigned long long *counters;  // [0] non-finite updates, [1] det skips, [2] pipeline wait time-outs
     double *partials; // energy partial sums
     double *energy_out;
     float4 *tape;     // tape_steps * N displacements
@@ -59,6 +59,12 @@ int num_sms();
 void launch_predict(const Dev &d, int n, int n_free, float h, float3 g, int init_mode,
                     bool cheby, cudaStream_t s);
 void launch_sweep(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s);
+// pipelined sweep (TMA bulk copies of each chunk's slots into shared memory);
+// maxs = slot capacity of one stage, chunks of block/8 vertices
+size_t sweep_pipe_smem(int maxs);
+int sweep_pipe_chunk(int block);
+cudaError_t sweep_pipe_prepare(int block, int maxs, int *ctas_per_sm);
+void launch_sweep_pipe(const Dev &d, const SweepParams &p, int block, int maxs, int grid_cap, cudaStream_t s);
 void launch_cheby(const Dev &d, int n_free, int n, float omega, cudaStream_t s);
 void launch_finish(const Dev &d, int n, float h, float4 *tape_row, cudaStream_t s);
 // caller order <-> internal order; with `rest` non-null the caller array holds

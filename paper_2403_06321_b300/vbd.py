@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libvbd.so")
 
 STATUS = {0: "VBD_OK", 1: "VBD_ERR_INVALID_ARG", 2: "VBD_ERR_BAD_MESH", 3: "VBD_ERR_BAD_COLORING",
           4: "VBD_ERR_NOT_COLORED", 5: "VBD_ERR_WORKSPACE", 6: "VBD_ERR_CUDA", 7: "VBD_ERR_NONFINITE",
-          8: "VBD_ERR_NO_TAPE", 9: "VBD_ERR_STATE"}
+          8: "VBD_ERR_NO_TAPE", 9: "VBD_ERR_STATE", 10: "VBD_ERR_TIMEOUT"}
 STATUS_CODE = {v: k for k, v in STATUS.items()}
 
 # every entry point declared in include/vbd.h
@@ -59,7 +59,8 @@ class vbd_params(C.Structure):
 class vbd_info(C.Structure):
     _fields_ = [("n_verts", C.c_int32), ("n_tets", C.c_int32), ("n_meshes", C.c_int32),
                 ("n_free", C.c_int32), ("n_colors", C.c_int32), ("n_slots", C.c_int64),
-                ("lanes_per_vertex", C.c_int32), ("block_threads", C.c_int32), ("use_graph", C.c_int32)]
+                ("lanes_per_vertex", C.c_int32), ("block_threads", C.c_int32), ("pipeline", C.c_int32),
+                ("pipe_stage_slots", C.c_int32), ("pipe_ctas_per_sm", C.c_int32), ("use_graph", C.c_int32)]
 
 
 _lib = None
@@ -97,7 +98,7 @@ def load() -> C.CDLL:
         "vbd_energy_static": (C.c_int, [P, P]),
         "vbd_sync_status": (C.c_int, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "vbd_backward": (C.c_int, [P, P, P, P, I32]),
-        "vbd_set_launch": (C.c_int, [P, I32, I32]),
+        "vbd_set_launch": (C.c_int, [P, I32, I32, I32]),
         "vbd_set_graph": (C.c_int, [P, I32]),
         "vbd_autotune": (C.c_int, [P, F, I32, C.POINTER(F)]),
         "vbd_last_error": (C.c_char_p, [P]),
@@ -236,8 +237,8 @@ def vbd_backward(ctx: int, dL_dxT, dL_dlogE, dL_dv0, adj_iters: int) -> None:
     _check("vbd_backward", ctx, load().vbd_backward(ctx, _ptr(dL_dxT), _ptr(dL_dlogE), _ptr(dL_dv0), adj_iters))
 
 
-def vbd_set_launch(ctx: int, lanes_per_vertex: int = 0, block_threads: int = 0) -> None:
-    _check("vbd_set_launch", ctx, load().vbd_set_launch(ctx, lanes_per_vertex, block_threads))
+def vbd_set_launch(ctx: int, lanes_per_vertex: int = 0, block_threads: int = 0, pipeline: int = -1) -> None:
+    _check("vbd_set_launch", ctx, load().vbd_set_launch(ctx, lanes_per_vertex, block_threads, pipeline))
 
 
 def vbd_set_graph(ctx: int, enable: bool) -> None:

@@ -110,7 +110,7 @@ def test_info_workspace_and_call_order(lib):
             vbd.vbd_step(ctx, 1 / 60, 5)
         assert e.value.status == "VBD_ERR_WORKSPACE"
         with pytest.raises(vbd.VbdError) as e:
-            vbd.vbd_set_launch(ctx, 3, 0)
+            vbd.vbd_set_launch(ctx, 3, 0, 0)
         assert e.value.status == "VBD_ERR_INVALID_ARG"
     finally:
         vbd.vbd_destroy(ctx)

@@ -48,10 +48,16 @@ def test_one_iteration_from_perturbed_state_ragged(orc):
     x0[m.pinned == 1] = m.rest[m.pinned == 1]
     colors, _ = orc.color_greedy(m.n_verts, m.tets)
     pd = params_of(synth.SimConfig())
-    for lanes in (4, 8, 16, 32):
-        xg, vg = gpu_run(m, pd, colors, 1 / 60, 1, 1, x0, v0, lanes=lanes)
-        xo, vo = oracle_run(orc, m, pd, colors, 1 / 60, 1, 1, x0, v0)
-        assert _err(xg, xo, m.rest) <= 1e-6, lanes
+    xo, vo = oracle_run(orc, m, pd, colors, 1 / 60, 1, 1, x0, v0)
+    shapes = [dict(pipeline=1, block=128), dict(pipeline=1, block=256)] + \
+             [dict(pipeline=0, lanes=l) for l in (4, 8, 16, 32)]
+    results = []
+    for sh in shapes:
+        xg, vg = gpu_run(m, pd, colors, 1 / 60, 1, 1, x0, v0, **sh)
+        assert _err(xg, xo, m.rest) <= 1e-6, sh
+        results.append(xg)
+    # same lanes-per-vertex reduction order: pipelined and plain 8-lane sweeps agree bit for bit
+    assert np.array_equal(results[0], results[3]) and np.array_equal(results[1], results[3])
 
 
 def test_ground_contact_and_chebyshev(orc):
@@ -101,9 +107,10 @@ def test_graph_replay_equals_eager():
     m, cfg = synth.cantilever_beam()
     colors = synth.kuhn_coloring(m.grid_ijk)
     pd = params_of(cfg, cheby_rho=0.8)
-    xa, va = gpu_run(m, pd, colors, cfg.h, 7, 5, graph=True)
-    xb, vb = gpu_run(m, pd, colors, cfg.h, 7, 5, graph=False)
-    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    for pipe in (1, 0):
+        xa, va = gpu_run(m, pd, colors, cfg.h, 7, 5, graph=True, pipeline=pipe)
+        xb, vb = gpu_run(m, pd, colors, cfg.h, 7, 5, graph=False, pipeline=pipe)
+        assert np.array_equal(xa, xb) and np.array_equal(va, vb)
 
 
 def test_energy_fp64_matches_oracle(orc):
