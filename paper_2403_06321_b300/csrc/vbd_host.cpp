@@ -58,10 +58,7 @@ struct vbd_ctx {
     std::vector<int> color_begin;    // n_colors + 1, over the free range
     long long n_slots = 0;
     std::vector<int> slot_off;       // n_free + 1
-    std::vector<int4> s0;
-    std::vector<float4> s1, s2;
-    std::vector<float2> s3;
-    std::vector<int> slot_tet, slot_loc;
+    std::vector<int> inc_off, inc_tet, inc_loc;  // vertex -> incident tets (caller ids)
     // device
     bool bound = false;
     char *ws = nullptr;
@@ -356,6 +353,38 @@ void enqueue_iterations(vbd_ctx *c, int first_n, int iters, cudaStream_t s) {
     }
 }
 
+// Slot records of free vertices [k0, k1) (internal ids), in slot order.
+void build_slots(const vbd_ctx *c, int k0, int k1, int4 *s0, float4 *s1, float4 *s2, float2 *s3,
+                 int *stet, int *sloc) {
+    size_t w = 0;
+    for (int k = k0; k < k1; ++k) {
+        const int i = c->orig_of_new[k];
+        for (int q = c->inc_off[i]; q < c->inc_off[i + 1]; ++q, ++w) {
+            const int j = c->inc_tet[q], a = c->inc_loc[q];
+            const double *Bj = &c->B[9 * (size_t)j];
+            int ids[3];
+            double g[3][3];
+            int m = 0;
+            for (int b = 0; b < 4; ++b) {
+                if (b == a) continue;
+                ids[m] = c->new_of_orig[c->tets[4 * (size_t)j + b]];
+                shape_grad(Bj, b, g[m]);
+                ++m;
+            }
+            const float Vmu = (float)(c->V[j] * c->mu[j]);
+            const float Vlam = (float)(c->V[j] * c->lam[j]);
+            int vmu_bits;
+            std::memcpy(&vmu_bits, &Vmu, 4);
+            s0[w] = make_int4(ids[0], ids[1], ids[2], vmu_bits);
+            s1[w] = make_float4((float)g[0][0], (float)g[0][1], (float)g[0][2], (float)g[1][0]);
+            s2[w] = make_float4((float)g[1][1], (float)g[1][2], (float)g[2][0], (float)g[2][1]);
+            s3[w] = make_float2((float)g[2][2], Vlam);
+            stet[w] = j;
+            sloc[w] = a;
+        }
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -496,49 +525,14 @@ vbd_status vbd_color(vbd_ctx *ctx, const int32_t *colors, int32_t *n_colors_out)
     ctx->color_begin.assign(nc + 1, 0);
     for (int k = 0; k < ctx->n_free; ++k) ctx->color_begin[col[order[k]] + 1]++;
     for (int c = 0; c < nc; ++c) ctx->color_begin[c + 1] += ctx->color_begin[c];
-    // incidence slots of free vertices
-    std::vector<int> off, tet, loc;
-    incidence(N, T, ctx->tets, off, tet, loc);
+    // incidence slots of free vertices: offsets now, records at bind time
+    incidence(N, T, ctx->tets, ctx->inc_off, ctx->inc_tet, ctx->inc_loc);
     ctx->slot_off.assign(ctx->n_free + 1, 0);
     for (int k = 0; k < ctx->n_free; ++k) {
         const int i = order[k];
-        ctx->slot_off[k + 1] = ctx->slot_off[k] + (off[i + 1] - off[i]);
+        ctx->slot_off[k + 1] = ctx->slot_off[k] + (ctx->inc_off[i + 1] - ctx->inc_off[i]);
     }
-    const long long S = ctx->slot_off[ctx->n_free];
-    ctx->n_slots = S;
-    ctx->s0.resize(S);
-    ctx->s1.resize(S);
-    ctx->s2.resize(S);
-    ctx->s3.resize(S);
-    ctx->slot_tet.resize(S);
-    ctx->slot_loc.resize(S);
-    for (int k = 0; k < ctx->n_free; ++k) {
-        const int i = order[k];
-        long long s = ctx->slot_off[k];
-        for (int q = off[i]; q < off[i + 1]; ++q, ++s) {
-            const int j = tet[q], a = loc[q];
-            const double *Bj = &ctx->B[9 * (size_t)j];
-            int ids[3];
-            double g[3][3];
-            int m = 0;
-            for (int b = 0; b < 4; ++b) {
-                if (b == a) continue;
-                ids[m] = ctx->new_of_orig[ctx->tets[4 * j + b]];
-                shape_grad(Bj, b, g[m]);
-                ++m;
-            }
-            const float Vmu = (float)(ctx->V[j] * ctx->mu[j]);
-            const float Vlam = (float)(ctx->V[j] * ctx->lam[j]);
-            int vmu_bits;
-            std::memcpy(&vmu_bits, &Vmu, 4);
-            ctx->s0[s] = make_int4(ids[0], ids[1], ids[2], vmu_bits);
-            ctx->s1[s] = make_float4((float)g[0][0], (float)g[0][1], (float)g[0][2], (float)g[1][0]);
-            ctx->s2[s] = make_float4((float)g[1][1], (float)g[1][2], (float)g[2][0], (float)g[2][1]);
-            ctx->s3[s] = make_float2((float)g[2][2], Vlam);
-            ctx->slot_tet[s] = j;
-            ctx->slot_loc[s] = a;
-        }
-    }
+    ctx->n_slots = ctx->slot_off[ctx->n_free];
     ctx->colored = true;
     ctx->bound = false;
     ctx->in_step = false;
@@ -595,38 +589,63 @@ vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *st
     const int N = ctx->N, T = ctx->T;
     const long long S = ctx->n_slots;
     const Dev &d = ctx->d;
-    // static data
+    // static data; slot and tet records go up in chunks of at most kChunk
+    // entries so that host staging stays bounded at any mesh size
+    constexpr long long kChunk = 1 << 24;
     std::vector<float> massf(N);
     for (int k = 0; k < N; ++k) massf[k] = (float)ctx->mass[ctx->orig_of_new[k]];
-    std::vector<int4> tv(T);
-    std::vector<float> tB(9 * (size_t)T), tV(T), tnu(T), tmu(T), tlam(T);
-    for (int j = 0; j < T; ++j) {
-        const int *t = &ctx->tets[4 * j];
-        tv[j] = make_int4(ctx->new_of_orig[t[0]], ctx->new_of_orig[t[1]], ctx->new_of_orig[t[2]],
-                          ctx->new_of_orig[t[3]]);
-        for (int k = 0; k < 9; ++k) tB[9 * (size_t)j + k] = (float)ctx->B[9 * (size_t)j + k];
-        tV[j] = (float)ctx->V[j];
-        tnu[j] = ctx->poisson[j];
-        tmu[j] = (float)ctx->mu[j];
-        tlam[j] = (float)ctx->lam[j];
-    }
     CU(cudaMemcpyAsync(d.mass, massf.data(), 4 * (size_t)N, cudaMemcpyHostToDevice, s), "upload mass");
     CU(cudaMemcpyAsync(d.slot_off, ctx->slot_off.data(), 4 * ((size_t)ctx->n_free + 1), cudaMemcpyHostToDevice, s),
        "upload slot_off");
-    if (S > 0) {
-        CU(cudaMemcpyAsync(d.s0, ctx->s0.data(), 16 * (size_t)S, cudaMemcpyHostToDevice, s), "upload slots");
-        CU(cudaMemcpyAsync(d.s1, ctx->s1.data(), 16 * (size_t)S, cudaMemcpyHostToDevice, s), "upload slots");
-        CU(cudaMemcpyAsync(d.s2, ctx->s2.data(), 16 * (size_t)S, cudaMemcpyHostToDevice, s), "upload slots");
-        CU(cudaMemcpyAsync(d.s3, ctx->s3.data(), 8 * (size_t)S, cudaMemcpyHostToDevice, s), "upload slots");
-        CU(cudaMemcpyAsync(d.slot_tet, ctx->slot_tet.data(), 4 * (size_t)S, cudaMemcpyHostToDevice, s), "upload slots");
-        CU(cudaMemcpyAsync(d.slot_loc, ctx->slot_loc.data(), 4 * (size_t)S, cudaMemcpyHostToDevice, s), "upload slots");
+    {
+        std::vector<int4> h0;
+        std::vector<float4> h1, h2;
+        std::vector<float2> h3;
+        std::vector<int> ht, hl;
+        int k0 = 0;
+        while (k0 < ctx->n_free) {
+            int k1 = k0;
+            while (k1 < ctx->n_free && (long long)ctx->slot_off[k1 + 1] - ctx->slot_off[k0] <= kChunk) ++k1;
+            if (k1 == k0) k1 = k0 + 1;
+            const long long a0 = ctx->slot_off[k0], n = (long long)ctx->slot_off[k1] - a0;
+            h0.resize(n); h1.resize(n); h2.resize(n); h3.resize(n); ht.resize(n); hl.resize(n);
+            build_slots(ctx, k0, k1, h0.data(), h1.data(), h2.data(), h3.data(), ht.data(), hl.data());
+            CU(cudaMemcpyAsync(d.s0 + a0, h0.data(), 16 * (size_t)n, cudaMemcpyHostToDevice, s), "upload slots");
+            CU(cudaMemcpyAsync(d.s1 + a0, h1.data(), 16 * (size_t)n, cudaMemcpyHostToDevice, s), "upload slots");
+            CU(cudaMemcpyAsync(d.s2 + a0, h2.data(), 16 * (size_t)n, cudaMemcpyHostToDevice, s), "upload slots");
+            CU(cudaMemcpyAsync(d.s3 + a0, h3.data(), 8 * (size_t)n, cudaMemcpyHostToDevice, s), "upload slots");
+            CU(cudaMemcpyAsync(d.slot_tet + a0, ht.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s), "upload slots");
+            CU(cudaMemcpyAsync(d.slot_loc + a0, hl.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s), "upload slots");
+            CU(cudaStreamSynchronize(s), "upload slots");  // the staging vectors are reused
+            k0 = k1;
+        }
     }
-    CU(cudaMemcpyAsync(d.tet_v, tv.data(), 16 * (size_t)T, cudaMemcpyHostToDevice, s), "upload tets");
-    CU(cudaMemcpyAsync(d.tet_B, tB.data(), 36 * (size_t)T, cudaMemcpyHostToDevice, s), "upload tets");
-    CU(cudaMemcpyAsync(d.tet_V, tV.data(), 4 * (size_t)T, cudaMemcpyHostToDevice, s), "upload tets");
-    CU(cudaMemcpyAsync(d.tet_nu, tnu.data(), 4 * (size_t)T, cudaMemcpyHostToDevice, s), "upload tets");
-    CU(cudaMemcpyAsync(d.tet_mu, tmu.data(), 4 * (size_t)T, cudaMemcpyHostToDevice, s), "upload tets");
-    CU(cudaMemcpyAsync(d.tet_lam, tlam.data(), 4 * (size_t)T, cudaMemcpyHostToDevice, s), "upload tets");
+    {
+        std::vector<int4> tv;
+        std::vector<float> tB, tV, tnu, tmu, tlam;
+        for (long long j0 = 0; j0 < T; j0 += kChunk) {
+            const long long n = std::min<long long>(kChunk, T - j0);
+            tv.resize(n); tB.resize(9 * n); tV.resize(n); tnu.resize(n); tmu.resize(n); tlam.resize(n);
+            for (long long q = 0; q < n; ++q) {
+                const size_t j = (size_t)(j0 + q);
+                const int *t = &ctx->tets[4 * j];
+                tv[q] = make_int4(ctx->new_of_orig[t[0]], ctx->new_of_orig[t[1]], ctx->new_of_orig[t[2]],
+                                  ctx->new_of_orig[t[3]]);
+                for (int k = 0; k < 9; ++k) tB[9 * q + k] = (float)ctx->B[9 * j + k];
+                tV[q] = (float)ctx->V[j];
+                tnu[q] = ctx->poisson[j];
+                tmu[q] = (float)ctx->mu[j];
+                tlam[q] = (float)ctx->lam[j];
+            }
+            CU(cudaMemcpyAsync(d.tet_v + j0, tv.data(), 16 * (size_t)n, cudaMemcpyHostToDevice, s), "upload tets");
+            CU(cudaMemcpyAsync(d.tet_B + 9 * j0, tB.data(), 36 * (size_t)n, cudaMemcpyHostToDevice, s), "upload tets");
+            CU(cudaMemcpyAsync(d.tet_V + j0, tV.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s), "upload tets");
+            CU(cudaMemcpyAsync(d.tet_nu + j0, tnu.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s), "upload tets");
+            CU(cudaMemcpyAsync(d.tet_mu + j0, tmu.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s), "upload tets");
+            CU(cudaMemcpyAsync(d.tet_lam + j0, tlam.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s), "upload tets");
+            CU(cudaStreamSynchronize(s), "upload tets");
+        }
+    }
     CU(cudaMemcpyAsync(d.new_of_orig, ctx->new_of_orig.data(), 4 * (size_t)N, cudaMemcpyHostToDevice, s),
        "upload permutation");
     CU(cudaMemsetAsync(d.counters, 0, 64, s), "clear counters");

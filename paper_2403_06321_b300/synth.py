@@ -69,30 +69,30 @@ def kuhn_grid(nx: int, ny: int, nz: int, edge: float,
     faces conformingly.
     """
     nxv, nyv, nzv = nx + 1, ny + 1, nz + 1
-    k, j, i = np.meshgrid(np.arange(nzv), np.arange(nyv), np.arange(nxv), indexing="ij")
-    ijk = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1).astype(np.int32)
-    rest = origin + edge * ijk.astype(np.float64)
+    k, j, i = np.meshgrid(np.arange(nzv, dtype=np.int32), np.arange(nyv, dtype=np.int32),
+                          np.arange(nxv, dtype=np.int32), indexing="ij")
+    ijk = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1)
+    del i, j, k
+    rest = np.asarray(origin, dtype=np.float64) + edge * ijk.astype(np.float64)
 
-    ci, cj, ck = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
-    ci, cj, ck = ci.ravel(order="F"), cj.ravel(order="F"), ck.ravel(order="F")
+    # id of each cube's (0,0,0) corner, cubes in x-fastest order
+    ck, cj, ci = np.meshgrid(np.arange(nz, dtype=np.int64), np.arange(ny, dtype=np.int64),
+                             np.arange(nx, dtype=np.int64), indexing="ij")
+    base = (ci + nxv * (cj + nyv * ck)).ravel()
+    del ci, cj, ck
 
-    def vid(a, b, c):
-        return a + nxv * (b + nyv * c)
+    def off(e):
+        return int(e[0] + nxv * (e[1] + nyv * e[2]))
 
     unit = np.eye(3, dtype=np.int64)
-    tets = []
+    table = []
     for perm in itertools.permutations(range(3)):
         e0 = unit[perm[0]]
         e01 = unit[perm[0]] + unit[perm[1]]
-        t = np.stack([
-            vid(ci, cj, ck),
-            vid(ci + e0[0], cj + e0[1], ck + e0[2]),
-            vid(ci + e01[0], cj + e01[1], ck + e01[2]),
-            vid(ci + 1, cj + 1, ck + 1),
-        ], axis=1)
-        tets.append(t)
+        table.append([0, off(e0), off(e01), off((1, 1, 1))])
+    table = np.asarray(table, dtype=np.int64)  # (6, 4)
     # cube-major order: the 6 tets of one cube are adjacent
-    tets = np.stack(tets, axis=1).reshape(-1, 4).astype(np.int32)
+    tets = (base[:, None, None] + table[None, :, :]).reshape(-1, 4).astype(np.int32)
     return rest, tets, ijk
 
 

@@ -1,0 +1,99 @@
+"""Paper-scale mesh: 320^3 cubes (33,076,161 vertices, 196,608,000 tets, about
+1e8 degrees of freedom) with N(0, 0.5 m/s) initial velocities, ground penalty
+1e7, h = 1/60, 20 iterations per step, 5 steps.
+
+The oracle checks sampled vertices of the first colour pass one by one.  A
+vertex's local solve reads only its own incident tets, its mass and its
+neighbours' positions, so the oracle runs on the sub-mesh made of every tet
+incident to the sampled vertices: exact for those vertices (their lumped
+masses come from all of their tets).  Properties that hold at any size are
+checked on the full mesh: the FP64 energy never rises over a colour pass
+(no contact yet), and the five steps stay finite."""
+import numpy as np
+import pytest
+
+from paper_2403_06321_b300 import synth, vbd
+from gpu_util import bbox_diag, params_of
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def paper_scale():
+    from paper_2403_06321_b300.build import build
+    build()
+    m, cfg, v0 = synth.paper_scale_cube(320)
+    x0 = m.rest.astype(np.float32).astype(np.float64)
+    v0 = v0.astype(np.float32).astype(np.float64)
+    colors = synth.kuhn_coloring(m.grid_ijk)
+    sim = vbd.Sim(m, vbd.make_params(**params_of(cfg)), colors=colors)
+    yield m, cfg, x0, v0, colors, sim
+    sim.close()
+
+
+def _sub_model(orc, m, verts):
+    """Oracle model of all tets incident to `verts`, plus the index map."""
+    mark = np.zeros(m.n_verts, bool)
+    mark[verts] = True
+    hit = mark[m.tets].any(axis=1)
+    sub_tets = m.tets[hit]
+    used = np.unique(sub_tets)
+    remap = np.full(m.n_verts, -1, np.int64)
+    remap[used] = np.arange(used.size)
+    model = orc.Model(m.rest[used], remap[sub_tets].astype(np.int32), m.young[hit], m.poisson[hit],
+                      m.density[hit], m.pinned[used])
+    return model, used, remap
+
+
+def test_paper_scale_first_pass_sampled_and_energy(orc, paper_scale):
+    m, cfg, x0, v0, colors, sim = paper_scale
+    sim.set_state(x0, v0)
+    vbd.vbd_begin_step(sim.ctx, cfg.h)
+    G = [sim.energy()]
+    vbd.vbd_sweep_color(sim.ctx, 0)
+    xg, _ = sim.get_state()
+    xg = xg.cpu().numpy().astype(np.float64)
+    G.append(sim.energy())
+    for c in (1, 2, 3):
+        vbd.vbd_sweep_color(sim.ctx, c)
+        G.append(sim.energy())
+    vbd.vbd_end_step(sim.ctx)
+    sim.sync_status()
+    G = np.array(G)
+    print("paper scale G per pass:", G)
+    assert np.all(np.diff(G) <= 1e-9 * np.abs(G[:-1])) and G[-1] < G[0]
+
+    rng = np.random.default_rng(61)
+    sample = rng.choice(np.nonzero(colors == 0)[0], 300, replace=False)
+    model, used, remap = _sub_model(orc, m, sample)
+    p = orc.Params.make(**params_of(cfg))
+    xs, vs = x0[used], v0[used]
+    y = model.inertia_target(p, cfg.h, xs, vs)
+    xi = model.initial_guess(p, cfg.h, xs, vs, vs)
+    diag = bbox_diag(m.rest)
+    worst = 0.0
+    for i in sample:
+        k = remap[i]
+        dx, skipped, _ = model.vertex_solve(p, cfg.h, k, xi, y, xs)
+        assert skipped == 0
+        worst = max(worst, float(np.abs(xg[i] - (xi[k] + dx)).max()))
+    # vertices of other colours are still at their initial guess
+    for i in rng.choice(np.nonzero(colors != 0)[0], 300, replace=False):
+        k = remap[i] if remap[i] >= 0 else None
+        expect = x0[i] + cfg.h * v0[i] if k is None else xi[k]
+        worst = max(worst, float(np.abs(xg[i] - expect).max()))
+    print("paper scale first pass: worst |x_gpu - x_oracle| / bbox = %.3e" % (worst / diag))
+    assert worst <= 1e-6 * diag
+
+
+def test_paper_scale_five_steps_finite(paper_scale):
+    m, cfg, x0, v0, colors, sim = paper_scale
+    sim.set_state(x0, v0)
+    for _ in range(cfg.steps):
+        sim.step(cfg.h, cfg.iters)
+    sim.sync_status()
+    x, v = sim.get_state()
+    assert bool(x.isfinite().all()) and bool(v.isfinite().all())
+    # the body keeps its size: no vertex leaves a 1 m margin around its start
+    xn = x.cpu().numpy()
+    assert np.abs(xn - x0).max() < 1.0
