@@ -49,6 +49,10 @@ def parse_args(argv=None):
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--pipeline", type=int, default=-1, help="1 TMA-staged sweep, 0 plain sweep, -1 library default")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--mu-c", type=float, default=0.0, help="ground friction coefficient (Eqs. 13-16)")
+    ap.add_argument("--line-search", action="store_true", help="local backtracking on G_i (Sec. 3.2)")
+    ap.add_argument("--jacobi", action="store_true", help="block-Jacobi iterations")
+    ap.add_argument("--young", type=float, default=0.0, help="override Young's modulus of the workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -247,6 +251,8 @@ def workload_config(args, info) -> dict:
                        "drop 0.5 m onto ground k_c=1e7, h=1/60, %d iterations/step" % (
                            n, (n + 1) ** 3, 6 * n ** 3, args.iters),
            "iters_per_step": args.iters, "h": 1.0 / 60.0, "coloring": args.coloring,
+           "variant": {"mu_c": args.mu_c, "line_search": bool(args.line_search), "jacobi": bool(args.jacobi),
+                       "young_override": args.young or None},
            "l2": "inputs larger than L2 (slot stream %.2f GB per iteration)" % (6 * n ** 3 * 4 * 56 / 1e9)}
     if info is not None:
         cfg.update({"n_colors": info.n_colors, "n_free_verts": info.n_free, "n_slots": int(info.n_slots),
@@ -377,9 +383,12 @@ def run_ours(args):
     barrier(world)
 
     m, cfg = synth.large_cube(args.n)
+    if args.young > 0:
+        m.young[:] = args.young
     colors = synth.kuhn_coloring(m.grid_ijk) if args.coloring == "kuhn" else None
     params = vbd.make_params(gravity=cfg.gravity, ground_on=cfg.ground_on, k_c=cfg.k_c,
-                             init_mode=cfg.init_mode, det_eps=cfg.det_eps)
+                             init_mode=cfg.init_mode, det_eps=cfg.det_eps, mu_c=args.mu_c,
+                             line_search=args.line_search, jacobi=args.jacobi)
     stream = torch.cuda.Stream()
     sim = vbd.Sim(m, params, colors=colors, stream=stream)
     if args.lanes or args.block or args.pipeline >= 0:
@@ -450,9 +459,15 @@ def run_ours(args):
         return 0
     C = info.n_colors
     inc_per_vert = 4.0 * m.n_tets / m.n_verts
-    b_upd = inc_per_vert * B_INC + B_VTX + B_X * C
-    launches_sweep = K * iters * C
-    bytes_per_launch = info.n_free / C * b_upd
+    if args.jacobi:
+        # one pass over all vertices per iteration (+ its 32-byte copy-back)
+        b_upd = inc_per_vert * B_INC + B_VTX + B_X + 32
+        launches_sweep = K * iters
+        bytes_per_launch = info.n_free * b_upd
+    else:
+        b_upd = inc_per_vert * B_INC + B_VTX + B_X * C
+        launches_sweep = K * iters * C
+        bytes_per_launch = info.n_free / C * b_upd
     avg_launch_s = sweep_ms / 1e3 / launches_sweep
     achieved = bytes_per_launch / avg_launch_s / 1e9
     peak, peak_kind = measured_peak_hbm()
@@ -467,7 +482,7 @@ def run_ours(args):
                      "avg_launch_us": avg_launch_s * 1e6,
                      "sweep_share_of_step": sweep_ms / t_ms},
         "e2e": e2e,
-        "gpu_launches": K * (2 + iters * C),
+        "gpu_launches": K * (2 + iters * (2 if args.jacobi else C)),
         "clocks": clk,
     }
     if not args.no_extras and world == 1:

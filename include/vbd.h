@@ -84,10 +84,29 @@ typedef struct {
     float det_eps;           /* Sec. 3.2 skip when |det H_i| <= det_eps |tr H_i / 3|^3 */
     float k_d;               /* Rayleigh damping coefficient of Eqs. 10-11 (0 = off) */
     int32_t tape_steps;      /* steps of positions recorded for vbd_backward (0 = none) */
+    float mu_c;              /* ground friction coefficient of Eqs. 13-16 (0 = off) */
+    float eps_v;             /* friction velocity threshold of Eq. 15 [m/s] */
+    int32_t line_search;     /* 1: local backtracking on G_i after each Newton step (Sec. 3.2) */
+    int32_t jacobi;          /* 1: block Jacobi, every vertex against the previous iterate */
 } vbd_params;
 
 /* Library defaults: gravity (0,0,-9.8), ground off at z = 0 with n = +z,
- * k_c = 1e7, no acceleration, adaptive init, det_eps = 1e-12, no damping. */
+ * k_c = 1e7, no acceleration, adaptive init, det_eps = 1e-12, no damping,
+ * no friction (mu_c = 0, eps_v = 1e-3 m/s).  Friction acts on vertices in
+ * ground contact: the ground is static, so the tangential part u of
+ * x_i - x_i^t is the sliding displacement, the normal-force magnitude
+ * k_c d scales it, and the force -mu_c k_c d f1(|u|) u/|u| (f1 of Eq. 15)
+ * with Hessian mu_c k_c d f1(|u|)/|u| (I - n n^T) (Eq. 16) joins Eqs. 8-9.
+ * line_search (off by default, as in the paper's results): after the Newton
+ * step dx, alpha = 1, 1/2, ..., 1/128 is tried and the first alpha with
+ * G_i(x + alpha dx) <= G_i(x) kept (no move if none), G_i being inertia,
+ * elasticity and ground penalty (Eq. 4, Eq. 12).  G_i is exactly quadratic
+ * in x_i apart from the penalty's kink, so the test is evaluated in closed
+ * form without revisiting the tets.  jacobi (off by default): one pass per
+ * iteration over all free vertices, each solved against the previous
+ * iterate and written to an auxiliary buffer copied back after the pass
+ * (the x^new of Algorithm 1 applied to all vertices at once); colours are
+ * then not used. */
 void vbd_default_params(vbd_params *out);
 
 /* Sizes of a created context (filled after vbd_color for the colour data). */
@@ -215,7 +234,8 @@ vbd_status vbd_sync_status(vbd_ctx *ctx, int64_t *det_skips, int64_t *contacts);
  * at the recorded positions.  Inputs: dL_dxT (3N floats, caller order,
  * device): dL/dx of the final positions.  Outputs (device, overwritten):
  * dL_dlogE (T floats, caller tet order): dL/d log E per tet; dL_dv0 (3N):
- * dL/dv at the first recorded step; either may be NULL.  Synchronises only
+ * dL/dv at the first recorded step; either may be NULL.  Needs k_d = 0 and
+ * mu_c = 0 (damping and friction are not variational).  Synchronises only
  * to read the tape length. */
 vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, float *dL_dv0,
                         int32_t adj_iters);

@@ -48,12 +48,14 @@ def build(force: bool = False) -> str:
 class Params(C.Structure):
     _fields_ = [("gravity", C.c_double * 3), ("ground_on", C.c_int), ("ground_height", C.c_double),
                 ("ground_normal", C.c_double * 3), ("k_c", C.c_double), ("cheby_rho", C.c_double),
-                ("init_mode", C.c_int), ("det_eps", C.c_double), ("k_d", C.c_double)]
+                ("init_mode", C.c_int), ("det_eps", C.c_double), ("k_d", C.c_double),
+                ("mu_c", C.c_double), ("eps_v", C.c_double), ("line_search", C.c_int), ("jacobi", C.c_int)]
 
     @classmethod
     def make(cls, gravity=(0.0, 0.0, -9.8), ground_on=False, ground_height=0.0,
              ground_normal=(0.0, 0.0, 1.0), k_c=0.0, cheby_rho=0.0, init_mode=3,
-             det_eps=1e-12, k_d=0.0, **_ignored) -> "Params":
+             det_eps=1e-12, k_d=0.0, mu_c=0.0, eps_v=1e-3, line_search=False, jacobi=False,
+             **_ignored) -> "Params":
         p = cls()
         p.gravity[:] = [float(g) for g in gravity]
         p.ground_on = int(bool(ground_on))
@@ -64,6 +66,10 @@ class Params(C.Structure):
         p.init_mode = int(init_mode)
         p.det_eps = float(det_eps)
         p.k_d = float(k_d)
+        p.mu_c = float(mu_c)
+        p.eps_v = float(eps_v)
+        p.line_search = int(bool(line_search))
+        p.jacobi = int(bool(jacobi))
         return p
 
 
@@ -96,11 +102,13 @@ def lib():
             "orc_model_set_log_young": (None, [vp, _dp]),
             "orc_inertia_target": (None, [vp, C.POINTER(Params), C.c_double, _dp, _dp, _dp]),
             "orc_initial_guess": (None, [vp, C.POINTER(Params), C.c_double, _dp, _dp, _dp, _dp]),
+            "orc_ground_friction": (None, [C.POINTER(Params), C.c_double, _dp, _dp, C.c_double, _dp, _dp]),
             "orc_vertex_solve": (C.c_int, [vp, C.POINTER(Params), C.c_double, C.c_int, _dp, _dp, _dp, _dp,
                                            C.POINTER(C.c_int)]),
             "orc_sweep_color": (None, [vp, C.POINTER(Params), C.c_double, _ip, C.c_int, _dp, _dp, _dp, _up,
                                        C.POINTER(Stats)]),
             "orc_cheby_omega": (C.c_double, [C.c_int, C.c_double, C.c_double]),
+            "orc_local_energy": (C.c_double, [vp, C.POINTER(Params), C.c_double, C.c_int, _dp, _dp]),
             "orc_step": (C.c_int, [vp, C.POINTER(Params), _ip, C.c_int, C.c_double, C.c_int, _dp, _dp, _dp,
                                    C.POINTER(Stats)]),
             "orc_energy_G": (C.c_double, [vp, C.POINTER(Params), C.c_double, _dp, _dp]),
@@ -179,6 +187,13 @@ def tet_hess_block(x, B, V, mu, lam, k, l) -> np.ndarray:
     H = np.zeros(9)
     lib().orc_tet_hess_block(_d(x, 12), _d(B, 9), V, mu, lam, k, l, H)
     return H.reshape(3, 3)
+
+
+def ground_friction(p: "Params", h: float, xi, xti, lambda_n: float):
+    """(force, approximate Hessian) of the ground friction term for one vertex."""
+    f, H = np.zeros(3), np.zeros(9)
+    lib().orc_ground_friction(C.byref(p), h, _d(xi, 3), _d(xti, 3), lambda_n, f, H)
+    return f, H.reshape(3, 3)
 
 
 def cheby_omega(n: int, rho: float, omega_prev: float) -> float:
@@ -283,6 +298,9 @@ class Model:
         lib().orc_step(self._h, C.byref(p), np.ascontiguousarray(colors, np.int32), int(n_colors), h,
                        int(iters), x.reshape(-1), v.reshape(-1), vprev.reshape(-1), C.byref(st))
         return st
+
+    def local_energy(self, p: Params, h, i, x, y) -> float:
+        return lib().orc_local_energy(self._h, C.byref(p), h, int(i), _d(x).reshape(-1), _d(y).reshape(-1))
 
     def energy_G(self, p: Params, h, x, y) -> float:
         return lib().orc_energy_G(self._h, C.byref(p), h, _d(x).reshape(-1), _d(y).reshape(-1))

@@ -25,6 +25,20 @@
  *    keeps its Gauss-Seidel result (Sec. 3.8 collision skip).
  *  - First step: the caller passes v^{t-1} = v^t, so the adaptive
  *    acceleration estimate is 0.
+ *  - Line search (Sec. 3.2, optional): on the variational part of G_i
+ *    (inertia, elasticity, ground penalty; Eq. 4), try alpha = 1, 1/2, ...,
+ *    1/128 along the Newton step and keep the first with G_i not above its
+ *    current value; if none, the vertex does not move.
+ *  - Block Jacobi: every vertex of an iteration solves against the previous
+ *    iterate, and all moves are applied after the pass (x^new + copy-back
+ *    of Algorithm 1 over all vertices at once); colours are not used.
+ *  - Ground friction (Eqs. 13-16): the ground is static, so the relative
+ *    displacement is delta = x_i - x_i^t; u = its tangential part.  lambda
+ *    is read as the normal-force magnitude k_c d >= 0 (as printed, the
+ *    collision-gradient sign would push the vertex along its motion), so
+ *    the force -mu lambda f1(|u|) u/|u| opposes the sliding and the
+ *    Hessian term mu lambda f1(|u|)/|u| (I - n n^T) is positive
+ *    semidefinite; |u| is not differentiated (Eq. 16).
  */
 #include "vbd_oracle.h"
 
@@ -427,6 +441,49 @@ void orc_initial_guess(const orc_model *m, const orc_params *p, double h,
     }
 }
 
+/* G_i of Eq. 4 (inertia + incident tets) plus the ground penalty of Eq. 12. */
+double orc_local_energy(const orc_model *m, const orc_params *p, double h, int i,
+                        const double *x, const double *y) {
+    double d2 = 0.0;
+    for (int r = 0; r < 3; ++r) d2 += (x[3 * i + r] - y[3 * i + r]) * (x[3 * i + r] - y[3 * i + r]);
+    double G = m->mass[i] / (2.0 * h * h) * d2;
+    for (int s = m->inc_off[i]; s < m->inc_off[i + 1]; ++s) {
+        int j = m->inc_tet[s];
+        double xs[12];
+        gather_tet(m, j, x, xs);
+        G += orc_tet_energy(xs, m->B + 9 * (size_t)j, m->V[j], m->mu[j], m->lam[j]);
+    }
+    if (p->ground_on) {
+        const double *n = p->ground_normal;
+        double nn = sqrt(dot3(n, n));
+        double d = p->ground_height - dot3(x + 3 * i, n) / nn;
+        if (d > 0.0) G += 0.5 * p->k_c * d * d;
+    }
+    return G;
+}
+
+/* Ground friction of Eqs. 13-16 for one vertex in contact: adds the force
+ * to f and its approximate Hessian to H.  f1 (Eq. 15) blends static and
+ * dynamic friction over tangential displacements below eps_v h; f1(u)/u is
+ * evaluated in closed form so that u = 0 is regular. */
+void orc_ground_friction(const orc_params *p, double h, const double xi[3], const double xti[3],
+                         double lambda_n, double f[3], double H[9]) {
+    const double *n = p->ground_normal;
+    double nn = sqrt(dot3(n, n));
+    double nh[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
+    double dlt[3] = {xi[0] - xti[0], xi[1] - xti[1], xi[2] - xti[2]};
+    double dn = dot3(dlt, nh);
+    double ut[3] = {dlt[0] - dn * nh[0], dlt[1] - dn * nh[1], dlt[2] - dn * nh[2]};
+    double um = sqrt(dot3(ut, ut));
+    double eh = p->eps_v * h;
+    double f1_over_u = (um < eh) ? (2.0 / eh - um / (eh * eh)) : 1.0 / um;
+    double c = p->mu_c * lambda_n * f1_over_u;
+    for (int r = 0; r < 3; ++r) {
+        f[r] -= c * ut[r];
+        for (int s = 0; s < 3; ++s) H[r * 3 + s] += c * ((r == s ? 1.0 : 0.0) - nh[r] * nh[s]);
+    }
+}
+
 /* Local Newton step for vertex i (Eqs. 7-9, damping Eqs. 10-11, contact
  * Eq. 12, analytic 3x3 solve and singular skip of Sec. 3.2).  Returns 1 if
  * the vertex is skipped (dx = 0). */
@@ -464,6 +521,7 @@ int orc_vertex_solve(const orc_model *m, const orc_params *p, double h, int i,
                 f[r] += p->k_c * d * nh[r];
                 for (int s = 0; s < 3; ++s) H[r * 3 + s] += p->k_c * nh[r] * nh[s];
             }
+            if (p->mu_c > 0.0) orc_ground_friction(p, h, x + 3 * i, xt + 3 * i, p->k_c * d, f, H);
         }
     }
     double det = det3(H);
@@ -475,6 +533,22 @@ int orc_vertex_solve(const orc_model *m, const orc_params *p, double h, int i,
     double A[9];
     adj3(H, A);
     for (int r = 0; r < 3; ++r) dx[r] = (A[r * 3 + 0] * f[0] + A[r * 3 + 1] * f[1] + A[r * 3 + 2] * f[2]) / det;
+    if (p->line_search) {
+        /* backtracking from x_i + dx towards x_i on G_i (Algorithm 1) */
+        double *xw = (double *)x; /* evaluated in place, restored below */
+        double x0[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+        double G0 = orc_local_energy(m, p, h, i, x, y);
+        double alpha = 1.0;
+        int ok = 0;
+        for (int k = 0; k < 8 && !ok; ++k, alpha *= 0.5) {
+            for (int r = 0; r < 3; ++r) xw[3 * i + r] = x0[r] + alpha * dx[r];
+            if (orc_local_energy(m, p, h, i, x, y) <= G0) ok = 1;
+        }
+        for (int r = 0; r < 3; ++r) xw[3 * i + r] = x0[r];
+        if (!ok) alpha = 0.0;
+        else alpha *= 2.0; /* undo the increment of the accepting pass */
+        for (int r = 0; r < 3; ++r) dx[r] *= alpha;
+    }
     return 0;
 }
 
@@ -521,8 +595,28 @@ int orc_step(const orc_model *m, const orc_params *p, const int *colors, int n_c
     orc_initial_guess(m, p, h, xt, v, vprev, x);      /* Sec. 3.7 */
     memcpy(p1, x, sizeof(double) * n3);               /* x^(0) */
     double omega = 1.0;
+    double *xj = p->jacobi ? (double *)malloc(sizeof(double) * n3 + 1) : NULL;
     for (int n = 1; n <= iters; ++n) {
-        for (int c = 0; c < n_colors; ++c) orc_sweep_color(m, p, h, colors, c, x, y, xt, coll, st);
+        if (p->jacobi) {
+            /* block Jacobi: solve every free vertex against the previous iterate */
+            memcpy(xj, x, sizeof(double) * n3);
+            for (int i = 0; i < m->n_verts; ++i) {
+                if (m->pinned[i]) continue;
+                double dx[3];
+                int contact;
+                int skipped = orc_vertex_solve(m, p, h, i, x, y, xt, dx, &contact);
+                if (st) {
+                    st->vertex_solves++;
+                    st->det_skips += skipped;
+                    st->contacts += contact;
+                }
+                if (contact) coll[i] = 1;
+                for (int r = 0; r < 3; ++r) xj[3 * i + r] = x[3 * i + r] + dx[r];
+            }
+            memcpy(x, xj, sizeof(double) * n3);
+        } else {
+            for (int c = 0; c < n_colors; ++c) orc_sweep_color(m, p, h, colors, c, x, y, xt, coll, st);
+        }
         if (p->cheby_rho > 0.0) {
             omega = orc_cheby_omega(n, p->cheby_rho, omega);   /* Eq. 19 */
             for (int i = 0; i < m->n_verts; ++i) {
@@ -543,7 +637,7 @@ int orc_step(const orc_model *m, const orc_params *p, const int *colors, int n_c
         vprev[q] = v[q];
         v[q] = vn;
     }
-    free(xt); free(y); free(p1); free(p2); free(coll);
+    free(xt); free(y); free(p1); free(p2); free(coll); free(xj);
     return 0;
 }
 

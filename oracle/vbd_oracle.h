@@ -37,6 +37,10 @@ typedef struct {
     int init_mode;          /* Sec. 3.7: 0 previous, 1 inertia, 2 inertia+acc, 3 adaptive */
     double det_eps;         /* relative threshold of the Sec. 3.2 singular-Hessian skip */
     double k_d;             /* Rayleigh damping coefficient, Eqs. 10-11 (0 = off) */
+    double mu_c;            /* ground friction coefficient, Eqs. 13-16 (0 = off) */
+    double eps_v;           /* friction velocity threshold of Eq. 15 [m/s] */
+    int line_search;        /* 1: backtracking on G_i after each local step (Sec. 3.2) */
+    int jacobi;             /* 1: block Jacobi: all vertices from the previous iterate */
 } orc_params;
 
 typedef struct {
@@ -80,6 +84,8 @@ void orc_inertia_target(const orc_model *m, const orc_params *p, double h,
                         const double *xt, const double *vt, double *y);
 void orc_initial_guess(const orc_model *m, const orc_params *p, double h,
                        const double *xt, const double *vt, const double *vprev, double *x);
+void orc_ground_friction(const orc_params *p, double h, const double xi[3], const double xti[3],
+                         double lambda_n, double f[3], double H[9]);
 int orc_vertex_solve(const orc_model *m, const orc_params *p, double h, int i,
                      const double *x, const double *y, const double *xt,
                      double dx[3], int *in_contact);
@@ -87,6 +93,8 @@ void orc_sweep_color(const orc_model *m, const orc_params *p, double h, const in
                      int color, double *x, const double *y, const double *xt,
                      unsigned char *colliding, orc_stats *st);
 double orc_cheby_omega(int n, double rho, double omega_prev);
+double orc_local_energy(const orc_model *m, const orc_params *p, double h, int i,
+                        const double *x, const double *y);
 int orc_step(const orc_model *m, const orc_params *p, const int *colors, int n_colors,
              double h, int iters, double *x, double *v, double *vprev, orc_stats *st);
 

@@ -223,6 +223,7 @@ size_t carve(const vbd_ctx *c, char *base, Dev *d) {
     t.u = (float4 *)take(16 * N);
     t.ut = (float4 *)take(16 * N);
     t.rest = (float4 *)take(16 * N);
+    t.unew = (float4 *)take(16 * N);
     t.v = (float4 *)take(16 * N);
     t.vprev = (float4 *)take(16 * N);
     t.ym = (float4 *)take(16 * N);
@@ -279,6 +280,14 @@ SweepParams sweep_params(const vbd_ctx *c, int color) {
     p.det_eps = c->params.det_eps;
     p.kd_over_h = c->h > 0.f ? c->params.k_d / c->h : 0.f;
     p.inv_h2 = c->h > 0.f ? 1.f / (c->h * c->h) : 0.f;
+    p.mu_c = c->params.mu_c;
+    p.eps_h = c->params.eps_v * c->h;
+    p.line_search = c->params.line_search ? 1 : 0;
+    p.jacobi = c->params.jacobi ? 1 : 0;
+    if (p.jacobi && color >= 0) {  // one pass over every free vertex
+        p.vbegin = 0;
+        p.vend = c->n_free;
+    }
     return p;
 }
 
@@ -291,6 +300,7 @@ bool params_ok(const vbd_params *p, std::string &why) {
     if (!(p->det_eps >= 0.f)) { why = "det_eps must be >= 0"; return false; }
     if (!(p->k_c >= 0.f) || !(p->k_d >= 0.f)) { why = "k_c and k_d must be >= 0"; return false; }
     if (p->tape_steps < 0) { why = "tape_steps must be >= 0"; return false; }
+    if (!(p->mu_c >= 0.f) || !(p->eps_v > 0.f)) { why = "mu_c must be >= 0 and eps_v > 0"; return false; }
     for (int r = 0; r < 3; ++r)
         if (!std::isfinite(p->gravity[r])) { why = "gravity must be finite"; return false; }
     return true;
@@ -346,8 +356,13 @@ void launch_colour(vbd_ctx *c, int col, cudaStream_t s) {
 void enqueue_iterations(vbd_ctx *c, int first_n, int iters, cudaStream_t s) {
     const bool cheby = c->params.cheby_rho > 0.f;
     for (int n = first_n + 1; n <= first_n + iters; ++n) {
-        for (int col = 0; col < c->n_colors; ++col)
-            launch_colour(c, col, s);
+        if (c->params.jacobi) {
+            vbd::launch_sweep(c->d, sweep_params(c, 0), c->lanes, c->block, s);
+            vbd::launch_copy_back(c->d, c->n_free, s);
+        } else {
+            for (int col = 0; col < c->n_colors; ++col)
+                launch_colour(c, col, s);
+        }
         if (cheby)
             vbd::launch_cheby(c->d, c->n_free, n, (float)cheby_omega(n, c->params.cheby_rho), s);
     }
@@ -402,6 +417,10 @@ void vbd_default_params(vbd_params *out) {
     out->det_eps = 1e-12f;
     out->k_d = 0.f;
     out->tape_steps = 0;
+    out->mu_c = 0.f;
+    out->eps_v = 1e-3f;
+    out->line_search = 0;
+    out->jacobi = 0;
 }
 
 vbd_status vbd_create_mesh(const vbd_mesh_desc *desc, const vbd_params *params, vbd_ctx **out) {
@@ -775,6 +794,7 @@ vbd_status vbd_sweep_color(vbd_ctx *ctx, int32_t color) {
     if (st != VBD_OK) return st;
     if (!ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_sweep_color outside a step");
     if (color < 0 || color >= ctx->n_colors) return fail(ctx, VBD_ERR_INVALID_ARG, "colour out of range");
+    if (ctx->params.jacobi) return fail(ctx, VBD_ERR_STATE, "block Jacobi has no colour passes");
     launch_colour(ctx, color, ctx->stream);
     CU(cudaGetLastError(), "sweep");
     return VBD_OK;
@@ -908,7 +928,8 @@ vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, floa
     if (adj_iters < 1) return fail(ctx, VBD_ERR_INVALID_ARG, "adj_iters must be >= 1");
     if (ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_backward inside a step");
     if (ctx->tape_len < 1) return fail(ctx, VBD_ERR_NO_TAPE, "no recorded steps (tape_steps = 0?)");
-    if (ctx->params.k_d != 0.f) return fail(ctx, VBD_ERR_INVALID_ARG, "the adjoint needs k_d = 0");
+    if (ctx->params.k_d != 0.f || ctx->params.mu_c != 0.f)
+        return fail(ctx, VBD_ERR_INVALID_ARG, "the adjoint needs k_d = 0 and mu_c = 0");
     if (!is_device_ptr(dL_dxT) || (dL_dlogE && !is_device_ptr(dL_dlogE)) || (dL_dv0 && !is_device_ptr(dL_dv0)))
         return fail(ctx, VBD_ERR_INVALID_ARG, "vbd_backward takes device pointers");
     const Dev &d = ctx->d;

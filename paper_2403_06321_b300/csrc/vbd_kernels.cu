@@ -109,9 +109,11 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
     const float4 yv = d.ym[vi];
     const float mh2 = yv.w;
     const float kdh = p.kd_over_h;
-    float f0 = mh2 * (yv.x - xi.x) + a.f0;
-    float f1 = mh2 * (yv.y - xi.y) + a.f1;
-    float f2 = mh2 * (yv.z - xi.z) + a.f2;
+    // variational part (inertia + elasticity), kept for the line search
+    const float fv0 = mh2 * (yv.x - xi.x) + a.f0;
+    const float fv1 = mh2 * (yv.y - xi.y) + a.f1;
+    const float fv2 = mh2 * (yv.z - xi.z) + a.f2;
+    float f0 = fv0, f1 = fv1, f2 = fv2;
     const float s = 1.0f + kdh;
     float h00 = s * a.h00 + mh2, h11 = s * a.h11 + mh2, h22 = s * a.h22 + mh2;
     float h01 = s * a.h01, h02 = s * a.h02, h12 = s * a.h12;
@@ -123,17 +125,34 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
         f2 -= kdh * (a.h02 * dx + a.h12 * dy + a.h22 * dz);
     }
     float flag = xi.w;
+    float pen = 0.0f;
+    float4 X = make_float4(0.f, 0.f, 0.f, 0.f);
     if (p.ground_on) {
-        const float4 X = d.rest[vi];
-        const float pen = p.gh - (p.gn.x * (X.x + xi.x) + p.gn.y * (X.y + xi.y) + p.gn.z * (X.z + xi.z));
+        X = d.rest[vi];
+        pen = p.gh - (p.gn.x * (X.x + xi.x) + p.gn.y * (X.y + xi.y) + p.gn.z * (X.z + xi.z));
         if (pen > 0.0f) {
             const float kd = p.kc * pen;
             f0 += kd * p.gn.x; f1 += kd * p.gn.y; f2 += kd * p.gn.z;
             h00 += p.kc * p.gn.x * p.gn.x; h11 += p.kc * p.gn.y * p.gn.y; h22 += p.kc * p.gn.z * p.gn.z;
             h01 += p.kc * p.gn.x * p.gn.y; h02 += p.kc * p.gn.x * p.gn.z; h12 += p.kc * p.gn.y * p.gn.z;
             flag = 1.0f;
+            if (p.mu_c > 0.0f) {
+                // ground friction (Eqs. 13-16): static ground, sliding displacement
+                // u = tangential part of x_i - x_i^t, normal-force magnitude kd
+                const float4 ut = d.ut[vi];
+                float dx = xi.x - ut.x, dy = xi.y - ut.y, dz = xi.z - ut.z;
+                const float dn = dx * p.gn.x + dy * p.gn.y + dz * p.gn.z;
+                dx -= dn * p.gn.x; dy -= dn * p.gn.y; dz -= dn * p.gn.z;
+                const float um = sqrtf(dx * dx + dy * dy + dz * dz);
+                const float f1u = um < p.eps_h ? (2.0f / p.eps_h - um / (p.eps_h * p.eps_h)) : 1.0f / um;
+                const float c = p.mu_c * kd * f1u;
+                f0 -= c * dx; f1 -= c * dy; f2 -= c * dz;
+                h00 += c * (1.f - p.gn.x * p.gn.x); h11 += c * (1.f - p.gn.y * p.gn.y); h22 += c * (1.f - p.gn.z * p.gn.z);
+                h01 -= c * p.gn.x * p.gn.y; h02 -= c * p.gn.x * p.gn.z; h12 -= c * p.gn.y * p.gn.z;
+            }
         }
     }
+    float4 *out = p.jacobi ? d.unew : d.u;
     // adjugate of the symmetric H
     const float a00 = h11 * h22 - h12 * h12;
     const float a01 = h02 * h12 - h01 * h22;
@@ -145,18 +164,49 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
     const float tr3 = (h00 + h11 + h22) * (1.0f / 3.0f);
     if (!(fabsf(det) > p.det_eps * fabsf(tr3 * tr3 * tr3))) {
         atomicAdd(d.counters + 1, 1ull);
-        if (flag != xi.w) d.u[vi] = make_float4(xi.x, xi.y, xi.z, flag);
+        if (p.jacobi || flag != xi.w) out[vi] = make_float4(xi.x, xi.y, xi.z, flag);
         return;
     }
     const float inv = 1.0f / det;
-    const float dx = (a00 * f0 + a01 * f1 + a02 * f2) * inv;
-    const float dy = (a01 * f0 + a11 * f1 + a12 * f2) * inv;
-    const float dz = (a02 * f0 + a12 * f1 + a22 * f2) * inv;
+    float dx = (a00 * f0 + a01 * f1 + a02 * f2) * inv;
+    float dy = (a01 * f0 + a11 * f1 + a12 * f2) * inv;
+    float dz = (a02 * f0 + a12 * f1 + a22 * f2) * inv;
     if (!(isfinite(dx) && isfinite(dy) && isfinite(dz))) {
         atomicAdd(d.counters + 0, 1ull);
+        if (p.jacobi) out[vi] = xi;
         return;
     }
-    d.u[vi] = make_float4(xi.x + dx, xi.y + dy, xi.z + dz, flag);
+    if (p.line_search) {
+        // G_i along dx: inertia + elasticity are exactly quadratic in x_i, so
+        // G_i(x + alpha dx) - G_i(x) = -alpha fv.dx + alpha^2/2 dx.Hv.dx + ground
+        // penalty change, with fv, Hv the variational force and Hessian.
+        const float q1 = fv0 * dx + fv1 * dy + fv2 * dz;
+        const float hx = (a.h00 + mh2) * dx + a.h01 * dy + a.h02 * dz;
+        const float hy = a.h01 * dx + (a.h11 + mh2) * dy + a.h12 * dz;
+        const float hz = a.h02 * dx + a.h12 * dy + (a.h22 + mh2) * dz;
+        const float q2 = dx * hx + dy * hy + dz * hz;
+        const float p0 = fmaxf(pen, 0.0f);
+        const float ndx = p.gn.x * dx + p.gn.y * dy + p.gn.z * dz;
+        float alpha = 1.0f;
+        bool ok = false;
+        for (int k = 0; k < 8; ++k) {
+            float dG = alpha * (0.5f * alpha * q2 - q1);
+            if (p.ground_on) {
+                const float pa = fmaxf(pen - alpha * ndx, 0.0f);
+                dG += 0.5f * p.kc * (pa - p0) * (pa + p0);
+            }
+            if (dG <= 0.0f) {
+                ok = true;
+                break;
+            }
+            alpha *= 0.5f;
+        }
+        if (!ok) alpha = 0.0f;
+        dx *= alpha;
+        dy *= alpha;
+        dz *= alpha;
+    }
+    out[vi] = make_float4(xi.x + dx, xi.y + dy, xi.z + dz, flag);
 }
 
 template <int L>
@@ -461,6 +511,12 @@ __global__ void k_gather(const float4 *src, float *dst, const int *new_of_orig, 
     dst[3 * o + 2] = a.z;
 }
 
+// block Jacobi: the pass wrote every free vertex to unew; copy it back
+__global__ void k_copy_back(Dev d, int n_free) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_free) d.u[i] = d.unew[i];
+}
+
 __global__ void k_restore_x(Dev d, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) d.u[i] = d.ut[i];
@@ -637,6 +693,10 @@ void launch_scatter(const float *src, float4 *dst, const int *new_of_orig, const
 void launch_gather(const float4 *src, float *dst, const int *new_of_orig, const float4 *rest, int n,
                    cudaStream_t s) {
     k_gather<<<blocks_for(n, 256), 256, 0, s>>>(src, dst, new_of_orig, rest, n);
+}
+
+void launch_copy_back(const Dev &d, int n_free, cudaStream_t s) {
+    if (n_free > 0) k_copy_back<<<blocks_for(n_free, 256), 256, 0, s>>>(d, n_free);
 }
 
 void launch_restore_x(const Dev &d, int n, cudaStream_t s) {

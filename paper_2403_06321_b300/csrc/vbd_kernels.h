@@ -19,6 +19,7 @@ struct Dev {
     float4 *vprev;    // v^{t-1}
     float4 *ym;       // inertia target y - X (Eq. 3) in .xyz, m_i / h^2 in .w
     float4 *rest;     // rest position X (FP32), used to form x = X + u
+    float4 *unew;     // block-Jacobi target (x^new of Algorithm 1)
     float4 *cheb[2];  // Chebyshev history (Eq. 18), roles alternate with iteration parity
     float *mass;      // lumped mass
     int *slot_off;    // n_free + 1: slots of free vertex i are [slot_off[i], slot_off[i+1])
@@ -52,6 +53,10 @@ struct SweepParams {
     float det_eps;
     float kd_over_h;  // Rayleigh damping k_d / h
     float inv_h2;     // 1/h^2 (adjoint only)
+    float mu_c;       // ground friction coefficient (Eqs. 13-16)
+    float eps_h;      // eps_v * h: tangential displacement where f1 reaches 1
+    int line_search;  // backtracking on G_i (Sec. 3.2)
+    int jacobi;       // write to d.unew (every vertex) instead of updating d.u in place
 };
 
 int num_sms();
@@ -74,6 +79,7 @@ void launch_scatter(const float *src, float4 *dst, const int *new_of_orig, const
 void launch_gather(const float4 *src, float *dst, const int *new_of_orig, const float4 *rest, int n,
                    cudaStream_t s);
 void launch_restore_x(const Dev &d, int n, cudaStream_t s);
+void launch_copy_back(const Dev &d, int n_free, cudaStream_t s);
 void launch_energy(const Dev &d, int n_free, int n_tets, double h, const SweepParams &p,
                    cudaStream_t s);
 int energy_partials_needed(int n_free, int n_tets);

@@ -57,6 +57,10 @@ class SimConfig:
     init_mode: int = 3  # 0 previous, 1 inertia, 2 inertia+acceleration, 3 adaptive
     det_eps: float = 1e-12
     k_d: float = 0.0
+    mu_c: float = 0.0
+    eps_v: float = 1e-3
+    line_search: bool = False
+    jacobi: bool = False
 
 
 def kuhn_grid(nx: int, ny: int, nz: int, edge: float,

@@ -53,7 +53,8 @@ class vbd_params(C.Structure):
     _fields_ = [("gravity", C.c_float * 3), ("ground_on", C.c_int32), ("ground_height", C.c_float),
                 ("ground_normal", C.c_float * 3), ("k_c", C.c_float), ("cheby_rho", C.c_float),
                 ("init_mode", C.c_int32), ("det_eps", C.c_float), ("k_d", C.c_float),
-                ("tape_steps", C.c_int32)]
+                ("tape_steps", C.c_int32), ("mu_c", C.c_float), ("eps_v", C.c_float),
+                ("line_search", C.c_int32), ("jacobi", C.c_int32)]
 
 
 class vbd_info(C.Structure):
@@ -263,8 +264,8 @@ def vbd_destroy(ctx: int) -> None:
 # ------------------------------------------------------------------ helpers
 
 def make_params(gravity=(0.0, 0.0, -9.8), ground_on=False, ground_height=0.0, ground_normal=(0.0, 0.0, 1.0),
-                k_c=1e7, cheby_rho=0.0, init_mode=3, det_eps=1e-12, k_d=0.0, tape_steps=0, **_ignored
-                ) -> vbd_params:
+                k_c=1e7, cheby_rho=0.0, init_mode=3, det_eps=1e-12, k_d=0.0, tape_steps=0, mu_c=0.0,
+                eps_v=1e-3, line_search=False, jacobi=False, **_ignored) -> vbd_params:
     p = vbd_default_params()
     p.gravity[:] = [float(g) for g in gravity]
     p.ground_on = int(bool(ground_on))
@@ -276,6 +277,10 @@ def make_params(gravity=(0.0, 0.0, -9.8), ground_on=False, ground_height=0.0, gr
     p.det_eps = float(det_eps)
     p.k_d = float(k_d)
     p.tape_steps = int(tape_steps)
+    p.mu_c = float(mu_c)
+    p.eps_v = float(eps_v)
+    p.line_search = int(bool(line_search))
+    p.jacobi = int(bool(jacobi))
     return p
 
 

@@ -151,3 +151,63 @@ def test_nonfinite_update_is_reported():
         sim.sync_status()
     finally:
         sim.close()
+
+
+def test_ground_friction_sliding_and_sticking(orc):
+    """Jittered 4x4x2 block on the ground with friction (Eqs. 13-16): sliding
+    at 1 m/s (Coulomb regime) and at rest on a slope below the friction angle
+    (static regime, |u| < eps_v h)."""
+    m = synth.beam(4, 4, 2, edge=0.05, E=2e5, nu=0.35, pin_face=None, jitter_frac=0.1, seed=81)
+    colors, _ = orc.color_greedy(m.n_verts, m.tets)
+    v0 = np.zeros_like(m.rest)
+    v0[:, 0] = 1.0
+    th = np.arctan(0.2)
+    slope = (9.8 * np.sin(th), 0.0, -9.8 * np.cos(th))
+    for gravity, vinit in [((0, 0, -9.8), v0), (slope, np.zeros_like(m.rest))]:
+        pd = params_of(synth.SimConfig(), gravity=gravity, ground_on=True, k_c=1e6, mu_c=0.4, eps_v=1e-3)
+        xg, vg = gpu_run(m, pd, colors, 1 / 60, 25, 20, None, vinit)
+        xo, vo = oracle_run(orc, m, pd, colors, 1 / 60, 25, 20, None, vinit)
+        err = _err(xg, xo, m.rest)
+        print("friction g=%s: err/bbox = %.3e, mean vx gpu %.5f oracle %.5f" % (
+            np.round(gravity, 2), err, vg[:, 0].mean(), vo[:, 0].mean()))
+        assert err <= TOL
+
+
+def test_line_search_with_hard_contact(orc):
+    """Soft block hitting the ground at 5 m/s (k_c = 1e6): full Newton steps
+    overshoot into the penalty, and the local line search (Sec. 3.2) changes
+    the result (by ~8e-3 of the bbox); both variants match the oracle, whose
+    search evaluates G_i literally.  (At k_c = 1e8 vertices come to rest at
+    d ~ 1e-6 after one pass and the contact branch d > 0 is then decided by
+    rounding: FP32 and FP64 runs take different branches there.)"""
+    m = synth.beam(4, 3, 2, edge=0.05, E=1e4, nu=0.4, pin_face=None, jitter_frac=0.1, seed=73,
+                   origin=(0, 0, 0.004))
+    colors, _ = orc.color_greedy(m.n_verts, m.tets)
+    v0 = np.zeros_like(m.rest)
+    v0[:, 2] = -5.0
+    out = {}
+    for ls in (False, True):
+        pd = params_of(synth.SimConfig(), ground_on=True, k_c=1e6, line_search=ls)
+        xg, _ = gpu_run(m, pd, colors, 1 / 60, 12, 6, None, v0)
+        xo, _ = oracle_run(orc, m, pd, colors, 1 / 60, 12, 6, None, v0)
+        err = _err(xg, xo, m.rest)
+        print("line search %s: err/bbox = %.3e" % (ls, err))
+        assert err <= TOL
+        out[ls] = xo
+    assert _err(out[True], out[False], m.rest) > 1e-3
+
+
+def test_block_jacobi(orc):
+    """Block Jacobi (all vertices against the previous iterate, x^new and
+    copy-back), with and without the line search, on a soft beam where Jacobi
+    converges; the GPU ignores the colouring in this mode."""
+    m = synth.beam(6, 2, 2, edge=0.1, E=2e3, nu=0.4, jitter_frac=0.05, seed=82)
+    colors, _ = orc.color_greedy(m.n_verts, m.tets)
+    for ls in (False, True):
+        pd = params_of(synth.SimConfig(), jacobi=True, line_search=ls)
+        xg, _ = gpu_run(m, pd, colors, 1 / 60, 30, 10)
+        xo, _ = oracle_run(orc, m, pd, colors, 1 / 60, 30, 10)
+        assert _err(xg, xo, m.rest) <= TOL
+    xk, _ = gpu_run(m, params_of(synth.SimConfig(), jacobi=True), synth.kuhn_coloring(m.grid_ijk), 1 / 60, 30, 10)
+    xg, _ = gpu_run(m, params_of(synth.SimConfig(), jacobi=True), colors, 1 / 60, 30, 10)
+    assert np.array_equal(xk, xg)
