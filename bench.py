@@ -49,6 +49,7 @@ def parse_args(argv=None):
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--pipeline", type=int, default=-1, help="1 TMA-staged sweep, 0 plain sweep, -1 library default")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shape")
     ap.add_argument("--mu-c", type=float, default=0.0, help="ground friction coefficient (Eqs. 13-16)")
     ap.add_argument("--line-search", action="store_true", help="local backtracking on G_i (Sec. 3.2)")
     ap.add_argument("--jacobi", action="store_true", help="block-Jacobi iterations")
@@ -394,9 +395,12 @@ def run_ours(args):
     if args.lanes or args.block or args.pipeline >= 0:
         vbd.vbd_set_launch(sim.ctx, args.lanes, args.block, args.pipeline)
     vbd.vbd_set_graph(sim.ctx, not args.no_graph)
-    info = vbd.vbd_get_info(sim.ctx)
     iters, h, K = args.iters, cfg.h, args.steps
     zeros = np.zeros_like(m.rest)
+    sim.set_state(m.rest, zeros)
+    if not (args.no_autotune or args.lanes or args.block or args.pipeline >= 0):
+        vbd.vbd_autotune(sim.ctx, h, min(iters, 20))  # times each launch shape, keeps the fastest
+    info = vbd.vbd_get_info(sim.ctx)
 
     # warm-up (graph capture happens here), then reset to the initial state
     sim.set_state(m.rest, zeros)

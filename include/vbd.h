@@ -246,7 +246,7 @@ vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, floa
  * lanes per vertex (lanes_per_vertex is ignored).  pipeline = 0: one thread
  * group of lanes_per_vertex in {4, 8, 16, 32} per vertex loading its slots
  * from global memory, block_threads in {64, 128, 256} (default: pipeline 0,
- * 8 lanes, 128 threads, the fastest measured on B300).  0 keeps a value
+ * 4 lanes, 128 threads, the fastest measured on B300).  0 keeps a value
  * (pipeline < 0 keeps it too).  Must not be called during stream capture. */
 vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_threads, int32_t pipeline);
 

@@ -102,13 +102,16 @@ __global__ void __launch_bounds__(256) k_adj_sweep(Dev d, const float4 *__restri
         const int4 r0 = __ldcs(d.s0 + s);
         const float4 r1 = __ldcs(d.s1 + s);
         const float4 r2 = __ldcs(d.s2 + s);
-        const float2 r3 = __ldcs(d.s3 + s);
         const int nb[3] = {r0.x, r0.y, r0.z};
-        const float Vmu = __int_as_float(r0.w), Vlam = r3.y;
         float3 g[3];
-        g[0] = make_float3(r1.x, r1.y, r1.z);
-        g[1] = make_float3(r1.w, r2.x, r2.y);
-        g[2] = make_float3(r2.z, r2.w, r3.x);
+        g[0] = make_float3(__int_as_float(r0.w), r1.x, r1.y);
+        g[1] = make_float3(r1.z, r1.w, r2.x);
+        g[2] = make_float3(r2.y, r2.z, r2.w);
+        // tet volume from the gradients; mu, lambda of the tet (the adjoint
+        // reads the per-tet arrays, which hold the current log E)
+        const float V = __frcp_rn(6.0f * fabsf(dot(g[0], cross(g[1], g[2]))));
+        const int j = __ldcs(d.slot_tet + s);
+        const float Vmu = V * __ldg(d.tet_mu + j), Vlam = V * __ldg(d.tet_lam + j);
         const float3 gi = make_float3(-(g[0].x + g[1].x + g[2].x), -(g[0].y + g[1].y + g[2].y),
                                       -(g[0].z + g[1].z + g[2].z));
         float3 e[3], lk[3];

@@ -57,6 +57,7 @@ struct vbd_ctx {
     int n_free = 0;
     std::vector<int> color_begin;    // n_colors + 1, over the free range
     long long n_slots = 0;
+    bool per_tet_mat = false;        // some vertex's tets differ in material, or log E was set
     std::vector<int> slot_off;       // n_free + 1
     std::vector<int> inc_off, inc_tet, inc_loc;  // vertex -> incident tets (caller ids)
     // device
@@ -73,7 +74,7 @@ struct vbd_ctx {
     int tape_len = 0;
     std::vector<float> tape_h;
     // launch shape / graphs
-    int lanes = 8, block = 128;
+    int lanes = 4, block = 128;
     bool pipeline = false;
     int pipe_block = 128;
     int pipe_maxs = 0;          // slot capacity of one stage
@@ -234,7 +235,7 @@ size_t carve(const vbd_ctx *c, char *base, Dev *d) {
     t.s0 = (int4 *)take(16 * S);
     t.s1 = (float4 *)take(16 * S);
     t.s2 = (float4 *)take(16 * S);
-    t.s3 = (float2 *)take(8 * (S + 2));  // the pipelined sweep copies s3 from/to even slots
+    t.vmat = (float2 *)take(8 * N);
     t.slot_tet = (int *)take(4 * S);
     t.slot_loc = (int *)take(4 * S);
     t.tet_v = (int4 *)take(16 * T);
@@ -283,6 +284,7 @@ SweepParams sweep_params(const vbd_ctx *c, int color) {
     p.mu_c = c->params.mu_c;
     p.eps_h = c->params.eps_v * c->h;
     p.line_search = c->params.line_search ? 1 : 0;
+    p.per_tet_mat = c->per_tet_mat ? 1 : 0;
     p.jacobi = c->params.jacobi ? 1 : 0;
     if (p.jacobi && color >= 0) {  // one pass over every free vertex
         p.vbegin = 0;
@@ -368,9 +370,10 @@ void enqueue_iterations(vbd_ctx *c, int first_n, int iters, cudaStream_t s) {
     }
 }
 
-// Slot records of free vertices [k0, k1) (internal ids), in slot order.
-void build_slots(const vbd_ctx *c, int k0, int k1, int4 *s0, float4 *s1, float4 *s2, float2 *s3,
-                 int *stet, int *sloc) {
+// Slot records of free vertices [k0, k1) (internal ids), in slot order:
+// the other three vertices' ids and shape gradients (volume and material are
+// not stored per slot).
+void build_slots(const vbd_ctx *c, int k0, int k1, int4 *s0, float4 *s1, float4 *s2, int *stet, int *sloc) {
     size_t w = 0;
     for (int k = k0; k < k1; ++k) {
         const int i = c->orig_of_new[k];
@@ -378,22 +381,21 @@ void build_slots(const vbd_ctx *c, int k0, int k1, int4 *s0, float4 *s1, float4 
             const int j = c->inc_tet[q], a = c->inc_loc[q];
             const double *Bj = &c->B[9 * (size_t)j];
             int ids[3];
-            double g[3][3];
+            float g[9];
             int m = 0;
             for (int b = 0; b < 4; ++b) {
                 if (b == a) continue;
                 ids[m] = c->new_of_orig[c->tets[4 * (size_t)j + b]];
-                shape_grad(Bj, b, g[m]);
+                double gd[3];
+                shape_grad(Bj, b, gd);
+                for (int r = 0; r < 3; ++r) g[3 * m + r] = (float)gd[r];
                 ++m;
             }
-            const float Vmu = (float)(c->V[j] * c->mu[j]);
-            const float Vlam = (float)(c->V[j] * c->lam[j]);
-            int vmu_bits;
-            std::memcpy(&vmu_bits, &Vmu, 4);
-            s0[w] = make_int4(ids[0], ids[1], ids[2], vmu_bits);
-            s1[w] = make_float4((float)g[0][0], (float)g[0][1], (float)g[0][2], (float)g[1][0]);
-            s2[w] = make_float4((float)g[1][1], (float)g[1][2], (float)g[2][0], (float)g[2][1]);
-            s3[w] = make_float2((float)g[2][2], Vlam);
+            int gx_bits;
+            std::memcpy(&gx_bits, &g[0], 4);
+            s0[w] = make_int4(ids[0], ids[1], ids[2], gx_bits);
+            s1[w] = make_float4(g[1], g[2], g[3], g[4]);
+            s2[w] = make_float4(g[5], g[6], g[7], g[8]);
             stet[w] = j;
             sloc[w] = a;
         }
@@ -617,9 +619,29 @@ vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *st
     CU(cudaMemcpyAsync(d.slot_off, ctx->slot_off.data(), 4 * ((size_t)ctx->n_free + 1), cudaMemcpyHostToDevice, s),
        "upload slot_off");
     {
+        // per-vertex material when every tet around each free vertex shares it
+        std::vector<float2> vm(N, make_float2(0.f, 0.f));
+        bool homogeneous = true;
+        for (int k = 0; k < ctx->n_free && homogeneous; ++k) {
+            const int i = ctx->orig_of_new[k];
+            for (int q = ctx->inc_off[i]; q < ctx->inc_off[i + 1]; ++q) {
+                const int j = ctx->inc_tet[q];
+                const float2 mj = make_float2((float)ctx->mu[j], (float)ctx->lam[j]);
+                if (q == ctx->inc_off[i]) {
+                    vm[k] = mj;
+                } else if (mj.x != vm[k].x || mj.y != vm[k].y) {
+                    homogeneous = false;
+                    break;
+                }
+            }
+        }
+        ctx->per_tet_mat = !homogeneous;
+        CU(cudaMemcpyAsync(d.vmat, vm.data(), 8 * (size_t)N, cudaMemcpyHostToDevice, s), "upload vmat");
+        CU(cudaStreamSynchronize(s), "upload vmat");
+    }
+    {
         std::vector<int4> h0;
         std::vector<float4> h1, h2;
-        std::vector<float2> h3;
         std::vector<int> ht, hl;
         int k0 = 0;
         while (k0 < ctx->n_free) {
@@ -627,12 +649,11 @@ vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *st
             while (k1 < ctx->n_free && (long long)ctx->slot_off[k1 + 1] - ctx->slot_off[k0] <= kChunk) ++k1;
             if (k1 == k0) k1 = k0 + 1;
             const long long a0 = ctx->slot_off[k0], n = (long long)ctx->slot_off[k1] - a0;
-            h0.resize(n); h1.resize(n); h2.resize(n); h3.resize(n); ht.resize(n); hl.resize(n);
-            build_slots(ctx, k0, k1, h0.data(), h1.data(), h2.data(), h3.data(), ht.data(), hl.data());
+            h0.resize(n); h1.resize(n); h2.resize(n); ht.resize(n); hl.resize(n);
+            build_slots(ctx, k0, k1, h0.data(), h1.data(), h2.data(), ht.data(), hl.data());
             CU(cudaMemcpyAsync(d.s0 + a0, h0.data(), 16 * (size_t)n, cudaMemcpyHostToDevice, s), "upload slots");
             CU(cudaMemcpyAsync(d.s1 + a0, h1.data(), 16 * (size_t)n, cudaMemcpyHostToDevice, s), "upload slots");
             CU(cudaMemcpyAsync(d.s2 + a0, h2.data(), 16 * (size_t)n, cudaMemcpyHostToDevice, s), "upload slots");
-            CU(cudaMemcpyAsync(d.s3 + a0, h3.data(), 8 * (size_t)n, cudaMemcpyHostToDevice, s), "upload slots");
             CU(cudaMemcpyAsync(d.slot_tet + a0, ht.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s), "upload slots");
             CU(cudaMemcpyAsync(d.slot_loc + a0, hl.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s), "upload slots");
             CU(cudaStreamSynchronize(s), "upload slots");  // the staging vectors are reused
@@ -769,8 +790,14 @@ vbd_status vbd_set_log_young(vbd_ctx *ctx, const float *log_young) {
            "log_young upload");
         src = ctx->d.stage[2];
     }
-    vbd::launch_set_log_young(ctx->d, src, ctx->T, ctx->n_slots, ctx->stream);
+    vbd::launch_set_log_young(ctx->d, src, ctx->T, ctx->stream);
     CU(cudaGetLastError(), "set_log_young");
+    // materials may now differ between the tets of a vertex: read them per tet
+    if (!ctx->per_tet_mat) {
+        ctx->per_tet_mat = true;
+        ctx->version++;
+        clear_graphs(ctx);
+    }
     return VBD_OK;
 }
 
@@ -995,7 +1022,8 @@ vbd_status vbd_autotune(vbd_ctx *ctx, float h, int32_t iters, float *best_ms_per
     if (ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_autotune inside a step");
     if (iters < 1) return fail(ctx, VBD_ERR_INVALID_ARG, "iters must be >= 1");
     struct Shape { int pipe, lanes, block; };
-    const Shape shapes[] = {{1, 8, 128}, {1, 8, 256}, {0, 4, 128}, {0, 8, 128}, {0, 8, 256}, {0, 16, 256}};
+    const Shape shapes[] = {{0, 4, 64}, {0, 4, 128}, {0, 4, 256}, {0, 8, 128}, {0, 8, 256},
+                            {0, 16, 256}, {1, 8, 128}, {1, 8, 256}};
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0), "event");
     CU(cudaEventCreate(&e1), "event");

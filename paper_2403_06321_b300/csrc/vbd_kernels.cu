@@ -8,8 +8,10 @@
 //   k_finish             v = (x - x^t)/h (Eq. 6), once per step
 //
 // The sweep is memory bound: per (vertex, incident tet) pair ("slot") it
-// streams 56 bytes of precomputed rest data once per iteration and gathers
-// three neighbour positions.  Slots of one colour are contiguous, so the
+// streams 48 bytes of precomputed rest data (three vertex ids and the three
+// shape gradients) once per iteration and gathers three neighbour positions;
+// the tet's volume follows from the gradients, its material from the vertex
+// (or, for per-tet materials, from the tet's arrays).  Slots of one colour are contiguous, so the
 // stream is fully sequential; L lanes of a warp cooperate on one vertex
 // (lanes stride over its slots), reduce f_i and H_i with xor shuffles in a
 // fixed order (deterministic), and one lane solves the 3x3 system.
@@ -48,16 +50,32 @@ struct Acc {
 //   c' = cof(F) g_i - g_i = (tr D) g_i - D^T g_i + cof(D) g_i,   c = g_i + c'
 //   V P g_i    = V mu (D g_i - c') + V lam (J - 1) c     (alpha lam = lam + mu)
 //   f_i -= V P g_i,   H_i += V mu |g_i|^2 I + V lam c c^T.
-__device__ __forceinline__ void accumulate_slot(const float4 *__restrict__ u, int4 r0, float4 r1,
-                                                float4 r2, float2 r3, float3 ui, Acc &acc) {
+// Material of a slot: the tet's volume is 1 / (6 |det[g_a; g_b; g_c]|) (any
+// three of a tet's four shape gradients are the rows of the inverse rest edge
+// matrix up to a sign), mu and lambda are the vertex's, or the tet's.
+__device__ __forceinline__ float2 slot_material(const Dev &d, const SweepParams &p, int s, float2 vm,
+                                                float3 ga, float3 gb, float3 gc) {
+    const float detg = dot(ga, cross(gb, gc));
+    const float V = __frcp_rn(6.0f * fabsf(detg));
+    if (p.per_tet_mat) {
+        const int j = __ldcs(d.slot_tet + s);
+        vm = make_float2(__ldg(d.tet_mu + j), __ldg(d.tet_lam + j));
+    }
+    return make_float2(V * vm.x, V * vm.y);
+}
+
+__device__ __forceinline__ void accumulate_slot(const Dev &d, const SweepParams &p, int s, float2 vm,
+                                                int4 r0, float4 r1, float4 r2, float3 ui, Acc &acc) {
+    const float4 *__restrict__ u = d.u;
     const float3 da = f3(__ldg(u + r0.x)) - ui;
     const float3 db = f3(__ldg(u + r0.y)) - ui;
     const float3 dc = f3(__ldg(u + r0.z)) - ui;
-    const float Vmu = __int_as_float(r0.w);
-    const float Vlam = r3.y;
-    const float3 ga = make_float3(r1.x, r1.y, r1.z);
-    const float3 gb = make_float3(r1.w, r2.x, r2.y);
-    const float3 gc = make_float3(r2.z, r2.w, r3.x);
+    const float3 ga = make_float3(__int_as_float(r0.w), r1.x, r1.y);
+    const float3 gb = make_float3(r1.z, r1.w, r2.x);
+    const float3 gc = make_float3(r2.y, r2.z, r2.w);
+    const float2 mat = slot_material(d, p, s, vm, ga, gb, gc);
+    const float Vmu = mat.x;
+    const float Vlam = mat.y;
     const float3 gi = make_float3(-(ga.x + gb.x + gc.x), -(ga.y + gb.y + gc.y), -(ga.z + gb.z + gc.z));
     // columns of D: D_s = da * ga[s] + db * gb[s] + dc * gc[s]
     const float3 D0 = make_float3(da.x * ga.x + db.x * gb.x + dc.x * gc.x,
@@ -70,9 +88,9 @@ __device__ __forceinline__ void accumulate_slot(const float4 *__restrict__ u, in
                                   da.y * ga.z + db.y * gb.z + dc.y * gc.z,
                                   da.z * ga.z + db.z * gb.z + dc.z * gc.z);
     const float tr = D0.x + D1.y + D2.z;
-    const float m2 = (D0.x * D1.y - D1.x * D0.y) + (D0.x * D2.z - D2.x * D0.z) + (D1.y * D2.z - D2.y * D1.z);
     const float3 q0 = cross(D1, D2), q1 = cross(D2, D0), q2 = cross(D0, D1);  // columns of cof(D)
-    const float jm1 = tr + m2 + dot(D0, q0);
+    // the sum of the principal 2x2 minors of D is the trace of cof(D)
+    const float jm1 = tr + (q0.x + q1.y + q2.z) + dot(D0, q0);
     const float3 cp = make_float3(tr * gi.x - dot(D0, gi) + gi.x * q0.x + gi.y * q1.x + gi.z * q2.x,
                                   tr * gi.y - dot(D1, gi) + gi.x * q0.y + gi.y * q1.y + gi.z * q2.y,
                                   tr * gi.z - dot(D2, gi) + gi.x * q0.z + gi.y * q1.z + gi.z * q2.z);
@@ -84,10 +102,10 @@ __device__ __forceinline__ void accumulate_slot(const float4 *__restrict__ u, in
     acc.f0 -= Vmu * (Dg.x - cp.x) + k * c.x;
     acc.f1 -= Vmu * (Dg.y - cp.y) + k * c.y;
     acc.f2 -= Vmu * (Dg.z - cp.z) + k * c.z;
-    const float d = Vmu * dot(gi, gi);
-    acc.h00 += d + Vlam * c.x * c.x;
-    acc.h11 += d + Vlam * c.y * c.y;
-    acc.h22 += d + Vlam * c.z * c.z;
+    const float dg = Vmu * dot(gi, gi);
+    acc.h00 += dg + Vlam * c.x * c.x;
+    acc.h11 += dg + Vlam * c.y * c.y;
+    acc.h22 += dg + Vlam * c.z * c.z;
     acc.h01 += Vlam * c.x * c.y;
     acc.h02 += Vlam * c.x * c.z;
     acc.h12 += Vlam * c.y * c.z;
@@ -223,14 +241,10 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, SweepParams p) {
         s1 = d.slot_off[vi + 1];
     }
     const float3 x3 = f3(xi);
+    const float2 vm = (active && !p.per_tet_mat) ? __ldg(d.vmat + vi) : make_float2(0.f, 0.f);
     Acc acc = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int s = s0 + lane; s < s1; s += L) {
-        const int4 r0 = __ldcs(d.s0 + s);
-        const float4 r1 = __ldcs(d.s1 + s);
-        const float4 r2 = __ldcs(d.s2 + s);
-        const float2 r3 = __ldcs(d.s3 + s);
-        accumulate_slot(d.u, r0, r1, r2, r3, x3, acc);
-    }
+    for (int s = s0 + lane; s < s1; s += L)
+        accumulate_slot(d, p, s, vm, __ldcs(d.s0 + s), __ldcs(d.s1 + s), __ldcs(d.s2 + s), x3, acc);
     acc.f0 = sub_reduce<L>(acc.f0);
     acc.f1 = sub_reduce<L>(acc.f1);
     acc.f2 = sub_reduce<L>(acc.f2);
@@ -247,7 +261,7 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, SweepParams p) {
 // Persistent CTAs of TT threads walk the colour range in chunks of TT / 8
 // consecutive vertices (8 lanes per vertex as in k_sweep).  A chunk's slot
 // records are contiguous, so one thread copies them global -> shared with
-// four bulk copies (cp.async.bulk, completion counted in bytes on an
+// three bulk copies (cp.async.bulk, completion counted in bytes on an
 // mbarrier), two chunks ahead of the consumers.  The stream is then in flight
 // without occupying registers, which is what limits k_sweep.  Every wait is
 // bounded: on time-out the CTA records an error (counters[2]), waits (again
@@ -260,7 +274,7 @@ constexpr long long kWaitCycles = 4000000000ll;   // ~2 s of SM clock
 struct StageMeta {
     int a;       // first slot of the chunk
     int n;       // slot count
-    int a3;      // first slot of the s3 copy (even)
+    int pad;
     int direct;  // 1: consumers read global memory (chunk larger than a stage, or empty)
 };
 
@@ -294,7 +308,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 struct StageView {
     int4 *s0;
     float4 *s1, *s2;
-    float2 *s3;
 };
 
 __device__ __forceinline__ StageView stage_view(char *base, int maxs) {
@@ -302,14 +315,12 @@ __device__ __forceinline__ StageView stage_view(char *base, int maxs) {
     v.s0 = (int4 *)base;
     v.s1 = (float4 *)(base + 16 * (size_t)maxs);
     v.s2 = (float4 *)(base + 32 * (size_t)maxs);
-    v.s3 = (float2 *)(base + 48 * (size_t)maxs);
     return v;
 }
 
-// Bytes of one stage: three 16-byte arrays and one 8-byte array with two
-// spare entries (the s3 copy starts on an even slot), rounded to 128.
+// Bytes of one stage: three 16-byte arrays, rounded to 128.
 __host__ __device__ inline size_t pipe_stage_bytes(int maxs) {
-    return ((size_t)48 * maxs + 8 * ((size_t)maxs + 2) + 127) & ~(size_t)127;
+    return ((size_t)48 * maxs + 127) & ~(size_t)127;
 }
 __host__ __device__ inline size_t pipe_smem_bytes(int maxs) {
     return 128 + kPipeStages * pipe_stage_bytes(maxs);
@@ -325,7 +336,7 @@ __device__ __forceinline__ void pipe_issue(const Dev &d, const SweepParams &p, i
     StageMeta m;
     m.a = a;
     m.n = n;
-    m.a3 = a & ~1;
+    m.pad = 0;
     m.direct = (n <= 0 || n > maxs) ? 1 : 0;
     meta[st] = m;
     const unsigned ab = smem_addr(bar + st);
@@ -333,14 +344,12 @@ __device__ __forceinline__ void pipe_issue(const Dev &d, const SweepParams &p, i
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(ab) : "memory");
         return;
     }
-    const int b3 = (b + 1) & ~1;
-    const unsigned tx = 48u * (unsigned)n + 8u * (unsigned)(b3 - m.a3);
+    const unsigned tx = 48u * (unsigned)n;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(ab), "r"(tx) : "memory");
     StageView v = stage_view(stages + st * pipe_stage_bytes(maxs), maxs);
     bulk_g2s(v.s0, d.s0 + a, 16u * n, bar + st);
     bulk_g2s(v.s1, d.s1 + a, 16u * n, bar + st);
     bulk_g2s(v.s2, d.s2 + a, 16u * n, bar + st);
-    bulk_g2s(v.s3, d.s3 + m.a3, 8u * (unsigned)(b3 - m.a3), bar + st);
 }
 
 template <int TT>
@@ -400,14 +409,14 @@ __global__ void __launch_bounds__(TT) k_sweep_pipe(Dev d, SweepParams p, int max
             s1 = d.slot_off[vi + 1] - m.a;
         }
         const float3 x3 = f3(xi);
+        const float2 vm = (active && !p.per_tet_mat) ? __ldg(d.vmat + vi) : make_float2(0.f, 0.f);
         Acc acc = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (!m.direct) {
-            const int o3 = m.a - m.a3;
             for (int s = s0 + lane; s < s1; s += L)
-                accumulate_slot(d.u, v.s0[s], v.s1[s], v.s2[s], v.s3[s + o3], x3, acc);
+                accumulate_slot(d, p, s + m.a, vm, v.s0[s], v.s1[s], v.s2[s], x3, acc);
         } else {
             for (int s = s0 + lane + m.a; s < s1 + m.a; s += L)
-                accumulate_slot(d.u, __ldcs(d.s0 + s), __ldcs(d.s1 + s), __ldcs(d.s2 + s), __ldcs(d.s3 + s), x3, acc);
+                accumulate_slot(d, p, s, vm, __ldcs(d.s0 + s), __ldcs(d.s1 + s), __ldcs(d.s2 + s), x3, acc);
         }
         acc.f0 = sub_reduce<L>(acc.f0);
         acc.f1 = sub_reduce<L>(acc.f1);
@@ -593,25 +602,14 @@ __global__ void k_reduce_partials(const double *partials, int n, double *out) {
     block_sum_store(e, out);
 }
 
-__global__ void k_set_log_young(Dev d, const float *log_young, int n_tets, long long n_slots) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n_tets) {
-        const float E = expf(log_young[i]);
-        const float nu = d.tet_nu[i];
-        const float mu = E / (2.f * (1.f + nu));
-        d.tet_mu[i] = mu;
-        d.tet_lam[i] = E * nu / ((1.f + nu) * (1.f - 2.f * nu)) + mu;
-    }
-    if (i < n_slots) {
-        const int j = d.slot_tet[i];
-        const float E = expf(log_young[j]);
-        const float nu = d.tet_nu[j];
-        const float V = d.tet_V[j];
-        const float mu = E / (2.f * (1.f + nu));
-        const float lam = E * nu / ((1.f + nu) * (1.f - 2.f * nu)) + mu;
-        d.s0[i].w = __float_as_int(V * mu);
-        d.s3[i].y = V * lam;
-    }
+__global__ void k_set_log_young(Dev d, const float *log_young, int n_tets) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_tets) return;
+    const float E = expf(log_young[i]);
+    const float nu = d.tet_nu[i];
+    const float mu = E / (2.f * (1.f + nu));
+    d.tet_mu[i] = mu;
+    d.tet_lam[i] = E * nu / ((1.f + nu) * (1.f - 2.f * nu)) + mu;
 }
 
 inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -723,10 +721,8 @@ void launch_energy(const Dev &d, int n_free, int n_tets, double h, const SweepPa
     k_reduce_partials<<<1, EB, 0, s>>>(d.partials, gv + gt, d.energy_out);
 }
 
-void launch_set_log_young(const Dev &d, const float *log_young, int n_tets, long long n_slots,
-                          cudaStream_t s) {
-    const long long n = std::max<long long>(n_tets, n_slots);
-    k_set_log_young<<<blocks_for(n, 256), 256, 0, s>>>(d, log_young, n_tets, n_slots);
+void launch_set_log_young(const Dev &d, const float *log_young, int n_tets, cudaStream_t s) {
+    k_set_log_young<<<blocks_for(n_tets, 256), 256, 0, s>>>(d, log_young, n_tets);
 }
 
 // ---- energy with library-owned scratch --------------------------------------

@@ -23,11 +23,11 @@ struct Dev {
     float4 *cheb[2];  // Chebyshev history (Eq. 18), roles alternate with iteration parity
     float *mass;      // lumped mass
     int *slot_off;    // n_free + 1: slots of free vertex i are [slot_off[i], slot_off[i+1])
-    // incidence slots (one per (free vertex, incident tet)), 56 bytes each:
-    int4 *s0;         // other three vertex ids, bits of V*mu
-    float4 *s1;       // g_a.xyz, g_b.x
-    float4 *s2;       // g_b.yz, g_c.xy
-    float2 *s3;       // g_c.z, V*lambda
+    // incidence slots (one per (free vertex, incident tet)), 48 bytes each:
+    int4 *s0;         // other three vertex ids, bits of g_a.x
+    float4 *s1;       // g_a.yz, g_b.xy
+    float4 *s2;       // g_b.z, g_c.xyz
+    float2 *vmat;     // per free vertex: (mu, lambda) shared by all its tets
     int *slot_tet;    // caller tet id of each slot
     int *slot_loc;    // local index (0..3) of the slot's own vertex in that tet
     // per tet (caller order)
@@ -56,6 +56,7 @@ struct SweepParams {
     float mu_c;       // ground friction coefficient (Eqs. 13-16)
     float eps_h;      // eps_v * h: tangential displacement where f1 reaches 1
     int line_search;  // backtracking on G_i (Sec. 3.2)
+    int per_tet_mat;  // 1: mu, lambda per tet (via slot_tet); 0: per vertex (vmat)
     int jacobi;       // write to d.unew (every vertex) instead of updating d.u in place
 };
 
@@ -88,8 +89,7 @@ int energy_static_capacity();
 int energy_static_partials_needed(int n_free, int n_tets);
 cudaError_t launch_energy_static(const Dev &d, int n_free, int n_tets, double h, const SweepParams &p,
                                  double *G_out, cudaStream_t s);
-void launch_set_log_young(const Dev &d, const float *log_young, int n_tets, long long n_slots,
-                          cudaStream_t s);
+void launch_set_log_young(const Dev &d, const float *log_young, int n_tets, cudaStream_t s);
 
 // adjoint
 void launch_adj_rhs(const Dev &d, int n, int n_free, float inv_h, cudaStream_t s);
