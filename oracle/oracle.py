@@ -78,9 +78,11 @@ class Stats(C.Structure):
 
 
 def lib():
+    """The oracle library; VBD_ORACLE_LIB names another build of vbd_oracle.c
+    (used only by the planted-mistake tests, which compile mutated copies)."""
     global _lib
     if _lib is None:
-        L = C.CDLL(build())
+        L = C.CDLL(os.environ.get("VBD_ORACLE_LIB") or build())
         vp = C.c_void_p
         sig = {
             "orc_lame": (None, [C.c_double, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]),

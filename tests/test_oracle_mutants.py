@@ -1,0 +1,69 @@
+"""Planted mistakes: each test compiles a copy of the oracle with one
+plausible error (a dropped term, a wrong sign, a transposed operand, a wrong
+constant) and checks that the pins of the named test file fail against it.
+The identity copy must pass, so failures come from the planted mistake.
+CPU only; the mistakes live only in temporary copies."""
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "vbd_oracle.c")
+
+# (name, text in vbd_oracle.c, replacement, pin file that must catch it)
+MUTANTS = [
+    ("hessian_skew_sign", "cross3(gl, gk, gx);", "cross3(gk, gl, gx);", "test_oracle_element.py"),
+    ("hessian_drops_lambda_cc", "+ lam * ck[r] * cl[s]", "", "test_oracle_element.py"),
+    ("alpha_one", "1.0 + mu / lam", "1.0", "test_oracle_element.py"),
+    ("lame_without_mu_shift", "E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)) + *mu;",
+     "E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));", "test_oracle_element.py"),
+    ("F_uses_B_transposed", "acc += Ds[r * 3 + a] * B[a * 3 + s];", "acc += Ds[r * 3 + a] * B[s * 3 + a];",
+     "test_oracle_element.py"),
+    ("mass_over_three", "density[j] * m->V[j] / 4.0", "density[j] * m->V[j] / 3.0", "test_oracle_element.py"),
+    ("inertia_gravity_sign", "+ h * h * p->gravity[r];", "- h * h * p->gravity[r];", "test_oracle_solver.py"),
+    ("adaptive_clamp_top", "if (a_ext_comp > gnorm) atil = 1.0;", "if (a_ext_comp > gnorm) atil = 0.0;",
+     "test_oracle_solver.py"),
+    ("chebyshev_omega2_sign", "2.0 / (2.0 - rho * rho)", "2.0 / (2.0 + rho * rho)", "test_oracle_solver.py"),
+    ("chebyshev_no_collision_skip", "if (n >= 2 && !m->pinned[i] && !coll[i])", "if (n >= 2 && !m->pinned[i])",
+     "test_oracle_solver.py"),
+    ("velocity_times_h", "double vn = (x[q] - xt[q]) / h;", "double vn = (x[q] - xt[q]) * h;",
+     "test_oracle_solver.py"),
+    ("contact_force_sign", "f[r] += p->k_c * d * nh[r];", "f[r] -= p->k_c * d * nh[r];", "test_oracle_solver.py"),
+    ("damping_force_sign", "f[r] -= p->k_d / h * Hel[r * 3 + s]", "f[r] += p->k_d / h * Hel[r * 3 + s]",
+     "test_oracle_solver.py"),
+    ("colouring_tie_break", "return (i > j) - (i < j);\n}\n\n/* Returns", "return (i < j) - (i > j);\n}\n\n/* Returns",
+     "test_oracle_solver.py"),
+    ("friction_pushes_along_motion", "f[r] -= c * ut[r];", "f[r] += c * ut[r];", "test_oracle_friction.py"),
+    ("line_search_accepts_increase", "<= G0) ok = 1;", ">= G0) ok = 1;", "test_oracle_variants.py"),
+]
+
+
+def _run_pins(src_text, pin_file):
+    with tempfile.TemporaryDirectory() as tmp:
+        c = os.path.join(tmp, "vbd_oracle.c")
+        with open(c, "w") as f:
+            f.write(src_text)
+        lib = os.path.join(tmp, "libmutant.so")
+        subprocess.check_call(["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-fno-fast-math",
+                               "-ffp-contract=off", "-I", os.path.join(ROOT, "oracle"), "-o", lib, c, "-lm"])
+        env = dict(os.environ, VBD_ORACLE_LIB=lib)
+        res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                              os.path.join(ROOT, "tests", pin_file)], env=env, cwd=ROOT,
+                             capture_output=True, text=True, timeout=600)
+        return res.returncode
+
+
+def test_identity_copy_passes():
+    src = open(SRC).read()
+    for pin in ("test_oracle_element.py", "test_oracle_solver.py"):
+        assert _run_pins(src, pin) == 0, pin
+
+
+@pytest.mark.parametrize("name,old,new,pin", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(name, old, new, pin):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, "mutation target missing: %s" % name
+    assert _run_pins(src.replace(old, new), pin) != 0, "%s was not caught by %s" % (name, pin)
