@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(256) k_adj_sweep(Dev d, const float4 *__restri
         s0 = d.slot_off[vi];
         s1 = d.slot_off[vi + 1];
     }
+    const float2 vm = (active && !p.per_tet_mat) ? __ldg(d.vmat + vi) : make_float2(0.f, 0.f);
     AdjAcc a = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int s = s0 + lane; s < s1; s += L) {
         const int4 r0 = __ldcs(d.s0 + s);
@@ -107,11 +108,15 @@ __global__ void __launch_bounds__(256) k_adj_sweep(Dev d, const float4 *__restri
         g[0] = make_float3(__int_as_float(r0.w), r1.x, r1.y);
         g[1] = make_float3(r1.z, r1.w, r2.x);
         g[2] = make_float3(r2.y, r2.z, r2.w);
-        // tet volume from the gradients; mu, lambda of the tet (the adjoint
-        // reads the per-tet arrays, which hold the current log E)
+        // tet volume from the gradients; mu, lambda of the vertex, or of the
+        // tet when materials differ around vertices (after vbd_set_log_young)
         const float V = __frcp_rn(6.0f * fabsf(dot(g[0], cross(g[1], g[2]))));
-        const int j = __ldcs(d.slot_tet + s);
-        const float Vmu = V * __ldg(d.tet_mu + j), Vlam = V * __ldg(d.tet_lam + j);
+        float2 mat = vm;
+        if (p.per_tet_mat) {
+            const int j = __ldcs(d.slot_tet + s);
+            mat = make_float2(__ldg(d.tet_mu + j), __ldg(d.tet_lam + j));
+        }
+        const float Vmu = V * mat.x, Vlam = V * mat.y;
         const float3 gi = make_float3(-(g[0].x + g[1].x + g[2].x), -(g[0].y + g[1].y + g[2].y),
                                       -(g[0].z + g[1].z + g[2].z));
         float3 e[3], lk[3];
