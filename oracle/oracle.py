@@ -49,13 +49,14 @@ class Params(C.Structure):
     _fields_ = [("gravity", C.c_double * 3), ("ground_on", C.c_int), ("ground_height", C.c_double),
                 ("ground_normal", C.c_double * 3), ("k_c", C.c_double), ("cheby_rho", C.c_double),
                 ("init_mode", C.c_int), ("det_eps", C.c_double), ("k_d", C.c_double),
-                ("mu_c", C.c_double), ("eps_v", C.c_double), ("line_search", C.c_int), ("jacobi", C.c_int)]
+                ("mu_c", C.c_double), ("eps_v", C.c_double), ("line_search", C.c_int), ("jacobi", C.c_int),
+                ("self_collision", C.c_int), ("dcd_radius", C.c_double)]
 
     @classmethod
     def make(cls, gravity=(0.0, 0.0, -9.8), ground_on=False, ground_height=0.0,
              ground_normal=(0.0, 0.0, 1.0), k_c=0.0, cheby_rho=0.0, init_mode=3,
              det_eps=1e-12, k_d=0.0, mu_c=0.0, eps_v=1e-3, line_search=False, jacobi=False,
-             **_ignored) -> "Params":
+             self_collision=False, dcd_radius=0.0, **_ignored) -> "Params":
         p = cls()
         p.gravity[:] = [float(g) for g in gravity]
         p.ground_on = int(bool(ground_on))
@@ -70,6 +71,8 @@ class Params(C.Structure):
         p.eps_v = float(eps_v)
         p.line_search = int(bool(line_search))
         p.jacobi = int(bool(jacobi))
+        p.self_collision = int(bool(self_collision))
+        p.dcd_radius = float(dcd_radius)
         return p
 
 
@@ -111,6 +114,12 @@ def lib():
                                        C.POINTER(Stats)]),
             "orc_cheby_omega": (C.c_double, [C.c_int, C.c_double, C.c_double]),
             "orc_local_energy": (C.c_double, [vp, C.POINTER(Params), C.c_double, C.c_int, _dp, _dp]),
+            "orc_model_n_tris": (C.c_int, [vp]),
+            "orc_model_tris": (None, [vp, _ip]),
+            "orc_closest_point_tri": (None, [_dp, _dp, _dp, _dp, _dp, _dp]),
+            "orc_dcd": (None, [vp, C.POINTER(Params), _dp]),
+            "orc_model_contacts": (None, [vp, _ip]),
+            "orc_self_contact": (C.c_int, [vp, C.POINTER(Params), C.c_int, _dp, _dp, _dp]),
             "orc_step": (C.c_int, [vp, C.POINTER(Params), _ip, C.c_int, C.c_double, C.c_int, _dp, _dp, _dp,
                                    C.POINTER(Stats)]),
             "orc_energy_G": (C.c_double, [vp, C.POINTER(Params), C.c_double, _dp, _dp]),
@@ -196,6 +205,13 @@ def ground_friction(p: "Params", h: float, xi, xti, lambda_n: float):
     f, H = np.zeros(3), np.zeros(9)
     lib().orc_ground_friction(C.byref(p), h, _d(xi, 3), _d(xti, 3), lambda_n, f, H)
     return f, H.reshape(3, 3)
+
+
+def closest_point_tri(p, a, b, c):
+    """(closest point, barycentric weights) of triangle abc to point p."""
+    q, w = np.zeros(3), np.zeros(3)
+    lib().orc_closest_point_tri(_d(p, 3), _d(a, 3), _d(b, 3), _d(c, 3), q, w)
+    return q, w
 
 
 def cheby_omega(n: int, rho: float, omega_prev: float) -> float:
@@ -300,6 +316,28 @@ class Model:
         lib().orc_step(self._h, C.byref(p), np.ascontiguousarray(colors, np.int32), int(n_colors), h,
                        int(iters), x.reshape(-1), v.reshape(-1), vprev.reshape(-1), C.byref(st))
         return st
+
+    def tris(self) -> np.ndarray:
+        """Boundary triangles (outward at rest), (F, 3)."""
+        t = np.zeros(3 * lib().orc_model_n_tris(self._h), np.int32)
+        lib().orc_model_tris(self._h, t)
+        return t.reshape(-1, 3)
+
+    def dcd(self, p: Params, x) -> np.ndarray:
+        """Runs the DCD at positions x and returns the per-vertex contact triangle (-1 = none)."""
+        lib().orc_dcd(self._h, C.byref(p), _d(x).reshape(-1))
+        return self.contacts()
+
+    def self_contact(self, p: Params, i, x):
+        """(force, Hessian, hit) of the self-contact terms acting on vertex i."""
+        f, H = np.zeros(3), np.zeros(9)
+        hit = lib().orc_self_contact(self._h, C.byref(p), int(i), _d(x).reshape(-1), f, H)
+        return f, H.reshape(3, 3), bool(hit)
+
+    def contacts(self) -> np.ndarray:
+        c = np.zeros(self.n, np.int32)
+        lib().orc_model_contacts(self._h, c)
+        return c
 
     def local_energy(self, p: Params, h, i, x, y) -> float:
         return lib().orc_local_energy(self._h, C.byref(p), h, int(i), _d(x).reshape(-1), _d(y).reshape(-1))

@@ -32,6 +32,18 @@
  *  - Block Jacobi: every vertex of an iteration solves against the previous
  *    iterate, and all moves are applied after the pass (x^new + copy-back
  *    of Algorithm 1 over all vertices at once); colours are not used.
+ *  - Self-collision (Sec. 3.5, vertex-triangle only, DCD only): at the start
+ *    of the step each boundary vertex is paired with the nearest boundary
+ *    triangle it lies behind (signed distance < 0 to the triangle's outward
+ *    plane) within dcd_radius, skipping triangles that touch the vertex or
+ *    one of its tet neighbours.  At every evaluation the closest point x_b
+ *    on that triangle, its barycentric weights w and the unit normal n are
+ *    recomputed from the current positions; with d = (x_b - x_a).n > 0 the
+ *    penalty k_c d^2 / 2 of Eq. 12 (n held constant) gives the vertex
+ *    +k_c d n and the triangle corners -k_c d w_k n, Hessians k_c n n^T and
+ *    k_c w_k^2 n n^T.  These elements may join two vertices of one colour,
+ *    so colour passes then use x^new and a copy-back (Algorithm 1): every
+ *    vertex of the pass solves against the positions at its start.
  *  - Ground friction (Eqs. 13-16): the ground is static, so the relative
  *    displacement is delta = x_i - x_i^t; u = its tangential part.  lambda
  *    is read as the normal-force magnitude k_c d >= 0 (as printed, the
@@ -58,6 +70,10 @@ struct orc_model {
     int *inc_off;        /* N+1: vertex -> incident tets */
     int *inc_tet;        /* 4T */
     int *inc_loc;        /* 4T: local index (0..3) of the vertex in that tet */
+    int n_tris;          /* boundary triangles, oriented outward at rest */
+    int *tris;           /* 3 * n_tris */
+    unsigned char *on_surface; /* N */
+    int *contact;        /* N: triangle hit by the vertex (DCD at x^t), or -1 */
 };
 
 /* ------------------------------------------------------------------ */
@@ -236,6 +252,13 @@ static int cmp_int(const void *a, const void *b) {
     return (x > y) - (x < y);
 }
 
+static int cmp_face(const void *pa, const void *pb) {
+    const int *x = (const int *)pa, *y = (const int *)pb;
+    for (int k = 0; k < 3; ++k)
+        if (x[k] != y[k]) return (x[k] > y[k]) - (x[k] < y[k]);
+    return 0;
+}
+
 static int *g_deg_for_sort;
 static int cmp_visit(const void *a, const void *b) {
     int i = *(const int *)a, j = *(const int *)b;
@@ -367,6 +390,52 @@ orc_model *orc_model_new(int n, int t, const double *rest, const int *tets,
             m->inc_loc[s] = a;
         }
     free(fill);
+    /* boundary triangles: tet faces that occur once, oriented away from the
+     * tet's fourth vertex */
+    {
+        int nf = 4 * t;
+        int *faces = (int *)malloc(sizeof(int) * 5 * (size_t)nf + 1);  /* sorted triple, tet, local face */
+        for (int j = 0; j < t; ++j)
+            for (int f = 0; f < 4; ++f) {
+                int q = 0, v[3];
+                for (int k = 0; k < 4; ++k)
+                    if (k != f) v[q++] = tets[4 * j + k];
+                /* sort the triple */
+                for (int x0 = 0; x0 < 3; ++x0)
+                    for (int x1 = x0 + 1; x1 < 3; ++x1)
+                        if (v[x1] < v[x0]) { int tmp = v[x0]; v[x0] = v[x1]; v[x1] = tmp; }
+                int *r = faces + 5 * (4 * (size_t)j + f);
+                r[0] = v[0]; r[1] = v[1]; r[2] = v[2]; r[3] = j; r[4] = f;
+            }
+        qsort(faces, (size_t)nf, 5 * sizeof(int), cmp_face);
+        m->tris = (int *)malloc(sizeof(int) * 3 * (size_t)nf + 1);
+        m->on_surface = (unsigned char *)calloc((size_t)n + 1, 1);
+        m->n_tris = 0;
+        for (int k = 0; k < nf; ++k) {
+            const int *r = faces + 5 * (size_t)k;
+            int dup = (k > 0 && cmp_face(r, r - 5) == 0) || (k + 1 < nf && cmp_face(r, r + 5) == 0);
+            if (dup) continue;
+            int j = r[3], f = r[4];
+            int v[3], q = 0;
+            for (int kk = 0; kk < 4; ++kk)
+                if (kk != f) v[q++] = tets[4 * j + kk];
+            int opp = tets[4 * j + f];
+            double e0[3], e1[3], nrm[3], to[3];
+            for (int c = 0; c < 3; ++c) {
+                e0[c] = rest[3 * v[1] + c] - rest[3 * v[0] + c];
+                e1[c] = rest[3 * v[2] + c] - rest[3 * v[0] + c];
+                to[c] = rest[3 * opp + c] - rest[3 * v[0] + c];
+            }
+            cross3(e0, e1, nrm);
+            if (dot3(nrm, to) > 0.0) { int tmp = v[1]; v[1] = v[2]; v[2] = tmp; }
+            int *o = m->tris + 3 * (size_t)m->n_tris++;
+            o[0] = v[0]; o[1] = v[1]; o[2] = v[2];
+            m->on_surface[v[0]] = m->on_surface[v[1]] = m->on_surface[v[2]] = 1;
+        }
+        free(faces);
+        m->contact = (int *)malloc(sizeof(int) * (size_t)n + 1);
+        for (int i = 0; i < n; ++i) m->contact[i] = -1;
+    }
     return m;
 }
 
@@ -374,7 +443,120 @@ void orc_model_free(orc_model *m) {
     if (!m) return;
     free(m->tets); free(m->B); free(m->V); free(m->mu); free(m->lam); free(m->poisson);
     free(m->mass); free(m->pinned); free(m->inc_off); free(m->inc_tet); free(m->inc_loc);
+    free(m->tris); free(m->on_surface); free(m->contact);
     free(m);
+}
+
+int orc_model_n_tris(const orc_model *m) { return m->n_tris; }
+
+void orc_model_tris(const orc_model *m, int *tris) {
+    memcpy(tris, m->tris, sizeof(int) * 3 * (size_t)m->n_tris);
+}
+
+void orc_model_contacts(const orc_model *m, int *contact) {
+    memcpy(contact, m->contact, sizeof(int) * (size_t)m->n_verts);
+}
+
+/* Closest point q of triangle (a, b, c) to p, with barycentric weights w
+ * (q = w0 a + w1 b + w2 c): the projection onto the plane if it falls
+ * inside, otherwise the nearest of the closest points on the three edges. */
+void orc_closest_point_tri(const double p[3], const double a[3], const double b[3], const double c[3],
+                           double q[3], double w[3]) {
+    double e0[3], e1[3], r[3];
+    for (int k = 0; k < 3; ++k) {
+        e0[k] = b[k] - a[k];
+        e1[k] = c[k] - a[k];
+        r[k] = p[k] - a[k];
+    }
+    double d00 = dot3(e0, e0), d01 = dot3(e0, e1), d11 = dot3(e1, e1);
+    double d20 = dot3(r, e0), d21 = dot3(r, e1);
+    double den = d00 * d11 - d01 * d01;
+    double wb = (d11 * d20 - d01 * d21) / den;
+    double wc = (d00 * d21 - d01 * d20) / den;
+    double wa = 1.0 - wb - wc;
+    if (wa >= 0.0 && wb >= 0.0 && wc >= 0.0) {
+        w[0] = wa; w[1] = wb; w[2] = wc;
+    } else {
+        const double *P[3] = {a, b, c};
+        double best = -1.0;
+        for (int e = 0; e < 3; ++e) {
+            const double *p0 = P[e], *p1 = P[(e + 1) % 3];
+            double dd[3], pp[3];
+            for (int k = 0; k < 3; ++k) { dd[k] = p1[k] - p0[k]; pp[k] = p[k] - p0[k]; }
+            double tt = dot3(pp, dd) / dot3(dd, dd);
+            if (tt < 0.0) tt = 0.0;
+            if (tt > 1.0) tt = 1.0;
+            double dist2 = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                double z = p0[k] + tt * dd[k] - p[k];
+                dist2 += z * z;
+            }
+            if (best < 0.0 || dist2 < best) {
+                best = dist2;
+                w[0] = w[1] = w[2] = 0.0;
+                w[e] = 1.0 - tt;
+                w[(e + 1) % 3] = tt;
+            }
+        }
+    }
+    for (int k = 0; k < 3; ++k) q[k] = w[0] * a[k] + w[1] * b[k] + w[2] * c[k];
+}
+
+/* unit normal of boundary triangle T at positions x */
+static void tri_normal(const orc_model *m, int T, const double *x, double n[3]) {
+    const int *v = m->tris + 3 * (size_t)T;
+    double e0[3], e1[3];
+    for (int k = 0; k < 3; ++k) {
+        e0[k] = x[3 * v[1] + k] - x[3 * v[0] + k];
+        e1[k] = x[3 * v[2] + k] - x[3 * v[0] + k];
+    }
+    cross3(e0, e1, n);
+    double l = sqrt(dot3(n, n));
+    for (int k = 0; k < 3; ++k) n[k] /= l;
+}
+
+/* penetration depth of vertex a into its contact triangle at positions x:
+ * d = (x_b - x_a).n with x_b the closest point; also returns n and w */
+static double contact_depth(const orc_model *m, int a, const double *x, double n[3], double w[3]) {
+    const int T = m->contact[a];
+    const int *v = m->tris + 3 * (size_t)T;
+    double q[3];
+    orc_closest_point_tri(x + 3 * a, x + 3 * v[0], x + 3 * v[1], x + 3 * v[2], q, w);
+    tri_normal(m, T, x, n);
+    return (q[0] - x[3 * a]) * n[0] + (q[1] - x[3 * a + 1]) * n[1] + (q[2] - x[3 * a + 2]) * n[2];
+}
+
+/* DCD at positions x (the step start): the nearest boundary triangle within
+ * dcd_radius, skipping triangles that touch the vertex or a vertex sharing a
+ * tet with it (ties: lower triangle index); the vertex collides with it if
+ * it lies behind that triangle's outward plane. */
+void orc_dcd(orc_model *m, const orc_params *p, const double *x) {
+    int n = m->n_verts;
+    int *stamp = (int *)calloc((size_t)n + 1, sizeof(int));
+    for (int a = 0; a < n; ++a) {
+        m->contact[a] = -1;
+        if (!m->on_surface[a]) continue;
+        for (int s = m->inc_off[a]; s < m->inc_off[a + 1]; ++s)
+            for (int k = 0; k < 4; ++k) stamp[m->tets[4 * (size_t)m->inc_tet[s] + k]] = a + 1;
+        double best = 0.0, best_side = 0.0;
+        int best_T = -1;
+        for (int T = 0; T < m->n_tris; ++T) {
+            const int *v = m->tris + 3 * (size_t)T;
+            if (stamp[v[0]] == a + 1 || stamp[v[1]] == a + 1 || stamp[v[2]] == a + 1) continue;
+            double q[3], w[3], nn[3];
+            orc_closest_point_tri(x + 3 * a, x + 3 * v[0], x + 3 * v[1], x + 3 * v[2], q, w);
+            tri_normal(m, T, x, nn);
+            double dv[3] = {x[3 * a] - q[0], x[3 * a + 1] - q[1], x[3 * a + 2] - q[2]};
+            double dist = sqrt(dot3(dv, dv));
+            if (dist <= p->dcd_radius && (best_T < 0 || dist < best)) {
+                best = dist;
+                best_T = T;
+                best_side = dot3(dv, nn);
+            }
+        }
+        if (best_T >= 0 && best_side < 0.0) m->contact[a] = best_T;
+    }
+    free(stamp);
 }
 
 int orc_model_n_verts(const orc_model *m) { return m->n_verts; }
@@ -459,7 +641,51 @@ double orc_local_energy(const orc_model *m, const orc_params *p, double h, int i
         double d = p->ground_height - dot3(x + 3 * i, n) / nn;
         if (d > 0.0) G += 0.5 * p->k_c * d * d;
     }
+    if (p->self_collision)
+        for (int a = 0; a < m->n_verts; ++a) {
+            if (m->contact[a] < 0) continue;
+            const int *v = m->tris + 3 * (size_t)m->contact[a];
+            if (a != i && v[0] != i && v[1] != i && v[2] != i) continue;
+            double nn[3], w[3];
+            double d = contact_depth(m, a, x, nn, w);
+            if (d > 0.0) G += 0.5 * p->k_c * d * d;
+        }
     return G;
+}
+
+/* Vertex-triangle penalty (Eq. 12) with the step's DCD pairs acting on
+ * vertex i, as the colliding vertex and as a corner of a hit triangle: adds
+ * forces to f and Hessians to H; returns 1 if any pair is penetrating. */
+int orc_self_contact(const orc_model *m, const orc_params *p, int i, const double *x,
+                     double f[3], double H[9]) {
+    int hit = 0;
+    double nn[3], w[3];
+    if (m->contact[i] >= 0) {
+        double d = contact_depth(m, i, x, nn, w);
+        if (d > 0.0) {
+            hit = 1;
+            for (int r = 0; r < 3; ++r) {
+                f[r] += p->k_c * d * nn[r];
+                for (int c = 0; c < 3; ++c) H[r * 3 + c] += p->k_c * nn[r] * nn[c];
+            }
+        }
+    }
+    for (int a = 0; a < m->n_verts; ++a) {
+        if (m->contact[a] < 0) continue;
+        const int *v = m->tris + 3 * (size_t)m->contact[a];
+        int corner = (v[0] == i) ? 0 : (v[1] == i) ? 1 : (v[2] == i) ? 2 : -1;
+        if (corner < 0) continue;
+        double d = contact_depth(m, a, x, nn, w);
+        if (d > 0.0) {
+            hit = 1;
+            double wk = w[corner];
+            for (int r = 0; r < 3; ++r) {
+                f[r] -= p->k_c * d * wk * nn[r];
+                for (int c = 0; c < 3; ++c) H[r * 3 + c] += p->k_c * wk * wk * nn[r] * nn[c];
+            }
+        }
+    }
+    return hit;
 }
 
 /* Ground friction of Eqs. 13-16 for one vertex in contact: adds the force
@@ -524,6 +750,7 @@ int orc_vertex_solve(const orc_model *m, const orc_params *p, double h, int i,
             if (p->mu_c > 0.0) orc_ground_friction(p, h, x + 3 * i, xt + 3 * i, p->k_c * d, f, H);
         }
     }
+    if (p->self_collision && orc_self_contact(m, p, i, x, f, H)) *in_contact = 1;
     double det = det3(H);
     double tr3 = (H[0] + H[4] + H[8]) / 3.0;
     if (fabs(det) <= p->det_eps * fabs(tr3 * tr3 * tr3)) {
@@ -558,19 +785,28 @@ int orc_vertex_solve(const orc_model *m, const orc_params *p, double h, int i,
 void orc_sweep_color(const orc_model *m, const orc_params *p, double h, const int *colors,
                      int color, double *x, const double *y, const double *xt,
                      unsigned char *colliding, orc_stats *st) {
+    /* with self-contacts two vertices of one colour may be coupled: solve all
+     * against the pass-start positions (x^new), then copy back */
+    size_t n3 = 3 * (size_t)m->n_verts;
+    double *xs = x;
+    if (p->self_collision) {
+        xs = (double *)malloc(sizeof(double) * n3 + 1);
+        memcpy(xs, x, sizeof(double) * n3);
+    }
     for (int i = 0; i < m->n_verts; ++i) {
         if (colors[i] != color || m->pinned[i]) continue;
         double dx[3];
         int contact;
-        int skipped = orc_vertex_solve(m, p, h, i, x, y, xt, dx, &contact);
+        int skipped = orc_vertex_solve(m, p, h, i, xs, y, xt, dx, &contact);
         if (st) {
             st->vertex_solves++;
             st->det_skips += skipped;
             st->contacts += contact;
         }
         if (contact && colliding) colliding[i] = 1;
-        for (int r = 0; r < 3; ++r) x[3 * i + r] += dx[r];
+        for (int r = 0; r < 3; ++r) x[3 * i + r] = xs[3 * i + r] + dx[r];
     }
+    if (xs != x) free(xs);
 }
 
 /* Eq. 19: omega_1 = 1, omega_2 = 2/(2 - rho^2), omega_n = 4/(4 - rho^2 omega_{n-1}) */
@@ -591,6 +827,7 @@ int orc_step(const orc_model *m, const orc_params *p, const int *colors, int n_c
     double *p2 = (double *)malloc(sizeof(double) * n3 + 1);
     unsigned char *coll = (unsigned char *)calloc((size_t)m->n_verts + 1, 1);
     memcpy(xt, x, sizeof(double) * n3);
+    if (p->self_collision) orc_dcd((orc_model *)m, p, xt);  /* initial DCD using x^t */
     orc_inertia_target(m, p, h, xt, v, y);            /* Eq. 3 */
     orc_initial_guess(m, p, h, xt, v, vprev, x);      /* Sec. 3.7 */
     memcpy(p1, x, sizeof(double) * n3);               /* x^(0) */
@@ -667,6 +904,13 @@ double orc_energy_G(const orc_model *m, const orc_params *p, double h,
         gather_tet(m, j, x, xs);
         G += orc_tet_energy(xs, m->B + 9 * (size_t)j, m->V[j], m->mu[j], m->lam[j]);
     }
+    if (p->self_collision)
+        for (int a = 0; a < m->n_verts; ++a)
+            if (m->contact[a] >= 0) {
+                double nn[3], w[3];
+                double d = contact_depth(m, a, x, nn, w);
+                if (d > 0.0) G += 0.5 * p->k_c * d * d;
+            }
     return G;
 }
 

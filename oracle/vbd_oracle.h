@@ -41,6 +41,8 @@ typedef struct {
     double eps_v;           /* friction velocity threshold of Eq. 15 [m/s] */
     int line_search;        /* 1: backtracking on G_i after each local step (Sec. 3.2) */
     int jacobi;             /* 1: block Jacobi: all vertices from the previous iterate */
+    int self_collision;     /* 1: vertex-triangle penalty contacts from a DCD at x^t (Sec. 3.5) */
+    double dcd_radius;      /* DCD search radius */
 } orc_params;
 
 typedef struct {
@@ -78,6 +80,16 @@ int orc_model_n_tets(const orc_model *m);
 void orc_model_mass(const orc_model *m, double *mass);
 void orc_model_tet_data(const orc_model *m, double *B, double *V, double *mu, double *lam);
 void orc_model_set_log_young(orc_model *m, const double *log_young);
+
+/* ---- self-collision (Sec. 3.5: vertex-triangle, DCD at the step start) -- */
+int orc_model_n_tris(const orc_model *m);
+void orc_model_tris(const orc_model *m, int *tris);
+void orc_closest_point_tri(const double p[3], const double a[3], const double b[3], const double c[3],
+                           double q[3], double w[3]);
+void orc_dcd(orc_model *m, const orc_params *p, const double *x);
+void orc_model_contacts(const orc_model *m, int *contact);
+int orc_self_contact(const orc_model *m, const orc_params *p, int i, const double *x,
+                     double f[3], double H[9]);
 
 /* ---- one time step (Algorithm 1) --------------------------------------- */
 void orc_inertia_target(const orc_model *m, const orc_params *p, double h,

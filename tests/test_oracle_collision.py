@@ -1,0 +1,150 @@
+"""Pins of the oracle's self-collision (Sec. 3.5: vertex-triangle penalty of
+Eq. 12 with pairs from a DCD at the step start).  CPU only."""
+import numpy as np
+import pytest
+
+from paper_2403_06321_b300 import synth
+
+H = 1.0 / 60.0
+
+
+def test_closest_point_on_triangle_beats_dense_sampling(orc):
+    rng = np.random.default_rng(101)
+    u = np.linspace(0, 1, 161)
+    U, V = np.meshgrid(u, u)
+    keep = U + V <= 1
+    bary = np.stack([1 - U[keep] - V[keep], U[keep], V[keep]], axis=1)
+    for _ in range(40):
+        a, b, c = rng.normal(size=(3, 3))
+        p = rng.normal(size=3) * 1.5
+        q, w = orc.closest_point_tri(p, a, b, c)
+        assert np.all(w >= -1e-15) and abs(w.sum() - 1) < 1e-12
+        assert np.allclose(q, w[0] * a + w[1] * b + w[2] * c)
+        samples = bary @ np.stack([a, b, c])
+        dmin = np.linalg.norm(samples - p, axis=1).min()
+        assert np.linalg.norm(q - p) <= dmin + 1e-12
+
+
+def test_boundary_triangles_of_a_box(orc):
+    """A Kuhn box has 2 triangles per boundary square, normals pointing out,
+    total area = box surface area."""
+    nx, ny, nz, e = 3, 2, 4, 0.1
+    m = synth.beam(nx, ny, nz, edge=e, pin_face=None)
+    model = orc.Model.from_mesh(m)
+    tris = model.tris()
+    assert len(tris) == 2 * 2 * (nx * ny + ny * nz + nz * nx)
+    X = m.rest
+    centre = X.mean(axis=0)
+    area = 0.0
+    for t in tris:
+        n = np.cross(X[t[1]] - X[t[0]], X[t[2]] - X[t[0]])
+        area += 0.5 * np.linalg.norm(n)
+        assert n @ (X[t].mean(axis=0) - centre) > 0
+    assert area == pytest.approx(2 * e * e * (nx * ny + ny * nz + nz * nx), rel=1e-12)
+
+
+def _two_blocks(gap, seed=102):
+    """A free 2x2x1 block above (or sunk into) a pinned 3x3x1 block."""
+    lower = synth.beam(3, 3, 1, edge=0.1, E=1e5, nu=0.4, pin_face="z-", jitter_frac=0.05, seed=seed)
+    upper = synth.beam(2, 2, 1, edge=0.1, E=1e5, nu=0.4, pin_face=None, jitter_frac=0.05, seed=seed + 1,
+                       origin=(0.05, 0.05, 0.1 + gap))
+    cat, voff, _ = synth.concat([lower, upper])
+    cat.grid_ijk = None
+    return cat, voff
+
+
+def test_dcd_pairs_penetrating_vertices_only(orc):
+    cat, voff = _two_blocks(-0.01)  # upper block sunk 1 cm into the lower one
+    model = orc.Model.from_mesh(cat)
+    p = orc.Params.make(self_collision=True, dcd_radius=0.05, k_c=1e5)
+    contact = model.dcd(p, cat.rest)
+    tris = model.tris()
+    low = np.arange(voff[1])
+    hit = np.nonzero(contact >= 0)[0]
+    assert hit.size > 0
+    for a in hit:
+        t = tris[contact[a]]
+        # upper-block vertices hit lower-block triangles and vice versa, never their own body
+        assert (a in low) != (t[0] in low)
+    sunk = [a for a in range(voff[1], voff[2]) if cat.rest[a, 2] < 0.1 - 1e-3]
+    assert set(sunk) <= set(hit.tolist())
+    # a single body at rest, and two separated bodies, have no pairs
+    single = synth.beam(4, 3, 2, jitter_frac=0.1, seed=103, pin_face=None)
+    assert (orc.Model.from_mesh(single).dcd(p, single.rest) < 0).all()
+    cat2, _ = _two_blocks(0.02)
+    assert (orc.Model.from_mesh(cat2).dcd(p, cat2.rest) < 0).all()
+
+
+def test_contact_forces_are_the_gradient_and_balance(orc):
+    """For a projection inside its triangle, d is the distance from the
+    vertex to the triangle's plane.  Moving the vertex along n changes d by
+    minus the move; moving corner k along n lifts the plane under the
+    projection by w_k times the move; in-plane moves leave d alone.  So the
+    forces k_c d n and -k_c d w_k n are exactly -dE/dx of the total contact
+    energy sum k_c d^2 / 2, and they sum to zero."""
+    lower = synth.beam(3, 3, 1, edge=0.1, E=1e5, nu=0.4, pin_face="z-", jitter_frac=0.02, seed=105)
+    upper = synth.beam(2, 2, 1, edge=0.1, E=1e5, nu=0.4, pin_face=None, jitter_frac=0.02, seed=106,
+                       origin=(0.03, 0.02, 0.09))
+    cat, voff, _ = synth.concat([lower, upper])
+    model = orc.Model.from_mesh(cat)
+    p = orc.Params.make(self_collision=True, dcd_radius=0.05, k_c=1e5)
+    contact = model.dcd(p, cat.rest)
+    tris = model.tris()
+    pairs = np.nonzero(contact >= 0)[0]
+    assert pairs.size >= 4
+    x = cat.rest
+    for a in pairs:
+        _, w = orc.closest_point_tri(x[a], *x[tris[contact[a]]])
+        assert w.min() > 1e-3  # interior projections only
+    involved = sorted(set(pairs.tolist()) | set(tris[contact[pairs]].ravel().tolist()))
+    y = x.copy()  # no inertia gradient
+    el = model.elastic_grad(x).reshape(-1, 3)
+    total = np.zeros(3)
+    for v in involved:
+        f, _, _ = model.self_contact(p, v, x)
+        e = 1e-7
+        g = np.zeros(3)
+        for r in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[v, r] += e
+            xm[v, r] -= e
+            g[r] = (model.energy_G(p, H, xp, y) - model.energy_G(p, H, xm, y)) / (2 * e)
+        g -= el[v]  # leaves the contact energy's gradient
+        if model.free[v]:
+            assert np.allclose(f, -g, rtol=1e-5, atol=1e-5 * np.abs(f).max())
+        total += f
+    assert np.abs(total).max() <= 1e-9 * max(1.0, np.abs(total).max())
+
+    # Gauss-Newton Hessian of k_c d^2 / 2 is k_c grad d grad d^T = f f^T / (k_c d^2)
+    # for a vertex in one pair; d is recomputed here from the plane geometry.
+    n_pairs = {v: 0 for v in involved}
+    depth = {}
+    for a in pairs:
+        t = tris[contact[a]]
+        nrm = np.cross(x[t[1]] - x[t[0]], x[t[2]] - x[t[0]])
+        nrm /= np.linalg.norm(nrm)
+        d = -(x[a] - x[t[0]]) @ nrm
+        for v in [a, *t]:
+            n_pairs[v] += 1
+            depth[v] = d
+    single = [v for v in involved if n_pairs[v] == 1 and depth[v] > 0]
+    assert len(single) >= 3
+    for v in single:
+        f, Hc, _ = model.self_contact(p, v, x)
+        assert np.allclose(Hc, np.outer(f, f) / (p.k_c * depth[v] ** 2), rtol=1e-9, atol=1e-9 * np.abs(Hc).max())
+
+
+@pytest.mark.parametrize("collide", [True, False])
+def test_block_dropped_on_block(orc, collide):
+    cat, voff = _two_blocks(0.002)
+    model = orc.Model.from_mesh(cat)
+    colors, nc = orc.color_greedy(cat.n_verts, cat.tets)
+    p = orc.Params.make(gravity=(0, 0, -9.8), self_collision=collide, dcd_radius=0.05, k_c=1e5)
+    v0 = np.zeros_like(cat.rest)
+    v0[voff[1]:, 2] = -1.0
+    x, _, _ = orc.run(model, p, colors, nc, H, 40, 20, cat.rest, v0)
+    zmin_upper = x[voff[1]:, 2].min()
+    if collide:
+        assert zmin_upper > 0.1 - 0.01  # rests on the lower block (penalty depth ~ m g / k_c)
+    else:
+        assert zmin_upper < 0.0  # falls through

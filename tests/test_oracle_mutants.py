@@ -38,6 +38,12 @@ MUTANTS = [
      "test_oracle_solver.py"),
     ("friction_pushes_along_motion", "f[r] -= c * ut[r];", "f[r] += c * ut[r];", "test_oracle_friction.py"),
     ("line_search_accepts_increase", "<= G0) ok = 1;", ">= G0) ok = 1;", "test_oracle_variants.py"),
+    ("self_contact_corner_force_sign", "f[r] -= p->k_c * d * wk * nn[r];", "f[r] += p->k_c * d * wk * nn[r];",
+     "test_oracle_collision.py"),
+    ("self_contact_corner_drops_weight", "double wk = w[corner];", "double wk = 1.0;", "test_oracle_collision.py"),
+    ("self_contact_corner_hessian_linear_weight", "p->k_c * wk * wk * nn[r] * nn[c]", "p->k_c * wk * nn[r] * nn[c]",
+     "test_oracle_collision.py"),
+    ("closest_point_unclamped_edge", "if (tt > 1.0) tt = 1.0;", "", "test_oracle_collision.py"),
 ]
 
 
@@ -58,7 +64,7 @@ def _run_pins(src_text, pin_file):
 
 def test_identity_copy_passes():
     src = open(SRC).read()
-    for pin in ("test_oracle_element.py", "test_oracle_solver.py"):
+    for pin in ("test_oracle_element.py", "test_oracle_solver.py", "test_oracle_collision.py"):
         assert _run_pins(src, pin) == 0, pin
 
 
