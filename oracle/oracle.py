@@ -117,6 +117,7 @@ def lib():
             "orc_model_n_tris": (C.c_int, [vp]),
             "orc_model_tris": (None, [vp, _ip]),
             "orc_closest_point_tri": (None, [_dp, _dp, _dp, _dp, _dp, _dp]),
+            "orc_point_in_tet": (C.c_int, [_dp, _ip, _dp]),
             "orc_dcd": (None, [vp, C.POINTER(Params), _dp]),
             "orc_model_contacts": (None, [vp, _ip]),
             "orc_self_contact": (C.c_int, [vp, C.POINTER(Params), C.c_int, _dp, _dp, _dp]),
@@ -212,6 +213,11 @@ def closest_point_tri(p, a, b, c):
     q, w = np.zeros(3), np.zeros(3)
     lib().orc_closest_point_tri(_d(p, 3), _d(a, 3), _d(b, 3), _d(c, 3), q, w)
     return q, w
+
+
+def point_in_tet(x, tet, q) -> bool:
+    """Whether q lies in the closed tet x[tet] (barycentric coordinates >= 0)."""
+    return bool(lib().orc_point_in_tet(_d(x).reshape(-1), np.ascontiguousarray(tet, np.int32), _d(q, 3)))
 
 
 def cheby_omega(n: int, rho: float, omega_prev: float) -> float:

@@ -33,10 +33,10 @@
  *    iterate, and all moves are applied after the pass (x^new + copy-back
  *    of Algorithm 1 over all vertices at once); colours are not used.
  *  - Self-collision (Sec. 3.5, vertex-triangle only, DCD only): at the start
- *    of the step each boundary vertex is paired with the nearest boundary
- *    triangle it lies behind (signed distance < 0 to the triangle's outward
- *    plane) within dcd_radius, skipping triangles that touch the vertex or
- *    one of its tet neighbours.  At every evaluation the closest point x_b
+ *    of the step a boundary vertex that has already penetrated, i.e. lies
+ *    inside (or on) a tet it does not belong to, is paired with the nearest
+ *    boundary triangle within dcd_radius, skipping triangles that touch the
+ *    vertex or one of its tet neighbours.  At every evaluation the closest point x_b
  *    on that triangle, its barycentric weights w and the unit normal n are
  *    recomputed from the current positions; with d = (x_b - x_a).n > 0 the
  *    penalty k_c d^2 / 2 of Eq. 12 (n held constant) gives the vertex
@@ -526,35 +526,63 @@ static double contact_depth(const orc_model *m, int a, const double *x, double n
     return (q[0] - x[3 * a]) * n[0] + (q[1] - x[3 * a + 1]) * n[1] + (q[2] - x[3 * a + 2]) * n[2];
 }
 
-/* DCD at positions x (the step start): the nearest boundary triangle within
- * dcd_radius, skipping triangles that touch the vertex or a vertex sharing a
- * tet with it (ties: lower triangle index); the vertex collides with it if
- * it lies behind that triangle's outward plane. */
+/* 1 if point q lies in the closed tet (x[t[0]], .., x[t[3]]): its barycentric
+ * coordinates, from the edge matrix E = [x1 - x0, x2 - x0, x3 - x0] by
+ * Cramer's rule, are all >= 0.  0 for a flat tet. */
+int orc_point_in_tet(const double *x, const int *t, const double q[3]) {
+    double E[9], r[3];
+    for (int k = 0; k < 3; ++k) {
+        for (int c = 0; c < 3; ++c) E[3 * k + c] = x[3 * t[c + 1] + k] - x[3 * t[0] + k];
+        r[k] = q[k] - x[3 * t[0] + k];
+    }
+    double D = det3(E);
+    if (D == 0.0) return 0;
+    double lam_sum = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        double Ec[9];
+        memcpy(Ec, E, sizeof(Ec));
+        for (int k = 0; k < 3; ++k) Ec[3 * k + c] = r[k];
+        double l = det3(Ec) / D;
+        if (l < 0.0) return 0;
+        lam_sum += l;
+    }
+    return 1.0 - lam_sum >= 0.0;
+}
+
+/* DCD at positions x (the step start).  A boundary vertex has penetrated
+ * when it lies in a tet it is not a vertex of; it is then paired with the
+ * nearest boundary triangle within dcd_radius, skipping triangles that touch
+ * the vertex or a vertex sharing a tet with it (ties: lower triangle index). */
 void orc_dcd(orc_model *m, const orc_params *p, const double *x) {
     int n = m->n_verts;
     int *stamp = (int *)calloc((size_t)n + 1, sizeof(int));
     for (int a = 0; a < n; ++a) {
         m->contact[a] = -1;
         if (!m->on_surface[a]) continue;
+        int inside = 0;
+        for (int j = 0; j < m->n_tets && !inside; ++j) {
+            const int *t = m->tets + 4 * (size_t)j;
+            if (t[0] == a || t[1] == a || t[2] == a || t[3] == a) continue;
+            inside = orc_point_in_tet(x, t, x + 3 * a);
+        }
+        if (!inside) continue;
         for (int s = m->inc_off[a]; s < m->inc_off[a + 1]; ++s)
             for (int k = 0; k < 4; ++k) stamp[m->tets[4 * (size_t)m->inc_tet[s] + k]] = a + 1;
-        double best = 0.0, best_side = 0.0;
+        double best = 0.0;
         int best_T = -1;
         for (int T = 0; T < m->n_tris; ++T) {
             const int *v = m->tris + 3 * (size_t)T;
             if (stamp[v[0]] == a + 1 || stamp[v[1]] == a + 1 || stamp[v[2]] == a + 1) continue;
-            double q[3], w[3], nn[3];
+            double q[3], w[3];
             orc_closest_point_tri(x + 3 * a, x + 3 * v[0], x + 3 * v[1], x + 3 * v[2], q, w);
-            tri_normal(m, T, x, nn);
             double dv[3] = {x[3 * a] - q[0], x[3 * a + 1] - q[1], x[3 * a + 2] - q[2]};
             double dist = sqrt(dot3(dv, dv));
             if (dist <= p->dcd_radius && (best_T < 0 || dist < best)) {
                 best = dist;
                 best_T = T;
-                best_side = dot3(dv, nn);
             }
         }
-        if (best_T >= 0 && best_side < 0.0) m->contact[a] = best_T;
+        m->contact[a] = best_T;
     }
     free(stamp);
 }

@@ -86,6 +86,7 @@ int orc_model_n_tris(const orc_model *m);
 void orc_model_tris(const orc_model *m, int *tris);
 void orc_closest_point_tri(const double p[3], const double a[3], const double b[3], const double c[3],
                            double q[3], double w[3]);
+int orc_point_in_tet(const double *x, const int *tet, const double q[3]);
 void orc_dcd(orc_model *m, const orc_params *p, const double *x);
 void orc_model_contacts(const orc_model *m, int *contact);
 int orc_self_contact(const orc_model *m, const orc_params *p, int i, const double *x,

@@ -53,21 +53,58 @@ def _two_blocks(gap, seed=102):
     return cat, voff
 
 
-def test_dcd_pairs_penetrating_vertices_only(orc):
-    cat, voff = _two_blocks(-0.01)  # upper block sunk 1 cm into the lower one
+def test_point_in_tet_is_barycentric_membership(orc):
+    """Against sampled barycentric combinations: points with all weights >= 0
+    are inside, points with one weight < 0 are outside."""
+    rng = np.random.default_rng(104)
+    for _ in range(20):
+        x = rng.normal(size=(4, 3))
+        t = np.arange(4)
+        for _ in range(20):
+            lam = rng.dirichlet(np.ones(4))
+            assert orc.point_in_tet(x, t, lam @ x)
+            lam[rng.integers(4)] -= 1.0 + rng.random()
+            lam /= lam.sum() if abs(lam.sum()) > 1e-3 else 1.0
+            if lam.min() < 0 and abs(lam.sum() - 1) < 1e-9:
+                assert not orc.point_in_tet(x, t, lam @ x)
+
+
+def test_dcd_pairs_exactly_the_vertices_inside_the_other_box(orc):
+    """Two unjittered boxes, the free 2x2x1 one sunk 1 cm into the pinned
+    3x3x1 one.  The paired vertices are those strictly inside the other box
+    (a plain box test), each with a triangle of the face it is 1 cm behind;
+    lower-box vertices next to the upper box's rim, which lie behind the
+    plane of its bottom but outside it, stay unpaired."""
+    lower = synth.beam(3, 3, 1, edge=0.1, pin_face="z-")
+    upper = synth.beam(2, 2, 1, edge=0.1, pin_face=None, origin=(0.03, 0.04, 0.09))
+    cat, voff, _ = synth.concat([lower, upper])
     model = orc.Model.from_mesh(cat)
     p = orc.Params.make(self_collision=True, dcd_radius=0.05, k_c=1e5)
-    contact = model.dcd(p, cat.rest)
+    x = cat.rest
+    contact = model.dcd(p, x)
     tris = model.tris()
-    low = np.arange(voff[1])
-    hit = np.nonzero(contact >= 0)[0]
-    assert hit.size > 0
-    for a in hit:
+    lo, hi = np.array([0.0, 0.0, 0.0]), np.array([0.3, 0.3, 0.1])
+    ulo, uhi = np.array([0.03, 0.04, 0.09]), np.array([0.23, 0.24, 0.19])
+    inside_lower = np.all((x > lo) & (x < hi), axis=1)
+    inside_upper = np.all((x > ulo) & (x < uhi), axis=1)
+    expect = np.zeros(cat.n_verts, bool)
+    expect[voff[1]:] = inside_lower[voff[1]:]
+    expect[:voff[1]] = inside_upper[:voff[1]]
+    assert expect.sum() == 9 + 4
+    assert np.array_equal(contact >= 0, expect)
+    for a in np.nonzero(expect)[0]:
         t = tris[contact[a]]
-        # upper-block vertices hit lower-block triangles and vice versa, never their own body
-        assert (a in low) != (t[0] in low)
-    sunk = [a for a in range(voff[1], voff[2]) if cat.rest[a, 2] < 0.1 - 1e-3]
-    assert set(sunk) <= set(hit.tolist())
+        n = np.cross(x[t[1]] - x[t[0]], x[t[2]] - x[t[0]])
+        n /= np.linalg.norm(n)
+        if a >= voff[1]:  # under the lower box's top face (normal +z)
+            assert np.allclose(x[t, 2], 0.1) and n[2] == pytest.approx(1.0)
+        else:  # above the upper box's bottom face (normal -z)
+            assert np.allclose(x[t, 2], 0.09) and n[2] == pytest.approx(-1.0)
+        q, w = orc.closest_point_tri(x[a], *x[t])
+        assert (q - x[a]) @ n == pytest.approx(0.01, abs=1e-12)
+    rim = [a for a in range(voff[1]) if abs(x[a, 2] - 0.1) < 1e-12 and not inside_upper[a]
+           and np.linalg.norm(np.maximum(np.maximum(ulo - x[a], x[a] - uhi), 0)) < p.dcd_radius]
+    assert len(rim) >= 4 and np.all(contact[rim] < 0)
     # a single body at rest, and two separated bodies, have no pairs
     single = synth.beam(4, 3, 2, jitter_frac=0.1, seed=103, pin_face=None)
     assert (orc.Model.from_mesh(single).dcd(p, single.rest) < 0).all()

@@ -44,6 +44,9 @@ MUTANTS = [
     ("self_contact_corner_hessian_linear_weight", "p->k_c * wk * wk * nn[r] * nn[c]", "p->k_c * wk * nn[r] * nn[c]",
      "test_oracle_collision.py"),
     ("closest_point_unclamped_edge", "if (tt > 1.0) tt = 1.0;", "", "test_oracle_collision.py"),
+    ("inside_test_counts_own_tets", "if (t[0] == a || t[1] == a || t[2] == a || t[3] == a) continue;", "",
+     "test_oracle_collision.py"),
+    ("inside_test_sign", "if (l < 0.0) return 0;", "if (l > 0.0) return 0;", "test_oracle_collision.py"),
 ]
 
 
