@@ -552,7 +552,10 @@ int orc_point_in_tet(const double *x, const int *t, const double q[3]) {
 /* DCD at positions x (the step start).  A boundary vertex has penetrated
  * when it lies in a tet it is not a vertex of; it is then paired with the
  * nearest boundary triangle within dcd_radius, skipping triangles that touch
- * the vertex or a vertex sharing a tet with it (ties: lower triangle index). */
+ * the vertex or a vertex sharing a tet with it.  Triangles whose distance is
+ * within 1e-5 dcd_radius of the nearest count as tied (a nearest point on an
+ * edge or corner is shared by several triangles; rounding must not choose)
+ * and the lowest index wins. */
 void orc_dcd(orc_model *m, const orc_params *p, const double *x) {
     int n = m->n_verts;
     int *stamp = (int *)calloc((size_t)n + 1, sizeof(int));
@@ -568,21 +571,25 @@ void orc_dcd(orc_model *m, const orc_params *p, const double *x) {
         if (!inside) continue;
         for (int s = m->inc_off[a]; s < m->inc_off[a + 1]; ++s)
             for (int k = 0; k < 4; ++k) stamp[m->tets[4 * (size_t)m->inc_tet[s] + k]] = a + 1;
-        double best = 0.0;
-        int best_T = -1;
-        for (int T = 0; T < m->n_tris; ++T) {
-            const int *v = m->tris + 3 * (size_t)T;
-            if (stamp[v[0]] == a + 1 || stamp[v[1]] == a + 1 || stamp[v[2]] == a + 1) continue;
-            double q[3], w[3];
-            orc_closest_point_tri(x + 3 * a, x + 3 * v[0], x + 3 * v[1], x + 3 * v[2], q, w);
-            double dv[3] = {x[3 * a] - q[0], x[3 * a + 1] - q[1], x[3 * a + 2] - q[2]};
-            double dist = sqrt(dot3(dv, dv));
-            if (dist <= p->dcd_radius && (best_T < 0 || dist < best)) {
-                best = dist;
-                best_T = T;
+        double best = -1.0;
+        for (int pass = 0; pass < 2; ++pass) {
+            /* pass 0: the nearest distance; pass 1: the lowest index near it */
+            for (int T = 0; T < m->n_tris; ++T) {
+                const int *v = m->tris + 3 * (size_t)T;
+                if (stamp[v[0]] == a + 1 || stamp[v[1]] == a + 1 || stamp[v[2]] == a + 1) continue;
+                double q[3], w[3];
+                orc_closest_point_tri(x + 3 * a, x + 3 * v[0], x + 3 * v[1], x + 3 * v[2], q, w);
+                double dv[3] = {x[3 * a] - q[0], x[3 * a + 1] - q[1], x[3 * a + 2] - q[2]};
+                double dist = sqrt(dot3(dv, dv));
+                if (dist > p->dcd_radius) continue;
+                if (pass == 0 && (best < 0.0 || dist < best)) best = dist;
+                if (pass == 1 && dist <= best + 1e-5 * p->dcd_radius) {
+                    m->contact[a] = T;
+                    break;
+                }
             }
+            if (best < 0.0) break;
         }
-        m->contact[a] = best_T;
     }
     free(stamp);
 }

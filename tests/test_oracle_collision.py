@@ -185,3 +185,24 @@ def test_block_dropped_on_block(orc, collide):
         assert zmin_upper > 0.1 - 0.01  # rests on the lower block (penalty depth ~ m g / k_c)
     else:
         assert zmin_upper < 0.0  # falls through
+
+
+def test_dcd_tie_on_a_shared_edge_goes_to_the_lower_index(orc):
+    """A vertex sunk 1 cm under the middle of a top-face diagonal of an
+    unjittered box is equally near the two triangles sharing that diagonal;
+    the pair takes the lower index of the two."""
+    lower = synth.beam(3, 3, 1, edge=0.1, pin_face="z-")
+    upper = synth.beam(1, 1, 1, edge=0.1, pin_face=None, origin=(0.05, 0.05, 0.09))
+    cat, voff, _ = synth.concat([lower, upper])
+    model = orc.Model.from_mesh(cat)
+    p = orc.Params.make(self_collision=True, dcd_radius=0.05, k_c=1e5)
+    x = cat.rest
+    contact = model.dcd(p, x)
+    tris = model.tris()
+    a = voff[1]  # the upper block's corner at (0.05, 0.05, 0.09)
+    assert np.allclose(x[a], [0.05, 0.05, 0.09])
+    tied = [T for T, t in enumerate(tris)
+            if np.allclose(x[t, 2], 0.1) and any(np.allclose(x[k, :2], [0, 0]) for k in t)
+            and any(np.allclose(x[k, :2], [0.1, 0.1]) for k in t)]
+    assert len(tied) == 2
+    assert contact[a] == min(tied)
