@@ -88,6 +88,8 @@ typedef struct {
     float eps_v;             /* friction velocity threshold of Eq. 15 [m/s] */
     int32_t line_search;     /* 1: local backtracking on G_i after each Newton step (Sec. 3.2) */
     int32_t jacobi;          /* 1: block Jacobi, every vertex against the previous iterate */
+    int32_t self_collision;  /* 1: vertex-triangle contact between boundary elements (Sec. 3.5) */
+    float dcd_radius;        /* detection distance r of the self-collision pairs [m] */
 } vbd_params;
 
 /* Library defaults: gravity (0,0,-9.8), ground off at z = 0 with n = +z,
@@ -106,7 +108,23 @@ typedef struct {
  * iteration over all free vertices, each solved against the previous
  * iterate and written to an auxiliary buffer copied back after the pass
  * (the x^new of Algorithm 1 applied to all vertices at once); colours are
- * then not used. */
+ * then not used.
+ * self_collision (off by default; dcd_radius 0.01 m): at the start of every
+ * step (on x^t) each boundary vertex a that has penetrated, i.e. lies in
+ * (or on) a tet it is not a vertex of, is paired with the nearest boundary
+ * triangle that shares no tet with it and lies within dcd_radius
+ * (triangles within 1e-5 dcd_radius of the nearest distance count as tied;
+ * the lowest index wins).  Boundary triangles are the tet
+ * faces owned by one tet, oriented outward at rest.  During the step a pair
+ * with depth d = (q - x_a).n > 0 (q the nearest point of the triangle, w its
+ * barycentric weights, n the unit normal at the current positions) adds the
+ * penalty of Eq. 12 with the same k_c: k_c d n and k_c n n^T to vertex a,
+ * -k_c d w_k n and k_c w_k^2 n n^T to corner k.  Every colour pass then
+ * solves its vertices against the pass-start positions and copies them back
+ * (x^new of Algorithm 1), because a contact can couple two vertices of one
+ * colour; the pipelined sweep is not used.  Needs dcd_radius > 0; not
+ * available with line_search; enlarges the workspace, so set it before
+ * vbd_bind. */
 void vbd_default_params(vbd_params *out);
 
 /* Sizes of a created context (filled after vbd_color for the colour data). */
@@ -120,6 +138,8 @@ typedef struct {
     int32_t pipe_stage_slots; /* slot capacity of one pipeline stage */
     int32_t pipe_ctas_per_sm; /* resident CTAs per SM of the pipelined sweep */
     int32_t use_graph;       /* vbd_iterate replays a CUDA graph */
+    int32_t n_surface_tris;  /* boundary triangles (0 until self-collision needed them) */
+    int32_t n_surface_verts; /* vertices of those triangles */
 } vbd_info;
 
 /* Creates a context from host arrays (copied).  Computes per-tet rest data
@@ -144,6 +164,13 @@ vbd_status vbd_color(vbd_ctx *ctx, const int32_t *colors, int32_t *n_colors_out)
 vbd_status vbd_get_colors(const vbd_ctx *ctx, int32_t *colors_out);
 
 vbd_status vbd_get_info(const vbd_ctx *ctx, vbd_info *out);
+
+/* Boundary triangles used by self-collision (Sec. 3.5): *n_tris_out
+ * receives their count and, when tris_out is not NULL, tris_out (host,
+ * 3 * count ints) their caller vertex ids, each outward at rest, in
+ * ascending order of the sorted id triple.  Builds the surface if needed.
+ * VBD_ERR_NOT_COLORED before vbd_color. */
+vbd_status vbd_get_surface(vbd_ctx *ctx, int32_t *n_tris_out, int32_t *tris_out);
 
 /* Bytes of device workspace needed with the current colouring and params
  * (tape_steps enlarges it).  VBD_ERR_NOT_COLORED before vbd_color. */
@@ -189,7 +216,8 @@ vbd_status vbd_iterate(vbd_ctx *ctx, int32_t iters);
 
 /* One Gauss-Seidel pass over the vertices of one colour (in place; vertices
  * of one colour share no tet, so in-place writes equal the x^new copy-back
- * of Algorithm 1 on this path). */
+ * of Algorithm 1 on this path; with self-collision the pass writes x^new
+ * and copies it back, see vbd_default_params). */
 vbd_status vbd_sweep_color(vbd_ctx *ctx, int32_t color);
 
 /* Chebyshev update (Eq. 18) after iteration n (1-based) of the current step. */
@@ -220,11 +248,20 @@ vbd_status vbd_energy(vbd_ctx *ctx, double *G_out);
  * plus tets), or when G_out is not device memory. */
 vbd_status vbd_energy_static(vbd_ctx *ctx, double *G_out);
 
+/* Self-collision pairs of the current step (found by vbd_begin_step on
+ * x^t): contact_out (host, N ints, caller order) receives for each vertex
+ * the index of its paired triangle in the vbd_get_surface list, or -1.
+ * VBD_ERR_STATE when the binding has no self-collision arrays.
+ * Synchronising. */
+vbd_status vbd_get_contacts(vbd_ctx *ctx, int32_t *contact_out);
+
 /* Waits for the stream and reads the device counters: VBD_ERR_TIMEOUT if a
  * bounded wait inside the pipelined sweep gave up (the step's results are
  * then invalid), else VBD_ERR_NONFINITE if any solve produced a non-finite
- * update since the last call (that update was not applied).  det_skips /
- * contacts may be NULL.  Synchronising. */
+ * update since the last call (that update was not applied).  det_skips
+ * receives the singular-Hessian skips, contacts the self-collision pairs
+ * found by detection, both summed since the last call; either may be NULL.
+ * Synchronising. */
 vbd_status vbd_sync_status(vbd_ctx *ctx, int64_t *det_skips, int64_t *contacts);
 
 /* Adjoint of the recorded steps (tape_steps > 0; no paper counterpart, the

@@ -9,8 +9,9 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libvbd.so")
-SOURCES = ["vbd_kernels.cu", "vbd_adjoint.cu", "vbd_host.cpp"]
-HEADERS = [os.path.join(CSRC, "vbd_kernels.h"), os.path.join(ROOT, "include", "vbd.h")]
+SOURCES = ["vbd_kernels.cu", "vbd_collide.cu", "vbd_adjoint.cu", "vbd_host.cpp"]
+HEADERS = [os.path.join(CSRC, "vbd_kernels.h"), os.path.join(CSRC, "vbd_geom.cuh"),
+           os.path.join(ROOT, "include", "vbd.h")]
 
 NVCC_FLAGS = [
     "-O3", "-std=c++17", "-lineinfo",

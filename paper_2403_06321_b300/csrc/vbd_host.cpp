@@ -60,6 +60,13 @@ struct vbd_ctx {
     bool per_tet_mat = false;        // some vertex's tets differ in material, or log E was set
     std::vector<int> slot_off;       // n_free + 1
     std::vector<int> inc_off, inc_tet, inc_loc;  // vertex -> incident tets (caller ids)
+    // boundary surface for self-collision (internal vertex ids), built on demand
+    bool surface_built = false;
+    std::vector<int> tris;           // 3 per triangle, outward at rest, ascending by sorted caller ids
+    std::vector<int> surf;           // boundary vertices, ascending
+    std::vector<int> ring_off, ring; // per boundary vertex: sorted ids of the vertices of its tets
+    int n_buckets = 0, n_tet_buckets = 0;
+    bool sc_carved = false;          // the bound workspace holds the self-collision arrays
     // device
     bool bound = false;
     char *ws = nullptr;
@@ -211,6 +218,11 @@ int greedy_coloring(int N, int T, const std::vector<int> &tets, std::vector<int>
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// the workspace carries the self-collision arrays
+bool sc_wanted(const vbd_ctx *c) { return c->params.self_collision && c->surface_built; }
+
+int surf_count(const vbd_ctx *c) { return sc_wanted(c) ? (int)c->surf.size() : 0; }
+
 // Carves the workspace; with base == nullptr only measures it.
 size_t carve(const vbd_ctx *c, char *base, Dev *d) {
     size_t off = 0;
@@ -247,7 +259,7 @@ size_t carve(const vbd_ctx *c, char *base, Dev *d) {
     t.new_of_orig = (int *)take(4 * N);
     for (int k = 0; k < 3; ++k) t.stage[k] = (float *)take(12 * N);
     t.counters = (unsigned long long *)take(8 * 8);
-    t.partials = (double *)take(8 * (size_t)vbd::energy_partials_needed(c->n_free, c->T));
+    t.partials = (double *)take(8 * (size_t)vbd::energy_partials_needed(c->n_free, c->T, surf_count(c)));
     t.energy_out = (double *)take(8);
     t.tape = (float4 *)take(16 * N * (size_t)std::max(c->params.tape_steps, 0));
     t.lam = (float4 *)take(16 * N);
@@ -255,6 +267,27 @@ size_t carve(const vbd_ctx *c, char *base, Dev *d) {
     t.xbar = (float4 *)take(16 * N);
     t.vbar = (float4 *)take(16 * N);
     t.gtheta = (float *)take(4 * T);
+    if (sc_wanted(c)) {
+        const size_t nt = c->tris.size() / 3, ns = c->surf.size(), nb = (size_t)c->n_buckets;
+        const size_t nf = (size_t)c->n_free;
+        t.tri = (int4 *)take(16 * nt);
+        t.surf = (int *)take(4 * ns);
+        t.ring_off = (int *)take(4 * (ns + 1));
+        t.ring = (int *)take(4 * c->ring.size());
+        t.contact = (int *)take(4 * N);
+        t.rev_off = (int *)take(4 * (nf + 1));
+        t.rev = (int *)take(4 * 3 * ns);
+        t.rev_fill = (int *)take(4 * nf);
+        t.cell_start = (int *)take(4 * (nb + 1));
+        t.cell_fill = (int *)take(4 * nb);
+        t.cell_tri = (int *)take(4 * nt);
+        const size_t nbt = (size_t)c->n_tet_buckets;
+        t.tet_start = (int *)take(4 * (nbt + 1));
+        t.tet_fill = (int *)take(4 * nbt);
+        t.cell_tet = (int *)take(4 * T);
+        t.scan_tmp = (int *)take(4 * (size_t)vbd::scan_tmp_needed((int)std::max({nb, nbt, nf})));
+        t.cell_size = (unsigned *)take(8);
+    }
     if (d) *d = t;
     return off;
 }
@@ -285,8 +318,9 @@ SweepParams sweep_params(const vbd_ctx *c, int color) {
     p.eps_h = c->params.eps_v * c->h;
     p.line_search = c->params.line_search ? 1 : 0;
     p.per_tet_mat = c->per_tet_mat ? 1 : 0;
-    p.jacobi = c->params.jacobi ? 1 : 0;
-    if (p.jacobi && color >= 0) {  // one pass over every free vertex
+    p.self_collision = c->params.self_collision && c->sc_carved ? 1 : 0;
+    p.to_unew = (c->params.jacobi || p.self_collision) ? 1 : 0;
+    if (c->params.jacobi && color >= 0) {  // one pass over every free vertex
         p.vbegin = 0;
         p.vend = c->n_free;
     }
@@ -305,6 +339,13 @@ bool params_ok(const vbd_params *p, std::string &why) {
     if (!(p->mu_c >= 0.f) || !(p->eps_v > 0.f)) { why = "mu_c must be >= 0 and eps_v > 0"; return false; }
     for (int r = 0; r < 3; ++r)
         if (!std::isfinite(p->gravity[r])) { why = "gravity must be finite"; return false; }
+    if (p->self_collision) {
+        if (!(p->dcd_radius > 0.f) || !std::isfinite(p->dcd_radius)) {
+            why = "dcd_radius must be > 0 with self_collision";
+            return false;
+        }
+        if (p->line_search) { why = "line_search is not available with self_collision"; return false; }
+    }
     return true;
 }
 
@@ -347,11 +388,20 @@ vbd_status prepare_pipeline(vbd_ctx *ctx) {
     return VBD_OK;
 }
 
+// One colour pass.  With self-collision two vertices of one colour can be
+// coupled through a contact pair, so the pass writes x^new (Algorithm 1) to
+// d.unew and copies it back afterwards; the pipelined kernel has no contact
+// forces, so that path always uses k_sweep.
 void launch_colour(vbd_ctx *c, int col, cudaStream_t s) {
-    if (c->pipeline)
-        vbd::launch_sweep_pipe(c->d, sweep_params(c, col), c->pipe_block, c->pipe_maxs, c->pipe_grid_cap, s);
-    else
-        vbd::launch_sweep(c->d, sweep_params(c, col), c->lanes, c->block, s);
+    const SweepParams p = sweep_params(c, col);
+    if (p.self_collision) {
+        vbd::launch_sweep(c->d, p, c->lanes, c->block, s);
+        vbd::launch_copy_back(c->d, p.vbegin, p.vend, s);
+    } else if (c->pipeline) {
+        vbd::launch_sweep_pipe(c->d, p, c->pipe_block, c->pipe_maxs, c->pipe_grid_cap, s);
+    } else {
+        vbd::launch_sweep(c->d, p, c->lanes, c->block, s);
+    }
 }
 
 // enqueue iterations n = first_n+1 .. first_n+iters on stream s
@@ -360,7 +410,7 @@ void enqueue_iterations(vbd_ctx *c, int first_n, int iters, cudaStream_t s) {
     for (int n = first_n + 1; n <= first_n + iters; ++n) {
         if (c->params.jacobi) {
             vbd::launch_sweep(c->d, sweep_params(c, 0), c->lanes, c->block, s);
-            vbd::launch_copy_back(c->d, c->n_free, s);
+            vbd::launch_copy_back(c->d, 0, c->n_free, s);
         } else {
             for (int col = 0; col < c->n_colors; ++col)
                 launch_colour(c, col, s);
@@ -402,6 +452,90 @@ void build_slots(const vbd_ctx *c, int k0, int k1, int4 *s0, float4 *s1, float4 
     }
 }
 
+// Boundary surface for self-collision: the tet faces that belong to exactly
+// one tet, each oriented so that its normal (v1 - v0) x (v2 - v0) points away
+// from that tet's fourth vertex at rest, listed in ascending order of their
+// sorted caller vertex ids; the vertices they use; and, per boundary vertex,
+// every vertex it shares a tet with (itself included), whose triangles the
+// detection skips.  Needs the colouring (stores internal ids).
+void build_surface(vbd_ctx *c) {
+    struct Face {
+        int k[3];   // sorted caller ids
+        int tet, opp;
+    };
+    const size_t T = (size_t)c->T;
+    std::vector<Face> faces(4 * T);
+    for (size_t j = 0; j < T; ++j) {
+        const int *t = &c->tets[4 * j];
+        for (int f = 0; f < 4; ++f) {
+            Face &F = faces[4 * j + f];
+            int m = 0;
+            for (int b = 0; b < 4; ++b)
+                if (b != f) F.k[m++] = t[b];
+            std::sort(F.k, F.k + 3);
+            F.tet = (int)j;
+            F.opp = f;
+        }
+    }
+    auto key_less = [](const Face &a, const Face &b) {
+        return std::lexicographical_compare(a.k, a.k + 3, b.k, b.k + 3);
+    };
+    auto key_eq = [](const Face &a, const Face &b) {
+        return a.k[0] == b.k[0] && a.k[1] == b.k[1] && a.k[2] == b.k[2];
+    };
+    std::sort(faces.begin(), faces.end(), key_less);
+    c->tris.clear();
+    std::vector<char> on(c->N, 0);
+    for (size_t q = 0; q < faces.size();) {
+        size_t r = q + 1;
+        while (r < faces.size() && key_eq(faces[r], faces[q])) ++r;
+        if (r == q + 1) {
+            const Face &F = faces[q];
+            const int *t = &c->tets[4 * (size_t)F.tet];
+            int v[3], m = 0;
+            for (int b = 0; b < 4; ++b)
+                if (b != F.opp) v[m++] = t[b];
+            const double *X0 = &c->rest[3 * (size_t)v[0]], *X1 = &c->rest[3 * (size_t)v[1]];
+            const double *X2 = &c->rest[3 * (size_t)v[2]], *Xo = &c->rest[3 * (size_t)t[F.opp]];
+            const double e0[3] = {X1[0] - X0[0], X1[1] - X0[1], X1[2] - X0[2]};
+            const double e1[3] = {X2[0] - X0[0], X2[1] - X0[1], X2[2] - X0[2]};
+            const double n[3] = {e0[1] * e1[2] - e0[2] * e1[1], e0[2] * e1[0] - e0[0] * e1[2],
+                                 e0[0] * e1[1] - e0[1] * e1[0]};
+            const double side = n[0] * (Xo[0] - X0[0]) + n[1] * (Xo[1] - X0[1]) + n[2] * (Xo[2] - X0[2]);
+            if (side > 0.0) std::swap(v[1], v[2]);
+            for (int b = 0; b < 3; ++b) {
+                c->tris.push_back(c->new_of_orig[v[b]]);
+                on[v[b]] = 1;
+            }
+        }
+        q = r;
+    }
+    std::vector<Face>().swap(faces);
+    c->surf.clear();
+    for (int k = 0; k < c->N; ++k)
+        if (on[c->orig_of_new[k]]) c->surf.push_back(k);
+    c->ring_off.assign(c->surf.size() + 1, 0);
+    c->ring.clear();
+    std::vector<int> nb;
+    for (size_t k = 0; k < c->surf.size(); ++k) {
+        const int i = c->orig_of_new[c->surf[k]];
+        nb.clear();
+        for (int q = c->inc_off[i]; q < c->inc_off[i + 1]; ++q)
+            for (int b = 0; b < 4; ++b) nb.push_back(c->new_of_orig[c->tets[4 * (size_t)c->inc_tet[q] + b]]);
+        std::sort(nb.begin(), nb.end());
+        nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+        c->ring.insert(c->ring.end(), nb.begin(), nb.end());
+        c->ring_off[k + 1] = (int)c->ring.size();
+    }
+    int nbk = 1024;
+    while ((size_t)nbk < 2 * (c->tris.size() / 3) && nbk < (1 << 30)) nbk <<= 1;
+    c->n_buckets = nbk;
+    nbk = 1024;
+    while (nbk < c->T && nbk < (1 << 30)) nbk <<= 1;
+    c->n_tet_buckets = nbk;
+    c->surface_built = true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -423,6 +557,8 @@ void vbd_default_params(vbd_params *out) {
     out->eps_v = 1e-3f;
     out->line_search = 0;
     out->jacobi = 0;
+    out->self_collision = 0;
+    out->dcd_radius = 0.01f;
 }
 
 vbd_status vbd_create_mesh(const vbd_mesh_desc *desc, const vbd_params *params, vbd_ctx **out) {
@@ -555,6 +691,8 @@ vbd_status vbd_color(vbd_ctx *ctx, const int32_t *colors, int32_t *n_colors_out)
     }
     ctx->n_slots = ctx->slot_off[ctx->n_free];
     ctx->colored = true;
+    ctx->surface_built = false;  // it holds internal ids of the previous order
+    if (ctx->params.self_collision) build_surface(ctx);
     ctx->bound = false;
     ctx->in_step = false;
     ctx->tape_len = 0;
@@ -584,6 +722,18 @@ vbd_status vbd_get_info(const vbd_ctx *ctx, vbd_info *out) {
     out->pipe_stage_slots = ctx->pipe_maxs;
     out->pipe_ctas_per_sm = ctx->pipe_ctas_per_sm;
     out->use_graph = ctx->use_graph ? 1 : 0;
+    out->n_surface_tris = ctx->surface_built ? (int32_t)(ctx->tris.size() / 3) : 0;
+    out->n_surface_verts = ctx->surface_built ? (int32_t)ctx->surf.size() : 0;
+    return VBD_OK;
+}
+
+vbd_status vbd_get_surface(vbd_ctx *ctx, int32_t *n_tris_out, int32_t *tris_out) {
+    if (!ctx || !n_tris_out) return VBD_ERR_INVALID_ARG;
+    if (!ctx->colored) return fail(ctx, VBD_ERR_NOT_COLORED, "vbd_color has not run");
+    if (!ctx->surface_built) build_surface(ctx);
+    *n_tris_out = (int32_t)(ctx->tris.size() / 3);
+    if (tris_out)
+        for (size_t k = 0; k < ctx->tris.size(); ++k) tris_out[k] = ctx->orig_of_new[ctx->tris[k]];
     return VBD_OK;
 }
 
@@ -605,7 +755,7 @@ vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *st
     ctx->ws_bytes = bytes;
     ctx->stream = (cudaStream_t)stream;
     carve(ctx, ctx->ws, &ctx->d);
-    ctx->n_partials = vbd::energy_partials_needed(ctx->n_free, ctx->T);
+    ctx->n_partials = vbd::energy_partials_needed(ctx->n_free, ctx->T, surf_count(ctx));
     cudaStream_t s = ctx->stream;
     const int N = ctx->N, T = ctx->T;
     const long long S = ctx->n_slots;
@@ -697,6 +847,23 @@ vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *st
     }
     CU(cudaMemcpyAsync(d.rest, restf.data(), 16 * (size_t)N, cudaMemcpyHostToDevice, s), "upload rest");
     CU(cudaMemsetAsync(d.u, 0, 16 * (size_t)N, s), "clear u");
+    ctx->sc_carved = sc_wanted(ctx);
+    if (ctx->sc_carved) {
+        const size_t nt = ctx->tris.size() / 3;
+        std::vector<int4> tv(nt);
+        for (size_t t = 0; t < nt; ++t)
+            tv[t] = make_int4(ctx->tris[3 * t], ctx->tris[3 * t + 1], ctx->tris[3 * t + 2], 0);
+        CU(cudaMemcpyAsync(d.tri, tv.data(), 16 * nt, cudaMemcpyHostToDevice, s), "upload surface");
+        CU(cudaMemcpyAsync(d.surf, ctx->surf.data(), 4 * ctx->surf.size(), cudaMemcpyHostToDevice, s),
+           "upload surface");
+        CU(cudaMemcpyAsync(d.ring_off, ctx->ring_off.data(), 4 * ctx->ring_off.size(), cudaMemcpyHostToDevice, s),
+           "upload surface");
+        CU(cudaMemcpyAsync(d.ring, ctx->ring.data(), 4 * ctx->ring.size(), cudaMemcpyHostToDevice, s),
+           "upload surface");
+        CU(cudaMemsetAsync(d.contact, 0xff, 4 * (size_t)N, s), "clear contacts");  // -1: no pair
+        CU(cudaMemsetAsync(d.rev_off, 0, 4 * ((size_t)ctx->n_free + 1), s), "clear contacts");
+        CU(cudaStreamSynchronize(s), "upload surface");
+    }
     CU(cudaMemsetAsync(d.v, 0, 16 * (size_t)N, s), "clear v");
     CU(cudaMemsetAsync(d.vprev, 0, 16 * (size_t)N, s), "clear v_prev");
     CU(cudaMemsetAsync(d.ut, 0, 16 * (size_t)N, s), "clear u^t");
@@ -720,7 +887,11 @@ vbd_status vbd_set_params(vbd_ctx *ctx, const vbd_params *params) {
     if (!params_ok(params, why)) return fail(ctx, VBD_ERR_INVALID_ARG, why);
     if (ctx->bound && params->tape_steps != ctx->params.tape_steps)
         return fail(ctx, VBD_ERR_STATE, "tape_steps changed: query the workspace size and bind again");
+    if (ctx->bound && params->self_collision && !ctx->sc_carved)
+        return fail(ctx, VBD_ERR_STATE,
+                    "self_collision needs its arrays in the workspace: set it before vbd_bind, then bind");
     ctx->params = *params;
+    if (ctx->params.self_collision && ctx->colored && !ctx->surface_built) build_surface(ctx);
     ctx->version++;
     clear_graphs(ctx);
     return VBD_OK;
@@ -808,6 +979,12 @@ vbd_status vbd_begin_step(vbd_ctx *ctx, float h) {
     if (ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_begin_step inside a step");
     ctx->h = h;
     ctx->iter_in_step = 0;
+    if (ctx->params.self_collision && ctx->sc_carved) {  // pairs from x^t (Sec. 3.5)
+        const vbd::CollideDims cd{(int)(ctx->tris.size() / 3), (int)ctx->surf.size(), ctx->n_buckets, ctx->T,
+                                  ctx->n_tet_buckets, ctx->params.dcd_radius};
+        vbd::launch_detect(ctx->d, cd, ctx->n_free, ctx->stream);
+        CU(cudaGetLastError(), "detect");
+    }
     const float *g = ctx->params.gravity;
     vbd::launch_predict(ctx->d, ctx->N, ctx->n_free, h, make_float3(g[0], g[1], g[2]), ctx->params.init_mode,
                         ctx->params.cheby_rho > 0.f, ctx->stream);
@@ -910,7 +1087,8 @@ vbd_status vbd_energy(vbd_ctx *ctx, double *G_out) {
     if (st != VBD_OK) return st;
     if (!G_out) return fail(ctx, VBD_ERR_INVALID_ARG, "G_out is NULL");
     if (!(ctx->h > 0.f)) return fail(ctx, VBD_ERR_STATE, "no step has begun (y undefined)");
-    vbd::launch_energy(ctx->d, ctx->n_free, ctx->T, (double)ctx->h, sweep_params(ctx, -1), ctx->stream);
+    const int ns = ctx->params.self_collision && ctx->sc_carved ? (int)ctx->surf.size() : 0;
+    vbd::launch_energy(ctx->d, ctx->n_free, ctx->T, ns, (double)ctx->h, sweep_params(ctx, -1), ctx->stream);
     CU(cudaGetLastError(), "energy");
     CU(cudaMemcpyAsync(G_out, ctx->d.energy_out, 8, cudaMemcpyDefault, ctx->stream), "energy download");
     CU(cudaStreamSynchronize(ctx->stream), "energy sync");
@@ -922,14 +1100,28 @@ vbd_status vbd_energy_static(vbd_ctx *ctx, double *G_out) {
     if (st != VBD_OK) return st;
     if (!G_out || !is_device_ptr(G_out)) return fail(ctx, VBD_ERR_INVALID_ARG, "G_out must be a device pointer");
     if (!(ctx->h > 0.f)) return fail(ctx, VBD_ERR_STATE, "no step has begun (y undefined)");
-    const int need = vbd::energy_static_partials_needed(ctx->n_free, ctx->T);
+    const int ns = ctx->params.self_collision && ctx->sc_carved ? (int)ctx->surf.size() : 0;
+    const int need = vbd::energy_static_partials_needed(ctx->n_free, ctx->T, ns);
     if (need > vbd::energy_static_capacity())
         return fail(ctx, VBD_ERR_INVALID_ARG,
                     "mesh too large for the static scratch: needs " + std::to_string(need) +
                         " partial sums, the library holds " + std::to_string(vbd::energy_static_capacity()));
-    cudaError_t e = vbd::launch_energy_static(ctx->d, ctx->n_free, ctx->T, (double)ctx->h,
+    cudaError_t e = vbd::launch_energy_static(ctx->d, ctx->n_free, ctx->T, ns, (double)ctx->h,
                                               sweep_params(ctx, -1), G_out, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "energy (static scratch)");
+    return VBD_OK;
+}
+
+vbd_status vbd_get_contacts(vbd_ctx *ctx, int32_t *contact_out) {
+    vbd_status st = check_bound(ctx);
+    if (st != VBD_OK) return st;
+    if (!contact_out) return fail(ctx, VBD_ERR_INVALID_ARG, "contact_out is NULL");
+    if (!ctx->sc_carved) return fail(ctx, VBD_ERR_STATE, "bound without self-collision");
+    std::vector<int> c(ctx->N);
+    CU(cudaMemcpyAsync(c.data(), ctx->d.contact, 4 * (size_t)ctx->N, cudaMemcpyDeviceToHost, ctx->stream),
+       "contacts download");
+    CU(cudaStreamSynchronize(ctx->stream), "contacts download");
+    for (int o = 0; o < ctx->N; ++o) contact_out[o] = c[ctx->new_of_orig[o]];
     return VBD_OK;
 }
 
@@ -942,7 +1134,7 @@ vbd_status vbd_sync_status(vbd_ctx *ctx, int64_t *det_skips, int64_t *contacts) 
     CU(cudaMemsetAsync(ctx->d.counters, 0, sizeof(c), ctx->stream), "clear counters");
     CU(cudaStreamSynchronize(ctx->stream), "sync");
     if (det_skips) *det_skips = (int64_t)c[1];
-    if (contacts) *contacts = 0;
+    if (contacts) *contacts = (int64_t)c[3];
     if (c[2] > 0) return fail(ctx, VBD_ERR_TIMEOUT, std::to_string(c[2]) + " pipelined-sweep waits timed out");
     if (c[0] > 0) return fail(ctx, VBD_ERR_NONFINITE, std::to_string(c[0]) + " non-finite updates");
     return VBD_OK;
@@ -955,8 +1147,8 @@ vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, floa
     if (adj_iters < 1) return fail(ctx, VBD_ERR_INVALID_ARG, "adj_iters must be >= 1");
     if (ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_backward inside a step");
     if (ctx->tape_len < 1) return fail(ctx, VBD_ERR_NO_TAPE, "no recorded steps (tape_steps = 0?)");
-    if (ctx->params.k_d != 0.f || ctx->params.mu_c != 0.f)
-        return fail(ctx, VBD_ERR_INVALID_ARG, "the adjoint needs k_d = 0 and mu_c = 0");
+    if (ctx->params.k_d != 0.f || ctx->params.mu_c != 0.f || ctx->params.self_collision)
+        return fail(ctx, VBD_ERR_INVALID_ARG, "the adjoint needs k_d = 0, mu_c = 0 and no self-collision");
     if (!is_device_ptr(dL_dxT) || (dL_dlogE && !is_device_ptr(dL_dlogE)) || (dL_dv0 && !is_device_ptr(dL_dv0)))
         return fail(ctx, VBD_ERR_INVALID_ARG, "vbd_backward takes device pointers");
     const Dev &d = ctx->d;

@@ -21,20 +21,18 @@
 #include <cstdio>
 #include <mutex>
 
+#include "vbd_geom.cuh"
+
 namespace vbd {
 
 namespace {
 
-constexpr unsigned FULL = 0xffffffffu;
+using geom::cross;
+using geom::dot;
+using geom::f3;
+using geom::operator-;
 
-__device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
-__device__ __forceinline__ float3 operator-(float3 a, float3 b) {
-    return make_float3(a.x - b.x, a.y - b.y, a.z - b.z);
-}
-__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ float3 cross(float3 a, float3 b) {
-    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
+constexpr unsigned FULL = 0xffffffffu;
 
 // f_i and the symmetric H_i (upper triangle) accumulated over incident tets
 struct Acc {
@@ -118,9 +116,50 @@ __device__ __forceinline__ float sub_reduce(float v) {
     return v;
 }
 
+// Vertex-triangle contact forces on vertex vi (Sec. 3.5, penalty of Eq. 12),
+// added to f and H (upper triangle h00 h01 h02 h11 h12 h22).  As the vertex of
+// its own pair: k_c d n and k_c n n^T.  As corner k of another vertex's
+// triangle: -k_c d w_k n and k_c w_k^2 n n^T.  Only pairs with d > 0 act.
+// Positions come from d.u, which holds the pass-start state: the colour's
+// updates go to d.unew and are copied back after the pass.  Returns whether
+// any pair acted.
+__device__ __forceinline__ bool add_self_contact(const Dev &d, float kc, int vi, float &f0, float &f1, float &f2,
+                                                 float &h00, float &h01, float &h02, float &h11, float &h12,
+                                                 float &h22) {
+    bool hit = false;
+    auto add = [&](float3 n, float fs, float hs) {
+        f0 += fs * n.x; f1 += fs * n.y; f2 += fs * n.z;
+        h00 += hs * n.x * n.x; h01 += hs * n.x * n.y; h02 += hs * n.x * n.z;
+        h11 += hs * n.y * n.y; h12 += hs * n.y * n.z; h22 += hs * n.z * n.z;
+    };
+    const int T = d.contact[vi];
+    if (T >= 0) {
+        float3 n, w;
+        const float dep = geom::pair_depth(d, vi, d.tri[T], n, w);
+        if (dep > 0.0f) {
+            add(n, kc * dep, kc);
+            hit = true;
+        }
+    }
+    const int r1 = d.rev_off[vi + 1];
+    for (int r = d.rev_off[vi]; r < r1; ++r) {
+        const int a = d.rev[r];
+        const int4 t = d.tri[d.contact[a]];
+        float3 n, w;
+        const float dep = geom::pair_depth(d, a, t, n, w);
+        if (dep > 0.0f) {
+            const float wk = (t.x == vi) ? w.x : ((t.y == vi) ? w.y : w.z);
+            add(n, -kc * dep * wk, kc * wk * wk);
+            hit = true;
+        }
+    }
+    return hit;
+}
+
 // Local solve of Sec. 3.2 for one vertex: Eq. 7 with the inertia terms of
-// Eqs. 8-9, damping (Eqs. 10-11), ground penalty (Eq. 12), singular skip,
-// analytic inverse.
+// Eqs. 8-9, damping (Eqs. 10-11), ground penalty (Eq. 12), self-contact,
+// singular skip, analytic inverse.
+template <bool SC>
 __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams &p, int vi, float4 xi,
                                                 const Acc &a) {
     // xi holds the displacement u_i; ym the displacement of the inertia target
@@ -170,7 +209,8 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
             }
         }
     }
-    float4 *out = p.jacobi ? d.unew : d.u;
+    if (SC && add_self_contact(d, p.kc, vi, f0, f1, f2, h00, h01, h02, h11, h12, h22)) flag = 1.0f;
+    float4 *out = p.to_unew ? d.unew : d.u;
     // adjugate of the symmetric H
     const float a00 = h11 * h22 - h12 * h12;
     const float a01 = h02 * h12 - h01 * h22;
@@ -182,7 +222,7 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
     const float tr3 = (h00 + h11 + h22) * (1.0f / 3.0f);
     if (!(fabsf(det) > p.det_eps * fabsf(tr3 * tr3 * tr3))) {
         atomicAdd(d.counters + 1, 1ull);
-        if (p.jacobi || flag != xi.w) out[vi] = make_float4(xi.x, xi.y, xi.z, flag);
+        if (p.to_unew || flag != xi.w) out[vi] = make_float4(xi.x, xi.y, xi.z, flag);
         return;
     }
     const float inv = 1.0f / det;
@@ -191,7 +231,7 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
     float dz = (a02 * f0 + a12 * f1 + a22 * f2) * inv;
     if (!(isfinite(dx) && isfinite(dy) && isfinite(dz))) {
         atomicAdd(d.counters + 0, 1ull);
-        if (p.jacobi) out[vi] = xi;
+        if (p.to_unew) out[vi] = xi;
         return;
     }
     if (p.line_search) {
@@ -227,7 +267,7 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
     out[vi] = make_float4(xi.x + dx, xi.y + dy, xi.z + dz, flag);
 }
 
-template <int L>
+template <int L, bool SC>
 __global__ void __launch_bounds__(256) k_sweep(Dev d, SweepParams p) {
     const int lane = threadIdx.x & (L - 1);
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -254,7 +294,7 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, SweepParams p) {
     acc.h11 = sub_reduce<L>(acc.h11);
     acc.h12 = sub_reduce<L>(acc.h12);
     acc.h22 = sub_reduce<L>(acc.h22);
-    if (active && lane == 0) solve_and_store(d, p, vi, xi, acc);
+    if (active && lane == 0) solve_and_store<SC>(d, p, vi, xi, acc);
 }
 
 // ---- pipelined sweep: slot records staged in shared memory by TMA ----------
@@ -427,7 +467,7 @@ __global__ void __launch_bounds__(TT) k_sweep_pipe(Dev d, SweepParams p, int max
         acc.h11 = sub_reduce<L>(acc.h11);
         acc.h12 = sub_reduce<L>(acc.h12);
         acc.h22 = sub_reduce<L>(acc.h22);
-        if (active && lane == 0) solve_and_store(d, p, vi, xi, acc);
+        if (active && lane == 0) solve_and_store<false>(d, p, vi, xi, acc);
     }
 }
 
@@ -520,10 +560,10 @@ __global__ void k_gather(const float4 *src, float *dst, const int *new_of_orig, 
     dst[3 * o + 2] = a.z;
 }
 
-// block Jacobi: the pass wrote every free vertex to unew; copy it back
-__global__ void k_copy_back(Dev d, int n_free) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n_free) d.u[i] = d.unew[i];
+// the pass wrote vertices [vbegin, vend) to unew (x^new of Algorithm 1); copy them back
+__global__ void k_copy_back(Dev d, int vbegin, int vend) {
+    const int i = vbegin + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < vend) d.u[i] = d.unew[i];
 }
 
 __global__ void k_restore_x(Dev d, int n) {
@@ -596,6 +636,20 @@ __global__ void __launch_bounds__(EB) k_energy_tets(Dev d, int n_tets, double *p
     block_sum_store(e, partials + blockIdx.x);
 }
 
+// self-contact energy k_c d^2 / 2 of every current pair with d > 0
+__global__ void __launch_bounds__(EB) k_energy_contacts(Dev d, int n_surf, double kc, double *partials) {
+    double e = 0.0;
+    for (int k = blockIdx.x * EB + threadIdx.x; k < n_surf; k += gridDim.x * EB) {
+        const int a = d.surf[k];
+        const int T = d.contact[a];
+        if (T < 0) continue;
+        float3 n, w;
+        const double dep = geom::pair_depth(d, a, d.tri[T], n, w);
+        if (dep > 0.0) e += 0.5 * kc * dep * dep;
+    }
+    block_sum_store(e, partials + blockIdx.x);
+}
+
 __global__ void k_reduce_partials(const double *partials, int n, double *out) {
     double e = 0.0;
     for (int i = threadIdx.x; i < n; i += EB) e += partials[i];
@@ -632,11 +686,20 @@ void launch_sweep(const Dev &d, const SweepParams &p, int lanes, int block, cuda
     const long long threads = (long long)(p.vend - p.vbegin) * lanes;
     if (threads <= 0) return;
     const unsigned grid = blocks_for(threads, block);
+    if (p.self_collision) {
+        switch (lanes) {
+        case 4: k_sweep<4, true><<<grid, block, 0, s>>>(d, p); break;
+        case 8: k_sweep<8, true><<<grid, block, 0, s>>>(d, p); break;
+        case 16: k_sweep<16, true><<<grid, block, 0, s>>>(d, p); break;
+        default: k_sweep<32, true><<<grid, block, 0, s>>>(d, p); break;
+        }
+        return;
+    }
     switch (lanes) {
-    case 4: k_sweep<4><<<grid, block, 0, s>>>(d, p); break;
-    case 8: k_sweep<8><<<grid, block, 0, s>>>(d, p); break;
-    case 16: k_sweep<16><<<grid, block, 0, s>>>(d, p); break;
-    default: k_sweep<32><<<grid, block, 0, s>>>(d, p); break;
+    case 4: k_sweep<4, false><<<grid, block, 0, s>>>(d, p); break;
+    case 8: k_sweep<8, false><<<grid, block, 0, s>>>(d, p); break;
+    case 16: k_sweep<16, false><<<grid, block, 0, s>>>(d, p); break;
+    default: k_sweep<32, false><<<grid, block, 0, s>>>(d, p); break;
     }
 }
 
@@ -693,32 +756,35 @@ void launch_gather(const float4 *src, float *dst, const int *new_of_orig, const 
     k_gather<<<blocks_for(n, 256), 256, 0, s>>>(src, dst, new_of_orig, rest, n);
 }
 
-void launch_copy_back(const Dev &d, int n_free, cudaStream_t s) {
-    if (n_free > 0) k_copy_back<<<blocks_for(n_free, 256), 256, 0, s>>>(d, n_free);
+void launch_copy_back(const Dev &d, int vbegin, int vend, cudaStream_t s) {
+    if (vend > vbegin) k_copy_back<<<blocks_for(vend - vbegin, 256), 256, 0, s>>>(d, vbegin, vend);
 }
 
 void launch_restore_x(const Dev &d, int n, cudaStream_t s) {
     k_restore_x<<<blocks_for(n, 256), 256, 0, s>>>(d, n);
 }
 
-static void energy_grid(int n_free, int n_tets, int *gv, int *gt) {
+static void energy_grid(int n_free, int n_tets, int n_surf, int *gv, int *gt, int *gc) {
     const int cap = 4 * 148;
     *gv = (int)std::min<long long>(cap, std::max<long long>(1, blocks_for(n_free, EB)));
     *gt = (int)std::min<long long>(cap, std::max<long long>(1, blocks_for(n_tets, EB)));
+    *gc = n_surf > 0 ? (int)std::min<long long>(cap, blocks_for(n_surf, EB)) : 0;
 }
 
-int energy_partials_needed(int n_free, int n_tets) {
-    int gv, gt;
-    energy_grid(n_free, n_tets, &gv, &gt);
-    return gv + gt;
+int energy_partials_needed(int n_free, int n_tets, int n_surf) {
+    int gv, gt, gc;
+    energy_grid(n_free, n_tets, n_surf, &gv, &gt, &gc);
+    return gv + gt + gc;
 }
 
-void launch_energy(const Dev &d, int n_free, int n_tets, double h, const SweepParams &p, cudaStream_t s) {
-    int gv, gt;
-    energy_grid(n_free, n_tets, &gv, &gt);
+void launch_energy(const Dev &d, int n_free, int n_tets, int n_surf, double h, const SweepParams &p,
+                   cudaStream_t s) {
+    int gv, gt, gc;
+    energy_grid(n_free, n_tets, n_surf, &gv, &gt, &gc);
     k_energy_verts<<<gv, EB, 0, s>>>(d, n_free, 1.0 / (2.0 * h * h), p, d.partials);
     k_energy_tets<<<gt, EB, 0, s>>>(d, n_tets, d.partials + gv);
-    k_reduce_partials<<<1, EB, 0, s>>>(d.partials, gv + gt, d.energy_out);
+    if (gc > 0) k_energy_contacts<<<gc, EB, 0, s>>>(d, n_surf, (double)p.kc, d.partials + gv + gt);
+    k_reduce_partials<<<1, EB, 0, s>>>(d.partials, gv + gt + gc, d.energy_out);
 }
 
 void launch_set_log_young(const Dev &d, const float *log_young, int n_tets, cudaStream_t s) {
@@ -742,10 +808,11 @@ double *g_static_ptr[kMaxDevices] = {};
 
 int energy_static_capacity() { return kStaticPartials; }
 
-int energy_static_partials_needed(int n_free, int n_tets) {
+int energy_static_partials_needed(int n_free, int n_tets, int n_surf) {
     const long long gv = std::max<long long>(1, blocks_for(n_free, EB));
     const long long gt = std::max<long long>(1, blocks_for(n_tets, EB));
-    return (int)std::min<long long>(gv + gt, 0x7fffffffLL);
+    const long long gc = n_surf > 0 ? blocks_for(n_surf, EB) : 0;
+    return (int)std::min<long long>(gv + gt + gc, 0x7fffffffLL);
 }
 
 // Device address of g_static_partials on the current device.  The symbol name
@@ -768,18 +835,20 @@ cudaError_t energy_static_scratch(double **out) {
     return cudaSuccess;
 }
 
-cudaError_t launch_energy_static(const Dev &d, int n_free, int n_tets, double h, const SweepParams &p,
-                                 double *G_out, cudaStream_t s) {
+cudaError_t launch_energy_static(const Dev &d, int n_free, int n_tets, int n_surf, double h,
+                                 const SweepParams &p, double *G_out, cudaStream_t s) {
     const int gv = std::max(1, (int)blocks_for(n_free, EB));
     const int gt = std::max(1, (int)blocks_for(n_tets, EB));
-    if ((long long)gv + gt > kStaticPartials) return cudaErrorInvalidValue;
+    const int gc = n_surf > 0 ? (int)blocks_for(n_surf, EB) : 0;
+    if ((long long)gv + gt + gc > kStaticPartials) return cudaErrorInvalidValue;
     double *part = nullptr;
     cudaError_t e = energy_static_scratch(&part);
     if (e != cudaSuccess) return e;
-    // every partial slot [0, gv + gt) is written before the final sum reads it
+    // every partial slot [0, gv + gt + gc) is written before the final sum reads it
     k_energy_verts<<<gv, EB, 0, s>>>(d, n_free, 1.0 / (2.0 * h * h), p, part);
     k_energy_tets<<<gt, EB, 0, s>>>(d, n_tets, part + gv);
-    k_reduce_partials<<<1, EB, 0, s>>>(part, gv + gt, G_out);
+    if (gc > 0) k_energy_contacts<<<gc, EB, 0, s>>>(d, n_surf, (double)p.kc, part + gv + gt);
+    k_reduce_partials<<<1, EB, 0, s>>>(part, gv + gt + gc, G_out);
     return cudaGetLastError();
 }
 

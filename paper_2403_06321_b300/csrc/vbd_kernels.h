@@ -13,7 +13,7 @@ namespace vbd {
 // that FP32 resolves small strains at any distance from the origin; every
 // quantity below that is a position (u, ut, ym, cheb, tape) is a displacement.
 struct Dev {
-    float4 *u;        // current displacement; .w = 1 once the vertex touched the ground this step
+    float4 *u;        // current displacement; .w = 1 once the vertex was in contact this step
     float4 *ut;       // u^t (start of step)
     float4 *v;        // v^t
     float4 *vprev;    // v^{t-1}
@@ -43,6 +43,23 @@ struct Dev {
     // adjoint
     float4 *lam, *rhs, *xbar, *vbar;
     float *gtheta;    // T
+    // self-collision (vertex-triangle pairs, Sec. 3.5); carved only when enabled
+    int4 *tri;        // boundary triangles: internal vertex ids, outward at rest (.w unused)
+    int *surf;        // internal ids of the boundary vertices
+    int *ring_off;    // n_surf + 1
+    int *ring;        // sorted ids of every vertex sharing a tet with surf[k] (itself included)
+    int *contact;     // N: triangle paired with the vertex by the last detection, -1 none
+    int *rev_off;     // n_free + 1: pairs in which free vertex i is a triangle corner
+    int *rev;         // 3 n_surf: the pairs' vertices, ascending per corner
+    int *rev_fill;    // n_free
+    int *cell_start;  // n_buckets + 1: triangles of each hash bucket (by centroid cell)
+    int *cell_fill;   // n_buckets
+    int *cell_tri;    // n_tris
+    int *tet_start;   // n_tet_buckets + 1: tets of each hash bucket (by centroid cell)
+    int *tet_fill;    // n_tet_buckets
+    int *cell_tet;    // T
+    int *scan_tmp;    // block totals of the prefix sums
+    unsigned *cell_size;  // bits (float) of the largest centroid-to-corner distance: [0] triangles, [1] tets
 };
 
 struct SweepParams {
@@ -57,7 +74,15 @@ struct SweepParams {
     float eps_h;      // eps_v * h: tangential displacement where f1 reaches 1
     int line_search;  // backtracking on G_i (Sec. 3.2)
     int per_tet_mat;  // 1: mu, lambda per tet (via slot_tet); 0: per vertex (vmat)
-    int jacobi;       // write to d.unew (every vertex) instead of updating d.u in place
+    int to_unew;      // write to d.unew instead of updating d.u in place (block Jacobi, self-collision)
+    int self_collision;  // add the vertex-triangle contact forces of the current pairs
+};
+
+// sizes of the self-collision arrays
+struct CollideDims {
+    int n_tris, n_surf, n_buckets;
+    int n_tets, n_tet_buckets;
+    float radius;     // detection distance
 };
 
 int num_sms();
@@ -80,15 +105,21 @@ void launch_scatter(const float *src, float4 *dst, const int *new_of_orig, const
 void launch_gather(const float4 *src, float *dst, const int *new_of_orig, const float4 *rest, int n,
                    cudaStream_t s);
 void launch_restore_x(const Dev &d, int n, cudaStream_t s);
-void launch_copy_back(const Dev &d, int n_free, cudaStream_t s);
-void launch_energy(const Dev &d, int n_free, int n_tets, double h, const SweepParams &p,
+void launch_copy_back(const Dev &d, int vbegin, int vend, cudaStream_t s);
+// n_surf > 0 adds the self-contact energy of the current pairs
+void launch_energy(const Dev &d, int n_free, int n_tets, int n_surf, double h, const SweepParams &p,
                    cudaStream_t s);
-int energy_partials_needed(int n_free, int n_tets);
+int energy_partials_needed(int n_free, int n_tets, int n_surf);
 // energy with its scratch in a static device array (see vbd_energy_static)
 int energy_static_capacity();
-int energy_static_partials_needed(int n_free, int n_tets);
-cudaError_t launch_energy_static(const Dev &d, int n_free, int n_tets, double h, const SweepParams &p,
-                                 double *G_out, cudaStream_t s);
+int energy_static_partials_needed(int n_free, int n_tets, int n_surf);
+cudaError_t launch_energy_static(const Dev &d, int n_free, int n_tets, int n_surf, double h,
+                                 const SweepParams &p, double *G_out, cudaStream_t s);
+
+// self-collision detection at x = X + u (vbd_collide.cu): fills d.contact,
+// d.rev_off and d.rev; counters[3] += pairs found
+int scan_tmp_needed(int n);
+void launch_detect(const Dev &d, const CollideDims &c, int n_free, cudaStream_t s);
 void launch_set_log_young(const Dev &d, const float *log_young, int n_tets, cudaStream_t s);
 
 // adjoint

@@ -61,6 +61,8 @@ class SimConfig:
     eps_v: float = 1e-3
     line_search: bool = False
     jacobi: bool = False
+    self_collision: bool = False
+    dcd_radius: float = 0.01
 
 
 def kuhn_grid(nx: int, ny: int, nz: int, edge: float,
@@ -192,6 +194,26 @@ def differentiable_beam(seed: int = 3) -> tuple[MeshInput, SimConfig, np.ndarray
     rng = np.random.default_rng(seed)
     target = m.rest[tip] + rng.uniform(-0.1, 0.1, size=3)
     return m, SimConfig(h=1 / 60, iters=50, steps=30), tip, target
+
+
+def colliding_slabs(n: int = 12, layers: int = 2, edge: float = 0.05, sink: float = 0.1, angle: float = 0.15,
+                    seed: int = 7) -> tuple[MeshInput, SimConfig, np.ndarray]:
+    """Self-collision workload: a jittered slab of n x n x layers cubes pinned
+    at its bottom face, and a free (n-2) x (n-2) x layers slab turned by
+    `angle` radians about z and lowered until it overlaps the first by `sink`
+    edges (boundary vertices of each end up inside the other).  One body in
+    the caller's numbering (the lower slab first); returns (mesh, config,
+    index of the first upper-slab vertex)."""
+    lower = beam(n, n, layers, edge, E=1e5, nu=0.4, pin_face="z-", jitter_frac=0.05, seed=seed)
+    upper = beam(n - 2, n - 2, layers, edge, E=1e5, nu=0.4, pin_face=None, jitter_frac=0.05, seed=seed + 1)
+    c, s_ = np.cos(angle), np.sin(angle)
+    R = np.array([[c, -s_, 0.0], [s_, c, 0.0], [0.0, 0.0, 1.0]])
+    centre = upper.rest.mean(axis=0)
+    target = np.array([0.5 * n * edge, 0.5 * n * edge, (1.5 * layers - sink) * edge])
+    upper.rest = (upper.rest - centre) @ R.T + target
+    cat, voff, _ = concat([lower, upper])
+    cfg = SimConfig(h=1 / 60, iters=20, steps=10, k_c=1e5, self_collision=True, dcd_radius=0.5 * edge)
+    return cat, cfg, int(voff[1])
 
 
 def concat(meshes: list[MeshInput]) -> tuple[MeshInput, np.ndarray, np.ndarray]:

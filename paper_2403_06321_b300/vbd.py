@@ -25,9 +25,10 @@ STATUS_CODE = {v: k for k, v in STATUS.items()}
 # every entry point declared in include/vbd.h
 ENTRY_POINTS = [
     "vbd_default_params", "vbd_create_mesh", "vbd_color", "vbd_get_colors", "vbd_get_info",
-    "vbd_workspace_size", "vbd_bind", "vbd_set_params", "vbd_set_state", "vbd_get_state",
+    "vbd_get_surface", "vbd_workspace_size", "vbd_bind", "vbd_set_params", "vbd_set_state", "vbd_get_state",
     "vbd_set_log_young", "vbd_step", "vbd_begin_step", "vbd_iterate", "vbd_sweep_color",
-    "vbd_accelerate", "vbd_end_step", "vbd_energy", "vbd_energy_static", "vbd_sync_status", "vbd_backward",
+    "vbd_accelerate", "vbd_end_step", "vbd_energy", "vbd_energy_static", "vbd_get_contacts", "vbd_sync_status",
+    "vbd_backward",
     "vbd_set_launch", "vbd_set_graph", "vbd_autotune", "vbd_last_error", "vbd_destroy",
 ]
 
@@ -54,14 +55,16 @@ class vbd_params(C.Structure):
                 ("ground_normal", C.c_float * 3), ("k_c", C.c_float), ("cheby_rho", C.c_float),
                 ("init_mode", C.c_int32), ("det_eps", C.c_float), ("k_d", C.c_float),
                 ("tape_steps", C.c_int32), ("mu_c", C.c_float), ("eps_v", C.c_float),
-                ("line_search", C.c_int32), ("jacobi", C.c_int32)]
+                ("line_search", C.c_int32), ("jacobi", C.c_int32), ("self_collision", C.c_int32),
+                ("dcd_radius", C.c_float)]
 
 
 class vbd_info(C.Structure):
     _fields_ = [("n_verts", C.c_int32), ("n_tets", C.c_int32), ("n_meshes", C.c_int32),
                 ("n_free", C.c_int32), ("n_colors", C.c_int32), ("n_slots", C.c_int64),
                 ("lanes_per_vertex", C.c_int32), ("block_threads", C.c_int32), ("pipeline", C.c_int32),
-                ("pipe_stage_slots", C.c_int32), ("pipe_ctas_per_sm", C.c_int32), ("use_graph", C.c_int32)]
+                ("pipe_stage_slots", C.c_int32), ("pipe_ctas_per_sm", C.c_int32), ("use_graph", C.c_int32),
+                ("n_surface_tris", C.c_int32), ("n_surface_verts", C.c_int32)]
 
 
 _lib = None
@@ -83,6 +86,7 @@ def load() -> C.CDLL:
         "vbd_color": (C.c_int, [P, P, C.POINTER(I32)]),
         "vbd_get_colors": (C.c_int, [P, P]),
         "vbd_get_info": (C.c_int, [P, C.POINTER(vbd_info)]),
+        "vbd_get_surface": (C.c_int, [P, C.POINTER(I32), P]),
         "vbd_workspace_size": (C.c_int, [P, C.POINTER(C.c_size_t)]),
         "vbd_bind": (C.c_int, [P, P, C.c_size_t, P]),
         "vbd_set_params": (C.c_int, [P, C.POINTER(vbd_params)]),
@@ -97,6 +101,7 @@ def load() -> C.CDLL:
         "vbd_end_step": (C.c_int, [P]),
         "vbd_energy": (C.c_int, [P, C.POINTER(D)]),
         "vbd_energy_static": (C.c_int, [P, P]),
+        "vbd_get_contacts": (C.c_int, [P, P]),
         "vbd_sync_status": (C.c_int, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "vbd_backward": (C.c_int, [P, P, P, P, I32]),
         "vbd_set_launch": (C.c_int, [P, I32, I32, I32]),
@@ -167,6 +172,15 @@ def vbd_get_info(ctx: int) -> vbd_info:
     return info
 
 
+def vbd_get_surface(ctx: int) -> np.ndarray:
+    """Boundary triangles (n, 3) in caller vertex ids."""
+    n = C.c_int32()
+    _check("vbd_get_surface", ctx, load().vbd_get_surface(ctx, C.byref(n), None))
+    out = np.zeros((n.value, 3), np.int32)
+    _check("vbd_get_surface", ctx, load().vbd_get_surface(ctx, C.byref(n), _ptr(out)))
+    return out
+
+
 def vbd_workspace_size(ctx: int) -> int:
     n = C.c_size_t()
     _check("vbd_workspace_size", ctx, load().vbd_workspace_size(ctx, C.byref(n)))
@@ -228,10 +242,18 @@ def vbd_energy_static(ctx: int, G_out) -> None:
     _check("vbd_energy_static", ctx, load().vbd_energy_static(ctx, _ptr(G_out)))
 
 
-def vbd_sync_status(ctx: int) -> int:
+def vbd_get_contacts(ctx: int, n_verts: int) -> np.ndarray:
+    out = np.zeros(n_verts, np.int32)
+    _check("vbd_get_contacts", ctx, load().vbd_get_contacts(ctx, _ptr(out)))
+    return out
+
+
+def vbd_sync_status(ctx: int, with_contacts: bool = False):
+    """Singular-Hessian skips since the last call; with_contacts=True also
+    returns the self-collision pairs detected since the last call."""
     skips, contacts = C.c_int64(), C.c_int64()
     _check("vbd_sync_status", ctx, load().vbd_sync_status(ctx, C.byref(skips), C.byref(contacts)))
-    return skips.value
+    return (skips.value, contacts.value) if with_contacts else skips.value
 
 
 def vbd_backward(ctx: int, dL_dxT, dL_dlogE, dL_dv0, adj_iters: int) -> None:
@@ -265,7 +287,8 @@ def vbd_destroy(ctx: int) -> None:
 
 def make_params(gravity=(0.0, 0.0, -9.8), ground_on=False, ground_height=0.0, ground_normal=(0.0, 0.0, 1.0),
                 k_c=1e7, cheby_rho=0.0, init_mode=3, det_eps=1e-12, k_d=0.0, tape_steps=0, mu_c=0.0,
-                eps_v=1e-3, line_search=False, jacobi=False, **_ignored) -> vbd_params:
+                eps_v=1e-3, line_search=False, jacobi=False, self_collision=False, dcd_radius=0.01,
+                **_ignored) -> vbd_params:
     p = vbd_default_params()
     p.gravity[:] = [float(g) for g in gravity]
     p.ground_on = int(bool(ground_on))
@@ -281,6 +304,8 @@ def make_params(gravity=(0.0, 0.0, -9.8), ground_on=False, ground_height=0.0, gr
     p.eps_v = float(eps_v)
     p.line_search = int(bool(line_search))
     p.jacobi = int(bool(jacobi))
+    p.self_collision = int(bool(self_collision))
+    p.dcd_radius = float(dcd_radius)
     return p
 
 

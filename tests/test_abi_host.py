@@ -129,3 +129,30 @@ def test_batched_union_rejects_cross_mesh_tets(lib):
     with pytest.raises(vbd.VbdError) as e:
         vbd.vbd_create_mesh(arr.desc(), vbd.make_params())
     assert e.value.status in ("VBD_ERR_BAD_MESH",)
+
+
+def test_surface_matches_oracle_and_self_collision_params(lib, orc):
+    """The library's boundary triangles (host preprocessing) equal the
+    oracle's, orientation and order included; the self-collision options are
+    validated and enlarge the workspace."""
+    lower = synth.beam(3, 3, 1, edge=0.1, pin_face="z-", jitter_frac=0.05, seed=102)
+    upper = synth.beam(2, 2, 1, edge=0.1, pin_face=None, jitter_frac=0.05, seed=103, origin=(0.05, 0.05, 0.09))
+    cat, voff, toff = synth.concat([lower, upper])
+    arr = vbd.MeshArrays(cat.rest, cat.tets, cat.young, cat.poisson, cat.density, cat.pinned, voff, toff)
+    ctx = vbd.vbd_create_mesh(arr.desc(), vbd.make_params())
+    try:
+        vbd.vbd_color(ctx, None)
+        size0 = vbd.vbd_workspace_size(ctx)
+        tris = vbd.vbd_get_surface(ctx)
+        assert np.array_equal(tris, orc.Model.from_mesh(cat).tris())
+        info = vbd.vbd_get_info(ctx)
+        assert info.n_surface_tris == len(tris)
+        assert info.n_surface_verts == len(np.unique(tris))
+        for bad in (dict(self_collision=True, dcd_radius=0.0), dict(self_collision=True, line_search=True)):
+            with pytest.raises(vbd.VbdError) as e:
+                vbd.vbd_set_params(ctx, vbd.make_params(**bad))
+            assert e.value.status == "VBD_ERR_INVALID_ARG"
+        vbd.vbd_set_params(ctx, vbd.make_params(self_collision=True, dcd_radius=0.02))
+        assert vbd.vbd_workspace_size(ctx) > size0
+    finally:
+        vbd.vbd_destroy(ctx)

@@ -1,0 +1,183 @@
+"""Self-collision (Sec. 3.5, vertex-triangle pairs with the penalty of Eq. 12)
+on the GPU against the FP64 oracle: the pairs the detection finds (index
+work, compared exactly where the choice is unique), the energy with contact
+terms, and whole trajectories with the same colouring (positions within
+1e-5 of the bounding-box diagonal)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2403_06321_b300 import synth, vbd
+from gpu_util import bbox_diag, params_of
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2403_06321_b300.build import build
+    build()
+    assert torch.cuda.is_available()
+
+
+def _f32(x):
+    return np.asarray(x, np.float32).astype(np.float64)
+
+
+def _pairs_agree(orc, model, p, x, tris, got, want):
+    """Exact agreement, except where the oracle's decision is not unique at
+    FP32 resolution: two triangles equally near (within 1e-5 r), or a vertex
+    that is paired on one side only and sits on the penetration boundary (its
+    nearest triangle within 1e-5 r) or at the detection distance."""
+    bad = np.nonzero(got != want)[0]
+    for a in bad:
+        dist = {}
+        for T in (got[a], want[a]):
+            if T >= 0:
+                q, _ = orc.closest_point_tri(x[a], *x[tris[T]])
+                dist[T] = np.linalg.norm(q - x[a])
+        if got[a] >= 0 and want[a] >= 0:
+            assert abs(dist[got[a]] - dist[want[a]]) <= 1e-5 * p.dcd_radius, a
+        else:
+            dT = dist[got[a] if got[a] >= 0 else want[a]]
+            assert min(dT, abs(dT - p.dcd_radius)) <= 1e-5 * p.dcd_radius, a
+    return len(bad)
+
+
+def _sim(m, pd, colors):
+    return vbd.Sim(m, vbd.make_params(**pd), colors=colors)
+
+
+@pytest.mark.parametrize("angle,sink", [(0.15, 0.1), (0.6, 0.35)])
+def test_detection_matches_oracle(orc, angle, sink):
+    m, cfg, _ = synth.colliding_slabs(n=14, angle=angle, sink=sink, seed=21)
+    pd = params_of(cfg)
+    x = _f32(m.rest)  # positions both sides hold exactly
+    model = orc.Model.from_mesh(m)
+    p = orc.Params.make(**pd)
+    want = model.dcd(p, x)
+    sim = _sim(m, pd, None)
+    try:
+        tris = vbd.vbd_get_surface(sim.ctx)
+        assert np.array_equal(tris, model.tris())
+        sim.set_state(x, np.zeros_like(x))
+        vbd.vbd_begin_step(sim.ctx, cfg.h)  # detection on x^t
+        got = vbd.vbd_get_contacts(sim.ctx, m.n_verts)
+        vbd.vbd_end_step(sim.ctx)
+        _, n_pairs = vbd.vbd_sync_status(sim.ctx, with_contacts=True)
+    finally:
+        sim.close()
+    assert (want >= 0).sum() > 100
+    assert n_pairs == int((got >= 0).sum())
+    n_bad = _pairs_agree(orc, model, p, x, tris, got, want)
+    print("detection angle %.2f sink %.2f: %d pairs, %d differ (ties)" % (angle, sink, (want >= 0).sum(), n_bad))
+    assert n_bad <= 2
+
+
+def test_energy_with_contacts_matches_oracle(orc):
+    m, cfg, u0 = synth.colliding_slabs(n=10, seed=22)
+    pd = params_of(cfg)
+    x = _f32(m.rest)
+    v = np.zeros_like(x)
+    v[u0:, 2] = -0.5
+    v = _f32(v)
+    sim = _sim(m, pd, None)
+    try:
+        sim.set_state(x, v)
+        vbd.vbd_begin_step(sim.ctx, cfg.h)
+        G_gpu = sim.energy()
+        xg, _ = sim.get_state()
+        xg = xg.cpu().numpy().astype(np.float64)
+        vbd.vbd_end_step(sim.ctx)
+    finally:
+        sim.close()
+    model = orc.Model.from_mesh(m)
+    p = orc.Params.make(**pd)
+    model.dcd(p, x)
+    y = model.inertia_target(p, cfg.h, x, v)
+    G0 = model.energy_G(p, cfg.h, xg, y)
+    G_nc = model.energy_G(orc.Params.make(**params_of(cfg, self_collision=False)), cfg.h, xg, y)
+    assert G0 - G_nc > 1e-3 * abs(G0)  # the contact terms matter here
+    assert G_gpu == pytest.approx(G0, rel=1e-5)
+
+
+@pytest.mark.parametrize("cheby", [0.0, 0.8])
+def test_slabs_trajectory_matches_oracle(orc, cheby):
+    """10 steps x 20 iterations of the slab scene (870 vertices, about 220
+    pairs per step); pairs compared at every step start."""
+    m, cfg, u0 = synth.colliding_slabs(seed=7)
+    pd = params_of(cfg, cheby_rho=cheby)
+    model = orc.Model.from_mesh(m)
+    p = orc.Params.make(**pd)
+    sim = _sim(m, pd, None)
+    try:
+        colors = vbd.vbd_get_colors(sim.ctx, m.n_verts)
+        nc = int(colors.max()) + 1
+        tris = vbd.vbd_get_surface(sim.ctx)
+        x = _f32(m.rest)
+        v = np.zeros_like(x)
+        vp = v.copy()
+        sim.set_state(x, v)
+        worst = 0.0
+        for step in range(cfg.steps):
+            vbd.vbd_begin_step(sim.ctx, cfg.h)
+            got = vbd.vbd_get_contacts(sim.ctx, m.n_verts)
+            vbd.vbd_iterate(sim.ctx, cfg.iters)
+            vbd.vbd_end_step(sim.ctx)
+            xt = x.copy()
+            model.step(p, colors, nc, cfg.h, cfg.iters, x, v, vp)  # DCD on x^t, then the iterations
+            want = model.contacts()
+            assert _pairs_agree(orc, model, p, xt, tris, got, want) == 0, step
+            assert (want >= 0).sum() > 20
+            xg, _ = sim.get_state()
+            worst = max(worst, float(np.abs(xg.cpu().numpy() - x).max()))
+        sim.sync_status()
+    finally:
+        sim.close()
+    err = worst / bbox_diag(m.rest)
+    print("slabs cheby %.1f: max |x_gpu - x_oracle| / bbox = %.3e" % (cheby, err))
+    assert np.abs(x - m.rest).max() > 1e-3  # the contact pushed the slabs apart
+    assert err <= TOL
+
+
+def test_block_rests_on_block_and_falls_through_without_contact(orc):
+    """The oracle's drop pin, on the GPU: with self-collision the upper block
+    comes to rest on the lower one; without it, it falls through."""
+    lower = synth.beam(3, 3, 1, edge=0.1, E=1e5, nu=0.4, pin_face="z-", jitter_frac=0.05, seed=102)
+    upper = synth.beam(2, 2, 1, edge=0.1, E=1e5, nu=0.4, pin_face=None, jitter_frac=0.05, seed=103,
+                       origin=(0.05, 0.05, 0.102))
+    cat, voff, _ = synth.concat([lower, upper])
+    v0 = np.zeros_like(cat.rest)
+    v0[voff[1]:, 2] = -1.0
+    for collide in (True, False):
+        pd = params_of(synth.SimConfig(k_c=1e5), self_collision=collide, dcd_radius=0.05)
+        sim = _sim(cat, pd, None)
+        try:
+            sim.set_state(cat.rest, v0)
+            for _ in range(20):
+                sim.step(1 / 60, 40)
+            sim.sync_status()
+            x, _ = sim.get_state()
+            zmin = float(x.cpu().numpy()[voff[1]:, 2].min())
+        finally:
+            sim.close()
+        if collide:
+            assert zmin > 0.1 - 0.01
+        else:
+            assert zmin < 0.0
+
+
+def test_self_collision_arguments(orc):
+    m, cfg, _ = synth.colliding_slabs(n=6)
+    sim = _sim(m, params_of(cfg, self_collision=False), None)
+    try:
+        with pytest.raises(vbd.VbdError) as e:  # the workspace has no contact arrays
+            vbd.vbd_set_params(sim.ctx, vbd.make_params(**params_of(cfg)))
+        assert e.value.status == "VBD_ERR_STATE"
+        with pytest.raises(vbd.VbdError) as e:
+            vbd.vbd_get_contacts(sim.ctx, m.n_verts)
+        assert e.value.status == "VBD_ERR_STATE"
+    finally:
+        sim.close()
