@@ -32,6 +32,8 @@ UNIT = "vertex-block updates/s"
 # algorithmic bytes per vertex-block update (per-incidence rest data + own
 # vertex I/O + one re-read of neighbour positions per colour pass)
 B_INC, B_VTX, B_X = 52, 44, 12
+B_SC = 24  # with self-collision: contact[i] and rev_off[i], rev_off[i+1], in the sweep and the copy-back
+DETECT_LAUNCHES = 20   # kernels and memsets of one self-collision detection (three prefix sums)
 CPU_SAMPLE_N = 32      # the CPU legs run a 32^3-cube crop of the same recipe
 CPU_SAMPLE_ITERS = 10
 
@@ -42,8 +44,10 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=100, help="cubes per side of the grid")
-    ap.add_argument("--iters", type=int, default=100)
+    ap.add_argument("--scene", choices=["cube", "slabs"], default="cube",
+                    help="cube: the large-cube drop (default); slabs: the self-collision slab scene")
+    ap.add_argument("--n", type=int, default=0, help="cubes per side (default 100 for cube, 300 for slabs)")
+    ap.add_argument("--iters", type=int, default=0, help="iterations per step (default 100 cube, 20 slabs)")
     ap.add_argument("--coloring", choices=["kuhn", "greedy"], default="kuhn")
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
@@ -57,9 +61,14 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batched and adjoint comparisons")
+                    help="skip the batched, adjoint and self-collision comparisons")
     ap.add_argument("--batch-meshes", type=int, default=4096)
-    return ap.parse_args(argv)
+    args = ap.parse_args(argv)
+    if not args.n:
+        args.n = 300 if args.scene == "slabs" else 100
+    if not args.iters:
+        args.iters = 20 if args.scene == "slabs" else 100
+    return args
 
 
 # ------------------------------------------------------------ distributed ---
@@ -246,15 +255,24 @@ def run_reference(args):
     return 0
 
 
-def workload_config(args, info) -> dict:
+def workload_config(args, info, mesh=None) -> dict:
     n = args.n
-    cfg = {"workload": "large_cube: %d^3 cubes x 6 tets (%d verts, %d tets), jitter 10%%, E=1e6 nu=0.45, "
-                       "drop 0.5 m onto ground k_c=1e7, h=1/60, %d iterations/step" % (
-                           n, (n + 1) ** 3, 6 * n ** 3, args.iters),
+    if args.scene == "slabs":
+        nv = (n + 1) ** 2 * 5 + (n - 1) ** 2 * 5
+        nt = 24 * (n * n + (n - 2) ** 2)
+        desc = ("colliding_slabs: %dx%dx4 + %dx%dx4 cubes x 6 tets (%d verts, %d tets), jitter 5%%, E=1e5 "
+                "nu=0.4, upper slab turned 0.15 rad and sunk 0.1 edge, self-collision r=0.5 edge k_c=1e5, "
+                "h=1/60, %d iterations/step" % (n, n, n - 2, n - 2, nv, nt, args.iters))
+    else:
+        desc = ("large_cube: %d^3 cubes x 6 tets (%d verts, %d tets), jitter 10%%, E=1e6 nu=0.45, "
+                "drop 0.5 m onto ground k_c=1e7, h=1/60, %d iterations/step" % (
+                    n, (n + 1) ** 3, 6 * n ** 3, args.iters))
+    n_tets = mesh.n_tets if mesh is not None else (nt if args.scene == "slabs" else 6 * n ** 3)
+    cfg = {"workload": desc,
            "iters_per_step": args.iters, "h": 1.0 / 60.0, "coloring": args.coloring,
            "variant": {"mu_c": args.mu_c, "line_search": bool(args.line_search), "jacobi": bool(args.jacobi),
-                       "young_override": args.young or None},
-           "l2": "inputs larger than L2 (slot stream %.2f GB per iteration)" % (6 * n ** 3 * 4 * 56 / 1e9)}
+                       "young_override": args.young or None, "self_collision": args.scene == "slabs"},
+           "l2": "inputs larger than L2 (slot stream %.2f GB per iteration)" % (n_tets * 4 * 48 / 1e9)}
     if info is not None:
         cfg.update({"n_colors": info.n_colors, "n_free_verts": info.n_free, "n_slots": int(info.n_slots),
                     "lanes_per_vertex": info.lanes_per_vertex, "block_threads": info.block_threads,
@@ -367,6 +385,55 @@ def run_adjoint(args) -> dict:
             "ratio_vs_plain": v_a / v_f, "ms_backward": t_a * 1e3, "ms_forward": t_f * 1e3}
 
 
+def run_self_collision(args) -> dict:
+    """Self-collision (vertex-triangle DCD at each step start, contact forces
+    in the sweep, x^new + copy-back per colour) on the slab scene at
+    300x300x4 + 298x298x4 cubes, against the same mesh and iterations with
+    self-collision off; plus the detection's own time per step."""
+    import numpy as np
+    import torch
+    from paper_2403_06321_b300 import synth, vbd
+    m, cfg, u0 = synth.colliding_slabs(n=300, layers=4, seed=31)
+    colors = synth.kuhn_coloring(m.grid_ijk)
+    h, iters, steps = cfg.h, cfg.iters, 5
+    out = {}
+    for sc in (True, False):
+        params = vbd.make_params(gravity=cfg.gravity, k_c=cfg.k_c, self_collision=sc, dcd_radius=cfg.dcd_radius)
+        stream = torch.cuda.Stream()
+        sim = vbd.Sim(m, params, colors=colors, stream=stream)
+        n_free = sim.info.n_free
+        sim.set_state(m.rest, np.zeros_like(m.rest))
+        for _ in range(2):
+            sim.step(h, iters)
+        vbd.vbd_sync_status(sim.ctx, with_contacts=True)
+        t = _timed(stream, lambda: sim.step(h, iters), steps)
+        _, pairs = vbd.vbd_sync_status(sim.ctx, with_contacts=True)
+        out[sc] = (n_free * iters * steps / t, t * 1e3 / steps, pairs / steps)
+        if sc:  # begin_step alone: detection + Eq. 3 prediction
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            tot = 0.0
+            for _ in range(steps):
+                torch.cuda.synchronize()
+                e0.record(stream)
+                vbd.vbd_begin_step(sim.ctx, h)
+                e1.record(stream)
+                vbd.vbd_iterate(sim.ctx, iters)
+                vbd.vbd_end_step(sim.ctx)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            out["begin_ms"] = tot / steps
+            info = sim.info
+        sim.sync_status()
+        sim.close()
+    return {"workload": "colliding slabs 300x300x4 + 298x298x4 cubes (%d verts, %d tets, %d boundary tris), "
+                        "r = 0.5 edge, k_c = 1e5, h=1/60, %d iterations/step, Kuhn 4-colouring" % (
+                            m.n_verts, m.n_tets, info.n_surface_tris, iters),
+            "value": out[True][0], "unit": UNIT, "ms_per_step": out[True][1],
+            "pairs_per_step": out[True][2], "detect_and_predict_ms_per_step": out["begin_ms"],
+            "value_without_self_collision": out[False][0], "ms_per_step_without": out[False][1],
+            "ratio_vs_plain": out[True][0] / out[False][0]}
+
+
 # --------------------------------------------------------------------- ours ---
 
 def run_ours(args):
@@ -383,13 +450,17 @@ def run_ours(args):
         build()
     barrier(world)
 
-    m, cfg = synth.large_cube(args.n)
+    if args.scene == "slabs":
+        m, cfg, _ = synth.colliding_slabs(n=args.n, layers=4, seed=31)
+    else:
+        m, cfg = synth.large_cube(args.n)
     if args.young > 0:
         m.young[:] = args.young
     colors = synth.kuhn_coloring(m.grid_ijk) if args.coloring == "kuhn" else None
     params = vbd.make_params(gravity=cfg.gravity, ground_on=cfg.ground_on, k_c=cfg.k_c,
                              init_mode=cfg.init_mode, det_eps=cfg.det_eps, mu_c=args.mu_c,
-                             line_search=args.line_search, jacobi=args.jacobi)
+                             line_search=args.line_search, jacobi=args.jacobi,
+                             self_collision=cfg.self_collision, dcd_radius=cfg.dcd_radius)
     stream = torch.cuda.Stream()
     sim = vbd.Sim(m, params, colors=colors, stream=stream)
     if args.lanes or args.block or args.pipeline >= 0:
@@ -470,28 +541,32 @@ def run_ours(args):
         bytes_per_launch = info.n_free * b_upd
     else:
         b_upd = inc_per_vert * B_INC + B_VTX + B_X * C
+        if args.scene == "slabs":
+            b_upd += B_SC  # pair index and corner-list offsets, read again by the copy-back
         launches_sweep = K * iters * C
         bytes_per_launch = info.n_free / C * b_upd
     avg_launch_s = sweep_ms / 1e3 / launches_sweep
     achieved = bytes_per_launch / avg_launch_s / 1e9
     peak, peak_kind = measured_peak_hbm()
-    traffic = profiled_traffic("large_cube")
+    traffic = profiled_traffic("large_cube") if args.scene == "cube" else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": t_job * 1e3 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic", "config": workload_config(args, info),
+        "dtype": "f32", "data": "synthetic", "config": workload_config(args, info, m),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
                      "kernel": ("k_sweep_pipe" if info.pipeline else "k_sweep") + " (one colour pass)", "alg_bytes_per_update": b_upd,
                      "avg_launch_us": avg_launch_s * 1e6,
                      "sweep_share_of_step": sweep_ms / t_ms},
         "e2e": e2e,
-        "gpu_launches": K * (2 + iters * (2 if args.jacobi else C)),
+        "gpu_launches": K * (2 + iters * (2 if args.jacobi else C)) if args.scene == "cube" else
+                        K * (2 + DETECT_LAUNCHES + iters * 2 * C),
         "clocks": clk,
     }
-    if not args.no_extras and world == 1:
+    if not args.no_extras and world == 1 and args.scene == "cube":
         line["batched"] = run_batched(args)
         line["adjoint"] = run_adjoint(args)
+        line["self_collision"] = run_self_collision(args)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = run_cpu_baseline()
     print(json.dumps(line), flush=True)

@@ -49,7 +49,8 @@ typedef enum {
     VBD_ERR_NONFINITE = 7,     /* a kernel met a non-finite position or solve */
     VBD_ERR_NO_TAPE = 8,       /* vbd_backward without recorded steps */
     VBD_ERR_STATE = 9,         /* call out of order (e.g. vbd_iterate before vbd_begin_step) */
-    VBD_ERR_TIMEOUT = 10       /* a bounded wait inside a kernel gave up; results are invalid */
+    VBD_ERR_TIMEOUT = 10,      /* a bounded wait inside a kernel gave up; results are invalid */
+    VBD_ERR_RANGE = 11         /* self-collision met positions beyond its grid's exact range */
 } vbd_status;
 
 typedef struct vbd_ctx vbd_ctx;
@@ -115,7 +116,10 @@ typedef struct {
  * triangle that shares no tet with it and lies within dcd_radius
  * (triangles within 1e-5 dcd_radius of the nearest distance count as tied;
  * the lowest index wins).  Boundary triangles are the tet
- * faces owned by one tet, oriented outward at rest.  During the step a pair
+ * faces owned by one tet, oriented outward at rest.  The detection grid
+ * works in FP32 with cells of about the element size: positions must stay
+ * within 65536 cells of the origin (else vbd_sync_status reports
+ * VBD_ERR_RANGE).  During the step a pair
  * with depth d = (q - x_a).n > 0 (q the nearest point of the triangle, w its
  * barycentric weights, n the unit normal at the current positions) adds the
  * penalty of Eq. 12 with the same k_c: k_c d n and k_c n n^T to vertex a,
@@ -258,7 +262,9 @@ vbd_status vbd_get_contacts(vbd_ctx *ctx, int32_t *contact_out);
 /* Waits for the stream and reads the device counters: VBD_ERR_TIMEOUT if a
  * bounded wait inside the pipelined sweep gave up (the step's results are
  * then invalid), else VBD_ERR_NONFINITE if any solve produced a non-finite
- * update since the last call (that update was not applied).  det_skips
+ * update since the last call (that update was not applied), else
+ * VBD_ERR_RANGE if the self-collision detection met positions beyond its
+ * grid's range (its pairs may then be incomplete).  det_skips
  * receives the singular-Hessian skips, contacts the self-collision pairs
  * found by detection, both summed since the last call; either may be NULL.
  * Synchronising. */

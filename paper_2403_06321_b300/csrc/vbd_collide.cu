@@ -7,12 +7,13 @@
 // 1e-5 r of the nearest distance count as tied and the lowest index wins.
 //
 // Broad phase: spatial hashes of triangle and tet centroids with one cell
-// size c = 1.01 max(R_tri + r, R_tet), R the largest centroid-to-corner
+// size c = 1.05 max(R_tri + r, R_tet), R the largest centroid-to-corner
 // distance of any triangle (tet) at this step.  A triangle within r of a
-// vertex, or a tet holding it, has its centroid within c of the vertex (the
-// element lies in the ball of radius R about its centroid), hence in one of
-// the 27 cells around the vertex's cell.  Each element is stored once
-// (count, prefix sum, fill), so the tables never overflow.
+// vertex, or a tet holding it, has its centroid within R + r (R) of the
+// vertex (the element lies in the ball of radius R about its centroid),
+// hence in one of the 27 cells around the vertex's cell; candidates whose
+// ball is out of reach are skipped before the exact tests.  Each element is
+// stored once (count, prefix sum, fill), so the tables never overflow.
 //
 // The sweep needs, for each free vertex, the pairs in which it is a triangle
 // corner: that reverse list is built the same way and then sorted per vertex
@@ -35,6 +36,7 @@ using geom::dot;
 using geom::f3;
 using geom::operator-;
 using geom::operator+;
+using geom::operator*;
 
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
@@ -42,178 +44,229 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 
 inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
-// The broad phase works in FP64 on x = X + u (both FP32, so the sum is exact):
-// cell indices then stay exact far from the origin.
-__device__ __forceinline__ double3 position(const Dev &d, int i) {
+// ---- broad phase ------------------------------------------------------------
+// FP32 throughout.  Cell coordinates floor(x / c) of a point and of an
+// element's centroid are exact enough while |x| / c < 2^16: the rounding of
+// x = X + u, of the centroid and of the product stays below 0.02 cells,
+// which the 5% margin of c covers, and below the 3% of c by which bounding
+// spheres are inflated.  Positions beyond that range are counted in
+// counters[4] (the host reports VBD_ERR_RANGE) and hashed after clamping.
+constexpr float kRange = 65536.0f;
+constexpr float kMargin = 1.05f;
+constexpr float kSlack = 0.03f;
+
+__device__ __forceinline__ float3 position(const Dev &d, int i) {
     const float4 X = __ldg(d.rest + i), u = __ldg(d.u + i);
-    return make_double3((double)X.x + u.x, (double)X.y + u.y, (double)X.z + u.z);
+    return make_float3(X.x + u.x, X.y + u.y, X.z + u.z);
 }
 
-// centroid of the first K corners of an element (K = 3 triangle, 4 tet)
-template <int K>
-__device__ __forceinline__ double3 centroid(const Dev &d, int4 v) {
-    const int c[4] = {v.x, v.y, v.z, v.w};
-    double3 m = make_double3(0.0, 0.0, 0.0);
-    for (int k = 0; k < K; ++k) {
-        const double3 p = position(d, c[k]);
-        m.x += p.x; m.y += p.y; m.z += p.z;
+__device__ __forceinline__ float cell_width(const Dev &d, float r) {
+    const float c = fmaxf(__uint_as_float(d.cell_size[0]) + r, __uint_as_float(d.cell_size[1]));
+    return kMargin * c + 1e-30f;
+}
+
+__device__ __forceinline__ int3 cell_of(const Dev &d, float3 p, float inv_c) {
+    float q[3] = {floorf(p.x * inv_c), floorf(p.y * inv_c), floorf(p.z * inv_c)};
+    bool ok = true;
+    for (int k = 0; k < 3; ++k) {
+        ok &= fabsf(q[k]) < kRange;  // false for NaN too
+        q[k] = fminf(fmaxf(q[k], -kRange), kRange);
+        if (q[k] != q[k]) q[k] = 0.0f;
     }
-    return make_double3(m.x / K, m.y / K, m.z / K);
+    if (!ok) atomicAdd(d.counters + 4, 1ull);
+    return make_int3((int)q[0], (int)q[1], (int)q[2]);
 }
 
-__device__ __forceinline__ double inv_cell_width(const Dev &d, float r) {
-    const double c = fmax((double)__uint_as_float(d.cell_size[0]) + r, (double)__uint_as_float(d.cell_size[1]));
-    return 1.0 / (1.01 * c + 1e-300);
+__device__ __forceinline__ int bucket_of(int i, int j, int k, int nb) {
+    unsigned h = (unsigned)i * 73856093u ^ (unsigned)j * 19349663u ^ (unsigned)k * 83492791u;
+    h ^= h >> 16;
+    h *= 0x7feb352du;
+    h ^= h >> 15;
+    return (int)(h & (unsigned)(nb - 1));
 }
 
-__device__ __forceinline__ long long cell_coord(double x, double inv_c) {
-    // clamp so that the conversion is defined for any finite or infinite input
-    const double q = fmin(fmax(floor(x * inv_c), -1.0e15), 1.0e15);
-    return (long long)q;
-}
-
-__device__ __forceinline__ int bucket_of(long long i, long long j, long long k, int nb) {
-    unsigned long long h = (unsigned long long)i * 0x9E3779B97F4A7C15ull;
-    h ^= (unsigned long long)j * 0xC2B2AE3D27D4EB4Full + (h << 6) + (h >> 2);
-    h ^= (unsigned long long)k * 0x165667B19E3779F9ull + (h << 6) + (h >> 2);
-    h ^= h >> 31;
-    return (int)(h & (unsigned long long)(nb - 1));
-}
-
-// largest centroid-to-corner distance of the elements, as float bits (the
-// values are non-negative, so unsigned order is float order)
+// Bounding sphere of each element (K = 3 triangle, 4 tet): centroid and the
+// largest centroid-to-corner distance; the largest radius goes to *rmax (as
+// float bits: non-negative floats order like their unsigned bits).
 template <int K>
-__global__ void k_radius(Dev d, const int4 *items, int n, unsigned *out) {
+__global__ void k_bounds(Dev d, const int4 *items, int n, float4 *sphere, unsigned *rmax) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     const int4 v = items[t];
-    const double3 m = centroid<K>(d, v);
     const int c[4] = {v.x, v.y, v.z, v.w};
-    double R2 = 0.0;
+    float3 p[K];
+    float3 m = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
     for (int k = 0; k < K; ++k) {
-        const double3 p = position(d, c[k]);
-        const double dx = p.x - m.x, dy = p.y - m.y, dz = p.z - m.z;
-        R2 = fmax(R2, dx * dx + dy * dy + dz * dz);
+        p[k] = position(d, c[k]);
+        m = m + p[k];
     }
-    float R = (float)sqrt(R2);
+    m = (1.0f / K) * m;
+    float R2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float3 e = p[k] - m;
+        R2 = fmaxf(R2, dot(e, e));
+    }
+    float R = sqrtf(R2);
     if (!(R >= 0.f)) R = 0.f;  // a NaN position never widens the cells
-    atomicMax(out, __float_as_uint(R));
+    sphere[t] = make_float4(m.x, m.y, m.z, R);
+    atomicMax(rmax, __float_as_uint(R));
 }
 
-template <int K>
-__device__ __forceinline__ int item_bucket(const Dev &d, int4 v, double inv_c, int nb) {
-    const double3 m = centroid<K>(d, v);
-    return bucket_of(cell_coord(m.x, inv_c), cell_coord(m.y, inv_c), cell_coord(m.z, inv_c), nb);
+__device__ __forceinline__ int sphere_bucket(const Dev &d, float4 s, float inv_c, int nb) {
+    const int3 q = cell_of(d, make_float3(s.x, s.y, s.z), inv_c);
+    return bucket_of(q.x, q.y, q.z, nb);
 }
 
-template <int K>
-__global__ void k_count(Dev d, const int4 *items, int n, int nb, float r, int *count) {
+__global__ void k_count(Dev d, const float4 *sphere, int n, int nb, float r, int *count) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
-    atomicAdd(count + item_bucket<K>(d, items[t], inv_cell_width(d, r), nb), 1);
+    atomicAdd(count + sphere_bucket(d, sphere[t], 1.0f / cell_width(d, r), nb), 1);
 }
 
-template <int K>
-__global__ void k_fill(Dev d, const int4 *items, int n, int nb, float r, const int *start, int *fill,
+__global__ void k_fill(Dev d, const float4 *sphere, int n, int nb, float r, const int *start, int *fill,
                        int *entries) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
-    const int b = item_bucket<K>(d, items[t], inv_cell_width(d, r), nb);
+    const int b = sphere_bucket(d, sphere[t], 1.0f / cell_width(d, r), nb);
     entries[start[b] + atomicAdd(fill + b, 1)] = t;
 }
 
+// ---- narrow phase -------------------------------------------------------------
 // Whether the origin lies in the closed tet with corners p0..p3 (positions
-// relative to the vertex): its barycentric coordinates, from the edge matrix
-// E = [p1 - p0, p2 - p0, p3 - p0] by Cramer's rule, are all >= 0.
+// relative to the vertex): its barycentric coordinates d_k / D, from the edge
+// matrix [p1 - p0, p2 - p0, p3 - p0] by Cramer's rule, are all >= 0 and sum
+// to at most 1 (compared without dividing).
 __device__ __forceinline__ bool origin_in_tet(float3 p0, float3 p1, float3 p2, float3 p3) {
     const float3 e1 = p1 - p0, e2 = p2 - p0, e3 = p3 - p0;
     const float3 r = make_float3(-p0.x, -p0.y, -p0.z);
-    const float D = dot(e1, cross(e2, e3));
+    float D = dot(e1, cross(e2, e3));
     if (D == 0.0f) return false;
-    const float l1 = dot(r, cross(e2, e3)) / D;
-    const float l2 = dot(e1, cross(r, e3)) / D;
-    const float l3 = dot(e1, cross(e2, r)) / D;
-    return l1 >= 0.0f && l2 >= 0.0f && l3 >= 0.0f && 1.0f - (l1 + l2 + l3) >= 0.0f;
+    float d1 = dot(r, cross(e2, e3)), d2 = dot(e1, cross(r, e3)), d3 = dot(e1, cross(e2, r));
+    if (D < 0.0f) {
+        D = -D; d1 = -d1; d2 = -d2; d3 = -d3;
+    }
+    return d1 >= 0.0f && d2 >= 0.0f && d3 >= 0.0f && d1 + d2 + d3 <= D;
 }
 
-// the 27 buckets around a cell, each once (two neighbour cells may share one)
-__device__ __forceinline__ int neighbour_buckets(long long ci, long long cj, long long ck, int nb, int out[27]) {
-    int n = 0;
-    for (int di = -1; di <= 1; ++di)
-        for (int dj = -1; dj <= 1; ++dj)
-            for (int dk = -1; dk <= 1; ++dk) {
-                const int b = bucket_of(ci + di, cj + dj, ck + dk, nb);
-                bool dup = false;
-                for (int q = 0; q < n; ++q) dup |= (out[q] == b);
-                if (!dup) out[n++] = b;
-            }
-    return n;
+// bucket of the n-th of the 27 cells around c (n = 0..26)
+__device__ __forceinline__ int neighbour_bucket(int3 c, int n, int nb) {
+    return bucket_of(c.x + n % 3 - 1, c.y + (n / 3) % 3 - 1, c.z + n / 9 - 1, nb);
 }
 
 __device__ __forceinline__ float3 rel(const Dev &d, int k, float3 Xa, float3 ua) {
     return (f3(__ldg(d.rest + k)) - Xa) + (f3(__ldg(d.u + k)) - ua);
 }
 
-// one thread per boundary vertex: penetration test, then the nearest
-// admissible triangle within r
-__global__ void k_query(Dev d, int n_surf, int nb_tri, int nb_tet, float r) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n_surf) return;
-    const int a = d.surf[k];
-    const double inv_c = inv_cell_width(d, r);
-    const double3 xa = position(d, a);
-    const long long ci = cell_coord(xa.x, inv_c), cj = cell_coord(xa.y, inv_c), ck = cell_coord(xa.z, inv_c);
-    const float3 Xa = f3(__ldg(d.rest + a)), ua = f3(__ldg(d.u + a));
-    int bk[27];
-    // penetration: inside a tet that does not hold the vertex
-    int nbk = neighbour_buckets(ci, cj, ck, nb_tet, bk);
-    bool inside = false;
-    for (int q = 0; q < nbk && !inside; ++q) {
-        const int e1 = d.tet_start[bk[q] + 1];
-        for (int e = d.tet_start[bk[q]]; e < e1 && !inside; ++e) {
-            const int4 v = d.tet_v[d.cell_tet[e]];
-            if (v.x == a || v.y == a || v.z == a || v.w == a) continue;
-            inside = origin_in_tet(rel(d, v.x, Xa, ua), rel(d, v.y, Xa, ua), rel(d, v.z, Xa, ua),
-                                   rel(d, v.w, Xa, ua));
+__device__ __forceinline__ bool sphere_far(float4 s, float3 x, float reach) {
+    const float3 e = make_float3(s.x - x.x, s.y - x.y, s.z - x.z);
+    const float lim = s.w + reach;
+    return dot(e, e) > lim * lim;
+}
+
+// Nearest admissible triangle of vertex a (boundary index k) among the
+// triangles of this lane's neighbour cells (n = lane, lane + Q, ... < 27):
+// pass 0 returns the nearest distance within r (or -1), pass 1 the lowest
+// triangle index within `lim` (or -1).  Triangles whose bounding sphere is
+// farther than r (plus the rounding slack) are skipped before the exact test.
+template <int Q>
+__device__ __forceinline__ float nearest_tri(const Dev &d, int k, float3 xa, float3 Xa, float3 ua, int3 cell,
+                                            int nb, int lane, float r, float slack, int pass, float lim,
+                                            int &pair) {
+    const int g0 = d.ring_off[k], g1 = d.ring_off[k + 1];
+    float best = -1.f;
+    for (int n = lane; n < 27; n += Q) {
+        const int b = neighbour_bucket(cell, n, nb);
+        const int e1 = d.cell_start[b + 1];
+        for (int e = d.cell_start[b]; e < e1; ++e) {
+            const int t = d.cell_tri[e];
+            if (pass == 1 && pair >= 0 && t >= pair) continue;
+            if (sphere_far(d.tri_sphere[t], xa, r + slack)) continue;
+            const int4 v = d.tri[t];
+            bool adjacent = false;
+            for (int g = g0; g < g1 && !adjacent; ++g) {
+                const int w = d.ring[g];
+                adjacent = (w == v.x) | (w == v.y) | (w == v.z);
+            }
+            if (adjacent) continue;
+            const float3 pa = rel(d, v.x, Xa, ua), pb = rel(d, v.y, Xa, ua), pc = rel(d, v.z, Xa, ua);
+            const float3 w = geom::nearest_weights(pa, pb, pc);
+            const float3 qp = make_float3(w.x * pa.x + w.y * pb.x + w.z * pc.x, w.x * pa.y + w.y * pb.y + w.z * pc.y,
+                                          w.x * pa.z + w.y * pb.z + w.z * pc.z);
+            const float dist = sqrtf(dot(qp, qp));
+            if (dist > r) continue;
+            if (pass == 0 && (best < 0.f || dist < best)) best = dist;
+            if (pass == 1 && dist <= lim) pair = t;
         }
     }
+    return best;
+}
+
+// Q lanes per boundary vertex, each taking every Q-th of the 27 neighbour
+// cells; their results are combined with shuffles (a minimum distance, an
+// "any" and a minimum index), so the outcome does not depend on the split.
+// The pair exists when a triangle lies within r and the vertex has
+// penetrated; the triangle search runs first, so that the tet test runs
+// only for the (few) vertices near another surface.
+constexpr int kQueryLanes = 8;
+
+__device__ __forceinline__ float group_min_dist(float v) {  // -1 = none
+#pragma unroll
+    for (int off = kQueryLanes / 2; off > 0; off >>= 1) {
+        const float o = __shfl_xor_sync(0xffffffffu, v, off);
+        if (o >= 0.f && (v < 0.f || o < v)) v = o;
+    }
+    return v;
+}
+
+__device__ __forceinline__ int group_min_index(int v) {  // -1 = none
+#pragma unroll
+    for (int off = kQueryLanes / 2; off > 0; off >>= 1) {
+        const int o = __shfl_xor_sync(0xffffffffu, v, off);
+        if (o >= 0 && (v < 0 || o < v)) v = o;
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(128) k_query(Dev d, int n_surf, int nb_tri, int nb_tet, float r) {
+    constexpr int Q = kQueryLanes;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = (int)(g / Q), lane = (int)(g % Q);
+    const bool active = k < n_surf;  // inactive lanes still join the shuffles
+    const int a = active ? d.surf[k] : 0;
+    const float c = cell_width(d, r);
+    const float slack = kSlack * c;
+    const float3 Xa = f3(__ldg(d.rest + a)), ua = f3(__ldg(d.u + a));
+    const float3 xa = Xa + ua;
+    const int3 cell = active ? cell_of(d, xa, 1.0f / c) : make_int3(0, 0, 0);
     int pair = -1;
-    if (inside) {
-        // pass 0: the nearest distance; pass 1: the lowest index within
-        // 1e-5 r of it (a nearest point on a shared edge or corner is equally
-        // near several triangles; rounding must not choose)
-        const int g0 = d.ring_off[k], g1 = d.ring_off[k + 1];
-        float best = -1.f;
-        nbk = neighbour_buckets(ci, cj, ck, nb_tri, bk);
-        for (int pass = 0; pass < 2 && !(pass == 1 && best < 0.f); ++pass) {
-            const float lim = best + 1e-5f * r;
-            for (int q = 0; q < nbk; ++q) {
-                const int e1 = d.cell_start[bk[q] + 1];
-                for (int e = d.cell_start[bk[q]]; e < e1; ++e) {
-                    const int t = d.cell_tri[e];
-                    if (pass == 1 && pair >= 0 && t >= pair) continue;
-                    const int4 v = d.tri[t];
-                    bool adjacent = false;
-                    for (int g = g0; g < g1 && !adjacent; ++g) {
-                        const int w = d.ring[g];
-                        adjacent = (w == v.x) | (w == v.y) | (w == v.z);
-                    }
-                    if (adjacent) continue;
-                    const float3 pa = rel(d, v.x, Xa, ua), pb = rel(d, v.y, Xa, ua), pc = rel(d, v.z, Xa, ua);
-                    const float3 w = geom::nearest_weights(pa, pb, pc);
-                    const float3 qp = make_float3(w.x * pa.x + w.y * pb.x + w.z * pc.x,
-                                                  w.x * pa.y + w.y * pb.y + w.z * pc.y,
-                                                  w.x * pa.z + w.y * pb.z + w.z * pc.z);
-                    const float dist = sqrtf(dot(qp, qp));
-                    if (dist > r) continue;
-                    if (pass == 0 && (best < 0.f || dist < best)) best = dist;
-                    if (pass == 1 && dist <= lim) pair = t;
-                }
+    float best = active ? nearest_tri<Q>(d, k, xa, Xa, ua, cell, nb_tri, lane, r, slack, 0, 0.f, pair) : -1.f;
+    best = group_min_dist(best);
+    bool inside = false;
+    if (best >= 0.f) {  // uniform over the group
+        // penetration: inside a tet that does not hold the vertex
+        for (int n = lane; n < 27 && !inside; n += Q) {
+            const int b = neighbour_bucket(cell, n, nb_tet);
+            const int e1 = d.tet_start[b + 1];
+            for (int e = d.tet_start[b]; e < e1 && !inside; ++e) {
+                const int j = d.cell_tet[e];
+                if (sphere_far(d.tet_sphere[j], xa, slack)) continue;
+                const int4 v = d.tet_v[j];
+                if (v.x == a || v.y == a || v.z == a || v.w == a) continue;
+                inside = origin_in_tet(rel(d, v.x, Xa, ua), rel(d, v.y, Xa, ua), rel(d, v.z, Xa, ua),
+                                       rel(d, v.w, Xa, ua));
             }
         }
     }
-    d.contact[a] = pair;
-    if (pair >= 0) atomicAdd(d.counters + 3, 1ull);
+    const unsigned group_mask = ((1u << Q) - 1u) << (threadIdx.x & 31 & ~(Q - 1));
+    inside = (__ballot_sync(0xffffffffu, inside) & group_mask) != 0;
+    if (inside) nearest_tri<Q>(d, k, xa, Xa, ua, cell, nb_tri, lane, r, slack, 1, best + 1e-5f * r, pair);
+    pair = group_min_index(pair);
+    if (active && lane == 0) {
+        d.contact[a] = pair;
+        if (pair >= 0) atomicAdd(d.counters + 3, 1ull);
+    }
 }
 
 __global__ void k_rev_count(Dev d, int n_surf, int n_free, int *count) {
@@ -337,25 +390,27 @@ int scan_tmp_needed(int n) { return (int)blocks_for(std::max(n, 1), kScanTile) +
 
 void launch_detect(const Dev &d, const CollideDims &c, int n_free, cudaStream_t s) {
     if (c.n_surf <= 0 || c.n_tris <= 0) return;
-    // broad phase: cell size, then triangles and tets bucketed by centroid cell
+    // broad phase: bounding spheres and the cell size, then triangles and
+    // tets bucketed by the cell of their centre
     cudaMemsetAsync(d.cell_size, 0, 2 * sizeof(unsigned), s);
-    k_radius<3><<<blocks_for(c.n_tris, 256), 256, 0, s>>>(d, d.tri, c.n_tris, d.cell_size);
-    k_radius<4><<<blocks_for(c.n_tets, 256), 256, 0, s>>>(d, d.tet_v, c.n_tets, d.cell_size + 1);
+    k_bounds<3><<<blocks_for(c.n_tris, 256), 256, 0, s>>>(d, d.tri, c.n_tris, d.tri_sphere, d.cell_size);
+    k_bounds<4><<<blocks_for(c.n_tets, 256), 256, 0, s>>>(d, d.tet_v, c.n_tets, d.tet_sphere, d.cell_size + 1);
     cudaMemsetAsync(d.cell_fill, 0, sizeof(int) * (size_t)c.n_buckets, s);
-    k_count<3><<<blocks_for(c.n_tris, 256), 256, 0, s>>>(d, d.tri, c.n_tris, c.n_buckets, c.radius, d.cell_fill);
+    k_count<<<blocks_for(c.n_tris, 256), 256, 0, s>>>(d, d.tri_sphere, c.n_tris, c.n_buckets, c.radius, d.cell_fill);
     exclusive_scan(d.cell_fill, d.cell_start, c.n_buckets, d.scan_tmp, s);
     cudaMemsetAsync(d.cell_fill, 0, sizeof(int) * (size_t)c.n_buckets, s);
-    k_fill<3><<<blocks_for(c.n_tris, 256), 256, 0, s>>>(d, d.tri, c.n_tris, c.n_buckets, c.radius, d.cell_start,
-                                                         d.cell_fill, d.cell_tri);
+    k_fill<<<blocks_for(c.n_tris, 256), 256, 0, s>>>(d, d.tri_sphere, c.n_tris, c.n_buckets, c.radius, d.cell_start,
+                                                     d.cell_fill, d.cell_tri);
     cudaMemsetAsync(d.tet_fill, 0, sizeof(int) * (size_t)c.n_tet_buckets, s);
-    k_count<4><<<blocks_for(c.n_tets, 256), 256, 0, s>>>(d, d.tet_v, c.n_tets, c.n_tet_buckets, c.radius,
-                                                          d.tet_fill);
+    k_count<<<blocks_for(c.n_tets, 256), 256, 0, s>>>(d, d.tet_sphere, c.n_tets, c.n_tet_buckets, c.radius,
+                                                      d.tet_fill);
     exclusive_scan(d.tet_fill, d.tet_start, c.n_tet_buckets, d.scan_tmp, s);
     cudaMemsetAsync(d.tet_fill, 0, sizeof(int) * (size_t)c.n_tet_buckets, s);
-    k_fill<4><<<blocks_for(c.n_tets, 256), 256, 0, s>>>(d, d.tet_v, c.n_tets, c.n_tet_buckets, c.radius,
-                                                         d.tet_start, d.tet_fill, d.cell_tet);
+    k_fill<<<blocks_for(c.n_tets, 256), 256, 0, s>>>(d, d.tet_sphere, c.n_tets, c.n_tet_buckets, c.radius,
+                                                     d.tet_start, d.tet_fill, d.cell_tet);
     // narrow phase
-    k_query<<<blocks_for(c.n_surf, 128), 128, 0, s>>>(d, c.n_surf, c.n_buckets, c.n_tet_buckets, c.radius);
+    k_query<<<blocks_for((long long)c.n_surf * kQueryLanes, 128), 128, 0, s>>>(d, c.n_surf, c.n_buckets,
+                                                                              c.n_tet_buckets, c.radius);
     // reverse lists for the sweep
     if (n_free <= 0) return;
     cudaMemsetAsync(d.rev_fill, 0, sizeof(int) * (size_t)n_free, s);

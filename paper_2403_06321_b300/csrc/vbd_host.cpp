@@ -278,6 +278,8 @@ size_t carve(const vbd_ctx *c, char *base, Dev *d) {
         t.rev_off = (int *)take(4 * (nf + 1));
         t.rev = (int *)take(4 * 3 * ns);
         t.rev_fill = (int *)take(4 * nf);
+        t.tri_sphere = (float4 *)take(16 * nt);
+        t.tet_sphere = (float4 *)take(16 * T);
         t.cell_start = (int *)take(4 * (nb + 1));
         t.cell_fill = (int *)take(4 * nb);
         t.cell_tri = (int *)take(4 * nt);
@@ -319,7 +321,7 @@ SweepParams sweep_params(const vbd_ctx *c, int color) {
     p.line_search = c->params.line_search ? 1 : 0;
     p.per_tet_mat = c->per_tet_mat ? 1 : 0;
     p.self_collision = c->params.self_collision && c->sc_carved ? 1 : 0;
-    p.to_unew = (c->params.jacobi || p.self_collision) ? 1 : 0;
+    p.to_unew = c->params.jacobi ? 1 : 0;
     if (c->params.jacobi && color >= 0) {  // one pass over every free vertex
         p.vbegin = 0;
         p.vend = c->n_free;
@@ -389,14 +391,14 @@ vbd_status prepare_pipeline(vbd_ctx *ctx) {
 }
 
 // One colour pass.  With self-collision two vertices of one colour can be
-// coupled through a contact pair, so the pass writes x^new (Algorithm 1) to
-// d.unew and copies it back afterwards; the pipelined kernel has no contact
-// forces, so that path always uses k_sweep.
+// coupled through a contact pair, so the vertices in pairs write x^new
+// (Algorithm 1) to d.unew, copied back afterwards; the pipelined kernel has
+// no contact forces, so that path always uses k_sweep.
 void launch_colour(vbd_ctx *c, int col, cudaStream_t s) {
     const SweepParams p = sweep_params(c, col);
     if (p.self_collision) {
         vbd::launch_sweep(c->d, p, c->lanes, c->block, s);
-        vbd::launch_copy_back(c->d, p.vbegin, p.vend, s);
+        vbd::launch_copy_back(c->d, p.vbegin, p.vend, !p.to_unew, s);
     } else if (c->pipeline) {
         vbd::launch_sweep_pipe(c->d, p, c->pipe_block, c->pipe_maxs, c->pipe_grid_cap, s);
     } else {
@@ -410,7 +412,7 @@ void enqueue_iterations(vbd_ctx *c, int first_n, int iters, cudaStream_t s) {
     for (int n = first_n + 1; n <= first_n + iters; ++n) {
         if (c->params.jacobi) {
             vbd::launch_sweep(c->d, sweep_params(c, 0), c->lanes, c->block, s);
-            vbd::launch_copy_back(c->d, 0, c->n_free, s);
+            vbd::launch_copy_back(c->d, 0, c->n_free, false, s);
         } else {
             for (int col = 0; col < c->n_colors; ++col)
                 launch_colour(c, col, s);
@@ -1136,6 +1138,9 @@ vbd_status vbd_sync_status(vbd_ctx *ctx, int64_t *det_skips, int64_t *contacts) 
     if (det_skips) *det_skips = (int64_t)c[1];
     if (contacts) *contacts = (int64_t)c[3];
     if (c[2] > 0) return fail(ctx, VBD_ERR_TIMEOUT, std::to_string(c[2]) + " pipelined-sweep waits timed out");
+    if (c[4] > 0)
+        return fail(ctx, VBD_ERR_RANGE, std::to_string(c[4]) +
+                                            " positions beyond the self-collision grid (|x| >= 65536 cells)");
     if (c[0] > 0) return fail(ctx, VBD_ERR_NONFINITE, std::to_string(c[0]) + " non-finite updates");
     return VBD_OK;
 }

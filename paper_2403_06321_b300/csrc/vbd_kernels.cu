@@ -116,52 +116,50 @@ __device__ __forceinline__ float sub_reduce(float v) {
     return v;
 }
 
-// Vertex-triangle contact forces on vertex vi (Sec. 3.5, penalty of Eq. 12),
-// added to f and H (upper triangle h00 h01 h02 h11 h12 h22).  As the vertex of
-// its own pair: k_c d n and k_c n n^T.  As corner k of another vertex's
-// triangle: -k_c d w_k n and k_c w_k^2 n n^T.  Only pairs with d > 0 act.
-// Positions come from d.u, which holds the pass-start state: the colour's
-// updates go to d.unew and are copied back after the pass.  Returns whether
-// any pair acted.
-__device__ __forceinline__ bool add_self_contact(const Dev &d, float kc, int vi, float &f0, float &f1, float &f2,
-                                                 float &h00, float &h01, float &h02, float &h11, float &h12,
-                                                 float &h22) {
-    bool hit = false;
-    auto add = [&](float3 n, float fs, float hs) {
-        f0 += fs * n.x; f1 += fs * n.y; f2 += fs * n.z;
-        h00 += hs * n.x * n.x; h01 += hs * n.x * n.y; h02 += hs * n.x * n.z;
-        h11 += hs * n.y * n.y; h12 += hs * n.y * n.z; h22 += hs * n.z * n.z;
-    };
-    const int T = d.contact[vi];
-    if (T >= 0) {
-        float3 n, w;
-        const float dep = geom::pair_depth(d, vi, d.tri[T], n, w);
-        if (dep > 0.0f) {
-            add(n, kc * dep, kc);
-            hit = true;
-        }
+// Vertex-triangle contact forces on vertex vi (Sec. 3.5, penalty of Eq. 12).
+// Its items are its own pair (if any) and the pairs in which it is a
+// triangle corner (d.rev, ascending).  As the vertex of its own pair it gets
+// k_c d n and k_c n n^T; as corner k of another vertex's triangle, -k_c d
+// w_k n and k_c w_k^2 n n^T; only pairs with d > 0 act.  The L lanes of the
+// vertex take the items in turn and their sums are reduced like the slots.
+// Positions come from d.u: a vertex in any pair ("involved") writes its
+// update to d.unew, copied back after the pass, so that d.u keeps the
+// pass-start positions its partners read (x^new of Algorithm 1); partners
+// of an involved vertex are involved too, and other vertices of the colour
+// touch only other colours, so they update in place.
+__device__ __forceinline__ bool contact_item(const Dev &d, float kc, int vi, int own, int item, int r0, Acc &c) {
+    int a, k = -1;
+    int4 t;
+    if (item == 0 && own >= 0) {
+        a = vi;
+        t = d.tri[own];
+    } else {
+        a = d.rev[r0 + item - (own >= 0 ? 1 : 0)];
+        t = d.tri[d.contact[a]];
+        k = (t.x == vi) ? 0 : ((t.y == vi) ? 1 : 2);
     }
-    const int r1 = d.rev_off[vi + 1];
-    for (int r = d.rev_off[vi]; r < r1; ++r) {
-        const int a = d.rev[r];
-        const int4 t = d.tri[d.contact[a]];
-        float3 n, w;
-        const float dep = geom::pair_depth(d, a, t, n, w);
-        if (dep > 0.0f) {
-            const float wk = (t.x == vi) ? w.x : ((t.y == vi) ? w.y : w.z);
-            add(n, -kc * dep * wk, kc * wk * wk);
-            hit = true;
-        }
+    float3 n, w;
+    const float dep = geom::pair_depth(d, a, t, n, w);
+    if (!(dep > 0.0f)) return false;
+    float fs = kc * dep, hs = kc;
+    if (k >= 0) {
+        const float wk = k == 0 ? w.x : (k == 1 ? w.y : w.z);
+        fs = -fs * wk;
+        hs = kc * wk * wk;
     }
-    return hit;
+    c.f0 += fs * n.x; c.f1 += fs * n.y; c.f2 += fs * n.z;
+    c.h00 += hs * n.x * n.x; c.h01 += hs * n.x * n.y; c.h02 += hs * n.x * n.z;
+    c.h11 += hs * n.y * n.y; c.h12 += hs * n.y * n.z; c.h22 += hs * n.z * n.z;
+    return true;
 }
 
 // Local solve of Sec. 3.2 for one vertex: Eq. 7 with the inertia terms of
 // Eqs. 8-9, damping (Eqs. 10-11), ground penalty (Eq. 12), self-contact,
 // singular skip, analytic inverse.
+// sc: self-contact sums (f, H) and bit 0 = some pair acted, bit 1 = involved
 template <bool SC>
 __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams &p, int vi, float4 xi,
-                                                const Acc &a) {
+                                                const Acc &a, const Acc &ca, int sc) {
     // xi holds the displacement u_i; ym the displacement of the inertia target
     const float4 yv = d.ym[vi];
     const float mh2 = yv.w;
@@ -209,8 +207,14 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
             }
         }
     }
-    if (SC && add_self_contact(d, p.kc, vi, f0, f1, f2, h00, h01, h02, h11, h12, h22)) flag = 1.0f;
-    float4 *out = p.to_unew ? d.unew : d.u;
+    bool stage = p.to_unew != 0;  // write to d.unew (copied back after the pass)
+    if (SC && (sc & 2)) {
+        f0 += ca.f0; f1 += ca.f1; f2 += ca.f2;
+        h00 += ca.h00; h01 += ca.h01; h02 += ca.h02; h11 += ca.h11; h12 += ca.h12; h22 += ca.h22;
+        if (sc & 1) flag = 1.0f;
+        stage = true;
+    }
+    float4 *out = stage ? d.unew : d.u;
     // adjugate of the symmetric H
     const float a00 = h11 * h22 - h12 * h12;
     const float a01 = h02 * h12 - h01 * h22;
@@ -222,7 +226,7 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
     const float tr3 = (h00 + h11 + h22) * (1.0f / 3.0f);
     if (!(fabsf(det) > p.det_eps * fabsf(tr3 * tr3 * tr3))) {
         atomicAdd(d.counters + 1, 1ull);
-        if (p.to_unew || flag != xi.w) out[vi] = make_float4(xi.x, xi.y, xi.z, flag);
+        if (stage || flag != xi.w) out[vi] = make_float4(xi.x, xi.y, xi.z, flag);
         return;
     }
     const float inv = 1.0f / det;
@@ -231,7 +235,7 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
     float dz = (a02 * f0 + a12 * f1 + a22 * f2) * inv;
     if (!(isfinite(dx) && isfinite(dy) && isfinite(dz))) {
         atomicAdd(d.counters + 0, 1ull);
-        if (p.to_unew) out[vi] = xi;
+        if (stage) out[vi] = xi;
         return;
     }
     if (p.line_search) {
@@ -268,7 +272,7 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
 }
 
 template <int L, bool SC>
-__global__ void __launch_bounds__(256) k_sweep(Dev d, SweepParams p) {
+__device__ __forceinline__ void sweep_body(const Dev &d, const SweepParams &p) {
     const int lane = threadIdx.x & (L - 1);
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int vi = p.vbegin + (int)(gt / L);
@@ -294,7 +298,46 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, SweepParams p) {
     acc.h11 = sub_reduce<L>(acc.h11);
     acc.h12 = sub_reduce<L>(acc.h12);
     acc.h22 = sub_reduce<L>(acc.h22);
-    if (active && lane == 0) solve_and_store<SC>(d, p, vi, xi, acc);
+    Acc ca = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int sc = 0;
+    if (SC) {
+        int own = -1, r0 = 0, n_items = 0;
+        if (active) {
+            own = d.contact[vi];
+            r0 = d.rev_off[vi];
+            n_items = (own >= 0 ? 1 : 0) + (d.rev_off[vi + 1] - r0);
+        }
+        int hit = 0;
+        for (int it = lane; it < n_items; it += L)
+            hit |= contact_item(d, p.kc, vi, own, it, r0, ca) ? 1 : 0;
+        if (__any_sync(FULL, n_items > 0)) {
+            ca.f0 = sub_reduce<L>(ca.f0);
+            ca.f1 = sub_reduce<L>(ca.f1);
+            ca.f2 = sub_reduce<L>(ca.f2);
+            ca.h00 = sub_reduce<L>(ca.h00);
+            ca.h01 = sub_reduce<L>(ca.h01);
+            ca.h02 = sub_reduce<L>(ca.h02);
+            ca.h11 = sub_reduce<L>(ca.h11);
+            ca.h12 = sub_reduce<L>(ca.h12);
+            ca.h22 = sub_reduce<L>(ca.h22);
+#pragma unroll
+            for (int off = L / 2; off > 0; off >>= 1) hit |= __shfl_xor_sync(FULL, hit, off);
+        }
+        sc = (n_items > 0 ? 2 : 0) | hit;
+    }
+    if (active && lane == 0) solve_and_store<SC>(d, p, vi, xi, acc, ca, sc);
+}
+
+template <int L>
+__global__ void __launch_bounds__(256) k_sweep(Dev d, SweepParams p) {
+    sweep_body<L, false>(d, p);
+}
+
+// with self-contact forces; capped at 64 registers so that enough warps stay
+// resident to hide the gather latency
+template <int L>
+__global__ void __launch_bounds__(256, 4) k_sweep_sc(Dev d, SweepParams p) {
+    sweep_body<L, true>(d, p);
 }
 
 // ---- pipelined sweep: slot records staged in shared memory by TMA ----------
@@ -467,7 +510,7 @@ __global__ void __launch_bounds__(TT) k_sweep_pipe(Dev d, SweepParams p, int max
         acc.h11 = sub_reduce<L>(acc.h11);
         acc.h12 = sub_reduce<L>(acc.h12);
         acc.h22 = sub_reduce<L>(acc.h22);
-        if (active && lane == 0) solve_and_store<false>(d, p, vi, xi, acc);
+        if (active && lane == 0) solve_and_store<false>(d, p, vi, xi, acc, acc, 0);
     }
 }
 
@@ -560,10 +603,13 @@ __global__ void k_gather(const float4 *src, float *dst, const int *new_of_orig, 
     dst[3 * o + 2] = a.z;
 }
 
-// the pass wrote vertices [vbegin, vend) to unew (x^new of Algorithm 1); copy them back
-__global__ void k_copy_back(Dev d, int vbegin, int vend) {
+// the pass wrote vertices [vbegin, vend) to unew (x^new of Algorithm 1); copy
+// them back -- with involved_only, just the vertices in a self-contact pair
+__global__ void k_copy_back(Dev d, int vbegin, int vend, int involved_only) {
     const int i = vbegin + blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < vend) d.u[i] = d.unew[i];
+    if (i >= vend) return;
+    if (involved_only && d.contact[i] < 0 && d.rev_off[i + 1] == d.rev_off[i]) return;
+    d.u[i] = d.unew[i];
 }
 
 __global__ void k_restore_x(Dev d, int n) {
@@ -688,18 +734,18 @@ void launch_sweep(const Dev &d, const SweepParams &p, int lanes, int block, cuda
     const unsigned grid = blocks_for(threads, block);
     if (p.self_collision) {
         switch (lanes) {
-        case 4: k_sweep<4, true><<<grid, block, 0, s>>>(d, p); break;
-        case 8: k_sweep<8, true><<<grid, block, 0, s>>>(d, p); break;
-        case 16: k_sweep<16, true><<<grid, block, 0, s>>>(d, p); break;
-        default: k_sweep<32, true><<<grid, block, 0, s>>>(d, p); break;
+        case 4: k_sweep_sc<4><<<grid, block, 0, s>>>(d, p); break;
+        case 8: k_sweep_sc<8><<<grid, block, 0, s>>>(d, p); break;
+        case 16: k_sweep_sc<16><<<grid, block, 0, s>>>(d, p); break;
+        default: k_sweep_sc<32><<<grid, block, 0, s>>>(d, p); break;
         }
         return;
     }
     switch (lanes) {
-    case 4: k_sweep<4, false><<<grid, block, 0, s>>>(d, p); break;
-    case 8: k_sweep<8, false><<<grid, block, 0, s>>>(d, p); break;
-    case 16: k_sweep<16, false><<<grid, block, 0, s>>>(d, p); break;
-    default: k_sweep<32, false><<<grid, block, 0, s>>>(d, p); break;
+    case 4: k_sweep<4><<<grid, block, 0, s>>>(d, p); break;
+    case 8: k_sweep<8><<<grid, block, 0, s>>>(d, p); break;
+    case 16: k_sweep<16><<<grid, block, 0, s>>>(d, p); break;
+    default: k_sweep<32><<<grid, block, 0, s>>>(d, p); break;
     }
 }
 
@@ -756,8 +802,9 @@ void launch_gather(const float4 *src, float *dst, const int *new_of_orig, const 
     k_gather<<<blocks_for(n, 256), 256, 0, s>>>(src, dst, new_of_orig, rest, n);
 }
 
-void launch_copy_back(const Dev &d, int vbegin, int vend, cudaStream_t s) {
-    if (vend > vbegin) k_copy_back<<<blocks_for(vend - vbegin, 256), 256, 0, s>>>(d, vbegin, vend);
+void launch_copy_back(const Dev &d, int vbegin, int vend, bool involved_only, cudaStream_t s) {
+    if (vend > vbegin)
+        k_copy_back<<<blocks_for(vend - vbegin, 256), 256, 0, s>>>(d, vbegin, vend, involved_only ? 1 : 0);
 }
 
 void launch_restore_x(const Dev &d, int n, cudaStream_t s) {

@@ -36,7 +36,8 @@ struct Dev {
     float *tet_V, *tet_nu, *tet_mu, *tet_lam;
     int *new_of_orig; // N
     float *stage[3];  // 3N each, state exchange with caller order
-    unsigned long long *counters;  // [0] non-finite updates, [1] det skips, [2] pipeline wait time-outs
+    unsigned long long *counters;  // [0] non-finite updates, [1] det skips, [2] pipeline wait time-outs,
+                                   // [3] self-collision pairs found, [4] positions beyond the collision grid
     double *partials; // energy partial sums
     double *energy_out;
     float4 *tape;     // tape_steps * N displacements
@@ -52,6 +53,8 @@ struct Dev {
     int *rev_off;     // n_free + 1: pairs in which free vertex i is a triangle corner
     int *rev;         // 3 n_surf: the pairs' vertices, ascending per corner
     int *rev_fill;    // n_free
+    float4 *tri_sphere;  // n_tris: centroid and radius of each triangle's bounding ball at this step
+    float4 *tet_sphere;  // T: the same for the tets
     int *cell_start;  // n_buckets + 1: triangles of each hash bucket (by centroid cell)
     int *cell_fill;   // n_buckets
     int *cell_tri;    // n_tris
@@ -74,7 +77,7 @@ struct SweepParams {
     float eps_h;      // eps_v * h: tangential displacement where f1 reaches 1
     int line_search;  // backtracking on G_i (Sec. 3.2)
     int per_tet_mat;  // 1: mu, lambda per tet (via slot_tet); 0: per vertex (vmat)
-    int to_unew;      // write to d.unew instead of updating d.u in place (block Jacobi, self-collision)
+    int to_unew;      // every vertex writes to d.unew instead of updating d.u in place (block Jacobi)
     int self_collision;  // add the vertex-triangle contact forces of the current pairs
 };
 
@@ -105,7 +108,7 @@ void launch_scatter(const float *src, float4 *dst, const int *new_of_orig, const
 void launch_gather(const float4 *src, float *dst, const int *new_of_orig, const float4 *rest, int n,
                    cudaStream_t s);
 void launch_restore_x(const Dev &d, int n, cudaStream_t s);
-void launch_copy_back(const Dev &d, int vbegin, int vend, cudaStream_t s);
+void launch_copy_back(const Dev &d, int vbegin, int vend, bool involved_only, cudaStream_t s);
 // n_surf > 0 adds the self-contact energy of the current pairs
 void launch_energy(const Dev &d, int n_free, int n_tets, int n_surf, double h, const SweepParams &p,
                    cudaStream_t s);

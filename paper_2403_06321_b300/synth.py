@@ -212,6 +212,7 @@ def colliding_slabs(n: int = 12, layers: int = 2, edge: float = 0.05, sink: floa
     target = np.array([0.5 * n * edge, 0.5 * n * edge, (1.5 * layers - sink) * edge])
     upper.rest = (upper.rest - centre) @ R.T + target
     cat, voff, _ = concat([lower, upper])
+    cat.grid_ijk = np.concatenate([lower.grid_ijk, upper.grid_ijk])  # per slab: Kuhn colouring stays valid
     cfg = SimConfig(h=1 / 60, iters=20, steps=10, k_c=1e5, self_collision=True, dcd_radius=0.5 * edge)
     return cat, cfg, int(voff[1])
 

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libvbd.so")
 
 STATUS = {0: "VBD_OK", 1: "VBD_ERR_INVALID_ARG", 2: "VBD_ERR_BAD_MESH", 3: "VBD_ERR_BAD_COLORING",
           4: "VBD_ERR_NOT_COLORED", 5: "VBD_ERR_WORKSPACE", 6: "VBD_ERR_CUDA", 7: "VBD_ERR_NONFINITE",
-          8: "VBD_ERR_NO_TAPE", 9: "VBD_ERR_STATE", 10: "VBD_ERR_TIMEOUT"}
+          8: "VBD_ERR_NO_TAPE", 9: "VBD_ERR_STATE", 10: "VBD_ERR_TIMEOUT", 11: "VBD_ERR_RANGE"}
 STATUS_CODE = {v: k for k, v in STATUS.items()}
 
 # every entry point declared in include/vbd.h

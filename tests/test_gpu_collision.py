@@ -181,3 +181,45 @@ def test_self_collision_arguments(orc):
         assert e.value.status == "VBD_ERR_STATE"
     finally:
         sim.close()
+
+
+def test_large_slabs_detection_sampled(orc):
+    """The slab scene at bench size (300x300x4 and 298x298x4 cubes: 900,010
+    vertices, 4,291,296 tets, 367,180 boundary vertices): the pairs of sampled
+    boundary vertices, each recomputed alone by the oracle (brute force over
+    every tet and triangle); then three steps stay finite and lift the
+    upper slab's penetrating vertices."""
+    m, cfg, u0 = synth.colliding_slabs(n=300, layers=4, seed=31)
+    pd = params_of(cfg)
+    x = _f32(m.rest)
+    sim = _sim(m, pd, synth.kuhn_coloring(m.grid_ijk))
+    try:
+        tris = vbd.vbd_get_surface(sim.ctx)
+        sim.set_state(x, np.zeros_like(x))
+        vbd.vbd_begin_step(sim.ctx, cfg.h)
+        got = vbd.vbd_get_contacts(sim.ctx, m.n_verts)
+        vbd.vbd_iterate(sim.ctx, cfg.iters)
+        vbd.vbd_end_step(sim.ctx)
+        for _ in range(2):
+            sim.step(cfg.h, cfg.iters)
+        sim.sync_status()
+        xg, _ = sim.get_state()
+        xg = xg.cpu().numpy().astype(np.float64)
+    finally:
+        sim.close()
+    model = orc.Model.from_mesh(m)
+    assert np.array_equal(tris, model.tris())
+    p = orc.Params.make(**pd)
+    surf = np.unique(tris)
+    rng = np.random.default_rng(32)
+    paired = np.nonzero(got >= 0)[0]
+    assert paired.size > 1000
+    sample = np.concatenate([rng.choice(paired, 30, replace=False), rng.choice(surf, 30, replace=False)])
+    want = got.copy()
+    for a in sample:
+        want[a] = model.dcd_vertex(p, x, a)
+    assert _pairs_agree(orc, model, p, x, tris, got[sample], want[sample]) == 0
+    assert np.isfinite(xg).all()
+    # the overlap shrinks: the upper slab's penetrating vertices rise on average
+    sunk = paired[paired >= u0]
+    assert sunk.size > 1000 and xg[sunk, 2].mean() > x[sunk, 2].mean()
