@@ -33,6 +33,9 @@ UNIT = "vertex-block updates/s"
 # vertex I/O + one re-read of neighbour positions per colour pass)
 B_INC, B_VTX, B_X = 52, 44, 12
 B_SC = 24  # with self-collision: contact[i] and rev_off[i], rev_off[i+1], in the sweep and the copy-back
+VARIANTS = {0: "plain", 1: "tma_staged", 2: "persistent", 3: "two_phase_scatter"}
+KERNELS = {0: "k_sweep", 1: "k_sweep_pipe", 2: "k_sweep_persist", 3: "k_scatter_slots + k_scatter_reduce"}
+NOMINAL_HBM_GBS = 7700.0  # B300 HBM3e nominal bandwidth, for context beside the measured peak
 DETECT_LAUNCHES = 20   # kernels and memsets of one self-collision detection (three prefix sums)
 CPU_SAMPLE_N = 32      # the CPU legs run a 32^3-cube crop of the same recipe
 CPU_SAMPLE_ITERS = 10
@@ -51,7 +54,8 @@ def parse_args(argv=None):
     ap.add_argument("--coloring", choices=["kuhn", "greedy"], default="kuhn")
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
-    ap.add_argument("--pipeline", type=int, default=-1, help="1 TMA-staged sweep, 0 plain sweep, -1 library default")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="sweep kernel: 0 plain, 1 TMA-staged, 2 persistent, 3 two-phase scatter; -1 autotune")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shape")
     ap.add_argument("--mu-c", type=float, default=0.0, help="ground friction coefficient (Eqs. 13-16)")
@@ -276,7 +280,7 @@ def workload_config(args, info, mesh=None) -> dict:
     if info is not None:
         cfg.update({"n_colors": info.n_colors, "n_free_verts": info.n_free, "n_slots": int(info.n_slots),
                     "lanes_per_vertex": info.lanes_per_vertex, "block_threads": info.block_threads,
-                    "tma_pipeline": bool(info.pipeline), "stage_slots": info.pipe_stage_slots,
+                    "sweep_variant": VARIANTS[info.pipeline], "stage_slots": info.pipe_stage_slots,
                     "ctas_per_sm": info.pipe_ctas_per_sm,
                     "cuda_graph": bool(info.use_graph), "parallelism": "replicas"})
     return cfg
@@ -309,6 +313,8 @@ def run_batched(args) -> dict:
     params = vbd.make_params(gravity=cfg.gravity, init_mode=cfg.init_mode, det_eps=cfg.det_eps)
     stream = torch.cuda.Stream()
     sim = vbd.Sim(cat, params, colors=colors, stream=stream, vert_offset=voff, tet_offset=toff)
+    sim.set_state(cat.rest, np.zeros_like(cat.rest))
+    vbd.vbd_autotune(sim.ctx, cfg.h, cfg.iters)  # launch shape for this batch
     info = vbd.vbd_get_info(sim.ctx)
     sim.set_state(cat.rest, np.zeros_like(cat.rest))
     steps = 5
@@ -340,6 +346,8 @@ def run_batched(args) -> dict:
     return {"workload": "%d beams, %d verts, %d tets, Kuhn 4-colouring, h=1/60, %d iterations/step, "
                         "one launch per colour for all meshes, CUDA graph per step" % (
                             len(meshes), cat.n_verts, cat.n_tets, iters),
+            "launch": {"sweep_variant": VARIANTS[info.pipeline], "lanes_per_vertex": info.lanes_per_vertex,
+                       "block_threads": info.block_threads},
             "value": v_batched, "unit": UNIT, "ms_per_step": t_b * 1e3 / steps,
             "per_mesh_value": v_plain, "per_mesh_ms_per_step": t_p * 1e3 / psteps,
             "speedup_vs_plain": v_batched / v_plain, "n_free_verts": int(info.n_free)}
@@ -434,6 +442,52 @@ def run_self_collision(args) -> dict:
             "ratio_vs_plain": out[True][0] / out[False][0]}
 
 
+def run_small_configs(args) -> dict:
+    """The two workloads that fit in L2 (cantilever beam, differentiable
+    beam): latency- and launch-bound, so only time per step is reported,
+    plus the differentiable beam's adjoint (vbd_backward) over its 30 steps."""
+    import numpy as np
+    import torch
+    from paper_2403_06321_b300 import synth, vbd
+    out = {}
+    m, cfg = synth.cantilever_beam()
+    stream = torch.cuda.Stream()
+    sim = vbd.Sim(m, vbd.make_params(gravity=cfg.gravity), colors=synth.kuhn_coloring(m.grid_ijk), stream=stream)
+    sim.set_state(m.rest, np.zeros_like(m.rest))
+    for _ in range(5):
+        sim.step(cfg.h, cfg.iters)
+    t = _timed(stream, lambda: sim.step(cfg.h, cfg.iters), cfg.steps)
+    sim.sync_status()
+    sim.close()
+    out["cantilever_beam"] = {"workload": "10x3x3 cubes (176 verts, 540 tets), x=0 face pinned, h=1/60, "
+                                          "%d iterations/step" % cfg.iters,
+                              "ms_per_step": t * 1e3 / cfg.steps}
+    m, cfg, tip, target = synth.differentiable_beam()
+    params = vbd.make_params(gravity=cfg.gravity, tape_steps=cfg.steps)
+    sim = vbd.Sim(m, params, colors=synth.kuhn_coloring(m.grid_ijk), stream=stream)
+    dev = sim.workspace.device
+    zeros = np.zeros_like(m.rest)
+    gx = torch.zeros(3 * m.n_verts, dtype=torch.float32, device=dev)
+    gE = torch.empty(m.n_tets, dtype=torch.float32, device=dev)
+    gv = torch.empty(3 * m.n_verts, dtype=torch.float32, device=dev)
+
+    def fwd():
+        sim.set_state(m.rest, zeros)
+        for _ in range(cfg.steps):
+            sim.step(cfg.h, cfg.iters)
+    fwd()
+    vbd.vbd_backward(sim.ctx, gx, gE, gv, cfg.iters)
+    t_f = _timed(stream, fwd, 1)
+    t_b = _timed(stream, lambda: vbd.vbd_backward(sim.ctx, gx, gE, gv, cfg.iters), 1)
+    sim.sync_status()
+    sim.close()
+    out["differentiable_beam"] = {"workload": "40x8x8 cubes (3,321 verts, 15,360 tets), %d steps x %d iterations, "
+                                              "adjoint %d block-GS iterations per step" % (
+                                                  cfg.steps, cfg.iters, cfg.iters),
+                                  "ms_per_step": t_f * 1e3 / cfg.steps, "ms_backward_per_step": t_b * 1e3 / cfg.steps}
+    return out
+
+
 # --------------------------------------------------------------------- ours ---
 
 def run_ours(args):
@@ -460,16 +514,17 @@ def run_ours(args):
     params = vbd.make_params(gravity=cfg.gravity, ground_on=cfg.ground_on, k_c=cfg.k_c,
                              init_mode=cfg.init_mode, det_eps=cfg.det_eps, mu_c=args.mu_c,
                              line_search=args.line_search, jacobi=args.jacobi,
-                             self_collision=cfg.self_collision, dcd_radius=cfg.dcd_radius)
+                             self_collision=cfg.self_collision, dcd_radius=cfg.dcd_radius,
+                             scatter_sweep=args.variant == 3)
     stream = torch.cuda.Stream()
     sim = vbd.Sim(m, params, colors=colors, stream=stream)
-    if args.lanes or args.block or args.pipeline >= 0:
-        vbd.vbd_set_launch(sim.ctx, args.lanes, args.block, args.pipeline)
+    if args.lanes or args.block or args.variant >= 0:
+        vbd.vbd_set_launch(sim.ctx, args.lanes, args.block, args.variant)
     vbd.vbd_set_graph(sim.ctx, not args.no_graph)
     iters, h, K = args.iters, cfg.h, args.steps
     zeros = np.zeros_like(m.rest)
     sim.set_state(m.rest, zeros)
-    if not (args.no_autotune or args.lanes or args.block or args.pipeline >= 0):
+    if not (args.no_autotune or args.lanes or args.block or args.variant >= 0):
         vbd.vbd_autotune(sim.ctx, h, min(iters, 20))  # times each launch shape, keeps the fastest
     info = vbd.vbd_get_info(sim.ctx)
 
@@ -555,7 +610,8 @@ def run_ours(args):
         "dtype": "f32", "data": "synthetic", "config": workload_config(args, info, m),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                     "kernel": ("k_sweep_pipe" if info.pipeline else "k_sweep") + " (one colour pass)", "alg_bytes_per_update": b_upd,
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_gbs": NOMINAL_HBM_GBS,
+                     "kernel": KERNELS[info.pipeline] + " (one colour pass)", "alg_bytes_per_update": b_upd,
                      "avg_launch_us": avg_launch_s * 1e6,
                      "sweep_share_of_step": sweep_ms / t_ms},
         "e2e": e2e,
@@ -567,6 +623,7 @@ def run_ours(args):
         line["batched"] = run_batched(args)
         line["adjoint"] = run_adjoint(args)
         line["self_collision"] = run_self_collision(args)
+        line["small_configs"] = run_small_configs(args)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = run_cpu_baseline()
     print(json.dumps(line), flush=True)

@@ -91,6 +91,8 @@ typedef struct {
     int32_t jacobi;          /* 1: block Jacobi, every vertex against the previous iterate */
     int32_t self_collision;  /* 1: vertex-triangle contact between boundary elements (Sec. 3.5) */
     float dcd_radius;        /* detection distance r of the self-collision pairs [m] */
+    int32_t scatter_sweep;   /* 1: carve the buffers of the two-phase scatter sweep (variant 3 of
+                                vbd_set_launch); enlarges the workspace, so set it before vbd_bind */
 } vbd_params;
 
 /* Library defaults: gravity (0,0,-9.8), ground off at z = 0 with n = +z,
@@ -138,7 +140,8 @@ typedef struct {
     int32_t n_colors;        /* 0 before vbd_color */
     int64_t n_slots;         /* (free vertex, incident tet) pairs streamed per iteration */
     int32_t lanes_per_vertex, block_threads;   /* current sweep launch shape */
-    int32_t pipeline;        /* 1: slot records staged in shared memory by TMA bulk copies */
+    int32_t pipeline;        /* sweep variant of vbd_set_launch (0 plain, 1 TMA-staged, 2 persistent,
+                                3 two-phase scatter) */
     int32_t pipe_stage_slots; /* slot capacity of one pipeline stage */
     int32_t pipe_ctas_per_sm; /* resident CTAs per SM of the pipelined sweep */
     int32_t use_graph;       /* vbd_iterate replays a CUDA graph */
@@ -283,15 +286,28 @@ vbd_status vbd_sync_status(vbd_ctx *ctx, int64_t *det_skips, int64_t *contacts);
 vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, float *dL_dv0,
                         int32_t adj_iters);
 
-/* Sweep launch shape.  pipeline = 1: persistent CTAs of
- * block_threads in {128, 256} stage each chunk of block_threads/8 vertices'
- * slot records in shared memory with TMA bulk copies, two chunks ahead, 8
- * lanes per vertex (lanes_per_vertex is ignored).  pipeline = 0: one thread
- * group of lanes_per_vertex in {4, 8, 16, 32} per vertex loading its slots
- * from global memory, block_threads in {64, 128, 256} (default: pipeline 0,
- * 4 lanes, 128 threads, the fastest measured on B300).  0 keeps a value
- * (pipeline < 0 keeps it too).  Must not be called during stream capture. */
-vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_threads, int32_t pipeline);
+/* Sweep launch shape and kernel variant.  variant:
+ *  0  plain: one thread group of lanes_per_vertex in {4, 8, 16, 32} per
+ *     vertex, loading its slot records from global memory, block_threads in
+ *     {64, 128, 256}, one CTA per block of vertices;
+ *  1  TMA-staged: persistent CTAs of block_threads in {128, 256} stage each
+ *     chunk of block_threads/8 vertices' slot records in shared memory with
+ *     TMA bulk copies, two chunks ahead, 8 lanes per vertex
+ *     (lanes_per_vertex is ignored);
+ *  2  persistent: variant 0's kernel on a grid of (SMs x resident CTAs)
+ *     that strides over the colour's vertices (default, with 4 lanes and
+ *     256 threads: the fastest measured on B300);
+ *  3  two-phase tet-scatter-into-slots: one thread per incidence writes that
+ *     tet's force and Hessian block on its vertex to a scratch slot, then a
+ *     per-vertex kernel adds them up and solves (needs scatter_sweep = 1 at
+ *     bind time, else VBD_ERR_STATE).
+ * All variants give the same positions: 0 and 2 bit for bit with equal
+ * lanes, 1 equals 0 with 8 lanes, and 3 agrees to FP32 rounding (each
+ * incidence's terms are rounded before they are summed).  Self-collision passes always use the
+ * plain form with contacts, and block Jacobi the plain form.  0 keeps a
+ * shape value, a negative variant keeps the variant.  Must not be called
+ * during stream capture. */
+vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_threads, int32_t variant);
 
 /* Enables (1) or disables (0) CUDA-graph replay of vbd_iterate. */
 vbd_status vbd_set_graph(vbd_ctx *ctx, int32_t enable);

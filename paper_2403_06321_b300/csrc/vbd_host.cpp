@@ -25,6 +25,8 @@ using vbd::SweepParams;
 namespace {
 
 constexpr int kMaxColors = 4096;
+// adjoint sweep launch shape (measured best on B300; independent of the forward's)
+constexpr int kAdjLanes = 4, kAdjBlock = 128;
 
 struct GraphEntry {
     int first_n, iters;
@@ -81,8 +83,8 @@ struct vbd_ctx {
     int tape_len = 0;
     std::vector<float> tape_h;
     // launch shape / graphs
-    int lanes = 4, block = 128;
-    bool pipeline = false;
+    int lanes = 4, block = 256;
+    int variant = 2;            // sweep kernel: 0 plain, 1 TMA-staged, 2 persistent, 3 two-phase scatter
     int pipe_block = 128;
     int pipe_maxs = 0;          // slot capacity of one stage
     int pipe_ctas_per_sm = 0;
@@ -218,6 +220,14 @@ int greedy_coloring(int N, int T, const std::vector<int> &tets, std::vector<int>
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// largest number of slots of one colour (the scatter sweep's scratch)
+long long max_colour_slots(const vbd_ctx *c) {
+    long long mx = 0;
+    for (int col = 0; col < c->n_colors; ++col)
+        mx = std::max<long long>(mx, (long long)c->slot_off[c->color_begin[col + 1]] - c->slot_off[c->color_begin[col]]);
+    return mx;
+}
+
 // the workspace carries the self-collision arrays
 bool sc_wanted(const vbd_ctx *c) { return c->params.self_collision && c->surface_built; }
 
@@ -248,6 +258,13 @@ size_t carve(const vbd_ctx *c, char *base, Dev *d) {
     t.s1 = (float4 *)take(16 * S);
     t.s2 = (float4 *)take(16 * S);
     t.vmat = (float2 *)take(8 * N);
+    if (c->params.scatter_sweep) {
+        const size_t cs = (size_t)std::max(max_colour_slots(c), 1LL);
+        t.slot_vtx = (int *)take(4 * S);
+        t.scr0 = (float4 *)take(16 * cs);
+        t.scr1 = (float4 *)take(16 * cs);
+        t.scr2 = (float *)take(4 * cs);
+    }
     t.slot_tet = (int *)take(4 * S);
     t.slot_loc = (int *)take(4 * S);
     t.tet_v = (int4 *)take(16 * T);
@@ -399,8 +416,12 @@ void launch_colour(vbd_ctx *c, int col, cudaStream_t s) {
     if (p.self_collision) {
         vbd::launch_sweep(c->d, p, c->lanes, c->block, s);
         vbd::launch_copy_back(c->d, p.vbegin, p.vend, !p.to_unew, s);
-    } else if (c->pipeline) {
+    } else if (c->variant == 1) {
         vbd::launch_sweep_pipe(c->d, p, c->pipe_block, c->pipe_maxs, c->pipe_grid_cap, s);
+    } else if (c->variant == 2) {
+        vbd::launch_sweep_persist(c->d, p, c->lanes, c->block, s);
+    } else if (c->variant == 3) {
+        vbd::launch_sweep_scatter(c->d, p, c->slot_off[p.vbegin], c->slot_off[p.vend], c->lanes, c->block, s);
     } else {
         vbd::launch_sweep(c->d, p, c->lanes, c->block, s);
     }
@@ -718,9 +739,9 @@ vbd_status vbd_get_info(const vbd_ctx *ctx, vbd_info *out) {
     out->n_free = ctx->colored ? ctx->n_free : 0;
     out->n_colors = ctx->colored ? ctx->n_colors : 0;
     out->n_slots = ctx->colored ? ctx->n_slots : 0;
-    out->lanes_per_vertex = ctx->pipeline ? 8 : ctx->lanes;
-    out->block_threads = ctx->pipeline ? ctx->pipe_block : ctx->block;
-    out->pipeline = ctx->pipeline ? 1 : 0;
+    out->lanes_per_vertex = ctx->variant == 1 ? 8 : ctx->lanes;
+    out->block_threads = ctx->variant == 1 ? ctx->pipe_block : ctx->block;
+    out->pipeline = ctx->variant;
     out->pipe_stage_slots = ctx->pipe_maxs;
     out->pipe_ctas_per_sm = ctx->pipe_ctas_per_sm;
     out->use_graph = ctx->use_graph ? 1 : 0;
@@ -794,7 +815,7 @@ vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *st
     {
         std::vector<int4> h0;
         std::vector<float4> h1, h2;
-        std::vector<int> ht, hl;
+        std::vector<int> ht, hl, hv;
         int k0 = 0;
         while (k0 < ctx->n_free) {
             int k1 = k0;
@@ -808,6 +829,13 @@ vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *st
             CU(cudaMemcpyAsync(d.s2 + a0, h2.data(), 16 * (size_t)n, cudaMemcpyHostToDevice, s), "upload slots");
             CU(cudaMemcpyAsync(d.slot_tet + a0, ht.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s), "upload slots");
             CU(cudaMemcpyAsync(d.slot_loc + a0, hl.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s), "upload slots");
+            if (d.slot_vtx) {  // own vertex of each slot, for the scatter sweep
+                hv.resize(n);
+                for (int k = k0; k < k1; ++k)
+                    for (int q = ctx->slot_off[k]; q < ctx->slot_off[k + 1]; ++q) hv[q - a0] = k;
+                CU(cudaMemcpyAsync(d.slot_vtx + a0, hv.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s),
+                   "upload slots");
+            }
             CU(cudaStreamSynchronize(s), "upload slots");  // the staging vectors are reused
             k0 = k1;
         }
@@ -1169,7 +1197,7 @@ vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, floa
         vbd::launch_adj_rhs(d, N, ctx->n_free, 1.f / h, s);
         for (int it = 0; it < adj_iters; ++it)
             for (int col = 0; col < ctx->n_colors; ++col)
-                vbd::launch_adj_sweep(d, xs, sweep_params(ctx, col), ctx->lanes, ctx->block, s);
+                vbd::launch_adj_sweep(d, xs, sweep_params(ctx, col), kAdjLanes, kAdjBlock, s);
         vbd::launch_adj_post(d, xs, N, ctx->n_free, ctx->T, h, s);
     }
     ctx->h = h_saved;
@@ -1178,9 +1206,15 @@ vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, floa
     return VBD_OK;
 }
 
-vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_threads, int32_t pipeline) {
+vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_threads, int32_t variant) {
     if (!ctx) return VBD_ERR_INVALID_ARG;
-    const bool pipe = pipeline < 0 ? ctx->pipeline : pipeline != 0;
+    if (variant > 3) return fail(ctx, VBD_ERR_INVALID_ARG, "sweep variant must be 0..3 (or < 0 to keep it)");
+    const int var = variant < 0 ? ctx->variant : variant;
+    const bool pipe = var == 1;
+    if (var == 3 && !ctx->params.scatter_sweep)
+        return fail(ctx, VBD_ERR_STATE, "the scatter sweep needs scatter_sweep = 1 in the params at bind time");
+    if (var == 3 && ctx->bound && !ctx->d.slot_vtx)
+        return fail(ctx, VBD_ERR_STATE, "the bound workspace has no scatter buffers: bind again");
     if (lanes_per_vertex != 0 && lanes_per_vertex != 4 && lanes_per_vertex != 8 && lanes_per_vertex != 16 &&
         lanes_per_vertex != 32)
         return fail(ctx, VBD_ERR_INVALID_ARG, "lanes_per_vertex must be 4, 8, 16 or 32");
@@ -1190,7 +1224,7 @@ vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_
     } else if (block_threads != 0 && block_threads != 64 && block_threads != 128 && block_threads != 256) {
         return fail(ctx, VBD_ERR_INVALID_ARG, "block_threads must be 64, 128 or 256");
     }
-    ctx->pipeline = pipe;
+    ctx->variant = var;
     if (lanes_per_vertex) ctx->lanes = lanes_per_vertex;
     if (block_threads) {
         if (pipe)
@@ -1220,14 +1254,15 @@ vbd_status vbd_autotune(vbd_ctx *ctx, float h, int32_t iters, float *best_ms_per
     if (iters < 1) return fail(ctx, VBD_ERR_INVALID_ARG, "iters must be >= 1");
     struct Shape { int pipe, lanes, block; };
     const Shape shapes[] = {{0, 4, 64}, {0, 4, 128}, {0, 4, 256}, {0, 8, 128}, {0, 8, 256},
-                            {0, 16, 256}, {1, 8, 128}, {1, 8, 256}};
+                            {0, 16, 256}, {1, 8, 128}, {1, 8, 256}, {2, 4, 128}, {2, 4, 256},
+                            {2, 8, 256}, {3, 4, 128}};
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0), "event");
     CU(cudaEventCreate(&e1), "event");
     const bool graph_saved = ctx->use_graph;
     ctx->use_graph = false;
     float best = 1e30f;
-    Shape bs = {ctx->pipeline ? 1 : 0, ctx->lanes, ctx->pipeline ? ctx->pipe_block : ctx->block};
+    Shape bs = {ctx->variant, ctx->lanes, ctx->variant == 1 ? ctx->pipe_block : ctx->block};
     for (const Shape &sh : shapes) {
         if (vbd_set_launch(ctx, sh.lanes, sh.block, sh.pipe) != VBD_OK) continue;
         float ms = 0.f;

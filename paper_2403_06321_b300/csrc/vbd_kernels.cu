@@ -271,10 +271,10 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
     out[vi] = make_float4(xi.x + dx, xi.y + dy, xi.z + dz, flag);
 }
 
+// One colour pass for the vertex of global thread gt (L lanes per vertex).
 template <int L, bool SC>
-__device__ __forceinline__ void sweep_body(const Dev &d, const SweepParams &p) {
+__device__ __forceinline__ void sweep_body(const Dev &d, const SweepParams &p, long long gt) {
     const int lane = threadIdx.x & (L - 1);
-    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int vi = p.vbegin + (int)(gt / L);
     const bool active = vi < p.vend;
     float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -330,14 +330,78 @@ __device__ __forceinline__ void sweep_body(const Dev &d, const SweepParams &p) {
 
 template <int L>
 __global__ void __launch_bounds__(256) k_sweep(Dev d, SweepParams p) {
-    sweep_body<L, false>(d, p);
+    sweep_body<L, false>(d, p, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// persistent form: a grid of (SMs x resident CTAs) walks the colour's
+// vertices in grid-sized strides (the stride is uniform over a warp, so
+// every lane joins the shuffles of each round)
+template <int L>
+__global__ void __launch_bounds__(256) k_sweep_persist(Dev d, SweepParams p, long long threads) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < threads; base += stride)
+        sweep_body<L, false>(d, p, base + threadIdx.x);
 }
 
 // with self-contact forces; capped at 64 registers so that enough warps stay
 // resident to hide the gather latency
 template <int L>
 __global__ void __launch_bounds__(256, 4) k_sweep_sc(Dev d, SweepParams p) {
-    sweep_body<L, true>(d, p);
+    sweep_body<L, true>(d, p, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// ---- two-phase tet-scatter-into-slots sweep ----------------------------------
+// Phase 1: one thread per incidence slot of the colour computes that tet's
+// force and Hessian block on the slot's vertex (the same arithmetic as
+// accumulate_slot) and writes the 9 sums to the slot's place in a scratch
+// buffer.  Phase 2: L lanes per vertex add up the vertex's scratch entries
+// (in slot order, xor-reduced like k_sweep) and solve.  It moves 36 bytes
+// more per slot twice (write and read back) than the gather, which is why the
+// gather is the default; it exists to measure that choice.
+__global__ void __launch_bounds__(256) k_scatter_slots(Dev d, SweepParams p, int sbegin, int nslots) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nslots) return;
+    const int s = sbegin + t;
+    const int vi = __ldcs(d.slot_vtx + s);
+    const float3 x3 = f3(__ldg(d.u + vi));
+    const float2 vm = p.per_tet_mat ? make_float2(0.f, 0.f) : __ldg(d.vmat + vi);
+    Acc acc = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    accumulate_slot(d, p, s, vm, __ldcs(d.s0 + s), __ldcs(d.s1 + s), __ldcs(d.s2 + s), x3, acc);
+    __stcs(d.scr0 + t, make_float4(acc.f0, acc.f1, acc.f2, acc.h00));
+    __stcs(d.scr1 + t, make_float4(acc.h01, acc.h02, acc.h11, acc.h12));
+    __stcs(d.scr2 + t, acc.h22);
+}
+
+template <int L>
+__global__ void __launch_bounds__(256) k_scatter_reduce(Dev d, SweepParams p, int sbegin) {
+    const int lane = threadIdx.x & (L - 1);
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int vi = p.vbegin + (int)(gt / L);
+    const bool active = vi < p.vend;
+    float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
+    int s0 = 0, s1 = 0;
+    if (active) {
+        xi = d.u[vi];
+        s0 = d.slot_off[vi] - sbegin;
+        s1 = d.slot_off[vi + 1] - sbegin;
+    }
+    Acc acc = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int k = s0 + lane; k < s1; k += L) {
+        const float4 a = __ldcs(d.scr0 + k), b = __ldcs(d.scr1 + k);
+        acc.f0 += a.x; acc.f1 += a.y; acc.f2 += a.z; acc.h00 += a.w;
+        acc.h01 += b.x; acc.h02 += b.y; acc.h11 += b.z; acc.h12 += b.w;
+        acc.h22 += __ldcs(d.scr2 + k);
+    }
+    acc.f0 = sub_reduce<L>(acc.f0);
+    acc.f1 = sub_reduce<L>(acc.f1);
+    acc.f2 = sub_reduce<L>(acc.f2);
+    acc.h00 = sub_reduce<L>(acc.h00);
+    acc.h01 = sub_reduce<L>(acc.h01);
+    acc.h02 = sub_reduce<L>(acc.h02);
+    acc.h11 = sub_reduce<L>(acc.h11);
+    acc.h12 = sub_reduce<L>(acc.h12);
+    acc.h22 = sub_reduce<L>(acc.h22);
+    if (active && lane == 0) solve_and_store<false>(d, p, vi, xi, acc, acc, 0);
 }
 
 // ---- pipelined sweep: slot records staged in shared memory by TMA ----------
@@ -726,6 +790,40 @@ void launch_predict(const Dev &d, int n, int n_free, float h, float3 g, int init
                     cudaStream_t s) {
     const float gnorm = sqrtf(g.x * g.x + g.y * g.y + g.z * g.z);
     k_predict<<<blocks_for(n, 256), 256, 0, s>>>(d, n, n_free, h, g, gnorm, init_mode, cheby ? 1 : 0);
+}
+
+template <int L>
+static unsigned persist_grid(int block) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_persist<L>, block, 0) != cudaSuccess || occ < 1)
+        occ = 1;
+    return (unsigned)(num_sms() * occ);
+}
+
+void launch_sweep_persist(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s) {
+    const long long threads = (long long)(p.vend - p.vbegin) * lanes;
+    if (threads <= 0) return;
+    const unsigned need = blocks_for(threads, block);
+    switch (lanes) {
+    case 4: k_sweep_persist<4><<<std::min(need, persist_grid<4>(block)), block, 0, s>>>(d, p, threads); break;
+    case 8: k_sweep_persist<8><<<std::min(need, persist_grid<8>(block)), block, 0, s>>>(d, p, threads); break;
+    case 16: k_sweep_persist<16><<<std::min(need, persist_grid<16>(block)), block, 0, s>>>(d, p, threads); break;
+    default: k_sweep_persist<32><<<std::min(need, persist_grid<32>(block)), block, 0, s>>>(d, p, threads); break;
+    }
+}
+
+void launch_sweep_scatter(const Dev &d, const SweepParams &p, int sbegin, int send, int lanes, int block,
+                          cudaStream_t s) {
+    const long long threads = (long long)(p.vend - p.vbegin) * lanes;
+    if (threads <= 0) return;
+    if (send > sbegin) k_scatter_slots<<<blocks_for(send - sbegin, 256), 256, 0, s>>>(d, p, sbegin, send - sbegin);
+    const unsigned grid = blocks_for(threads, block);
+    switch (lanes) {
+    case 4: k_scatter_reduce<4><<<grid, block, 0, s>>>(d, p, sbegin); break;
+    case 8: k_scatter_reduce<8><<<grid, block, 0, s>>>(d, p, sbegin); break;
+    case 16: k_scatter_reduce<16><<<grid, block, 0, s>>>(d, p, sbegin); break;
+    default: k_scatter_reduce<32><<<grid, block, 0, s>>>(d, p, sbegin); break;
+    }
 }
 
 void launch_sweep(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s) {

@@ -28,6 +28,9 @@ struct Dev {
     float4 *s1;       // g_a.yz, g_b.xy
     float4 *s2;       // g_b.z, g_c.xyz
     float2 *vmat;     // per free vertex: (mu, lambda) shared by all its tets
+    int *slot_vtx;    // own vertex of each slot (two-phase scatter sweep only)
+    float4 *scr0, *scr1;  // scatter sweep scratch per slot of one colour: f0 f1 f2 h00 | h01 h02 h11 h12
+    float *scr2;      //                                               h22
     int *slot_tet;    // caller tet id of each slot
     int *slot_loc;    // local index (0..3) of the slot's own vertex in that tet
     // per tet (caller order)
@@ -93,6 +96,11 @@ int num_sms();
 void launch_predict(const Dev &d, int n, int n_free, float h, float3 g, int init_mode,
                     bool cheby, cudaStream_t s);
 void launch_sweep(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s);
+// persistent grid-stride form of launch_sweep (grid = SMs x resident CTAs)
+void launch_sweep_persist(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s);
+// two-phase tet-scatter-into-slots form; slots [sbegin, send) are the colour's
+void launch_sweep_scatter(const Dev &d, const SweepParams &p, int sbegin, int send, int lanes, int block,
+                          cudaStream_t s);
 // pipelined sweep (TMA bulk copies of each chunk's slots into shared memory);
 // maxs = slot capacity of one stage, chunks of block/8 vertices
 size_t sweep_pipe_smem(int maxs);

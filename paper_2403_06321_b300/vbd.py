@@ -56,7 +56,7 @@ class vbd_params(C.Structure):
                 ("init_mode", C.c_int32), ("det_eps", C.c_float), ("k_d", C.c_float),
                 ("tape_steps", C.c_int32), ("mu_c", C.c_float), ("eps_v", C.c_float),
                 ("line_search", C.c_int32), ("jacobi", C.c_int32), ("self_collision", C.c_int32),
-                ("dcd_radius", C.c_float)]
+                ("dcd_radius", C.c_float), ("scatter_sweep", C.c_int32)]
 
 
 class vbd_info(C.Structure):
@@ -260,8 +260,9 @@ def vbd_backward(ctx: int, dL_dxT, dL_dlogE, dL_dv0, adj_iters: int) -> None:
     _check("vbd_backward", ctx, load().vbd_backward(ctx, _ptr(dL_dxT), _ptr(dL_dlogE), _ptr(dL_dv0), adj_iters))
 
 
-def vbd_set_launch(ctx: int, lanes_per_vertex: int = 0, block_threads: int = 0, pipeline: int = -1) -> None:
-    _check("vbd_set_launch", ctx, load().vbd_set_launch(ctx, lanes_per_vertex, block_threads, pipeline))
+def vbd_set_launch(ctx: int, lanes_per_vertex: int = 0, block_threads: int = 0, variant: int = -1) -> None:
+    """variant: 0 plain, 1 TMA-staged, 2 persistent, 3 two-phase scatter (< 0 keeps it)."""
+    _check("vbd_set_launch", ctx, load().vbd_set_launch(ctx, lanes_per_vertex, block_threads, variant))
 
 
 def vbd_set_graph(ctx: int, enable: bool) -> None:
@@ -288,7 +289,7 @@ def vbd_destroy(ctx: int) -> None:
 def make_params(gravity=(0.0, 0.0, -9.8), ground_on=False, ground_height=0.0, ground_normal=(0.0, 0.0, 1.0),
                 k_c=1e7, cheby_rho=0.0, init_mode=3, det_eps=1e-12, k_d=0.0, tape_steps=0, mu_c=0.0,
                 eps_v=1e-3, line_search=False, jacobi=False, self_collision=False, dcd_radius=0.01,
-                **_ignored) -> vbd_params:
+                scatter_sweep=False, **_ignored) -> vbd_params:
     p = vbd_default_params()
     p.gravity[:] = [float(g) for g in gravity]
     p.ground_on = int(bool(ground_on))
@@ -306,6 +307,7 @@ def make_params(gravity=(0.0, 0.0, -9.8), ground_on=False, ground_height=0.0, gr
     p.jacobi = int(bool(jacobi))
     p.self_collision = int(bool(self_collision))
     p.dcd_radius = float(dcd_radius)
+    p.scatter_sweep = int(bool(scatter_sweep))
     return p
 
 

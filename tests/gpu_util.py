@@ -22,13 +22,15 @@ def bbox_diag(x: np.ndarray) -> float:
 
 
 def gpu_run(mesh, pdict: dict, colors, h, iters, steps, x0=None, v0=None, vprev0=None,
-            lanes=None, block=None, graph=True, vert_offset=None, tet_offset=None, pipeline=-1):
+            lanes=None, block=None, graph=True, vert_offset=None, tet_offset=None, variant=-1):
     """Returns (x, v) as float64 numpy arrays in caller order."""
+    if variant == 3:
+        pdict = dict(pdict, scatter_sweep=True)
     sim = vbd.Sim(mesh, vbd.make_params(**pdict), colors=colors,
                   vert_offset=vert_offset, tet_offset=tet_offset)
     try:
-        if lanes or block or pipeline >= 0:
-            vbd.vbd_set_launch(sim.ctx, lanes or 0, block or 0, pipeline)
+        if lanes or block or variant >= 0:
+            vbd.vbd_set_launch(sim.ctx, lanes or 0, block or 0, variant)
         vbd.vbd_set_graph(sim.ctx, graph)
         x0 = mesh.rest if x0 is None else x0
         v0 = np.zeros_like(mesh.rest) if v0 is None else v0

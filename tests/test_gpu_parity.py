@@ -49,8 +49,10 @@ def test_one_iteration_from_perturbed_state_ragged(orc):
     colors, _ = orc.color_greedy(m.n_verts, m.tets)
     pd = params_of(synth.SimConfig())
     xo, vo = oracle_run(orc, m, pd, colors, 1 / 60, 1, 1, x0, v0)
-    shapes = [dict(pipeline=1, block=128), dict(pipeline=1, block=256)] + \
-             [dict(pipeline=0, lanes=l) for l in (4, 8, 16, 32)]
+    shapes = [dict(variant=1, block=128), dict(variant=1, block=256)] + \
+             [dict(variant=0, lanes=l) for l in (4, 8, 16, 32)] + \
+             [dict(variant=2, lanes=4), dict(variant=2, lanes=8, block=256), dict(variant=3, lanes=4),
+              dict(variant=3, lanes=8)]
     results = []
     for sh in shapes:
         xg, vg = gpu_run(m, pd, colors, 1 / 60, 1, 1, x0, v0, **sh)
@@ -58,6 +60,12 @@ def test_one_iteration_from_perturbed_state_ragged(orc):
         results.append(xg)
     # same lanes-per-vertex reduction order: pipelined and plain 8-lane sweeps agree bit for bit
     assert np.array_equal(results[0], results[3]) and np.array_equal(results[1], results[3])
+    # the persistent form is the plain kernel on another grid
+    assert np.array_equal(results[6], results[2]) and np.array_equal(results[7], results[3])
+    # the scatter form sums the same per-slot terms in the same order, but each
+    # term is rounded before it is added (no fused multiply-add into the sum)
+    for a, b in ((results[8], results[2]), (results[9], results[3])):
+        assert _err(a, b, m.rest) <= 1e-7
 
 
 def test_ground_contact_and_chebyshev(orc):
@@ -107,9 +115,9 @@ def test_graph_replay_equals_eager():
     m, cfg = synth.cantilever_beam()
     colors = synth.kuhn_coloring(m.grid_ijk)
     pd = params_of(cfg, cheby_rho=0.8)
-    for pipe in (1, 0):
-        xa, va = gpu_run(m, pd, colors, cfg.h, 7, 5, graph=True, pipeline=pipe)
-        xb, vb = gpu_run(m, pd, colors, cfg.h, 7, 5, graph=False, pipeline=pipe)
+    for pipe in (1, 0, 2, 3):
+        xa, va = gpu_run(m, pd, colors, cfg.h, 7, 5, graph=True, variant=pipe)
+        xb, vb = gpu_run(m, pd, colors, cfg.h, 7, 5, graph=False, variant=pipe)
         assert np.array_equal(xa, xb) and np.array_equal(va, vb)
 
 
