@@ -93,6 +93,10 @@ typedef struct {
     float dcd_radius;        /* detection distance r of the self-collision pairs [m] */
     int32_t scatter_sweep;   /* 1: carve the buffers of the two-phase scatter sweep (variant 3 of
                                 vbd_set_launch); enlarges the workspace, so set it before vbd_bind */
+    int32_t xnew_copy_back;  /* 1: every colour pass writes x^new and copies it back, as Algorithm 1
+                                prints it; without self-collision the default in-place writes give
+                                the same positions bit for bit (no two vertices of one colour share
+                                a tet), so this exists to check that */
 } vbd_params;
 
 /* Library defaults: gravity (0,0,-9.8), ground off at z = 0 with n = +z,

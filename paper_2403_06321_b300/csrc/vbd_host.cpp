@@ -338,7 +338,7 @@ SweepParams sweep_params(const vbd_ctx *c, int color) {
     p.line_search = c->params.line_search ? 1 : 0;
     p.per_tet_mat = c->per_tet_mat ? 1 : 0;
     p.self_collision = c->params.self_collision && c->sc_carved ? 1 : 0;
-    p.to_unew = c->params.jacobi ? 1 : 0;
+    p.to_unew = (c->params.jacobi || c->params.xnew_copy_back) ? 1 : 0;
     if (c->params.jacobi && color >= 0) {  // one pass over every free vertex
         p.vbegin = 0;
         p.vend = c->n_free;
@@ -416,6 +416,9 @@ void launch_colour(vbd_ctx *c, int col, cudaStream_t s) {
     if (p.self_collision) {
         vbd::launch_sweep(c->d, p, c->lanes, c->block, s);
         vbd::launch_copy_back(c->d, p.vbegin, p.vend, !p.to_unew, s);
+    } else if (p.to_unew) {  // Algorithm 1 as printed: x^new, then copy back
+        vbd::launch_sweep(c->d, p, c->lanes, c->block, s);
+        vbd::launch_copy_back(c->d, p.vbegin, p.vend, false, s);
     } else if (c->variant == 1) {
         vbd::launch_sweep_pipe(c->d, p, c->pipe_block, c->pipe_maxs, c->pipe_grid_cap, s);
     } else if (c->variant == 2) {
