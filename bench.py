@@ -181,9 +181,10 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload_key: str):
-    """DRAM bytes per sweep launch from the committed ncu summary, if it was
-    taken on the current kernel source."""
+def profiled_traffic(workload_key: str, updates_per_launch: float):
+    """DRAM bytes per sweep launch from the committed ncu summary (bytes per
+    vertex update, measured on a smaller case of the same recipe, times the
+    updates of this launch), if it was taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "sweep_%s.md" % workload_key)
     try:
         lines = open(p).read().splitlines()
@@ -197,7 +198,7 @@ def profiled_traffic(workload_key: str):
     if kv.get("kernel_source_sha") != kernel_source_sha():
         return None
     try:
-        return float(kv["dram_bytes_per_launch"])
+        return float(kv["dram_bytes_per_update"]) * updates_per_launch
     except (KeyError, ValueError):
         return None
 
@@ -603,7 +604,8 @@ def run_ours(args):
     avg_launch_s = sweep_ms / 1e3 / launches_sweep
     achieved = bytes_per_launch / avg_launch_s / 1e9
     peak, peak_kind = measured_peak_hbm()
-    traffic = profiled_traffic("large_cube") if args.scene == "cube" else None
+    traffic = (profiled_traffic("large_cube", info.n_free / C)
+               if args.scene == "cube" and not args.jacobi and info.pipeline in (0, 2) else None)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": t_job * 1e3 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
