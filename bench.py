@@ -67,6 +67,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched, adjoint and self-collision comparisons")
     ap.add_argument("--batch-meshes", type=int, default=4096)
+    ap.add_argument("--only", choices=["batched", "adjoint", "self_collision", "small_configs"], default=None,
+                    help="run one of the comparisons alone and print it as the JSON line (for profiling)")
     args = ap.parse_args(argv)
     if not args.n:
         args.n = 300 if args.scene == "slabs" else 100
@@ -632,10 +634,23 @@ def run_ours(args):
     return 0
 
 
+def run_only(args) -> int:
+    import torch
+    from paper_2403_06321_b300.build import build
+    build()
+    torch.cuda.set_device(0)
+    fn = {"batched": run_batched, "adjoint": run_adjoint, "self_collision": run_self_collision,
+          "small_configs": run_small_configs}[args.only]
+    print(json.dumps({"only": args.only, args.only: fn(args)}), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args)
     return run_ours(args)
 
 
