@@ -97,3 +97,26 @@ def test_adjoint_differentiable_beam_full_size(orc):
         np.abs(xg - xo).max() / diag, _rel(gE, oE), _rel(gv, ov)))
     assert np.abs(xg - xo).max() <= 1e-5 * diag
     assert _rel(gE, oE) <= 1e-3 and _rel(gv, ov) <= 1e-3
+
+
+def test_adjoint_with_ground_contact(orc):
+    """A free block falling onto the ground (k_c = 1e5), 6 steps solved to
+    convergence on both sides; the adjoint then includes the contact
+    Hessian k_c n n^T of every penetrating vertex."""
+    m = synth.beam(4, 3, 2, edge=0.05, E=1e5, nu=0.4, pin_face=None, jitter_frac=0.05, seed=53)
+    m.rest[:, 2] -= m.rest[:, 2].min()  # lowest vertex on the plane
+    colors, _ = orc.color_greedy(m.n_verts, m.tets)
+    pd = params_of(synth.SimConfig(), ground_on=True, k_c=1e5)
+    rng = np.random.default_rng(54)
+    v0 = rng.normal(0, 0.05, m.rest.shape)
+    v0[:, 2] = -0.3
+    top = np.nonzero(m.grid_ijk[:, 2] == 2)[0]
+    target = m.rest[top] + np.array([0.01, -0.02, -0.01])
+    h, steps = 1 / 60, 6
+    gE, gv, xg = _gpu_grads(m, pd, colors, h, 600, steps, v0, top, target, adj_iters=400)
+    oE, ov, xo = _oracle_grads(orc, m, pd, colors, h, 0, steps, v0, top, target, newton=True)
+    assert (xo[:, 2] < 0).sum() >= 4  # vertices in contact at the last step
+    print("ground contact: |x|err %.2e  dlogE rel %.2e  dv0 rel %.2e" % (
+        np.abs(xg - xo).max(), _rel(gE, oE), _rel(gv, ov)))
+    assert np.abs(xg - xo).max() < 1e-5
+    assert _rel(gE, oE) <= 1e-3 and _rel(gv, ov) <= 1e-3

@@ -103,43 +103,81 @@ def test_energy_with_contacts_matches_oracle(orc):
     assert G_gpu == pytest.approx(G0, rel=1e-5)
 
 
-@pytest.mark.parametrize("cheby", [0.0, 0.8])
-def test_slabs_trajectory_matches_oracle(orc, cheby):
-    """10 steps x 20 iterations of the slab scene (870 vertices, about 220
-    pairs per step); pairs compared at every step start."""
-    m, cfg, u0 = synth.colliding_slabs(seed=7)
-    pd = params_of(cfg, cheby_rho=cheby)
+def _trajectory(orc, m, pd, h, iters, steps, v0=None):
+    """Step by step on both sides with the library's colouring; returns the
+    worst position error over the steps (/ bbox), the oracle's final
+    positions, and the pair count of each step."""
     model = orc.Model.from_mesh(m)
     p = orc.Params.make(**pd)
     sim = _sim(m, pd, None)
+    counts = []
     try:
         colors = vbd.vbd_get_colors(sim.ctx, m.n_verts)
         nc = int(colors.max()) + 1
         tris = vbd.vbd_get_surface(sim.ctx)
         x = _f32(m.rest)
-        v = np.zeros_like(x)
+        v = np.zeros_like(x) if v0 is None else _f32(v0)
         vp = v.copy()
         sim.set_state(x, v)
         worst = 0.0
-        for step in range(cfg.steps):
-            vbd.vbd_begin_step(sim.ctx, cfg.h)
+        for step in range(steps):
+            vbd.vbd_begin_step(sim.ctx, h)
             got = vbd.vbd_get_contacts(sim.ctx, m.n_verts)
-            vbd.vbd_iterate(sim.ctx, cfg.iters)
+            vbd.vbd_iterate(sim.ctx, iters)
             vbd.vbd_end_step(sim.ctx)
             xt = x.copy()
-            model.step(p, colors, nc, cfg.h, cfg.iters, x, v, vp)  # DCD on x^t, then the iterations
+            model.step(p, colors, nc, h, iters, x, v, vp)  # DCD on x^t, then the iterations
             want = model.contacts()
             assert _pairs_agree(orc, model, p, xt, tris, got, want) == 0, step
-            assert (want >= 0).sum() > 20
+            counts.append(int((want >= 0).sum()))
             xg, _ = sim.get_state()
             worst = max(worst, float(np.abs(xg.cpu().numpy() - x).max()))
         sim.sync_status()
     finally:
         sim.close()
-    err = worst / bbox_diag(m.rest)
-    print("slabs cheby %.1f: max |x_gpu - x_oracle| / bbox = %.3e" % (cheby, err))
+    return worst / bbox_diag(m.rest), x, counts
+
+
+@pytest.mark.parametrize("extra", [dict(), dict(cheby_rho=0.8), dict(k_d=1e-5)],
+                         ids=["plain", "chebyshev", "damping"])
+def test_slabs_trajectory_matches_oracle(orc, extra):
+    """10 steps x 20 iterations of the slab scene (870 vertices, about 220
+    pairs per step); pairs compared at every step start; self-contact alone,
+    with Chebyshev and with Rayleigh damping."""
+    m, cfg, u0 = synth.colliding_slabs(seed=7)
+    err, x, counts = _trajectory(orc, m, params_of(cfg, **extra), cfg.h, cfg.iters, cfg.steps)
+    print("slabs %s: max |x_gpu - x_oracle| / bbox = %.3e, pairs %s" % (extra, err, counts))
+    assert min(counts) > 20
     assert np.abs(x - m.rest).max() > 1e-3  # the contact pushed the slabs apart
     assert err <= TOL
+
+
+def test_blocks_sliding_on_the_ground_with_self_contact(orc):
+    """A free 3x3x1 block resting on the ground and a 2x2x1 block sunk 4 mm
+    into it, both sliding at 0.3 m/s: ground penalty, ground friction
+    (mu = 0.3) and self-contact together, 10 steps x 20 iterations."""
+    lower = synth.beam(3, 3, 1, edge=0.1, E=1e5, nu=0.4, pin_face=None, jitter_frac=0.02, seed=111)
+    lower.rest[:, 2] -= lower.rest[:, 2].min() - 0.001
+    upper = synth.beam(2, 2, 1, edge=0.1, E=1e5, nu=0.4, pin_face=None, jitter_frac=0.02, seed=112,
+                       origin=(0.03, 0.04, 0.096))
+    cat, voff, _ = synth.concat([lower, upper])
+    pd = params_of(synth.SimConfig(k_c=1e5, self_collision=True, dcd_radius=0.05), ground_on=True, mu_c=0.3)
+    v0 = np.zeros_like(cat.rest)
+    v0[:, 0] = 0.3
+    err, x, counts = _trajectory(orc, cat, pd, 1 / 60, 20, 10, v0)
+    print("blocks on ground: err / bbox = %.3e, pairs %s" % (err, counts))
+    assert min(counts) > 0 and x[:voff[1], 2].min() < 0.0  # both kinds of contact act
+    assert err <= TOL
+
+
+def test_jacobi_with_self_contact_first_iterations(orc):
+    """Block Jacobi with self-contact (every vertex against the previous
+    iterate).  It diverges on this scene after a few steps, as Jacobi does on
+    stiff settings, so one step of 3 iterations is compared."""
+    m, cfg, u0 = synth.colliding_slabs(seed=7)
+    err, x, counts = _trajectory(orc, m, params_of(cfg, jacobi=True), cfg.h, 3, 1)
+    print("jacobi + self-contact: err / bbox = %.3e" % err)
+    assert counts[0] > 100 and err <= 1e-6
 
 
 def test_block_rests_on_block_and_falls_through_without_contact(orc):
