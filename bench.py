@@ -33,8 +33,9 @@ UNIT = "vertex-block updates/s"
 # vertex I/O + one re-read of neighbour positions per colour pass)
 B_INC, B_VTX, B_X = 52, 44, 12
 B_SC = 24  # with self-collision: contact[i] and rev_off[i], rev_off[i+1], in the sweep and the copy-back
-VARIANTS = {0: "plain", 1: "tma_staged", 2: "persistent", 3: "two_phase_scatter"}
-KERNELS = {0: "k_sweep", 1: "k_sweep_pipe", 2: "k_sweep_persist", 3: "k_scatter_slots + k_scatter_reduce"}
+VARIANTS = {0: "plain", 1: "tma_staged", 2: "persistent", 3: "two_phase_scatter", 4: "fused_cluster_loop"}
+KERNELS = {0: "k_sweep", 1: "k_sweep_pipe", 2: "k_sweep_persist", 3: "k_scatter_slots + k_scatter_reduce",
+           4: "k_iterate_fused"}
 NOMINAL_HBM_GBS = 7700.0  # B300 HBM3e nominal bandwidth, for context beside the measured peak
 DETECT_LAUNCHES = 20   # kernels and memsets of one self-collision detection (three prefix sums)
 CPU_SAMPLE_N = 32      # the CPU legs run a 32^3-cube crop of the same recipe
@@ -55,7 +56,8 @@ def parse_args(argv=None):
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--variant", type=int, default=-1,
-                    help="sweep kernel: 0 plain, 1 TMA-staged, 2 persistent, 3 two-phase scatter; -1 autotune")
+                    help="sweep kernel: 0 plain, 1 TMA-staged, 2 persistent, 3 two-phase scatter, "
+                         "4 fused loop (small meshes); -1 autotune")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shape")
     ap.add_argument("--mu-c", type=float, default=0.0, help="ground friction coefficient (Eqs. 13-16)")
@@ -457,6 +459,9 @@ def run_small_configs(args) -> dict:
     stream = torch.cuda.Stream()
     sim = vbd.Sim(m, vbd.make_params(gravity=cfg.gravity), colors=synth.kuhn_coloring(m.grid_ijk), stream=stream)
     sim.set_state(m.rest, np.zeros_like(m.rest))
+    vbd.vbd_autotune(sim.ctx, cfg.h, cfg.iters)
+    chosen = VARIANTS[vbd.vbd_get_info(sim.ctx).pipeline]
+    sim.set_state(m.rest, np.zeros_like(m.rest))
     for _ in range(5):
         sim.step(cfg.h, cfg.iters)
     t = _timed(stream, lambda: sim.step(cfg.h, cfg.iters), cfg.steps)
@@ -464,12 +469,15 @@ def run_small_configs(args) -> dict:
     sim.close()
     out["cantilever_beam"] = {"workload": "10x3x3 cubes (176 verts, 540 tets), x=0 face pinned, h=1/60, "
                                           "%d iterations/step" % cfg.iters,
-                              "ms_per_step": t * 1e3 / cfg.steps}
+                              "ms_per_step": t * 1e3 / cfg.steps, "sweep_variant": chosen}
     m, cfg, tip, target = synth.differentiable_beam()
     params = vbd.make_params(gravity=cfg.gravity, tape_steps=cfg.steps)
     sim = vbd.Sim(m, params, colors=synth.kuhn_coloring(m.grid_ijk), stream=stream)
     dev = sim.workspace.device
     zeros = np.zeros_like(m.rest)
+    sim.set_state(m.rest, zeros)
+    vbd.vbd_autotune(sim.ctx, cfg.h, cfg.iters)
+    chosen = VARIANTS[vbd.vbd_get_info(sim.ctx).pipeline]
     gx = torch.zeros(3 * m.n_verts, dtype=torch.float32, device=dev)
     gE = torch.empty(m.n_tets, dtype=torch.float32, device=dev)
     gv = torch.empty(3 * m.n_verts, dtype=torch.float32, device=dev)
@@ -487,7 +495,8 @@ def run_small_configs(args) -> dict:
     out["differentiable_beam"] = {"workload": "40x8x8 cubes (3,321 verts, 15,360 tets), %d steps x %d iterations, "
                                               "adjoint %d block-GS iterations per step" % (
                                                   cfg.steps, cfg.iters, cfg.iters),
-                                  "ms_per_step": t_f * 1e3 / cfg.steps, "ms_backward_per_step": t_b * 1e3 / cfg.steps}
+                                  "ms_per_step": t_f * 1e3 / cfg.steps, "ms_backward_per_step": t_b * 1e3 / cfg.steps,
+                                  "sweep_variant": chosen}
     return out
 
 

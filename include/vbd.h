@@ -145,7 +145,7 @@ typedef struct {
     int64_t n_slots;         /* (free vertex, incident tet) pairs streamed per iteration */
     int32_t lanes_per_vertex, block_threads;   /* current sweep launch shape */
     int32_t pipeline;        /* sweep variant of vbd_set_launch (0 plain, 1 TMA-staged, 2 persistent,
-                                3 two-phase scatter) */
+                                3 two-phase scatter, 4 fused loop) */
     int32_t pipe_stage_slots; /* slot capacity of one pipeline stage */
     int32_t pipe_ctas_per_sm; /* resident CTAs per SM of the pipelined sweep */
     int32_t use_graph;       /* vbd_iterate replays a CUDA graph */
@@ -304,8 +304,14 @@ vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, floa
  *  3  two-phase tet-scatter-into-slots: one thread per incidence writes that
  *     tet's force and Hessian block on its vertex to a scratch slot, then a
  *     per-vertex kernel adds them up and solves (needs scatter_sweep = 1 at
- *     bind time, else VBD_ERR_STATE).
- * All variants give the same positions: 0 and 2 bit for bit with equal
+ *     bind time, else VBD_ERR_STATE);
+ *  4  fused loop for small meshes: each vbd_iterate is one launch of one
+ *     thread-block cluster (up to 8 CTAs of 512 threads) that runs every
+ *     colour pass and the Chebyshev update, the CTAs meeting at the
+ *     hardware cluster barrier between passes (block_threads is ignored;
+ *     VBD_ERR_INVALID_ARG when the largest colour exceeds two rounds of the
+ *     cluster, 2048 vertices with 4 lanes).
+ * All variants give the same positions: 0, 2 and 4 bit for bit with equal
  * lanes, 1 equals 0 with 8 lanes, and 3 agrees to FP32 rounding (each
  * incidence's terms are rounded before they are summed).  Self-collision passes always use the
  * plain form with contacts, and block Jacobi the plain form.  0 keeps a

@@ -84,7 +84,9 @@ struct vbd_ctx {
     std::vector<float> tape_h;
     // launch shape / graphs
     int lanes = 4, block = 256;
-    int variant = 2;            // sweep kernel: 0 plain, 1 TMA-staged, 2 persistent, 3 two-phase scatter
+    int variant = 2;            // sweep kernel: 0 plain, 1 TMA-staged, 2 persistent, 3 two-phase scatter,
+                                // 4 fused iteration loop in one cluster
+    int fused_cluster = 0;      // CTAs of that cluster
     int pipe_block = 128;
     int pipe_maxs = 0;          // slot capacity of one stage
     int pipe_ctas_per_sm = 0;
@@ -254,6 +256,7 @@ size_t carve(const vbd_ctx *c, char *base, Dev *d) {
     t.cheb[1] = (float4 *)take(16 * N);
     t.mass = (float *)take(4 * N);
     t.slot_off = (int *)take(4 * ((size_t)c->n_free + 1));
+    t.color_begin = (int *)take(4 * ((size_t)c->n_colors + 1));
     t.s0 = (int4 *)take(16 * S);
     t.s1 = (float4 *)take(16 * S);
     t.s2 = (float4 *)take(16 * S);
@@ -430,9 +433,35 @@ void launch_colour(vbd_ctx *c, int col, cudaStream_t s) {
     }
 }
 
+// largest colour (free vertices)
+int max_colour_verts(const vbd_ctx *c) {
+    int mx = 0;
+    for (int col = 0; col < c->n_colors; ++col) mx = std::max(mx, c->color_begin[col + 1] - c->color_begin[col]);
+    return mx;
+}
+
+// the fused loop applies to plain Gauss-Seidel passes (no self-collision, no
+// Jacobi, no explicit x^new copy-back) of a mesh whose largest colour fits
+bool fused_applies(const vbd_ctx *c) {
+    return c->variant == 4 && c->fused_cluster > 0 && !c->params.jacobi && !c->params.xnew_copy_back &&
+           !(c->params.self_collision && c->sc_carved);
+}
+
 // enqueue iterations n = first_n+1 .. first_n+iters on stream s
 void enqueue_iterations(vbd_ctx *c, int first_n, int iters, cudaStream_t s) {
     const bool cheby = c->params.cheby_rho > 0.f;
+    if (fused_applies(c)) {
+        vbd::FusedParams f{};
+        f.p = sweep_params(c, 0);
+        f.n_colors = c->n_colors;
+        f.first_n = first_n;
+        f.iters = iters;
+        f.cheby = cheby ? 1 : 0;
+        f.n_free = c->n_free;
+        f.rho = (double)c->params.cheby_rho;
+        vbd::launch_iterate_fused(c->d, f, c->lanes, c->fused_cluster, s);
+        return;
+    }
     for (int n = first_n + 1; n <= first_n + iters; ++n) {
         if (c->params.jacobi) {
             vbd::launch_sweep(c->d, sweep_params(c, 0), c->lanes, c->block, s);
@@ -743,7 +772,7 @@ vbd_status vbd_get_info(const vbd_ctx *ctx, vbd_info *out) {
     out->n_colors = ctx->colored ? ctx->n_colors : 0;
     out->n_slots = ctx->colored ? ctx->n_slots : 0;
     out->lanes_per_vertex = ctx->variant == 1 ? 8 : ctx->lanes;
-    out->block_threads = ctx->variant == 1 ? ctx->pipe_block : ctx->block;
+    out->block_threads = ctx->variant == 1 ? ctx->pipe_block : (ctx->variant == 4 ? vbd::kFusedThreads : ctx->block);
     out->pipeline = ctx->variant;
     out->pipe_stage_slots = ctx->pipe_maxs;
     out->pipe_ctas_per_sm = ctx->pipe_ctas_per_sm;
@@ -794,6 +823,8 @@ vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *st
     CU(cudaMemcpyAsync(d.mass, massf.data(), 4 * (size_t)N, cudaMemcpyHostToDevice, s), "upload mass");
     CU(cudaMemcpyAsync(d.slot_off, ctx->slot_off.data(), 4 * ((size_t)ctx->n_free + 1), cudaMemcpyHostToDevice, s),
        "upload slot_off");
+    CU(cudaMemcpyAsync(d.color_begin, ctx->color_begin.data(), 4 * ((size_t)ctx->n_colors + 1),
+                       cudaMemcpyHostToDevice, s), "upload colour ranges");
     {
         // per-vertex material when every tet around each free vertex shares it
         std::vector<float2> vm(N, make_float2(0.f, 0.f));
@@ -1211,7 +1242,7 @@ vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, floa
 
 vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_threads, int32_t variant) {
     if (!ctx) return VBD_ERR_INVALID_ARG;
-    if (variant > 3) return fail(ctx, VBD_ERR_INVALID_ARG, "sweep variant must be 0..3 (or < 0 to keep it)");
+    if (variant > 4) return fail(ctx, VBD_ERR_INVALID_ARG, "sweep variant must be 0..4 (or < 0 to keep it)");
     const int var = variant < 0 ? ctx->variant : variant;
     const bool pipe = var == 1;
     if (var == 3 && !ctx->params.scatter_sweep)
@@ -1226,6 +1257,16 @@ vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_
             return fail(ctx, VBD_ERR_INVALID_ARG, "the pipelined sweep takes block_threads 128 or 256");
     } else if (block_threads != 0 && block_threads != 64 && block_threads != 128 && block_threads != 256) {
         return fail(ctx, VBD_ERR_INVALID_ARG, "block_threads must be 64, 128 or 256");
+    }
+    if (var == 4) {
+        if (!ctx->colored) return fail(ctx, VBD_ERR_NOT_COLORED, "the fused loop needs the colouring");
+        const int cl = vbd::fused_clusters_needed(max_colour_verts(ctx), lanes_per_vertex ? lanes_per_vertex : ctx->lanes);
+        if (cl == 0)
+            return fail(ctx, VBD_ERR_INVALID_ARG, "largest colour too large for the fused loop (at most " +
+                                                      std::to_string(vbd::kFusedMaxCluster * vbd::kFusedThreads *
+                                                                     vbd::kFusedMaxRounds / 4) +
+                                                      " vertices with 4 lanes)");
+        ctx->fused_cluster = cl;
     }
     ctx->variant = var;
     if (lanes_per_vertex) ctx->lanes = lanes_per_vertex;
@@ -1256,9 +1297,9 @@ vbd_status vbd_autotune(vbd_ctx *ctx, float h, int32_t iters, float *best_ms_per
     if (ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_autotune inside a step");
     if (iters < 1) return fail(ctx, VBD_ERR_INVALID_ARG, "iters must be >= 1");
     struct Shape { int pipe, lanes, block; };
-    const Shape shapes[] = {{0, 4, 64}, {0, 4, 128}, {0, 4, 256}, {0, 8, 128}, {0, 8, 256},
-                            {0, 16, 256}, {1, 8, 128}, {1, 8, 256}, {2, 4, 128}, {2, 4, 256},
-                            {2, 8, 256}, {3, 4, 128}};
+    const Shape shapes[] = {{0, 4, 64}, {0, 4, 128}, {0, 4, 256}, {0, 8, 64}, {0, 8, 128}, {0, 8, 256},
+                            {0, 16, 64}, {0, 16, 256}, {1, 8, 128}, {1, 8, 256}, {2, 4, 128}, {2, 4, 256},
+                            {2, 8, 256}, {3, 4, 128}, {4, 4, 0}, {4, 8, 0}, {4, 16, 0}};
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0), "event");
     CU(cudaEventCreate(&e1), "event");

@@ -21,7 +21,11 @@
 #include <cstdio>
 #include <mutex>
 
+#include <cooperative_groups.h>
+
 #include "vbd_geom.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace vbd {
 
@@ -62,12 +66,21 @@ __device__ __forceinline__ float2 slot_material(const Dev &d, const SweepParams 
     return make_float2(V * vm.x, V * vm.y);
 }
 
+// Neighbour positions: through the read-only path when no other CTA writes d.u
+// during the launch (one launch per colour), else from L2 (COH: the fused
+// iteration kernel, where other CTAs of the cluster wrote the previous colour).
+template <bool COH>
+__device__ __forceinline__ float4 load_u(const float4 *u, int i) {
+    return COH ? __ldcg(u + i) : __ldg(u + i);
+}
+
+template <bool COH = false>
 __device__ __forceinline__ void accumulate_slot(const Dev &d, const SweepParams &p, int s, float2 vm,
                                                 int4 r0, float4 r1, float4 r2, float3 ui, Acc &acc) {
     const float4 *__restrict__ u = d.u;
-    const float3 da = f3(__ldg(u + r0.x)) - ui;
-    const float3 db = f3(__ldg(u + r0.y)) - ui;
-    const float3 dc = f3(__ldg(u + r0.z)) - ui;
+    const float3 da = f3(load_u<COH>(u, r0.x)) - ui;
+    const float3 db = f3(load_u<COH>(u, r0.y)) - ui;
+    const float3 dc = f3(load_u<COH>(u, r0.z)) - ui;
     const float3 ga = make_float3(__int_as_float(r0.w), r1.x, r1.y);
     const float3 gb = make_float3(r1.z, r1.w, r2.x);
     const float3 gc = make_float3(r2.y, r2.z, r2.w);
@@ -272,7 +285,7 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
 }
 
 // One colour pass for the vertex of global thread gt (L lanes per vertex).
-template <int L, bool SC>
+template <int L, bool SC, bool COH = false>
 __device__ __forceinline__ void sweep_body(const Dev &d, const SweepParams &p, long long gt) {
     const int lane = threadIdx.x & (L - 1);
     const int vi = p.vbegin + (int)(gt / L);
@@ -280,7 +293,7 @@ __device__ __forceinline__ void sweep_body(const Dev &d, const SweepParams &p, l
     float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
     int s0 = 0, s1 = 0;
     if (active) {
-        xi = d.u[vi];
+        xi = COH ? __ldcg(d.u + vi) : d.u[vi];
         s0 = d.slot_off[vi];
         s1 = d.slot_off[vi + 1];
     }
@@ -288,7 +301,7 @@ __device__ __forceinline__ void sweep_body(const Dev &d, const SweepParams &p, l
     const float2 vm = (active && !p.per_tet_mat) ? __ldg(d.vmat + vi) : make_float2(0.f, 0.f);
     Acc acc = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int s = s0 + lane; s < s1; s += L)
-        accumulate_slot(d, p, s, vm, __ldcs(d.s0 + s), __ldcs(d.s1 + s), __ldcs(d.s2 + s), x3, acc);
+        accumulate_slot<COH>(d, p, s, vm, __ldcs(d.s0 + s), __ldcs(d.s1 + s), __ldcs(d.s2 + s), x3, acc);
     acc.f0 = sub_reduce<L>(acc.f0);
     acc.f1 = sub_reduce<L>(acc.f1);
     acc.f2 = sub_reduce<L>(acc.f2);
@@ -615,19 +628,57 @@ __global__ void k_predict(Dev d, int n, int n_free, float h, float3 g, float gno
 // Eq. 18 after iteration n: history buffer cheb[n & 1] holds x^(n-2) on entry
 // and x^(n) on exit; the other buffer holds x^(n-1).  Vertices flagged in
 // ground contact (x.w != 0) keep the Gauss-Seidel result.
-__global__ void k_cheby(Dev d, int n_free, int n, float omega) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_free) return;
+template <bool COH>
+__device__ __forceinline__ void cheby_vertex(const Dev &d, int i, int n, float omega) {
     float4 *hist = d.cheb[n & 1];
-    const float4 xb = d.u[i];
+    const float4 xb = COH ? __ldcg(d.u + i) : d.u[i];
     float4 xn = xb;
     if (n >= 2 && xb.w == 0.f) {
-        const float4 q = hist[i];
+        const float4 q = COH ? __ldcg(hist + i) : hist[i];
         xn = make_float4(omega * (xb.x - q.x) + q.x, omega * (xb.y - q.y) + q.y,
                          omega * (xb.z - q.z) + q.z, xb.w);
         d.u[i] = xn;
     }
     hist[i] = xn;
+}
+
+__global__ void k_cheby(Dev d, int n_free, int n, float omega) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_free) cheby_vertex<false>(d, i, n, omega);
+}
+
+// ---- fused iteration loop for small meshes ------------------------------------
+// All iterations of vbd_iterate in one launch of one thread-block cluster: the
+// CTAs split each colour pass (and the Chebyshev update) and meet at the
+// hardware cluster barrier between passes, whose release/acquire ordering
+// makes one pass's writes visible to the next; positions are then read from
+// L2 (__ldcg), never through the non-coherent path.  Same arithmetic as the
+// per-colour launches, so the results are identical bit for bit.
+template <int L>
+__global__ void __launch_bounds__(kFusedThreads) k_iterate_fused(Dev d, FusedParams f) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const long long rank = cluster.block_rank();
+    const long long stride = (long long)cluster.num_blocks() * blockDim.x;
+    for (int n = f.first_n + 1; n <= f.first_n + f.iters; ++n) {
+        for (int c = 0; c < f.n_colors; ++c) {
+            SweepParams p = f.p;
+            p.vbegin = d.color_begin[c];
+            p.vend = d.color_begin[c + 1];
+            const long long threads = (long long)(p.vend - p.vbegin) * L;
+            for (long long base = rank * blockDim.x; base < threads; base += stride)
+                sweep_body<L, false, true>(d, p, base + threadIdx.x);
+            cluster.sync();
+        }
+        if (f.cheby) {
+            // omega_n of Eq. 19, the same FP64 recurrence as the host's
+            const double r2 = f.rho * f.rho;
+            double w = 1.0;
+            for (int k = 2; k <= n; ++k) w = (k == 2) ? 2.0 / (2.0 - r2) : 4.0 / (4.0 - r2 * w);
+            for (long long i = rank * blockDim.x + threadIdx.x; i < f.n_free; i += stride)
+                cheby_vertex<true>(d, (int)i, n, (float)w);
+            cluster.sync();
+        }
+    }
 }
 
 // Eq. 6; v^{t-1} <- v^t; optional tape row.
@@ -880,6 +931,34 @@ void launch_sweep_pipe(const Dev &d, const SweepParams &p, int block, int maxs, 
         k_sweep_pipe<256><<<grid, 256, smem, s>>>(d, p, maxs);
     else
         k_sweep_pipe<128><<<grid, 128, smem, s>>>(d, p, maxs);
+}
+
+int fused_clusters_needed(int max_colour_verts, int lanes) {
+    const long long threads = (long long)max_colour_verts * lanes;
+    const long long per_round = (long long)kFusedMaxCluster * kFusedThreads;
+    if (threads > per_round * kFusedMaxRounds) return 0;
+    return (int)std::max<long long>(1, std::min<long long>(kFusedMaxCluster, (threads + kFusedThreads - 1) / kFusedThreads));
+}
+
+cudaError_t launch_iterate_fused(const Dev &d, const FusedParams &f, int lanes, int cluster, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cluster, 1, 1);
+    cfg.blockDim = dim3(kFusedThreads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    switch (lanes) {
+    case 4: return cudaLaunchKernelEx(&cfg, k_iterate_fused<4>, d, f);
+    case 8: return cudaLaunchKernelEx(&cfg, k_iterate_fused<8>, d, f);
+    case 16: return cudaLaunchKernelEx(&cfg, k_iterate_fused<16>, d, f);
+    default: return cudaLaunchKernelEx(&cfg, k_iterate_fused<32>, d, f);
+    }
 }
 
 void launch_cheby(const Dev &d, int n_free, int n, float omega, cudaStream_t s) {

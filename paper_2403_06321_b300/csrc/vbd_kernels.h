@@ -23,6 +23,7 @@ struct Dev {
     float4 *cheb[2];  // Chebyshev history (Eq. 18), roles alternate with iteration parity
     float *mass;      // lumped mass
     int *slot_off;    // n_free + 1: slots of free vertex i are [slot_off[i], slot_off[i+1])
+    int *color_begin; // n_colors + 1: free vertices of colour c are [color_begin[c], color_begin[c+1])
     // incidence slots (one per (free vertex, incident tet)), 48 bytes each:
     int4 *s0;         // other three vertex ids, bits of g_a.x
     float4 *s1;       // g_a.yz, g_b.xy
@@ -84,6 +85,16 @@ struct SweepParams {
     int self_collision;  // add the vertex-triangle contact forces of the current pairs
 };
 
+// the fused iteration loop (one launch of one thread-block cluster per vbd_iterate)
+struct FusedParams {
+    SweepParams p;    // vbegin / vend are set per colour from Dev::color_begin
+    int n_colors, first_n, iters, cheby, n_free;
+    double rho;
+};
+constexpr int kFusedThreads = 512;
+constexpr int kFusedMaxCluster = 8;   // portable cluster size
+constexpr int kFusedMaxRounds = 2;    // passes of the CTAs over the largest colour
+
 // sizes of the self-collision arrays
 struct CollideDims {
     int n_tris, n_surf, n_buckets;
@@ -108,6 +119,9 @@ int sweep_pipe_chunk(int block);
 cudaError_t sweep_pipe_prepare(int block, int maxs, int *ctas_per_sm);
 void launch_sweep_pipe(const Dev &d, const SweepParams &p, int block, int maxs, int grid_cap, cudaStream_t s);
 void launch_cheby(const Dev &d, int n_free, int n, float omega, cudaStream_t s);
+// CTAs of the cluster for the fused loop, or 0 when the largest colour does not fit
+int fused_clusters_needed(int max_colour_verts, int lanes);
+cudaError_t launch_iterate_fused(const Dev &d, const FusedParams &f, int lanes, int cluster, cudaStream_t s);
 void launch_finish(const Dev &d, int n, float h, float4 *tape_row, cudaStream_t s);
 // caller order <-> internal order; with `rest` non-null the caller array holds
 // positions and the internal one displacements (u = x - X)

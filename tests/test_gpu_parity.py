@@ -52,7 +52,7 @@ def test_one_iteration_from_perturbed_state_ragged(orc):
     shapes = [dict(variant=1, block=128), dict(variant=1, block=256)] + \
              [dict(variant=0, lanes=l) for l in (4, 8, 16, 32)] + \
              [dict(variant=2, lanes=4), dict(variant=2, lanes=8, block=256), dict(variant=3, lanes=4),
-              dict(variant=3, lanes=8)]
+              dict(variant=3, lanes=8), dict(variant=4, lanes=4), dict(variant=4, lanes=8)]
     results = []
     for sh in shapes:
         xg, vg = gpu_run(m, pd, colors, 1 / 60, 1, 1, x0, v0, **sh)
@@ -66,6 +66,8 @@ def test_one_iteration_from_perturbed_state_ragged(orc):
     # term is rounded before it is added (no fused multiply-add into the sum)
     for a, b in ((results[8], results[2]), (results[9], results[3])):
         assert _err(a, b, m.rest) <= 1e-7
+    # the fused cluster loop runs the same passes inside one launch
+    assert np.array_equal(results[10], results[2]) and np.array_equal(results[11], results[3])
 
 
 def test_ground_contact_and_chebyshev(orc):
@@ -115,10 +117,14 @@ def test_graph_replay_equals_eager():
     m, cfg = synth.cantilever_beam()
     colors = synth.kuhn_coloring(m.grid_ijk)
     pd = params_of(cfg, cheby_rho=0.8)
-    for pipe in (1, 0, 2, 3):
+    out = {}
+    for pipe in (1, 0, 2, 3, 4):
         xa, va = gpu_run(m, pd, colors, cfg.h, 7, 5, graph=True, variant=pipe)
         xb, vb = gpu_run(m, pd, colors, cfg.h, 7, 5, graph=False, variant=pipe)
         assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+        out[pipe] = xa
+    # persistent and fused (with its in-kernel Chebyshev update) equal the plain launches
+    assert np.array_equal(out[2], out[0]) and np.array_equal(out[4], out[0])
 
 
 def test_energy_fp64_matches_oracle(orc):
