@@ -447,6 +447,21 @@ def run_self_collision(args) -> dict:
             "ratio_vs_plain": out[True][0] / out[False][0]}
 
 
+def launches_per_step(args, info, iters: int, C: int) -> int:
+    """Kernels of one timed step: predict + finish, and per iteration the
+    sweep launches of the chosen variant (self-collision: sweep + copy-back
+    per colour, plus the detection; Jacobi: one pass + copy-back; the fused
+    loop: one launch for all iterations)."""
+    if args.scene == "slabs":
+        return 2 + DETECT_LAUNCHES + iters * 2 * C
+    if args.jacobi:
+        return 2 + iters * 2
+    per_colour = {3: 2}.get(info.pipeline, 1)
+    if info.pipeline == 4:
+        return 3
+    return 2 + iters * C * per_colour
+
+
 def run_small_configs(args) -> dict:
     """The two workloads that fit in L2 (cantilever beam, differentiable
     beam): latency- and launch-bound, so only time per step is reported,
@@ -628,8 +643,7 @@ def run_ours(args):
                      "avg_launch_us": avg_launch_s * 1e6,
                      "sweep_share_of_step": sweep_ms / t_ms},
         "e2e": e2e,
-        "gpu_launches": K * (2 + iters * (2 if args.jacobi else C)) if args.scene == "cube" else
-                        K * (2 + DETECT_LAUNCHES + iters * 2 * C),
+        "gpu_launches": K * launches_per_step(args, info, iters, C),
         "clocks": clk,
     }
     if not args.no_extras and world == 1 and args.scene == "cube":

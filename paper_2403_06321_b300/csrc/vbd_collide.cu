@@ -6,13 +6,14 @@
 // the detection distance r that shares no tet with it; triangles within
 // 1e-5 r of the nearest distance count as tied and the lowest index wins.
 //
-// Broad phase: spatial hashes of triangle and tet centroids with one cell
-// size c = 1.05 max(R_tri + r, R_tet), R the largest centroid-to-corner
-// distance of any triangle (tet) at this step.  A triangle within r of a
-// vertex, or a tet holding it, has its centroid within R + r (R) of the
-// vertex (the element lies in the ball of radius R about its centroid),
-// hence in one of the 27 cells around the vertex's cell; candidates whose
-// ball is out of reach are skipped before the exact tests.  Each element is
+// Broad phase: spatial hashes of triangle and tet centroids, with cells of
+// c_tri = 1.05 (R_tri + r) and c_tet = 1.05 R_tet, R the largest
+// centroid-to-corner distance of any triangle (tet) at this step.  A triangle
+// within r of a vertex, or a tet holding it, has its centroid within R + r
+// (R) of the vertex (the element lies in the ball of radius R about its
+// centroid), hence in one of the 27 cells around the vertex's cell of that
+// table; candidates whose ball is out of reach are skipped before the exact
+// tests.  Each element is
 // stored once (count, prefix sum, fill), so the tables never overflow.
 //
 // The sweep needs, for each free vertex, the pairs in which it is a triangle
@@ -60,9 +61,20 @@ __device__ __forceinline__ float3 position(const Dev &d, int i) {
     return make_float3(X.x + u.x, X.y + u.y, X.z + u.z);
 }
 
-__device__ __forceinline__ float cell_width(const Dev &d, float r) {
-    const float c = fmaxf(__uint_as_float(d.cell_size[0]) + r, __uint_as_float(d.cell_size[1]));
-    return kMargin * c + 1e-30f;
+// cell of the triangle table: a triangle within r of a vertex has its
+// centroid within R_tri + r of it
+__device__ __forceinline__ float tri_cell_width(const Dev &d, float r) {
+    return kMargin * (__uint_as_float(d.cell_size[0]) + r) + 1e-30f;
+}
+
+// cell of the tet table: a tet holding a point has its centroid within R_tet
+__device__ __forceinline__ float tet_cell_width(const Dev &d) {
+    return kMargin * __uint_as_float(d.cell_size[1]) + 1e-30f;
+}
+
+template <int K>
+__device__ __forceinline__ float table_cell_width(const Dev &d, float r) {
+    return K == 3 ? tri_cell_width(d, r) : tet_cell_width(d);
 }
 
 __device__ __forceinline__ int3 cell_of(const Dev &d, float3 p, float inv_c) {
@@ -119,17 +131,19 @@ __device__ __forceinline__ int sphere_bucket(const Dev &d, float4 s, float inv_c
     return bucket_of(q.x, q.y, q.z, nb);
 }
 
+template <int K>
 __global__ void k_count(Dev d, const float4 *sphere, int n, int nb, float r, int *count) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
-    atomicAdd(count + sphere_bucket(d, sphere[t], 1.0f / cell_width(d, r), nb), 1);
+    atomicAdd(count + sphere_bucket(d, sphere[t], 1.0f / table_cell_width<K>(d, r), nb), 1);
 }
 
+template <int K>
 __global__ void k_fill(Dev d, const float4 *sphere, int n, int nb, float r, const int *start, int *fill,
                        int *entries) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
-    const int b = sphere_bucket(d, sphere[t], 1.0f / cell_width(d, r), nb);
+    const int b = sphere_bucket(d, sphere[t], 1.0f / table_cell_width<K>(d, r), nb);
     entries[start[b] + atomicAdd(fill + b, 1)] = t;
 }
 
@@ -235,7 +249,7 @@ __global__ void __launch_bounds__(128) k_query(Dev d, int n_surf, int nb_tri, in
     const int k = (int)(g / Q), lane = (int)(g % Q);
     const bool active = k < n_surf;  // inactive lanes still join the shuffles
     const int a = active ? d.surf[k] : 0;
-    const float c = cell_width(d, r);
+    const float c = tri_cell_width(d, r);
     const float slack = kSlack * c;
     const float3 Xa = f3(__ldg(d.rest + a)), ua = f3(__ldg(d.u + a));
     const float3 xa = Xa + ua;
@@ -246,12 +260,15 @@ __global__ void __launch_bounds__(128) k_query(Dev d, int n_surf, int nb_tri, in
     bool inside = false;
     if (best >= 0.f) {  // uniform over the group
         // penetration: inside a tet that does not hold the vertex
+        const float ct = tet_cell_width(d);
+        const float tslack = kSlack * ct;
+        const int3 tcell = cell_of(d, xa, 1.0f / ct);
         for (int n = lane; n < 27 && !inside; n += Q) {
-            const int b = neighbour_bucket(cell, n, nb_tet);
+            const int b = neighbour_bucket(tcell, n, nb_tet);
             const int e1 = d.tet_start[b + 1];
             for (int e = d.tet_start[b]; e < e1 && !inside; ++e) {
                 const int j = d.cell_tet[e];
-                if (sphere_far(d.tet_sphere[j], xa, slack)) continue;
+                if (sphere_far(d.tet_sphere[j], xa, tslack)) continue;
                 const int4 v = d.tet_v[j];
                 if (v.x == a || v.y == a || v.z == a || v.w == a) continue;
                 inside = origin_in_tet(rel(d, v.x, Xa, ua), rel(d, v.y, Xa, ua), rel(d, v.z, Xa, ua),
@@ -396,18 +413,19 @@ void launch_detect(const Dev &d, const CollideDims &c, int n_free, cudaStream_t 
     k_bounds<3><<<blocks_for(c.n_tris, 256), 256, 0, s>>>(d, d.tri, c.n_tris, d.tri_sphere, d.cell_size);
     k_bounds<4><<<blocks_for(c.n_tets, 256), 256, 0, s>>>(d, d.tet_v, c.n_tets, d.tet_sphere, d.cell_size + 1);
     cudaMemsetAsync(d.cell_fill, 0, sizeof(int) * (size_t)c.n_buckets, s);
-    k_count<<<blocks_for(c.n_tris, 256), 256, 0, s>>>(d, d.tri_sphere, c.n_tris, c.n_buckets, c.radius, d.cell_fill);
+    k_count<3><<<blocks_for(c.n_tris, 256), 256, 0, s>>>(d, d.tri_sphere, c.n_tris, c.n_buckets, c.radius,
+                                                         d.cell_fill);
     exclusive_scan(d.cell_fill, d.cell_start, c.n_buckets, d.scan_tmp, s);
     cudaMemsetAsync(d.cell_fill, 0, sizeof(int) * (size_t)c.n_buckets, s);
-    k_fill<<<blocks_for(c.n_tris, 256), 256, 0, s>>>(d, d.tri_sphere, c.n_tris, c.n_buckets, c.radius, d.cell_start,
-                                                     d.cell_fill, d.cell_tri);
+    k_fill<3><<<blocks_for(c.n_tris, 256), 256, 0, s>>>(d, d.tri_sphere, c.n_tris, c.n_buckets, c.radius,
+                                                        d.cell_start, d.cell_fill, d.cell_tri);
     cudaMemsetAsync(d.tet_fill, 0, sizeof(int) * (size_t)c.n_tet_buckets, s);
-    k_count<<<blocks_for(c.n_tets, 256), 256, 0, s>>>(d, d.tet_sphere, c.n_tets, c.n_tet_buckets, c.radius,
-                                                      d.tet_fill);
+    k_count<4><<<blocks_for(c.n_tets, 256), 256, 0, s>>>(d, d.tet_sphere, c.n_tets, c.n_tet_buckets, c.radius,
+                                                         d.tet_fill);
     exclusive_scan(d.tet_fill, d.tet_start, c.n_tet_buckets, d.scan_tmp, s);
     cudaMemsetAsync(d.tet_fill, 0, sizeof(int) * (size_t)c.n_tet_buckets, s);
-    k_fill<<<blocks_for(c.n_tets, 256), 256, 0, s>>>(d, d.tet_sphere, c.n_tets, c.n_tet_buckets, c.radius,
-                                                     d.tet_start, d.tet_fill, d.cell_tet);
+    k_fill<4><<<blocks_for(c.n_tets, 256), 256, 0, s>>>(d, d.tet_sphere, c.n_tets, c.n_tet_buckets, c.radius,
+                                                        d.tet_start, d.tet_fill, d.cell_tet);
     // narrow phase
     k_query<<<blocks_for((long long)c.n_surf * kQueryLanes, 128), 128, 0, s>>>(d, c.n_surf, c.n_buckets,
                                                                               c.n_tet_buckets, c.radius);

@@ -569,6 +569,38 @@ void build_surface(vbd_ctx *c) {
     c->surf.clear();
     for (int k = 0; k < c->N; ++k)
         if (on[c->orig_of_new[k]]) c->surf.push_back(k);
+    // Detection visits the boundary vertices in this order: along a Morton
+    // curve of the rest positions, neighbouring lanes probe the same cells.
+    {
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int k : c->surf)
+            for (int a = 0; a < 3; ++a) {
+                const double x = c->rest[3 * (size_t)c->orig_of_new[k] + a];
+                lo[a] = std::min(lo[a], x);
+                hi[a] = std::max(hi[a], x);
+            }
+        auto spread = [](uint64_t v) {  // 21 bits -> every third bit of 63
+            v &= 0x1fffff;
+            v = (v | v << 32) & 0x1f00000000ffffULL;
+            v = (v | v << 16) & 0x1f0000ff0000ffULL;
+            v = (v | v << 8) & 0x100f00f00f00f00fULL;
+            v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+            v = (v | v << 2) & 0x1249249249249249ULL;
+            return v;
+        };
+        std::vector<std::pair<uint64_t, int>> key(c->surf.size());
+        for (size_t q = 0; q < c->surf.size(); ++q) {
+            uint64_t code = 0;
+            for (int a = 0; a < 3; ++a) {
+                const double x = c->rest[3 * (size_t)c->orig_of_new[c->surf[q]] + a];
+                const double t = hi[a] > lo[a] ? (x - lo[a]) / (hi[a] - lo[a]) : 0.0;
+                code |= spread((uint64_t)std::min(2097151.0, std::max(0.0, t * 2097151.0))) << a;
+            }
+            key[q] = {code, c->surf[q]};
+        }
+        std::sort(key.begin(), key.end());
+        for (size_t q = 0; q < key.size(); ++q) c->surf[q] = key[q].second;
+    }
     c->ring_off.assign(c->surf.size() + 1, 0);
     c->ring.clear();
     std::vector<int> nb;

@@ -261,3 +261,21 @@ def test_large_slabs_detection_sampled(orc):
     # the overlap shrinks: the upper slab's penetrating vertices rise on average
     sunk = paired[paired >= u0]
     assert sunk.size > 1000 and xg[sunk, 2].mean() > x[sunk, 2].mean()
+
+
+def test_positions_beyond_the_grid_range_are_reported(orc):
+    """The detection grid is exact while positions stay within 65536 cells of
+    the origin; a scene moved 1e5 m away is detected safely (coordinates are
+    clamped) and vbd_sync_status reports VBD_ERR_RANGE."""
+    m, cfg, _ = synth.colliding_slabs(n=6)
+    m.rest = m.rest + np.array([1e5, 0.0, 0.0])
+    sim = _sim(m, params_of(cfg), None)
+    try:
+        sim.set_state(m.rest, np.zeros_like(m.rest))
+        sim.step(cfg.h, 2)
+        with pytest.raises(vbd.VbdError) as e:
+            sim.sync_status()
+        assert e.value.status == "VBD_ERR_RANGE"
+        sim.sync_status()  # the counter was cleared by the report
+    finally:
+        sim.close()
