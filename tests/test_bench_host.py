@@ -27,6 +27,9 @@ def _rank(rank, world, port, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     t, u = bench.reduce_job(1.0 + rank, 10.0 * (rank + 1), world)
     bench.barrier(world)
+    # one rank saw a throttled clock: both ranks re-measure
+    again = bench.any_rank(rank == 1, world)
+    assert again and not bench.any_rank(False, world)
     q.put((rank, t, u))
     dist.destroy_process_group()
 
@@ -56,3 +59,19 @@ def test_reference_arm_json_line():
         assert k in line, k
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_clock_records_that_invalidate_a_measurement():
+    import importlib.util
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(root, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    ok = {"sm_mhz": 2020.0, "sm_max_mhz": 2032.0, "reasons": ["sw_power_cap"]}
+    assert not b.clocks_rejected(ok)
+    assert b.clocks_rejected(dict(ok, reasons=["hw_slowdown"]))
+    assert b.clocks_rejected(dict(ok, reasons=["sw_thermal_slowdown", "sw_power_cap"]))
+    assert b.clocks_rejected({"sm_mhz": 1100.0, "sm_max_mhz": 2032.0, "reasons": []})  # locked low
+    assert not b.clocks_rejected({"sm_mhz": 1100.0, "sm_max_mhz": 2032.0, "reasons": ["sw_power_cap"]})
+    assert not b.clocks_rejected({"sm_mhz": None, "sm_max_mhz": None, "reasons": []})
