@@ -319,6 +319,14 @@ vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, floa
  * during stream capture. */
 vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_threads, int32_t variant);
 
+/* Test hook for the time-out report of the TMA-staged sweep (variant 1):
+ * while enabled, each CTA's first stage waits for 16 bytes more than its
+ * bulk copies deliver, so that wait runs out after about 2 s of SM clock;
+ * the CTA records the time-out, drains its own copies (again bounded) and
+ * leaves, and the next vbd_sync_status returns VBD_ERR_TIMEOUT.  Nothing
+ * faults and the context stays usable.  Other variants ignore it. */
+vbd_status vbd_debug_stall_pipeline(vbd_ctx *ctx, int32_t enable);
+
 /* Enables (1) or disables (0) CUDA-graph replay of vbd_iterate. */
 vbd_status vbd_set_graph(vbd_ctx *ctx, int32_t enable);
 

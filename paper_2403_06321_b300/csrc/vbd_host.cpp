@@ -87,6 +87,7 @@ struct vbd_ctx {
     int variant = 2;            // sweep kernel: 0 plain, 1 TMA-staged, 2 persistent, 3 two-phase scatter,
                                 // 4 fused iteration loop in one cluster
     int fused_cluster = 0;      // CTAs of that cluster
+    bool stall_test = false;    // vbd_debug_stall_pipeline
     int pipe_block = 128;
     int pipe_maxs = 0;          // slot capacity of one stage
     int pipe_ctas_per_sm = 0;
@@ -342,6 +343,7 @@ SweepParams sweep_params(const vbd_ctx *c, int color) {
     p.per_tet_mat = c->per_tet_mat ? 1 : 0;
     p.self_collision = c->params.self_collision && c->sc_carved ? 1 : 0;
     p.to_unew = (c->params.jacobi || c->params.xnew_copy_back) ? 1 : 0;
+    p.stall_test = c->stall_test ? 1 : 0;
     if (c->params.jacobi && color >= 0) {  // one pass over every free vertex
         p.vbegin = 0;
         p.vend = c->n_free;
@@ -1312,6 +1314,14 @@ vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_
         vbd_status ps = prepare_pipeline(ctx);
         if (ps != VBD_OK) return ps;
     }
+    ctx->version++;
+    clear_graphs(ctx);
+    return VBD_OK;
+}
+
+vbd_status vbd_debug_stall_pipeline(vbd_ctx *ctx, int32_t enable) {
+    if (!ctx) return VBD_ERR_INVALID_ARG;
+    ctx->stall_test = enable != 0;
     ctx->version++;
     clear_graphs(ctx);
     return VBD_OK;

@@ -491,7 +491,8 @@ __host__ __device__ inline size_t pipe_smem_bytes(int maxs) {
 
 // issued by one thread: chunk q of the colour range into stage st
 __device__ __forceinline__ void pipe_issue(const Dev &d, const SweepParams &p, int q, int cv, int maxs,
-                                           char *stages, StageMeta *meta, unsigned long long *bar, int st) {
+                                           char *stages, StageMeta *meta, unsigned long long *bar, int st,
+                                           bool stall = false) {
     const int v0 = p.vbegin + q * cv;
     const int v1 = min(p.vend, v0 + cv);
     const int a = d.slot_off[v0], b = d.slot_off[v1];
@@ -507,7 +508,7 @@ __device__ __forceinline__ void pipe_issue(const Dev &d, const SweepParams &p, i
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(ab) : "memory");
         return;
     }
-    const unsigned tx = 48u * (unsigned)n;
+    const unsigned tx = 48u * (unsigned)n + (stall ? 16u : 0u);  // stall: 16 bytes never come
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(ab), "r"(tx) : "memory");
     StageView v = stage_view(stages + st * pipe_stage_bytes(maxs), maxs);
     bulk_g2s(v.s0, d.s0 + a, 16u * n, bar + st);
@@ -535,7 +536,8 @@ __global__ void __launch_bounds__(TT) k_sweep_pipe(Dev d, SweepParams p, int max
     if (threadIdx.x == 0)
         for (int st = 0; st < kPipeStages; ++st)
             if (first + st * stride < nchunks)
-                pipe_issue(d, p, first + st * stride, CV, maxs, stages, meta, bar, st);
+                pipe_issue(d, p, first + st * stride, CV, maxs, stages, meta, bar, st,
+                           p.stall_test != 0 && st == 0);
     const int lane = threadIdx.x & (L - 1);
     for (int k = 0;; ++k) {
         const int q = first + k * stride;

@@ -29,7 +29,8 @@ ENTRY_POINTS = [
     "vbd_set_log_young", "vbd_step", "vbd_begin_step", "vbd_iterate", "vbd_sweep_color",
     "vbd_accelerate", "vbd_end_step", "vbd_energy", "vbd_energy_static", "vbd_get_contacts", "vbd_sync_status",
     "vbd_backward",
-    "vbd_set_launch", "vbd_set_graph", "vbd_autotune", "vbd_last_error", "vbd_destroy",
+    "vbd_set_launch", "vbd_debug_stall_pipeline", "vbd_set_graph", "vbd_autotune", "vbd_last_error",
+    "vbd_destroy",
 ]
 
 
@@ -105,6 +106,7 @@ def load() -> C.CDLL:
         "vbd_sync_status": (C.c_int, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "vbd_backward": (C.c_int, [P, P, P, P, I32]),
         "vbd_set_launch": (C.c_int, [P, I32, I32, I32]),
+        "vbd_debug_stall_pipeline": (C.c_int, [P, I32]),
         "vbd_set_graph": (C.c_int, [P, I32]),
         "vbd_autotune": (C.c_int, [P, F, I32, C.POINTER(F)]),
         "vbd_last_error": (C.c_char_p, [P]),
@@ -263,6 +265,10 @@ def vbd_backward(ctx: int, dL_dxT, dL_dlogE, dL_dv0, adj_iters: int) -> None:
 def vbd_set_launch(ctx: int, lanes_per_vertex: int = 0, block_threads: int = 0, variant: int = -1) -> None:
     """variant: 0 plain, 1 TMA-staged, 2 persistent, 3 two-phase scatter, 4 fused loop (< 0 keeps it)."""
     _check("vbd_set_launch", ctx, load().vbd_set_launch(ctx, lanes_per_vertex, block_threads, variant))
+
+
+def vbd_debug_stall_pipeline(ctx: int, enable: bool) -> None:
+    _check("vbd_debug_stall_pipeline", ctx, load().vbd_debug_stall_pipeline(ctx, 1 if enable else 0))
 
 
 def vbd_set_graph(ctx: int, enable: bool) -> None:

@@ -225,3 +225,34 @@ def test_block_jacobi(orc):
     xk, _ = gpu_run(m, params_of(synth.SimConfig(), jacobi=True), synth.kuhn_coloring(m.grid_ijk), 1 / 60, 30, 10)
     xg, _ = gpu_run(m, params_of(synth.SimConfig(), jacobi=True), colors, 1 / 60, 30, 10)
     assert np.array_equal(xk, xg)
+
+
+def test_pipeline_wait_time_out_is_reported_and_recoverable():
+    """A bounded wait of the TMA-staged sweep that runs out (the test hook
+    makes each CTA's first stage expect 16 bytes that never arrive) is
+    reported as VBD_ERR_TIMEOUT; the context then runs normally and gives the
+    same result as a context that never timed out."""
+    m, cfg = synth.cantilever_beam()
+    colors = synth.kuhn_coloring(m.grid_ijk)
+    pd = params_of(cfg)
+    ref, _ = gpu_run(m, pd, colors, cfg.h, 5, 3, variant=1)
+    sim = vbd.Sim(m, vbd.make_params(**pd), colors=colors)
+    try:
+        vbd.vbd_set_launch(sim.ctx, 0, 0, 1)
+        sim.set_state(m.rest, np.zeros_like(m.rest))
+        vbd.vbd_debug_stall_pipeline(sim.ctx, True)
+        vbd.vbd_begin_step(sim.ctx, cfg.h)
+        vbd.vbd_sweep_color(sim.ctx, 0)
+        vbd.vbd_end_step(sim.ctx)
+        with pytest.raises(vbd.VbdError) as e:
+            sim.sync_status()
+        assert e.value.status == "VBD_ERR_TIMEOUT"
+        vbd.vbd_debug_stall_pipeline(sim.ctx, False)
+        sim.set_state(m.rest, np.zeros_like(m.rest))
+        for _ in range(3):
+            sim.step(cfg.h, 5)
+        sim.sync_status()
+        x, _ = sim.get_state()
+        assert np.array_equal(x.cpu().numpy().astype(np.float64), ref)
+    finally:
+        sim.close()
