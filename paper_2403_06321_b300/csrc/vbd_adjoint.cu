@@ -129,17 +129,33 @@ __global__ void __launch_bounds__(128, 8) k_adj_sweep(Dev d, const float4 *__res
         const DForm F = make_dform(e, g);
         const float3 ci = F.cof(gi);
         const float kJ = Vlam * F.jm1 - Vmu;  // V lam (J - alpha)
-        float sc = 0.f;                         // sum_k c_k . lam_k
-        float3 q = make_float3(0.f, 0.f, 0.f);
+        // sum_k H_ik lam_k = V [mu dF g_i + lam (cof F : dF) c_i + lam (J - alpha) dcof(F)[dF] g_i]
+        // with the direction dF = sum_k lam_k g_k^T (columns dF0..dF2); the last
+        // term equals sum_k (F (g_k x g_i)) x lam_k, the skew part of the blocks.
+        float3 dF0 = make_float3(0.f, 0.f, 0.f), dF1 = dF0, dF2 = dF0;
         for (int k = 0; k < 3; ++k) {
-            const float gg = Vmu * dot(gi, g[k]);
-            q.x += gg * lk[k].x; q.y += gg * lk[k].y; q.z += gg * lk[k].z;
-            sc += dot(F.cof(g[k]), lk[k]);
-            const float3 w0 = cross(g[k], gi);      // F (g_k x g_i) = w0 + D w0
-            const float3 Dw = F.dmul(w0);
-            const float3 w = cross(make_float3(w0.x + Dw.x, w0.y + Dw.y, w0.z + Dw.z), lk[k]);
-            q.x += kJ * w.x; q.y += kJ * w.y; q.z += kJ * w.z;
+            dF0.x += lk[k].x * g[k].x; dF0.y += lk[k].y * g[k].x; dF0.z += lk[k].z * g[k].x;
+            dF1.x += lk[k].x * g[k].y; dF1.y += lk[k].y * g[k].y; dF1.z += lk[k].z * g[k].y;
+            dF2.x += lk[k].x * g[k].z; dF2.y += lk[k].y * g[k].z; dF2.z += lk[k].z * g[k].z;
         }
+        const float3 dFg = mulF(dF0, dF1, dF2, gi);
+        // cof F : dF, with cof(F) e_c = (1 + tr D) e_c - D^T e_c + cof(D) e_c
+        const float trdF = dF0.x + dF1.y + dF2.z;
+        const float trdFD = dF0.x * F.D0.x + dF0.y * F.D1.x + dF0.z * F.D2.x +
+                            dF1.x * F.D0.y + dF1.y * F.D1.y + dF1.z * F.D2.y +
+                            dF2.x * F.D0.z + dF2.y * F.D1.z + dF2.z * F.D2.z;
+        const float sc = (1.f + F.tr) * trdF - trdFD + dot(dF0, F.q0) + dot(dF1, F.q1) + dot(dF2, F.q2);
+        // dcof(F)[dF] g_i: cof F has columns f1 x f2, f2 x f0, f0 x f1 (f_c = e_c + D_c)
+        const float3 f0 = make_float3(1.f + F.D0.x, F.D0.y, F.D0.z);
+        const float3 f1 = make_float3(F.D1.x, 1.f + F.D1.y, F.D1.z);
+        const float3 f2 = make_float3(F.D2.x, F.D2.y, 1.f + F.D2.z);
+        const float3 c0 = cross(dF1, f2), c0b = cross(f1, dF2);
+        const float3 c1 = cross(dF2, f0), c1b = cross(f2, dF0);
+        const float3 c2 = cross(dF0, f1), c2b = cross(f0, dF1);
+        const float3 w = make_float3(gi.x * (c0.x + c0b.x) + gi.y * (c1.x + c1b.x) + gi.z * (c2.x + c2b.x),
+                                     gi.x * (c0.y + c0b.y) + gi.y * (c1.y + c1b.y) + gi.z * (c2.y + c2b.y),
+                                     gi.x * (c0.z + c0b.z) + gi.y * (c1.z + c1b.z) + gi.z * (c2.z + c2b.z));
+        float3 q = make_float3(Vmu * dFg.x + kJ * w.x, Vmu * dFg.y + kJ * w.y, Vmu * dFg.z + kJ * w.z);
         q.x += Vlam * ci.x * sc; q.y += Vlam * ci.y * sc; q.z += Vlam * ci.z * sc;
         a.q0 += q.x; a.q1 += q.y; a.q2 += q.z;
         const float dd = Vmu * dot(gi, gi);
