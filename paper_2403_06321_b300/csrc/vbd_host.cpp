@@ -16,6 +16,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "vbd.h"
 #include "vbd_kernels.h"
 
@@ -23,6 +25,15 @@ using vbd::Dev;
 using vbd::SweepParams;
 
 namespace {
+
+// NVTX range over an entry point (a no-op unless a profiler is attached), so
+// that profiles can be cut by ABI call, e.g. ncu --nvtx --nvtx-include "vbd_iterate/"
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 constexpr int kMaxColors = 4096;
 // adjoint sweep launch shape (measured best on B300; independent of the forward's)
@@ -731,6 +742,7 @@ vbd_status vbd_create_mesh(const vbd_mesh_desc *desc, const vbd_params *params, 
 }
 
 vbd_status vbd_color(vbd_ctx *ctx, const int32_t *colors, int32_t *n_colors_out) {
+    Range range_("vbd_color");
     if (!ctx) return VBD_ERR_INVALID_ARG;
     const int N = ctx->N, T = ctx->T;
     std::vector<int> col(N);
@@ -834,6 +846,7 @@ vbd_status vbd_workspace_size(const vbd_ctx *ctx, size_t *bytes) {
 }
 
 vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *stream) {
+    Range range_("vbd_bind");
     if (!ctx || !device_workspace) return VBD_ERR_INVALID_ARG;
     if (!ctx->colored) return fail(ctx, VBD_ERR_NOT_COLORED, "vbd_color must run before vbd_bind");
     const size_t need = carve(ctx, nullptr, nullptr);
@@ -1003,6 +1016,7 @@ static vbd_status check_bound(vbd_ctx *ctx) {
 }
 
 vbd_status vbd_set_state(vbd_ctx *ctx, const float *x, const float *v, const float *v_prev) {
+    Range range_("vbd_set_state");
     vbd_status st = check_bound(ctx);
     if (st != VBD_OK) return st;
     if (!x || !v) return fail(ctx, VBD_ERR_INVALID_ARG, "x and v are required");
@@ -1027,6 +1041,7 @@ vbd_status vbd_set_state(vbd_ctx *ctx, const float *x, const float *v, const flo
 }
 
 vbd_status vbd_get_state(vbd_ctx *ctx, float *x, float *v) {
+    Range range_("vbd_get_state");
     vbd_status st = check_bound(ctx);
     if (st != VBD_OK) return st;
     const size_t bytes = 12 * (size_t)ctx->N;
@@ -1071,6 +1086,7 @@ vbd_status vbd_set_log_young(vbd_ctx *ctx, const float *log_young) {
 }
 
 vbd_status vbd_begin_step(vbd_ctx *ctx, float h) {
+    Range range_("vbd_begin_step");
     vbd_status st = check_bound(ctx);
     if (st != VBD_OK) return st;
     if (!(h > 0.f) || !std::isfinite(h)) return fail(ctx, VBD_ERR_INVALID_ARG, "h must be > 0");
@@ -1115,6 +1131,7 @@ vbd_status vbd_accelerate(vbd_ctx *ctx, int32_t n) {
 }
 
 vbd_status vbd_iterate(vbd_ctx *ctx, int32_t iters) {
+    Range range_("vbd_iterate");
     vbd_status st = check_bound(ctx);
     if (st != VBD_OK) return st;
     if (!ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_iterate outside a step");
@@ -1154,6 +1171,7 @@ vbd_status vbd_iterate(vbd_ctx *ctx, int32_t iters) {
 }
 
 vbd_status vbd_end_step(vbd_ctx *ctx) {
+    Range range_("vbd_end_step");
     vbd_status st = check_bound(ctx);
     if (st != VBD_OK) return st;
     if (!ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_end_step outside a step");
@@ -1170,6 +1188,7 @@ vbd_status vbd_end_step(vbd_ctx *ctx) {
 }
 
 vbd_status vbd_step(vbd_ctx *ctx, float h, int32_t iters) {
+    Range range_("vbd_step");
     vbd_status st = vbd_begin_step(ctx, h);
     if (st != VBD_OK) return st;
     st = vbd_iterate(ctx, iters);
@@ -1181,6 +1200,7 @@ vbd_status vbd_step(vbd_ctx *ctx, float h, int32_t iters) {
 }
 
 vbd_status vbd_energy(vbd_ctx *ctx, double *G_out) {
+    Range range_("vbd_energy");
     vbd_status st = check_bound(ctx);
     if (st != VBD_OK) return st;
     if (!G_out) return fail(ctx, VBD_ERR_INVALID_ARG, "G_out is NULL");
@@ -1242,6 +1262,7 @@ vbd_status vbd_sync_status(vbd_ctx *ctx, int64_t *det_skips, int64_t *contacts) 
 }
 
 vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, float *dL_dv0, int32_t adj_iters) {
+    Range range_("vbd_backward");
     vbd_status st = check_bound(ctx);
     if (st != VBD_OK) return st;
     if (!dL_dxT) return fail(ctx, VBD_ERR_INVALID_ARG, "dL_dxT is NULL");
@@ -1334,6 +1355,7 @@ vbd_status vbd_set_graph(vbd_ctx *ctx, int32_t enable) {
 }
 
 vbd_status vbd_autotune(vbd_ctx *ctx, float h, int32_t iters, float *best_ms_per_iter) {
+    Range range_("vbd_autotune");
     vbd_status st = check_bound(ctx);
     if (st != VBD_OK) return st;
     if (ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_autotune inside a step");
