@@ -58,7 +58,8 @@ typedef struct vbd_ctx vbd_ctx;
 /* One mesh, or the union of n_meshes independent meshes (batched mode):
  * mesh b owns vertices [vert_offset[b], vert_offset[b+1]) and tets
  * [tet_offset[b], tet_offset[b+1]); tets index the global vertex range.
- * Meshes never interact, so the union is swept in one launch per colour. */
+ * Meshes share no tet, so the union is swept in one launch per colour; they
+ * interact only through self-collision pairs, when that is on. */
 typedef struct {
     int32_t n_meshes;             /* >= 1 */
     const int32_t *vert_offset;   /* host, n_meshes+1, or NULL when n_meshes == 1 */
