@@ -118,9 +118,11 @@ def lib():
             "orc_model_tris": (None, [vp, _ip]),
             "orc_closest_point_tri": (None, [_dp, _dp, _dp, _dp, _dp, _dp]),
             "orc_point_in_tet": (C.c_int, [_dp, _ip, _dp]),
+            "orc_dcd_vertex": (C.c_int, [vp, C.POINTER(Params), _dp, C.c_int]),
             "orc_dcd": (None, [vp, C.POINTER(Params), _dp]),
             "orc_model_contacts": (None, [vp, _ip]),
-            "orc_self_contact": (C.c_int, [vp, C.POINTER(Params), C.c_int, _dp, _dp, _dp]),
+            "orc_self_contact": (C.c_int, [vp, C.POINTER(Params), C.c_double, C.c_int, _dp, C.c_void_p, _dp,
+                                            _dp]),
             "orc_step": (C.c_int, [vp, C.POINTER(Params), _ip, C.c_int, C.c_double, C.c_int, _dp, _dp, _dp,
                                    C.POINTER(Stats)]),
             "orc_energy_G": (C.c_double, [vp, C.POINTER(Params), C.c_double, _dp, _dp]),
@@ -334,10 +336,17 @@ class Model:
         lib().orc_dcd(self._h, C.byref(p), _d(x).reshape(-1))
         return self.contacts()
 
-    def self_contact(self, p: Params, i, x):
-        """(force, Hessian, hit) of the self-contact terms acting on vertex i."""
+    def dcd_vertex(self, p: Params, x, a) -> int:
+        """The DCD pair of vertex a alone at positions x (triangle index or -1)."""
+        return int(lib().orc_dcd_vertex(self._h, C.byref(p), _d(x).reshape(-1), int(a)))
+
+    def self_contact(self, p: Params, i, x, h=1.0 / 60.0, xt=None):
+        """(force, Hessian, hit) of the self-contact terms acting on vertex i;
+        with xt (positions at the step start) and mu_c > 0, friction too."""
         f, H = np.zeros(3), np.zeros(9)
-        hit = lib().orc_self_contact(self._h, C.byref(p), int(i), _d(x).reshape(-1), f, H)
+        xt_arr = None if xt is None else _d(xt).reshape(-1)
+        hit = lib().orc_self_contact(self._h, C.byref(p), float(h), int(i), _d(x).reshape(-1),
+                                     None if xt_arr is None else xt_arr.ctypes.data, f, H)
         return f, H.reshape(3, 3), bool(hit)
 
     def contacts(self) -> np.ndarray:

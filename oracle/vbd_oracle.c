@@ -549,49 +549,50 @@ int orc_point_in_tet(const double *x, const int *t, const double q[3]) {
     return 1.0 - lam_sum >= 0.0;
 }
 
-/* DCD at positions x (the step start).  A boundary vertex has penetrated
+/* DCD at positions x (the step start), one vertex: returns the triangle
+ * paired with vertex a, or -1.  A boundary vertex has penetrated
  * when it lies in a tet it is not a vertex of; it is then paired with the
  * nearest boundary triangle within dcd_radius, skipping triangles that touch
  * the vertex or a vertex sharing a tet with it.  Triangles whose distance is
  * within 1e-5 dcd_radius of the nearest count as tied (a nearest point on an
  * edge or corner is shared by several triangles; rounding must not choose)
  * and the lowest index wins. */
-void orc_dcd(orc_model *m, const orc_params *p, const double *x) {
-    int n = m->n_verts;
-    int *stamp = (int *)calloc((size_t)n + 1, sizeof(int));
-    for (int a = 0; a < n; ++a) {
-        m->contact[a] = -1;
-        if (!m->on_surface[a]) continue;
-        int inside = 0;
-        for (int j = 0; j < m->n_tets && !inside; ++j) {
-            const int *t = m->tets + 4 * (size_t)j;
-            if (t[0] == a || t[1] == a || t[2] == a || t[3] == a) continue;
-            inside = orc_point_in_tet(x, t, x + 3 * a);
-        }
-        if (!inside) continue;
-        for (int s = m->inc_off[a]; s < m->inc_off[a + 1]; ++s)
-            for (int k = 0; k < 4; ++k) stamp[m->tets[4 * (size_t)m->inc_tet[s] + k]] = a + 1;
-        double best = -1.0;
-        for (int pass = 0; pass < 2; ++pass) {
-            /* pass 0: the nearest distance; pass 1: the lowest index near it */
-            for (int T = 0; T < m->n_tris; ++T) {
-                const int *v = m->tris + 3 * (size_t)T;
-                if (stamp[v[0]] == a + 1 || stamp[v[1]] == a + 1 || stamp[v[2]] == a + 1) continue;
-                double q[3], w[3];
-                orc_closest_point_tri(x + 3 * a, x + 3 * v[0], x + 3 * v[1], x + 3 * v[2], q, w);
-                double dv[3] = {x[3 * a] - q[0], x[3 * a + 1] - q[1], x[3 * a + 2] - q[2]};
-                double dist = sqrt(dot3(dv, dv));
-                if (dist > p->dcd_radius) continue;
-                if (pass == 0 && (best < 0.0 || dist < best)) best = dist;
-                if (pass == 1 && dist <= best + 1e-5 * p->dcd_radius) {
-                    m->contact[a] = T;
-                    break;
-                }
-            }
-            if (best < 0.0) break;
-        }
+int orc_dcd_vertex(const orc_model *m, const orc_params *p, const double *x, int a) {
+    if (!m->on_surface[a]) return -1;
+    int inside = 0;
+    for (int j = 0; j < m->n_tets && !inside; ++j) {
+        const int *t = m->tets + 4 * (size_t)j;
+        if (t[0] == a || t[1] == a || t[2] == a || t[3] == a) continue;
+        inside = orc_point_in_tet(x, t, x + 3 * a);
     }
-    free(stamp);
+    if (!inside) return -1;
+    double best = -1.0;
+    for (int pass = 0; pass < 2; ++pass) {
+        /* pass 0: the nearest distance; pass 1: the lowest index near it */
+        for (int T = 0; T < m->n_tris; ++T) {
+            const int *v = m->tris + 3 * (size_t)T;
+            int adjacent = 0;  /* a triangle vertex shares a tet with a */
+            for (int s = m->inc_off[a]; s < m->inc_off[a + 1] && !adjacent; ++s)
+                for (int k = 0; k < 4; ++k) {
+                    int w = m->tets[4 * (size_t)m->inc_tet[s] + k];
+                    adjacent |= (w == v[0]) | (w == v[1]) | (w == v[2]);
+                }
+            if (adjacent) continue;
+            double q[3], w[3];
+            orc_closest_point_tri(x + 3 * a, x + 3 * v[0], x + 3 * v[1], x + 3 * v[2], q, w);
+            double dv[3] = {x[3 * a] - q[0], x[3 * a + 1] - q[1], x[3 * a + 2] - q[2]};
+            double dist = sqrt(dot3(dv, dv));
+            if (dist > p->dcd_radius) continue;
+            if (pass == 0 && (best < 0.0 || dist < best)) best = dist;
+            if (pass == 1 && dist <= best + 1e-5 * p->dcd_radius) return T;
+        }
+        if (best < 0.0) break;
+    }
+    return -1;
+}
+
+void orc_dcd(orc_model *m, const orc_params *p, const double *x) {
+    for (int a = 0; a < m->n_verts; ++a) m->contact[a] = orc_dcd_vertex(m, p, x, a);
 }
 
 int orc_model_n_verts(const orc_model *m) { return m->n_verts; }
@@ -688,13 +689,43 @@ double orc_local_energy(const orc_model *m, const orc_params *p, double h, int i
     return G;
 }
 
+/* Friction of one self-contact pair (Sec. 3.6, Eqs. 13-16), lagged: the
+ * contact points move by delta = (x_a - x_a^t) - sum_k w_k (x_k - x_k^t)
+ * (x_b = sum_k w_k x_k with this evaluation's weights), u is its part
+ * tangent to n, and the pair's normal force magnitude lambda = k_c d scales
+ * the potential mu_c lambda f0(|u|).  A vertex whose delta derivative is
+ * s I (s = 1 for the colliding vertex, -w_k for corner k) gets the force
+ * -s c u and the Hessian s^2 c (I - n n^T), c = mu_c lambda f1(|u|)/|u|. */
+static void pair_friction(const orc_model *m, const orc_params *p, double h, int a, const int *v,
+                          const double w[3], const double n[3], double lambda_n, const double *x,
+                          const double *xt, double s, double f[3], double H[9]) {
+    double dlt[3];
+    for (int r = 0; r < 3; ++r) {
+        dlt[r] = x[3 * a + r] - xt[3 * a + r];
+        for (int k = 0; k < 3; ++k) dlt[r] -= w[k] * (x[3 * v[k] + r] - xt[3 * v[k] + r]);
+    }
+    double dn = dot3(dlt, n);
+    double ut[3] = {dlt[0] - dn * n[0], dlt[1] - dn * n[1], dlt[2] - dn * n[2]};
+    double um = sqrt(dot3(ut, ut));
+    double eh = p->eps_v * h;
+    double f1_over_u = (um < eh) ? (2.0 / eh - um / (eh * eh)) : 1.0 / um;
+    double c = p->mu_c * lambda_n * f1_over_u;
+    for (int r = 0; r < 3; ++r) {
+        f[r] -= s * c * ut[r];
+        for (int q = 0; q < 3; ++q) H[r * 3 + q] += s * s * c * ((r == q ? 1.0 : 0.0) - n[r] * n[q]);
+    }
+    (void)m;
+}
+
 /* Vertex-triangle penalty (Eq. 12) with the step's DCD pairs acting on
  * vertex i, as the colliding vertex and as a corner of a hit triangle: adds
- * forces to f and Hessians to H; returns 1 if any pair is penetrating. */
-int orc_self_contact(const orc_model *m, const orc_params *p, int i, const double *x,
-                     double f[3], double H[9]) {
+ * forces to f and Hessians to H; with mu_c > 0 and xt given, the pairs'
+ * friction too (h is the step size).  Returns 1 if any pair penetrates. */
+int orc_self_contact(const orc_model *m, const orc_params *p, double h, int i, const double *x,
+                     const double *xt, double f[3], double H[9]) {
     int hit = 0;
     double nn[3], w[3];
+    const int friction = p->mu_c > 0.0 && xt != NULL;
     if (m->contact[i] >= 0) {
         double d = contact_depth(m, i, x, nn, w);
         if (d > 0.0) {
@@ -703,6 +734,9 @@ int orc_self_contact(const orc_model *m, const orc_params *p, int i, const doubl
                 f[r] += p->k_c * d * nn[r];
                 for (int c = 0; c < 3; ++c) H[r * 3 + c] += p->k_c * nn[r] * nn[c];
             }
+            if (friction)
+                pair_friction(m, p, h, i, m->tris + 3 * (size_t)m->contact[i], w, nn, p->k_c * d, x, xt, 1.0,
+                              f, H);
         }
     }
     for (int a = 0; a < m->n_verts; ++a) {
@@ -718,6 +752,7 @@ int orc_self_contact(const orc_model *m, const orc_params *p, int i, const doubl
                 f[r] -= p->k_c * d * wk * nn[r];
                 for (int c = 0; c < 3; ++c) H[r * 3 + c] += p->k_c * wk * wk * nn[r] * nn[c];
             }
+            if (friction) pair_friction(m, p, h, a, v, w, nn, p->k_c * d, x, xt, -wk, f, H);
         }
     }
     return hit;
@@ -785,7 +820,7 @@ int orc_vertex_solve(const orc_model *m, const orc_params *p, double h, int i,
             if (p->mu_c > 0.0) orc_ground_friction(p, h, x + 3 * i, xt + 3 * i, p->k_c * d, f, H);
         }
     }
-    if (p->self_collision && orc_self_contact(m, p, i, x, f, H)) *in_contact = 1;
+    if (p->self_collision && orc_self_contact(m, p, h, i, x, xt, f, H)) *in_contact = 1;
     double det = det3(H);
     double tr3 = (H[0] + H[4] + H[8]) / 3.0;
     if (fabs(det) <= p->det_eps * fabs(tr3 * tr3 * tr3)) {

@@ -87,10 +87,11 @@ void orc_model_tris(const orc_model *m, int *tris);
 void orc_closest_point_tri(const double p[3], const double a[3], const double b[3], const double c[3],
                            double q[3], double w[3]);
 int orc_point_in_tet(const double *x, const int *tet, const double q[3]);
+int orc_dcd_vertex(const orc_model *m, const orc_params *p, const double *x, int a);
 void orc_dcd(orc_model *m, const orc_params *p, const double *x);
 void orc_model_contacts(const orc_model *m, int *contact);
-int orc_self_contact(const orc_model *m, const orc_params *p, int i, const double *x,
-                     double f[3], double H[9]);
+int orc_self_contact(const orc_model *m, const orc_params *p, double h, int i, const double *x,
+                     const double *xt, double f[3], double H[9]);
 
 /* ---- one time step (Algorithm 1) --------------------------------------- */
 void orc_inertia_target(const orc_model *m, const orc_params *p, double h,

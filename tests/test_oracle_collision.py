@@ -206,3 +206,101 @@ def test_dcd_tie_on_a_shared_edge_goes_to_the_lower_index(orc):
             and any(np.allclose(x[k, :2], [0.1, 0.1]) for k in t)]
     assert len(tied) == 2
     assert contact[a] == min(tied)
+
+
+def _f0(u, eh):
+    """Antiderivative of f1 (Eq. 15) with f0(0) = 0."""
+    return np.where(u < eh, u * u / eh - u ** 3 / (3 * eh * eh), u - eh / 3)
+
+
+def test_self_contact_friction_is_gradient_of_lagged_potential(orc):
+    """Friction of the self-contact pairs (Sec. 3.6 applied to vertex-triangle
+    pairs) equals minus the gradient of sum_pairs mu_c lambda f0(|u|), with
+    lambda = k_c d, the normal and the barycentric weights held at their
+    current values (lagged), u the tangential part of
+    (x_a - x_a^t) - sum_k w_k (x_k - x_k^t); the forces sum to zero."""
+    lower = synth.beam(3, 3, 1, edge=0.1, E=1e5, nu=0.4, pin_face="z-", jitter_frac=0.02, seed=105)
+    upper = synth.beam(2, 2, 1, edge=0.1, E=1e5, nu=0.4, pin_face=None, jitter_frac=0.02, seed=106,
+                       origin=(0.03, 0.02, 0.09))
+    cat, voff, _ = synth.concat([lower, upper])
+    model = orc.Model.from_mesh(cat)
+    pf = orc.Params.make(self_collision=True, dcd_radius=0.05, k_c=1e5, mu_c=0.4, eps_v=0.05)
+    p0 = orc.Params.make(self_collision=True, dcd_radius=0.05, k_c=1e5)
+    x = cat.rest
+    contact = model.dcd(pf, x)
+    tris = model.tris()
+    pairs = np.nonzero(contact >= 0)[0]
+    rng = np.random.default_rng(107)
+    xt = x - rng.normal(0.0, 4e-4, x.shape)  # tangential motion both below and above eps_v h
+    eh = pf.eps_v * H
+    geo = {}
+    for a in pairs:
+        t = tris[contact[a]]
+        q, w = orc.closest_point_tri(x[a], *x[t])
+        n = np.cross(x[t[1]] - x[t[0]], x[t[2]] - x[t[0]])
+        n /= np.linalg.norm(n)
+        d = (q - x[a]) @ n
+        if d > 0:
+            geo[a] = (t, w, n, pf.k_c * d)
+    mags = []
+
+    def potential(z):
+        tot = 0.0
+        for a, (t, w, n, lam) in geo.items():
+            dl = (z[a] - xt[a]) - sum(w[k] * (z[t[k]] - xt[t[k]]) for k in range(3))
+            u = dl - (dl @ n) * n
+            tot += pf.mu_c * lam * _f0(np.linalg.norm(u), eh)
+        return tot
+
+    for a, (t, w, n, lam) in geo.items():
+        dl = (x[a] - xt[a]) - sum(w[k] * (x[t[k]] - xt[t[k]]) for k in range(3))
+        mags.append(np.linalg.norm(dl - (dl @ n) * n))
+    assert min(mags) < eh < max(mags)  # both friction regimes are exercised
+    involved = sorted(set(geo) | set(np.concatenate([g[0] for g in geo.values()]).tolist()))
+    total = np.zeros(3)
+    fmax = 0.0
+    for v in involved:
+        ff = model.self_contact(pf, v, x, H, xt)[0] - model.self_contact(p0, v, x)[0]
+        fmax = max(fmax, float(np.abs(ff).max()))
+        e = 1e-9
+        g = np.zeros(3)
+        for r in range(3):
+            zp, zm = x.copy(), x.copy()
+            zp[v, r] += e
+            zm[v, r] -= e
+            g[r] = (potential(zp) - potential(zm)) / (2 * e)
+        assert np.allclose(ff, -g, rtol=1e-5, atol=1e-6 * max(1e-12, np.abs(ff).max()))
+        total += ff
+    assert fmax > 0 and np.abs(total).max() <= 1e-12 * max(1.0, fmax)
+
+
+def test_block_sliding_on_a_rigid_block_decelerates_at_mu_g(orc):
+    """Coulomb regime on a self-contact: a free block sliding at 2 m/s on a
+    fully pinned block carries its weight through vertex-triangle pairs, so
+    its mean velocity falls by mu g per unit time."""
+    mu = 0.3
+    lower = synth.beam(6, 3, 1, edge=0.1, E=1e6, nu=0.3, pin_face="z-")
+    lower.pinned[:] = 1
+    upper = synth.beam(2, 2, 1, edge=0.1, E=1e6, nu=0.3, pin_face=None, origin=(0.03, 0.04, 0.1 - 5e-5))
+    cat, voff, _ = synth.concat([lower, upper])
+    model = orc.Model.from_mesh(cat)
+    colors, nc = orc.color_greedy(cat.n_verts, cat.tets)
+    p = orc.Params.make(gravity=(0, 0, -9.8), k_c=1e6, self_collision=True, dcd_radius=0.05, mu_c=mu, eps_v=1e-3)
+    x = cat.rest.copy()
+    v = np.zeros_like(x)
+    v[voff[1]:, 0] = 2.0
+    vp = v.copy()
+    vs = []
+    for _ in range(13):
+        model.step(p, colors, nc, H, 500, x, v, vp)
+        vs.append(v[voff[1]:, 0].mean())
+    decel = (vs[3] - vs[12]) / (9 * H)
+    assert decel == pytest.approx(mu * 9.8, rel=0.02)
+    p_nf = orc.Params.make(gravity=(0, 0, -9.8), k_c=1e6, self_collision=True, dcd_radius=0.05)
+    x = cat.rest.copy()
+    v = np.zeros_like(x)
+    v[voff[1]:, 0] = 2.0
+    vp = v.copy()
+    for _ in range(4):
+        model.step(p_nf, colors, nc, H, 500, x, v, vp)
+    assert abs(v[voff[1]:, 0].mean() - 2.0) < 0.02  # without friction it keeps sliding

@@ -47,6 +47,9 @@ MUTANTS = [
     ("inside_test_counts_own_tets", "if (t[0] == a || t[1] == a || t[2] == a || t[3] == a) continue;", "",
      "test_oracle_collision.py"),
     ("inside_test_sign", "if (l < 0.0) return 0;", "if (l > 0.0) return 0;", "test_oracle_collision.py"),
+    ("self_friction_corner_unweighted", "x, xt, -wk, f, H);", "x, xt, -1.0, f, H);", "test_oracle_collision.py"),
+    ("self_friction_relative_motion_sign", "dlt[r] -= w[k] * (x[3 * v[k] + r]", "dlt[r] += w[k] * (x[3 * v[k] + r]",
+     "test_oracle_collision.py"),
 ]
 
 
