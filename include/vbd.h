@@ -130,7 +130,11 @@ typedef struct {
  * with depth d = (q - x_a).n > 0 (q the nearest point of the triangle, w its
  * barycentric weights, n the unit normal at the current positions) adds the
  * penalty of Eq. 12 with the same k_c: k_c d n and k_c n n^T to vertex a,
- * -k_c d w_k n and k_c w_k^2 n n^T to corner k.  Every colour pass then
+ * -k_c d w_k n and k_c w_k^2 n n^T to corner k.  With mu_c > 0 the pairs
+ * get friction as well (Eqs. 13-16): the contact points moved by
+ * (x_a - x_a^t) - sum_k w_k (x_k - x_k^t) since the step start, u is its
+ * tangential part, c = mu_c k_c d f1(|u|)/|u|, and vertex a gets -c u with
+ * c (I - n n^T), corner k +w_k c u with w_k^2 c (I - n n^T).  Every colour pass then
  * solves its vertices against the pass-start positions and copies them back
  * (x^new of Algorithm 1), because a contact can couple two vertices of one
  * colour; the pipelined sweep is not used.  Needs dcd_radius > 0; not

@@ -140,7 +140,15 @@ __device__ __forceinline__ float sub_reduce(float v) {
 // pass-start positions its partners read (x^new of Algorithm 1); partners
 // of an involved vertex are involved too, and other vertices of the colour
 // touch only other colours, so they update in place.
-__device__ __forceinline__ bool contact_item(const Dev &d, float kc, int vi, int own, int item, int r0, Acc &c) {
+// With ground friction on (mu_c > 0) the pairs get friction too (Sec. 3.6):
+// the contact points moved by delta = (x_a - x_a^t) - sum_k w_k (x_k - x_k^t)
+// since the step start (displacements: the rest positions cancel), u is its
+// part tangent to n, and with the pair's normal force k_c d a vertex whose
+// delta derivative is s I (1 for the pair's vertex, -w_k for corner k) gets
+// -s c u and s^2 c (I - n n^T), c = mu_c k_c d f1(|u|)/|u| (Eq. 15).
+__device__ __forceinline__ bool contact_item(const Dev &d, const SweepParams &p, int vi, int own, int item, int r0,
+                                             Acc &c) {
+    const float kc = p.kc;
     int a, k = -1;
     int4 t;
     if (item == 0 && own >= 0) {
@@ -154,15 +162,31 @@ __device__ __forceinline__ bool contact_item(const Dev &d, float kc, int vi, int
     float3 n, w;
     const float dep = geom::pair_depth(d, a, t, n, w);
     if (!(dep > 0.0f)) return false;
-    float fs = kc * dep, hs = kc;
-    if (k >= 0) {
-        const float wk = k == 0 ? w.x : (k == 1 ? w.y : w.z);
-        fs = -fs * wk;
-        hs = kc * wk * wk;
-    }
+    // s = 1 for the pair's vertex, -w_k for corner k: the penalty force is
+    // k_c d s n and its Hessian s^2 k_c n n^T (d decreases along n at the vertex)
+    const float sgn = k < 0 ? 1.0f : -(k == 0 ? w.x : (k == 1 ? w.y : w.z));
+    const float fs = sgn * kc * dep, hs = sgn * sgn * kc;
     c.f0 += fs * n.x; c.f1 += fs * n.y; c.f2 += fs * n.z;
     c.h00 += hs * n.x * n.x; c.h01 += hs * n.x * n.y; c.h02 += hs * n.x * n.z;
     c.h11 += hs * n.y * n.y; c.h12 += hs * n.y * n.z; c.h22 += hs * n.z * n.z;
+    if (p.mu_c > 0.0f) {
+        const float3 da = f3(__ldg(d.u + a)) - f3(__ldg(d.ut + a));
+        const float3 d0 = f3(__ldg(d.u + t.x)) - f3(__ldg(d.ut + t.x));
+        const float3 d1 = f3(__ldg(d.u + t.y)) - f3(__ldg(d.ut + t.y));
+        const float3 d2 = f3(__ldg(d.u + t.z)) - f3(__ldg(d.ut + t.z));
+        float3 dl = make_float3(da.x - (w.x * d0.x + w.y * d1.x + w.z * d2.x),
+                                da.y - (w.x * d0.y + w.y * d1.y + w.z * d2.y),
+                                da.z - (w.x * d0.z + w.y * d1.z + w.z * d2.z));
+        const float dn = dot(dl, n);
+        dl = make_float3(dl.x - dn * n.x, dl.y - dn * n.y, dl.z - dn * n.z);
+        const float um = sqrtf(dot(dl, dl));
+        const float f1u = um < p.eps_h ? (2.0f / p.eps_h - um / (p.eps_h * p.eps_h)) : 1.0f / um;
+        const float cf = p.mu_c * kc * dep * f1u;
+        const float ff = -sgn * cf, hf = sgn * sgn * cf;
+        c.f0 += ff * dl.x; c.f1 += ff * dl.y; c.f2 += ff * dl.z;
+        c.h00 += hf * (1.f - n.x * n.x); c.h11 += hf * (1.f - n.y * n.y); c.h22 += hf * (1.f - n.z * n.z);
+        c.h01 -= hf * n.x * n.y; c.h02 -= hf * n.x * n.z; c.h12 -= hf * n.y * n.z;
+    }
     return true;
 }
 
@@ -322,7 +346,7 @@ __device__ __forceinline__ void sweep_body(const Dev &d, const SweepParams &p, l
         }
         int hit = 0;
         for (int it = lane; it < n_items; it += L)
-            hit |= contact_item(d, p.kc, vi, own, it, r0, ca) ? 1 : 0;
+            hit |= contact_item(d, p, vi, own, it, r0, ca) ? 1 : 0;
         if (__any_sync(FULL, n_items > 0)) {
             ca.f0 = sub_reduce<L>(ca.f0);
             ca.f1 = sub_reduce<L>(ca.f1);

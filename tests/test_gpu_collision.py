@@ -138,8 +138,8 @@ def _trajectory(orc, m, pd, h, iters, steps, v0=None):
     return worst / bbox_diag(m.rest), x, counts
 
 
-@pytest.mark.parametrize("extra", [dict(), dict(cheby_rho=0.8), dict(k_d=1e-5)],
-                         ids=["plain", "chebyshev", "damping"])
+@pytest.mark.parametrize("extra", [dict(), dict(cheby_rho=0.8), dict(k_d=1e-5), dict(mu_c=0.3, eps_v=1e-2)],
+                         ids=["plain", "chebyshev", "damping", "friction"])
 def test_slabs_trajectory_matches_oracle(orc, extra):
     """10 steps x 20 iterations of the slab scene (870 vertices, about 220
     pairs per step); pairs compared at every step start; self-contact alone,
@@ -168,6 +168,22 @@ def test_blocks_sliding_on_the_ground_with_self_contact(orc):
     print("blocks on ground: err / bbox = %.3e, pairs %s" % (err, counts))
     assert min(counts) > 0 and x[:voff[1], 2].min() < 0.0  # both kinds of contact act
     assert err <= TOL
+
+
+def test_block_sliding_on_a_rigid_block_with_friction(orc):
+    """The oracle's Coulomb pin on the GPU: a block sliding at 2 m/s on a
+    fully pinned block, friction mu_c = 0.3 on the self-contact pairs; the
+    trajectories agree and the GPU's deceleration is mu g."""
+    lower = synth.beam(6, 3, 1, edge=0.1, E=1e6, nu=0.3, pin_face="z-")
+    lower.pinned[:] = 1
+    upper = synth.beam(2, 2, 1, edge=0.1, E=1e6, nu=0.3, pin_face=None, origin=(0.03, 0.04, 0.1 - 5e-5))
+    cat, voff, _ = synth.concat([lower, upper])
+    pd = params_of(synth.SimConfig(k_c=1e6, self_collision=True, dcd_radius=0.05), mu_c=0.3, eps_v=1e-3)
+    v0 = np.zeros_like(cat.rest)
+    v0[voff[1]:, 0] = 2.0
+    err, x, counts = _trajectory(orc, cat, pd, 1 / 60, 200, 10, v0)
+    print("block on rigid block with friction: err / bbox = %.3e, pairs %s" % (err, counts))
+    assert min(counts) >= 9 and err <= TOL
 
 
 def test_jacobi_with_self_contact_first_iterations(orc):
