@@ -295,3 +295,42 @@ def test_positions_beyond_the_grid_range_are_reported(orc):
         sim.sync_status()  # the counter was cleared by the report
     finally:
         sim.close()
+
+
+def _random_blocks(seed: int):
+    rng = np.random.default_rng(2000 + seed)
+    e = 0.05
+    nl = [int(v) for v in rng.integers(3, 7, 2)] + [int(rng.integers(1, 3))]
+    nu = [int(v) for v in rng.integers(2, 5, 2)] + [int(rng.integers(1, 3))]
+    lower = synth.beam(*nl, edge=e, E=float(np.exp(rng.uniform(np.log(3e4), np.log(3e5)))), nu=0.4,
+                       pin_face="z-", jitter_frac=float(rng.uniform(0.0, 0.06)), seed=int(rng.integers(1 << 30)))
+    upper = synth.beam(*nu, edge=e, E=float(np.exp(rng.uniform(np.log(3e4), np.log(3e5)))), nu=0.4,
+                       pin_face=None, jitter_frac=float(rng.uniform(0.0, 0.06)), seed=int(rng.integers(1 << 30)))
+    ang = float(rng.uniform(-0.4, 0.4))
+    c, s_ = np.cos(ang), np.sin(ang)
+    R = np.array([[c, -s_, 0.0], [s_, c, 0.0], [0.0, 0.0, 1.0]])
+    top = nl[2] * e
+    sink = float(rng.uniform(0.02, 0.3)) * e
+    centre = upper.rest.mean(axis=0)
+    target = np.array([0.5 * nl[0] * e + rng.uniform(-0.1, 0.1) * e, 0.5 * nl[1] * e + rng.uniform(-0.1, 0.1) * e,
+                       top + 0.5 * nu[2] * e - sink])
+    upper.rest = (upper.rest - centre) @ R.T + target
+    cat, voff, _ = synth.concat([lower, upper])
+    pd = params_of(synth.SimConfig(k_c=float(rng.choice([3e4, 1e5, 3e5])), self_collision=True,
+                                   dcd_radius=float(rng.uniform(0.3, 0.6)) * e),
+                   cheby_rho=float(rng.choice([0.0, 0.0, 0.7])), k_d=float(rng.choice([0.0, 1e-6])),
+                   mu_c=float(rng.choice([0.0, 0.2, 0.5])), eps_v=float(rng.choice([1e-3, 1e-2])))
+    v0 = np.zeros_like(cat.rest)
+    v0[voff[1]:] = rng.normal(0.0, 0.2, 3)
+    return cat, pd, v0, int(rng.integers(5, 20)), int(rng.integers(3, 7))
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_block_pairs_match_oracle(orc, seed):
+    """Seeded random pairs of blocks (sizes, materials, jitter, a turned and
+    sunk upper block, radius, k_c, friction, Chebyshev, damping, velocity):
+    pairs equal at every step start, positions within 1e-5 of the bbox."""
+    cat, pd, v0, iters, steps = _random_blocks(seed)
+    err, x, counts = _trajectory(orc, cat, pd, 1 / 60, iters, steps, v0)
+    print("random blocks %d: %d verts, pairs %s, err / bbox %.2e" % (seed, cat.n_verts, counts, err))
+    assert max(counts) > 0 and err <= TOL
