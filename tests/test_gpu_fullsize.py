@@ -80,3 +80,37 @@ def test_energy_never_rises_per_pass(big):
     print("large cube G per pass:", G)
     assert np.all(np.diff(G) <= 1e-9 * np.abs(G[:-1]))
     assert G[-1] < G[0]
+
+
+def test_sweep_variants_agree_at_full_size(big):
+    """One full iteration (all colours) of the benchmark cube with each sweep
+    kernel: the persistent grid equals the plain grid bit for bit at equal
+    lanes, the TMA-staged kernel equals the plain 8-lane sweep bit for bit,
+    the two-phase scatter agrees to FP32 rounding, and the fused cluster
+    loop refuses a mesh this large."""
+    m, cfg, x0, v0 = big
+    colors = synth.kuhn_coloring(m.grid_ijk)
+    pd = params_of(cfg)
+    out = {}
+    sim = vbd.Sim(m, vbd.make_params(scatter_sweep=True, **pd), colors=colors)
+    try:
+        for key, (lanes, block, variant) in {"plain4": (4, 256, 0), "persist4": (4, 256, 2),
+                                             "plain8": (8, 256, 0), "tma8": (8, 256, 1),
+                                             "scatter4": (4, 256, 3)}.items():
+            vbd.vbd_set_launch(sim.ctx, lanes, block if variant != 1 else 256, variant)
+            sim.set_state(x0, v0)
+            vbd.vbd_begin_step(sim.ctx, cfg.h)
+            vbd.vbd_iterate(sim.ctx, 1)
+            vbd.vbd_end_step(sim.ctx)
+            sim.sync_status()
+            out[key] = sim.get_state()[0].cpu().numpy()
+        with pytest.raises(vbd.VbdError) as e:
+            vbd.vbd_set_launch(sim.ctx, 4, 0, 4)
+        assert e.value.status == "VBD_ERR_INVALID_ARG"
+    finally:
+        sim.close()
+    assert np.array_equal(out["persist4"], out["plain4"])
+    assert np.array_equal(out["tma8"], out["plain8"])
+    diag = bbox_diag(m.rest)
+    assert float(np.abs(out["scatter4"] - out["plain4"]).max()) <= 1e-7 * diag
+    assert float(np.abs(out["plain8"] - out["plain4"]).max()) <= 1e-7 * diag
