@@ -50,13 +50,16 @@ class Params(C.Structure):
                 ("ground_normal", C.c_double * 3), ("k_c", C.c_double), ("cheby_rho", C.c_double),
                 ("init_mode", C.c_int), ("det_eps", C.c_double), ("k_d", C.c_double),
                 ("mu_c", C.c_double), ("eps_v", C.c_double), ("line_search", C.c_int), ("jacobi", C.c_int),
-                ("self_collision", C.c_int), ("dcd_radius", C.c_double)]
+                ("self_collision", C.c_int), ("dcd_radius", C.c_double), ("n_walls", C.c_int),
+                ("walls", C.c_double * 24)]
 
     @classmethod
     def make(cls, gravity=(0.0, 0.0, -9.8), ground_on=False, ground_height=0.0,
              ground_normal=(0.0, 0.0, 1.0), k_c=0.0, cheby_rho=0.0, init_mode=3,
              det_eps=1e-12, k_d=0.0, mu_c=0.0, eps_v=1e-3, line_search=False, jacobi=False,
-             self_collision=False, dcd_radius=0.0, **_ignored) -> "Params":
+             self_collision=False, dcd_radius=0.0, walls=(), **_ignored) -> "Params":
+        """walls: up to 6 world-box half-spaces (nx, ny, nz, offset), the allowed
+        side being x.n/|n| >= offset (Sec. 3.4)."""
         p = cls()
         p.gravity[:] = [float(g) for g in gravity]
         p.ground_on = int(bool(ground_on))
@@ -73,6 +76,12 @@ class Params(C.Structure):
         p.jacobi = int(bool(jacobi))
         p.self_collision = int(bool(self_collision))
         p.dcd_radius = float(dcd_radius)
+        walls = [tuple(float(v) for v in w) for w in walls]
+        if len(walls) > 6 or any(len(w) != 4 for w in walls):
+            raise ValueError("walls: at most 6 tuples (nx, ny, nz, offset)")
+        p.n_walls = len(walls)
+        for k, w in enumerate(walls):
+            p.walls[4 * k:4 * k + 4] = list(w)
         return p
 
 
@@ -383,12 +392,20 @@ class Model:
         return g.reshape(self.t, 4, 3)
 
     # -- dense global references (small meshes only)
-    def _ground_terms(self, p: Params, x):
-        n = np.array(p.ground_normal[:], dtype=np.float64)
-        n /= np.linalg.norm(n)
-        d = p.ground_height - x @ n
-        act = (d > 0) & self.free if p.ground_on else np.zeros(self.n, bool)
-        return n, d, act
+    def _plane_terms(self, p: Params, x):
+        """[(unit normal n, depths d, active mask)] of every static half-space
+        (the ground, then the walls; Sec. 3.4, Eq. 12)."""
+        planes = []
+        if p.ground_on:
+            planes.append((np.array(p.ground_normal[:], dtype=np.float64), p.ground_height))
+        for k in range(p.n_walls):
+            planes.append((np.array(p.walls[4 * k:4 * k + 3], dtype=np.float64), p.walls[4 * k + 3]))
+        out = []
+        for n, c in planes:
+            n = n / np.linalg.norm(n)
+            d = c - x @ n
+            out.append((n, d, (d > 0) & self.free))
+        return out
 
     def global_grad_hess(self, p: Params, h, x, y):
         """dG/dx and d2G/dx2 of Eq. 2 (+ ground penalty), dense, all DoFs."""
@@ -396,10 +413,10 @@ class Model:
         M = np.repeat(np.where(self.free, m, 0.0), 3)
         g = M / h ** 2 * (x - y).reshape(-1) + self.elastic_grad(x)
         H = self.elastic_hess(x) + np.diag(M / h ** 2)
-        n, d, act = self._ground_terms(p, x)
-        for i in np.nonzero(act)[0]:
-            g[3 * i:3 * i + 3] -= p.k_c * d[i] * n
-            H[3 * i:3 * i + 3, 3 * i:3 * i + 3] += p.k_c * np.outer(n, n)
+        for n, d, act in self._plane_terms(p, x):
+            for i in np.nonzero(act)[0]:
+                g[3 * i:3 * i + 3] -= p.k_c * d[i] * n
+                H[3 * i:3 * i + 3, 3 * i:3 * i + 3] += p.k_c * np.outer(n, n)
         return g, H
 
     def newton_solve(self, p: Params, h, x0, y, tol=1e-11, max_iter=200) -> np.ndarray:
@@ -460,7 +477,7 @@ def dense_adjoint(model: Model, p: Params, h: float, xs: list, dL_dxT: np.ndarra
         sparse = n > 400
     for t in range(T - 1, -1, -1):
         x1 = np.asarray(xs[t + 1], np.float64).reshape(-1, 3)
-        nrm, d, act = model._ground_terms(p, x1)
+        planes = model._plane_terms(p, x1)
         diag = m / h ** 2
         r = xbar + vbar / h
         lam = np.zeros(3 * n)
@@ -468,20 +485,22 @@ def dense_adjoint(model: Model, p: Params, h: float, xs: list, dL_dxT: np.ndarra
             import scipy.sparse as sp
             import scipy.sparse.linalg as spla
             H = model.elastic_hess(x1, sparse=True) + sp.diags(diag)
-            if act.any():
-                rows, cols, vals = [], [], []
+            rows, cols, vals = [], [], []
+            for nrm, d, act in planes:
                 for i in np.nonzero(act)[0]:
                     for a_ in range(3):
                         for b_ in range(3):
                             rows.append(3 * i + a_); cols.append(3 * i + b_)
                             vals.append(p.k_c * nrm[a_] * nrm[b_])
+            if rows:
                 H = H + sp.csr_matrix((vals, (rows, cols)), shape=H.shape)
             idx = np.nonzero(fd)[0]
             lam[fd] = spla.spsolve(H[idx][:, idx].tocsc(), r[fd])
         else:
             H = model.elastic_hess(x1) + np.diag(diag)
-            for i in np.nonzero(act)[0]:
-                H[3 * i:3 * i + 3, 3 * i:3 * i + 3] += p.k_c * np.outer(nrm, nrm)
+            for nrm, d, act in planes:
+                for i in np.nonzero(act)[0]:
+                    H[3 * i:3 * i + 3, 3 * i:3 * i + 3] += p.k_c * np.outer(nrm, nrm)
             lam[fd] = np.linalg.solve(H[np.ix_(fd, fd)], r[fd])
         tg = model.tet_grads(x1)  # (T, 4, 3)
         lam3 = lam.reshape(-1, 3)

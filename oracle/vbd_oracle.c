@@ -17,6 +17,9 @@
  *  - Singular-Hessian skip (Sec. 3.2): |det H| <= det_eps * |tr H / 3|^3.
  *  - Contact (Eq. 12) with a ground half-space: x_b is the projection of
  *    the vertex on the plane, d = max(0, height - x.n), n held constant.
+ *  - World-box walls (Sec. 3.4 treats unilateral constraints as potentials):
+ *    each wall is one more static half-space with the ground's penalty,
+ *    stiffness k_c and friction (mu_c, eps_v); their terms add up.
  *  - Colouring (Sec. 3.9 gives no algorithm): greedy, vertices visited by
  *    decreasing number of distinct neighbours, ties by lower id, each
  *    taking the smallest colour unused by its neighbours.
@@ -659,7 +662,28 @@ void orc_initial_guess(const orc_model *m, const orc_params *p, double h,
     }
 }
 
-/* G_i of Eq. 4 (inertia + incident tets) plus the ground penalty of Eq. 12. */
+/* The static half-spaces of the unilateral constraints (Sec. 3.4): the ground
+ * (when on) and the world-box walls, as unit normals nh and offsets c; the
+ * allowed side is x.nh >= c.  Returns their number. */
+static int contact_planes(const orc_params *p, double nh[1 + ORC_MAX_WALLS][3],
+                          double c[1 + ORC_MAX_WALLS]) {
+    int k = 0;
+    if (p->ground_on) {
+        double nn = sqrt(dot3(p->ground_normal, p->ground_normal));
+        for (int r = 0; r < 3; ++r) nh[k][r] = p->ground_normal[r] / nn;
+        c[k++] = p->ground_height;
+    }
+    for (int w = 0; w < p->n_walls && w < ORC_MAX_WALLS; ++w) {
+        const double *n = p->walls + 4 * w;
+        double nn = sqrt(dot3(n, n));
+        for (int r = 0; r < 3; ++r) nh[k][r] = n[r] / nn;
+        c[k++] = n[3];
+    }
+    return k;
+}
+
+/* G_i of Eq. 4 (inertia + incident tets) plus the contact penalties of Eq. 12
+ * (ground, walls, self-contact pairs). */
 double orc_local_energy(const orc_model *m, const orc_params *p, double h, int i,
                         const double *x, const double *y) {
     double d2 = 0.0;
@@ -671,10 +695,10 @@ double orc_local_energy(const orc_model *m, const orc_params *p, double h, int i
         gather_tet(m, j, x, xs);
         G += orc_tet_energy(xs, m->B + 9 * (size_t)j, m->V[j], m->mu[j], m->lam[j]);
     }
-    if (p->ground_on) {
-        const double *n = p->ground_normal;
-        double nn = sqrt(dot3(n, n));
-        double d = p->ground_height - dot3(x + 3 * i, n) / nn;
+    double nh[1 + ORC_MAX_WALLS][3], c[1 + ORC_MAX_WALLS];
+    int np = contact_planes(p, nh, c);
+    for (int k = 0; k < np; ++k) {
+        double d = c[k] - dot3(x + 3 * i, nh[k]);
         if (d > 0.0) G += 0.5 * p->k_c * d * d;
     }
     if (p->self_collision)
@@ -758,15 +782,13 @@ int orc_self_contact(const orc_model *m, const orc_params *p, double h, int i, c
     return hit;
 }
 
-/* Ground friction of Eqs. 13-16 for one vertex in contact: adds the force
- * to f and its approximate Hessian to H.  f1 (Eq. 15) blends static and
- * dynamic friction over tangential displacements below eps_v h; f1(u)/u is
- * evaluated in closed form so that u = 0 is regular. */
-void orc_ground_friction(const orc_params *p, double h, const double xi[3], const double xti[3],
-                         double lambda_n, double f[3], double H[9]) {
-    const double *n = p->ground_normal;
-    double nn = sqrt(dot3(n, n));
-    double nh[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
+/* Friction of Eqs. 13-16 against a static half-space with unit normal nh,
+ * for one vertex in contact: adds the force to f and its approximate
+ * Hessian to H.  f1 (Eq. 15) blends static and dynamic friction over
+ * tangential displacements below eps_v h; f1(u)/u is evaluated in closed
+ * form so that u = 0 is regular. */
+static void plane_friction(const orc_params *p, double h, const double nh[3], const double xi[3],
+                           const double xti[3], double lambda_n, double f[3], double H[9]) {
     double dlt[3] = {xi[0] - xti[0], xi[1] - xti[1], xi[2] - xti[2]};
     double dn = dot3(dlt, nh);
     double ut[3] = {dlt[0] - dn * nh[0], dlt[1] - dn * nh[1], dlt[2] - dn * nh[2]};
@@ -778,6 +800,15 @@ void orc_ground_friction(const orc_params *p, double h, const double xi[3], cons
         f[r] -= c * ut[r];
         for (int s = 0; s < 3; ++s) H[r * 3 + s] += c * ((r == s ? 1.0 : 0.0) - nh[r] * nh[s]);
     }
+}
+
+/* Ground friction (Eqs. 13-16) for one vertex in ground contact. */
+void orc_ground_friction(const orc_params *p, double h, const double xi[3], const double xti[3],
+                         double lambda_n, double f[3], double H[9]) {
+    const double *n = p->ground_normal;
+    double nn = sqrt(dot3(n, n));
+    double nh[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
+    plane_friction(p, h, nh, xi, xti, lambda_n, f, H);
 }
 
 /* Local Newton step for vertex i (Eqs. 7-9, damping Eqs. 10-11, contact
@@ -806,18 +837,17 @@ int orc_vertex_solve(const orc_model *m, const orc_params *p, double h, int i,
             for (int s = 0; s < 3; ++s) f[r] -= p->k_d / h * Hel[r * 3 + s] * (x[3 * i + s] - xt[3 * i + s]);
     }
     *in_contact = 0;
-    if (p->ground_on) {
-        const double *n = p->ground_normal;
-        double nn = sqrt(dot3(n, n));
-        double nh[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
-        double d = p->ground_height - dot3(x + 3 * i, nh);
+    double nh[1 + ORC_MAX_WALLS][3], c[1 + ORC_MAX_WALLS];
+    int np = contact_planes(p, nh, c);
+    for (int k = 0; k < np; ++k) {
+        double d = c[k] - dot3(x + 3 * i, nh[k]);
         if (d > 0.0) {
             *in_contact = 1;
             for (int r = 0; r < 3; ++r) {
-                f[r] += p->k_c * d * nh[r];
-                for (int s = 0; s < 3; ++s) H[r * 3 + s] += p->k_c * nh[r] * nh[s];
+                f[r] += p->k_c * d * nh[k][r];
+                for (int s = 0; s < 3; ++s) H[r * 3 + s] += p->k_c * nh[k][r] * nh[k][s];
             }
-            if (p->mu_c > 0.0) orc_ground_friction(p, h, x + 3 * i, xt + 3 * i, p->k_c * d, f, H);
+            if (p->mu_c > 0.0) plane_friction(p, h, nh[k], x + 3 * i, xt + 3 * i, p->k_c * d, f, H);
         }
     }
     if (p->self_collision && orc_self_contact(m, p, h, i, x, xt, f, H)) *in_contact = 1;
@@ -953,19 +983,19 @@ int orc_step(const orc_model *m, const orc_params *p, const int *colors, int n_c
 /* ------------------------------------------------------------------ */
 
 /* Eq. 2 variational energy G(x) = 1/(2h^2) |x - y|_M^2 + E(x) over the free
- * vertices, with the ground penalty of Eq. 12 when enabled. */
+ * vertices, with the ground and wall penalties of Eq. 12 when enabled. */
 double orc_energy_G(const orc_model *m, const orc_params *p, double h,
                     const double *x, const double *y) {
     double G = 0.0;
+    double nh[1 + ORC_MAX_WALLS][3], c[1 + ORC_MAX_WALLS];
+    int np = contact_planes(p, nh, c);
     for (int i = 0; i < m->n_verts; ++i) {
         if (m->pinned[i]) continue;
         double d2 = 0.0;
         for (int r = 0; r < 3; ++r) d2 += (x[3 * i + r] - y[3 * i + r]) * (x[3 * i + r] - y[3 * i + r]);
         G += m->mass[i] / (2.0 * h * h) * d2;
-        if (p->ground_on) {
-            const double *n = p->ground_normal;
-            double nn = sqrt(dot3(n, n));
-            double d = p->ground_height - (x[3 * i] * n[0] + x[3 * i + 1] * n[1] + x[3 * i + 2] * n[2]) / nn;
+        for (int k = 0; k < np; ++k) {
+            double d = c[k] - dot3(x + 3 * i, nh[k]);
             if (d > 0.0) G += 0.5 * p->k_c * d * d;
         }
     }

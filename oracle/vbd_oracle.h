@@ -43,12 +43,17 @@ typedef struct {
     int jacobi;             /* 1: block Jacobi: all vertices from the previous iterate */
     int self_collision;     /* 1: vertex-triangle penalty contacts from a DCD at x^t (Sec. 3.5) */
     double dcd_radius;      /* DCD search radius */
+    int n_walls;            /* world-box walls (Sec. 3.4), 0..ORC_MAX_WALLS */
+    double walls[4 * 6];    /* wall k: normal walls[4k..4k+2] (any length), offset walls[4k+3];
+                               the allowed side is x.n/|n| >= offset */
 } orc_params;
+
+#define ORC_MAX_WALLS 6
 
 typedef struct {
     long long vertex_solves;   /* local solves performed */
     long long det_skips;       /* solves skipped by the |det H| test */
-    long long contacts;        /* solves that saw ground penetration */
+    long long contacts;        /* solves that saw a ground, wall or self-contact penetration */
 } orc_stats;
 
 /* ---- materials and element (Sec. 5: stable neo-Hookean without log term) -- */

@@ -31,7 +31,8 @@ MUTANTS = [
      "test_oracle_solver.py"),
     ("velocity_times_h", "double vn = (x[q] - xt[q]) / h;", "double vn = (x[q] - xt[q]) * h;",
      "test_oracle_solver.py"),
-    ("contact_force_sign", "f[r] += p->k_c * d * nh[r];", "f[r] -= p->k_c * d * nh[r];", "test_oracle_solver.py"),
+    ("contact_force_sign", "f[r] += p->k_c * d * nh[k][r];", "f[r] -= p->k_c * d * nh[k][r];",
+     "test_oracle_solver.py"),
     ("damping_force_sign", "f[r] -= p->k_d / h * Hel[r * 3 + s]", "f[r] += p->k_d / h * Hel[r * 3 + s]",
      "test_oracle_solver.py"),
     ("colouring_tie_break", "return (i > j) - (i < j);\n}\n\n/* Returns", "return (i < j) - (i > j);\n}\n\n/* Returns",
@@ -50,6 +51,16 @@ MUTANTS = [
     ("self_friction_corner_unweighted", "x, xt, -wk, f, H);", "x, xt, -1.0, f, H);", "test_oracle_collision.py"),
     ("self_friction_relative_motion_sign", "dlt[r] -= w[k] * (x[3 * v[k] + r]", "dlt[r] += w[k] * (x[3 * v[k] + r]",
      "test_oracle_collision.py"),
+    ("wall_offset_sign", "c[k++] = n[3];", "c[k++] = -n[3];", "test_oracle_walls.py"),
+    ("wall_normal_not_normalised", "for (int r = 0; r < 3; ++r) nh[k][r] = n[r] / nn;",
+     "for (int r = 0; r < 3; ++r) nh[k][r] = n[r];", "test_oracle_walls.py"),
+    ("walls_skip_the_last", "for (int w = 0; w < p->n_walls && w < ORC_MAX_WALLS; ++w)",
+     "for (int w = 0; w + 1 < p->n_walls && w < ORC_MAX_WALLS; ++w)", "test_oracle_walls.py"),
+    ("wall_friction_first_normal", "plane_friction(p, h, nh[k], x + 3 * i", "plane_friction(p, h, nh[0], x + 3 * i",
+     "test_oracle_walls.py"),
+    ("wall_energy_dropped", "    for (int k = 0; k < np; ++k) {\n        double d = c[k] - dot3(x + 3 * i, nh[k]);\n        if (d > 0.0) G += 0.5",
+     "    for (int k = 0; k < 0; ++k) {\n        double d = c[k] - dot3(x + 3 * i, nh[k]);\n        if (d > 0.0) G += 0.5",
+     "test_oracle_walls.py"),
 ]
 
 
@@ -70,7 +81,8 @@ def _run_pins(src_text, pin_file):
 
 def test_identity_copy_passes():
     src = open(SRC).read()
-    for pin in ("test_oracle_element.py", "test_oracle_solver.py", "test_oracle_collision.py"):
+    for pin in ("test_oracle_element.py", "test_oracle_solver.py", "test_oracle_collision.py",
+                "test_oracle_walls.py"):
         assert _run_pins(src, pin) == 0, pin
 
 
