@@ -673,7 +673,8 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
                      "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_gbs": NOMINAL_HBM_GBS,
-                     "kernel": KERNELS[info.pipeline] + " (one colour pass)", "alg_bytes_per_update": b_upd,
+                     "kernel": ("k_sweep_sc" if args.scene == "slabs" else KERNELS[info.pipeline])
+                     + " (one colour pass)", "alg_bytes_per_update": b_upd,
                      "avg_launch_us": avg_launch_s * 1e6,
                      "sweep_share_of_step": sweep_ms / t_ms},
         "e2e": e2e,

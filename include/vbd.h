@@ -98,7 +98,12 @@ typedef struct {
                                 prints it; without self-collision the default in-place writes give
                                 the same positions bit for bit (no two vertices of one colour share
                                 a tet), so this exists to check that */
+    int32_t n_walls;         /* world-box walls in use, 0..VBD_MAX_WALLS */
+    float walls[6][4];       /* wall k: normal walls[k][0..2] (need not be unit length) and offset
+                                walls[k][3]; the allowed side is {x : x . n/|n| >= offset} */
 } vbd_params;
+
+#define VBD_MAX_WALLS 6
 
 /* Library defaults: gravity (0,0,-9.8), ground off at z = 0 with n = +z,
  * k_c = 1e7, no acceleration, adaptive init, det_eps = 1e-12, no damping,
@@ -107,10 +112,15 @@ typedef struct {
  * x_i - x_i^t is the sliding displacement, the normal-force magnitude
  * k_c d scales it, and the force -mu_c k_c d f1(|u|) u/|u| (f1 of Eq. 15)
  * with Hessian mu_c k_c d f1(|u|)/|u| (I - n n^T) (Eq. 16) joins Eqs. 8-9.
+ * World-box walls (none by default; Sec. 3.4 treats such unilateral
+ * constraints as potentials) are static half-spaces like the ground: a
+ * vertex at depth d = offset - x.n/|n| > 0 gets the same penalty (k_c) and
+ * friction (mu_c, eps_v), and the terms of the ground and of every wall add
+ * up.
  * line_search (off by default, as in the paper's results): after the Newton
  * step dx, alpha = 1, 1/2, ..., 1/128 is tried and the first alpha with
  * G_i(x + alpha dx) <= G_i(x) kept (no move if none), G_i being inertia,
- * elasticity and ground penalty (Eq. 4, Eq. 12).  G_i is exactly quadratic
+ * elasticity and the ground and wall penalties (Eq. 4, Eq. 12).  G_i is exactly quadratic
  * in x_i apart from the penalty's kink, so the test is evaluated in closed
  * form without revisiting the tets.  jacobi (off by default): one pass per
  * iteration over all free vertices, each solved against the previous
@@ -244,8 +254,8 @@ vbd_status vbd_accelerate(vbd_ctx *ctx, int32_t n);
 vbd_status vbd_end_step(vbd_ctx *ctx);
 
 /* FP64 variational energy G(x) of Eq. 2 for the current x and the inertia
- * target y of the current step (free vertices; ground penalty included when
- * on).  Synchronising. */
+ * target y of the current step (free vertices; ground and wall penalties
+ * included when on; self-contact pairs included).  Synchronising. */
 vbd_status vbd_energy(vbd_ctx *ctx, double *G_out);
 
 /* FP64 energy G(x), as vbd_energy, for callers that cannot allocate device

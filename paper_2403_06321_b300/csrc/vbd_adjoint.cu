@@ -6,7 +6,7 @@
 // Positions are displacements u = x - X (tape rows included), and the element
 // is evaluated from F = I + D as in the forward sweep.
 // For a recorded step t with end positions x_{t+1} and H = M/h^2 + d2E/dx2
-// (+ the ground penalty Hessian), going backwards:
+// (+ the ground and wall penalty Hessians), going backwards:
 //   r = xbar_{t+1} + vbar_{t+1} / h,   H lam = r   (colour-ordered block GS),
 //   xbar_t = M/h^2 lam - vbar_{t+1}/h,  vbar_t = M/h lam,
 //   d L / d log E_j -= sum_{i in tet j} lam_i . dE_j/dx_i.
@@ -174,12 +174,15 @@ __global__ void __launch_bounds__(128, 8) k_adj_sweep(Dev d, const float4 *__res
     const float4 r = d.rhs[vi];
     const float b0 = r.x - a.q0, b1 = r.y - a.q1, b2 = r.z - a.q2;
     float h00 = a.h00 + mh2, h11 = a.h11 + mh2, h22 = a.h22 + mh2, h01 = a.h01, h02 = a.h02, h12 = a.h12;
-    if (p.ground_on) {
+    if (p.n_planes > 0) {  // ground and wall penalty Hessians (Eq. 12, Sec. 3.4)
         const float4 X = d.rest[vi];
-        const float pen = p.gh - (p.gn.x * (X.x + ui.x) + p.gn.y * (X.y + ui.y) + p.gn.z * (X.z + ui.z));
-        if (pen > 0.f) {
-            h00 += p.kc * p.gn.x * p.gn.x; h11 += p.kc * p.gn.y * p.gn.y; h22 += p.kc * p.gn.z * p.gn.z;
-            h01 += p.kc * p.gn.x * p.gn.y; h02 += p.kc * p.gn.x * p.gn.z; h12 += p.kc * p.gn.y * p.gn.z;
+        for (int k = 0; k < p.n_planes; ++k) {
+            const float4 pl = p.planes[k];
+            const float pen = pl.w - (pl.x * (X.x + ui.x) + pl.y * (X.y + ui.y) + pl.z * (X.z + ui.z));
+            if (pen > 0.f) {
+                h00 += p.kc * pl.x * pl.x; h11 += p.kc * pl.y * pl.y; h22 += p.kc * pl.z * pl.z;
+                h01 += p.kc * pl.x * pl.y; h02 += p.kc * pl.x * pl.z; h12 += p.kc * pl.y * pl.z;
+            }
         }
     }
     const float a00 = h11 * h22 - h12 * h12, a01 = h02 * h12 - h01 * h22, a02 = h01 * h12 - h02 * h11;

@@ -339,12 +339,13 @@ SweepParams sweep_params(const vbd_ctx *c, int color) {
     SweepParams p{};
     p.vbegin = color >= 0 ? c->color_begin[color] : 0;
     p.vend = color >= 0 ? c->color_begin[color + 1] : 0;
-    const float *n = c->params.ground_normal;
-    const float nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-    p.gn = make_float3(n[0] / nn, n[1] / nn, n[2] / nn);
-    p.gh = c->params.ground_height;
+    auto add_plane = [&p](const float *n, float offset) {
+        const float nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        p.planes[p.n_planes++] = make_float4(n[0] / nn, n[1] / nn, n[2] / nn, offset);
+    };
+    if (c->params.ground_on) add_plane(c->params.ground_normal, c->params.ground_height);
+    for (int k = 0; k < c->params.n_walls; ++k) add_plane(c->params.walls[k], c->params.walls[k][3]);
     p.kc = c->params.k_c;
-    p.ground_on = c->params.ground_on ? 1 : 0;
     p.det_eps = c->params.det_eps;
     p.kd_over_h = c->h > 0.f ? c->params.k_d / c->h : 0.f;
     p.inv_h2 = c->h > 0.f ? 1.f / (c->h * c->h) : 0.f;
@@ -366,6 +367,15 @@ bool params_ok(const vbd_params *p, std::string &why) {
     const float *n = p->ground_normal;
     const float nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
     if (!(nn > 0.f) || !std::isfinite(nn)) { why = "ground_normal must be non-zero"; return false; }
+    if (p->n_walls < 0 || p->n_walls > VBD_MAX_WALLS) { why = "n_walls must be 0..6"; return false; }
+    for (int k = 0; k < p->n_walls; ++k) {
+        const float *w = p->walls[k];
+        const float wn = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+        if (!(wn > 0.f) || !std::isfinite(wn) || !std::isfinite(w[3])) {
+            why = "walls need a non-zero finite normal and a finite offset";
+            return false;
+        }
+    }
     if (!(p->cheby_rho >= 0.f && p->cheby_rho < 1.f)) { why = "cheby_rho must be in [0, 1)"; return false; }
     if (p->init_mode < 0 || p->init_mode > 3) { why = "init_mode must be 0..3"; return false; }
     if (!(p->det_eps >= 0.f)) { why = "det_eps must be >= 0"; return false; }

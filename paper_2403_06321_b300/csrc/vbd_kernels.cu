@@ -191,10 +191,12 @@ __device__ __forceinline__ bool contact_item(const Dev &d, const SweepParams &p,
 }
 
 // Local solve of Sec. 3.2 for one vertex: Eq. 7 with the inertia terms of
-// Eqs. 8-9, damping (Eqs. 10-11), ground penalty (Eq. 12), self-contact,
-// singular skip, analytic inverse.
-// sc: self-contact sums (f, H) and bit 0 = some pair acted, bit 1 = involved
-template <bool SC>
+// Eqs. 8-9, damping (Eqs. 10-11), ground and wall penalties (Eq. 12,
+// Sec. 3.4), self-contact, singular skip, analytic inverse.
+// sc: self-contact sums (f, H) and bit 0 = some pair acted, bit 1 = involved.
+// LS = false compiles the line search out (the register-capped sweeps keep
+// its operands live otherwise); LS = true runs it when p.line_search is set.
+template <bool SC, bool LS = true>
 __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams &p, int vi, float4 xi,
                                                 const Acc &a, const Acc &ca, int sc) {
     // xi holds the displacement u_i; ym the displacement of the inertia target
@@ -217,39 +219,48 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
         f2 -= kdh * (a.h02 * dx + a.h12 * dy + a.h22 * dz);
     }
     float flag = xi.w;
-    float pen = 0.0f;
-    float4 X = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (p.ground_on) {
-        X = d.rest[vi];
-        pen = p.gh - (p.gn.x * (X.x + xi.x) + p.gn.y * (X.y + xi.y) + p.gn.z * (X.z + xi.z));
-        if (pen > 0.0f) {
-            const float kd = p.kc * pen;
-            f0 += kd * p.gn.x; f1 += kd * p.gn.y; f2 += kd * p.gn.z;
-            h00 += p.kc * p.gn.x * p.gn.x; h11 += p.kc * p.gn.y * p.gn.y; h22 += p.kc * p.gn.z * p.gn.z;
-            h01 += p.kc * p.gn.x * p.gn.y; h02 += p.kc * p.gn.x * p.gn.z; h12 += p.kc * p.gn.y * p.gn.z;
-            flag = 1.0f;
-            if (p.mu_c > 0.0f) {
-                // ground friction (Eqs. 13-16): static ground, sliding displacement
-                // u = tangential part of x_i - x_i^t, normal-force magnitude kd
-                const float4 ut = d.ut[vi];
-                float dx = xi.x - ut.x, dy = xi.y - ut.y, dz = xi.z - ut.z;
-                const float dn = dx * p.gn.x + dy * p.gn.y + dz * p.gn.z;
-                dx -= dn * p.gn.x; dy -= dn * p.gn.y; dz -= dn * p.gn.z;
-                const float um = sqrtf(dx * dx + dy * dy + dz * dz);
-                const float f1u = um < p.eps_h ? (2.0f / p.eps_h - um / (p.eps_h * p.eps_h)) : 1.0f / um;
-                const float c = p.mu_c * kd * f1u;
-                f0 -= c * dx; f1 -= c * dy; f2 -= c * dz;
-                h00 += c * (1.f - p.gn.x * p.gn.x); h11 += c * (1.f - p.gn.y * p.gn.y); h22 += c * (1.f - p.gn.z * p.gn.z);
-                h01 -= c * p.gn.x * p.gn.y; h02 -= c * p.gn.x * p.gn.z; h12 -= c * p.gn.y * p.gn.z;
-            }
-        }
-    }
+    // self-contact sums first, so that they are dead before the plane loop
     bool stage = p.to_unew != 0;  // write to d.unew (copied back after the pass)
     if (SC && (sc & 2)) {
         f0 += ca.f0; f1 += ca.f1; f2 += ca.f2;
         h00 += ca.h00; h01 += ca.h01; h02 += ca.h02; h11 += ca.h11; h12 += ca.h12; h22 += ca.h22;
         if (sc & 1) flag = 1.0f;
         stage = true;
+    }
+    // ground and walls (Sec. 3.4): penalty of Eq. 12 per static half-space,
+    // at the position P = X + u
+    float3 P = make_float3(0.f, 0.f, 0.f);
+    if (p.n_planes > 0) {
+        const float4 X = d.rest[vi];
+        P = make_float3(X.x + xi.x, X.y + xi.y, X.z + xi.z);
+    }
+    // unrolled: constant plane indices keep the plane data in the constant bank
+#pragma unroll
+    for (int k = 0; k < kMaxPlanes; ++k) {
+        if (k >= p.n_planes) break;
+        const float4 pl = p.planes[k];
+        const float pen = pl.w - (pl.x * P.x + pl.y * P.y + pl.z * P.z);
+        if (pen > 0.0f) {
+            const float kd = p.kc * pen;
+            f0 += kd * pl.x; f1 += kd * pl.y; f2 += kd * pl.z;
+            h00 += p.kc * pl.x * pl.x; h11 += p.kc * pl.y * pl.y; h22 += p.kc * pl.z * pl.z;
+            h01 += p.kc * pl.x * pl.y; h02 += p.kc * pl.x * pl.z; h12 += p.kc * pl.y * pl.z;
+            flag = 1.0f;
+            if (p.mu_c > 0.0f) {
+                // friction (Eqs. 13-16) on a static plane: sliding displacement
+                // u = tangential part of x_i - x_i^t, normal-force magnitude kd
+                const float4 ut = d.ut[vi];
+                float dx = xi.x - ut.x, dy = xi.y - ut.y, dz = xi.z - ut.z;
+                const float dn = dx * pl.x + dy * pl.y + dz * pl.z;
+                dx -= dn * pl.x; dy -= dn * pl.y; dz -= dn * pl.z;
+                const float um = sqrtf(dx * dx + dy * dy + dz * dz);
+                const float f1u = um < p.eps_h ? (2.0f / p.eps_h - um / (p.eps_h * p.eps_h)) : 1.0f / um;
+                const float c = p.mu_c * kd * f1u;
+                f0 -= c * dx; f1 -= c * dy; f2 -= c * dz;
+                h00 += c * (1.f - pl.x * pl.x); h11 += c * (1.f - pl.y * pl.y); h22 += c * (1.f - pl.z * pl.z);
+                h01 -= c * pl.x * pl.y; h02 -= c * pl.x * pl.z; h12 -= c * pl.y * pl.z;
+            }
+        }
     }
     float4 *out = stage ? d.unew : d.u;
     // adjugate of the symmetric H
@@ -275,23 +286,27 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
         if (stage) out[vi] = xi;
         return;
     }
-    if (p.line_search) {
+    if (LS && p.line_search) {
         // G_i along dx: inertia + elasticity are exactly quadratic in x_i, so
-        // G_i(x + alpha dx) - G_i(x) = -alpha fv.dx + alpha^2/2 dx.Hv.dx + ground
-        // penalty change, with fv, Hv the variational force and Hessian.
+        // G_i(x + alpha dx) - G_i(x) = -alpha fv.dx + alpha^2/2 dx.Hv.dx + the
+        // change of the plane penalties, with fv, Hv the variational force and
+        // Hessian.
         const float q1 = fv0 * dx + fv1 * dy + fv2 * dz;
         const float hx = (a.h00 + mh2) * dx + a.h01 * dy + a.h02 * dz;
         const float hy = a.h01 * dx + (a.h11 + mh2) * dy + a.h12 * dz;
         const float hz = a.h02 * dx + a.h12 * dy + (a.h22 + mh2) * dz;
         const float q2 = dx * hx + dy * hy + dz * hz;
-        const float p0 = fmaxf(pen, 0.0f);
-        const float ndx = p.gn.x * dx + p.gn.y * dy + p.gn.z * dz;
         float alpha = 1.0f;
         bool ok = false;
         for (int k = 0; k < 8; ++k) {
             float dG = alpha * (0.5f * alpha * q2 - q1);
-            if (p.ground_on) {
-                const float pa = fmaxf(pen - alpha * ndx, 0.0f);
+#pragma unroll
+            for (int j = 0; j < kMaxPlanes; ++j) {
+                if (j >= p.n_planes) break;
+                const float4 pl = p.planes[j];
+                const float pen = pl.w - (pl.x * P.x + pl.y * P.y + pl.z * P.z);
+                const float p0 = fmaxf(pen, 0.0f);
+                const float pa = fmaxf(pen - alpha * (pl.x * dx + pl.y * dy + pl.z * dz), 0.0f);
                 dG += 0.5f * p.kc * (pa - p0) * (pa + p0);
             }
             if (dG <= 0.0f) {
@@ -309,11 +324,12 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
 }
 
 // One colour pass for the vertex of global thread gt (L lanes per vertex).
-template <int L, bool SC, bool COH = false>
-__device__ __forceinline__ void sweep_body(const Dev &d, const SweepParams &p, long long gt) {
+template <int L, bool SC, bool COH = false, bool LS = true>
+__device__ __forceinline__ void sweep_body(const Dev &d, const SweepParams &p, long long gt,
+                                           int vbegin, int vend) {
     const int lane = threadIdx.x & (L - 1);
-    const int vi = p.vbegin + (int)(gt / L);
-    const bool active = vi < p.vend;
+    const int vi = vbegin + (int)(gt / L);
+    const bool active = vi < vend;
     float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
     int s0 = 0, s1 = 0;
     if (active) {
@@ -362,32 +378,33 @@ __device__ __forceinline__ void sweep_body(const Dev &d, const SweepParams &p, l
         }
         sc = (n_items > 0 ? 2 : 0) | hit;
     }
-    if (active && lane == 0) solve_and_store<SC>(d, p, vi, xi, acc, ca, sc);
+    if (active && lane == 0) solve_and_store<SC, LS>(d, p, vi, xi, acc, ca, sc);
 }
 
 // Both gather kernels are held to 48 registers (5 CTAs of 256 threads per
-// SM, no spills): 40 resident warps hide the gather latency better than 32
-// at 56 registers (measured 62.1 vs 64.0 us per 1M-vertex pass).
-template <int L>
+// SM, no spills without the line search): 40 resident warps hide the gather
+// latency better than 32 at 56 registers (measured 62.1 vs 64.0 us per
+// 1M-vertex pass).  LS: instance with the line search (Sec. 3.2) compiled in.
+template <int L, bool LS>
 __global__ void __launch_bounds__(256, 5) k_sweep(Dev d, SweepParams p) {
-    sweep_body<L, false>(d, p, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    sweep_body<L, false, false, LS>(d, p, (long long)blockIdx.x * blockDim.x + threadIdx.x, p.vbegin, p.vend);
 }
 
 // persistent form: a grid of (SMs x resident CTAs) walks the colour's
 // vertices in grid-sized strides (the stride is uniform over a warp, so
 // every lane joins the shuffles of each round)
-template <int L>
+template <int L, bool LS>
 __global__ void __launch_bounds__(256, 5) k_sweep_persist(Dev d, SweepParams p, long long threads) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < threads; base += stride)
-        sweep_body<L, false>(d, p, base + threadIdx.x);
+        sweep_body<L, false, false, LS>(d, p, base + threadIdx.x, p.vbegin, p.vend);
 }
 
 // with self-contact forces; capped at 64 registers so that enough warps stay
 // resident to hide the gather latency
 template <int L>
 __global__ void __launch_bounds__(256, 4) k_sweep_sc(Dev d, SweepParams p) {
-    sweep_body<L, true>(d, p, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    sweep_body<L, true, false, false>(d, p, (long long)blockIdx.x * blockDim.x + threadIdx.x, p.vbegin, p.vend);
 }
 
 // ---- two-phase tet-scatter-into-slots sweep ----------------------------------
@@ -656,7 +673,8 @@ __global__ void k_predict(Dev d, int n, int n_free, float h, float3 g, float gno
 
 // Eq. 18 after iteration n: history buffer cheb[n & 1] holds x^(n-2) on entry
 // and x^(n) on exit; the other buffer holds x^(n-1).  Vertices flagged in
-// ground contact (x.w != 0) keep the Gauss-Seidel result.
+// contact (x.w != 0: ground, wall or self-contact) keep the Gauss-Seidel
+// result.
 template <bool COH>
 __device__ __forceinline__ void cheby_vertex(const Dev &d, int i, int n, float omega) {
     float4 *hist = d.cheb[n & 1];
@@ -684,18 +702,16 @@ __global__ void k_cheby(Dev d, int n_free, int n, float omega) {
 // L2 (__ldcg), never through the non-coherent path.  Same arithmetic as the
 // per-colour launches, so the results are identical bit for bit.
 template <int L>
-__global__ void __launch_bounds__(kFusedThreads) k_iterate_fused(Dev d, FusedParams f) {
+__global__ void __launch_bounds__(kFusedThreads, 1) k_iterate_fused(Dev d, FusedParams f) {
     cg::cluster_group cluster = cg::this_cluster();
     const long long rank = cluster.block_rank();
     const long long stride = (long long)cluster.num_blocks() * blockDim.x;
     for (int n = f.first_n + 1; n <= f.first_n + f.iters; ++n) {
         for (int c = 0; c < f.n_colors; ++c) {
-            SweepParams p = f.p;
-            p.vbegin = d.color_begin[c];
-            p.vend = d.color_begin[c + 1];
-            const long long threads = (long long)(p.vend - p.vbegin) * L;
+            const int vbegin = d.color_begin[c], vend = d.color_begin[c + 1];
+            const long long threads = (long long)(vend - vbegin) * L;
             for (long long base = rank * blockDim.x; base < threads; base += stride)
-                sweep_body<L, false, true>(d, p, base + threadIdx.x);
+                sweep_body<L, false, true>(d, f.p, base + threadIdx.x, vbegin, vend);
             cluster.sync();
         }
         if (f.cheby) {
@@ -785,10 +801,10 @@ __global__ void __launch_bounds__(EB) k_energy_verts(Dev d, int n_free, double i
         const float4 x = d.u[i], y = d.ym[i], X = d.rest[i];
         const double dx = (double)x.x - y.x, dy = (double)x.y - y.y, dz = (double)x.z - y.z;
         e += (double)d.mass[i] * inv_2h2 * (dx * dx + dy * dy + dz * dz);
-        if (p.ground_on) {
-            const double pen = (double)p.gh - ((double)p.gn.x * ((double)X.x + x.x) +
-                                               (double)p.gn.y * ((double)X.y + x.y) +
-                                               (double)p.gn.z * ((double)X.z + x.z));
+        for (int k = 0; k < p.n_planes; ++k) {
+            const float4 pl = p.planes[k];
+            const double pen = (double)pl.w - ((double)pl.x * ((double)X.x + x.x) + (double)pl.y * ((double)X.y + x.y) +
+                                               (double)pl.z * ((double)X.z + x.z));
             if (pen > 0.0) e += 0.5 * (double)p.kc * pen * pen;
         }
     }
@@ -872,24 +888,38 @@ void launch_predict(const Dev &d, int n, int n_free, float h, float3 g, int init
     k_predict<<<blocks_for(n, 256), 256, 0, s>>>(d, n, n_free, h, g, gnorm, init_mode, cheby ? 1 : 0);
 }
 
-template <int L>
+template <int L, bool LS>
 static unsigned persist_grid(int block) {
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_persist<L>, block, 0) != cudaSuccess || occ < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_persist<L, LS>, block, 0) != cudaSuccess ||
+        occ < 1)
         occ = 1;
     return (unsigned)(num_sms() * occ);
+}
+
+template <bool LS>
+static void launch_persist_ls(const Dev &d, const SweepParams &p, int lanes, int block, long long threads,
+                              cudaStream_t s) {
+    const unsigned need = blocks_for(threads, block);
+    switch (lanes) {
+    case 4: k_sweep_persist<4, LS><<<std::min(need, persist_grid<4, LS>(block)), block, 0, s>>>(d, p, threads); break;
+    case 8: k_sweep_persist<8, LS><<<std::min(need, persist_grid<8, LS>(block)), block, 0, s>>>(d, p, threads); break;
+    case 16:
+        k_sweep_persist<16, LS><<<std::min(need, persist_grid<16, LS>(block)), block, 0, s>>>(d, p, threads);
+        break;
+    default:
+        k_sweep_persist<32, LS><<<std::min(need, persist_grid<32, LS>(block)), block, 0, s>>>(d, p, threads);
+        break;
+    }
 }
 
 void launch_sweep_persist(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s) {
     const long long threads = (long long)(p.vend - p.vbegin) * lanes;
     if (threads <= 0) return;
-    const unsigned need = blocks_for(threads, block);
-    switch (lanes) {
-    case 4: k_sweep_persist<4><<<std::min(need, persist_grid<4>(block)), block, 0, s>>>(d, p, threads); break;
-    case 8: k_sweep_persist<8><<<std::min(need, persist_grid<8>(block)), block, 0, s>>>(d, p, threads); break;
-    case 16: k_sweep_persist<16><<<std::min(need, persist_grid<16>(block)), block, 0, s>>>(d, p, threads); break;
-    default: k_sweep_persist<32><<<std::min(need, persist_grid<32>(block)), block, 0, s>>>(d, p, threads); break;
-    }
+    if (p.line_search)
+        launch_persist_ls<true>(d, p, lanes, block, threads, s);
+    else
+        launch_persist_ls<false>(d, p, lanes, block, threads, s);
 }
 
 void launch_sweep_scatter(const Dev &d, const SweepParams &p, int sbegin, int send, int lanes, int block,
@@ -919,11 +949,20 @@ void launch_sweep(const Dev &d, const SweepParams &p, int lanes, int block, cuda
         }
         return;
     }
+    if (p.line_search) {
+        switch (lanes) {
+        case 4: k_sweep<4, true><<<grid, block, 0, s>>>(d, p); break;
+        case 8: k_sweep<8, true><<<grid, block, 0, s>>>(d, p); break;
+        case 16: k_sweep<16, true><<<grid, block, 0, s>>>(d, p); break;
+        default: k_sweep<32, true><<<grid, block, 0, s>>>(d, p); break;
+        }
+        return;
+    }
     switch (lanes) {
-    case 4: k_sweep<4><<<grid, block, 0, s>>>(d, p); break;
-    case 8: k_sweep<8><<<grid, block, 0, s>>>(d, p); break;
-    case 16: k_sweep<16><<<grid, block, 0, s>>>(d, p); break;
-    default: k_sweep<32><<<grid, block, 0, s>>>(d, p); break;
+    case 4: k_sweep<4, false><<<grid, block, 0, s>>>(d, p); break;
+    case 8: k_sweep<8, false><<<grid, block, 0, s>>>(d, p); break;
+    case 16: k_sweep<16, false><<<grid, block, 0, s>>>(d, p); break;
+    default: k_sweep<32, false><<<grid, block, 0, s>>>(d, p); break;
     }
 }
 

@@ -69,11 +69,14 @@ struct Dev {
     unsigned *cell_size;  // bits (float) of the largest centroid-to-corner distance: [0] triangles, [1] tets
 };
 
+// static half-spaces of the unilateral constraints (Sec. 3.4): the ground and up to six walls
+constexpr int kMaxPlanes = 7;
+
 struct SweepParams {
     int vbegin, vend;
-    float3 gn;        // unit ground normal
-    float gh, kc;     // ground height, collision stiffness
-    int ground_on;
+    float4 planes[kMaxPlanes];  // xyz unit normal, w offset: the allowed side is x.n >= w
+    int n_planes;     // planes in use (ground first when on, then the walls)
+    float kc;         // collision stiffness (Eq. 12)
     float det_eps;
     float kd_over_h;  // Rayleigh damping k_d / h
     float inv_h2;     // 1/h^2 (adjoint only)
@@ -89,7 +92,7 @@ struct SweepParams {
 
 // the fused iteration loop (one launch of one thread-block cluster per vbd_iterate)
 struct FusedParams {
-    SweepParams p;    // vbegin / vend are set per colour from Dev::color_begin
+    SweepParams p;    // vbegin / vend unused: each colour range comes from Dev::color_begin
     int n_colors, first_n, iters, cheby, n_free;
     double rho;
 };

@@ -63,6 +63,22 @@ class SimConfig:
     jacobi: bool = False
     self_collision: bool = False
     dcd_radius: float = 0.01
+    walls: tuple = ()  # world-box half-spaces (nx, ny, nz, offset): x.n/|n| >= offset
+
+
+def world_box(lo, hi) -> list:
+    """The six inward-facing walls of the axis-aligned box [lo, hi] as
+    (nx, ny, nz, offset) half-spaces, in the order -x, +x, -y, +y, -z, +z
+    faces (Sec. 3.4 world-box constraints)."""
+    walls = []
+    for a in range(3):
+        n = [0.0, 0.0, 0.0]
+        n[a] = 1.0
+        walls.append(tuple(n) + (float(lo[a]),))
+        n = [0.0, 0.0, 0.0]
+        n[a] = -1.0
+        walls.append(tuple(n) + (-float(hi[a]),))
+    return walls
 
 
 def kuhn_grid(nx: int, ny: int, nz: int, edge: float,

@@ -156,3 +156,34 @@ def test_surface_matches_oracle_and_self_collision_params(lib, orc):
         assert vbd.vbd_workspace_size(ctx) > size0
     finally:
         vbd.vbd_destroy(ctx)
+
+
+def test_wall_params_are_validated(lib):
+    """World-box walls: at most six, each with a non-zero finite normal and a
+    finite offset; the Python helper refuses malformed tuples."""
+    m = synth.beam(2, 1, 1, edge=0.1)
+    arr = vbd.MeshArrays(m.rest, m.tets, m.young, m.poisson, m.density, m.pinned)
+    ctx = vbd.vbd_create_mesh(arr.desc(), vbd.make_params(walls=synth.world_box((-1, -1, 0), (1, 1, 2))))
+    try:
+        box = vbd.make_params(walls=synth.world_box((-1, -1, 0), (1, 1, 2)))
+        assert box.n_walls == 6 and list(box.walls[1]) == [-1.0, 0.0, 0.0, -1.0]
+        for k in (0, 3, 5):
+            bad = vbd.make_params(walls=synth.world_box((-1, -1, 0), (1, 1, 2)))
+            bad.walls[k][0] = bad.walls[k][1] = bad.walls[k][2] = 0.0
+            with pytest.raises(vbd.VbdError) as e:
+                vbd.vbd_set_params(ctx, bad)
+            assert e.value.status == "VBD_ERR_INVALID_ARG"
+        bad = vbd.make_params(walls=[(0, 0, 1, float("nan"))])
+        with pytest.raises(vbd.VbdError):
+            vbd.vbd_set_params(ctx, bad)
+        bad = vbd.make_params()
+        bad.n_walls = 7
+        with pytest.raises(vbd.VbdError):
+            vbd.vbd_set_params(ctx, bad)
+        with pytest.raises(ValueError):
+            vbd.make_params(walls=[(0, 0, 1)])
+        with pytest.raises(ValueError):
+            vbd.make_params(walls=[(0, 0, 1, 0)] * 7)
+        vbd.vbd_set_params(ctx, vbd.make_params(walls=[(0, 0, 1, 0)], ground_on=True))
+    finally:
+        vbd.vbd_destroy(ctx)

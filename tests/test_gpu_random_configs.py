@@ -1,8 +1,8 @@
 """Seeded random combinations of the options the sweep composes, each run on
 the GPU (through the C ABI) and by the FP64 oracle with the same colouring:
 mesh shape and jitter, per-tet materials, pins, init mode, ground contact
-with friction, Chebyshev, damping, line search, colouring and sweep
-variant.  Tolerance 1e-5 of the bounding-box diagonal."""
+with friction, world-box walls, Chebyshev, damping, line search, colouring
+and sweep variant.  Tolerance 1e-5 of the bounding-box diagonal."""
 import numpy as np
 import pytest
 import torch
@@ -49,6 +49,13 @@ def _case(seed: int):
     lanes = int(rng.choice([4, 8, 16]))
     h = float(rng.choice([1 / 60, 1 / 120, 1 / 300]))
     iters, steps = int(rng.integers(3, 15)), int(rng.integers(2, 8))
+    if rng.random() < 0.4:  # world-box walls just outside the rest mesh, slightly tilted
+        walls = []
+        for w in synth.world_box(m.rest.min(0), m.rest.max(0))[:int(rng.integers(1, 7))]:
+            n = np.array(w[:3]) + rng.normal(0.0, 0.1, 3)
+            n /= np.linalg.norm(n)
+            walls.append(tuple(n) + (float((m.rest @ n).min() - rng.uniform(0.0, 0.5) * edge),))
+        pd["walls"] = walls
     return m, pd, v0, greedy, variant, lanes, h, iters, steps
 
 
