@@ -33,9 +33,10 @@ UNIT = "vertex-block updates/s"
 # vertex I/O + one re-read of neighbour positions per colour pass)
 B_INC, B_VTX, B_X = 52, 44, 12
 B_SC = 24  # with self-collision: contact[i] and rev_off[i], rev_off[i+1], in the sweep and the copy-back
-VARIANTS = {0: "plain", 1: "tma_staged", 2: "persistent", 3: "two_phase_scatter", 4: "fused_cluster_loop"}
+VARIANTS = {0: "plain", 1: "tma_staged", 2: "persistent", 3: "two_phase_scatter", 4: "fused_cluster_loop",
+            5: "compact_rest_slots"}
 KERNELS = {0: "k_sweep", 1: "k_sweep_pipe", 2: "k_sweep_persist", 3: "k_scatter_slots + k_scatter_reduce",
-           4: "k_iterate_fused"}
+           4: "k_iterate_fused", 5: "k_sweep_rest"}
 NOMINAL_HBM_GBS = 7700.0  # B300 HBM3e nominal bandwidth, for context beside the measured peak
 DETECT_LAUNCHES = 20   # kernels and memsets of one self-collision detection (three prefix sums)
 CPU_SAMPLE_N = 32      # the CPU legs run a 32^3-cube crop of the same recipe

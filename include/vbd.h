@@ -160,7 +160,7 @@ typedef struct {
     int64_t n_slots;         /* (free vertex, incident tet) pairs streamed per iteration */
     int32_t lanes_per_vertex, block_threads;   /* current sweep launch shape */
     int32_t pipeline;        /* sweep variant of vbd_set_launch (0 plain, 1 TMA-staged, 2 persistent,
-                                3 two-phase scatter, 4 fused loop) */
+                                3 two-phase scatter, 4 fused loop, 5 compact slots) */
     int32_t pipe_stage_slots; /* slot capacity of one pipeline stage */
     int32_t pipe_ctas_per_sm; /* resident CTAs per SM of the pipelined sweep */
     int32_t use_graph;       /* vbd_iterate replays a CUDA graph */
@@ -325,10 +325,18 @@ vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, floa
  *     colour pass and the Chebyshev update, the CTAs meeting at the
  *     hardware cluster barrier between passes (block_threads is ignored;
  *     VBD_ERR_INVALID_ARG when the largest colour exceeds two rounds of the
- *     cluster, 2048 vertices with 4 lanes).
+ *     cluster, 2048 vertices with 4 lanes);
+ *  5  compact slots: variant 2's persistent grid reading only the 16-byte
+ *     neighbour-id word of each slot and recomputing the shape gradients
+ *     and volume from the FP32 rest positions (three more gathered
+ *     positions per slot, a third of the streamed bytes; on B300 as fast as
+ *     2 on a 1M-vertex cube and 7 % faster on a 33M-vertex one, where it
+ *     stays below the power cap that throttles 2).
  * All variants give the same positions: 0, 2 and 4 bit for bit with equal
  * lanes, 1 equals 0 with 8 lanes, and 3 agrees to FP32 rounding (each
- * incidence's terms are rounded before they are summed).  Self-collision passes always use the
+ * incidence's terms are rounded before they are summed); 5 differs from 0
+ * by the rounding of the rest positions to FP32 (about 2e-7 of the
+ * bounding-box diagonal after one iteration of a 1M-vertex cube).  Self-collision passes always use the
  * plain form with contacts, and block Jacobi the plain form.  0 keeps a
  * shape value, a negative variant keeps the variant.  Must not be called
  * during stream capture. */

@@ -96,7 +96,7 @@ struct vbd_ctx {
     // launch shape / graphs
     int lanes = 4, block = 256;
     int variant = 2;            // sweep kernel: 0 plain, 1 TMA-staged, 2 persistent, 3 two-phase scatter,
-                                // 4 fused iteration loop in one cluster
+                                // 4 fused iteration loop in one cluster, 5 compact slots
     int fused_cluster = 0;      // CTAs of that cluster
     bool stall_test = false;    // vbd_debug_stall_pipeline
     int pipe_block = 128;
@@ -449,6 +449,8 @@ void launch_colour(vbd_ctx *c, int col, cudaStream_t s) {
         vbd::launch_sweep_pipe(c->d, p, c->pipe_block, c->pipe_maxs, c->pipe_grid_cap, s);
     } else if (c->variant == 2) {
         vbd::launch_sweep_persist(c->d, p, c->lanes, c->block, s);
+    } else if (c->variant == 5) {
+        vbd::launch_sweep_rest(c->d, p, c->lanes, c->block, s);
     } else if (c->variant == 3) {
         vbd::launch_sweep_scatter(c->d, p, c->slot_off[p.vbegin], c->slot_off[p.vend], c->lanes, c->block, s);
     } else {
@@ -1307,7 +1309,7 @@ vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, floa
 
 vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_threads, int32_t variant) {
     if (!ctx) return VBD_ERR_INVALID_ARG;
-    if (variant > 4) return fail(ctx, VBD_ERR_INVALID_ARG, "sweep variant must be 0..4 (or < 0 to keep it)");
+    if (variant > 5) return fail(ctx, VBD_ERR_INVALID_ARG, "sweep variant must be 0..5 (or < 0 to keep it)");
     const int var = variant < 0 ? ctx->variant : variant;
     const bool pipe = var == 1;
     if (var == 3 && !ctx->params.scatter_sweep)
@@ -1373,7 +1375,8 @@ vbd_status vbd_autotune(vbd_ctx *ctx, float h, int32_t iters, float *best_ms_per
     struct Shape { int pipe, lanes, block; };
     const Shape shapes[] = {{0, 4, 64}, {0, 4, 128}, {0, 4, 256}, {0, 8, 64}, {0, 8, 128}, {0, 8, 256},
                             {0, 16, 64}, {0, 16, 256}, {1, 8, 128}, {1, 8, 256}, {2, 4, 128}, {2, 4, 256},
-                            {2, 8, 256}, {3, 4, 128}, {4, 4, 0}, {4, 8, 0}, {4, 16, 0}};
+                            {2, 8, 256}, {3, 4, 128}, {4, 4, 0}, {4, 8, 0}, {4, 16, 0}, {5, 4, 128},
+                            {5, 4, 256}};
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0), "event");
     CU(cudaEventCreate(&e1), "event");

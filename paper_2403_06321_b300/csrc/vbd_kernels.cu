@@ -4,6 +4,8 @@
 //   k_predict            y (Eq. 3) and the initial guess (Sec. 3.7), once per step
 //   k_sweep<L>           one Gauss-Seidel pass over one colour (Sec. 3.1-3.9),
 //                        iters * n_colors launches per step -- the hot path
+//                        (k_sweep_persist: the same on a persistent grid;
+//                        k_sweep_rest: gradients recomputed from rest positions)
 //   k_cheby              Chebyshev update (Eqs. 18-19), once per iteration if enabled
 //   k_finish             v = (x - x^t)/h (Eq. 6), once per step
 //
@@ -74,19 +76,10 @@ __device__ __forceinline__ float4 load_u(const float4 *u, int i) {
     return COH ? __ldcg(u + i) : __ldg(u + i);
 }
 
-template <bool COH = false>
-__device__ __forceinline__ void accumulate_slot(const Dev &d, const SweepParams &p, int s, float2 vm,
-                                                int4 r0, float4 r1, float4 r2, float3 ui, Acc &acc) {
-    const float4 *__restrict__ u = d.u;
-    const float3 da = f3(load_u<COH>(u, r0.x)) - ui;
-    const float3 db = f3(load_u<COH>(u, r0.y)) - ui;
-    const float3 dc = f3(load_u<COH>(u, r0.z)) - ui;
-    const float3 ga = make_float3(__int_as_float(r0.w), r1.x, r1.y);
-    const float3 gb = make_float3(r1.z, r1.w, r2.x);
-    const float3 gc = make_float3(r2.y, r2.z, r2.w);
-    const float2 mat = slot_material(d, p, s, vm, ga, gb, gc);
-    const float Vmu = mat.x;
-    const float Vlam = mat.y;
+// The element part shared by both slot forms: d_k = u_k - u_i, g_k the shape
+// gradients of the three other vertices, Vmu = V mu, Vlam = V lambda.
+__device__ __forceinline__ void tet_contrib(float3 da, float3 db, float3 dc, float3 ga, float3 gb, float3 gc,
+                                            float Vmu, float Vlam, Acc &acc) {
     const float3 gi = make_float3(-(ga.x + gb.x + gc.x), -(ga.y + gb.y + gc.y), -(ga.z + gb.z + gc.z));
     // columns of D: D_s = da * ga[s] + db * gb[s] + dc * gc[s]
     const float3 D0 = make_float3(da.x * ga.x + db.x * gb.x + dc.x * gc.x,
@@ -120,6 +113,51 @@ __device__ __forceinline__ void accumulate_slot(const Dev &d, const SweepParams 
     acc.h01 += Vlam * c.x * c.y;
     acc.h02 += Vlam * c.x * c.z;
     acc.h12 += Vlam * c.y * c.z;
+}
+
+template <bool COH = false>
+__device__ __forceinline__ void accumulate_slot(const Dev &d, const SweepParams &p, int s, float2 vm,
+                                                int4 r0, float4 r1, float4 r2, float3 ui, Acc &acc) {
+    const float4 *__restrict__ u = d.u;
+    const float3 da = f3(load_u<COH>(u, r0.x)) - ui;
+    const float3 db = f3(load_u<COH>(u, r0.y)) - ui;
+    const float3 dc = f3(load_u<COH>(u, r0.z)) - ui;
+    const float3 ga = make_float3(__int_as_float(r0.w), r1.x, r1.y);
+    const float3 gb = make_float3(r1.z, r1.w, r2.x);
+    const float3 gc = make_float3(r2.y, r2.z, r2.w);
+    const float2 mat = slot_material(d, p, s, vm, ga, gb, gc);
+    tet_contrib(da, db, dc, ga, gb, gc, mat.x, mat.y, acc);
+}
+
+// Compact form of a slot (variant 5): only the three neighbour ids of the
+// 48-byte record are read (16 bytes with the unused fourth word); the shape
+// gradients and the volume are recomputed from the rest positions:
+// with rest edges e_k = X_k - X_i, the rows of the inverse rest edge matrix
+// are g_a = (e_b x e_c)/det, g_b = (e_c x e_a)/det, g_c = (e_a x e_b)/det,
+// det = e_a . (e_b x e_c), V = |det| / 6.  It trades 32 streamed bytes per
+// slot for three gathered rest positions and about 40 flops.
+template <bool COH = false>
+__device__ __forceinline__ void accumulate_slot_rest(const Dev &d, const SweepParams &p, int s, float2 vm,
+                                                     int4 r0, float3 ui, float3 Xi, Acc &acc) {
+    const float4 *__restrict__ u = d.u;
+    const float3 da = f3(load_u<COH>(u, r0.x)) - ui;
+    const float3 db = f3(load_u<COH>(u, r0.y)) - ui;
+    const float3 dc = f3(load_u<COH>(u, r0.z)) - ui;
+    const float3 ea = f3(__ldg(d.rest + r0.x)) - Xi;
+    const float3 eb = f3(__ldg(d.rest + r0.y)) - Xi;
+    const float3 ec = f3(__ldg(d.rest + r0.z)) - Xi;
+    float3 ga = cross(eb, ec), gb = cross(ec, ea), gc = cross(ea, eb);
+    const float det = dot(ea, ga);
+    const float inv = __frcp_rn(det);
+    ga = make_float3(ga.x * inv, ga.y * inv, ga.z * inv);
+    gb = make_float3(gb.x * inv, gb.y * inv, gb.z * inv);
+    gc = make_float3(gc.x * inv, gc.y * inv, gc.z * inv);
+    const float V = fabsf(det) * (1.0f / 6.0f);
+    if (p.per_tet_mat) {
+        const int j = __ldcs(d.slot_tet + s);
+        vm = make_float2(__ldg(d.tet_mu + j), __ldg(d.tet_lam + j));
+    }
+    tet_contrib(da, db, dc, ga, gb, gc, V * vm.x, V * vm.y, acc);
 }
 
 template <int L>
@@ -324,7 +362,8 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
 }
 
 // One colour pass for the vertex of global thread gt (L lanes per vertex).
-template <int L, bool SC, bool COH = false, bool LS = true>
+// RS: compact slots, shape gradients recomputed from the rest positions.
+template <int L, bool SC, bool COH = false, bool LS = true, bool RS = false>
 __device__ __forceinline__ void sweep_body(const Dev &d, const SweepParams &p, long long gt,
                                            int vbegin, int vend) {
     const int lane = threadIdx.x & (L - 1);
@@ -340,8 +379,14 @@ __device__ __forceinline__ void sweep_body(const Dev &d, const SweepParams &p, l
     const float3 x3 = f3(xi);
     const float2 vm = (active && !p.per_tet_mat) ? __ldg(d.vmat + vi) : make_float2(0.f, 0.f);
     Acc acc = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int s = s0 + lane; s < s1; s += L)
-        accumulate_slot<COH>(d, p, s, vm, __ldcs(d.s0 + s), __ldcs(d.s1 + s), __ldcs(d.s2 + s), x3, acc);
+    if (RS) {
+        const float3 X3 = active ? f3(__ldg(d.rest + vi)) : make_float3(0.f, 0.f, 0.f);
+        for (int s = s0 + lane; s < s1; s += L)
+            accumulate_slot_rest<COH>(d, p, s, vm, __ldcs(d.s0 + s), x3, X3, acc);
+    } else {
+        for (int s = s0 + lane; s < s1; s += L)
+            accumulate_slot<COH>(d, p, s, vm, __ldcs(d.s0 + s), __ldcs(d.s1 + s), __ldcs(d.s2 + s), x3, acc);
+    }
     acc.f0 = sub_reduce<L>(acc.f0);
     acc.f1 = sub_reduce<L>(acc.f1);
     acc.f2 = sub_reduce<L>(acc.f2);
@@ -398,6 +443,14 @@ __global__ void __launch_bounds__(256, 5) k_sweep_persist(Dev d, SweepParams p, 
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < threads; base += stride)
         sweep_body<L, false, false, LS>(d, p, base + threadIdx.x, p.vbegin, p.vend);
+}
+
+// persistent form over compact slots (gradients from the rest positions)
+template <int L, bool LS>
+__global__ void __launch_bounds__(256, 4) k_sweep_rest(Dev d, SweepParams p, long long threads) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < threads; base += stride)
+        sweep_body<L, false, false, LS, true>(d, p, base + threadIdx.x, p.vbegin, p.vend);
 }
 
 // with self-contact forces; capped at 64 registers so that enough warps stay
@@ -920,6 +973,35 @@ void launch_sweep_persist(const Dev &d, const SweepParams &p, int lanes, int blo
         launch_persist_ls<true>(d, p, lanes, block, threads, s);
     else
         launch_persist_ls<false>(d, p, lanes, block, threads, s);
+}
+
+template <int L, bool LS>
+static unsigned rest_grid(int block) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_rest<L, LS>, block, 0) != cudaSuccess || occ < 1)
+        occ = 1;
+    return (unsigned)(num_sms() * occ);
+}
+
+template <bool LS>
+static void launch_rest_ls(const Dev &d, const SweepParams &p, int lanes, int block, long long threads,
+                           cudaStream_t s) {
+    const unsigned need = blocks_for(threads, block);
+    switch (lanes) {
+    case 4: k_sweep_rest<4, LS><<<std::min(need, rest_grid<4, LS>(block)), block, 0, s>>>(d, p, threads); break;
+    case 8: k_sweep_rest<8, LS><<<std::min(need, rest_grid<8, LS>(block)), block, 0, s>>>(d, p, threads); break;
+    case 16: k_sweep_rest<16, LS><<<std::min(need, rest_grid<16, LS>(block)), block, 0, s>>>(d, p, threads); break;
+    default: k_sweep_rest<32, LS><<<std::min(need, rest_grid<32, LS>(block)), block, 0, s>>>(d, p, threads); break;
+    }
+}
+
+void launch_sweep_rest(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s) {
+    const long long threads = (long long)(p.vend - p.vbegin) * lanes;
+    if (threads <= 0) return;
+    if (p.line_search)
+        launch_rest_ls<true>(d, p, lanes, block, threads, s);
+    else
+        launch_rest_ls<false>(d, p, lanes, block, threads, s);
 }
 
 void launch_sweep_scatter(const Dev &d, const SweepParams &p, int sbegin, int send, int lanes, int block,

@@ -114,6 +114,8 @@ void launch_predict(const Dev &d, int n, int n_free, float h, float3 g, int init
 void launch_sweep(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s);
 // persistent grid-stride form of launch_sweep (grid = SMs x resident CTAs)
 void launch_sweep_persist(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s);
+// persistent sweep over compact slots (shape gradients from the rest positions)
+void launch_sweep_rest(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s);
 // two-phase tet-scatter-into-slots form; slots [sbegin, send) are the colour's
 void launch_sweep_scatter(const Dev &d, const SweepParams &p, int sbegin, int send, int lanes, int block,
                           cudaStream_t s);

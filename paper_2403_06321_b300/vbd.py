@@ -264,7 +264,8 @@ def vbd_backward(ctx: int, dL_dxT, dL_dlogE, dL_dv0, adj_iters: int) -> None:
 
 
 def vbd_set_launch(ctx: int, lanes_per_vertex: int = 0, block_threads: int = 0, variant: int = -1) -> None:
-    """variant: 0 plain, 1 TMA-staged, 2 persistent, 3 two-phase scatter, 4 fused loop (< 0 keeps it)."""
+    """variant: 0 plain, 1 TMA-staged, 2 persistent, 3 two-phase scatter, 4 fused loop,
+    5 compact slots (< 0 keeps it)."""
     _check("vbd_set_launch", ctx, load().vbd_set_launch(ctx, lanes_per_vertex, block_threads, variant))
 
 

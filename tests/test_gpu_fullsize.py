@@ -86,7 +86,8 @@ def test_sweep_variants_agree_at_full_size(big):
     """One full iteration (all colours) of the benchmark cube with each sweep
     kernel: the persistent grid equals the plain grid bit for bit at equal
     lanes, the TMA-staged kernel equals the plain 8-lane sweep bit for bit,
-    the two-phase scatter agrees to FP32 rounding, and the fused cluster
+    the two-phase scatter agrees to FP32 rounding, the compact slots (shape
+    gradients from the rest positions) to 1e-6 of the bbox, and the fused cluster
     loop refuses a mesh this large."""
     m, cfg, x0, v0 = big
     colors = synth.kuhn_coloring(m.grid_ijk)
@@ -96,7 +97,7 @@ def test_sweep_variants_agree_at_full_size(big):
     try:
         for key, (lanes, block, variant) in {"plain4": (4, 256, 0), "persist4": (4, 256, 2),
                                              "plain8": (8, 256, 0), "tma8": (8, 256, 1),
-                                             "scatter4": (4, 256, 3)}.items():
+                                             "scatter4": (4, 256, 3), "rest4": (4, 256, 5)}.items():
             vbd.vbd_set_launch(sim.ctx, lanes, block if variant != 1 else 256, variant)
             sim.set_state(x0, v0)
             vbd.vbd_begin_step(sim.ctx, cfg.h)
@@ -114,3 +115,7 @@ def test_sweep_variants_agree_at_full_size(big):
     diag = bbox_diag(m.rest)
     assert float(np.abs(out["scatter4"] - out["plain4"]).max()) <= 1e-7 * diag
     assert float(np.abs(out["plain8"] - out["plain4"]).max()) <= 1e-7 * diag
+    # gradients from the FP32 rest positions instead of the FP64-derived ones
+    rest_err = float(np.abs(out["rest4"] - out["plain4"]).max()) / diag
+    print("compact rest slots vs stored gradients: %.2e of the bbox" % rest_err)
+    assert rest_err <= 1e-6

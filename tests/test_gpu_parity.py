@@ -52,7 +52,8 @@ def test_one_iteration_from_perturbed_state_ragged(orc):
     shapes = [dict(variant=1, block=128), dict(variant=1, block=256)] + \
              [dict(variant=0, lanes=l) for l in (4, 8, 16, 32)] + \
              [dict(variant=2, lanes=4), dict(variant=2, lanes=8, block=256), dict(variant=3, lanes=4),
-              dict(variant=3, lanes=8), dict(variant=4, lanes=4), dict(variant=4, lanes=8)]
+              dict(variant=3, lanes=8), dict(variant=4, lanes=4), dict(variant=4, lanes=8),
+              dict(variant=5, lanes=4), dict(variant=5, lanes=8, block=128)]
     results = []
     for sh in shapes:
         xg, vg = gpu_run(m, pd, colors, 1 / 60, 1, 1, x0, v0, **sh)
@@ -118,7 +119,7 @@ def test_graph_replay_equals_eager():
     colors = synth.kuhn_coloring(m.grid_ijk)
     pd = params_of(cfg, cheby_rho=0.8)
     out = {}
-    for pipe in (1, 0, 2, 3, 4):
+    for pipe in (1, 0, 2, 3, 4, 5):
         xa, va = gpu_run(m, pd, colors, cfg.h, 7, 5, graph=True, variant=pipe)
         xb, vb = gpu_run(m, pd, colors, cfg.h, 7, 5, graph=False, variant=pipe)
         assert np.array_equal(xa, xb) and np.array_equal(va, vb)
