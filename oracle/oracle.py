@@ -114,6 +114,7 @@ def lib():
             "orc_model_mass": (None, [vp, _dp]),
             "orc_model_tet_data": (None, [vp, _dp, _dp, _dp, _dp]),
             "orc_model_set_log_young": (None, [vp, _dp]),
+            "orc_model_set_subspace": (C.c_int, [vp, C.c_int, C.c_int, _dp]),
             "orc_inertia_target": (None, [vp, C.POINTER(Params), C.c_double, _dp, _dp, _dp]),
             "orc_initial_guess": (None, [vp, C.POINTER(Params), C.c_double, _dp, _dp, _dp, _dp]),
             "orc_ground_friction": (None, [C.POINTER(Params), C.c_double, _dp, _dp, C.c_double, _dp, _dp]),
@@ -268,10 +269,45 @@ class Model:
         if not self._h:
             raise ValueError("oracle model rejected mesh (status %d)" % status.value)
         self.poisson = _d(poisson).copy()
+        self.sub_dim = np.full(self.n, 3, np.int32)
+        self.sub_dir = np.zeros((self.n, 3))
 
     @classmethod
     def from_mesh(cls, m) -> "Model":
-        return cls(m.rest, m.tets, m.young, m.poisson, m.density, m.pinned)
+        model = cls(m.rest, m.tets, m.young, m.poisson, m.density, m.pinned)
+        sub_dim = getattr(m, "sub_dim", None)
+        if sub_dim is not None:
+            for i in np.nonzero(np.asarray(sub_dim) < 3)[0]:
+                model.set_subspace(int(i), int(sub_dim[i]), m.sub_dir[i])
+        return model
+
+    def set_subspace(self, i: int, L: int, direction) -> None:
+        """Sec. 3.4 subspace constraint: L = 1 line (direction), 2 plane (normal), 3 none."""
+        if lib().orc_model_set_subspace(self._h, int(i), int(L), _d(direction, 3)) != 0:
+            raise ValueError("bad subspace constraint for vertex %d" % i)
+        self.sub_dim[i] = int(L)
+        self.sub_dir[i] = np.asarray(direction, np.float64)
+
+    def reduced_basis(self) -> np.ndarray:
+        """(3N, k) orthonormal basis of the admissible displacements: the
+        three axes of every free vertex, the line direction or two in-plane
+        axes of a subspace-constrained one (from an SVD, independently of the
+        basis the local solve uses), nothing for a pinned vertex."""
+        cols = []
+        for i in range(self.n):
+            if self.pinned[i]:
+                continue
+            L = int(self.sub_dim[i])
+            if L == 3:
+                Q = np.eye(3)
+            else:
+                d = self.sub_dir[i] / np.linalg.norm(self.sub_dir[i])
+                Q = d[:, None] if L == 1 else np.linalg.svd(d[None, :])[2][1:].T
+            for c in range(Q.shape[1]):
+                col = np.zeros(3 * self.n)
+                col[3 * i:3 * i + 3] = Q[:, c]
+                cols.append(col)
+        return np.array(cols).T
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -420,27 +456,30 @@ class Model:
         return g, H
 
     def newton_solve(self, p: Params, h, x0, y, tol=1e-11, max_iter=200) -> np.ndarray:
-        """Global minimiser of G (Eqs. 1-2) over free DoFs: dense Newton with
-        backtracking on G, from x0.  Used as the backward-Euler reference."""
+        """Global minimiser of G (Eqs. 1-2) over the admissible displacements
+        from x0 (free DoFs, restricted to their subspaces where constrained,
+        Sec. 3.4): dense Newton in the coordinates of reduced_basis() with
+        backtracking on G.  Used as the backward-Euler reference."""
         x = np.array(x0, dtype=np.float64).reshape(-1, 3)
-        fd = np.repeat(self.free, 3)
+        Bm = self.reduced_basis()
+        if Bm.size == 0:
+            return x
         scale = None
         for _ in range(max_iter):
             g, H = self.global_grad_hess(p, h, x, y)
-            gf = g[fd]
+            gz = Bm.T @ g
             if scale is None:
-                scale = max(np.abs(gf).max(), 1e-300)
-            if np.abs(gf).max() <= tol * scale:
+                scale = max(np.abs(gz).max(), 1e-300)
+            if np.abs(gz).max() <= tol * scale:
                 break
-            Hf = H[np.ix_(fd, fd)]
+            Hz = Bm.T @ H @ Bm
             try:
-                dxf = -np.linalg.solve(Hf, gf)
+                dz = -np.linalg.solve(Hz, gz)
             except np.linalg.LinAlgError:
-                dxf = -gf
-            if dxf @ gf > 0:
-                dxf = -gf
-            dx = np.zeros(3 * self.n)
-            dx[fd] = dxf
+                dz = -gz
+            if dz @ gz > 0:
+                dz = -gz
+            dx = Bm @ dz
             G0 = self.energy_G(p, h, x, y)
             a = 1.0
             while a > 1e-12:

@@ -17,6 +17,12 @@
  *  - Singular-Hessian skip (Sec. 3.2): |det H| <= det_eps * |tr H / 3|^3.
  *  - Contact (Eq. 12) with a ground half-space: x_b is the projection of
  *    the vertex on the plane, d = max(0, height - x.n), n held constant.
+ *  - Subspace constraints (Sec. 3.4, bilateral): a constrained vertex moves
+ *    in x^t + span(Q) with Q an orthonormal 3 x L basis (L = 1 line, 2
+ *    plane); its local step solves Q^T H Q dz = Q^T f (dx = Q dz) with the
+ *    singular test of Sec. 3.2 on the L x L matrix, and its initial guess is
+ *    projected onto x^t + span(Q).  The subspace moves with x^t, so a vertex
+ *    placed on a fixed line or plane stays on it.
  *  - World-box walls (Sec. 3.4 treats unilateral constraints as potentials):
  *    each wall is one more static half-space with the ground's penalty,
  *    stiffness k_c and friction (mu_c, eps_v); their terms add up.
@@ -77,6 +83,8 @@ struct orc_model {
     int *tris;           /* 3 * n_tris */
     unsigned char *on_surface; /* N */
     int *contact;        /* N: triangle hit by the vertex (DCD at x^t), or -1 */
+    int *sub_dim;        /* N: L of the vertex's subspace constraint (Sec. 3.4), 3 = none */
+    double *sub_basis;   /* 9N: orthonormal basis q_1..q_L of that subspace, 3 doubles each */
 };
 
 /* ------------------------------------------------------------------ */
@@ -439,14 +447,84 @@ orc_model *orc_model_new(int n, int t, const double *rest, const int *tets,
         m->contact = (int *)malloc(sizeof(int) * (size_t)n + 1);
         for (int i = 0; i < n; ++i) m->contact[i] = -1;
     }
+    m->sub_dim = (int *)malloc(sizeof(int) * (size_t)n + 1);
+    m->sub_basis = (double *)calloc(9 * (size_t)n + 1, sizeof(double));
+    for (int i = 0; i < n; ++i) m->sub_dim[i] = 3;
     return m;
+}
+
+/* Bilateral subspace constraint of Sec. 3.4 on vertex i: its position is
+ * kept in x^t + span(q_1..q_L), L = 1 (a line with direction dir) or L = 2
+ * (a plane with normal dir); L = 3 lifts the constraint.  The basis is
+ * orthonormal: for L = 2, q_1 is the coordinate axis least aligned with the
+ * normal with its normal part removed, q_2 = n x q_1.  Returns 0, or 1 for
+ * a bad argument (index, L, zero direction). */
+int orc_model_set_subspace(orc_model *m, int i, int L, const double dir[3]) {
+    if (i < 0 || i >= m->n_verts || L < 1 || L > 3) return 1;
+    double *q = m->sub_basis + 9 * (size_t)i;
+    m->sub_dim[i] = 3;
+    if (L == 3) return 0;
+    double nn = sqrt(dot3(dir, dir));
+    if (!(nn > 0.0) || !isfinite(nn)) return 1;
+    double d[3] = {dir[0] / nn, dir[1] / nn, dir[2] / nn};
+    if (L == 1) {
+        for (int r = 0; r < 3; ++r) q[r] = d[r];
+    } else {
+        int a = 0;
+        for (int r = 1; r < 3; ++r)
+            if (fabs(d[r]) < fabs(d[a])) a = r;
+        double e[3] = {0.0, 0.0, 0.0};
+        e[a] = 1.0;
+        double en = dot3(e, d);
+        for (int r = 0; r < 3; ++r) e[r] -= en * d[r];
+        double el = sqrt(dot3(e, e));
+        for (int r = 0; r < 3; ++r) q[r] = e[r] / el;
+        cross3(d, q, q + 3);
+    }
+    m->sub_dim[i] = L;
+    return 0;
+}
+
+/* Restricts the Newton step of a subspace-constrained vertex (Sec. 3.4):
+ * in the coordinates z of x_i = x_i^t + Q z the local force and Hessian are
+ * b = Q^T f and A = Q^T H Q, the L x L system A dz = b is solved, and
+ * dx = Q dz.  Returns 1 when A is singular by the Sec. 3.2 test on L x L
+ * matrices, |det A| <= det_eps |tr A / L|^L (dx = 0). */
+static int subspace_step(const orc_model *m, const orc_params *p, int i, const double f[3], const double H[9],
+                         double dx[3]) {
+    const int L = m->sub_dim[i];
+    const double *q = m->sub_basis + 9 * (size_t)i;
+    double b[2], A[4];
+    for (int a = 0; a < L; ++a) {
+        b[a] = dot3(q + 3 * a, f);
+        for (int c = 0; c < L; ++c) {
+            double Hq[3];
+            for (int r = 0; r < 3; ++r) Hq[r] = H[r * 3 + 0] * q[3 * c] + H[r * 3 + 1] * q[3 * c + 1] + H[r * 3 + 2] * q[3 * c + 2];
+            A[a * L + c] = dot3(q + 3 * a, Hq);
+        }
+    }
+    double dz[2];
+    dx[0] = dx[1] = dx[2] = 0.0;
+    if (L == 1) {
+        if (fabs(A[0]) <= p->det_eps * fabs(A[0])) return 1;
+        dz[0] = b[0] / A[0];
+    } else {
+        double det = A[0] * A[3] - A[1] * A[2];
+        double tr2 = 0.5 * (A[0] + A[3]);
+        if (fabs(det) <= p->det_eps * tr2 * tr2) return 1;
+        dz[0] = (A[3] * b[0] - A[1] * b[1]) / det;
+        dz[1] = (A[0] * b[1] - A[2] * b[0]) / det;
+    }
+    for (int a = 0; a < L; ++a)
+        for (int r = 0; r < 3; ++r) dx[r] += q[3 * a + r] * dz[a];
+    return 0;
 }
 
 void orc_model_free(orc_model *m) {
     if (!m) return;
     free(m->tets); free(m->B); free(m->V); free(m->mu); free(m->lam); free(m->poisson);
     free(m->mass); free(m->pinned); free(m->inc_off); free(m->inc_tet); free(m->inc_loc);
-    free(m->tris); free(m->on_surface); free(m->contact);
+    free(m->tris); free(m->on_surface); free(m->contact); free(m->sub_dim); free(m->sub_basis);
     free(m);
 }
 
@@ -659,6 +737,16 @@ void orc_initial_guess(const orc_model *m, const orc_params *p, double h,
         }
         }
         for (int r = 0; r < 3; ++r) out[r] = xi[r] + h * vi[r] + h * h * atil * g[r];
+        if (m->sub_dim[i] < 3) {
+            /* a subspace-constrained vertex starts on x^t + span(Q) (Sec. 3.4) */
+            const double *q = m->sub_basis + 9 * (size_t)i;
+            double d[3] = {out[0] - xi[0], out[1] - xi[1], out[2] - xi[2]};
+            for (int r = 0; r < 3; ++r) out[r] = xi[r];
+            for (int a = 0; a < m->sub_dim[i]; ++a) {
+                double c = dot3(q + 3 * a, d);
+                for (int r = 0; r < 3; ++r) out[r] += c * q[3 * a + r];
+            }
+        }
     }
 }
 
@@ -851,15 +939,19 @@ int orc_vertex_solve(const orc_model *m, const orc_params *p, double h, int i,
         }
     }
     if (p->self_collision && orc_self_contact(m, p, h, i, x, xt, f, H)) *in_contact = 1;
-    double det = det3(H);
-    double tr3 = (H[0] + H[4] + H[8]) / 3.0;
-    if (fabs(det) <= p->det_eps * fabs(tr3 * tr3 * tr3)) {
-        dx[0] = dx[1] = dx[2] = 0.0;
-        return 1;
+    if (m->sub_dim[i] < 3) {
+        if (subspace_step(m, p, i, f, H, dx)) return 1;
+    } else {
+        double det = det3(H);
+        double tr3 = (H[0] + H[4] + H[8]) / 3.0;
+        if (fabs(det) <= p->det_eps * fabs(tr3 * tr3 * tr3)) {
+            dx[0] = dx[1] = dx[2] = 0.0;
+            return 1;
+        }
+        double A[9];
+        adj3(H, A);
+        for (int r = 0; r < 3; ++r) dx[r] = (A[r * 3 + 0] * f[0] + A[r * 3 + 1] * f[1] + A[r * 3 + 2] * f[2]) / det;
     }
-    double A[9];
-    adj3(H, A);
-    for (int r = 0; r < 3; ++r) dx[r] = (A[r * 3 + 0] * f[0] + A[r * 3 + 1] * f[1] + A[r * 3 + 2] * f[2]) / det;
     if (p->line_search) {
         /* backtracking from x_i + dx towards x_i on G_i (Algorithm 1) */
         double *xw = (double *)x; /* evaluated in place, restored below */

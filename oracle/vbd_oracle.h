@@ -98,6 +98,10 @@ void orc_model_contacts(const orc_model *m, int *contact);
 int orc_self_contact(const orc_model *m, const orc_params *p, double h, int i, const double *x,
                      const double *xt, double f[3], double H[9]);
 
+/* Subspace constraint of Sec. 3.4 on vertex i: L = 1 line (dir = direction),
+ * 2 plane (dir = normal), 3 = none.  Returns 0, or 1 for a bad argument. */
+int orc_model_set_subspace(orc_model *m, int i, int L, const double dir[3]);
+
 /* ---- one time step (Algorithm 1) --------------------------------------- */
 void orc_inertia_target(const orc_model *m, const orc_params *p, double h,
                         const double *xt, const double *vt, double *y);

@@ -31,6 +31,10 @@ class MeshInput:
     density: np.ndarray  # (T,) float32 [kg/m^3]
     pinned: np.ndarray  # (N,) uint8, 1 = position fixed (bilateral constraint)
     grid_ijk: Optional[np.ndarray] = None  # (N, 3) int32 lattice coordinates
+    # subspace constraints (Sec. 3.4): L per vertex (1 line, 2 plane, 3 none) and
+    # the line direction or plane normal; None = no constrained vertex
+    sub_dim: Optional[np.ndarray] = None  # (N,) int32
+    sub_dir: Optional[np.ndarray] = None  # (N, 3) float64
 
     @property
     def n_verts(self) -> int:

@@ -61,6 +61,15 @@ MUTANTS = [
     ("wall_energy_dropped", "    for (int k = 0; k < np; ++k) {\n        double d = c[k] - dot3(x + 3 * i, nh[k]);\n        if (d > 0.0) G += 0.5",
      "    for (int k = 0; k < 0; ++k) {\n        double d = c[k] - dot3(x + 3 * i, nh[k]);\n        if (d > 0.0) G += 0.5",
      "test_oracle_walls.py"),
+    ("subspace_guess_not_projected", "        if (m->sub_dim[i] < 3) {\n            /* a subspace-constrained",
+     "        if (0) {\n            /* a subspace-constrained", "test_oracle_subspace.py"),
+    ("subspace_rhs_first_axis", "b[a] = dot3(q + 3 * a, f);", "b[a] = dot3(q, f);", "test_oracle_subspace.py"),
+    ("subspace_step_first_axis_only", "    for (int a = 0; a < L; ++a)\n        for (int r = 0; r < 3; ++r) dx[r] +=",
+     "    for (int a = 0; a < 1; ++a)\n        for (int r = 0; r < 3; ++r) dx[r] +=", "test_oracle_subspace.py"),
+    ("subspace_2x2_solve_sign", "dz[1] = (A[0] * b[1] - A[2] * b[0]) / det;", "dz[1] = (A[0] * b[1] + A[2] * b[0]) / det;",
+     "test_oracle_subspace.py"),
+    ("plane_basis_not_orthogonalised", "for (int r = 0; r < 3; ++r) e[r] -= en * d[r];", "",
+     "test_oracle_subspace.py"),
 ]
 
 
@@ -82,7 +91,7 @@ def _run_pins(src_text, pin_file):
 def test_identity_copy_passes():
     src = open(SRC).read()
     for pin in ("test_oracle_element.py", "test_oracle_solver.py", "test_oracle_collision.py",
-                "test_oracle_walls.py"):
+                "test_oracle_walls.py", "test_oracle_subspace.py"):
         assert _run_pins(src, pin) == 0, pin
 
 
