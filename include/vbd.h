@@ -210,6 +210,23 @@ vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *st
 /* Replaces the parameters.  Changing tape_steps requires a new vbd_bind. */
 vbd_status vbd_set_params(vbd_ctx *ctx, const vbd_params *params);
 
+/* Bilateral subspace constraints (Sec. 3.4): vertex[k] (caller id, not
+ * pinned, each at most once) moves only within x^t + span(Q_k) during every
+ * step, Q_k an orthonormal basis of a line (dim[k] = 1, dir[3k..3k+2] its
+ * direction) or of a plane (dim[k] = 2, dir its normal); directions need
+ * not be unit length.  The vertex's local step solves the reduced system
+ * Q^T H Q dz = Q^T f (1x1 or 2x2, with the Sec. 3.2 singular test on it)
+ * and moves by Q dz; its initial guess is projected onto x^t + span(Q).  A
+ * vertex placed on a fixed line or plane therefore stays on it.  Host
+ * arrays of n entries; n = 0 removes all constraints.  Must be called
+ * before vbd_bind (the tables live in the workspace), else VBD_ERR_STATE;
+ * VBD_ERR_INVALID_ARG for an index out of range, a pinned or repeated
+ * vertex, a dimension other than 1 or 2, or a zero or non-finite
+ * direction.  vbd_backward refuses contexts with constraints
+ * (VBD_ERR_STATE). */
+vbd_status vbd_set_subspaces(vbd_ctx *ctx, int32_t n, const int32_t *vertex, const int32_t *dim,
+                             const float *dir);
+
 /* Sets x^t, v^t and v^{t-1} (3N floats each, caller order, host or device).
  * v_prev == NULL means v^{t-1} = v^t (zero estimated acceleration, the
  * first-step convention of Sec. 3.7 (d)).  Clears the tape. */

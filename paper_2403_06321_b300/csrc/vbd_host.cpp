@@ -80,6 +80,9 @@ struct vbd_ctx {
     std::vector<int> ring_off, ring; // per boundary vertex: sorted ids of the vertices of its tets
     int n_buckets = 0, n_tet_buckets = 0;
     bool sc_carved = false;          // the bound workspace holds the self-collision arrays
+    // subspace constraints (Sec. 3.4), caller vertex ids, as last given
+    std::vector<int> sub_vertex, sub_dim;
+    std::vector<double> sub_dir;     // 3 per constraint: line direction or plane normal
     // device
     bool bound = false;
     char *ws = nullptr;
@@ -248,6 +251,32 @@ bool sc_wanted(const vbd_ctx *c) { return c->params.self_collision && c->surface
 int surf_count(const vbd_ctx *c) { return sc_wanted(c) ? (int)c->surf.size() : 0; }
 
 // Carves the workspace; with base == nullptr only measures it.
+// Orthonormal basis of a subspace constraint (Sec. 3.4): L = 1, the unit
+// line direction (second vector zero); L = 2, two unit vectors spanning the
+// plane normal to dir (Gram-Schmidt on the coordinate axis least aligned
+// with the normal, then the normal's cross product with it).
+void subspace_basis(int L, const double *dir, double b[2][3]) {
+    const double nn = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+    const double n[3] = {dir[0] / nn, dir[1] / nn, dir[2] / nn};
+    for (int r = 0; r < 3; ++r) b[1][r] = 0.0;
+    if (L == 1) {
+        for (int r = 0; r < 3; ++r) b[0][r] = n[r];
+        return;
+    }
+    int a = 0;
+    for (int r = 1; r < 3; ++r)
+        if (std::fabs(n[r]) < std::fabs(n[a])) a = r;
+    double e[3] = {0.0, 0.0, 0.0};
+    e[a] = 1.0;
+    const double en = n[a];
+    for (int r = 0; r < 3; ++r) e[r] -= en * n[r];
+    const double el = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    for (int r = 0; r < 3; ++r) b[0][r] = e[r] / el;
+    b[1][0] = n[1] * b[0][2] - n[2] * b[0][1];
+    b[1][1] = n[2] * b[0][0] - n[0] * b[0][2];
+    b[1][2] = n[0] * b[0][1] - n[1] * b[0][0];
+}
+
 size_t carve(const vbd_ctx *c, char *base, Dev *d) {
     size_t off = 0;
     auto take = [&](size_t bytes) -> char * {
@@ -282,6 +311,10 @@ size_t carve(const vbd_ctx *c, char *base, Dev *d) {
     }
     t.slot_tet = (int *)take(4 * S);
     t.slot_loc = (int *)take(4 * S);
+    if (!c->sub_vertex.empty()) {
+        t.sub_id = (int *)take(4 * ((size_t)c->n_free + 1));
+        t.sub_q = (float4 *)take(32 * c->sub_vertex.size());
+    }
     t.tet_v = (int4 *)take(16 * T);
     t.tet_B = (float *)take(36 * T);
     t.tet_V = (float *)take(4 * T);
@@ -346,6 +379,7 @@ SweepParams sweep_params(const vbd_ctx *c, int color) {
     if (c->params.ground_on) add_plane(c->params.ground_normal, c->params.ground_height);
     for (int k = 0; k < c->params.n_walls; ++k) add_plane(c->params.walls[k], c->params.walls[k][3]);
     p.kc = c->params.k_c;
+    p.n_sub = (int)c->sub_vertex.size();
     p.det_eps = c->params.det_eps;
     p.kd_over_h = c->h > 0.f ? c->params.k_d / c->h : 0.f;
     p.inv_h2 = c->h > 0.f ? 1.f / (c->h * c->h) : 0.f;
@@ -884,6 +918,22 @@ vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *st
        "upload slot_off");
     CU(cudaMemcpyAsync(d.color_begin, ctx->color_begin.data(), 4 * ((size_t)ctx->n_colors + 1),
                        cudaMemcpyHostToDevice, s), "upload colour ranges");
+    if (!ctx->sub_vertex.empty()) {
+        // constraint index per free vertex and an orthonormal basis per constraint
+        const size_t ns = ctx->sub_vertex.size();
+        std::vector<int> sid((size_t)ctx->n_free + 1, -1);
+        std::vector<float4> q(2 * ns);
+        for (size_t k = 0; k < ns; ++k) {
+            sid[ctx->new_of_orig[ctx->sub_vertex[k]]] = (int)k;
+            double b[2][3];
+            subspace_basis(ctx->sub_dim[k], &ctx->sub_dir[3 * k], b);
+            q[2 * k] = make_float4((float)b[0][0], (float)b[0][1], (float)b[0][2], (float)ctx->sub_dim[k]);
+            q[2 * k + 1] = make_float4((float)b[1][0], (float)b[1][1], (float)b[1][2], 0.f);
+        }
+        CU(cudaMemcpyAsync(d.sub_id, sid.data(), 4 * sid.size(), cudaMemcpyHostToDevice, s), "upload sub_id");
+        CU(cudaMemcpyAsync(d.sub_q, q.data(), 16 * q.size(), cudaMemcpyHostToDevice, s), "upload sub_q");
+        CU(cudaStreamSynchronize(s), "upload subspaces");
+    }
     {
         // per-vertex material when every tet around each free vertex shares it
         std::vector<float2> vm(N, make_float2(0.f, 0.f));
@@ -1020,6 +1070,32 @@ vbd_status vbd_set_params(vbd_ctx *ctx, const vbd_params *params) {
     return VBD_OK;
 }
 
+vbd_status vbd_set_subspaces(vbd_ctx *ctx, int32_t n, const int32_t *vertex, const int32_t *dim,
+                             const float *dir) {
+    if (!ctx) return VBD_ERR_INVALID_ARG;
+    if (ctx->bound) return fail(ctx, VBD_ERR_STATE, "set subspace constraints before vbd_bind");
+    if (n < 0 || (n > 0 && (!vertex || !dim || !dir))) return fail(ctx, VBD_ERR_INVALID_ARG, "bad constraint arrays");
+    std::vector<char> seen((size_t)ctx->N, 0);
+    for (int k = 0; k < n; ++k) {
+        const int i = vertex[k];
+        if (i < 0 || i >= ctx->N) return fail(ctx, VBD_ERR_INVALID_ARG, "constrained vertex out of range");
+        if (ctx->pinned[i]) return fail(ctx, VBD_ERR_INVALID_ARG, "a pinned vertex cannot take a subspace");
+        if (seen[i]) return fail(ctx, VBD_ERR_INVALID_ARG, "vertex constrained twice");
+        seen[i] = 1;
+        if (dim[k] != 1 && dim[k] != 2) return fail(ctx, VBD_ERR_INVALID_ARG, "subspace dimension must be 1 or 2");
+        const float *e = dir + 3 * k;
+        const double en = std::sqrt((double)e[0] * e[0] + (double)e[1] * e[1] + (double)e[2] * e[2]);
+        if (!(en > 0.0) || !std::isfinite(en)) return fail(ctx, VBD_ERR_INVALID_ARG, "zero or non-finite direction");
+    }
+    ctx->sub_vertex.assign(vertex, vertex + n);
+    ctx->sub_dim.assign(dim, dim + n);
+    ctx->sub_dir.resize(3 * (size_t)n);
+    for (int k = 0; k < 3 * n; ++k) ctx->sub_dir[k] = dir[k];
+    ctx->version++;
+    clear_graphs(ctx);
+    return VBD_OK;
+}
+
 static vbd_status check_bound(vbd_ctx *ctx) {
     if (!ctx) return VBD_ERR_INVALID_ARG;
     if (!ctx->colored) return fail(ctx, VBD_ERR_NOT_COLORED, "vbd_color has not run");
@@ -1113,7 +1189,7 @@ vbd_status vbd_begin_step(vbd_ctx *ctx, float h) {
     }
     const float *g = ctx->params.gravity;
     vbd::launch_predict(ctx->d, ctx->N, ctx->n_free, h, make_float3(g[0], g[1], g[2]), ctx->params.init_mode,
-                        ctx->params.cheby_rho > 0.f, ctx->stream);
+                        ctx->params.cheby_rho > 0.f, !ctx->sub_vertex.empty(), ctx->stream);
     CU(cudaGetLastError(), "predict");
     ctx->in_step = true;
     return VBD_OK;
@@ -1283,6 +1359,8 @@ vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, floa
     if (ctx->tape_len < 1) return fail(ctx, VBD_ERR_NO_TAPE, "no recorded steps (tape_steps = 0?)");
     if (ctx->params.k_d != 0.f || ctx->params.mu_c != 0.f || ctx->params.self_collision)
         return fail(ctx, VBD_ERR_INVALID_ARG, "the adjoint needs k_d = 0, mu_c = 0 and no self-collision");
+    if (!ctx->sub_vertex.empty())
+        return fail(ctx, VBD_ERR_STATE, "the adjoint does not cover subspace-constrained vertices");
     if (!is_device_ptr(dL_dxT) || (dL_dlogE && !is_device_ptr(dL_dlogE)) || (dL_dv0 && !is_device_ptr(dL_dv0)))
         return fail(ctx, VBD_ERR_INVALID_ARG, "vbd_backward takes device pointers");
     const Dev &d = ctx->d;

@@ -232,9 +232,10 @@ __device__ __forceinline__ bool contact_item(const Dev &d, const SweepParams &p,
 // Eqs. 8-9, damping (Eqs. 10-11), ground and wall penalties (Eq. 12,
 // Sec. 3.4), self-contact, singular skip, analytic inverse.
 // sc: self-contact sums (f, H) and bit 0 = some pair acted, bit 1 = involved.
-// LS = false compiles the line search out (the register-capped sweeps keep
-// its operands live otherwise); LS = true runs it when p.line_search is set.
-template <bool SC, bool LS = true>
+// EXT = false compiles the optional parts out (the register-capped sweeps
+// keep their operands live otherwise): the line search and the subspace
+// step; EXT = true runs them when p.line_search / p.n_sub ask for them.
+template <bool SC, bool EXT = true>
 __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams &p, int vi, float4 xi,
                                                 const Acc &a, const Acc &ca, int sc) {
     // xi holds the displacement u_i; ym the displacement of the inertia target
@@ -301,30 +302,70 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
         }
     }
     float4 *out = stage ? d.unew : d.u;
-    // adjugate of the symmetric H
-    const float a00 = h11 * h22 - h12 * h12;
-    const float a01 = h02 * h12 - h01 * h22;
-    const float a02 = h01 * h12 - h02 * h11;
-    const float a11 = h00 * h22 - h02 * h02;
-    const float a12 = h01 * h02 - h00 * h12;
-    const float a22 = h00 * h11 - h01 * h01;
-    const float det = h00 * a00 + h01 * a01 + h02 * a02;
-    const float tr3 = (h00 + h11 + h22) * (1.0f / 3.0f);
-    if (!(fabsf(det) > p.det_eps * fabsf(tr3 * tr3 * tr3))) {
-        atomicAdd(d.counters + 1, 1ull);
-        if (stage || flag != xi.w) out[vi] = make_float4(xi.x, xi.y, xi.z, flag);
-        return;
+    float dx, dy, dz;
+    const int sub = (EXT && p.n_sub > 0) ? d.sub_id[vi] : -1;
+    if (sub >= 0) {
+        // subspace constraint (Sec. 3.4): Q^T H Q dz = Q^T f in the basis q_1
+        // (.w = L) and q_2 of the line or plane, dx = Q dz, with the singular
+        // test of Sec. 3.2 on the L x L matrix
+        const float4 qa = d.sub_q[2 * sub], qb = d.sub_q[2 * sub + 1];
+        const float ha0 = h00 * qa.x + h01 * qa.y + h02 * qa.z;
+        const float ha1 = h01 * qa.x + h11 * qa.y + h12 * qa.z;
+        const float ha2 = h02 * qa.x + h12 * qa.y + h22 * qa.z;
+        const float A00 = qa.x * ha0 + qa.y * ha1 + qa.z * ha2;
+        const float b0 = qa.x * f0 + qa.y * f1 + qa.z * f2;
+        bool singular;
+        float z0, z1 = 0.f;
+        if (qa.w < 1.5f) {
+            singular = !(fabsf(A00) > p.det_eps * fabsf(A00));
+            z0 = b0 / A00;
+        } else {
+            const float A01 = qb.x * ha0 + qb.y * ha1 + qb.z * ha2;
+            const float A11 = qb.x * (h00 * qb.x + h01 * qb.y + h02 * qb.z) +
+                              qb.y * (h01 * qb.x + h11 * qb.y + h12 * qb.z) +
+                              qb.z * (h02 * qb.x + h12 * qb.y + h22 * qb.z);
+            const float b1 = qb.x * f0 + qb.y * f1 + qb.z * f2;
+            const float det2 = A00 * A11 - A01 * A01;
+            const float tr2 = 0.5f * (A00 + A11);
+            singular = !(fabsf(det2) > p.det_eps * tr2 * tr2);
+            const float inv2 = 1.0f / det2;
+            z0 = (A11 * b0 - A01 * b1) * inv2;
+            z1 = (A00 * b1 - A01 * b0) * inv2;
+        }
+        if (singular) {
+            atomicAdd(d.counters + 1, 1ull);
+            if (stage || flag != xi.w) out[vi] = make_float4(xi.x, xi.y, xi.z, flag);
+            return;
+        }
+        dx = qa.x * z0 + qb.x * z1;
+        dy = qa.y * z0 + qb.y * z1;
+        dz = qa.z * z0 + qb.z * z1;
+    } else {
+        // adjugate of the symmetric H
+        const float a00 = h11 * h22 - h12 * h12;
+        const float a01 = h02 * h12 - h01 * h22;
+        const float a02 = h01 * h12 - h02 * h11;
+        const float a11 = h00 * h22 - h02 * h02;
+        const float a12 = h01 * h02 - h00 * h12;
+        const float a22 = h00 * h11 - h01 * h01;
+        const float det = h00 * a00 + h01 * a01 + h02 * a02;
+        const float tr3 = (h00 + h11 + h22) * (1.0f / 3.0f);
+        if (!(fabsf(det) > p.det_eps * fabsf(tr3 * tr3 * tr3))) {
+            atomicAdd(d.counters + 1, 1ull);
+            if (stage || flag != xi.w) out[vi] = make_float4(xi.x, xi.y, xi.z, flag);
+            return;
+        }
+        const float inv = 1.0f / det;
+        dx = (a00 * f0 + a01 * f1 + a02 * f2) * inv;
+        dy = (a01 * f0 + a11 * f1 + a12 * f2) * inv;
+        dz = (a02 * f0 + a12 * f1 + a22 * f2) * inv;
     }
-    const float inv = 1.0f / det;
-    float dx = (a00 * f0 + a01 * f1 + a02 * f2) * inv;
-    float dy = (a01 * f0 + a11 * f1 + a12 * f2) * inv;
-    float dz = (a02 * f0 + a12 * f1 + a22 * f2) * inv;
     if (!(isfinite(dx) && isfinite(dy) && isfinite(dz))) {
         atomicAdd(d.counters + 0, 1ull);
         if (stage) out[vi] = xi;
         return;
     }
-    if (LS && p.line_search) {
+    if (EXT && p.line_search) {
         // G_i along dx: inertia + elasticity are exactly quadratic in x_i, so
         // G_i(x + alpha dx) - G_i(x) = -alpha fv.dx + alpha^2/2 dx.Hv.dx + the
         // change of the plane penalties, with fv, Hv the variational force and
@@ -363,7 +404,7 @@ __device__ __forceinline__ void solve_and_store(const Dev &d, const SweepParams 
 
 // One colour pass for the vertex of global thread gt (L lanes per vertex).
 // RS: compact slots, shape gradients recomputed from the rest positions.
-template <int L, bool SC, bool COH = false, bool LS = true, bool RS = false>
+template <int L, bool SC, bool COH = false, bool EXT = true, bool RS = false>
 __device__ __forceinline__ void sweep_body(const Dev &d, const SweepParams &p, long long gt,
                                            int vbegin, int vend) {
     const int lane = threadIdx.x & (L - 1);
@@ -423,41 +464,42 @@ __device__ __forceinline__ void sweep_body(const Dev &d, const SweepParams &p, l
         }
         sc = (n_items > 0 ? 2 : 0) | hit;
     }
-    if (active && lane == 0) solve_and_store<SC, LS>(d, p, vi, xi, acc, ca, sc);
+    if (active && lane == 0) solve_and_store<SC, EXT>(d, p, vi, xi, acc, ca, sc);
 }
 
 // Both gather kernels are held to 48 registers (5 CTAs of 256 threads per
 // SM, no spills without the line search): 40 resident warps hide the gather
 // latency better than 32 at 56 registers (measured 62.1 vs 64.0 us per
-// 1M-vertex pass).  LS: instance with the line search (Sec. 3.2) compiled in.
-template <int L, bool LS>
+// 1M-vertex pass).  EXT: instance with the line search (Sec. 3.2) and the
+// subspace step (Sec. 3.4) compiled in.
+template <int L, bool EXT>
 __global__ void __launch_bounds__(256, 5) k_sweep(Dev d, SweepParams p) {
-    sweep_body<L, false, false, LS>(d, p, (long long)blockIdx.x * blockDim.x + threadIdx.x, p.vbegin, p.vend);
+    sweep_body<L, false, false, EXT>(d, p, (long long)blockIdx.x * blockDim.x + threadIdx.x, p.vbegin, p.vend);
 }
 
 // persistent form: a grid of (SMs x resident CTAs) walks the colour's
 // vertices in grid-sized strides (the stride is uniform over a warp, so
 // every lane joins the shuffles of each round)
-template <int L, bool LS>
+template <int L, bool EXT>
 __global__ void __launch_bounds__(256, 5) k_sweep_persist(Dev d, SweepParams p, long long threads) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < threads; base += stride)
-        sweep_body<L, false, false, LS>(d, p, base + threadIdx.x, p.vbegin, p.vend);
+        sweep_body<L, false, false, EXT>(d, p, base + threadIdx.x, p.vbegin, p.vend);
 }
 
 // persistent form over compact slots (gradients from the rest positions)
-template <int L, bool LS>
+template <int L, bool EXT>
 __global__ void __launch_bounds__(256, 4) k_sweep_rest(Dev d, SweepParams p, long long threads) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < threads; base += stride)
-        sweep_body<L, false, false, LS, true>(d, p, base + threadIdx.x, p.vbegin, p.vend);
+        sweep_body<L, false, false, EXT, true>(d, p, base + threadIdx.x, p.vbegin, p.vend);
 }
 
 // with self-contact forces; capped at 64 registers so that enough warps stay
-// resident to hide the gather latency
-template <int L>
+// resident to hide the gather latency (EXT: with the subspace step)
+template <int L, bool EXT>
 __global__ void __launch_bounds__(256, 4) k_sweep_sc(Dev d, SweepParams p) {
-    sweep_body<L, true, false, false>(d, p, (long long)blockIdx.x * blockDim.x + threadIdx.x, p.vbegin, p.vend);
+    sweep_body<L, true, false, EXT>(d, p, (long long)blockIdx.x * blockDim.x + threadIdx.x, p.vbegin, p.vend);
 }
 
 // ---- two-phase tet-scatter-into-slots sweep ----------------------------------
@@ -692,7 +734,7 @@ __global__ void __launch_bounds__(TT) k_sweep_pipe(Dev d, SweepParams p, int max
 
 // Eq. 3 and Sec. 3.7 options (a)-(d), Eq. 17.  Pinned vertices (ids >= n_free) keep x^t.
 __global__ void k_predict(Dev d, int n, int n_free, float h, float3 g, float gnorm, int mode,
-                          int cheby) {
+                          int cheby, int has_sub) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float4 xi = d.u[i];
@@ -719,6 +761,15 @@ __global__ void k_predict(Dev d, int n, int n_free, float h, float3 g, float gno
         const float ah2 = h2 * at;
         xn = make_float4(xi.x + h * vi.x + ah2 * g.x, xi.y + h * vi.y + ah2 * g.y,
                          xi.z + h * vi.z + ah2 * g.z, 0.f);
+        const int sub = has_sub ? d.sub_id[i] : -1;
+        if (sub >= 0) {  // a subspace-constrained vertex starts on x^t + span(Q) (Sec. 3.4)
+            const float4 qa = d.sub_q[2 * sub], qb = d.sub_q[2 * sub + 1];
+            const float ex = xn.x - xi.x, ey = xn.y - xi.y, ez = xn.z - xi.z;
+            const float ca = qa.x * ex + qa.y * ey + qa.z * ez;
+            const float cb = qa.w < 1.5f ? 0.f : qb.x * ex + qb.y * ey + qb.z * ez;
+            xn = make_float4(xi.x + ca * qa.x + cb * qb.x, xi.y + ca * qa.y + cb * qb.y,
+                             xi.z + ca * qa.z + cb * qb.z, 0.f);
+        }
     }
     d.u[i] = xn;
     if (cheby) d.cheb[0][i] = xn;
@@ -936,32 +987,36 @@ int num_sms() {
 }
 
 void launch_predict(const Dev &d, int n, int n_free, float h, float3 g, int init_mode, bool cheby,
-                    cudaStream_t s) {
+                    bool has_sub, cudaStream_t s) {
     const float gnorm = sqrtf(g.x * g.x + g.y * g.y + g.z * g.z);
-    k_predict<<<blocks_for(n, 256), 256, 0, s>>>(d, n, n_free, h, g, gnorm, init_mode, cheby ? 1 : 0);
+    k_predict<<<blocks_for(n, 256), 256, 0, s>>>(d, n, n_free, h, g, gnorm, init_mode, cheby ? 1 : 0,
+                                                  has_sub ? 1 : 0);
 }
 
-template <int L, bool LS>
+// the sweep instance with the optional epilogue parts
+static bool needs_ext(const SweepParams &p) { return p.line_search || p.n_sub > 0; }
+
+template <int L, bool EXT>
 static unsigned persist_grid(int block) {
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_persist<L, LS>, block, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_persist<L, EXT>, block, 0) != cudaSuccess ||
         occ < 1)
         occ = 1;
     return (unsigned)(num_sms() * occ);
 }
 
-template <bool LS>
-static void launch_persist_ls(const Dev &d, const SweepParams &p, int lanes, int block, long long threads,
+template <bool EXT>
+static void launch_persist_ext(const Dev &d, const SweepParams &p, int lanes, int block, long long threads,
                               cudaStream_t s) {
     const unsigned need = blocks_for(threads, block);
     switch (lanes) {
-    case 4: k_sweep_persist<4, LS><<<std::min(need, persist_grid<4, LS>(block)), block, 0, s>>>(d, p, threads); break;
-    case 8: k_sweep_persist<8, LS><<<std::min(need, persist_grid<8, LS>(block)), block, 0, s>>>(d, p, threads); break;
+    case 4: k_sweep_persist<4, EXT><<<std::min(need, persist_grid<4, EXT>(block)), block, 0, s>>>(d, p, threads); break;
+    case 8: k_sweep_persist<8, EXT><<<std::min(need, persist_grid<8, EXT>(block)), block, 0, s>>>(d, p, threads); break;
     case 16:
-        k_sweep_persist<16, LS><<<std::min(need, persist_grid<16, LS>(block)), block, 0, s>>>(d, p, threads);
+        k_sweep_persist<16, EXT><<<std::min(need, persist_grid<16, EXT>(block)), block, 0, s>>>(d, p, threads);
         break;
     default:
-        k_sweep_persist<32, LS><<<std::min(need, persist_grid<32, LS>(block)), block, 0, s>>>(d, p, threads);
+        k_sweep_persist<32, EXT><<<std::min(need, persist_grid<32, EXT>(block)), block, 0, s>>>(d, p, threads);
         break;
     }
 }
@@ -969,39 +1024,39 @@ static void launch_persist_ls(const Dev &d, const SweepParams &p, int lanes, int
 void launch_sweep_persist(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s) {
     const long long threads = (long long)(p.vend - p.vbegin) * lanes;
     if (threads <= 0) return;
-    if (p.line_search)
-        launch_persist_ls<true>(d, p, lanes, block, threads, s);
+    if (needs_ext(p))
+        launch_persist_ext<true>(d, p, lanes, block, threads, s);
     else
-        launch_persist_ls<false>(d, p, lanes, block, threads, s);
+        launch_persist_ext<false>(d, p, lanes, block, threads, s);
 }
 
-template <int L, bool LS>
+template <int L, bool EXT>
 static unsigned rest_grid(int block) {
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_rest<L, LS>, block, 0) != cudaSuccess || occ < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_rest<L, EXT>, block, 0) != cudaSuccess || occ < 1)
         occ = 1;
     return (unsigned)(num_sms() * occ);
 }
 
-template <bool LS>
-static void launch_rest_ls(const Dev &d, const SweepParams &p, int lanes, int block, long long threads,
+template <bool EXT>
+static void launch_rest_ext(const Dev &d, const SweepParams &p, int lanes, int block, long long threads,
                            cudaStream_t s) {
     const unsigned need = blocks_for(threads, block);
     switch (lanes) {
-    case 4: k_sweep_rest<4, LS><<<std::min(need, rest_grid<4, LS>(block)), block, 0, s>>>(d, p, threads); break;
-    case 8: k_sweep_rest<8, LS><<<std::min(need, rest_grid<8, LS>(block)), block, 0, s>>>(d, p, threads); break;
-    case 16: k_sweep_rest<16, LS><<<std::min(need, rest_grid<16, LS>(block)), block, 0, s>>>(d, p, threads); break;
-    default: k_sweep_rest<32, LS><<<std::min(need, rest_grid<32, LS>(block)), block, 0, s>>>(d, p, threads); break;
+    case 4: k_sweep_rest<4, EXT><<<std::min(need, rest_grid<4, EXT>(block)), block, 0, s>>>(d, p, threads); break;
+    case 8: k_sweep_rest<8, EXT><<<std::min(need, rest_grid<8, EXT>(block)), block, 0, s>>>(d, p, threads); break;
+    case 16: k_sweep_rest<16, EXT><<<std::min(need, rest_grid<16, EXT>(block)), block, 0, s>>>(d, p, threads); break;
+    default: k_sweep_rest<32, EXT><<<std::min(need, rest_grid<32, EXT>(block)), block, 0, s>>>(d, p, threads); break;
     }
 }
 
 void launch_sweep_rest(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s) {
     const long long threads = (long long)(p.vend - p.vbegin) * lanes;
     if (threads <= 0) return;
-    if (p.line_search)
-        launch_rest_ls<true>(d, p, lanes, block, threads, s);
+    if (needs_ext(p))
+        launch_rest_ext<true>(d, p, lanes, block, threads, s);
     else
-        launch_rest_ls<false>(d, p, lanes, block, threads, s);
+        launch_rest_ext<false>(d, p, lanes, block, threads, s);
 }
 
 void launch_sweep_scatter(const Dev &d, const SweepParams &p, int sbegin, int send, int lanes, int block,
@@ -1023,15 +1078,24 @@ void launch_sweep(const Dev &d, const SweepParams &p, int lanes, int block, cuda
     if (threads <= 0) return;
     const unsigned grid = blocks_for(threads, block);
     if (p.self_collision) {
+        if (needs_ext(p)) {
+            switch (lanes) {
+            case 4: k_sweep_sc<4, true><<<grid, block, 0, s>>>(d, p); break;
+            case 8: k_sweep_sc<8, true><<<grid, block, 0, s>>>(d, p); break;
+            case 16: k_sweep_sc<16, true><<<grid, block, 0, s>>>(d, p); break;
+            default: k_sweep_sc<32, true><<<grid, block, 0, s>>>(d, p); break;
+            }
+            return;
+        }
         switch (lanes) {
-        case 4: k_sweep_sc<4><<<grid, block, 0, s>>>(d, p); break;
-        case 8: k_sweep_sc<8><<<grid, block, 0, s>>>(d, p); break;
-        case 16: k_sweep_sc<16><<<grid, block, 0, s>>>(d, p); break;
-        default: k_sweep_sc<32><<<grid, block, 0, s>>>(d, p); break;
+        case 4: k_sweep_sc<4, false><<<grid, block, 0, s>>>(d, p); break;
+        case 8: k_sweep_sc<8, false><<<grid, block, 0, s>>>(d, p); break;
+        case 16: k_sweep_sc<16, false><<<grid, block, 0, s>>>(d, p); break;
+        default: k_sweep_sc<32, false><<<grid, block, 0, s>>>(d, p); break;
         }
         return;
     }
-    if (p.line_search) {
+    if (needs_ext(p)) {
         switch (lanes) {
         case 4: k_sweep<4, true><<<grid, block, 0, s>>>(d, p); break;
         case 8: k_sweep<8, true><<<grid, block, 0, s>>>(d, p); break;

@@ -34,6 +34,9 @@ struct Dev {
     float *scr2;      //                                               h22
     int *slot_tet;    // caller tet id of each slot
     int *slot_loc;    // local index (0..3) of the slot's own vertex in that tet
+    // subspace constraints (Sec. 3.4), when any vertex has one
+    int *sub_id;      // n_free: index of the vertex's constraint, or -1
+    float4 *sub_q;    // 2 per constraint: q_1 (.w = L) and q_2, an orthonormal basis of the subspace
     // per tet (caller order)
     int4 *tet_v;      // vertex ids (internal numbering)
     float *tet_B;     // 9 per tet: inverse rest edge matrix, row-major
@@ -76,6 +79,7 @@ struct SweepParams {
     int vbegin, vend;
     float4 planes[kMaxPlanes];  // xyz unit normal, w offset: the allowed side is x.n >= w
     int n_planes;     // planes in use (ground first when on, then the walls)
+    int n_sub;        // subspace-constrained vertices (Sec. 3.4); > 0 reads Dev::sub_id
     float kc;         // collision stiffness (Eq. 12)
     float det_eps;
     float kd_over_h;  // Rayleigh damping k_d / h
@@ -110,7 +114,7 @@ struct CollideDims {
 int num_sms();
 
 void launch_predict(const Dev &d, int n, int n_free, float h, float3 g, int init_mode,
-                    bool cheby, cudaStream_t s);
+                    bool cheby, bool has_sub, cudaStream_t s);
 void launch_sweep(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s);
 // persistent grid-stride form of launch_sweep (grid = SMs x resident CTAs)
 void launch_sweep_persist(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s);

@@ -25,7 +25,8 @@ STATUS_CODE = {v: k for k, v in STATUS.items()}
 # every entry point declared in include/vbd.h
 ENTRY_POINTS = [
     "vbd_default_params", "vbd_create_mesh", "vbd_color", "vbd_get_colors", "vbd_get_info",
-    "vbd_get_surface", "vbd_workspace_size", "vbd_bind", "vbd_set_params", "vbd_set_state", "vbd_get_state",
+    "vbd_get_surface", "vbd_workspace_size", "vbd_bind", "vbd_set_params", "vbd_set_subspaces", "vbd_set_state",
+    "vbd_get_state",
     "vbd_set_log_young", "vbd_step", "vbd_begin_step", "vbd_iterate", "vbd_sweep_color",
     "vbd_accelerate", "vbd_end_step", "vbd_energy", "vbd_energy_static", "vbd_get_contacts", "vbd_sync_status",
     "vbd_backward",
@@ -84,6 +85,7 @@ def load() -> C.CDLL:
     P, I32, F, D = C.c_void_p, C.c_int32, C.c_float, C.c_double
     sig = {
         "vbd_default_params": (None, [C.POINTER(vbd_params)]),
+        "vbd_set_subspaces": (C.c_int, [P, I32, P, P, P]),
         "vbd_create_mesh": (C.c_int, [C.POINTER(vbd_mesh_desc), C.POINTER(vbd_params), C.POINTER(P)]),
         "vbd_color": (C.c_int, [P, P, C.POINTER(I32)]),
         "vbd_get_colors": (C.c_int, [P, P]),
@@ -196,6 +198,19 @@ def vbd_bind(ctx: int, workspace, nbytes: int, stream: int) -> None:
 
 def vbd_set_params(ctx: int, params: vbd_params) -> None:
     _check("vbd_set_params", ctx, load().vbd_set_params(ctx, C.byref(params)))
+
+
+def vbd_set_subspaces(ctx: int, vertex, dim, direction) -> None:
+    """Subspace constraints (Sec. 3.4): vertex ids (caller order), dim 1 (line)
+    or 2 (plane), direction (n, 3): line direction or plane normal."""
+    vertex = np.ascontiguousarray(vertex, dtype=np.int32).reshape(-1)
+    dim = np.ascontiguousarray(dim, dtype=np.int32).reshape(-1)
+    direction = np.ascontiguousarray(direction, dtype=np.float32).reshape(-1)
+    if not (len(dim) == len(vertex) and len(direction) == 3 * len(vertex)):
+        raise ValueError("vertex, dim and direction must describe the same constraints")
+    _check("vbd_set_subspaces", ctx, load().vbd_set_subspaces(
+        ctx, len(vertex), vertex.ctypes.data if len(vertex) else None, dim.ctypes.data if len(vertex) else None,
+        direction.ctypes.data if len(vertex) else None))
 
 
 def vbd_set_state(ctx: int, x, v, v_prev=None) -> None:
@@ -371,6 +386,10 @@ class Sim:
         self.tape_steps = int(params.tape_steps)
         self.ctx = vbd_create_mesh(arrs.desc(), params)
         try:
+            sub_dim = getattr(mesh, "sub_dim", None)
+            if sub_dim is not None:
+                k = np.nonzero(np.asarray(sub_dim) < 3)[0]
+                vbd_set_subspaces(self.ctx, k, np.asarray(sub_dim)[k], np.asarray(mesh.sub_dir)[k])
             self.n_colors = vbd_color(self.ctx, colors)
             self.ws_bytes = vbd_workspace_size(self.ctx)
             self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)

@@ -187,3 +187,31 @@ def test_wall_params_are_validated(lib):
         vbd.vbd_set_params(ctx, vbd.make_params(walls=[(0, 0, 1, 0)], ground_on=True))
     finally:
         vbd.vbd_destroy(ctx)
+
+
+def test_subspace_constraints_are_validated(lib):
+    """Subspace constraints (Sec. 3.4): caller ids in range, not pinned, once
+    each, dimension 1 or 2, a non-zero finite direction; they enlarge the
+    workspace."""
+    m = synth.beam(3, 2, 2, edge=0.1)
+    arr = vbd.MeshArrays(m.rest, m.tets, m.young, m.poisson, m.density, m.pinned)
+    ctx = vbd.vbd_create_mesh(arr.desc(), vbd.make_params())
+    try:
+        pinned = int(np.nonzero(m.pinned)[0][0])
+        free = np.nonzero(m.pinned == 0)[0][:3]
+        for vertex, dim, d in (([-1], [1], [(1, 0, 0)]), ([pinned], [2], [(1, 0, 0)]),
+                               ([free[0], free[0]], [1, 1], [(1, 0, 0)] * 2), ([free[0]], [0], [(1, 0, 0)]),
+                               ([free[0]], [1], [(0, 0, 0)]), ([free[0]], [2], [(np.inf, 1, 0)])):
+            with pytest.raises(vbd.VbdError) as e:
+                vbd.vbd_set_subspaces(ctx, vertex, dim, d)
+            assert e.value.status == "VBD_ERR_INVALID_ARG"
+        with pytest.raises(ValueError):
+            vbd.vbd_set_subspaces(ctx, [free[0]], [1, 2], [(1, 0, 0)])
+        vbd.vbd_color(ctx, None)
+        size0 = vbd.vbd_workspace_size(ctx)
+        vbd.vbd_set_subspaces(ctx, free, [1, 2, 1], [(1, 0, 0), (0, 0, 2), (0.3, 0.4, 0)])
+        assert vbd.vbd_workspace_size(ctx) > size0
+        vbd.vbd_set_subspaces(ctx, [], [], np.zeros((0, 3)))
+        assert vbd.vbd_workspace_size(ctx) == size0
+    finally:
+        vbd.vbd_destroy(ctx)
