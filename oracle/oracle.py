@@ -50,14 +50,14 @@ class Params(C.Structure):
                 ("ground_normal", C.c_double * 3), ("k_c", C.c_double), ("cheby_rho", C.c_double),
                 ("init_mode", C.c_int), ("det_eps", C.c_double), ("k_d", C.c_double),
                 ("mu_c", C.c_double), ("eps_v", C.c_double), ("line_search", C.c_int), ("jacobi", C.c_int),
-                ("self_collision", C.c_int), ("dcd_radius", C.c_double), ("n_walls", C.c_int),
-                ("walls", C.c_double * 24)]
+                ("self_collision", C.c_int), ("dcd_radius", C.c_double), ("ccd_interval", C.c_int),
+                ("n_walls", C.c_int), ("walls", C.c_double * 24)]
 
     @classmethod
     def make(cls, gravity=(0.0, 0.0, -9.8), ground_on=False, ground_height=0.0,
              ground_normal=(0.0, 0.0, 1.0), k_c=0.0, cheby_rho=0.0, init_mode=3,
              det_eps=1e-12, k_d=0.0, mu_c=0.0, eps_v=1e-3, line_search=False, jacobi=False,
-             self_collision=False, dcd_radius=0.0, walls=(), **_ignored) -> "Params":
+             self_collision=False, dcd_radius=0.0, walls=(), ccd_interval=0, **_ignored) -> "Params":
         """walls: up to 6 world-box half-spaces (nx, ny, nz, offset), the allowed
         side being x.n/|n| >= offset (Sec. 3.4)."""
         p = cls()
@@ -76,6 +76,7 @@ class Params(C.Structure):
         p.jacobi = int(bool(jacobi))
         p.self_collision = int(bool(self_collision))
         p.dcd_radius = float(dcd_radius)
+        p.ccd_interval = int(ccd_interval)
         walls = [tuple(float(v) for v in w) for w in walls]
         if len(walls) > 6 or any(len(w) != 4 for w in walls):
             raise ValueError("walls: at most 6 tuples (nx, ny, nz, offset)")
@@ -128,6 +129,10 @@ def lib():
             "orc_model_tris": (None, [vp, _ip]),
             "orc_closest_point_tri": (None, [_dp, _dp, _dp, _dp, _dp, _dp]),
             "orc_point_in_tet": (C.c_int, [_dp, _ip, _dp]),
+            "orc_ccd_vertex": (C.c_int, [vp, _dp, _dp, C.c_int, C.POINTER(C.c_double), _dp]),
+            "orc_ccd": (C.c_int, [vp, _dp, _dp]),
+            "orc_cubic_first_root": (C.c_double, [_dp, C.c_double]),
+            "orc_model_contact_weights": (None, [vp, _dp, _up]),
             "orc_dcd_vertex": (C.c_int, [vp, C.POINTER(Params), _dp, C.c_int]),
             "orc_dcd": (None, [vp, C.POINTER(Params), _dp]),
             "orc_model_contacts": (None, [vp, _ip]),
@@ -211,6 +216,11 @@ def tet_hess_block(x, B, V, mu, lam, k, l) -> np.ndarray:
     H = np.zeros(9)
     lib().orc_tet_hess_block(_d(x, 12), _d(B, 9), V, mu, lam, k, l, H)
     return H.reshape(3, 3)
+
+
+def cubic_first_root(c, t_min=0.0) -> float:
+    """Earliest root in [t_min, 1] of c0 + c1 t + c2 t^2 + c3 t^3, or -1."""
+    return float(lib().orc_cubic_first_root(_d(c, 4), float(t_min)))
 
 
 def ground_friction(p: "Params", h: float, xi, xti, lambda_n: float):
@@ -398,6 +408,24 @@ class Model:
         c = np.zeros(self.n, np.int32)
         lib().orc_model_contacts(self._h, c)
         return c
+
+    def contact_weights(self):
+        """(impact weights (N, 3), CCD flag (N,)) of the current pairs."""
+        w = np.zeros(3 * self.n)
+        f = np.zeros(self.n, np.uint8)
+        lib().orc_model_contact_weights(self._h, w, f)
+        return w.reshape(-1, 3), f.astype(bool)
+
+    def ccd_vertex(self, x0, x1, a):
+        """(triangle or -1, time of impact, weights) of vertex a's CCD (Sec. 3.5)."""
+        toi = C.c_double(-1.0)
+        w = np.zeros(3)
+        T = lib().orc_ccd_vertex(self._h, _d(x0).reshape(-1), _d(x1).reshape(-1), int(a), C.byref(toi), w)
+        return int(T), float(toi.value), w
+
+    def ccd(self, x0, x1) -> int:
+        """CCD of every vertex without a step-start pair; returns the pair count."""
+        return int(lib().orc_ccd(self._h, _d(x0).reshape(-1), _d(x1).reshape(-1)))
 
     def local_energy(self, p: Params, h, i, x, y) -> float:
         return lib().orc_local_energy(self._h, C.byref(p), h, int(i), _d(x).reshape(-1), _d(y).reshape(-1))

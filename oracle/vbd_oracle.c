@@ -53,6 +53,17 @@
  *    k_c w_k^2 n n^T.  These elements may join two vertices of one colour,
  *    so colour passes then use x^new and a copy-back (Algorithm 1): every
  *    vertex of the pass solves against the positions at its start.
+ *  - Vertex-triangle CCD (Sec. 3.5): before every ccd_interval-th iteration
+ *    (iterations 1, 1 + n_col, ...) each boundary vertex without a
+ *    step-start pair is swept against the boundary triangles that share no
+ *    tet with it, along the straight paths from x^t to the current iterate.
+ *    Its impact is the earliest root t in [0, 1] of the coplanarity cubic
+ *    at which it lies in the closed triangle (impacts within 1e-5 in t are
+ *    tied; the lowest triangle index wins).  The pair keeps the impact
+ *    point's barycentric weights w (the contact point is sum w_k x_k) and
+ *    uses the triangle's current normal, with the penalty and friction of
+ *    the DCD pairs; each CCD replaces the previous CCD pairs.  Edge-edge
+ *    contacts are not detected.
  *  - Ground friction (Eqs. 13-16): the ground is static, so the relative
  *    displacement is delta = x_i - x_i^t; u = its tangential part.  lambda
  *    is read as the normal-force magnitude k_c d >= 0 (as printed, the
@@ -83,6 +94,8 @@ struct orc_model {
     int *tris;           /* 3 * n_tris */
     unsigned char *on_surface; /* N */
     int *contact;        /* N: triangle hit by the vertex (DCD at x^t), or -1 */
+    double *contact_w;   /* 3N: impact weights of a CCD pair (fixed for the pair's life) */
+    unsigned char *contact_ccd; /* N: 1 = the vertex's pair came from CCD, 0 = from the DCD */
     int *sub_dim;        /* N: L of the vertex's subspace constraint (Sec. 3.4), 3 = none */
     double *sub_basis;   /* 9N: orthonormal basis q_1..q_L of that subspace, 3 doubles each */
 };
@@ -446,6 +459,8 @@ orc_model *orc_model_new(int n, int t, const double *rest, const int *tets,
         free(faces);
         m->contact = (int *)malloc(sizeof(int) * (size_t)n + 1);
         for (int i = 0; i < n; ++i) m->contact[i] = -1;
+        m->contact_w = (double *)calloc(3 * (size_t)n + 1, sizeof(double));
+        m->contact_ccd = (unsigned char *)calloc((size_t)n + 1, 1);
     }
     m->sub_dim = (int *)malloc(sizeof(int) * (size_t)n + 1);
     m->sub_basis = (double *)calloc(9 * (size_t)n + 1, sizeof(double));
@@ -524,7 +539,8 @@ void orc_model_free(orc_model *m) {
     if (!m) return;
     free(m->tets); free(m->B); free(m->V); free(m->mu); free(m->lam); free(m->poisson);
     free(m->mass); free(m->pinned); free(m->inc_off); free(m->inc_tet); free(m->inc_loc);
-    free(m->tris); free(m->on_surface); free(m->contact); free(m->sub_dim); free(m->sub_basis);
+    free(m->tris); free(m->on_surface); free(m->contact); free(m->contact_w); free(m->contact_ccd);
+    free(m->sub_dim); free(m->sub_basis);
     free(m);
 }
 
@@ -602,7 +618,14 @@ static double contact_depth(const orc_model *m, int a, const double *x, double n
     const int T = m->contact[a];
     const int *v = m->tris + 3 * (size_t)T;
     double q[3];
-    orc_closest_point_tri(x + 3 * a, x + 3 * v[0], x + 3 * v[1], x + 3 * v[2], q, w);
+    if (m->contact_ccd[a]) {
+        /* CCD pair: the impact point keeps its barycentric weights (Sec. 3.5) */
+        for (int k = 0; k < 3; ++k) w[k] = m->contact_w[3 * (size_t)a + k];
+        for (int r = 0; r < 3; ++r)
+            q[r] = w[0] * x[3 * v[0] + r] + w[1] * x[3 * v[1] + r] + w[2] * x[3 * v[2] + r];
+    } else {
+        orc_closest_point_tri(x + 3 * a, x + 3 * v[0], x + 3 * v[1], x + 3 * v[2], q, w);
+    }
     tri_normal(m, T, x, n);
     return (q[0] - x[3 * a]) * n[0] + (q[1] - x[3 * a + 1]) * n[1] + (q[2] - x[3 * a + 2]) * n[2];
 }
@@ -673,7 +696,163 @@ int orc_dcd_vertex(const orc_model *m, const orc_params *p, const double *x, int
 }
 
 void orc_dcd(orc_model *m, const orc_params *p, const double *x) {
-    for (int a = 0; a < m->n_verts; ++a) m->contact[a] = orc_dcd_vertex(m, p, x, a);
+    for (int a = 0; a < m->n_verts; ++a) {
+        m->contact[a] = orc_dcd_vertex(m, p, x, a);
+        m->contact_ccd[a] = 0;
+    }
+}
+
+/* f(t) = c0 + c1 t + c2 t^2 + c3 t^3.  Its earliest root in [t_min, 1]: the
+ * interval is cut at the roots of f' into monotone pieces, and the first
+ * piece that starts at a zero or changes sign is bisected to full FP64
+ * precision.  Returns -1 when f has no root there; a cubic that vanishes
+ * identically (coplanar motion) counts as no root. */
+double orc_cubic_first_root(const double c[4], double t_min) {
+    double scale = fabs(c[0]) + fabs(c[1]) + fabs(c[2]) + fabs(c[3]);
+    if (!(scale > 0.0)) return -1.0;
+    double cut[4];
+    int nc = 0;
+    cut[nc++] = t_min;
+    /* roots of f' = c1 + 2 c2 t + 3 c3 t^2 inside (t_min, 1), ascending */
+    double qa = 3.0 * c[3], qb = 2.0 * c[2], qc = c[1], r[2];
+    int nr = 0;
+    if (qa != 0.0) {
+        double disc = qb * qb - 4.0 * qa * qc;
+        if (disc >= 0.0) {
+            double sq = sqrt(disc);
+            r[0] = (-qb - sq) / (2.0 * qa);
+            r[1] = (-qb + sq) / (2.0 * qa);
+            if (r[0] > r[1]) { double t = r[0]; r[0] = r[1]; r[1] = t; }
+            nr = 2;
+        }
+    } else if (qb != 0.0) {
+        r[0] = -qc / qb;
+        nr = 1;
+    }
+    for (int k = 0; k < nr; ++k)
+        if (r[k] > t_min && r[k] < 1.0) cut[nc++] = r[k];
+    cut[nc++] = 1.0;
+    for (int k = 0; k + 1 < nc; ++k) {
+        double lo = cut[k], hi = cut[k + 1];
+        double flo = ((c[3] * lo + c[2]) * lo + c[1]) * lo + c[0];
+        double fhi = ((c[3] * hi + c[2]) * hi + c[1]) * hi + c[0];
+        if (flo == 0.0) return lo;
+        if ((flo < 0.0) == (fhi < 0.0) && fhi != 0.0) continue;
+        for (int it = 0; it < 200 && hi - lo > 1e-15; ++it) {
+            double mid = 0.5 * (lo + hi);
+            double fm = ((c[3] * mid + c[2]) * mid + c[1]) * mid + c[0];
+            if (fm == 0.0) { lo = hi = mid; break; }
+            if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; } else { hi = mid; }
+        }
+        return hi;
+    }
+    return -1.0;
+}
+
+/* Time of impact of vertex a with triangle v along the linear trajectories
+ * (Sec. 3.5 CCD).  With r_k(t) = x_k(t) - x_a(t) = A_k + t B_k for the three
+ * corners, the vertex is in the triangle's plane where
+ * f(t) = r_1 . (r_2 x r_3) = 0, a cubic whose coefficients follow from the
+ * trilinear expansion in (A_k, B_k).  Its roots are visited in order; the
+ * first one at which the vertex lies inside the (closed) triangle, by
+ * barycentric weights of the projected point, is the impact.  Returns the
+ * time or -1; w receives the weights. */
+static double vt_impact(const double *x0, const double *x1, int a, const int *v, double w[3]) {
+    double A[3][3], B[3][3];
+    for (int k = 0; k < 3; ++k)
+        for (int r = 0; r < 3; ++r) {
+            A[k][r] = x0[3 * v[k] + r] - x0[3 * a + r];
+            B[k][r] = (x1[3 * v[k] + r] - x1[3 * a + r]) - A[k][r];
+        }
+    double t23[3], c[4], tmp[3];
+    cross3(A[1], A[2], t23);
+    c[0] = dot3(A[0], t23);
+    c[1] = dot3(B[0], t23);
+    cross3(B[1], A[2], tmp); c[1] += dot3(A[0], tmp);
+    cross3(A[1], B[2], tmp); c[1] += dot3(A[0], tmp);
+    cross3(B[1], A[2], tmp); c[2] = dot3(B[0], tmp);
+    cross3(A[1], B[2], tmp); c[2] += dot3(B[0], tmp);
+    cross3(B[1], B[2], tmp); c[2] += dot3(A[0], tmp);
+    c[3] = dot3(B[0], tmp);
+    double t0 = 0.0;
+    for (int rep = 0; rep < 3; ++rep) {
+        double t = orc_cubic_first_root(c, t0);
+        if (t < 0.0) return -1.0;
+        /* barycentric weights of the vertex, projected onto the triangle at t */
+        double r1[3], r2[3], r3[3], n[3], e1[3], e2[3], s1[3], s2[3], s3[3];
+        for (int q = 0; q < 3; ++q) {
+            r1[q] = A[0][q] + t * B[0][q];
+            r2[q] = A[1][q] + t * B[1][q];
+            r3[q] = A[2][q] + t * B[2][q];
+            e1[q] = r2[q] - r1[q];
+            e2[q] = r3[q] - r1[q];
+        }
+        cross3(e1, e2, n);
+        double nn = dot3(n, n);
+        if (nn > 0.0) {
+            cross3(r2, r3, s1);  /* twice the area of (a, 2, 3) along n, and so on */
+            cross3(r3, r1, s2);
+            cross3(r1, r2, s3);
+            w[0] = dot3(s1, n) / nn;
+            w[1] = dot3(s2, n) / nn;
+            w[2] = dot3(s3, n) / nn;
+            if (w[0] >= 0.0 && w[1] >= 0.0 && w[2] >= 0.0) return t;
+        }
+        /* not inside at this root: look for the next one */
+        t0 = t + 1e-12;
+        if (t0 >= 1.0) return -1.0;
+    }
+    return -1.0;
+}
+
+int orc_ccd_vertex(const orc_model *m, const double *x0, const double *x1, int a, double *toi, double wout[3]) {
+    if (!m->on_surface[a]) return -1;
+    double best = 2.0;
+    int best_T = -1;
+    for (int T = 0; T < m->n_tris; ++T) {
+        const int *v = m->tris + 3 * (size_t)T;
+        int adjacent = 0;  /* a triangle vertex shares a tet with a */
+        for (int s = m->inc_off[a]; s < m->inc_off[a + 1] && !adjacent; ++s)
+            for (int k = 0; k < 4; ++k) {
+                int q = m->tets[4 * (size_t)m->inc_tet[s] + k];
+                adjacent |= (q == v[0]) | (q == v[1]) | (q == v[2]);
+            }
+        if (adjacent) continue;
+        double w[3];
+        double t = vt_impact(x0, x1, a, v, w);
+        /* earliest impact; impacts within 1e-5 of it count as tied and the
+         * lowest triangle index wins (triangles are visited in order) */
+        if (t >= 0.0 && t < best - 1e-5) {
+            best = t;
+            best_T = T;
+            for (int k = 0; k < 3; ++k) wout[k] = w[k];
+        }
+    }
+    if (best_T >= 0 && toi) *toi = best;
+    return best_T;
+}
+
+int orc_ccd(orc_model *m, const double *x0, const double *x1) {
+    int n = 0;
+    for (int a = 0; a < m->n_verts; ++a) {
+        if (m->contact[a] >= 0 && !m->contact_ccd[a]) continue;  /* keeps its step-start pair */
+        double toi, w[3];
+        int T = orc_ccd_vertex(m, x0, x1, a, &toi, w);
+        m->contact[a] = T;
+        m->contact_ccd[a] = T >= 0;
+        if (T >= 0) {
+            for (int k = 0; k < 3; ++k) m->contact_w[3 * (size_t)a + k] = w[k];
+            ++n;
+        }
+    }
+    return n;
+}
+
+void orc_model_contact_weights(const orc_model *m, double *w, unsigned char *is_ccd) {
+    for (int a = 0; a < m->n_verts; ++a) {
+        is_ccd[a] = m->contact_ccd ? m->contact_ccd[a] : 0;
+        for (int k = 0; k < 3; ++k) w[3 * (size_t)a + k] = m->contact_w ? m->contact_w[3 * (size_t)a + k] : 0.0;
+    }
 }
 
 int orc_model_n_verts(const orc_model *m) { return m->n_verts; }
@@ -1026,6 +1205,9 @@ int orc_step(const orc_model *m, const orc_params *p, const int *colors, int n_c
     double omega = 1.0;
     double *xj = p->jacobi ? (double *)malloc(sizeof(double) * n3 + 1) : NULL;
     for (int n = 1; n <= iters; ++n) {
+        /* CCD along x^t -> x^(n-1) before every ccd_interval-th iteration (Sec. 3.5) */
+        if (p->self_collision && p->ccd_interval > 0 && (n - 1) % p->ccd_interval == 0)
+            orc_ccd((orc_model *)m, xt, x);
         if (p->jacobi) {
             /* block Jacobi: solve every free vertex against the previous iterate */
             memcpy(xj, x, sizeof(double) * n3);

@@ -43,6 +43,7 @@ typedef struct {
     int jacobi;             /* 1: block Jacobi: all vertices from the previous iterate */
     int self_collision;     /* 1: vertex-triangle penalty contacts from a DCD at x^t (Sec. 3.5) */
     double dcd_radius;      /* DCD search radius */
+    int ccd_interval;       /* > 0: vertex-triangle CCD before every ccd_interval-th iteration (Sec. 3.5) */
     int n_walls;            /* world-box walls (Sec. 3.4), 0..ORC_MAX_WALLS */
     double walls[4 * 6];    /* wall k: normal walls[4k..4k+2] (any length), offset walls[4k+3];
                                the allowed side is x.n/|n| >= offset */
@@ -94,6 +95,18 @@ void orc_closest_point_tri(const double p[3], const double a[3], const double b[
 int orc_point_in_tet(const double *x, const int *tet, const double q[3]);
 int orc_dcd_vertex(const orc_model *m, const orc_params *p, const double *x, int a);
 void orc_dcd(orc_model *m, const orc_params *p, const double *x);
+/* Vertex-triangle CCD along x(tau) = (1 - tau) x0 + tau x1, tau in [0, 1]
+ * (Sec. 3.5): earliest impact of boundary vertex a with a boundary triangle
+ * that shares no tet with it; returns the triangle (or -1) with its time of
+ * impact and the barycentric weights of the impact point. */
+int orc_ccd_vertex(const orc_model *m, const double *x0, const double *x1, int a, double *toi, double w[3]);
+/* CCD of every boundary vertex without a step-start (DCD) pair; replaces the
+ * previous CCD pairs.  Returns the number of CCD pairs. */
+int orc_ccd(orc_model *m, const double *x0, const double *x1);
+/* Earliest root in [0, 1] of c0 + c1 t + c2 t^2 + c3 t^3 at or after t_min
+ * whose point passes `accept`; -1 if none (exposed for the pins). */
+double orc_cubic_first_root(const double c[4], double t_min);
+void orc_model_contact_weights(const orc_model *m, double *w, unsigned char *is_ccd);
 void orc_model_contacts(const orc_model *m, int *contact);
 int orc_self_contact(const orc_model *m, const orc_params *p, double h, int i, const double *x,
                      const double *xt, double f[3], double H[9]);

@@ -70,6 +70,13 @@ MUTANTS = [
      "test_oracle_subspace.py"),
     ("plane_basis_not_orthogonalised", "for (int r = 0; r < 3; ++r) e[r] -= en * d[r];", "",
      "test_oracle_subspace.py"),
+    ("ccd_cubic_term_dropped", "cross3(A[1], B[2], tmp); c[1] += dot3(A[0], tmp);", "", "test_oracle_ccd.py"),
+    ("ccd_inside_test_two_weights", "if (w[0] >= 0.0 && w[1] >= 0.0 && w[2] >= 0.0) return t;",
+     "if (w[0] >= 0.0 && w[1] >= 0.0) return t;", "test_oracle_ccd.py"),
+    ("ccd_latest_impact_wins", "if (t >= 0.0 && t < best - 1e-5) {", "if (t >= 0.0 && (best > 1.5 || t > best + 1e-5)) {",
+     "test_oracle_ccd.py"),
+    ("ccd_pair_uses_nearest_point", "    if (m->contact_ccd[a]) {\n        /* CCD pair",
+     "    if (0) {\n        /* CCD pair", "test_oracle_ccd.py"),
 ]
 
 
@@ -91,7 +98,7 @@ def _run_pins(src_text, pin_file):
 def test_identity_copy_passes():
     src = open(SRC).read()
     for pin in ("test_oracle_element.py", "test_oracle_solver.py", "test_oracle_collision.py",
-                "test_oracle_walls.py", "test_oracle_subspace.py"):
+                "test_oracle_walls.py", "test_oracle_subspace.py", "test_oracle_ccd.py"):
         assert _run_pins(src, pin) == 0, pin
 
 
