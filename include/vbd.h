@@ -101,6 +101,8 @@ typedef struct {
     int32_t n_walls;         /* world-box walls in use, 0..VBD_MAX_WALLS */
     float walls[6][4];       /* wall k: normal walls[k][0..2] (need not be unit length) and offset
                                 walls[k][3]; the allowed side is {x : x . n/|n| >= offset} */
+    int32_t ccd_interval;    /* > 0 (with self_collision): vertex-triangle CCD before iterations
+                                1, 1 + ccd_interval, ... of each step (Sec. 3.5); 0 = DCD only */
 } vbd_params;
 
 #define VBD_MAX_WALLS 6
@@ -147,7 +149,18 @@ typedef struct {
  * c (I - n n^T), corner k +w_k c u with w_k^2 c (I - n n^T).  Every colour pass then
  * solves its vertices against the pass-start positions and copies them back
  * (x^new of Algorithm 1), because a contact can couple two vertices of one
- * colour; the pipelined sweep is not used.  Needs dcd_radius > 0; not
+ * colour; the pipelined sweep is not used.
+ * ccd_interval = n_col > 0 adds the CCD of Sec. 3.5: before iterations 1,
+ * 1 + n_col, 1 + 2 n_col, ... each boundary vertex without a step-start
+ * pair is swept along its straight path from x^t to the current iterate
+ * against the boundary triangles that share no tet with it (their corners
+ * moving the same way); the earliest time at which it lies in a closed
+ * triangle (the coplanarity cubic's first admissible root; impacts within
+ * 1e-5 in time are tied, the lowest index wins) gives a pair that acts
+ * through the impact point, whose barycentric weights stay fixed, with the
+ * triangle's current normal and the same penalty and friction.  Each CCD
+ * replaces the previous CCD pairs; step-start pairs stay.  Edge-edge
+ * contacts are not detected.  Needs dcd_radius > 0; not
  * available with line_search; enlarges the workspace, so set it before
  * vbd_bind. */
 void vbd_default_params(vbd_params *out);

@@ -16,6 +16,18 @@
 // tests.  Each element is
 // stored once (count, prefix sum, fill), so the tables never overflow.
 //
+// CCD (Sec. 3.5), before every n_col-th iteration: each boundary vertex
+// without a step-start pair is swept along its straight path from x^t to
+// the current iterate against the boundary triangles (their corners moving
+// the same way) that share no tet with it.  Broad phase: bounding spheres of
+// each triangle's six corner positions (both ends of its motion) hashed with
+// cells of 1.05 (R_tri + R_v), R_v the largest half path of a vertex; a
+// triangle that meets the vertex's path has its sphere centre within
+// R_tri + R_v of the path's midpoint.  Narrow phase: the earliest root of the
+// coplanarity cubic at which the vertex lies in the closed triangle; impacts
+// within 1e-5 in time are tied and the lowest triangle index wins.  The pair
+// keeps the impact point's barycentric weights (contact_w).
+//
 // The sweep needs, for each free vertex, the pairs in which it is a triangle
 // corner: that reverse list is built the same way and then sorted per vertex
 // so that forces are always summed in the same order.
@@ -72,9 +84,15 @@ __device__ __forceinline__ float tet_cell_width(const Dev &d) {
     return kMargin * __uint_as_float(d.cell_size[1]) + 1e-30f;
 }
 
+// cell of the swept-triangle table (CCD): a triangle whose motion meets a
+// vertex's path has its sphere centre within R_tri + R_v of the path's midpoint
+__device__ __forceinline__ float swept_cell_width(const Dev &d) {
+    return kMargin * (__uint_as_float(d.cell_size[0]) + __uint_as_float(d.cell_size[2])) + 1e-30f;
+}
+
 template <int K>
 __device__ __forceinline__ float table_cell_width(const Dev &d, float r) {
-    return K == 3 ? tri_cell_width(d, r) : tet_cell_width(d);
+    return K == 3 ? tri_cell_width(d, r) : (K == 4 ? tet_cell_width(d) : swept_cell_width(d));
 }
 
 __device__ __forceinline__ int3 cell_of(const Dev &d, float3 p, float inv_c) {
@@ -123,6 +141,46 @@ __global__ void k_bounds(Dev d, const int4 *items, int n, float4 *sphere, unsign
     float R = sqrtf(R2);
     if (!(R >= 0.f)) R = 0.f;  // a NaN position never widens the cells
     sphere[t] = make_float4(m.x, m.y, m.z, R);
+    atomicMax(rmax, __float_as_uint(R));
+}
+
+// Bounding sphere of each triangle's corners at both ends of their motion
+// (x^t = X + ut and the current X + u), for the CCD.
+__global__ void k_bounds_swept(Dev d, int n, float4 *sphere, unsigned *rmax) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int4 v = d.tri[t];
+    const int c[3] = {v.x, v.y, v.z};
+    float3 p[6];
+    float3 m = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float3 X = f3(__ldg(d.rest + c[k]));
+        p[k] = X + f3(__ldg(d.ut + c[k]));
+        p[k + 3] = X + f3(__ldg(d.u + c[k]));
+        m = m + p[k] + p[k + 3];
+    }
+    m = (1.0f / 6.0f) * m;
+    float R2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float3 e = p[k] - m;
+        R2 = fmaxf(R2, dot(e, e));
+    }
+    float R = sqrtf(R2);
+    if (!(R >= 0.f)) R = 0.f;
+    sphere[t] = make_float4(m.x, m.y, m.z, R);
+    atomicMax(rmax, __float_as_uint(R));
+}
+
+// the largest half path |u - ut| / 2 of a boundary vertex
+__global__ void k_path_radius(Dev d, int n_surf, unsigned *rmax) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_surf) return;
+    const int a = d.surf[k];
+    const float3 e = f3(__ldg(d.u + a)) - f3(__ldg(d.ut + a));
+    float R = 0.5f * sqrtf(dot(e, e));
+    if (!(R >= 0.f)) R = 0.f;
     atomicMax(rmax, __float_as_uint(R));
 }
 
@@ -282,7 +340,170 @@ __global__ void __launch_bounds__(128) k_query(Dev d, int n_surf, int nb_tri, in
     pair = group_min_index(pair);
     if (active && lane == 0) {
         d.contact[a] = pair;
+        if (d.contact_w) d.contact_w[a] = make_float4(0.f, 0.f, 0.f, 0.f);  // a DCD pair (or none)
         if (pair >= 0) atomicAdd(d.counters + 3, 1ull);
+    }
+}
+
+// ---- CCD narrow phase ------------------------------------------------------------
+// Earliest root in [t0, 1] of c0 + c1 t + c2 t^2 + c3 t^3: the interval is cut
+// at the roots of the derivative into monotone pieces; the first piece that
+// starts at a zero or changes sign is bisected (at most 40 halvings, to
+// FP32 resolution).  -1 if none; a cubic that vanishes identically (coplanar
+// motion) has no root.
+__device__ __forceinline__ float cubic_first_root(float c0, float c1, float c2, float c3, float t0) {
+    if (!(fabsf(c0) + fabsf(c1) + fabsf(c2) + fabsf(c3) > 0.f)) return -1.f;
+    float cut[4];
+    int nc = 0;
+    cut[nc++] = t0;
+    const float qa = 3.f * c3, qb = 2.f * c2, qc = c1;
+    float r0 = 2.f, r1 = 2.f;
+    if (qa != 0.f) {
+        const float disc = qb * qb - 4.f * qa * qc;
+        if (disc >= 0.f) {
+            const float sq = sqrtf(disc);
+            r0 = (-qb - sq) / (2.f * qa);
+            r1 = (-qb + sq) / (2.f * qa);
+            if (r0 > r1) { const float t = r0; r0 = r1; r1 = t; }
+        }
+    } else if (qb != 0.f) {
+        r0 = -qc / qb;
+    }
+    if (r0 > t0 && r0 < 1.f) cut[nc++] = r0;
+    if (r1 > t0 && r1 < 1.f) cut[nc++] = r1;
+    cut[nc++] = 1.f;
+    for (int k = 0; k + 1 < nc; ++k) {
+        float lo = cut[k], hi = cut[k + 1];
+        float flo = ((c3 * lo + c2) * lo + c1) * lo + c0;
+        const float fhi = ((c3 * hi + c2) * hi + c1) * hi + c0;
+        if (flo == 0.f) return lo;
+        if ((flo < 0.f) == (fhi < 0.f) && fhi != 0.f) continue;
+        for (int it = 0; it < 40 && hi - lo > 1e-7f; ++it) {
+            const float mid = 0.5f * (lo + hi);
+            const float fm = ((c3 * mid + c2) * mid + c1) * mid + c0;
+            if (fm == 0.f) return mid;
+            if ((fm < 0.f) == (flo < 0.f)) {
+                lo = mid;
+                flo = fm;
+            } else {
+                hi = mid;
+            }
+        }
+        return hi;
+    }
+    return -1.f;
+}
+
+// Time of impact of a vertex with a triangle whose corners, relative to the
+// vertex, move as A_k + t B_k (t in [0, 1]); -1 if none.  The coplanarity
+// cubic r_1 . (r_2 x r_3) comes from the trilinear expansion; its roots are
+// taken in order and the first with the vertex in the closed triangle (all
+// barycentric weights >= 0) is the impact, its weights in w.
+__device__ __forceinline__ float vt_impact(float3 A0, float3 A1, float3 A2, float3 B0, float3 B1, float3 B2,
+                                           float3 &w) {
+    const float3 a12 = cross(A1, A2);
+    const float c0 = dot(A0, a12);
+    const float c1 = dot(B0, a12) + dot(A0, cross(B1, A2)) + dot(A0, cross(A1, B2));
+    const float3 b12 = cross(B1, B2);
+    const float c2 = dot(B0, cross(B1, A2)) + dot(B0, cross(A1, B2)) + dot(A0, b12);
+    const float c3 = dot(B0, b12);
+    float t0 = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {
+        const float t = cubic_first_root(c0, c1, c2, c3, t0);
+        if (t < 0.f) return -1.f;
+        const float3 r1 = A0 + t * B0, r2 = A1 + t * B1, r3 = A2 + t * B2;
+        const float3 n = cross(r2 - r1, r3 - r1);
+        const float nn = dot(n, n);
+        if (nn > 0.f) {
+            w = make_float3(dot(cross(r2, r3), n) / nn, dot(cross(r3, r1), n) / nn, dot(cross(r1, r2), n) / nn);
+            if (w.x >= 0.f && w.y >= 0.f && w.z >= 0.f) return t;
+        }
+        t0 = t + 1e-6f;
+        if (t0 >= 1.f) return -1.f;
+    }
+    return -1.f;
+}
+
+// relative start position and motion of corner k seen from vertex a
+__device__ __forceinline__ void rel_path(const Dev &d, int k, float3 Xa, float3 uta, float3 ua, float3 &A, float3 &B) {
+    const float3 utk = f3(__ldg(d.ut + k));
+    A = (f3(__ldg(d.rest + k)) - Xa) + (utk - uta);
+    B = (f3(__ldg(d.u + k)) - ua) - (utk - uta);
+}
+
+// earliest admissible impact of vertex a (boundary index k) among the
+// triangles of this lane's cells: pass 0 returns the earliest time (or -1),
+// pass 1 the lowest triangle index hit by time `lim` (or -1)
+template <int Q>
+__device__ __forceinline__ float earliest_impact(const Dev &d, int k, float3 Xa, float3 uta, float3 ua, float3 mid,
+                                                float Ra, int3 cell, int nb, int lane, float slack, int pass,
+                                                float lim, int &pair) {
+    const int g0 = d.ring_off[k], g1 = d.ring_off[k + 1];
+    float best = -1.f;
+    for (int n = lane; n < 27; n += Q) {
+        const int b = neighbour_bucket(cell, n, nb);
+        const int e1 = d.cell_start[b + 1];
+        for (int e = d.cell_start[b]; e < e1; ++e) {
+            const int t = d.cell_tri[e];
+            if (pass == 1 && pair >= 0 && t >= pair) continue;
+            if (sphere_far(d.tri_sphere[t], mid, Ra + slack)) continue;
+            const int4 v = d.tri[t];
+            bool adjacent = false;
+            for (int g = g0; g < g1 && !adjacent; ++g) {
+                const int q = d.ring[g];
+                adjacent = (q == v.x) | (q == v.y) | (q == v.z);
+            }
+            if (adjacent) continue;
+            float3 A0, A1, A2, B0, B1, B2, w;
+            rel_path(d, v.x, Xa, uta, ua, A0, B0);
+            rel_path(d, v.y, Xa, uta, ua, A1, B1);
+            rel_path(d, v.z, Xa, uta, ua, A2, B2);
+            const float ti = vt_impact(A0, A1, A2, B0, B1, B2, w);
+            if (ti < 0.f) continue;
+            if (pass == 0 && (best < 0.f || ti < best)) best = ti;
+            if (pass == 1 && ti <= lim) pair = t;
+        }
+    }
+    return best;
+}
+
+__global__ void __launch_bounds__(128) k_ccd(Dev d, int n_surf, int nb) {
+    constexpr int Q = kQueryLanes;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = (int)(g / Q), lane = (int)(g % Q);
+    const bool active = k < n_surf;  // inactive lanes still join the shuffles
+    const int a = active ? d.surf[k] : 0;
+    // a vertex paired at the step start keeps that pair (uniform over the group)
+    const bool keep = active && d.contact[a] >= 0 && !(d.contact_w[a].w > 0.5f);
+    const float3 Xa = f3(__ldg(d.rest + a)), uta = f3(__ldg(d.ut + a)), ua = f3(__ldg(d.u + a));
+    const float3 path = ua - uta;
+    const float3 mid = Xa + uta + 0.5f * path;
+    const float Ra = 0.5f * sqrtf(dot(path, path));
+    const float c = swept_cell_width(d);
+    const float slack = kSlack * c;
+    const int3 cell = (active && !keep) ? cell_of(d, mid, 1.0f / c) : make_int3(0, 0, 0);
+    int pair = -1;
+    float best = (active && !keep)
+                     ? earliest_impact<Q>(d, k, Xa, uta, ua, mid, Ra, cell, nb, lane, slack, 0, 0.f, pair)
+                     : -1.f;
+    best = group_min_dist(best);
+    if (best >= 0.f)  // uniform over the group
+        earliest_impact<Q>(d, k, Xa, uta, ua, mid, Ra, cell, nb, lane, slack, 1, best + 1e-5f, pair);
+    pair = group_min_index(pair);
+    if (!active || lane != 0 || keep) return;
+    if (pair >= 0) {
+        const int4 v = d.tri[pair];
+        float3 A0, A1, A2, B0, B1, B2, w = make_float3(0.f, 0.f, 0.f);
+        rel_path(d, v.x, Xa, uta, ua, A0, B0);
+        rel_path(d, v.y, Xa, uta, ua, A1, B1);
+        rel_path(d, v.z, Xa, uta, ua, A2, B2);
+        vt_impact(A0, A1, A2, B0, B1, B2, w);
+        d.contact[a] = pair;
+        d.contact_w[a] = make_float4(w.x, w.y, w.z, 1.f);
+        atomicAdd(d.counters + 3, 1ull);
+    } else {
+        d.contact[a] = -1;
+        d.contact_w[a] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
@@ -401,6 +622,17 @@ void exclusive_scan(const int *in, int *out, int n, int *tmp, cudaStream_t s) {
     k_scan_add<<<std::max(1u, blocks_for(n, 256)), 256, 0, s>>>(out, n, tmp, tiles);
 }
 
+// reverse corner lists of the current pairs, for the sweep
+void build_reverse_lists(const Dev &d, const CollideDims &c, int n_free, cudaStream_t s) {
+    if (n_free <= 0) return;
+    cudaMemsetAsync(d.rev_fill, 0, sizeof(int) * (size_t)n_free, s);
+    k_rev_count<<<blocks_for(c.n_surf, 256), 256, 0, s>>>(d, c.n_surf, n_free, d.rev_fill);
+    exclusive_scan(d.rev_fill, d.rev_off, n_free, d.scan_tmp, s);
+    cudaMemsetAsync(d.rev_fill, 0, sizeof(int) * (size_t)n_free, s);
+    k_rev_fill<<<blocks_for(c.n_surf, 256), 256, 0, s>>>(d, c.n_surf, n_free);
+    k_rev_sort<<<blocks_for(c.n_surf, 256), 256, 0, s>>>(d, c.n_surf, n_free);
+}
+
 }  // namespace
 
 int scan_tmp_needed(int n) { return (int)blocks_for(std::max(n, 1), kScanTile) + 1; }
@@ -429,14 +661,23 @@ void launch_detect(const Dev &d, const CollideDims &c, int n_free, cudaStream_t 
     // narrow phase
     k_query<<<blocks_for((long long)c.n_surf * kQueryLanes, 128), 128, 0, s>>>(d, c.n_surf, c.n_buckets,
                                                                               c.n_tet_buckets, c.radius);
-    // reverse lists for the sweep
-    if (n_free <= 0) return;
-    cudaMemsetAsync(d.rev_fill, 0, sizeof(int) * (size_t)n_free, s);
-    k_rev_count<<<blocks_for(c.n_surf, 256), 256, 0, s>>>(d, c.n_surf, n_free, d.rev_fill);
-    exclusive_scan(d.rev_fill, d.rev_off, n_free, d.scan_tmp, s);
-    cudaMemsetAsync(d.rev_fill, 0, sizeof(int) * (size_t)n_free, s);
-    k_rev_fill<<<blocks_for(c.n_surf, 256), 256, 0, s>>>(d, c.n_surf, n_free);
-    k_rev_sort<<<blocks_for(c.n_surf, 256), 256, 0, s>>>(d, c.n_surf, n_free);
+    build_reverse_lists(d, c, n_free, s);
+}
+
+void launch_ccd(const Dev &d, const CollideDims &c, int n_free, cudaStream_t s) {
+    if (c.n_surf <= 0 || c.n_tris <= 0 || !d.contact_w) return;
+    // broad phase: spheres of the triangles' motions and the vertices' half paths
+    cudaMemsetAsync(d.cell_size, 0, 3 * sizeof(unsigned), s);
+    k_bounds_swept<<<blocks_for(c.n_tris, 256), 256, 0, s>>>(d, c.n_tris, d.tri_sphere, d.cell_size);
+    k_path_radius<<<blocks_for(c.n_surf, 256), 256, 0, s>>>(d, c.n_surf, d.cell_size + 2);
+    cudaMemsetAsync(d.cell_fill, 0, sizeof(int) * (size_t)c.n_buckets, s);
+    k_count<5><<<blocks_for(c.n_tris, 256), 256, 0, s>>>(d, d.tri_sphere, c.n_tris, c.n_buckets, 0.f, d.cell_fill);
+    exclusive_scan(d.cell_fill, d.cell_start, c.n_buckets, d.scan_tmp, s);
+    cudaMemsetAsync(d.cell_fill, 0, sizeof(int) * (size_t)c.n_buckets, s);
+    k_fill<5><<<blocks_for(c.n_tris, 256), 256, 0, s>>>(d, d.tri_sphere, c.n_tris, c.n_buckets, 0.f, d.cell_start,
+                                                        d.cell_fill, d.cell_tri);
+    k_ccd<<<blocks_for((long long)c.n_surf * kQueryLanes, 128), 128, 0, s>>>(d, c.n_surf, c.n_buckets);
+    build_reverse_lists(d, c, n_free, s);
 }
 
 }  // namespace vbd

@@ -56,28 +56,26 @@ __device__ __forceinline__ float3 nearest_weights(float3 a, float3 b, float3 c) 
     return make_float3(w[0], w[1], w[2]);
 }
 
-// One vertex-triangle pair seen from the vertex: a, b, c are the corners
-// relative to the vertex.  Returns the penetration depth d = (q - x).n of
-// Eq. 12 with q the nearest point and n the triangle's unit normal (positive
-// when the vertex is behind the triangle), and writes n and the weights.
-__device__ __forceinline__ float vt_depth(float3 a, float3 b, float3 c, float3 &n, float3 &w) {
-    w = nearest_weights(a, b, c);
-    const float3 q = make_float3(w.x * a.x + w.y * b.x + w.z * c.x, w.x * a.y + w.y * b.y + w.z * c.y,
-                                 w.x * a.z + w.y * b.z + w.z * c.z);
-    const float3 nn = cross(b - a, c - a);
-    n = rsqrtf(dot(nn, nn)) * nn;
-    return dot(q, n);
-}
-
-// Depth, normal and weights of the pair (vertex a, triangle t) at x = X + u.
+// Depth, normal and weights of the pair (vertex a, triangle t) at x = X + u:
+// d = (q - x_a).n of Eq. 12 with q the contact point and n the triangle's
+// unit normal (positive when the vertex is behind the triangle).
 // Differences are formed separately for the rest positions and the
-// displacements, so that FP32 keeps the small gaps exact to rounding.
+// displacements, so that FP32 keeps the small gaps exact to rounding.  A
+// pair found by CCD (contact_w[a].w = 1) acts through its impact point,
+// whose barycentric weights stay fixed (Sec. 3.5); a DCD pair through the
+// nearest point.
 __device__ __forceinline__ float pair_depth(const Dev &d, int a, int4 t, float3 &n, float3 &w) {
     const float3 Xa = f3(__ldg(d.rest + a)), ua = f3(__ldg(d.u + a));
     const float3 pa = (f3(__ldg(d.rest + t.x)) - Xa) + (f3(__ldg(d.u + t.x)) - ua);
     const float3 pb = (f3(__ldg(d.rest + t.y)) - Xa) + (f3(__ldg(d.u + t.y)) - ua);
     const float3 pc = (f3(__ldg(d.rest + t.z)) - Xa) + (f3(__ldg(d.u + t.z)) - ua);
-    return vt_depth(pa, pb, pc, n, w);
+    const float4 cw = d.contact_w ? d.contact_w[a] : make_float4(0.f, 0.f, 0.f, 0.f);
+    w = cw.w > 0.5f ? make_float3(cw.x, cw.y, cw.z) : nearest_weights(pa, pb, pc);
+    const float3 q = make_float3(w.x * pa.x + w.y * pb.x + w.z * pc.x, w.x * pa.y + w.y * pb.y + w.z * pc.y,
+                                 w.x * pa.z + w.y * pb.z + w.z * pc.z);
+    const float3 nn = cross(pb - pa, pc - pa);
+    n = rsqrtf(dot(nn, nn)) * nn;
+    return dot(q, n);
 }
 
 }  // namespace geom

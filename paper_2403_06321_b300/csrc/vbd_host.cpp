@@ -353,7 +353,8 @@ size_t carve(const vbd_ctx *c, char *base, Dev *d) {
         t.tet_fill = (int *)take(4 * nbt);
         t.cell_tet = (int *)take(4 * T);
         t.scan_tmp = (int *)take(4 * (size_t)vbd::scan_tmp_needed((int)std::max({nb, nbt, nf})));
-        t.cell_size = (unsigned *)take(8);
+        t.cell_size = (unsigned *)take(16);
+        t.contact_w = (float4 *)take(16 * N);
     }
     if (d) *d = t;
     return off;
@@ -402,6 +403,7 @@ bool params_ok(const vbd_params *p, std::string &why) {
     const float nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
     if (!(nn > 0.f) || !std::isfinite(nn)) { why = "ground_normal must be non-zero"; return false; }
     if (p->n_walls < 0 || p->n_walls > VBD_MAX_WALLS) { why = "n_walls must be 0..6"; return false; }
+    if (p->ccd_interval < 0) { why = "ccd_interval must be >= 0"; return false; }
     for (int k = 0; k < p->n_walls; ++k) {
         const float *w = p->walls[k];
         const float wn = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
@@ -499,6 +501,12 @@ int max_colour_verts(const vbd_ctx *c) {
     return mx;
 }
 
+// sizes of the self-collision tables
+vbd::CollideDims collide_dims(const vbd_ctx *c) {
+    return vbd::CollideDims{(int)(c->tris.size() / 3), (int)c->surf.size(), c->n_buckets, c->T, c->n_tet_buckets,
+                            c->params.dcd_radius};
+}
+
 // the fused loop applies to plain Gauss-Seidel passes (no self-collision, no
 // Jacobi, no explicit x^new copy-back) of a mesh whose largest colour fits
 bool fused_applies(const vbd_ctx *c) {
@@ -521,7 +529,10 @@ void enqueue_iterations(vbd_ctx *c, int first_n, int iters, cudaStream_t s) {
         vbd::launch_iterate_fused(c->d, f, c->lanes, c->fused_cluster, s);
         return;
     }
+    const bool ccd = c->params.self_collision && c->sc_carved && c->params.ccd_interval > 0;
     for (int n = first_n + 1; n <= first_n + iters; ++n) {
+        // CCD along x^t -> x^(n-1) before every ccd_interval-th iteration (Sec. 3.5)
+        if (ccd && (n - 1) % c->params.ccd_interval == 0) vbd::launch_ccd(c->d, collide_dims(c), c->n_free, s);
         if (c->params.jacobi) {
             vbd::launch_sweep(c->d, sweep_params(c, 0), c->lanes, c->block, s);
             vbd::launch_copy_back(c->d, 0, c->n_free, false, s);
@@ -1182,9 +1193,7 @@ vbd_status vbd_begin_step(vbd_ctx *ctx, float h) {
     ctx->h = h;
     ctx->iter_in_step = 0;
     if (ctx->params.self_collision && ctx->sc_carved) {  // pairs from x^t (Sec. 3.5)
-        const vbd::CollideDims cd{(int)(ctx->tris.size() / 3), (int)ctx->surf.size(), ctx->n_buckets, ctx->T,
-                                  ctx->n_tet_buckets, ctx->params.dcd_radius};
-        vbd::launch_detect(ctx->d, cd, ctx->n_free, ctx->stream);
+        vbd::launch_detect(ctx->d, collide_dims(ctx), ctx->n_free, ctx->stream);
         CU(cudaGetLastError(), "detect");
     }
     const float *g = ctx->params.gravity;

@@ -69,7 +69,9 @@ struct Dev {
     int *tet_fill;    // n_tet_buckets
     int *cell_tet;    // T
     int *scan_tmp;    // block totals of the prefix sums
-    unsigned *cell_size;  // bits (float) of the largest centroid-to-corner distance: [0] triangles, [1] tets
+    unsigned *cell_size;  // bits (float) of the largest centroid-to-corner distance: [0] triangles, [1] tets,
+                          // [2] the largest half path of a boundary vertex (CCD)
+    float4 *contact_w;    // N: a CCD pair's impact weights (.w = 1); .w = 0 for a DCD pair or none
 };
 
 // static half-spaces of the unilateral constraints (Sec. 3.4): the ground and up to six walls
@@ -156,6 +158,8 @@ cudaError_t launch_energy_static(const Dev &d, int n_free, int n_tets, int n_sur
 // d.rev_off and d.rev; counters[3] += pairs found
 int scan_tmp_needed(int n);
 void launch_detect(const Dev &d, const CollideDims &c, int n_free, cudaStream_t s);
+// vertex-triangle CCD along x^t (Dev::ut) -> the current iterate (Dev::u), Sec. 3.5
+void launch_ccd(const Dev &d, const CollideDims &c, int n_free, cudaStream_t s);
 void launch_set_log_young(const Dev &d, const float *log_young, int n_tets, cudaStream_t s);
 
 // adjoint

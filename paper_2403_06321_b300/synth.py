@@ -68,6 +68,7 @@ class SimConfig:
     self_collision: bool = False
     dcd_radius: float = 0.01
     walls: tuple = ()  # world-box half-spaces (nx, ny, nz, offset): x.n/|n| >= offset
+    ccd_interval: int = 0  # vertex-triangle CCD every n_col iterations (with self_collision)
 
 
 def world_box(lo, hi) -> list:

@@ -59,7 +59,7 @@ class vbd_params(C.Structure):
                 ("tape_steps", C.c_int32), ("mu_c", C.c_float), ("eps_v", C.c_float),
                 ("line_search", C.c_int32), ("jacobi", C.c_int32), ("self_collision", C.c_int32),
                 ("dcd_radius", C.c_float), ("scatter_sweep", C.c_int32), ("xnew_copy_back", C.c_int32),
-                ("n_walls", C.c_int32), ("walls", (C.c_float * 4) * 6)]
+                ("n_walls", C.c_int32), ("walls", (C.c_float * 4) * 6), ("ccd_interval", C.c_int32)]
 
 
 class vbd_info(C.Structure):
@@ -312,7 +312,7 @@ def vbd_destroy(ctx: int) -> None:
 def make_params(gravity=(0.0, 0.0, -9.8), ground_on=False, ground_height=0.0, ground_normal=(0.0, 0.0, 1.0),
                 k_c=1e7, cheby_rho=0.0, init_mode=3, det_eps=1e-12, k_d=0.0, tape_steps=0, mu_c=0.0,
                 eps_v=1e-3, line_search=False, jacobi=False, self_collision=False, dcd_radius=0.01,
-                scatter_sweep=False, xnew_copy_back=False, walls=(), **_ignored) -> vbd_params:
+                scatter_sweep=False, xnew_copy_back=False, walls=(), ccd_interval=0, **_ignored) -> vbd_params:
     """vbd_params from keywords.  walls: up to 6 world-box half-spaces
     (nx, ny, nz, offset), the allowed side being x.n/|n| >= offset."""
     p = vbd_default_params()
@@ -334,6 +334,7 @@ def make_params(gravity=(0.0, 0.0, -9.8), ground_on=False, ground_height=0.0, gr
     p.dcd_radius = float(dcd_radius)
     p.scatter_sweep = int(bool(scatter_sweep))
     p.xnew_copy_back = int(bool(xnew_copy_back))
+    p.ccd_interval = int(ccd_interval)
     walls = [tuple(float(v) for v in w) for w in walls]
     if len(walls) > 6 or any(len(w) != 4 for w in walls):
         raise ValueError("walls: at most 6 tuples (nx, ny, nz, offset)")

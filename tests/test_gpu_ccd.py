@@ -1,0 +1,113 @@
+"""Vertex-triangle CCD (Sec. 3.5: before every n_col-th iteration, along the
+straight paths from x^t to the current iterate) on the GPU against the FP64
+oracle: blocks thrown at a pinned block fast enough to pass its top face
+within one step, with CCD every 1, 3 or 5 iterations, alone and with
+Chebyshev, damping and friction.  The pairs of the last CCD of every step are
+compared exactly; positions within 1e-5 of the bounding-box diagonal."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2403_06321_b300 import synth, vbd
+from gpu_util import bbox_diag, params_of
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2403_06321_b300.build import build
+    build()
+    assert torch.cuda.is_available()
+
+
+def _f32(x):
+    return np.asarray(x, np.float32).astype(np.float64)
+
+
+def _scene(seed=131, origin=(0.02, 0.03, 0.13), upper_dims=(2, 2, 1)):
+    lower = synth.beam(3, 3, 1, edge=0.1, E=1e5, nu=0.4, pin_face="z-", jitter_frac=0.03, seed=seed)
+    upper = synth.beam(*upper_dims, edge=0.1, E=1e5, nu=0.4, pin_face=None, jitter_frac=0.03, seed=seed + 1,
+                       origin=origin)
+    cat, voff, _ = synth.concat([lower, upper])
+    cat.grid_ijk = None
+    return cat, voff
+
+
+def _run(orc, m, pd, v0, h, iters, steps):
+    """Step by step on both sides with the library's colouring; returns the
+    worst position error (/ bbox), the oracle's final state and the number
+    of CCD pairs after each step."""
+    model = orc.Model.from_mesh(m)
+    p = orc.Params.make(**pd)
+    sim = vbd.Sim(m, vbd.make_params(**pd))
+    counts = []
+    try:
+        colors = vbd.vbd_get_colors(sim.ctx, m.n_verts)
+        nc = int(colors.max()) + 1
+        x = _f32(m.rest)
+        v = _f32(v0)
+        vp = v.copy()
+        sim.set_state(x, v)
+        worst = 0.0
+        for step in range(steps):
+            sim.step(h, iters)
+            model.step(p, colors, nc, h, iters, x, v, vp)
+            got = vbd.vbd_get_contacts(sim.ctx, m.n_verts)
+            want = model.contacts()
+            _, is_ccd = model.contact_weights()
+            bad = np.nonzero(got != want)[0]
+            assert bad.size == 0, (step, bad, got[bad], want[bad])
+            counts.append(int(is_ccd.sum()))
+            xg, _ = sim.get_state()
+            worst = max(worst, float(np.abs(xg.cpu().numpy() - x).max()))
+        sim.sync_status()
+    finally:
+        sim.close()
+    return worst / bbox_diag(m.rest), x, v, counts
+
+
+@pytest.mark.parametrize("interval", [1, 3, 5])
+def test_fast_block_matches_oracle(orc, interval):
+    m, voff = _scene()
+    pd = params_of(synth.SimConfig(k_c=1e5, self_collision=True, dcd_radius=0.05, ccd_interval=interval))
+    v0 = np.zeros_like(m.rest)
+    v0[voff[1]:, 2] = -6.0
+    err, x, v, counts = _run(orc, m, pd, v0, 1 / 60, 30, 12)
+    print("fast block, CCD every %d: err/bbox %.2e, CCD pairs %s" % (interval, err, counts))
+    assert max(counts) >= 4  # the bottom vertices were caught by CCD
+    top = m.rest[:voff[1], 2].max()
+    assert x[voff[1]:, 2].min() > top - 0.02  # and the block stayed on top
+    assert err <= TOL
+
+
+@pytest.mark.parametrize("extra", [dict(cheby_rho=0.7), dict(k_d=1e-5), dict(mu_c=0.3, eps_v=1e-2)],
+                         ids=["chebyshev", "damping", "friction"])
+def test_oblique_throw_with_options_matches_oracle(orc, extra):
+    """A block thrown down and sideways: it lands on the pinned block and
+    slides (with friction, stops) while CCD runs every 2 iterations."""
+    m, voff = _scene(seed=141, origin=(0.03, 0.02, 0.12))
+    pd = params_of(synth.SimConfig(k_c=1e5, self_collision=True, dcd_radius=0.05, ccd_interval=2), **extra)
+    v0 = np.zeros_like(m.rest)
+    v0[voff[1]:] = (0.8, 0.3, -5.0)
+    err, x, v, counts = _run(orc, m, pd, v0, 1 / 60, 20, 12)
+    print("oblique throw %s: err/bbox %.2e, CCD pairs %s" % (extra, err, counts))
+    assert max(counts) >= 4
+    assert err <= TOL
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_seeded_throws_match_oracle(orc, seed):
+    rng = np.random.default_rng(150 + seed)
+    dims = (int(rng.integers(1, 3)), int(rng.integers(1, 3)), 1)
+    origin = (float(rng.uniform(0.01, 0.09)), float(rng.uniform(0.01, 0.09)), float(rng.uniform(0.105, 0.14)))
+    m, voff = _scene(seed=160 + seed, origin=origin, upper_dims=dims)
+    interval = int(rng.integers(1, 6))
+    pd = params_of(synth.SimConfig(k_c=1e5, self_collision=True, dcd_radius=0.05, ccd_interval=interval))
+    v0 = np.zeros_like(m.rest)
+    v0[voff[1]:] = (rng.uniform(-0.5, 0.5), rng.uniform(-0.5, 0.5), rng.uniform(-7.0, -3.0))
+    err, x, v, counts = _run(orc, m, pd, v0, 1 / 60, 25, 10)
+    print("seed %d (dims %s, CCD every %d): err/bbox %.2e, CCD pairs %s" % (seed, dims, interval, err, counts))
+    assert max(counts) >= 1
+    assert err <= TOL
