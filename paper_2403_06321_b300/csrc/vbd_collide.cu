@@ -424,6 +424,17 @@ __device__ __forceinline__ float vt_impact(float3 A0, float3 A1, float3 A2, floa
     return -1.f;
 }
 
+// whether the axis-aligned box of six points leaves out the origin
+__device__ __forceinline__ bool box_misses_origin(float3 p0, float3 p1, float3 p2, float3 p3, float3 p4, float3 p5) {
+    const float lox = fminf(fminf(fminf(p0.x, p1.x), fminf(p2.x, p3.x)), fminf(p4.x, p5.x));
+    const float hix = fmaxf(fmaxf(fmaxf(p0.x, p1.x), fmaxf(p2.x, p3.x)), fmaxf(p4.x, p5.x));
+    const float loy = fminf(fminf(fminf(p0.y, p1.y), fminf(p2.y, p3.y)), fminf(p4.y, p5.y));
+    const float hiy = fmaxf(fmaxf(fmaxf(p0.y, p1.y), fmaxf(p2.y, p3.y)), fmaxf(p4.y, p5.y));
+    const float loz = fminf(fminf(fminf(p0.z, p1.z), fminf(p2.z, p3.z)), fminf(p4.z, p5.z));
+    const float hiz = fmaxf(fmaxf(fmaxf(p0.z, p1.z), fmaxf(p2.z, p3.z)), fmaxf(p4.z, p5.z));
+    return lox > 0.f || hix < 0.f || loy > 0.f || hiy < 0.f || loz > 0.f || hiz < 0.f;
+}
+
 // relative start position and motion of corner k seen from vertex a
 __device__ __forceinline__ void rel_path(const Dev &d, int k, float3 Xa, float3 uta, float3 ua, float3 &A, float3 &B) {
     const float3 utk = f3(__ldg(d.ut + k));
@@ -458,6 +469,9 @@ __device__ __forceinline__ float earliest_impact(const Dev &d, int k, float3 Xa,
             rel_path(d, v.x, Xa, uta, ua, A0, B0);
             rel_path(d, v.y, Xa, uta, ua, A1, B1);
             rel_path(d, v.z, Xa, uta, ua, A2, B2);
+            // seen from the vertex the triangle moves inside the box of its six
+            // corner positions; if that box misses the origin there is no impact
+            if (box_misses_origin(A0, A1, A2, A0 + B0, A1 + B1, A2 + B2)) continue;
             const float ti = vt_impact(A0, A1, A2, B0, B1, B2, w);
             if (ti < 0.f) continue;
             if (pass == 0 && (best < 0.f || ti < best)) best = ti;
