@@ -531,6 +531,11 @@ def dense_adjoint(model: Model, p: Params, h: float, xs: list, dL_dxT: np.ndarra
     Returns (dL/dlogE per tet, dL/dv_0 (N,3), dL/dx_0 (N,3)).  The linear
     solve is dense LU for small meshes and a sparse direct solve (scipy) for
     larger ones (sparse=None picks by size).
+
+    With subspace constraints (Sec. 3.4) a step solves for x_{t+1} = x_t + B z
+    (B = reduced_basis()) with B^T dG/dx = 0, so lam = B (B^T H B)^-1 B^T r,
+    and since x_{t+1} follows x_t across the constrained directions,
+    xbar_t gains r - H lam (zero on the unconstrained free DoFs).
     """
     n = model.n
     fd = np.repeat(model.free, 3)
@@ -542,13 +547,22 @@ def dense_adjoint(model: Model, p: Params, h: float, xs: list, dL_dxT: np.ndarra
     T = len(xs) - 1
     if sparse is None:
         sparse = n > 400
+    Bm = model.reduced_basis() if (model.sub_dim < 3).any() else None
     for t in range(T - 1, -1, -1):
         x1 = np.asarray(xs[t + 1], np.float64).reshape(-1, 3)
         planes = model._plane_terms(p, x1)
         diag = m / h ** 2
         r = xbar + vbar / h
         lam = np.zeros(3 * n)
-        if sparse:
+        resid = np.zeros(3 * n)
+        if Bm is not None:
+            Hd = model.elastic_hess(x1) + np.diag(diag)
+            for nrm, d, act in planes:
+                for i in np.nonzero(act)[0]:
+                    Hd[3 * i:3 * i + 3, 3 * i:3 * i + 3] += p.k_c * np.outer(nrm, nrm)
+            lam = Bm @ np.linalg.solve(Bm.T @ Hd @ Bm, Bm.T @ r)
+            resid = r - Hd @ lam
+        elif sparse:
             import scipy.sparse as sp
             import scipy.sparse.linalg as spla
             H = model.elastic_hess(x1, sparse=True) + sp.diags(diag)
@@ -572,7 +586,7 @@ def dense_adjoint(model: Model, p: Params, h: float, xs: list, dL_dxT: np.ndarra
         tg = model.tet_grads(x1)  # (T, 4, 3)
         lam3 = lam.reshape(-1, 3)
         theta_bar -= np.einsum("tkr,tkr->t", tg, lam3[model.tets])
-        xbar_new = m / h ** 2 * lam - vbar / h
+        xbar_new = m / h ** 2 * lam - vbar / h + resid
         vbar = m / h * lam
         xbar = xbar_new
         xbar[~fd] = 0.0
