@@ -235,8 +235,9 @@ vbd_status vbd_set_params(vbd_ctx *ctx, const vbd_params *params);
  * before vbd_bind (the tables live in the workspace), else VBD_ERR_STATE;
  * VBD_ERR_INVALID_ARG for an index out of range, a pinned or repeated
  * vertex, a dimension other than 1 or 2, or a zero or non-finite
- * direction.  vbd_backward refuses contexts with constraints
- * (VBD_ERR_STATE). */
+ * direction.  vbd_backward covers them: their block of H lam = r is the
+ * reduced one, and their xbar keeps r - (H lam)_i, the part that follows
+ * x^t across the constrained directions. */
 vbd_status vbd_set_subspaces(vbd_ctx *ctx, int32_t n, const int32_t *vertex, const int32_t *dim,
                              const float *dir);
 

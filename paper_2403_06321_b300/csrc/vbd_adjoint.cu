@@ -185,13 +185,51 @@ __global__ void __launch_bounds__(128, 8) k_adj_sweep(Dev d, const float4 *__res
             }
         }
     }
-    const float a00 = h11 * h22 - h12 * h12, a01 = h02 * h12 - h01 * h22, a02 = h01 * h12 - h02 * h11;
-    const float a11 = h00 * h22 - h02 * h02, a12 = h01 * h02 - h00 * h12, a22 = h00 * h11 - h01 * h01;
-    const float det = h00 * a00 + h01 * a01 + h02 * a02;
-    const float inv = 1.f / det;
-    const float l0 = (a00 * b0 + a01 * b1 + a02 * b2) * inv;
-    const float l1 = (a01 * b0 + a11 * b1 + a12 * b2) * inv;
-    const float l2 = (a02 * b0 + a12 * b1 + a22 * b2) * inv;
+    const int sub = p.n_sub > 0 ? d.sub_id[vi] : -1;
+    if (p.adj_residual) {
+        // after the sweeps: r - (H lam)_i = b - H_ii lam_i of a constrained vertex,
+        // the part of xbar that follows x_t across its constrained directions
+        if (sub >= 0) {
+            const float4 l = d.lam[vi];
+            d.rhs[vi] = make_float4(b0 - (h00 * l.x + h01 * l.y + h02 * l.z), b1 - (h01 * l.x + h11 * l.y + h12 * l.z),
+                                    b2 - (h02 * l.x + h12 * l.y + h22 * l.z), 0.f);
+        }
+        return;
+    }
+    float l0, l1, l2;
+    if (sub >= 0) {
+        // reduced block (Sec. 3.4): lam_i = Q (Q^T H_ii Q)^-1 Q^T b
+        const float4 qa = d.sub_q[2 * sub], qb = d.sub_q[2 * sub + 1];
+        const float ha0 = h00 * qa.x + h01 * qa.y + h02 * qa.z;
+        const float ha1 = h01 * qa.x + h11 * qa.y + h12 * qa.z;
+        const float ha2 = h02 * qa.x + h12 * qa.y + h22 * qa.z;
+        const float A00 = qa.x * ha0 + qa.y * ha1 + qa.z * ha2;
+        const float c0 = qa.x * b0 + qa.y * b1 + qa.z * b2;
+        float z0, z1 = 0.f;
+        if (qa.w < 1.5f) {
+            z0 = c0 / A00;
+        } else {
+            const float A01 = qb.x * ha0 + qb.y * ha1 + qb.z * ha2;
+            const float A11 = qb.x * (h00 * qb.x + h01 * qb.y + h02 * qb.z) +
+                              qb.y * (h01 * qb.x + h11 * qb.y + h12 * qb.z) +
+                              qb.z * (h02 * qb.x + h12 * qb.y + h22 * qb.z);
+            const float c1 = qb.x * b0 + qb.y * b1 + qb.z * b2;
+            const float inv2 = 1.f / (A00 * A11 - A01 * A01);
+            z0 = (A11 * c0 - A01 * c1) * inv2;
+            z1 = (A00 * c1 - A01 * c0) * inv2;
+        }
+        l0 = qa.x * z0 + qb.x * z1;
+        l1 = qa.y * z0 + qb.y * z1;
+        l2 = qa.z * z0 + qb.z * z1;
+    } else {
+        const float a00 = h11 * h22 - h12 * h12, a01 = h02 * h12 - h01 * h22, a02 = h01 * h12 - h02 * h11;
+        const float a11 = h00 * h22 - h02 * h02, a12 = h01 * h02 - h00 * h12, a22 = h00 * h11 - h01 * h01;
+        const float det = h00 * a00 + h01 * a01 + h02 * a02;
+        const float inv = 1.f / det;
+        l0 = (a00 * b0 + a01 * b1 + a02 * b2) * inv;
+        l1 = (a01 * b0 + a11 * b1 + a12 * b2) * inv;
+        l2 = (a02 * b0 + a12 * b1 + a22 * b2) * inv;
+    }
     if (!(isfinite(l0) && isfinite(l1) && isfinite(l2))) {
         atomicAdd(d.counters + 0, 1ull);
         return;
@@ -218,8 +256,9 @@ __global__ void k_adj_rhs(Dev d, int n, int n_free, float inv_h) {
     d.rhs[i] = make_float4(xb.x + vb.x * inv_h, xb.y + vb.y * inv_h, xb.z + vb.z * inv_h, 0.f);
 }
 
-// xbar_t = M/h^2 lam - vbar/h, vbar_t = M/h lam (free vertices; pinned 0)
-__global__ void k_adj_post_verts(Dev d, int n, int n_free, float h) {
+// xbar_t = M/h^2 lam - vbar/h (+ r - (H lam)_i, stored in rhs, for a
+// subspace-constrained vertex), vbar_t = M/h lam (free vertices; pinned 0)
+__global__ void k_adj_post_verts(Dev d, int n, int n_free, float h, int has_sub) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (i >= n_free) {
@@ -230,7 +269,12 @@ __global__ void k_adj_post_verts(Dev d, int n, int n_free, float h) {
     const float m = d.mass[i];
     const float4 l = d.lam[i], vb = d.vbar[i];
     const float a = m / (h * h), b = m / h, c = 1.f / h;
-    d.xbar[i] = make_float4(a * l.x - c * vb.x, a * l.y - c * vb.y, a * l.z - c * vb.z, 0.f);
+    float4 xb = make_float4(a * l.x - c * vb.x, a * l.y - c * vb.y, a * l.z - c * vb.z, 0.f);
+    if (has_sub && d.sub_id[i] >= 0) {
+        const float4 e = d.rhs[i];
+        xb.x += e.x; xb.y += e.y; xb.z += e.z;
+    }
+    d.xbar[i] = xb;
     d.vbar[i] = make_float4(b * l.x, b * l.y, b * l.z, 0.f);
 }
 
@@ -299,11 +343,11 @@ void launch_adj_sweep(const Dev &d, const float4 *xs, const SweepParams &p, int 
     }
 }
 
-void launch_adj_post(const Dev &d, const float4 *xs, int n, int n_free, int n_tets, float h,
+void launch_adj_post(const Dev &d, const float4 *xs, int n, int n_free, int n_tets, float h, bool has_sub,
                      cudaStream_t s) {
     // tets first: they read lam, which the vertex pass does not change
     k_adj_post_tets<<<blocks_for(n_tets, 256), 256, 0, s>>>(d, xs, n_tets);
-    k_adj_post_verts<<<blocks_for(n, 256), 256, 0, s>>>(d, n, n_free, h);
+    k_adj_post_verts<<<blocks_for(n, 256), 256, 0, s>>>(d, n, n_free, h, has_sub ? 1 : 0);
 }
 
 void launch_adj_out(const Dev &d, float *dL_dlogE, float *dL_dv0, int n, int n_tets, cudaStream_t s) {

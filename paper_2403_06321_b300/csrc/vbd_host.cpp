@@ -1368,8 +1368,6 @@ vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, floa
     if (ctx->tape_len < 1) return fail(ctx, VBD_ERR_NO_TAPE, "no recorded steps (tape_steps = 0?)");
     if (ctx->params.k_d != 0.f || ctx->params.mu_c != 0.f || ctx->params.self_collision)
         return fail(ctx, VBD_ERR_INVALID_ARG, "the adjoint needs k_d = 0, mu_c = 0 and no self-collision");
-    if (!ctx->sub_vertex.empty())
-        return fail(ctx, VBD_ERR_STATE, "the adjoint does not cover subspace-constrained vertices");
     if (!is_device_ptr(dL_dxT) || (dL_dlogE && !is_device_ptr(dL_dlogE)) || (dL_dv0 && !is_device_ptr(dL_dv0)))
         return fail(ctx, VBD_ERR_INVALID_ARG, "vbd_backward takes device pointers");
     const Dev &d = ctx->d;
@@ -1386,7 +1384,14 @@ vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, floa
         for (int it = 0; it < adj_iters; ++it)
             for (int col = 0; col < ctx->n_colors; ++col)
                 vbd::launch_adj_sweep(d, xs, sweep_params(ctx, col), kAdjLanes, kAdjBlock, s);
-        vbd::launch_adj_post(d, xs, N, ctx->n_free, ctx->T, h, s);
+        const bool has_sub = !ctx->sub_vertex.empty();
+        if (has_sub)  // r - (H lam)_i of the constrained vertices, for xbar
+            for (int col = 0; col < ctx->n_colors; ++col) {
+                vbd::SweepParams rp = sweep_params(ctx, col);
+                rp.adj_residual = 1;
+                vbd::launch_adj_sweep(d, xs, rp, kAdjLanes, kAdjBlock, s);
+            }
+        vbd::launch_adj_post(d, xs, N, ctx->n_free, ctx->T, h, has_sub, s);
     }
     ctx->h = h_saved;
     vbd::launch_adj_out(d, dL_dlogE, dL_dv0, N, ctx->T, s);

@@ -82,6 +82,7 @@ struct SweepParams {
     float4 planes[kMaxPlanes];  // xyz unit normal, w offset: the allowed side is x.n >= w
     int n_planes;     // planes in use (ground first when on, then the walls)
     int n_sub;        // subspace-constrained vertices (Sec. 3.4); > 0 reads Dev::sub_id
+    int adj_residual; // adjoint only: store r - (H lam)_i of constrained vertices in Dev::rhs, lam unchanged
     float kc;         // collision stiffness (Eq. 12)
     float det_eps;
     float kd_over_h;  // Rayleigh damping k_d / h
@@ -166,7 +167,7 @@ void launch_set_log_young(const Dev &d, const float *log_young, int n_tets, cuda
 void launch_adj_rhs(const Dev &d, int n, int n_free, float inv_h, cudaStream_t s);
 void launch_adj_sweep(const Dev &d, const float4 *xs, const SweepParams &p, int lanes, int block,
                       cudaStream_t s);
-void launch_adj_post(const Dev &d, const float4 *xs, int n, int n_free, int n_tets, float h,
+void launch_adj_post(const Dev &d, const float4 *xs, int n, int n_free, int n_tets, float h, bool has_sub,
                      cudaStream_t s);
 void launch_adj_seed(const Dev &d, const float *dL_dx, int n, cudaStream_t s);
 void launch_adj_out(const Dev &d, float *dL_dlogE, float *dL_dv0, int n, int n_tets,
