@@ -133,6 +133,11 @@ def lib():
             "orc_ccd": (C.c_int, [vp, _dp, _dp]),
             "orc_cubic_first_root": (C.c_double, [_dp, C.c_double]),
             "orc_model_contact_weights": (None, [vp, _dp, _up]),
+            "orc_ee_impact": (C.c_double, [_dp, _dp, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
+                                           C.POINTER(C.c_double)]),
+            "orc_model_n_edges": (C.c_int, [vp]),
+            "orc_model_edges": (None, [vp, _ip]),
+            "orc_model_ee_pairs": (C.c_int, [vp, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
             "orc_dcd_vertex": (C.c_int, [vp, C.POINTER(Params), _dp, C.c_int]),
             "orc_dcd": (None, [vp, C.POINTER(Params), _dp]),
             "orc_model_contacts": (None, [vp, _ip]),
@@ -216,6 +221,14 @@ def tet_hess_block(x, B, V, mu, lam, k, l) -> np.ndarray:
     H = np.zeros(9)
     lib().orc_tet_hess_block(_d(x, 12), _d(B, 9), V, mu, lam, k, l, H)
     return H.reshape(3, 3)
+
+
+def ee_impact(x0, x1, p0, p1, q0, q1):
+    """(time of impact or -1, s, u) of edges (p0, p1), (q0, q1) moving linearly."""
+    s, u = C.c_double(-1.0), C.c_double(-1.0)
+    t = lib().orc_ee_impact(_d(x0).reshape(-1), _d(x1).reshape(-1), int(p0), int(p1), int(q0), int(q1),
+                            C.byref(s), C.byref(u))
+    return float(t), float(s.value), float(u.value)
 
 
 def cubic_first_root(c, t_min=0.0) -> float:
@@ -422,6 +435,28 @@ class Model:
         w = np.zeros(3)
         T = lib().orc_ccd_vertex(self._h, _d(x0).reshape(-1), _d(x1).reshape(-1), int(a), C.byref(toi), w)
         return int(T), float(toi.value), w
+
+    def edges(self) -> np.ndarray:
+        e = np.zeros(2 * lib().orc_model_n_edges(self._h), np.int32)
+        lib().orc_model_edges(self._h, e)
+        return e.reshape(-1, 2)
+
+    def ee_pairs(self):
+        """Edge-edge pairs, by holding edge: (partner per edge (-1 = none),
+        carried flag, (s, u) per edge, normal per edge)."""
+        ne = lib().orc_model_n_edges(self._h)
+        partner = np.zeros(ne, np.int32)
+        carried = np.zeros(ne, np.uint8)
+        su = np.zeros(2 * ne)
+        n = np.zeros(3 * ne)
+        lib().orc_model_ee_pairs(self._h, partner.ctypes.data, carried.ctypes.data, su.ctypes.data, n.ctypes.data)
+        return partner, carried.astype(bool), su.reshape(-1, 2), n.reshape(-1, 3)
+
+    def ee_pair_list(self):
+        """[(v0, v1, v2, v3), (s, u), normal] for each current edge-edge pair."""
+        partner, _, su, n = self.ee_pairs()
+        e = self.edges()
+        return [((*e[k], *e[partner[k]]), su[k], n[k]) for k in np.nonzero(partner >= 0)[0]]
 
     def ccd(self, x0, x1) -> int:
         """CCD of every vertex without a step-start pair; returns the pair count."""

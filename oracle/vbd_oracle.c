@@ -62,8 +62,23 @@
  *    tied; the lowest triangle index wins).  The pair keeps the impact
  *    point's barycentric weights w (the contact point is sum w_k x_k) and
  *    uses the triangle's current normal, with the penalty and friction of
- *    the DCD pairs; each CCD replaces the previous CCD pairs.  Edge-edge
- *    contacts are not detected.
+ *    the DCD pairs; each CCD replaces the previous CCD pairs.
+ *  - Edge-edge CCD (Sec. 3.5), in the same calls: boundary edges (edges of
+ *    boundary triangles) are swept against each other (candidates: none of
+ *    the other edge's vertices shares a tet with one of its own); the
+ *    impact is the first root of the coplanarity cubic at which the two
+ *    segments cross.  Each edge keeps the edge it hits first (1e-5 ties, the
+ *    lowest index); each hit is one pair, counted once.  The contact points
+ *    x_a, x_b keep their impact parameters, and the normal n is the unit
+ *    vector of x_b - x_a at the detection positions (the current iterate,
+ *    where the edges have crossed), frozen for the pair's life (the paper
+ *    takes n along x_b - x_a; freezing it makes d = (x_b - x_a).n change
+ *    sign when the edges are back across).  d = max(0, (x_b - x_a).n) with
+ *    the penalty of Eq. 12; no friction on these pairs.  Neither CCD (from
+ *    x^t) nor the vertex DCD can see two edges that are already crossed, so
+ *    a pair still penetrated (d > 0) at the next step start is carried into
+ *    that step, as the DCD's vertex pairs are; a carried pair ends at the
+ *    first step start where d <= 0.
  *  - Ground friction (Eqs. 13-16): the ground is static, so the relative
  *    displacement is delta = x_i - x_i^t; u = its tangential part.  lambda
  *    is read as the normal-force magnitude k_c d >= 0 (as printed, the
@@ -96,6 +111,13 @@ struct orc_model {
     int *contact;        /* N: triangle hit by the vertex (DCD at x^t), or -1 */
     double *contact_w;   /* 3N: impact weights of a CCD pair (fixed for the pair's life) */
     unsigned char *contact_ccd; /* N: 1 = the vertex's pair came from CCD, 0 = from the DCD */
+    int n_edges;         /* boundary edges (edges of boundary triangles), ascending (lo, hi) */
+    int *edges;          /* 2 * n_edges */
+    /* edge-edge pairs, held by the edge that found them (Sec. 3.5 CCD) */
+    int *ee_partner;     /* n_edges: the other edge of the pair this edge holds, or -1 */
+    unsigned char *ee_carried; /* n_edges: 1 = the pair was still penetrated at the step start */
+    double *ee_su;       /* 2 per edge: impact parameters s on this edge, u on the partner */
+    double *ee_n;        /* 3 per edge: contact normal, frozen at detection */
     int *sub_dim;        /* N: L of the vertex's subspace constraint (Sec. 3.4), 3 = none */
     double *sub_basis;   /* 9N: orthonormal basis q_1..q_L of that subspace, 3 doubles each */
 };
@@ -274,6 +296,12 @@ void orc_tet_hess(const double x[12], const double B[9], double V, double mu, do
 static int cmp_int(const void *a, const void *b) {
     int x = *(const int *)a, y = *(const int *)b;
     return (x > y) - (x < y);
+}
+
+static int cmp_edge(const void *pa, const void *pb) {
+    const int *a = (const int *)pa, *b = (const int *)pb;
+    if (a[0] != b[0]) return (a[0] > b[0]) - (a[0] < b[0]);
+    return (a[1] > b[1]) - (a[1] < b[1]);
 }
 
 static int cmp_face(const void *pa, const void *pb) {
@@ -461,6 +489,29 @@ orc_model *orc_model_new(int n, int t, const double *rest, const int *tets,
         for (int i = 0; i < n; ++i) m->contact[i] = -1;
         m->contact_w = (double *)calloc(3 * (size_t)n + 1, sizeof(double));
         m->contact_ccd = (unsigned char *)calloc((size_t)n + 1, 1);
+        /* boundary edges: the sorted vertex pairs of the boundary triangles, once each */
+        int *ed = (int *)malloc(sizeof(int) * 6 * (size_t)m->n_tris + 2);
+        for (int T = 0; T < m->n_tris; ++T)
+            for (int k = 0; k < 3; ++k) {
+                int a = m->tris[3 * T + k], b = m->tris[3 * T + (k + 1) % 3];
+                ed[6 * T + 2 * k] = a < b ? a : b;
+                ed[6 * T + 2 * k + 1] = a < b ? b : a;
+            }
+        qsort(ed, 3 * (size_t)m->n_tris, 2 * sizeof(int), cmp_edge);
+        m->edges = (int *)malloc(sizeof(int) * 6 * (size_t)m->n_tris + 2);
+        m->n_edges = 0;
+        for (int k = 0; k < 3 * m->n_tris; ++k)
+            if (k == 0 || cmp_edge(ed + 2 * k, ed + 2 * (k - 1)) != 0) {
+                m->edges[2 * m->n_edges] = ed[2 * k];
+                m->edges[2 * m->n_edges + 1] = ed[2 * k + 1];
+                m->n_edges++;
+            }
+        free(ed);
+        m->ee_partner = (int *)malloc(sizeof(int) * (size_t)m->n_edges + 1);
+        m->ee_carried = (unsigned char *)calloc((size_t)m->n_edges + 1, 1);
+        for (int e = 0; e < m->n_edges; ++e) m->ee_partner[e] = -1;
+        m->ee_su = (double *)malloc(sizeof(double) * 2 * (size_t)m->n_edges + 2);
+        m->ee_n = (double *)malloc(sizeof(double) * 3 * (size_t)m->n_edges + 3);
     }
     m->sub_dim = (int *)malloc(sizeof(int) * (size_t)n + 1);
     m->sub_basis = (double *)calloc(9 * (size_t)n + 1, sizeof(double));
@@ -540,6 +591,7 @@ void orc_model_free(orc_model *m) {
     free(m->tets); free(m->B); free(m->V); free(m->mu); free(m->lam); free(m->poisson);
     free(m->mass); free(m->pinned); free(m->inc_off); free(m->inc_tet); free(m->inc_loc);
     free(m->tris); free(m->on_surface); free(m->contact); free(m->contact_w); free(m->contact_ccd);
+    free(m->edges); free(m->ee_partner); free(m->ee_carried); free(m->ee_su); free(m->ee_n);
     free(m->sub_dim); free(m->sub_basis);
     free(m);
 }
@@ -695,7 +747,19 @@ int orc_dcd_vertex(const orc_model *m, const orc_params *p, const double *x, int
     return -1;
 }
 
+static double ee_depth(const orc_model *m, int e, const double *x, int v[4], double c[4]);
+
 void orc_dcd(orc_model *m, const orc_params *p, const double *x) {
+    /* edge-edge pairs (found by CCD) that are still penetrated at x^t are
+     * carried into the step; the others end */
+    for (int e = 0; e < m->n_edges; ++e) {
+        m->ee_carried[e] = 0;
+        if (m->ee_partner[e] < 0) continue;
+        int v[4];
+        double c[4];
+        if (ee_depth(m, e, x, v, c) > 0.0) m->ee_carried[e] = 1;
+        else m->ee_partner[e] = -1;
+    }
     for (int a = 0; a < m->n_verts; ++a) {
         m->contact[a] = orc_dcd_vertex(m, p, x, a);
         m->contact_ccd[a] = 0;
@@ -832,7 +896,140 @@ int orc_ccd_vertex(const orc_model *m, const double *x0, const double *x1, int a
     return best_T;
 }
 
+/* Time of impact of edges (p0, p1) and (q0, q1) moving linearly (Sec. 3.5
+ * CCD): with A_k + t B_k the positions of p1, q0, q1 relative to p0, the
+ * four points are coplanar where the cubic (p1 - p0) . ((q0 - p0) x
+ * (q1 - p0)) vanishes; its roots are visited in order and the first at
+ * which the segments cross (in their common plane, p0 + s (p1 - p0) =
+ * q0 + u (q1 - q0) with s, u in [0, 1]) is the impact.  Parallel segments
+ * count as no crossing.  Returns t or -1; s, u receive the parameters. */
+double orc_ee_impact(const double *x0, const double *x1, int p0, int p1, int q0, int q1, double *s_out,
+                     double *u_out) {
+    const int id[3] = {p1, q0, q1};
+    double A[3][3], B[3][3];
+    for (int k = 0; k < 3; ++k)
+        for (int r = 0; r < 3; ++r) {
+            A[k][r] = x0[3 * id[k] + r] - x0[3 * p0 + r];
+            B[k][r] = (x1[3 * id[k] + r] - x1[3 * p0 + r]) - A[k][r];
+        }
+    double t23[3], c[4], tmp[3];
+    cross3(A[1], A[2], t23);
+    c[0] = dot3(A[0], t23);
+    c[1] = dot3(B[0], t23);
+    cross3(B[1], A[2], tmp); c[1] += dot3(A[0], tmp);
+    cross3(A[1], B[2], tmp); c[1] += dot3(A[0], tmp);
+    cross3(B[1], A[2], tmp); c[2] = dot3(B[0], tmp);
+    cross3(A[1], B[2], tmp); c[2] += dot3(B[0], tmp);
+    cross3(B[1], B[2], tmp); c[2] += dot3(A[0], tmp);
+    c[3] = dot3(B[0], tmp);
+    double t0 = 0.0;
+    for (int rep = 0; rep < 3; ++rep) {
+        double t = orc_cubic_first_root(c, t0);
+        if (t < 0.0) return -1.0;
+        double e[3], w[3], g[3], n[3], wg[3], we[3];
+        for (int r = 0; r < 3; ++r) {
+            e[r] = A[0][r] + t * B[0][r];               /* p1 - p0 */
+            w[r] = A[1][r] + t * B[1][r];               /* q0 - p0 */
+            g[r] = (A[2][r] + t * B[2][r]) - w[r];      /* q1 - q0 */
+        }
+        cross3(e, g, n);
+        double nn = dot3(n, n);
+        if (nn > 0.0) {
+            cross3(w, g, wg);
+            cross3(w, e, we);
+            double s = dot3(wg, n) / nn, u = dot3(we, n) / nn;
+            if (s >= 0.0 && s <= 1.0 && u >= 0.0 && u <= 1.0) {
+                *s_out = s;
+                *u_out = u;
+                return t;
+            }
+        }
+        t0 = t + 1e-12;
+        if (t0 >= 1.0) return -1.0;
+    }
+    return -1.0;
+}
+
+/* whether vertex q shares a tet with vertex a (or is a) */
+static int shares_tet(const orc_model *m, int a, int q) {
+    for (int s = m->inc_off[a]; s < m->inc_off[a + 1]; ++s)
+        for (int k = 0; k < 4; ++k)
+            if (m->tets[4 * (size_t)m->inc_tet[s] + k] == q) return 1;
+    return a == q;
+}
+
+/* Edge-edge CCD: each boundary edge that holds no carried pair takes the
+ * boundary edge it hits first (ties within 1e-5 in time: the lowest index),
+ * among edges none of whose vertices shares a tet with one of its own.  The
+ * pair is held by the finding edge, unless the partner found this edge too
+ * with a lower index (it then holds it) or the partner already holds the
+ * same pair as a carried one.  The contact points keep their impact
+ * parameters; the normal is that of x_b - x_a at x1, frozen for the pair's
+ * life (a pair whose points coincide there is dropped). */
+static void ee_ccd(orc_model *m, const double *x0, const double *x1) {
+    int *found = (int *)malloc(sizeof(int) * (size_t)m->n_edges + 1);
+    double *su = (double *)malloc(sizeof(double) * 2 * (size_t)m->n_edges + 2);
+    for (int e = 0; e < m->n_edges; ++e) {
+        found[e] = -1;
+        if (m->ee_carried[e]) continue;
+        const int p0 = m->edges[2 * e], p1 = m->edges[2 * e + 1];
+        double best = 2.0;
+        for (int f = 0; f < m->n_edges; ++f) {
+            const int q0 = m->edges[2 * f], q1 = m->edges[2 * f + 1];
+            if (shares_tet(m, p0, q0) || shares_tet(m, p0, q1) || shares_tet(m, p1, q0) || shares_tet(m, p1, q1))
+                continue;
+            double s, u;
+            double t = orc_ee_impact(x0, x1, p0, p1, q0, q1, &s, &u);
+            if (t >= 0.0 && t < best - 1e-5) {
+                best = t;
+                found[e] = f;
+                su[2 * e] = s;
+                su[2 * e + 1] = u;
+            }
+        }
+    }
+    for (int e = 0; e < m->n_edges; ++e) {
+        if (m->ee_carried[e]) continue;
+        const int f = found[e];
+        m->ee_partner[e] = -1;
+        if (f < 0) continue;
+        if (found[f] == e && f < e) continue;                   /* held by f */
+        if (m->ee_carried[f] && m->ee_partner[f] == e) continue;  /* already carried by f */
+        const int v[4] = {m->edges[2 * e], m->edges[2 * e + 1], m->edges[2 * f], m->edges[2 * f + 1]};
+        const double s = su[2 * e], u = su[2 * e + 1];
+        double dlt[3];
+        for (int r = 0; r < 3; ++r)
+            dlt[r] = ((1.0 - u) * x1[3 * v[2] + r] + u * x1[3 * v[3] + r]) -
+                     ((1.0 - s) * x1[3 * v[0] + r] + s * x1[3 * v[1] + r]);
+        double len = sqrt(dot3(dlt, dlt));
+        if (!(len > 0.0)) continue;
+        m->ee_partner[e] = f;
+        m->ee_su[2 * (size_t)e] = s;
+        m->ee_su[2 * (size_t)e + 1] = u;
+        for (int r = 0; r < 3; ++r) m->ee_n[3 * (size_t)e + r] = dlt[r] / len;
+    }
+    free(found);
+    free(su);
+}
+
+/* Depth of the edge-edge pair held by edge e at positions x, its four
+ * vertices v and their derivative weights: d = (x_b - x_a) . n with
+ * x_a = (1 - s) p0 + s p1 on edge e, x_b = (1 - u) q0 + u q1 on the partner
+ * and n frozen, so dd/dx_v = c_v n with c = (-(1 - s), -s, 1 - u, u). */
+static double ee_depth(const orc_model *m, int e, const double *x, int v[4], double c[4]) {
+    const int f = m->ee_partner[e];
+    v[0] = m->edges[2 * e]; v[1] = m->edges[2 * e + 1];
+    v[2] = m->edges[2 * f]; v[3] = m->edges[2 * f + 1];
+    const double s = m->ee_su[2 * (size_t)e], u = m->ee_su[2 * (size_t)e + 1];
+    c[0] = -(1.0 - s); c[1] = -s; c[2] = 1.0 - u; c[3] = u;
+    double d = 0.0;
+    for (int j = 0; j < 4; ++j)
+        for (int r = 0; r < 3; ++r) d += c[j] * x[3 * v[j] + r] * m->ee_n[3 * (size_t)e + r];
+    return d;
+}
+
 int orc_ccd(orc_model *m, const double *x0, const double *x1) {
+    ee_ccd(m, x0, x1);
     int n = 0;
     for (int a = 0; a < m->n_verts; ++a) {
         if (m->contact[a] >= 0 && !m->contact_ccd[a]) continue;  /* keeps its step-start pair */
@@ -977,6 +1174,15 @@ double orc_local_energy(const orc_model *m, const orc_params *p, double h, int i
             double d = contact_depth(m, a, x, nn, w);
             if (d > 0.0) G += 0.5 * p->k_c * d * d;
         }
+    if (p->self_collision)
+        for (int e = 0; e < m->n_edges; ++e) {
+            if (m->ee_partner[e] < 0) continue;
+            int v[4];
+            double cw[4];
+            double d = ee_depth(m, e, x, v, cw);
+            if (v[0] != i && v[1] != i && v[2] != i && v[3] != i) continue;
+            if (d > 0.0) G += 0.5 * p->k_c * d * d;
+        }
     return G;
 }
 
@@ -1044,6 +1250,22 @@ int orc_self_contact(const orc_model *m, const orc_params *p, double h, int i, c
                 for (int c = 0; c < 3; ++c) H[r * 3 + c] += p->k_c * wk * wk * nn[r] * nn[c];
             }
             if (friction) pair_friction(m, p, h, a, v, w, nn, p->k_c * d, x, xt, -wk, f, H);
+        }
+    }
+    for (int e = 0; e < m->n_edges; ++e) {  /* edge-edge pairs (Sec. 3.5), no friction */
+        if (m->ee_partner[e] < 0) continue;
+        int v[4];
+        double c[4];
+        double d = ee_depth(m, e, x, v, c);
+        int j = (v[0] == i) ? 0 : (v[1] == i) ? 1 : (v[2] == i) ? 2 : (v[3] == i) ? 3 : -1;
+        if (j < 0) continue;
+        if (d > 0.0) {
+            hit = 1;
+            const double *n = m->ee_n + 3 * (size_t)e;
+            for (int r = 0; r < 3; ++r) {
+                f[r] -= p->k_c * d * c[j] * n[r];
+                for (int q = 0; q < 3; ++q) H[r * 3 + q] += p->k_c * c[j] * c[j] * n[r] * n[q];
+            }
         }
     }
     return hit;
@@ -1278,14 +1500,40 @@ double orc_energy_G(const orc_model *m, const orc_params *p, double h,
         gather_tet(m, j, x, xs);
         G += orc_tet_energy(xs, m->B + 9 * (size_t)j, m->V[j], m->mu[j], m->lam[j]);
     }
-    if (p->self_collision)
+    if (p->self_collision) {
         for (int a = 0; a < m->n_verts; ++a)
             if (m->contact[a] >= 0) {
                 double nn[3], w[3];
                 double d = contact_depth(m, a, x, nn, w);
                 if (d > 0.0) G += 0.5 * p->k_c * d * d;
             }
+        for (int e = 0; e < m->n_edges; ++e) {
+            if (m->ee_partner[e] < 0) continue;
+            int v[4];
+            double cw[4];
+            double d = ee_depth(m, e, x, v, cw);
+            if (d > 0.0) G += 0.5 * p->k_c * d * d;
+        }
+    }
     return G;
+}
+
+int orc_model_n_edges(const orc_model *m) { return m->n_edges; }
+
+void orc_model_edges(const orc_model *m, int *edges) {
+    memcpy(edges, m->edges, sizeof(int) * 2 * (size_t)m->n_edges);
+}
+
+/* the current edge-edge pairs, by holding edge: partner (or -1), carried
+ * flag, (s, u) and the normal per edge; returns the number of pairs */
+int orc_model_ee_pairs(const orc_model *m, int *partner, unsigned char *carried, double *su, double *n) {
+    int k = 0;
+    for (int e = 0; e < m->n_edges; ++e) k += m->ee_partner[e] >= 0;
+    if (partner) memcpy(partner, m->ee_partner, sizeof(int) * (size_t)m->n_edges);
+    if (carried) memcpy(carried, m->ee_carried, (size_t)m->n_edges);
+    if (su) memcpy(su, m->ee_su, sizeof(double) * 2 * (size_t)m->n_edges);
+    if (n) memcpy(n, m->ee_n, sizeof(double) * 3 * (size_t)m->n_edges);
+    return k;
 }
 
 void orc_elastic_grad(const orc_model *m, const double *x, double *grad) {

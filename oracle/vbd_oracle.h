@@ -107,6 +107,11 @@ int orc_ccd(orc_model *m, const double *x0, const double *x1);
  * whose point passes `accept`; -1 if none (exposed for the pins). */
 double orc_cubic_first_root(const double c[4], double t_min);
 void orc_model_contact_weights(const orc_model *m, double *w, unsigned char *is_ccd);
+/* edge-edge CCD of one edge pair; returns the time of impact or -1 */
+double orc_ee_impact(const double *x0, const double *x1, int p0, int p1, int q0, int q1, double *s, double *u);
+int orc_model_n_edges(const orc_model *m);
+void orc_model_edges(const orc_model *m, int *edges);
+int orc_model_ee_pairs(const orc_model *m, int *partner, unsigned char *carried, double *su, double *n);
 void orc_model_contacts(const orc_model *m, int *contact);
 int orc_self_contact(const orc_model *m, const orc_params *p, double h, int i, const double *x,
                      const double *xt, double f[3], double H[9]);

@@ -243,3 +243,142 @@ def test_ccd_keeps_step_start_pairs_and_replaces_its_own(orc):
     assert T >= 0
     model.ccd(xin, x0)
     assert model.contacts()[4] == T and not model.contact_weights()[1][4]
+
+
+# ---- edge-edge CCD ---------------------------------------------------------
+
+def test_edge_edge_impact_closed_form(orc):
+    """A static edge along x and an edge along y falling through it: they
+    cross when the falling edge reaches z = 0, at the parameters of the
+    crossing point on each edge; passing beyond an end or moving in parallel
+    is no impact."""
+    x0 = np.array([[-1, 0.1, 0], [1, 0.1, 0], [0.3, -1, 0.5], [0.3, 1, 0.5]], float)
+    x1 = x0.copy()
+    x1[2:, 2] = -0.5
+    t, s, u = orc.ee_impact(x0, x1, 0, 1, 2, 3)
+    assert t == pytest.approx(0.5, abs=1e-12)
+    assert s == pytest.approx(0.65, abs=1e-12) and u == pytest.approx(0.55, abs=1e-12)
+    x0b, x1b = x0.copy(), x1.copy()
+    x0b[2:, 0] = x1b[2:, 0] = 1.5  # beyond the static edge's end
+    assert orc.ee_impact(x0b, x1b, 0, 1, 2, 3)[0] == -1.0
+    x0c, x1c = x0.copy(), x1.copy()
+    x0c[2:] = [[-1, 0.5, 0.5], [1, 0.5, 0.5]]  # parallel to the static edge
+    x1c[2:] = [[-1, 0.5, -0.5], [1, 0.5, -0.5]]
+    assert orc.ee_impact(x0c, x1c, 0, 1, 2, 3)[0] == -1.0
+
+
+def test_edge_edge_impact_against_dense_sampling(orc):
+    """Random rotating, translating, stretching edge pairs: the first time
+    the four points become coplanar with the segments crossing, from a
+    20,001-sample scan of the coplanarity sign, matches the root finder
+    (crossings within 1e-3 of a segment end are left out)."""
+    rng = np.random.default_rng(171)
+    hits = 0
+    for trial in range(80):
+        x0 = rng.normal(0, 1, (4, 3))
+        x1 = x0 + rng.normal(0, 1, (4, 3))
+        t, s, u = orc.ee_impact(x0, x1, 0, 1, 2, 3)
+        ts = np.linspace(0, 1, 20001)
+        P = [(1 - ts)[:, None] * x0[k] + ts[:, None] * x1[k] for k in range(4)]
+        f = np.einsum("ij,ij->i", P[1] - P[0], np.cross(P[2] - P[0], P[3] - P[0]))
+        sc = np.nonzero(np.sign(f[:-1]) != np.sign(f[1:]))[0]
+        want = None
+        for i in sc:
+            tc = ts[i] - f[i] * (ts[i + 1] - ts[i]) / (f[i + 1] - f[i])
+            p0, p1, q0, q1 = [(1 - tc) * x0[k] + tc * x1[k] for k in range(4)]
+            e, g, w = p1 - p0, q1 - q0, q0 - p0
+            n = np.cross(e, g)
+            ss, uu = np.cross(w, g) @ n / (n @ n), np.cross(w, e) @ n / (n @ n)
+            if 0 <= ss <= 1 and 0 <= uu <= 1:
+                want = (tc, ss, uu)
+                break
+        if want is None:
+            assert t == -1.0, trial
+            continue
+        if min(want[1], 1 - want[1], want[2], 1 - want[2]) < 1e-3:
+            continue
+        hits += 1
+        assert t == pytest.approx(want[0], abs=1e-6), trial
+        assert s == pytest.approx(want[1], abs=1e-4) and u == pytest.approx(want[2], abs=1e-4)
+    assert hits >= 10
+
+
+def _ridges(drop=1.0):
+    """A lower tet whose top is a ridge along x at z = 0 and an upper tet
+    whose bottom is a ridge along y at z = 0.3: the ridges are the bodies'
+    extreme points, so falling onto each other they meet edge to edge."""
+    rest = np.array([[-1, 0, 0], [1, 0, 0], [0, -1, -1], [0, 1, -1],
+                     [0, -1, 0.3], [0, 1, 0.3], [-1, 0, 1.3], [1, 0, 1.3]], float)
+    m = synth.MeshInput(rest=rest, tets=np.array([[0, 1, 2, 3], [4, 5, 6, 7]], np.int32),
+                        young=np.full(2, 1e5, np.float32), poisson=np.full(2, 0.3, np.float32),
+                        density=np.full(2, 100.0, np.float32), pinned=np.array([1, 1, 1, 1, 0, 0, 0, 0], np.uint8))
+    return m
+
+
+def test_crossing_ridges_are_held_apart(orc):
+    """Thrown down onto the lower ridge, the upper ridge tunnels through it
+    with vertex-triangle CCD alone, since no vertex ever meets a face; the
+    edge-edge pairs stop it."""
+    m = _ridges()
+    model = orc.Model.from_mesh(m)
+    colors, nc = orc.color_greedy(m.n_verts, m.tets)
+    p = orc.Params.make(gravity=(0, 0, -9.8), self_collision=True, dcd_radius=0.1, k_c=1e5, ccd_interval=1)
+    v0 = np.zeros_like(m.rest)
+    v0[4:, 2] = -12.0  # 0.2 m per step
+    x, v, vp = m.rest.copy(), v0.copy(), v0.copy()
+    n_ee = []
+    for _ in range(10):
+        model.step(p, colors, nc, H, 20, x, v, vp)
+        n_ee.append(len(model.ee_pair_list()))
+    assert max(n_ee) >= 1
+    assert x[[4, 5], 2].min() > -0.05  # the upper ridge stays on the lower one
+    # the ridges' crossing point: the upper ridge's vertices straddle x = 0
+    x2, v2, vp2 = m.rest.copy(), v0.copy(), v0.copy()
+    model2 = orc.Model.from_mesh(m)
+    ridge_only = orc.Params.make(gravity=(0, 0, -9.8), self_collision=True, dcd_radius=0.1, k_c=1e5,
+                                 ccd_interval=0)
+    for _ in range(10):
+        model2.step(ridge_only, colors, nc, H, 20, x2, v2, vp2)
+    assert x2[[4, 5], 2].min() < -0.5  # without CCD it falls through
+
+
+def test_edge_edge_force_is_the_penalty_gradient(orc):
+    """With the normal frozen, the pair's depth is linear in the four
+    positions, so the forces -k_c d c_v n are exactly -dE/dx of the energy
+    and sum to zero; the Hessian blocks are k_c c_v^2 n n^T."""
+    m = _ridges()
+    model = orc.Model.from_mesh(m)
+    x0 = m.rest.copy()
+    x1 = m.rest.copy()
+    x1[4:, 2] -= 0.4  # ridges cross
+    x1[4:, 0] += 0.1
+    model.ccd(x0, x1)
+    pairs = model.ee_pair_list()
+    assert len(pairs) == 1 and sorted(pairs[0][0]) == [0, 1, 4, 5]
+    verts, su, n = [int(q) for q in pairs[0][0]], pairs[0][1], pairs[0][2]
+    assert abs(np.linalg.norm(n) - 1) < 1e-12 and abs(n[2]) > 0.9  # frozen x_b - x_a direction
+    p = orc.Params.make(self_collision=True, dcd_radius=0.1, k_c=1e5)
+    y = x1.copy()
+    el = model.elastic_grad(x1).reshape(-1, 3)
+    total = np.zeros(3)
+    for vert in (0, 1, 4, 5):
+        f, Hc, hit = model.self_contact(p, vert, x1)
+        assert hit
+        g = np.zeros(3)
+        for r in range(3):
+            xp, xm = x1.copy(), x1.copy()
+            xp[vert, r] += 1e-7
+            xm[vert, r] -= 1e-7
+            g[r] = (model.energy_G(p, H, xp, y) - model.energy_G(p, H, xm, y)) / 2e-7
+        g -= el[vert]
+        if model.free[vert]:
+            assert np.allclose(f, -g, rtol=1e-6, atol=1e-6 * np.abs(f).max())
+        total += f
+        j = verts.index(vert)
+        c = [-(1 - su[0]), -su[0], 1 - su[1], su[1]][j]
+        assert np.allclose(Hc, 1e5 * c * c * np.outer(n, n), rtol=1e-12, atol=1e-6)
+    assert np.abs(total).max() <= 1e-9 * max(1.0, np.abs(f).max())
+    # back across: no force
+    x2 = x1.copy()
+    x2[4:, 2] += 0.5
+    assert not model.self_contact(p, 4, x2)[2]

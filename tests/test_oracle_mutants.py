@@ -77,6 +77,14 @@ MUTANTS = [
      "test_oracle_ccd.py"),
     ("ccd_pair_uses_nearest_point", "    if (m->contact_ccd[a]) {\n        /* CCD pair",
      "    if (0) {\n        /* CCD pair", "test_oracle_ccd.py"),
+    ("ee_crossing_parameters_swapped", "double s = dot3(wg, n) / nn, u = dot3(we, n) / nn;",
+     "double s = dot3(we, n) / nn, u = dot3(wg, n) / nn;", "test_oracle_ccd.py"),
+    ("ee_depth_weights_sign", "c[0] = -(1.0 - s); c[1] = -s; c[2] = 1.0 - u; c[3] = u;",
+     "c[0] = 1.0 - s; c[1] = s; c[2] = -(1.0 - u); c[3] = -u;", "test_oracle_ccd.py"),
+    ("ee_pair_not_carried", "if (ee_depth(m, e, x, v, c) > 0.0) m->ee_carried[e] = 1;", "if (0) m->ee_carried[e] = 1;",
+     "test_oracle_ccd.py"),
+    ("ee_crossing_test_one_segment", "if (s >= 0.0 && s <= 1.0 && u >= 0.0 && u <= 1.0) {", "if (s >= 0.0 && s <= 1.0) {",
+     "test_oracle_ccd.py"),
 ]
 
 
