@@ -103,6 +103,9 @@ typedef struct {
                                 walls[k][3]; the allowed side is {x : x . n/|n| >= offset} */
     int32_t ccd_interval;    /* > 0 (with self_collision): vertex-triangle CCD before iterations
                                 1, 1 + ccd_interval, ... of each step (Sec. 3.5); 0 = DCD only */
+    int32_t ccd_edges;       /* 1: that CCD also pairs crossing boundary edges (Sec. 3.5, where
+                                both kinds are used); a separate switch so that the vertex-
+                                triangle CCD can run alone */
 } vbd_params;
 
 #define VBD_MAX_WALLS 6
@@ -159,8 +162,19 @@ typedef struct {
  * 1e-5 in time are tied, the lowest index wins) gives a pair that acts
  * through the impact point, whose barycentric weights stay fixed, with the
  * triangle's current normal and the same penalty and friction.  Each CCD
- * replaces the previous CCD pairs; step-start pairs stay.  Edge-edge
- * contacts are not detected.  Needs dcd_radius > 0; not
+ * replaces the previous CCD pairs; step-start pairs stay.  With ccd_edges
+ * the same CCD sweeps the boundary edges (edges of boundary triangles) against each
+ * other (partners share no tet): the first time two segments cross (the
+ * coplanarity cubic's first root with both crossing parameters in [0, 1];
+ * segments within about 6 degrees of parallel are not paired)
+ * makes a pair held by the edge that found it (each edge keeps its first
+ * hit, 1e-5 ties to the lowest index; a pair found from both edges is held
+ * by the lower one).  Its contact points keep their parameters and its
+ * normal n is the edges' unit common perpendicular where the CCD found them
+ * crossed, oriented along x_b - x_a, frozen; d = (x_b - x_a).n > 0 adds the penalty of Eq. 12 (no
+ * friction), -k_c d c_v n and k_c c_v^2 n n^T with c = (-(1 - s), -s,
+ * 1 - u, u) for the four vertices.  A pair still penetrated at the next
+ * step start is carried into that step.  Needs dcd_radius > 0; not
  * available with line_search; enlarges the workspace, so set it before
  * vbd_bind. */
 void vbd_default_params(vbd_params *out);
@@ -311,6 +325,17 @@ vbd_status vbd_energy_static(vbd_ctx *ctx, double *G_out);
  * VBD_ERR_STATE when the binding has no self-collision arrays.
  * Synchronising. */
 vbd_status vbd_get_contacts(vbd_ctx *ctx, int32_t *contact_out);
+
+/* Boundary edges and their edge-edge pairs (Sec. 3.5; pairs exist only with
+ * ccd_interval > 0).  n_edges_out receives the number of boundary edges
+ * (edges of the boundary triangles); edges_out (host, 2 per edge, may be
+ * NULL) their caller vertex ids (lower id first), in ascending order;
+ * partner_out (host, one per edge, may be NULL) for each edge the edge with
+ * which it holds a pair, or -1.  Each pair is held by one of its edges.
+ * VBD_ERR_STATE without a boundary surface (self_collision off when
+ * vbd_color ran) or, for partner_out, without the self-collision arrays in
+ * the bound workspace.  Synchronising when partner_out is given. */
+vbd_status vbd_get_edge_pairs(vbd_ctx *ctx, int32_t *n_edges_out, int32_t *edges_out, int32_t *partner_out);
 
 /* Waits for the stream and reads the device counters: VBD_ERR_TIMEOUT if a
  * bounded wait inside the pipelined sweep gave up (the step's results are

@@ -51,13 +51,15 @@ class Params(C.Structure):
                 ("init_mode", C.c_int), ("det_eps", C.c_double), ("k_d", C.c_double),
                 ("mu_c", C.c_double), ("eps_v", C.c_double), ("line_search", C.c_int), ("jacobi", C.c_int),
                 ("self_collision", C.c_int), ("dcd_radius", C.c_double), ("ccd_interval", C.c_int),
+                ("ccd_edges", C.c_int),
                 ("n_walls", C.c_int), ("walls", C.c_double * 24)]
 
     @classmethod
     def make(cls, gravity=(0.0, 0.0, -9.8), ground_on=False, ground_height=0.0,
              ground_normal=(0.0, 0.0, 1.0), k_c=0.0, cheby_rho=0.0, init_mode=3,
              det_eps=1e-12, k_d=0.0, mu_c=0.0, eps_v=1e-3, line_search=False, jacobi=False,
-             self_collision=False, dcd_radius=0.0, walls=(), ccd_interval=0, **_ignored) -> "Params":
+             self_collision=False, dcd_radius=0.0, walls=(), ccd_interval=0, ccd_edges=False,
+             **_ignored) -> "Params":
         """walls: up to 6 world-box half-spaces (nx, ny, nz, offset), the allowed
         side being x.n/|n| >= offset (Sec. 3.4)."""
         p = cls()
@@ -77,6 +79,7 @@ class Params(C.Structure):
         p.self_collision = int(bool(self_collision))
         p.dcd_radius = float(dcd_radius)
         p.ccd_interval = int(ccd_interval)
+        p.ccd_edges = int(bool(ccd_edges))
         walls = [tuple(float(v) for v in w) for w in walls]
         if len(walls) > 6 or any(len(w) != 4 for w in walls):
             raise ValueError("walls: at most 6 tuples (nx, ny, nz, offset)")
@@ -131,6 +134,7 @@ def lib():
             "orc_point_in_tet": (C.c_int, [_dp, _ip, _dp]),
             "orc_ccd_vertex": (C.c_int, [vp, _dp, _dp, C.c_int, C.POINTER(C.c_double), _dp]),
             "orc_ccd": (C.c_int, [vp, _dp, _dp]),
+            "orc_ccd_edges": (None, [vp, _dp, _dp]),
             "orc_cubic_first_root": (C.c_double, [_dp, C.c_double]),
             "orc_model_contact_weights": (None, [vp, _dp, _up]),
             "orc_ee_impact": (C.c_double, [_dp, _dp, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
@@ -458,9 +462,13 @@ class Model:
         e = self.edges()
         return [((*e[k], *e[partner[k]]), su[k], n[k]) for k in np.nonzero(partner >= 0)[0]]
 
-    def ccd(self, x0, x1) -> int:
-        """CCD of every vertex without a step-start pair; returns the pair count."""
-        return int(lib().orc_ccd(self._h, _d(x0).reshape(-1), _d(x1).reshape(-1)))
+    def ccd(self, x0, x1, edges=True) -> int:
+        """CCD of every vertex without a step-start pair (and, with edges, of
+        the boundary edges); returns the vertex-triangle pair count."""
+        n = int(lib().orc_ccd(self._h, _d(x0).reshape(-1), _d(x1).reshape(-1)))
+        if edges:
+            lib().orc_ccd_edges(self._h, _d(x0).reshape(-1), _d(x1).reshape(-1))
+        return n
 
     def local_energy(self, p: Params, h, i, x, y) -> float:
         return lib().orc_local_energy(self._h, C.byref(p), h, int(i), _d(x).reshape(-1), _d(y).reshape(-1))

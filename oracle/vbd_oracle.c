@@ -63,17 +63,21 @@
  *    point's barycentric weights w (the contact point is sum w_k x_k) and
  *    uses the triangle's current normal, with the penalty and friction of
  *    the DCD pairs; each CCD replaces the previous CCD pairs.
- *  - Edge-edge CCD (Sec. 3.5), in the same calls: boundary edges (edges of
+ *  - Edge-edge CCD (Sec. 3.5), in the same calls when ccd_edges is set:
+ *    boundary edges (edges of
  *    boundary triangles) are swept against each other (candidates: none of
  *    the other edge's vertices shares a tet with one of its own); the
  *    impact is the first root of the coplanarity cubic at which the two
- *    segments cross.  Each edge keeps the edge it hits first (1e-5 ties, the
+ *    segments cross (segments within about 6 degrees of parallel are not
+ *    paired: their crossing point is ill-conditioned).  Each edge keeps the edge it hits first (1e-5 ties, the
  *    lowest index); each hit is one pair, counted once.  The contact points
  *    x_a, x_b keep their impact parameters, and the normal n is the unit
- *    vector of x_b - x_a at the detection positions (the current iterate,
- *    where the edges have crossed), frozen for the pair's life (the paper
- *    takes n along x_b - x_a; freezing it makes d = (x_b - x_a).n change
- *    sign when the edges are back across).  d = max(0, (x_b - x_a).n) with
+ *    common perpendicular e x g of the two edges at the detection positions
+ *    (the current iterate, where the edges have crossed), oriented along
+ *    x_b - x_a there, and frozen for the pair's life.  The paper takes n
+ *    along x_b - x_a; for two lines that vector lies along e x g, which
+ *    stays well conditioned when the crossing is shallow, and freezing n
+ *    makes d = (x_b - x_a).n change sign when the edges are back across.  d = max(0, (x_b - x_a).n) with
  *    the penalty of Eq. 12; no friction on these pairs.  Neither CCD (from
  *    x^t) nor the vertex DCD can see two edges that are already crossed, so
  *    a pair still penetrated (d > 0) at the next step start is carried into
@@ -901,8 +905,11 @@ int orc_ccd_vertex(const orc_model *m, const double *x0, const double *x1, int a
  * four points are coplanar where the cubic (p1 - p0) . ((q0 - p0) x
  * (q1 - p0)) vanishes; its roots are visited in order and the first at
  * which the segments cross (in their common plane, p0 + s (p1 - p0) =
- * q0 + u (q1 - q0) with s, u in [0, 1]) is the impact.  Parallel segments
- * count as no crossing.  Returns t or -1; s, u receive the parameters. */
+ * q0 + u (q1 - q0) with s, u in [0, 1]) is the impact.  Segments within
+ * about 6 degrees of parallel (|e x g| < 0.1 |e| |g|) count as no
+ * crossing: their crossing point is ill-conditioned, and the vertex-triangle
+ * pairs of their end points take them.  Returns t or -1; s, u receive the
+ * parameters. */
 double orc_ee_impact(const double *x0, const double *x1, int p0, int p1, int q0, int q1, double *s_out,
                      double *u_out) {
     const int id[3] = {p1, q0, q1};
@@ -934,7 +941,9 @@ double orc_ee_impact(const double *x0, const double *x1, int p0, int p1, int q0,
         }
         cross3(e, g, n);
         double nn = dot3(n, n);
-        if (nn > 0.0) {
+        /* edges within about 6 degrees of parallel (|e x g| < 0.1 |e| |g|)
+         * have an ill-conditioned crossing point: not paired */
+        if (nn > 0.01 * dot3(e, e) * dot3(g, g)) {
             cross3(w, g, wg);
             cross3(w, e, we);
             double s = dot3(wg, n) / nn, u = dot3(we, n) / nn;
@@ -964,8 +973,9 @@ static int shares_tet(const orc_model *m, int a, int q) {
  * pair is held by the finding edge, unless the partner found this edge too
  * with a lower index (it then holds it) or the partner already holds the
  * same pair as a carried one.  The contact points keep their impact
- * parameters; the normal is that of x_b - x_a at x1, frozen for the pair's
- * life (a pair whose points coincide there is dropped). */
+ * parameters; the normal is the edges' unit common perpendicular at x1,
+ * oriented along x_b - x_a there and frozen for the pair's life (a pair
+ * with x_b - x_a perpendicular to it there is dropped). */
 static void ee_ccd(orc_model *m, const double *x0, const double *x1) {
     int *found = (int *)malloc(sizeof(int) * (size_t)m->n_edges + 1);
     double *su = (double *)malloc(sizeof(double) * 2 * (size_t)m->n_edges + 2);
@@ -997,16 +1007,23 @@ static void ee_ccd(orc_model *m, const double *x0, const double *x1) {
         if (m->ee_carried[f] && m->ee_partner[f] == e) continue;  /* already carried by f */
         const int v[4] = {m->edges[2 * e], m->edges[2 * e + 1], m->edges[2 * f], m->edges[2 * f + 1]};
         const double s = su[2 * e], u = su[2 * e + 1];
-        double dlt[3];
-        for (int r = 0; r < 3; ++r)
+        /* the normal: the common perpendicular e x g of the two edges at x1,
+         * pointing along x_b - x_a (for two lines x_b - x_a lies along it) */
+        double dlt[3], ee[3], gg[3], nrm[3];
+        for (int r = 0; r < 3; ++r) {
             dlt[r] = ((1.0 - u) * x1[3 * v[2] + r] + u * x1[3 * v[3] + r]) -
                      ((1.0 - s) * x1[3 * v[0] + r] + s * x1[3 * v[1] + r]);
-        double len = sqrt(dot3(dlt, dlt));
-        if (!(len > 0.0)) continue;
+            ee[r] = x1[3 * v[1] + r] - x1[3 * v[0] + r];
+            gg[r] = x1[3 * v[3] + r] - x1[3 * v[2] + r];
+        }
+        cross3(ee, gg, nrm);
+        double side = dot3(nrm, dlt), len = sqrt(dot3(nrm, nrm));
+        if (!(len > 0.0) || side == 0.0) continue;
+        if (side < 0.0) len = -len;
         m->ee_partner[e] = f;
         m->ee_su[2 * (size_t)e] = s;
         m->ee_su[2 * (size_t)e + 1] = u;
-        for (int r = 0; r < 3; ++r) m->ee_n[3 * (size_t)e + r] = dlt[r] / len;
+        for (int r = 0; r < 3; ++r) m->ee_n[3 * (size_t)e + r] = nrm[r] / len;
     }
     free(found);
     free(su);
@@ -1028,8 +1045,9 @@ static double ee_depth(const orc_model *m, int e, const double *x, int v[4], dou
     return d;
 }
 
+void orc_ccd_edges(orc_model *m, const double *x0, const double *x1) { ee_ccd(m, x0, x1); }
+
 int orc_ccd(orc_model *m, const double *x0, const double *x1) {
-    ee_ccd(m, x0, x1);
     int n = 0;
     for (int a = 0; a < m->n_verts; ++a) {
         if (m->contact[a] >= 0 && !m->contact_ccd[a]) continue;  /* keeps its step-start pair */
@@ -1428,8 +1446,10 @@ int orc_step(const orc_model *m, const orc_params *p, const int *colors, int n_c
     double *xj = p->jacobi ? (double *)malloc(sizeof(double) * n3 + 1) : NULL;
     for (int n = 1; n <= iters; ++n) {
         /* CCD along x^t -> x^(n-1) before every ccd_interval-th iteration (Sec. 3.5) */
-        if (p->self_collision && p->ccd_interval > 0 && (n - 1) % p->ccd_interval == 0)
+        if (p->self_collision && p->ccd_interval > 0 && (n - 1) % p->ccd_interval == 0) {
             orc_ccd((orc_model *)m, xt, x);
+            if (p->ccd_edges) orc_ccd_edges((orc_model *)m, xt, x);
+        }
         if (p->jacobi) {
             /* block Jacobi: solve every free vertex against the previous iterate */
             memcpy(xj, x, sizeof(double) * n3);

@@ -44,6 +44,7 @@ typedef struct {
     int self_collision;     /* 1: vertex-triangle penalty contacts from a DCD at x^t (Sec. 3.5) */
     double dcd_radius;      /* DCD search radius */
     int ccd_interval;       /* > 0: vertex-triangle CCD before every ccd_interval-th iteration (Sec. 3.5) */
+    int ccd_edges;          /* 1: the CCD also pairs crossing boundary edges (Sec. 3.5) */
     int n_walls;            /* world-box walls (Sec. 3.4), 0..ORC_MAX_WALLS */
     double walls[4 * 6];    /* wall k: normal walls[4k..4k+2] (any length), offset walls[4k+3];
                                the allowed side is x.n/|n| >= offset */
@@ -103,6 +104,8 @@ int orc_ccd_vertex(const orc_model *m, const double *x0, const double *x1, int a
 /* CCD of every boundary vertex without a step-start (DCD) pair; replaces the
  * previous CCD pairs.  Returns the number of CCD pairs. */
 int orc_ccd(orc_model *m, const double *x0, const double *x1);
+/* the edge-edge part of the CCD alone (pairs held by the edges) */
+void orc_ccd_edges(orc_model *m, const double *x0, const double *x1);
 /* Earliest root in [0, 1] of c0 + c1 t + c2 t^2 + c3 t^3 at or after t_min
  * whose point passes `accept`; -1 if none (exposed for the pins). */
 double orc_cubic_first_root(const double c[4], double t_min);

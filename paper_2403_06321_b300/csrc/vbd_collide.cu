@@ -50,6 +50,8 @@ using geom::f3;
 using geom::operator-;
 using geom::operator+;
 using geom::operator*;
+using geom::fminf3;
+using geom::fmaxf3;
 
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
@@ -90,9 +92,16 @@ __device__ __forceinline__ float swept_cell_width(const Dev &d) {
     return kMargin * (__uint_as_float(d.cell_size[0]) + __uint_as_float(d.cell_size[2])) + 1e-30f;
 }
 
+// cell of the edge table (edge-edge CCD): two edges whose motions meet have
+// sphere centres within 2 R_edge of each other
+__device__ __forceinline__ float edge_cell_width(const Dev &d) {
+    return kMargin * 2.0f * __uint_as_float(d.cell_size[3]) + 1e-30f;
+}
+
 template <int K>
 __device__ __forceinline__ float table_cell_width(const Dev &d, float r) {
-    return K == 3 ? tri_cell_width(d, r) : (K == 4 ? tet_cell_width(d) : swept_cell_width(d));
+    return K == 3 ? tri_cell_width(d, r)
+                  : (K == 4 ? tet_cell_width(d) : (K == 5 ? swept_cell_width(d) : edge_cell_width(d)));
 }
 
 __device__ __forceinline__ int3 cell_of(const Dev &d, float3 p, float inv_c) {
@@ -636,6 +645,259 @@ void exclusive_scan(const int *in, int *out, int n, int *tmp, cudaStream_t s) {
     k_scan_add<<<std::max(1u, blocks_for(n, 256)), 256, 0, s>>>(out, n, tmp, tiles);
 }
 
+
+// ---- edge-edge CCD ------------------------------------------------------------
+// Bounding sphere of each boundary edge's motion (both endpoints at x^t and
+// at the current iterate).
+__global__ void k_edge_bounds(Dev d, int n, unsigned *rmax) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int4 v = d.edge_v[e];
+    const float3 X0 = f3(__ldg(d.rest + v.x)), X1 = f3(__ldg(d.rest + v.y));
+    const float3 p[4] = {X0 + f3(__ldg(d.ut + v.x)), X1 + f3(__ldg(d.ut + v.y)), X0 + f3(__ldg(d.u + v.x)),
+                         X1 + f3(__ldg(d.u + v.y))};
+    const float3 m = 0.25f * (p[0] + p[1] + p[2] + p[3]);
+    float R2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float3 q = p[k] - m;
+        R2 = fmaxf(R2, dot(q, q));
+    }
+    float R = sqrtf(R2);
+    if (!(R >= 0.f)) R = 0.f;
+    d.edge_sphere[e] = make_float4(m.x, m.y, m.z, R);
+    atomicMax(rmax, __float_as_uint(R));
+}
+
+// Time of impact of edges (p0, p1) and (q0, q1): with A_k + t B_k the paths
+// of p1, q0, q1 relative to p0, the four points are coplanar where the
+// cubic (p1 - p0) . ((q0 - p0) x (q1 - p0)) vanishes; its roots are taken in
+// order and the first at which the segments cross (p0 + s (p1 - p0) =
+// q0 + u (q1 - q0), s and u in [0, 1], in their common plane) is the impact.
+// Segments within about 6 degrees of parallel (|e x g| < 0.1 |e| |g|) do not
+// count: their crossing point is ill-conditioned.  -1 if none; s, u out.
+__device__ __forceinline__ float ee_impact(float3 A0, float3 A1, float3 A2, float3 B0, float3 B1, float3 B2,
+                                           float &s, float &u) {
+    const float3 a12 = cross(A1, A2);
+    const float c0 = dot(A0, a12);
+    const float c1 = dot(B0, a12) + dot(A0, cross(B1, A2)) + dot(A0, cross(A1, B2));
+    const float3 b12 = cross(B1, B2);
+    const float c2 = dot(B0, cross(B1, A2)) + dot(B0, cross(A1, B2)) + dot(A0, b12);
+    const float c3 = dot(B0, b12);
+    float t0 = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {
+        const float t = cubic_first_root(c0, c1, c2, c3, t0);
+        if (t < 0.f) return -1.f;
+        const float3 e = A0 + t * B0, w = A1 + t * B1;
+        const float3 g = (A2 + t * B2) - w;
+        const float3 n = cross(e, g);
+        const float nn = dot(n, n);
+        if (nn > 0.01f * dot(e, e) * dot(g, g)) {  // not within ~6 degrees of parallel
+            s = dot(cross(w, g), n) / nn;
+            u = dot(cross(w, e), n) / nn;
+            if (s >= 0.f && s <= 1.f && u >= 0.f && u <= 1.f) return t;
+        }
+        t0 = t + 1e-6f;
+        if (t0 >= 1.f) return -1.f;
+    }
+    return -1.f;
+}
+
+// path of vertex k relative to vertex o: A (at x^t) + t B
+__device__ __forceinline__ void rel_path2(const Dev &d, int k, int o, float3 &A, float3 &B) {
+    const float3 uto = f3(__ldg(d.ut + o)), uo = f3(__ldg(d.u + o)), utk = f3(__ldg(d.ut + k));
+    A = (f3(__ldg(d.rest + k)) - f3(__ldg(d.rest + o))) + (utk - uto);
+    B = (f3(__ldg(d.u + k)) - uo) - (utk - uto);
+}
+
+// earliest impact of edge e (vertices p0, p1, rings k0, k1) among the edges
+// of this lane's cells; pass 0: earliest time, pass 1: lowest index hit by
+// `lim`.  Candidates: no vertex in the 1-ring of p0 or p1.
+template <int Q>
+__device__ __forceinline__ float earliest_edge(const Dev &d, int e, int4 ev, float4 sph, int3 cell, int nb, int lane,
+                                              float slack, int pass, float lim, int &pair) {
+    const int g0 = d.ring_off[ev.z], g1 = d.ring_off[ev.z + 1];
+    const int h0 = d.ring_off[ev.w], h1 = d.ring_off[ev.w + 1];
+    float best = -1.f;
+    for (int n = lane; n < 27; n += Q) {
+        const int b = neighbour_bucket(cell, n, nb);
+        const int e1 = d.edge_start[b + 1];
+        for (int k = d.edge_start[b]; k < e1; ++k) {
+            const int f = d.cell_edge[k];
+            if (f == e || (pass == 1 && pair >= 0 && f >= pair)) continue;
+            if (sphere_far(d.edge_sphere[f], make_float3(sph.x, sph.y, sph.z), sph.w + slack)) continue;
+            const int4 fv = d.edge_v[f];
+            bool adjacent = false;
+            for (int g = g0; g < g1 && !adjacent; ++g) {
+                const int q = d.ring[g];
+                adjacent = (q == fv.x) | (q == fv.y);
+            }
+            for (int g = h0; g < h1 && !adjacent; ++g) {
+                const int q = d.ring[g];
+                adjacent = (q == fv.x) | (q == fv.y);
+            }
+            if (adjacent) continue;
+            float3 A0, A1, A2, B0, B1, B2;
+            rel_path2(d, ev.y, ev.x, A0, B0);
+            rel_path2(d, fv.x, ev.x, A1, B1);
+            rel_path2(d, fv.y, ev.x, A2, B2);
+            // seen from p0, both segments move inside the box of their end
+            // positions; boxes that do not overlap cannot meet
+            const float3 z = make_float3(0.f, 0.f, 0.f);
+            const float3 lo_e = fminf3(fminf3(z, A0), A0 + B0), hi_e = fmaxf3(fmaxf3(z, A0), A0 + B0);
+            const float3 lo_f = fminf3(fminf3(A1, A2), fminf3(A1 + B1, A2 + B2));
+            const float3 hi_f = fmaxf3(fmaxf3(A1, A2), fmaxf3(A1 + B1, A2 + B2));
+            if (lo_f.x > hi_e.x || hi_f.x < lo_e.x || lo_f.y > hi_e.y || hi_f.y < lo_e.y || lo_f.z > hi_e.z ||
+                hi_f.z < lo_e.z)
+                continue;
+            float ss, uu;
+            const float t = ee_impact(A0, A1, A2, B0, B1, B2, ss, uu);
+            if (t < 0.f) continue;
+            if (pass == 0 && (best < 0.f || t < best)) best = t;
+            if (pass == 1 && t <= lim) pair = f;
+        }
+    }
+    return best;
+}
+
+__global__ void __launch_bounds__(128) k_ee_query(Dev d, int n_edges, int nb) {
+    constexpr int Q = kQueryLanes;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = (int)(g / Q), lane = (int)(g % Q);
+    const bool active = e < n_edges;
+    const bool carried = active && d.ee_partner[e] >= 0 && d.ee_prm[e].z > 0.5f;
+    const int4 ev = active ? d.edge_v[e] : make_int4(0, 0, 0, 0);
+    const float4 sph = active ? d.edge_sphere[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float c = edge_cell_width(d);
+    const float slack = kSlack * c;
+    const bool search = active && !carried;
+    const int3 cell = search ? cell_of(d, make_float3(sph.x, sph.y, sph.z), 1.0f / c) : make_int3(0, 0, 0);
+    int pair = -1;
+    float best = search ? earliest_edge<Q>(d, e, ev, sph, cell, nb, lane, slack, 0, 0.f, pair) : -1.f;
+    best = group_min_dist(best);
+    if (best >= 0.f) earliest_edge<Q>(d, e, ev, sph, cell, nb, lane, slack, 1, best + 1e-5f, pair);
+    pair = group_min_index(pair);
+    if (!active || lane != 0) return;
+    d.ee_found[e] = pair;
+    if (pair >= 0) {
+        const int4 fv = d.edge_v[pair];
+        float3 A0, A1, A2, B0, B1, B2;
+        rel_path2(d, ev.y, ev.x, A0, B0);
+        rel_path2(d, fv.x, ev.x, A1, B1);
+        rel_path2(d, fv.y, ev.x, A2, B2);
+        float ss = 0.f, uu = 0.f;
+        const float t = ee_impact(A0, A1, A2, B0, B1, B2, ss, uu);
+        d.ee_hit[e] = make_float4(ss, uu, t, 0.f);
+    }
+}
+
+// The pair each edge holds after a CCD: the edge it hit first, unless that
+// edge hit this one too and has the lower index (it holds the pair), or
+// already carries this pair; the normal is the edges' unit common
+// perpendicular at the current iterate, oriented along x_b - x_a there and
+// frozen (a pair with x_b - x_a perpendicular to it is dropped).  Carried
+// pairs stay.
+__global__ void k_ee_assign(Dev d, int n_edges) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_edges) return;
+    if (d.ee_partner[e] >= 0 && d.ee_prm[e].z > 0.5f) return;  // carried
+    const int f = d.ee_found[e];
+    int partner = -1;
+    if (f >= 0 && !(d.ee_found[f] == e && f < e) && !(d.ee_partner[f] == e && d.ee_prm[f].z > 0.5f)) {
+        const float4 h = d.ee_hit[e];
+        const int4 ev = d.edge_v[e], fv = d.edge_v[f];
+        float3 A0, B0, A1, B1, A2, B2;  // current positions relative to p0: A + B
+        rel_path2(d, ev.y, ev.x, A0, B0);
+        rel_path2(d, fv.x, ev.x, A1, B1);
+        rel_path2(d, fv.y, ev.x, A2, B2);
+        const float3 p1 = A0 + B0, q0 = A1 + B1, q1 = A2 + B2;
+        const float3 dl = ((1.f - h.y) * q0 + h.y * q1) - h.x * p1;
+        // the edges' common perpendicular, pointing along x_b - x_a
+        const float3 nv = cross(p1, q1 - q0);
+        const float side = dot(nv, dl);
+        float len = sqrtf(dot(nv, nv));
+        if (len > 0.f && side != 0.f) {
+            if (side < 0.f) len = -len;
+            partner = f;
+            d.ee_prm[e] = make_float4(h.x, h.y, 0.f, 0.f);
+            d.ee_nrm[e] = make_float4(nv.x / len, nv.y / len, nv.z / len, 0.f);
+            atomicAdd(d.counters + 3, 1ull);
+        }
+    }
+    d.ee_partner[e] = partner;
+}
+
+// At the step start: a pair whose depth is still positive (at x^t) is
+// carried into the step; the others end.
+__global__ void k_ee_carry(Dev d, int n_edges) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_edges) return;
+    const int f = d.ee_partner[e];
+    if (f < 0) return;
+    const float4 prm = d.ee_prm[e], n = d.ee_nrm[e];
+    const int4 ev = d.edge_v[e], fv = d.edge_v[f];
+    float3 A0, B0, A1, B1, A2, B2;
+    rel_path2(d, ev.y, ev.x, A0, B0);
+    rel_path2(d, fv.x, ev.x, A1, B1);
+    rel_path2(d, fv.y, ev.x, A2, B2);
+    const float3 p1 = A0 + B0, q0 = A1 + B1, q1 = A2 + B2;
+    const float3 dl = ((1.f - prm.y) * q0 + prm.y * q1) - prm.x * p1;
+    if (dot(dl, make_float3(n.x, n.y, n.z)) > 0.f) {
+        d.ee_prm[e] = make_float4(prm.x, prm.y, 1.f, 0.f);
+    } else {
+        d.ee_partner[e] = -1;
+        d.ee_prm[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// per free vertex, its edge-edge items (4 (holding edge) + role), sorted
+__global__ void k_ee_count(Dev d, int n_edges, int n_free, int *count) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_edges) return;
+    const int f = d.ee_partner[e];
+    if (f < 0) return;
+    const int4 ev = d.edge_v[e], fv = d.edge_v[f];
+    const int v[4] = {ev.x, ev.y, fv.x, fv.y};
+    for (int j = 0; j < 4; ++j)
+        if (v[j] < n_free) atomicAdd(count + v[j], 1);
+}
+
+__global__ void k_ee_fill(Dev d, int n_edges, int n_free) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_edges) return;
+    const int f = d.ee_partner[e];
+    if (f < 0) return;
+    const int4 ev = d.edge_v[e], fv = d.edge_v[f];
+    const int v[4] = {ev.x, ev.y, fv.x, fv.y};
+    for (int j = 0; j < 4; ++j)
+        if (v[j] < n_free) d.ee_item[d.ee_off[v[j]] + atomicAdd(d.ee_vfill + v[j], 1)] = 4 * e + j;
+}
+
+__global__ void k_ee_sort(Dev d, int n_free) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_free) return;
+    const int r0 = d.ee_off[i], r1 = d.ee_off[i + 1];
+    for (int p = r0 + 1; p < r1; ++p) {
+        const int key = d.ee_item[p];
+        int q = p - 1;
+        while (q >= r0 && d.ee_item[q] > key) {
+            d.ee_item[q + 1] = d.ee_item[q];
+            --q;
+        }
+        d.ee_item[q + 1] = key;
+    }
+}
+
+void build_ee_lists(const Dev &d, const CollideDims &c, int n_free, cudaStream_t s) {
+    if (n_free <= 0) return;
+    cudaMemsetAsync(d.ee_vfill, 0, sizeof(int) * (size_t)n_free, s);
+    k_ee_count<<<blocks_for(c.n_edges, 256), 256, 0, s>>>(d, c.n_edges, n_free, d.ee_vfill);
+    exclusive_scan(d.ee_vfill, d.ee_off, n_free, d.scan_tmp, s);
+    cudaMemsetAsync(d.ee_vfill, 0, sizeof(int) * (size_t)n_free, s);
+    k_ee_fill<<<blocks_for(c.n_edges, 256), 256, 0, s>>>(d, c.n_edges, n_free);
+    k_ee_sort<<<blocks_for(n_free, 256), 256, 0, s>>>(d, n_free);
+}
+
 // reverse corner lists of the current pairs, for the sweep
 void build_reverse_lists(const Dev &d, const CollideDims &c, int n_free, cudaStream_t s) {
     if (n_free <= 0) return;
@@ -676,6 +938,10 @@ void launch_detect(const Dev &d, const CollideDims &c, int n_free, cudaStream_t 
     k_query<<<blocks_for((long long)c.n_surf * kQueryLanes, 128), 128, 0, s>>>(d, c.n_surf, c.n_buckets,
                                                                               c.n_tet_buckets, c.radius);
     build_reverse_lists(d, c, n_free, s);
+    if (c.ee_on && c.n_edges > 0) {  // edge-edge pairs still penetrated at x^t are carried
+        k_ee_carry<<<blocks_for(c.n_edges, 256), 256, 0, s>>>(d, c.n_edges);
+        build_ee_lists(d, c, n_free, s);
+    }
 }
 
 void launch_ccd(const Dev &d, const CollideDims &c, int n_free, cudaStream_t s) {
@@ -692,6 +958,20 @@ void launch_ccd(const Dev &d, const CollideDims &c, int n_free, cudaStream_t s) 
                                                         d.cell_fill, d.cell_tri);
     k_ccd<<<blocks_for((long long)c.n_surf * kQueryLanes, 128), 128, 0, s>>>(d, c.n_surf, c.n_buckets);
     build_reverse_lists(d, c, n_free, s);
+    if (c.n_edges <= 0) return;
+    // edge-edge: spheres of the edges' motions, their hash, the query, the pairs
+    cudaMemsetAsync(d.cell_size + 3, 0, sizeof(unsigned), s);
+    k_edge_bounds<<<blocks_for(c.n_edges, 256), 256, 0, s>>>(d, c.n_edges, d.cell_size + 3);
+    cudaMemsetAsync(d.edge_fill, 0, sizeof(int) * (size_t)c.n_edge_buckets, s);
+    k_count<6><<<blocks_for(c.n_edges, 256), 256, 0, s>>>(d, d.edge_sphere, c.n_edges, c.n_edge_buckets, 0.f,
+                                                          d.edge_fill);
+    exclusive_scan(d.edge_fill, d.edge_start, c.n_edge_buckets, d.scan_tmp, s);
+    cudaMemsetAsync(d.edge_fill, 0, sizeof(int) * (size_t)c.n_edge_buckets, s);
+    k_fill<6><<<blocks_for(c.n_edges, 256), 256, 0, s>>>(d, d.edge_sphere, c.n_edges, c.n_edge_buckets, 0.f,
+                                                         d.edge_start, d.edge_fill, d.cell_edge);
+    k_ee_query<<<blocks_for((long long)c.n_edges * kQueryLanes, 128), 128, 0, s>>>(d, c.n_edges, c.n_edge_buckets);
+    k_ee_assign<<<blocks_for(c.n_edges, 256), 256, 0, s>>>(d, c.n_edges);
+    build_ee_lists(d, c, n_free, s);
 }
 
 }  // namespace vbd

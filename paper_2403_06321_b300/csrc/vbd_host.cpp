@@ -79,6 +79,9 @@ struct vbd_ctx {
     std::vector<int> surf;           // boundary vertices, ascending
     std::vector<int> ring_off, ring; // per boundary vertex: sorted ids of the vertices of its tets
     int n_buckets = 0, n_tet_buckets = 0;
+    std::vector<int> edges;          // boundary edges: 2 internal ids each, in ascending (lo, hi) caller-id order
+    std::vector<int> edge_ring;      // 2 per edge: boundary (ring) indices of its ends
+    int n_edge_buckets = 0;
     bool sc_carved = false;          // the bound workspace holds the self-collision arrays
     // subspace constraints (Sec. 3.4), caller vertex ids, as last given
     std::vector<int> sub_vertex, sub_dim;
@@ -246,6 +249,12 @@ long long max_colour_slots(const vbd_ctx *c) {
 }
 
 // the workspace carries the self-collision arrays
+// edge-edge pairs are tracked when the CCD runs (they come from it only)
+bool ee_on(const vbd_ctx *c) {
+    return c->params.self_collision && c->sc_carved && c->params.ccd_interval > 0 && c->params.ccd_edges &&
+           !c->edges.empty();
+}
+
 bool sc_wanted(const vbd_ctx *c) { return c->params.self_collision && c->surface_built; }
 
 int surf_count(const vbd_ctx *c) { return sc_wanted(c) ? (int)c->surf.size() : 0; }
@@ -352,9 +361,23 @@ size_t carve(const vbd_ctx *c, char *base, Dev *d) {
         t.tet_start = (int *)take(4 * (nbt + 1));
         t.tet_fill = (int *)take(4 * nbt);
         t.cell_tet = (int *)take(4 * T);
-        t.scan_tmp = (int *)take(4 * (size_t)vbd::scan_tmp_needed((int)std::max({nb, nbt, nf})));
+        const size_t ne = c->edges.size() / 2, nbe = (size_t)c->n_edge_buckets;
+        t.scan_tmp = (int *)take(4 * (size_t)vbd::scan_tmp_needed((int)std::max({nb, nbt, nf, nbe})));
         t.cell_size = (unsigned *)take(16);
         t.contact_w = (float4 *)take(16 * N);
+        t.edge_v = (int4 *)take(16 * ne);
+        t.edge_sphere = (float4 *)take(16 * ne);
+        t.edge_start = (int *)take(4 * (nbe + 1));
+        t.edge_fill = (int *)take(4 * nbe);
+        t.cell_edge = (int *)take(4 * ne);
+        t.ee_partner = (int *)take(4 * ne);
+        t.ee_found = (int *)take(4 * ne);
+        t.ee_prm = (float4 *)take(16 * ne);
+        t.ee_hit = (float4 *)take(16 * ne);
+        t.ee_nrm = (float4 *)take(16 * ne);
+        t.ee_off = (int *)take(4 * (nf + 1));
+        t.ee_vfill = (int *)take(4 * nf);
+        t.ee_item = (int *)take(4 * 4 * ne);
     }
     if (d) *d = t;
     return off;
@@ -381,6 +404,8 @@ SweepParams sweep_params(const vbd_ctx *c, int color) {
     for (int k = 0; k < c->params.n_walls; ++k) add_plane(c->params.walls[k], c->params.walls[k][3]);
     p.kc = c->params.k_c;
     p.n_sub = (int)c->sub_vertex.size();
+    p.ee_on = ee_on(c) ? 1 : 0;
+    p.n_edges = (int)(c->edges.size() / 2);
     p.det_eps = c->params.det_eps;
     p.kd_over_h = c->h > 0.f ? c->params.k_d / c->h : 0.f;
     p.inv_h2 = c->h > 0.f ? 1.f / (c->h * c->h) : 0.f;
@@ -477,10 +502,10 @@ void launch_colour(vbd_ctx *c, int col, cudaStream_t s) {
     const SweepParams p = sweep_params(c, col);
     if (p.self_collision) {
         vbd::launch_sweep(c->d, p, c->lanes, c->block, s);
-        vbd::launch_copy_back(c->d, p.vbegin, p.vend, !p.to_unew, s);
+        vbd::launch_copy_back(c->d, p.vbegin, p.vend, !p.to_unew, p.ee_on != 0, s);
     } else if (p.to_unew) {  // Algorithm 1 as printed: x^new, then copy back
         vbd::launch_sweep(c->d, p, c->lanes, c->block, s);
-        vbd::launch_copy_back(c->d, p.vbegin, p.vend, false, s);
+        vbd::launch_copy_back(c->d, p.vbegin, p.vend, false, false, s);
     } else if (c->variant == 1) {
         vbd::launch_sweep_pipe(c->d, p, c->pipe_block, c->pipe_maxs, c->pipe_grid_cap, s);
     } else if (c->variant == 2) {
@@ -504,7 +529,7 @@ int max_colour_verts(const vbd_ctx *c) {
 // sizes of the self-collision tables
 vbd::CollideDims collide_dims(const vbd_ctx *c) {
     return vbd::CollideDims{(int)(c->tris.size() / 3), (int)c->surf.size(), c->n_buckets, c->T, c->n_tet_buckets,
-                            c->params.dcd_radius};
+                            c->params.dcd_radius, (int)(c->edges.size() / 2), c->n_edge_buckets, ee_on(c) ? 1 : 0};
 }
 
 // the fused loop applies to plain Gauss-Seidel passes (no self-collision, no
@@ -535,7 +560,7 @@ void enqueue_iterations(vbd_ctx *c, int first_n, int iters, cudaStream_t s) {
         if (ccd && (n - 1) % c->params.ccd_interval == 0) vbd::launch_ccd(c->d, collide_dims(c), c->n_free, s);
         if (c->params.jacobi) {
             vbd::launch_sweep(c->d, sweep_params(c, 0), c->lanes, c->block, s);
-            vbd::launch_copy_back(c->d, 0, c->n_free, false, s);
+            vbd::launch_copy_back(c->d, 0, c->n_free, false, false, s);
         } else {
             for (int col = 0; col < c->n_colors; ++col)
                 launch_colour(c, col, s);
@@ -684,9 +709,35 @@ void build_surface(vbd_ctx *c) {
         c->ring.insert(c->ring.end(), nb.begin(), nb.end());
         c->ring_off[k + 1] = (int)c->ring.size();
     }
+    // boundary edges (edge-edge CCD): the triangles' edges as sorted caller-id
+    // pairs, once each, in ascending order; device ids and ring indices
+    {
+        std::vector<std::pair<int, int>> ed;
+        ed.reserve(c->tris.size());
+        for (size_t t = 0; t < c->tris.size(); t += 3)
+            for (int k = 0; k < 3; ++k) {
+                const int a = c->orig_of_new[c->tris[t + k]], b = c->orig_of_new[c->tris[t + (k + 1) % 3]];
+                ed.push_back({std::min(a, b), std::max(a, b)});
+            }
+        std::sort(ed.begin(), ed.end());
+        ed.erase(std::unique(ed.begin(), ed.end()), ed.end());
+        std::vector<int> surf_index(c->N, -1);
+        for (size_t k = 0; k < c->surf.size(); ++k) surf_index[c->surf[k]] = (int)k;
+        c->edges.resize(2 * ed.size());
+        c->edge_ring.resize(2 * ed.size());
+        for (size_t e = 0; e < ed.size(); ++e) {
+            c->edges[2 * e] = c->new_of_orig[ed[e].first];
+            c->edges[2 * e + 1] = c->new_of_orig[ed[e].second];
+            c->edge_ring[2 * e] = surf_index[c->edges[2 * e]];
+            c->edge_ring[2 * e + 1] = surf_index[c->edges[2 * e + 1]];
+        }
+    }
     int nbk = 1024;
     while ((size_t)nbk < 2 * (c->tris.size() / 3) && nbk < (1 << 30)) nbk <<= 1;
     c->n_buckets = nbk;
+    nbk = 1024;
+    while ((size_t)nbk < c->edges.size() && nbk < (1 << 30)) nbk <<= 1;  // >= 2 x edges
+    c->n_edge_buckets = nbk;
     nbk = 1024;
     while (nbk < c->T && nbk < (1 << 30)) nbk <<= 1;
     c->n_tet_buckets = nbk;
@@ -1045,7 +1096,18 @@ vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *st
         CU(cudaMemcpyAsync(d.ring, ctx->ring.data(), 4 * ctx->ring.size(), cudaMemcpyHostToDevice, s),
            "upload surface");
         CU(cudaMemsetAsync(d.contact, 0xff, 4 * (size_t)N, s), "clear contacts");  // -1: no pair
+        CU(cudaMemsetAsync(d.contact_w, 0, 16 * (size_t)N, s), "clear contacts");
         CU(cudaMemsetAsync(d.rev_off, 0, 4 * ((size_t)ctx->n_free + 1), s), "clear contacts");
+        const size_t ne = ctx->edges.size() / 2;
+        std::vector<int4> ev(ne);
+        for (size_t e = 0; e < ne; ++e)
+            ev[e] = make_int4(ctx->edges[2 * e], ctx->edges[2 * e + 1], ctx->edge_ring[2 * e], ctx->edge_ring[2 * e + 1]);
+        if (ne > 0) {
+            CU(cudaMemcpyAsync(d.edge_v, ev.data(), 16 * ne, cudaMemcpyHostToDevice, s), "upload edges");
+            CU(cudaMemsetAsync(d.ee_partner, 0xff, 4 * ne, s), "clear edge pairs");  // -1: none
+            CU(cudaMemsetAsync(d.ee_prm, 0, 16 * ne, s), "clear edge pairs");
+        }
+        CU(cudaMemsetAsync(d.ee_off, 0, 4 * ((size_t)ctx->n_free + 1), s), "clear edge pairs");
         CU(cudaStreamSynchronize(s), "upload surface");
     }
     CU(cudaMemsetAsync(d.v, 0, 16 * (size_t)N, s), "clear v");
@@ -1337,6 +1399,26 @@ vbd_status vbd_get_contacts(vbd_ctx *ctx, int32_t *contact_out) {
        "contacts download");
     CU(cudaStreamSynchronize(ctx->stream), "contacts download");
     for (int o = 0; o < ctx->N; ++o) contact_out[o] = c[ctx->new_of_orig[o]];
+    return VBD_OK;
+}
+
+vbd_status vbd_get_edge_pairs(vbd_ctx *ctx, int32_t *n_edges_out, int32_t *edges_out, int32_t *partner_out) {
+    if (!ctx || !n_edges_out) return VBD_ERR_INVALID_ARG;
+    if (!ctx->surface_built) return fail(ctx, VBD_ERR_STATE, "no boundary surface (self_collision off at colouring)");
+    const int ne = (int)(ctx->edges.size() / 2);
+    *n_edges_out = ne;
+    if (edges_out)
+        for (int e = 0; e < 2 * ne; ++e) edges_out[e] = ctx->orig_of_new[ctx->edges[e]];
+    if (partner_out) {
+        vbd_status st = check_bound(ctx);
+        if (st != VBD_OK) return st;
+        if (!ctx->sc_carved) return fail(ctx, VBD_ERR_STATE, "bound without self-collision");
+        if (ne > 0) {
+            CU(cudaMemcpyAsync(partner_out, ctx->d.ee_partner, 4 * (size_t)ne, cudaMemcpyDeviceToHost, ctx->stream),
+               "edge pairs download");
+            CU(cudaStreamSynchronize(ctx->stream), "edge pairs download");
+        }
+    }
     return VBD_OK;
 }
 

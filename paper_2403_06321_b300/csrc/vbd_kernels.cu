@@ -37,6 +37,7 @@ using geom::cross;
 using geom::dot;
 using geom::f3;
 using geom::operator-;
+using geom::operator+;
 
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -158,6 +159,36 @@ __device__ __forceinline__ void accumulate_slot_rest(const Dev &d, const SweepPa
         vm = make_float2(__ldg(d.tet_mu + j), __ldg(d.tet_lam + j));
     }
     tet_contrib(da, db, dc, ga, gb, gc, V * vm.x, V * vm.y, acc);
+}
+
+// Edge-edge pair item j = 4 (holding edge) + role (Sec. 3.5): with the
+// contact points x_a = (1 - s) p0 + s p1, x_b = (1 - u) q0 + u q1 and the
+// frozen normal n, d = (x_b - x_a).n = sum_v c_v x_v . n with
+// c = (-(1 - s), -s, 1 - u, u); for d > 0 the vertex of role r gets
+// -k_c d c_r n and k_c c_r^2 n n^T (Eq. 12, n held constant).
+__device__ __forceinline__ bool ee_item(const Dev &d, const SweepParams &p, int vi, int j, Acc &c) {
+    const int e = j >> 2, r = j & 3;
+    const int f = d.ee_partner[e];
+    if (f < 0) return false;
+    const int4 ev = d.edge_v[e], fv = d.edge_v[f];
+    const float4 prm = d.ee_prm[e], nv = d.ee_nrm[e];
+    const float cw[4] = {-(1.f - prm.x), -prm.x, 1.f - prm.y, prm.y};
+    const int vid[4] = {ev.x, ev.y, fv.x, fv.y};
+    // the weights sum to zero, so positions are taken relative to vertex vi
+    const float3 Xi = f3(__ldg(d.rest + vi)), ui = f3(__ldg(d.u + vi));
+    float dep = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float3 q = (f3(__ldg(d.rest + vid[k])) - Xi) + (f3(__ldg(d.u + vid[k])) - ui);
+        dep += cw[k] * (q.x * nv.x + q.y * nv.y + q.z * nv.z);
+    }
+    if (!(dep > 0.f)) return false;
+    const float cr = r == 0 ? cw[0] : (r == 1 ? cw[1] : (r == 2 ? cw[2] : cw[3]));
+    const float fs = -p.kc * dep * cr, hs = p.kc * cr * cr;
+    c.f0 += fs * nv.x; c.f1 += fs * nv.y; c.f2 += fs * nv.z;
+    c.h00 += hs * nv.x * nv.x; c.h01 += hs * nv.x * nv.y; c.h02 += hs * nv.x * nv.z;
+    c.h11 += hs * nv.y * nv.y; c.h12 += hs * nv.y * nv.z; c.h22 += hs * nv.z * nv.z;
+    return true;
 }
 
 template <int L>
@@ -440,15 +471,21 @@ __device__ __forceinline__ void sweep_body(const Dev &d, const SweepParams &p, l
     Acc ca = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int sc = 0;
     if (SC) {
-        int own = -1, r0 = 0, n_items = 0;
+        int own = -1, r0 = 0, n_vt = 0, e0 = 0, n_items = 0;
         if (active) {
             own = d.contact[vi];
             r0 = d.rev_off[vi];
-            n_items = (own >= 0 ? 1 : 0) + (d.rev_off[vi + 1] - r0);
+            n_vt = (own >= 0 ? 1 : 0) + (d.rev_off[vi + 1] - r0);
+            n_items = n_vt;
+            if (p.ee_on) {
+                e0 = d.ee_off[vi];
+                n_items += d.ee_off[vi + 1] - e0;
+            }
         }
         int hit = 0;
         for (int it = lane; it < n_items; it += L)
-            hit |= contact_item(d, p, vi, own, it, r0, ca) ? 1 : 0;
+            hit |= (it < n_vt ? contact_item(d, p, vi, own, it, r0, ca)
+                              : ee_item(d, p, vi, d.ee_item[e0 + it - n_vt], ca)) ? 1 : 0;
         if (__any_sync(FULL, n_items > 0)) {
             ca.f0 = sub_reduce<L>(ca.f0);
             ca.f1 = sub_reduce<L>(ca.f1);
@@ -869,10 +906,14 @@ __global__ void k_gather(const float4 *src, float *dst, const int *new_of_orig, 
 
 // the pass wrote vertices [vbegin, vend) to unew (x^new of Algorithm 1); copy
 // them back -- with involved_only, just the vertices in a self-contact pair
-__global__ void k_copy_back(Dev d, int vbegin, int vend, int involved_only) {
+// a vertex is involved when it has a vertex-triangle pair, is a corner of
+// one, or (ee_on) belongs to an edge-edge pair
+__global__ void k_copy_back(Dev d, int vbegin, int vend, int involved_only, int ee_on) {
     const int i = vbegin + blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= vend) return;
-    if (involved_only && d.contact[i] < 0 && d.rev_off[i + 1] == d.rev_off[i]) return;
+    if (involved_only && d.contact[i] < 0 && d.rev_off[i + 1] == d.rev_off[i] &&
+        !(ee_on && d.ee_off[i + 1] != d.ee_off[i]))
+        return;
     d.u[i] = d.unew[i];
 }
 
@@ -947,7 +988,7 @@ __global__ void __launch_bounds__(EB) k_energy_tets(Dev d, int n_tets, double *p
 }
 
 // self-contact energy k_c d^2 / 2 of every current pair with d > 0
-__global__ void __launch_bounds__(EB) k_energy_contacts(Dev d, int n_surf, double kc, double *partials) {
+__global__ void __launch_bounds__(EB) k_energy_contacts(Dev d, int n_surf, int n_edges, double kc, double *partials) {
     double e = 0.0;
     for (int k = blockIdx.x * EB + threadIdx.x; k < n_surf; k += gridDim.x * EB) {
         const int a = d.surf[k];
@@ -955,6 +996,21 @@ __global__ void __launch_bounds__(EB) k_energy_contacts(Dev d, int n_surf, doubl
         if (T < 0) continue;
         float3 n, w;
         const double dep = geom::pair_depth(d, a, d.tri[T], n, w);
+        if (dep > 0.0) e += 0.5 * kc * dep * dep;
+    }
+    // edge-edge pairs, held by their edges (n_edges = 0 when there are none)
+    for (int k = blockIdx.x * EB + threadIdx.x; k < n_edges; k += gridDim.x * EB) {
+        const int f = d.ee_partner[k];
+        if (f < 0) continue;
+        const int4 ev = d.edge_v[k], fv = d.edge_v[f];
+        const float4 prm = d.ee_prm[k], nv = d.ee_nrm[k];
+        const double cw[4] = {-(1.0 - prm.x), -(double)prm.x, 1.0 - prm.y, (double)prm.y};
+        const int vid[4] = {ev.x, ev.y, fv.x, fv.y};
+        double dep = 0.0;
+        for (int j = 0; j < 4; ++j) {
+            const float4 X = d.rest[vid[j]], u = d.u[vid[j]];
+            dep += cw[j] * (((double)X.x + u.x) * nv.x + ((double)X.y + u.y) * nv.y + ((double)X.z + u.z) * nv.z);
+        }
         if (dep > 0.0) e += 0.5 * kc * dep * dep;
     }
     block_sum_store(e, partials + blockIdx.x);
@@ -1193,9 +1249,10 @@ void launch_gather(const float4 *src, float *dst, const int *new_of_orig, const 
     k_gather<<<blocks_for(n, 256), 256, 0, s>>>(src, dst, new_of_orig, rest, n);
 }
 
-void launch_copy_back(const Dev &d, int vbegin, int vend, bool involved_only, cudaStream_t s) {
+void launch_copy_back(const Dev &d, int vbegin, int vend, bool involved_only, bool ee_on, cudaStream_t s) {
     if (vend > vbegin)
-        k_copy_back<<<blocks_for(vend - vbegin, 256), 256, 0, s>>>(d, vbegin, vend, involved_only ? 1 : 0);
+        k_copy_back<<<blocks_for(vend - vbegin, 256), 256, 0, s>>>(d, vbegin, vend, involved_only ? 1 : 0,
+                                                                   ee_on ? 1 : 0);
 }
 
 void launch_restore_x(const Dev &d, int n, cudaStream_t s) {
@@ -1221,7 +1278,7 @@ void launch_energy(const Dev &d, int n_free, int n_tets, int n_surf, double h, c
     energy_grid(n_free, n_tets, n_surf, &gv, &gt, &gc);
     k_energy_verts<<<gv, EB, 0, s>>>(d, n_free, 1.0 / (2.0 * h * h), p, d.partials);
     k_energy_tets<<<gt, EB, 0, s>>>(d, n_tets, d.partials + gv);
-    if (gc > 0) k_energy_contacts<<<gc, EB, 0, s>>>(d, n_surf, (double)p.kc, d.partials + gv + gt);
+    if (gc > 0) k_energy_contacts<<<gc, EB, 0, s>>>(d, n_surf, p.ee_on ? p.n_edges : 0, (double)p.kc, d.partials + gv + gt);
     k_reduce_partials<<<1, EB, 0, s>>>(d.partials, gv + gt + gc, d.energy_out);
 }
 
@@ -1285,7 +1342,7 @@ cudaError_t launch_energy_static(const Dev &d, int n_free, int n_tets, int n_sur
     // every partial slot [0, gv + gt + gc) is written before the final sum reads it
     k_energy_verts<<<gv, EB, 0, s>>>(d, n_free, 1.0 / (2.0 * h * h), p, part);
     k_energy_tets<<<gt, EB, 0, s>>>(d, n_tets, part + gv);
-    if (gc > 0) k_energy_contacts<<<gc, EB, 0, s>>>(d, n_surf, (double)p.kc, part + gv + gt);
+    if (gc > 0) k_energy_contacts<<<gc, EB, 0, s>>>(d, n_surf, p.ee_on ? p.n_edges : 0, (double)p.kc, part + gv + gt);
     k_reduce_partials<<<1, EB, 0, s>>>(part, gv + gt + gc, G_out);
     return cudaGetLastError();
 }

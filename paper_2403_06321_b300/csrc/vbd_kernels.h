@@ -72,6 +72,20 @@ struct Dev {
     unsigned *cell_size;  // bits (float) of the largest centroid-to-corner distance: [0] triangles, [1] tets,
                           // [2] the largest half path of a boundary vertex (CCD)
     float4 *contact_w;    // N: a CCD pair's impact weights (.w = 1); .w = 0 for a DCD pair or none
+    // edge-edge CCD pairs (Sec. 3.5), held by the edge that found them
+    int4 *edge_v;         // n_edges boundary edges: p0, p1 (internal ids), their boundary (ring) indices
+    float4 *edge_sphere;  // n_edges: bounding sphere of the edge's motion at the last CCD
+    int *edge_start;      // n_edge_buckets + 1: edges of each hash bucket
+    int *edge_fill;       // n_edge_buckets
+    int *cell_edge;       // n_edges
+    int *ee_partner;      // n_edges: the other edge of the held pair, or -1
+    int *ee_found;        // n_edges: the edge hit first at the last CCD, or -1
+    float4 *ee_prm;       // n_edges: s, u of the held pair, .z = 1 if carried from the previous step
+    float4 *ee_hit;       // n_edges: s, u of ee_found
+    float4 *ee_nrm;       // n_edges: the held pair's frozen normal
+    int *ee_off;          // n_free + 1: edge-edge items of each free vertex
+    int *ee_vfill;        // n_free
+    int *ee_item;         // 4 n_edges: 4 * (holding edge) + role of the vertex (0, 1 edge a; 2, 3 edge b)
 };
 
 // static half-spaces of the unilateral constraints (Sec. 3.4): the ground and up to six walls
@@ -83,6 +97,8 @@ struct SweepParams {
     int n_planes;     // planes in use (ground first when on, then the walls)
     int n_sub;        // subspace-constrained vertices (Sec. 3.4); > 0 reads Dev::sub_id
     int adj_residual; // adjoint only: store r - (H lam)_i of constrained vertices in Dev::rhs, lam unchanged
+    int ee_on;        // edge-edge pairs exist (CCD on): the sweep reads Dev::ee_off
+    int n_edges;      // boundary edges (energy of the edge-edge pairs)
     float kc;         // collision stiffness (Eq. 12)
     float det_eps;
     float kd_over_h;  // Rayleigh damping k_d / h
@@ -112,6 +128,8 @@ struct CollideDims {
     int n_tris, n_surf, n_buckets;
     int n_tets, n_tet_buckets;
     float radius;     // detection distance
+    int n_edges, n_edge_buckets;  // boundary edges and their hash (edge-edge CCD)
+    int ee_on;        // edge-edge pairs tracked (CCD on)
 };
 
 int num_sms();
@@ -144,7 +162,7 @@ void launch_scatter(const float *src, float4 *dst, const int *new_of_orig, const
 void launch_gather(const float4 *src, float *dst, const int *new_of_orig, const float4 *rest, int n,
                    cudaStream_t s);
 void launch_restore_x(const Dev &d, int n, cudaStream_t s);
-void launch_copy_back(const Dev &d, int vbegin, int vend, bool involved_only, cudaStream_t s);
+void launch_copy_back(const Dev &d, int vbegin, int vend, bool involved_only, bool ee_on, cudaStream_t s);
 // n_surf > 0 adds the self-contact energy of the current pairs
 void launch_energy(const Dev &d, int n_free, int n_tets, int n_surf, double h, const SweepParams &p,
                    cudaStream_t s);

@@ -69,6 +69,7 @@ class SimConfig:
     dcd_radius: float = 0.01
     walls: tuple = ()  # world-box half-spaces (nx, ny, nz, offset): x.n/|n| >= offset
     ccd_interval: int = 0  # vertex-triangle CCD every n_col iterations (with self_collision)
+    ccd_edges: bool = False  # that CCD also pairs crossing boundary edges
 
 
 def world_box(lo, hi) -> list:

@@ -28,7 +28,8 @@ ENTRY_POINTS = [
     "vbd_get_surface", "vbd_workspace_size", "vbd_bind", "vbd_set_params", "vbd_set_subspaces", "vbd_set_state",
     "vbd_get_state",
     "vbd_set_log_young", "vbd_step", "vbd_begin_step", "vbd_iterate", "vbd_sweep_color",
-    "vbd_accelerate", "vbd_end_step", "vbd_energy", "vbd_energy_static", "vbd_get_contacts", "vbd_sync_status",
+    "vbd_accelerate", "vbd_end_step", "vbd_energy", "vbd_energy_static", "vbd_get_contacts", "vbd_get_edge_pairs",
+    "vbd_sync_status",
     "vbd_backward",
     "vbd_set_launch", "vbd_debug_stall_pipeline", "vbd_set_graph", "vbd_autotune", "vbd_last_error",
     "vbd_destroy",
@@ -59,7 +60,8 @@ class vbd_params(C.Structure):
                 ("tape_steps", C.c_int32), ("mu_c", C.c_float), ("eps_v", C.c_float),
                 ("line_search", C.c_int32), ("jacobi", C.c_int32), ("self_collision", C.c_int32),
                 ("dcd_radius", C.c_float), ("scatter_sweep", C.c_int32), ("xnew_copy_back", C.c_int32),
-                ("n_walls", C.c_int32), ("walls", (C.c_float * 4) * 6), ("ccd_interval", C.c_int32)]
+                ("n_walls", C.c_int32), ("walls", (C.c_float * 4) * 6), ("ccd_interval", C.c_int32),
+                ("ccd_edges", C.c_int32)]
 
 
 class vbd_info(C.Structure):
@@ -86,6 +88,7 @@ def load() -> C.CDLL:
     sig = {
         "vbd_default_params": (None, [C.POINTER(vbd_params)]),
         "vbd_set_subspaces": (C.c_int, [P, I32, P, P, P]),
+        "vbd_get_edge_pairs": (C.c_int, [P, C.POINTER(I32), P, P]),
         "vbd_create_mesh": (C.c_int, [C.POINTER(vbd_mesh_desc), C.POINTER(vbd_params), C.POINTER(P)]),
         "vbd_color": (C.c_int, [P, P, C.POINTER(I32)]),
         "vbd_get_colors": (C.c_int, [P, P]),
@@ -213,6 +216,18 @@ def vbd_set_subspaces(ctx: int, vertex, dim, direction) -> None:
         direction.ctypes.data if len(vertex) else None))
 
 
+def vbd_get_edge_pairs(ctx: int, with_partners: bool = True):
+    """(edges (E, 2) caller ids, partner per edge or None) of the edge-edge CCD pairs."""
+    n = C.c_int32(0)
+    _check("vbd_get_edge_pairs", ctx, load().vbd_get_edge_pairs(ctx, C.byref(n), None, None))
+    edges = np.zeros(2 * n.value, np.int32)
+    partner = np.zeros(n.value, np.int32) if with_partners else None
+    _check("vbd_get_edge_pairs", ctx, load().vbd_get_edge_pairs(
+        ctx, C.byref(n), edges.ctypes.data if n.value else None,
+        partner.ctypes.data if (with_partners and n.value) else None))
+    return edges.reshape(-1, 2), partner
+
+
 def vbd_set_state(ctx: int, x, v, v_prev=None) -> None:
     _check("vbd_set_state", ctx, load().vbd_set_state(ctx, _ptr(x), _ptr(v), _ptr(v_prev)))
 
@@ -312,7 +327,8 @@ def vbd_destroy(ctx: int) -> None:
 def make_params(gravity=(0.0, 0.0, -9.8), ground_on=False, ground_height=0.0, ground_normal=(0.0, 0.0, 1.0),
                 k_c=1e7, cheby_rho=0.0, init_mode=3, det_eps=1e-12, k_d=0.0, tape_steps=0, mu_c=0.0,
                 eps_v=1e-3, line_search=False, jacobi=False, self_collision=False, dcd_radius=0.01,
-                scatter_sweep=False, xnew_copy_back=False, walls=(), ccd_interval=0, **_ignored) -> vbd_params:
+                scatter_sweep=False, xnew_copy_back=False, walls=(), ccd_interval=0, ccd_edges=False,
+                **_ignored) -> vbd_params:
     """vbd_params from keywords.  walls: up to 6 world-box half-spaces
     (nx, ny, nz, offset), the allowed side being x.n/|n| >= offset."""
     p = vbd_default_params()
@@ -335,6 +351,7 @@ def make_params(gravity=(0.0, 0.0, -9.8), ground_on=False, ground_height=0.0, gr
     p.scatter_sweep = int(bool(scatter_sweep))
     p.xnew_copy_back = int(bool(xnew_copy_back))
     p.ccd_interval = int(ccd_interval)
+    p.ccd_edges = int(bool(ccd_edges))
     walls = [tuple(float(v) for v in w) for w in walls]
     if len(walls) > 6 or any(len(w) != 4 for w in walls):
         raise ValueError("walls: at most 6 tuples (nx, ny, nz, offset)")

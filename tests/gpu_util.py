@@ -12,7 +12,8 @@ def params_of(cfg: synth.SimConfig, **over) -> dict:
              ground_normal=cfg.ground_normal, k_c=cfg.k_c, cheby_rho=cfg.cheby_rho,
              init_mode=cfg.init_mode, det_eps=cfg.det_eps, k_d=cfg.k_d, mu_c=cfg.mu_c, eps_v=cfg.eps_v,
              line_search=cfg.line_search, jacobi=cfg.jacobi, self_collision=cfg.self_collision,
-             dcd_radius=cfg.dcd_radius, walls=cfg.walls, ccd_interval=cfg.ccd_interval)
+             dcd_radius=cfg.dcd_radius, walls=cfg.walls, ccd_interval=cfg.ccd_interval,
+             ccd_edges=cfg.ccd_edges)
     d.update(over)
     return d
 

@@ -111,3 +111,84 @@ def test_seeded_throws_match_oracle(orc, seed):
     print("seed %d (dims %s, CCD every %d): err/bbox %.2e, CCD pairs %s" % (seed, dims, interval, err, counts))
     assert max(counts) >= 1
     assert err <= TOL
+
+
+# ---- edge-edge pairs ----------------------------------------------------------
+
+def _run_ee(orc, m, pd, v0, h, iters, steps):
+    """Like _run, comparing the edge-edge pairs (partner per boundary edge)
+    as well; returns the worst error (/ bbox), the final positions and the
+    edge-edge pair count after each step."""
+    model = orc.Model.from_mesh(m)
+    p = orc.Params.make(**pd)
+    sim = vbd.Sim(m, vbd.make_params(**pd))
+    counts = []
+    try:
+        edges, _ = vbd.vbd_get_edge_pairs(sim.ctx, with_partners=False)
+        assert np.array_equal(edges, model.edges())  # same boundary edges, same order
+        colors = vbd.vbd_get_colors(sim.ctx, m.n_verts)
+        nc = int(colors.max()) + 1
+        x = _f32(m.rest)
+        v = _f32(v0)
+        vp = v.copy()
+        sim.set_state(x, v)
+        worst = 0.0
+        for step in range(steps):
+            sim.step(h, iters)
+            model.step(p, colors, nc, h, iters, x, v, vp)
+            got = vbd.vbd_get_contacts(sim.ctx, m.n_verts)
+            assert np.array_equal(got, model.contacts()), step
+            _, partner = vbd.vbd_get_edge_pairs(sim.ctx)
+            want = model.ee_pairs()[0]
+            bad = np.nonzero(partner != want)[0]
+            assert bad.size == 0, (step, bad, partner[bad], want[bad])
+            counts.append(int((want >= 0).sum()))
+            xg, _ = sim.get_state()
+            worst = max(worst, float(np.abs(xg.cpu().numpy() - x).max()))
+            print("  step %d: err/bbox %.2e, edge-edge pairs %d" % (step, worst / bbox_diag(m.rest), counts[-1]))
+        sim.sync_status()
+    finally:
+        sim.close()
+    return worst / bbox_diag(m.rest), x, counts
+
+
+def _ridges():
+    rest = np.array([[-1, 0, 0], [1, 0, 0], [0, -1, -1], [0, 1, -1],
+                     [0, -1, 0.3], [0, 1, 0.3], [-1, 0, 1.3], [1, 0, 1.3]], float) * 0.1
+    return synth.MeshInput(rest=rest, tets=np.array([[0, 1, 2, 3], [4, 5, 6, 7]], np.int32),
+                           young=np.full(2, 1e5, np.float32), poisson=np.full(2, 0.3, np.float32),
+                           density=np.full(2, 1000.0, np.float32),
+                           pinned=np.array([1, 1, 1, 1, 0, 0, 0, 0], np.uint8))
+
+
+@pytest.mark.parametrize("interval", [1, 4])
+def test_crossing_ridges_match_oracle(orc, interval):
+    """Two tets meeting ridge to ridge (no vertex ever meets a face): only
+    edge-edge pairs act.  A ridge balanced on a ridge then tips over (an
+    unstable rest), so the comparison stops after 5 steps."""
+    m = _ridges()
+    pd = params_of(synth.SimConfig(k_c=1e5, self_collision=True, dcd_radius=0.01, ccd_interval=interval,
+                                   ccd_edges=True))
+    v0 = np.zeros_like(m.rest)
+    v0[4:, 2] = -1.5
+    err, x, counts = _run_ee(orc, m, pd, v0, 1 / 60, 20, 5)
+    print("ridges, CCD every %d: err/bbox %.2e, edge-edge pairs %s" % (interval, err, counts))
+    assert max(counts) >= 1
+    assert err <= TOL
+
+
+def test_crossed_bars_match_oracle(orc):
+    """A bar thrown crosswise onto a pinned bar: vertex-triangle and
+    edge-edge pairs together, with Chebyshev."""
+    lower = synth.beam(6, 1, 1, edge=0.05, E=1e5, nu=0.4, pin_face="z-", jitter_frac=0.03, seed=181)
+    upper = synth.beam(1, 6, 1, edge=0.05, E=1e5, nu=0.4, pin_face=None, jitter_frac=0.03, seed=182,
+                       origin=(0.12, -0.12, 0.07))
+    cat, voff, _ = synth.concat([lower, upper])
+    cat.grid_ijk = None
+    pd = params_of(synth.SimConfig(k_c=1e5, self_collision=True, dcd_radius=0.02, ccd_interval=2,
+                                   ccd_edges=True), cheby_rho=0.6)
+    v0 = np.zeros_like(cat.rest)
+    v0[voff[1]:, 2] = -3.0
+    err, x, counts = _run_ee(orc, cat, pd, v0, 1 / 60, 20, 10)
+    print("crossed bars: err/bbox %.2e, edge-edge pairs %s" % (err, counts))
+    assert err <= TOL

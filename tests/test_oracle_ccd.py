@@ -322,7 +322,8 @@ def test_crossing_ridges_are_held_apart(orc):
     m = _ridges()
     model = orc.Model.from_mesh(m)
     colors, nc = orc.color_greedy(m.n_verts, m.tets)
-    p = orc.Params.make(gravity=(0, 0, -9.8), self_collision=True, dcd_radius=0.1, k_c=1e5, ccd_interval=1)
+    p = orc.Params.make(gravity=(0, 0, -9.8), self_collision=True, dcd_radius=0.1, k_c=1e5, ccd_interval=1,
+                        ccd_edges=True)
     v0 = np.zeros_like(m.rest)
     v0[4:, 2] = -12.0  # 0.2 m per step
     x, v, vp = m.rest.copy(), v0.copy(), v0.copy()
@@ -336,10 +337,10 @@ def test_crossing_ridges_are_held_apart(orc):
     x2, v2, vp2 = m.rest.copy(), v0.copy(), v0.copy()
     model2 = orc.Model.from_mesh(m)
     ridge_only = orc.Params.make(gravity=(0, 0, -9.8), self_collision=True, dcd_radius=0.1, k_c=1e5,
-                                 ccd_interval=0)
+                                 ccd_interval=1, ccd_edges=False)
     for _ in range(10):
         model2.step(ridge_only, colors, nc, H, 20, x2, v2, vp2)
-    assert x2[[4, 5], 2].min() < -0.5  # without CCD it falls through
+    assert x2[[4, 5], 2].min() < -0.5  # with vertex-triangle CCD alone it falls through
 
 
 def test_edge_edge_force_is_the_penalty_gradient(orc):
