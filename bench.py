@@ -40,6 +40,8 @@ KERNELS = {0: "k_sweep", 1: "k_sweep_pipe", 2: "k_sweep_persist", 3: "k_scatter_
 NOMINAL_HBM_GBS = 7700.0  # B300 HBM3e nominal bandwidth, for context beside the measured peak
 DETECT_LAUNCHES = 20   # kernels and memsets of one self-collision detection (three prefix sums)
 CCD_LAUNCHES = 20      # kernels and memsets of one CCD (two prefix sums)
+EE_LAUNCHES = 17       # the edge-edge part of one CCD (two prefix sums)
+EE_CARRY_LAUNCHES = 9  # carrying edge-edge pairs at the step start (one prefix sum)
 CPU_SAMPLE_N = 32      # the CPU legs run a 32^3-cube crop of the same recipe
 CPU_SAMPLE_ITERS = 10
 
@@ -65,6 +67,7 @@ def parse_args(argv=None):
     ap.add_argument("--mu-c", type=float, default=0.0, help="ground friction coefficient (Eqs. 13-16)")
     ap.add_argument("--ccd-interval", type=int, default=0,
                     help="slabs scene: vertex-triangle CCD every n iterations (Sec. 3.5); 0 = DCD only")
+    ap.add_argument("--ccd-edges", action="store_true", help="slabs scene: the CCD also pairs crossing edges")
     ap.add_argument("--line-search", action="store_true", help="local backtracking on G_i (Sec. 3.2)")
     ap.add_argument("--jacobi", action="store_true", help="block-Jacobi iterations")
     ap.add_argument("--young", type=float, default=0.0, help="override Young's modulus of the workload")
@@ -309,7 +312,8 @@ def workload_config(args, info, mesh=None) -> dict:
            "iters_per_step": args.iters, "h": 1.0 / 60.0, "coloring": args.coloring,
            "variant": {"mu_c": args.mu_c, "line_search": bool(args.line_search), "jacobi": bool(args.jacobi),
                        "young_override": args.young or None, "self_collision": args.scene == "slabs",
-                       "ccd_interval": args.ccd_interval if args.scene == "slabs" else 0},
+                       "ccd_interval": args.ccd_interval if args.scene == "slabs" else 0,
+                       "ccd_edges": bool(args.ccd_edges) and args.scene == "slabs"},
            "l2": "inputs larger than L2 (slot stream %.2f GB per iteration)" % (n_tets * 4 * 48 / 1e9)}
     if info is not None:
         cfg.update({"n_colors": info.n_colors, "n_free_verts": info.n_free, "n_slots": int(info.n_slots),
@@ -483,7 +487,9 @@ def launches_per_step(args, info, iters: int, C: int) -> int:
     loop: one launch for all iterations)."""
     if args.scene == "slabs":
         n_ccd = -(-iters // args.ccd_interval) if args.ccd_interval > 0 else 0
-        return 2 + DETECT_LAUNCHES + n_ccd * CCD_LAUNCHES + iters * 2 * C
+        per_ccd = CCD_LAUNCHES + (EE_LAUNCHES if args.ccd_edges else 0)
+        carry = EE_CARRY_LAUNCHES if (args.ccd_edges and args.ccd_interval > 0) else 0
+        return 2 + DETECT_LAUNCHES + carry + n_ccd * per_ccd + iters * 2 * C
     if args.jacobi:
         return 2 + iters * 2
     per_colour = {3: 2}.get(info.pipeline, 1)
@@ -573,7 +579,8 @@ def run_ours(args):
                              line_search=args.line_search, jacobi=args.jacobi,
                              self_collision=cfg.self_collision, dcd_radius=cfg.dcd_radius,
                              scatter_sweep=args.variant == 3,
-                             ccd_interval=args.ccd_interval if args.scene == "slabs" else 0)
+                             ccd_interval=args.ccd_interval if args.scene == "slabs" else 0,
+                             ccd_edges=bool(args.ccd_edges) and args.scene == "slabs")
     stream = torch.cuda.Stream()
     sim = vbd.Sim(m, params, colors=colors, stream=stream)
     if args.lanes or args.block or args.variant >= 0:

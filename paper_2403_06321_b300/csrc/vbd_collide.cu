@@ -958,7 +958,7 @@ void launch_ccd(const Dev &d, const CollideDims &c, int n_free, cudaStream_t s) 
                                                         d.cell_fill, d.cell_tri);
     k_ccd<<<blocks_for((long long)c.n_surf * kQueryLanes, 128), 128, 0, s>>>(d, c.n_surf, c.n_buckets);
     build_reverse_lists(d, c, n_free, s);
-    if (c.n_edges <= 0) return;
+    if (!c.ee_on || c.n_edges <= 0) return;
     // edge-edge: spheres of the edges' motions, their hash, the query, the pairs
     cudaMemsetAsync(d.cell_size + 3, 0, sizeof(unsigned), s);
     k_edge_bounds<<<blocks_for(c.n_edges, 256), 256, 0, s>>>(d, c.n_edges, d.cell_size + 3);
