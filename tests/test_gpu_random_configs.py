@@ -1,8 +1,8 @@
 """Seeded random combinations of the options the sweep composes, each run on
 the GPU (through the C ABI) and by the FP64 oracle with the same colouring:
 mesh shape and jitter, per-tet materials, pins, init mode, ground contact
-with friction, world-box walls, Chebyshev, damping, line search, colouring
-and sweep variant.  Tolerance 1e-5 of the bounding-box diagonal."""
+with friction, world-box walls, subspace constraints, Chebyshev, damping,
+line search, colouring and sweep variant.  Tolerance 1e-5 of the bounding-box diagonal."""
 import numpy as np
 import pytest
 import torch
@@ -56,6 +56,14 @@ def _case(seed: int):
             n /= np.linalg.norm(n)
             walls.append(tuple(n) + (float((m.rest @ n).min() - rng.uniform(0.0, 0.5) * edge),))
         pd["walls"] = walls
+    if rng.random() < 0.3:  # a few free vertices restricted to random lines or planes
+        free = np.nonzero(m.pinned == 0)[0]
+        k = rng.choice(free, size=min(len(free), int(rng.integers(1, 12))), replace=False)
+        m.sub_dim = np.full(m.n_verts, 3, np.int32)
+        m.sub_dir = np.zeros((m.n_verts, 3))
+        m.sub_dim[k] = rng.integers(1, 3, len(k))
+        m.sub_dir[k] = rng.normal(0, 1, (len(k), 3))
+        v0[k] = 0.0  # start on the subspaces with no motion across them
     return m, pd, v0, greedy, variant, lanes, h, iters, steps
 
 
