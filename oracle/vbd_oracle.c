@@ -569,7 +569,8 @@ static int subspace_step(const orc_model *m, const orc_params *p, int i, const d
         b[a] = dot3(q + 3 * a, f);
         for (int c = 0; c < L; ++c) {
             double Hq[3];
-            for (int r = 0; r < 3; ++r) Hq[r] = H[r * 3 + 0] * q[3 * c] + H[r * 3 + 1] * q[3 * c + 1] + H[r * 3 + 2] * q[3 * c + 2];
+            for (int r = 0; r < 3; ++r)
+                Hq[r] = H[r * 3 + 0] * q[3 * c] + H[r * 3 + 1] * q[3 * c + 1] + H[r * 3 + 2] * q[3 * c + 2];
             A[a * L + c] = dot3(q + 3 * a, Hq);
         }
     }

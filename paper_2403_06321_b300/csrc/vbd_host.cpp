@@ -243,8 +243,10 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 // largest number of slots of one colour (the scatter sweep's scratch)
 long long max_colour_slots(const vbd_ctx *c) {
     long long mx = 0;
-    for (int col = 0; col < c->n_colors; ++col)
-        mx = std::max<long long>(mx, (long long)c->slot_off[c->color_begin[col + 1]] - c->slot_off[c->color_begin[col]]);
+    for (int col = 0; col < c->n_colors; ++col) {
+        const long long n = (long long)c->slot_off[c->color_begin[col + 1]] - c->slot_off[c->color_begin[col]];
+        mx = std::max<long long>(mx, n);
+    }
     return mx;
 }
 
@@ -1101,7 +1103,8 @@ vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *st
         const size_t ne = ctx->edges.size() / 2;
         std::vector<int4> ev(ne);
         for (size_t e = 0; e < ne; ++e)
-            ev[e] = make_int4(ctx->edges[2 * e], ctx->edges[2 * e + 1], ctx->edge_ring[2 * e], ctx->edge_ring[2 * e + 1]);
+            ev[e] = make_int4(ctx->edges[2 * e], ctx->edges[2 * e + 1], ctx->edge_ring[2 * e],
+                              ctx->edge_ring[2 * e + 1]);
         if (ne > 0) {
             CU(cudaMemcpyAsync(d.edge_v, ev.data(), 16 * ne, cudaMemcpyHostToDevice, s), "upload edges");
             CU(cudaMemsetAsync(d.ee_partner, 0xff, 4 * ne, s), "clear edge pairs");  // -1: none
@@ -1501,7 +1504,8 @@ vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_
     }
     if (var == 4) {
         if (!ctx->colored) return fail(ctx, VBD_ERR_NOT_COLORED, "the fused loop needs the colouring");
-        const int cl = vbd::fused_clusters_needed(max_colour_verts(ctx), lanes_per_vertex ? lanes_per_vertex : ctx->lanes);
+        const int lanes = lanes_per_vertex ? lanes_per_vertex : ctx->lanes;
+        const int cl = vbd::fused_clusters_needed(max_colour_verts(ctx), lanes);
         if (cl == 0)
             return fail(ctx, VBD_ERR_INVALID_ARG, "largest colour too large for the fused loop (at most " +
                                                       std::to_string(vbd::kFusedMaxCluster * vbd::kFusedThreads *

@@ -1207,7 +1207,8 @@ int fused_clusters_needed(int max_colour_verts, int lanes) {
     const long long threads = (long long)max_colour_verts * lanes;
     const long long per_round = (long long)kFusedMaxCluster * kFusedThreads;
     if (threads > per_round * kFusedMaxRounds) return 0;
-    return (int)std::max<long long>(1, std::min<long long>(kFusedMaxCluster, (threads + kFusedThreads - 1) / kFusedThreads));
+    return (int)std::max<long long>(1, std::min<long long>(kFusedMaxCluster,
+                                                           (threads + kFusedThreads - 1) / kFusedThreads));
 }
 
 cudaError_t launch_iterate_fused(const Dev &d, const FusedParams &f, int lanes, int cluster, cudaStream_t s) {
@@ -1278,7 +1279,8 @@ void launch_energy(const Dev &d, int n_free, int n_tets, int n_surf, double h, c
     energy_grid(n_free, n_tets, n_surf, &gv, &gt, &gc);
     k_energy_verts<<<gv, EB, 0, s>>>(d, n_free, 1.0 / (2.0 * h * h), p, d.partials);
     k_energy_tets<<<gt, EB, 0, s>>>(d, n_tets, d.partials + gv);
-    if (gc > 0) k_energy_contacts<<<gc, EB, 0, s>>>(d, n_surf, p.ee_on ? p.n_edges : 0, (double)p.kc, d.partials + gv + gt);
+    if (gc > 0)
+        k_energy_contacts<<<gc, EB, 0, s>>>(d, n_surf, p.ee_on ? p.n_edges : 0, (double)p.kc, d.partials + gv + gt);
     k_reduce_partials<<<1, EB, 0, s>>>(d.partials, gv + gt + gc, d.energy_out);
 }
 
@@ -1342,7 +1344,8 @@ cudaError_t launch_energy_static(const Dev &d, int n_free, int n_tets, int n_sur
     // every partial slot [0, gv + gt + gc) is written before the final sum reads it
     k_energy_verts<<<gv, EB, 0, s>>>(d, n_free, 1.0 / (2.0 * h * h), p, part);
     k_energy_tets<<<gt, EB, 0, s>>>(d, n_tets, part + gv);
-    if (gc > 0) k_energy_contacts<<<gc, EB, 0, s>>>(d, n_surf, p.ee_on ? p.n_edges : 0, (double)p.kc, part + gv + gt);
+    if (gc > 0)
+        k_energy_contacts<<<gc, EB, 0, s>>>(d, n_surf, p.ee_on ? p.n_edges : 0, (double)p.kc, part + gv + gt);
     k_reduce_partials<<<1, EB, 0, s>>>(part, gv + gt + gc, G_out);
     return cudaGetLastError();
 }
