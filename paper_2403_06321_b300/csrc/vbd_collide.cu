@@ -710,14 +710,32 @@ __device__ __forceinline__ void rel_path2(const Dev &d, int k, int o, float3 &A,
     B = (f3(__ldg(d.u + k)) - uo) - (utk - uto);
 }
 
+// path of vertex k relative to vertex o, with o's rest position, x^t and
+// current displacements given (the same arithmetic as rel_path2)
+__device__ __forceinline__ void rel_path_from(const Dev &d, int k, float3 Ro, float3 uto, float3 uo, float3 &A,
+                                              float3 &B) {
+    const float3 utk = f3(__ldg(d.ut + k));
+    A = (f3(__ldg(d.rest + k)) - Ro) + (utk - uto);
+    B = (f3(__ldg(d.u + k)) - uo) - (utk - uto);
+}
+
 // earliest impact of edge e (vertices p0, p1, rings k0, k1) among the edges
 // of this lane's cells; pass 0: earliest time, pass 1: lowest index hit by
-// `lim`.  Candidates: no vertex in the 1-ring of p0 or p1.
+// `lim`.  Candidates: no vertex in the 1-ring of p0 or p1.  The filters run
+// cheapest first (bounding spheres, a shared vertex, the motion boxes seen
+// from p0, then the rings); the candidate set does not depend on their order.
 template <int Q>
 __device__ __forceinline__ float earliest_edge(const Dev &d, int e, int4 ev, float4 sph, int3 cell, int nb, int lane,
                                               float slack, int pass, float lim, int &pair) {
     const int g0 = d.ring_off[ev.z], g1 = d.ring_off[ev.z + 1];
     const int h0 = d.ring_off[ev.w], h1 = d.ring_off[ev.w + 1];
+    const float3 Ro = f3(__ldg(d.rest + ev.x)), uto = f3(__ldg(d.ut + ev.x)), uo = f3(__ldg(d.u + ev.x));
+    float3 A0, B0;
+    rel_path_from(d, ev.y, Ro, uto, uo, A0, B0);
+    // seen from p0, both segments move inside the box of their end
+    // positions; boxes that do not overlap cannot meet
+    const float3 z = make_float3(0.f, 0.f, 0.f);
+    const float3 lo_e = fminf3(fminf3(z, A0), A0 + B0), hi_e = fmaxf3(fmaxf3(z, A0), A0 + B0);
     float best = -1.f;
     for (int n = lane; n < 27; n += Q) {
         const int b = neighbour_bucket(cell, n, nb);
@@ -727,6 +745,15 @@ __device__ __forceinline__ float earliest_edge(const Dev &d, int e, int4 ev, flo
             if (f == e || (pass == 1 && pair >= 0 && f >= pair)) continue;
             if (sphere_far(d.edge_sphere[f], make_float3(sph.x, sph.y, sph.z), sph.w + slack)) continue;
             const int4 fv = d.edge_v[f];
+            if (fv.x == ev.x || fv.x == ev.y || fv.y == ev.x || fv.y == ev.y) continue;  // in both rings
+            float3 A1, A2, B1, B2;
+            rel_path_from(d, fv.x, Ro, uto, uo, A1, B1);
+            rel_path_from(d, fv.y, Ro, uto, uo, A2, B2);
+            const float3 lo_f = fminf3(fminf3(A1, A2), fminf3(A1 + B1, A2 + B2));
+            const float3 hi_f = fmaxf3(fmaxf3(A1, A2), fmaxf3(A1 + B1, A2 + B2));
+            if (lo_f.x > hi_e.x || hi_f.x < lo_e.x || lo_f.y > hi_e.y || hi_f.y < lo_e.y || lo_f.z > hi_e.z ||
+                hi_f.z < lo_e.z)
+                continue;
             bool adjacent = false;
             for (int g = g0; g < g1 && !adjacent; ++g) {
                 const int q = d.ring[g];
@@ -737,19 +764,6 @@ __device__ __forceinline__ float earliest_edge(const Dev &d, int e, int4 ev, flo
                 adjacent = (q == fv.x) | (q == fv.y);
             }
             if (adjacent) continue;
-            float3 A0, A1, A2, B0, B1, B2;
-            rel_path2(d, ev.y, ev.x, A0, B0);
-            rel_path2(d, fv.x, ev.x, A1, B1);
-            rel_path2(d, fv.y, ev.x, A2, B2);
-            // seen from p0, both segments move inside the box of their end
-            // positions; boxes that do not overlap cannot meet
-            const float3 z = make_float3(0.f, 0.f, 0.f);
-            const float3 lo_e = fminf3(fminf3(z, A0), A0 + B0), hi_e = fmaxf3(fmaxf3(z, A0), A0 + B0);
-            const float3 lo_f = fminf3(fminf3(A1, A2), fminf3(A1 + B1, A2 + B2));
-            const float3 hi_f = fmaxf3(fmaxf3(A1, A2), fmaxf3(A1 + B1, A2 + B2));
-            if (lo_f.x > hi_e.x || hi_f.x < lo_e.x || lo_f.y > hi_e.y || hi_f.y < lo_e.y || lo_f.z > hi_e.z ||
-                hi_f.z < lo_e.z)
-                continue;
             float ss, uu;
             const float t = ee_impact(A0, A1, A2, B0, B1, B2, ss, uu);
             if (t < 0.f) continue;
