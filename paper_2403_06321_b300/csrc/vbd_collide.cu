@@ -719,14 +719,55 @@ __device__ __forceinline__ void rel_path_from(const Dev &d, int k, float3 Ro, fl
     B = (f3(__ldg(d.u + k)) - uo) - (utk - uto);
 }
 
+// The hits of one lane within 1e-5 in time of its earliest so far (the
+// tie window): up to two, else `full` and the query scans again.
+struct TieWindow {
+    float ta, tb;
+    int fa, fb, n;
+    bool full;
+    __device__ void add(float t, int f, float best) {
+        if (!(t <= best + 1e-5f)) return;
+        if (n == 0) {
+            ta = t;
+            fa = f;
+            n = 1;
+        } else if (n == 1) {
+            tb = t;
+            fb = f;
+            n = 2;
+        } else {
+            full = true;
+        }
+    }
+    // the earliest time has moved down to `best`: drop what left the window
+    __device__ void shrink(float best) {
+        const float w = best + 1e-5f;
+        if (n == 2 && !(tb <= w)) n = 1;
+        if (n >= 1 && !(ta <= w)) {
+            ta = tb;
+            fa = fb;
+            n -= 1;
+        }
+    }
+    // lowest index among the hits by `lim`, -1 if none
+    __device__ int lowest(float lim) const {
+        int f = -1;
+        if (n >= 1 && ta <= lim) f = fa;
+        if (n >= 2 && tb <= lim && (f < 0 || fb < f)) f = fb;
+        return f;
+    }
+};
+
 // earliest impact of edge e (vertices p0, p1, rings k0, k1) among the edges
-// of this lane's cells; pass 0: earliest time, pass 1: lowest index hit by
-// `lim`.  Candidates: no vertex in the 1-ring of p0 or p1.  The filters run
-// cheapest first (bounding spheres, a shared vertex, the motion boxes seen
-// from p0, then the rings); the candidate set does not depend on their order.
+// of this lane's cells; pass 0: earliest time, with the hits in its tie
+// window kept in `win`; pass 1 (only when a window was full): lowest index
+// hit by `lim`.  Candidates: no vertex in the 1-ring of p0 or p1.  The
+// filters run cheapest first (bounding spheres, a shared vertex, the motion
+// boxes seen from p0, then the rings); the candidate set does not depend on
+// their order.
 template <int Q>
 __device__ __forceinline__ float earliest_edge(const Dev &d, int e, int4 ev, float4 sph, int3 cell, int nb, int lane,
-                                              float slack, int pass, float lim, int &pair) {
+                                              float slack, int pass, float lim, int &pair, TieWindow &win) {
     const int g0 = d.ring_off[ev.z], g1 = d.ring_off[ev.z + 1];
     const int h0 = d.ring_off[ev.w], h1 = d.ring_off[ev.w + 1];
     const float3 Ro = f3(__ldg(d.rest + ev.x)), uto = f3(__ldg(d.ut + ev.x)), uo = f3(__ldg(d.u + ev.x));
@@ -767,7 +808,13 @@ __device__ __forceinline__ float earliest_edge(const Dev &d, int e, int4 ev, flo
             float ss, uu;
             const float t = ee_impact(A0, A1, A2, B0, B1, B2, ss, uu);
             if (t < 0.f) continue;
-            if (pass == 0 && (best < 0.f || t < best)) best = t;
+            if (pass == 0) {
+                if (best < 0.f || t < best) {
+                    best = t;
+                    win.shrink(best);
+                }
+                win.add(t, f, best);
+            }
             if (pass == 1 && t <= lim) pair = f;
         }
     }
@@ -787,9 +834,19 @@ __global__ void __launch_bounds__(128) k_ee_query(Dev d, int n_edges, int nb) {
     const bool search = active && !carried;
     const int3 cell = search ? cell_of(d, make_float3(sph.x, sph.y, sph.z), 1.0f / c) : make_int3(0, 0, 0);
     int pair = -1;
-    float best = search ? earliest_edge<Q>(d, e, ev, sph, cell, nb, lane, slack, 0, 0.f, pair) : -1.f;
+    TieWindow win = {0.f, 0.f, -1, -1, 0, false};
+    float best = search ? earliest_edge<Q>(d, e, ev, sph, cell, nb, lane, slack, 0, 0.f, pair, win) : -1.f;
     best = group_min_dist(best);
-    if (best >= 0.f) earliest_edge<Q>(d, e, ev, sph, cell, nb, lane, slack, 1, best + 1e-5f, pair);
+    // every lane's hits by best + 1e-5 are in its window unless it was full
+    // (a lane's window only drops hits later than its own earliest + 1e-5);
+    // the shuffles run on every lane of the warp
+    const bool rescan = group_min_index(win.full ? 0 : -1) == 0;
+    if (best >= 0.f) {
+        if (rescan)
+            earliest_edge<Q>(d, e, ev, sph, cell, nb, lane, slack, 1, best + 1e-5f, pair, win);
+        else
+            pair = win.lowest(best + 1e-5f);
+    }
     pair = group_min_index(pair);
     if (!active || lane != 0) return;
     d.ee_found[e] = pair;
