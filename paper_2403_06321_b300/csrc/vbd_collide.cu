@@ -451,13 +451,53 @@ __device__ __forceinline__ void rel_path(const Dev &d, int k, float3 Xa, float3 
     B = (f3(__ldg(d.u + k)) - ua) - (utk - uta);
 }
 
+// The hits of one lane within 1e-5 in time of its earliest so far (the
+// tie window): up to two, else `full` and the query scans again.
+struct TieWindow {
+    float ta, tb;
+    int fa, fb, n;
+    bool full;
+    __device__ void add(float t, int f, float best) {
+        if (!(t <= best + 1e-5f)) return;
+        if (n == 0) {
+            ta = t;
+            fa = f;
+            n = 1;
+        } else if (n == 1) {
+            tb = t;
+            fb = f;
+            n = 2;
+        } else {
+            full = true;
+        }
+    }
+    // the earliest time has moved down to `best`: drop what left the window
+    __device__ void shrink(float best) {
+        const float w = best + 1e-5f;
+        if (n == 2 && !(tb <= w)) n = 1;
+        if (n >= 1 && !(ta <= w)) {
+            ta = tb;
+            fa = fb;
+            n -= 1;
+        }
+    }
+    // lowest index among the hits by `lim`, -1 if none
+    __device__ int lowest(float lim) const {
+        int f = -1;
+        if (n >= 1 && ta <= lim) f = fa;
+        if (n >= 2 && tb <= lim && (f < 0 || fb < f)) f = fb;
+        return f;
+    }
+};
+
 // earliest admissible impact of vertex a (boundary index k) among the
-// triangles of this lane's cells: pass 0 returns the earliest time (or -1),
-// pass 1 the lowest triangle index hit by time `lim` (or -1)
+// triangles of this lane's cells: pass 0 returns the earliest time (or -1)
+// and keeps the hits of its tie window in `win`; pass 1 (only when a window
+// was full) the lowest triangle index hit by time `lim` (or -1)
 template <int Q>
 __device__ __forceinline__ float earliest_impact(const Dev &d, int k, float3 Xa, float3 uta, float3 ua, float3 mid,
                                                 float Ra, int3 cell, int nb, int lane, float slack, int pass,
-                                                float lim, int &pair) {
+                                                float lim, int &pair, TieWindow &win) {
     const int g0 = d.ring_off[k], g1 = d.ring_off[k + 1];
     float best = -1.f;
     for (int n = lane; n < 27; n += Q) {
@@ -483,7 +523,13 @@ __device__ __forceinline__ float earliest_impact(const Dev &d, int k, float3 Xa,
             if (box_misses_origin(A0, A1, A2, A0 + B0, A1 + B1, A2 + B2)) continue;
             const float ti = vt_impact(A0, A1, A2, B0, B1, B2, w);
             if (ti < 0.f) continue;
-            if (pass == 0 && (best < 0.f || ti < best)) best = ti;
+            if (pass == 0) {
+                if (best < 0.f || ti < best) {
+                    best = ti;
+                    win.shrink(best);
+                }
+                win.add(ti, t, best);
+            }
             if (pass == 1 && ti <= lim) pair = t;
         }
     }
@@ -506,12 +552,18 @@ __global__ void __launch_bounds__(128) k_ccd(Dev d, int n_surf, int nb) {
     const float slack = kSlack * c;
     const int3 cell = (active && !keep) ? cell_of(d, mid, 1.0f / c) : make_int3(0, 0, 0);
     int pair = -1;
+    TieWindow win = {0.f, 0.f, -1, -1, 0, false};
     float best = (active && !keep)
-                     ? earliest_impact<Q>(d, k, Xa, uta, ua, mid, Ra, cell, nb, lane, slack, 0, 0.f, pair)
+                     ? earliest_impact<Q>(d, k, Xa, uta, ua, mid, Ra, cell, nb, lane, slack, 0, 0.f, pair, win)
                      : -1.f;
     best = group_min_dist(best);
-    if (best >= 0.f)  // uniform over the group
-        earliest_impact<Q>(d, k, Xa, uta, ua, mid, Ra, cell, nb, lane, slack, 1, best + 1e-5f, pair);
+    const bool rescan = group_min_index(win.full ? 0 : -1) == 0;  // on every lane of the warp
+    if (best >= 0.f) {  // uniform over the group
+        if (rescan)
+            earliest_impact<Q>(d, k, Xa, uta, ua, mid, Ra, cell, nb, lane, slack, 1, best + 1e-5f, pair, win);
+        else
+            pair = win.lowest(best + 1e-5f);
+    }
     pair = group_min_index(pair);
     if (!active || lane != 0 || keep) return;
     if (pair >= 0) {
@@ -718,45 +770,6 @@ __device__ __forceinline__ void rel_path_from(const Dev &d, int k, float3 Ro, fl
     A = (f3(__ldg(d.rest + k)) - Ro) + (utk - uto);
     B = (f3(__ldg(d.u + k)) - uo) - (utk - uto);
 }
-
-// The hits of one lane within 1e-5 in time of its earliest so far (the
-// tie window): up to two, else `full` and the query scans again.
-struct TieWindow {
-    float ta, tb;
-    int fa, fb, n;
-    bool full;
-    __device__ void add(float t, int f, float best) {
-        if (!(t <= best + 1e-5f)) return;
-        if (n == 0) {
-            ta = t;
-            fa = f;
-            n = 1;
-        } else if (n == 1) {
-            tb = t;
-            fb = f;
-            n = 2;
-        } else {
-            full = true;
-        }
-    }
-    // the earliest time has moved down to `best`: drop what left the window
-    __device__ void shrink(float best) {
-        const float w = best + 1e-5f;
-        if (n == 2 && !(tb <= w)) n = 1;
-        if (n >= 1 && !(ta <= w)) {
-            ta = tb;
-            fa = fb;
-            n -= 1;
-        }
-    }
-    // lowest index among the hits by `lim`, -1 if none
-    __device__ int lowest(float lim) const {
-        int f = -1;
-        if (n >= 1 && ta <= lim) f = fa;
-        if (n >= 2 && tb <= lim && (f < 0 || fb < f)) f = fb;
-        return f;
-    }
-};
 
 // earliest impact of edge e (vertices p0, p1, rings k0, k1) among the edges
 // of this lane's cells; pass 0: earliest time, with the hits in its tie
