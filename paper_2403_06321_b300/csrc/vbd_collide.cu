@@ -205,13 +205,18 @@ __global__ void k_count(Dev d, const float4 *sphere, int n, int nb, float r, int
     atomicAdd(count + sphere_bucket(d, sphere[t], 1.0f / table_cell_width<K>(d, r), nb), 1);
 }
 
+// entries[] of bucket b: the ids whose sphere centre hashes to b; with
+// `sorted`, each entry's sphere beside it (the query streams those)
 template <int K>
 __global__ void k_fill(Dev d, const float4 *sphere, int n, int nb, float r, const int *start, int *fill,
-                       int *entries) {
+                       int *entries, float4 *sorted = nullptr) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
-    const int b = sphere_bucket(d, sphere[t], 1.0f / table_cell_width<K>(d, r), nb);
-    entries[start[b] + atomicAdd(fill + b, 1)] = t;
+    const float4 sp = sphere[t];
+    const int b = sphere_bucket(d, sp, 1.0f / table_cell_width<K>(d, r), nb);
+    const int k = start[b] + atomicAdd(fill + b, 1);
+    entries[k] = t;
+    if (sorted) sorted[k] = sp;
 }
 
 // ---- narrow phase -------------------------------------------------------------
@@ -795,9 +800,9 @@ __device__ __forceinline__ float earliest_edge(const Dev &d, int e, int4 ev, flo
         const int b = neighbour_bucket(cell, n, nb);
         const int e1 = d.edge_start[b + 1];
         for (int k = d.edge_start[b]; k < e1; ++k) {
+            if (sphere_far(d.cell_edge_sph[k], make_float3(sph.x, sph.y, sph.z), sph.w + slack)) continue;
             const int f = d.cell_edge[k];
             if (f == e || (pass == 1 && pair >= 0 && f >= pair)) continue;
-            if (sphere_far(d.edge_sphere[f], make_float3(sph.x, sph.y, sph.z), sph.w + slack)) continue;
             const int4 fv = d.edge_v[f];
             if (fv.x == ev.x || fv.x == ev.y || fv.y == ev.x || fv.y == ev.y) continue;  // in both rings
             float3 A1, A2, B1, B2;
@@ -1052,7 +1057,7 @@ void launch_ccd(const Dev &d, const CollideDims &c, int n_free, cudaStream_t s) 
     exclusive_scan(d.edge_fill, d.edge_start, c.n_edge_buckets, d.scan_tmp, s);
     cudaMemsetAsync(d.edge_fill, 0, sizeof(int) * (size_t)c.n_edge_buckets, s);
     k_fill<6><<<blocks_for(c.n_edges, 256), 256, 0, s>>>(d, d.edge_sphere, c.n_edges, c.n_edge_buckets, 0.f,
-                                                         d.edge_start, d.edge_fill, d.cell_edge);
+                                                         d.edge_start, d.edge_fill, d.cell_edge, d.cell_edge_sph);
     k_ee_query<<<blocks_for((long long)c.n_edges * kQueryLanes, 128), 128, 0, s>>>(d, c.n_edges, c.n_edge_buckets);
     k_ee_assign<<<blocks_for(c.n_edges, 256), 256, 0, s>>>(d, c.n_edges);
     build_ee_lists(d, c, n_free, s);

@@ -372,6 +372,7 @@ size_t carve(const vbd_ctx *c, char *base, Dev *d) {
         t.edge_start = (int *)take(4 * (nbe + 1));
         t.edge_fill = (int *)take(4 * nbe);
         t.cell_edge = (int *)take(4 * ne);
+        t.cell_edge_sph = (float4 *)take(16 * ne);
         t.ee_partner = (int *)take(4 * ne);
         t.ee_found = (int *)take(4 * ne);
         t.ee_prm = (float4 *)take(16 * ne);

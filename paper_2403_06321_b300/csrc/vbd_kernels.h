@@ -78,6 +78,7 @@ struct Dev {
     int *edge_start;      // n_edge_buckets + 1: edges of each hash bucket
     int *edge_fill;       // n_edge_buckets
     int *cell_edge;       // n_edges
+    float4 *cell_edge_sph; // n_edges: edge_sphere of each cell_edge entry, in table order
     int *ee_partner;      // n_edges: the other edge of the held pair, or -1
     int *ee_found;        // n_edges: the edge hit first at the last CCD, or -1
     float4 *ee_prm;       // n_edges: s, u of the held pair, .z = 1 if carried from the previous step
