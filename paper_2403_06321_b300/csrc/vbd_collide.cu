@@ -362,9 +362,9 @@ __global__ void __launch_bounds__(128) k_query(Dev d, int n_surf, int nb_tri, in
 // ---- CCD narrow phase ------------------------------------------------------------
 // Earliest root in [t0, 1] of c0 + c1 t + c2 t^2 + c3 t^3: the interval is cut
 // at the roots of the derivative into monotone pieces; the first piece that
-// starts at a zero or changes sign is bisected (at most 40 halvings, to
-// FP32 resolution).  -1 if none; a cubic that vanishes identically (coplanar
-// motion) has no root.
+// starts at a zero or changes sign is narrowed by false position (Illinois
+// variant; plain halving after 16 steps) to a bracket of 1e-7.  -1 if none;
+// a cubic that vanishes identically (coplanar motion) has no root.
 __device__ __forceinline__ float cubic_first_root(float c0, float c1, float c2, float c3, float t0) {
     if (!(fabsf(c0) + fabsf(c1) + fabsf(c2) + fabsf(c3) > 0.f)) return -1.f;
     float cut[4];
@@ -390,17 +390,30 @@ __device__ __forceinline__ float cubic_first_root(float c0, float c1, float c2, 
         float lo = cut[k], hi = cut[k + 1];
         float flo = ((c3 * lo + c2) * lo + c1) * lo + c0;
         const float fhi = ((c3 * hi + c2) * hi + c1) * hi + c0;
+        float fh = fhi;
         if (flo == 0.f) return lo;
-        if ((flo < 0.f) == (fhi < 0.f) && fhi != 0.f) continue;
-        for (int it = 0; it < 40 && hi - lo > 1e-7f; ++it) {
-            const float mid = 0.5f * (lo + hi);
-            const float fm = ((c3 * mid + c2) * mid + c1) * mid + c0;
-            if (fm == 0.f) return mid;
+        if ((flo < 0.f) == (fh < 0.f) && fh != 0.f) continue;
+        if (fh == 0.f) return hi;
+        // Illinois false position: the secant point of the bracket, and the
+        // value kept at an end that stays twice in a row halved, so that both
+        // ends close in; the midpoint where rounding puts the secant point
+        // outside the open bracket, and from step 16 on
+        int side = 0;
+        for (int it = 0; it < 64 && hi - lo > 1e-7f; ++it) {
+            float m = it < 16 ? (lo * fh - hi * flo) / (fh - flo) : 0.5f * (lo + hi);
+            if (!(m > lo && m < hi)) m = 0.5f * (lo + hi);
+            const float fm = ((c3 * m + c2) * m + c1) * m + c0;
+            if (fm == 0.f) return m;
             if ((fm < 0.f) == (flo < 0.f)) {
-                lo = mid;
+                lo = m;
                 flo = fm;
+                if (side == -1) fh *= 0.5f;
+                side = -1;
             } else {
-                hi = mid;
+                hi = m;
+                fh = fm;
+                if (side == 1) flo *= 0.5f;
+                side = 1;
             }
         }
         return hi;
