@@ -252,23 +252,64 @@ __device__ __forceinline__ bool sphere_far(float4 s, float3 x, float reach) {
 }
 
 // Nearest admissible triangle of vertex a (boundary index k) among the
+// The hits of one lane within `tol` of its best value so far (the tie
+// window): up to two, else `full` and the query scans again.
+struct TieWindow {
+    float ta, tb;
+    int fa, fb, n;
+    bool full;
+    __device__ void add(float t, int f, float best, float tol) {
+        if (!(t <= best + tol)) return;
+        if (n == 0) {
+            ta = t;
+            fa = f;
+            n = 1;
+        } else if (n == 1) {
+            tb = t;
+            fb = f;
+            n = 2;
+        } else {
+            full = true;
+        }
+    }
+    // the best value has moved down to `best`: drop what left the window
+    __device__ void shrink(float best, float tol) {
+        const float w = best + tol;
+        if (n == 2 && !(tb <= w)) n = 1;
+        if (n >= 1 && !(ta <= w)) {
+            ta = tb;
+            fa = fb;
+            n -= 1;
+        }
+    }
+    // lowest index among the hits by `lim`, -1 if none
+    __device__ int lowest(float lim) const {
+        int f = -1;
+        if (n >= 1 && ta <= lim) f = fa;
+        if (n >= 2 && tb <= lim && (f < 0 || fb < f)) f = fb;
+        return f;
+    }
+};
+
 // triangles of this lane's neighbour cells (n = lane, lane + Q, ... < 27):
-// pass 0 returns the nearest distance within r (or -1), pass 1 the lowest
-// triangle index within `lim` (or -1).  Triangles whose bounding sphere is
-// farther than r (plus the rounding slack) are skipped before the exact test.
+// pass 0 returns the nearest distance within r (or -1) and keeps the hits
+// of its tie window (1e-5 r) in `win`; pass 1 (only when a window was full)
+// the lowest triangle index within `lim` (or -1).  Triangles whose bounding
+// sphere is farther than r (plus the rounding slack) are skipped before the
+// exact test.
 template <int Q>
 __device__ __forceinline__ float nearest_tri(const Dev &d, int k, float3 xa, float3 Xa, float3 ua, int3 cell,
                                             int nb, int lane, float r, float slack, int pass, float lim,
-                                            int &pair) {
+                                            int &pair, TieWindow &win) {
     const int g0 = d.ring_off[k], g1 = d.ring_off[k + 1];
     float best = -1.f;
     for (int n = lane; n < 27; n += Q) {
         const int b = neighbour_bucket(cell, n, nb);
         const int e1 = d.cell_start[b + 1];
         for (int e = d.cell_start[b]; e < e1; ++e) {
+            if (sphere_far(d.cell_tri_sph[e], xa, r + slack)) continue;
             const int t = d.cell_tri[e];
             if (pass == 1 && pair >= 0 && t >= pair) continue;
-            if (sphere_far(d.tri_sphere[t], xa, r + slack)) continue;
             const int4 v = d.tri[t];
             bool adjacent = false;
             for (int g = g0; g < g1 && !adjacent; ++g) {
@@ -282,7 +323,13 @@ __device__ __forceinline__ float nearest_tri(const Dev &d, int k, float3 xa, flo
                                           w.x * pa.z + w.y * pb.z + w.z * pc.z);
             const float dist = sqrtf(dot(qp, qp));
             if (dist > r) continue;
-            if (pass == 0 && (best < 0.f || dist < best)) best = dist;
+            if (pass == 0) {
+                if (best < 0.f || dist < best) {
+                    best = dist;
+                    win.shrink(best, 1e-5f * r);
+                }
+                win.add(dist, t, best, 1e-5f * r);
+            }
             if (pass == 1 && dist <= lim) pair = t;
         }
     }
@@ -327,7 +374,8 @@ __global__ void __launch_bounds__(128) k_query(Dev d, int n_surf, int nb_tri, in
     const float3 xa = Xa + ua;
     const int3 cell = active ? cell_of(d, xa, 1.0f / c) : make_int3(0, 0, 0);
     int pair = -1;
-    float best = active ? nearest_tri<Q>(d, k, xa, Xa, ua, cell, nb_tri, lane, r, slack, 0, 0.f, pair) : -1.f;
+    TieWindow win = {0.f, 0.f, -1, -1, 0, false};
+    float best = active ? nearest_tri<Q>(d, k, xa, Xa, ua, cell, nb_tri, lane, r, slack, 0, 0.f, pair, win) : -1.f;
     best = group_min_dist(best);
     bool inside = false;
     if (best >= 0.f) {  // uniform over the group
@@ -339,9 +387,8 @@ __global__ void __launch_bounds__(128) k_query(Dev d, int n_surf, int nb_tri, in
             const int b = neighbour_bucket(tcell, n, nb_tet);
             const int e1 = d.tet_start[b + 1];
             for (int e = d.tet_start[b]; e < e1 && !inside; ++e) {
-                const int j = d.cell_tet[e];
-                if (sphere_far(d.tet_sphere[j], xa, tslack)) continue;
-                const int4 v = d.tet_v[j];
+                if (sphere_far(d.cell_tet_sph[e], xa, tslack)) continue;
+                const int4 v = d.tet_v[d.cell_tet[e]];
                 if (v.x == a || v.y == a || v.z == a || v.w == a) continue;
                 inside = origin_in_tet(rel(d, v.x, Xa, ua), rel(d, v.y, Xa, ua), rel(d, v.z, Xa, ua),
                                        rel(d, v.w, Xa, ua));
@@ -350,7 +397,13 @@ __global__ void __launch_bounds__(128) k_query(Dev d, int n_surf, int nb_tri, in
     }
     const unsigned group_mask = ((1u << Q) - 1u) << (threadIdx.x & 31 & ~(Q - 1));
     inside = (__ballot_sync(0xffffffffu, inside) & group_mask) != 0;
-    if (inside) nearest_tri<Q>(d, k, xa, Xa, ua, cell, nb_tri, lane, r, slack, 1, best + 1e-5f * r, pair);
+    const bool rescan = group_min_index(win.full ? 0 : -1) == 0;  // on every lane of the warp
+    if (inside) {
+        if (rescan)
+            nearest_tri<Q>(d, k, xa, Xa, ua, cell, nb_tri, lane, r, slack, 1, best + 1e-5f * r, pair, win);
+        else
+            pair = win.lowest(best + 1e-5f * r);
+    }
     pair = group_min_index(pair);
     if (active && lane == 0) {
         d.contact[a] = pair;
@@ -469,45 +522,6 @@ __device__ __forceinline__ void rel_path(const Dev &d, int k, float3 Xa, float3 
     B = (f3(__ldg(d.u + k)) - ua) - (utk - uta);
 }
 
-// The hits of one lane within 1e-5 in time of its earliest so far (the
-// tie window): up to two, else `full` and the query scans again.
-struct TieWindow {
-    float ta, tb;
-    int fa, fb, n;
-    bool full;
-    __device__ void add(float t, int f, float best) {
-        if (!(t <= best + 1e-5f)) return;
-        if (n == 0) {
-            ta = t;
-            fa = f;
-            n = 1;
-        } else if (n == 1) {
-            tb = t;
-            fb = f;
-            n = 2;
-        } else {
-            full = true;
-        }
-    }
-    // the earliest time has moved down to `best`: drop what left the window
-    __device__ void shrink(float best) {
-        const float w = best + 1e-5f;
-        if (n == 2 && !(tb <= w)) n = 1;
-        if (n >= 1 && !(ta <= w)) {
-            ta = tb;
-            fa = fb;
-            n -= 1;
-        }
-    }
-    // lowest index among the hits by `lim`, -1 if none
-    __device__ int lowest(float lim) const {
-        int f = -1;
-        if (n >= 1 && ta <= lim) f = fa;
-        if (n >= 2 && tb <= lim && (f < 0 || fb < f)) f = fb;
-        return f;
-    }
-};
-
 // earliest admissible impact of vertex a (boundary index k) among the
 // triangles of this lane's cells: pass 0 returns the earliest time (or -1)
 // and keeps the hits of its tie window in `win`; pass 1 (only when a window
@@ -522,9 +536,9 @@ __device__ __forceinline__ float earliest_impact(const Dev &d, int k, float3 Xa,
         const int b = neighbour_bucket(cell, n, nb);
         const int e1 = d.cell_start[b + 1];
         for (int e = d.cell_start[b]; e < e1; ++e) {
+            if (sphere_far(d.cell_tri_sph[e], mid, Ra + slack)) continue;
             const int t = d.cell_tri[e];
             if (pass == 1 && pair >= 0 && t >= pair) continue;
-            if (sphere_far(d.tri_sphere[t], mid, Ra + slack)) continue;
             const int4 v = d.tri[t];
             bool adjacent = false;
             for (int g = g0; g < g1 && !adjacent; ++g) {
@@ -544,9 +558,9 @@ __device__ __forceinline__ float earliest_impact(const Dev &d, int k, float3 Xa,
             if (pass == 0) {
                 if (best < 0.f || ti < best) {
                     best = ti;
-                    win.shrink(best);
+                    win.shrink(best, 1e-5f);
                 }
-                win.add(ti, t, best);
+                win.add(ti, t, best, 1e-5f);
             }
             if (pass == 1 && ti <= lim) pair = t;
         }
@@ -842,9 +856,9 @@ __device__ __forceinline__ float earliest_edge(const Dev &d, int e, int4 ev, flo
             if (pass == 0) {
                 if (best < 0.f || t < best) {
                     best = t;
-                    win.shrink(best);
+                    win.shrink(best, 1e-5f);
                 }
-                win.add(t, f, best);
+                win.add(t, f, best, 1e-5f);
             }
             if (pass == 1 && t <= lim) pair = f;
         }
@@ -1028,14 +1042,14 @@ void launch_detect(const Dev &d, const CollideDims &c, int n_free, cudaStream_t 
     exclusive_scan(d.cell_fill, d.cell_start, c.n_buckets, d.scan_tmp, s);
     cudaMemsetAsync(d.cell_fill, 0, sizeof(int) * (size_t)c.n_buckets, s);
     k_fill<3><<<blocks_for(c.n_tris, 256), 256, 0, s>>>(d, d.tri_sphere, c.n_tris, c.n_buckets, c.radius,
-                                                        d.cell_start, d.cell_fill, d.cell_tri);
+                                                        d.cell_start, d.cell_fill, d.cell_tri, d.cell_tri_sph);
     cudaMemsetAsync(d.tet_fill, 0, sizeof(int) * (size_t)c.n_tet_buckets, s);
     k_count<4><<<blocks_for(c.n_tets, 256), 256, 0, s>>>(d, d.tet_sphere, c.n_tets, c.n_tet_buckets, c.radius,
                                                          d.tet_fill);
     exclusive_scan(d.tet_fill, d.tet_start, c.n_tet_buckets, d.scan_tmp, s);
     cudaMemsetAsync(d.tet_fill, 0, sizeof(int) * (size_t)c.n_tet_buckets, s);
     k_fill<4><<<blocks_for(c.n_tets, 256), 256, 0, s>>>(d, d.tet_sphere, c.n_tets, c.n_tet_buckets, c.radius,
-                                                        d.tet_start, d.tet_fill, d.cell_tet);
+                                                        d.tet_start, d.tet_fill, d.cell_tet, d.cell_tet_sph);
     // narrow phase
     k_query<<<blocks_for((long long)c.n_surf * kQueryLanes, 128), 128, 0, s>>>(d, c.n_surf, c.n_buckets,
                                                                               c.n_tet_buckets, c.radius);
@@ -1057,7 +1071,7 @@ void launch_ccd(const Dev &d, const CollideDims &c, int n_free, cudaStream_t s) 
     exclusive_scan(d.cell_fill, d.cell_start, c.n_buckets, d.scan_tmp, s);
     cudaMemsetAsync(d.cell_fill, 0, sizeof(int) * (size_t)c.n_buckets, s);
     k_fill<5><<<blocks_for(c.n_tris, 256), 256, 0, s>>>(d, d.tri_sphere, c.n_tris, c.n_buckets, 0.f, d.cell_start,
-                                                        d.cell_fill, d.cell_tri);
+                                                        d.cell_fill, d.cell_tri, d.cell_tri_sph);
     k_ccd<<<blocks_for((long long)c.n_surf * kQueryLanes, 128), 128, 0, s>>>(d, c.n_surf, c.n_buckets);
     build_reverse_lists(d, c, n_free, s);
     if (!c.ee_on || c.n_edges <= 0) return;

@@ -359,10 +359,12 @@ size_t carve(const vbd_ctx *c, char *base, Dev *d) {
         t.cell_start = (int *)take(4 * (nb + 1));
         t.cell_fill = (int *)take(4 * nb);
         t.cell_tri = (int *)take(4 * nt);
+        t.cell_tri_sph = (float4 *)take(16 * nt);
         const size_t nbt = (size_t)c->n_tet_buckets;
         t.tet_start = (int *)take(4 * (nbt + 1));
         t.tet_fill = (int *)take(4 * nbt);
         t.cell_tet = (int *)take(4 * T);
+        t.cell_tet_sph = (float4 *)take(16 * T);
         const size_t ne = c->edges.size() / 2, nbe = (size_t)c->n_edge_buckets;
         t.scan_tmp = (int *)take(4 * (size_t)vbd::scan_tmp_needed((int)std::max({nb, nbt, nf, nbe})));
         t.cell_size = (unsigned *)take(16);

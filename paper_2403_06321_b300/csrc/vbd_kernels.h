@@ -65,9 +65,11 @@ struct Dev {
     int *cell_start;  // n_buckets + 1: triangles of each hash bucket (by centroid cell)
     int *cell_fill;   // n_buckets
     int *cell_tri;    // n_tris
+    float4 *cell_tri_sph; // n_tris: the sphere of each cell_tri entry, in table order
     int *tet_start;   // n_tet_buckets + 1: tets of each hash bucket (by centroid cell)
     int *tet_fill;    // n_tet_buckets
     int *cell_tet;    // T
+    float4 *cell_tet_sph; // T: the sphere of each cell_tet entry, in table order
     int *scan_tmp;    // block totals of the prefix sums
     unsigned *cell_size;  // bits (float) of the largest centroid-to-corner distance: [0] triangles, [1] tets,
                           // [2] the largest half path of a boundary vertex (CCD)
