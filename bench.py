@@ -74,9 +74,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batched, adjoint and self-collision comparisons")
+                    help="skip the batched, adjoint, self-collision and Chebyshev comparisons")
     ap.add_argument("--batch-meshes", type=int, default=4096)
-    ap.add_argument("--only", choices=["batched", "adjoint", "self_collision", "small_configs"], default=None,
+    ap.add_argument("--only", choices=["batched", "adjoint", "self_collision", "chebyshev", "small_configs"],
+                    default=None,
                     help="run one of the comparisons alone and print it as the JSON line (for profiling)")
     args = ap.parse_args(argv)
     if not args.n:
@@ -431,6 +432,38 @@ def run_adjoint(args) -> dict:
             "ratio_vs_plain": v_a / v_f, "ms_backward": t_a * 1e3, "ms_forward": t_f * 1e3}
 
 
+def run_chebyshev(args) -> dict:
+    """Chebyshev acceleration (Sec. 3.8, Eqs. 18-19) with rho = 0.95 on the
+    benchmark cube, against the same mesh, colouring and iterations without
+    it: the extra k_cheby pass per iteration (x, the two previous iterates
+    and the collision flags) is the whole cost."""
+    import numpy as np
+    import torch
+    from paper_2403_06321_b300 import synth, vbd
+    m, cfg = synth.large_cube(args.n)
+    colors = synth.kuhn_coloring(m.grid_ijk)
+    iters, steps = args.iters, 3
+    out = {}
+    for rho in (0.95, 0.0):
+        params = vbd.make_params(gravity=cfg.gravity, ground_on=cfg.ground_on, k_c=cfg.k_c,
+                                 init_mode=cfg.init_mode, det_eps=cfg.det_eps, cheby_rho=rho)
+        stream = torch.cuda.Stream()
+        sim = vbd.Sim(m, params, colors=colors, stream=stream)
+        n_free = sim.info.n_free
+        zeros = np.zeros_like(m.rest)
+        sim.set_state(m.rest, zeros)
+        sim.step(cfg.h, iters)  # warm-up (graph capture)
+        sim.set_state(m.rest, zeros)
+        t = _timed(stream, lambda: sim.step(cfg.h, iters), steps)
+        sim.sync_status()
+        sim.close()
+        out[rho] = (n_free * iters * steps / t, t * 1e3 / steps)
+    return {"workload": "large_cube %d^3, %d iterations/step, rho = 0.95" % (args.n, iters),
+            "value": out[0.95][0], "unit": UNIT, "ms_per_step": out[0.95][1],
+            "value_without": out[0.0][0], "ms_per_step_without": out[0.0][1],
+            "ratio_vs_plain": out[0.95][0] / out[0.0][0]}
+
+
 def run_self_collision(args) -> dict:
     """Self-collision (vertex-triangle DCD at each step start, contact forces
     in the sweep, x^new + copy-back per colour) on the slab scene at
@@ -699,6 +732,7 @@ def run_ours(args):
         line["batched"] = run_batched(args)
         line["adjoint"] = run_adjoint(args)
         line["self_collision"] = run_self_collision(args)
+        line["chebyshev"] = run_chebyshev(args)
         line["small_configs"] = run_small_configs(args)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = run_cpu_baseline()
@@ -712,7 +746,7 @@ def run_only(args) -> int:
     build()
     torch.cuda.set_device(0)
     fn = {"batched": run_batched, "adjoint": run_adjoint, "self_collision": run_self_collision,
-          "small_configs": run_small_configs}[args.only]
+          "chebyshev": run_chebyshev, "small_configs": run_small_configs}[args.only]
     print(json.dumps({"only": args.only, args.only: fn(args)}), flush=True)
     return 0
 

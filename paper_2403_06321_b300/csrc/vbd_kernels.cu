@@ -821,13 +821,18 @@ __device__ __forceinline__ void cheby_vertex(const Dev &d, int i, int n, float o
     float4 *hist = d.cheb[n & 1];
     const float4 xb = COH ? __ldcg(d.u + i) : d.u[i];
     float4 xn = xb;
+    // The history moves through L2 as a stream (evict-first), so that it does
+    // not displace the positions the colour passes gather from L2.
     if (n >= 2 && xb.w == 0.f) {
-        const float4 q = COH ? __ldcg(hist + i) : hist[i];
+        const float4 q = COH ? __ldcg(hist + i) : __ldcs(hist + i);
         xn = make_float4(omega * (xb.x - q.x) + q.x, omega * (xb.y - q.y) + q.y,
                          omega * (xb.z - q.z) + q.z, xb.w);
         d.u[i] = xn;
     }
-    hist[i] = xn;
+    if (COH)
+        hist[i] = xn;
+    else
+        __stcs(hist + i, xn);
 }
 
 __global__ void k_cheby(Dev d, int n_free, int n, float omega) {
