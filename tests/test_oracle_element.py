@@ -119,7 +119,8 @@ def test_tet_hessian_blocks_match_fd_of_gradient(orc, seed):
         for s in range(3):
             xp, xm = x.copy(), x.copy()
             xp[l, s] += h; xm[l, s] -= h
-            num[:, 3 * l + s] = ((orc.tet_grad(xp, B, V, mu, lam) - orc.tet_grad(xm, B, V, mu, lam)) / (2 * h)).reshape(-1)
+            dg = orc.tet_grad(xp, B, V, mu, lam) - orc.tet_grad(xm, B, V, mu, lam)
+            num[:, 3 * l + s] = (dg / (2 * h)).reshape(-1)
     assert np.allclose(H, num, rtol=1e-6, atol=1e-6 * np.abs(H).max())
     assert np.allclose(H, H.T, atol=1e-9 * np.abs(H).max())
     for k in range(4):

@@ -58,23 +58,27 @@ MUTANTS = [
      "for (int w = 0; w + 1 < p->n_walls && w < ORC_MAX_WALLS; ++w)", "test_oracle_walls.py"),
     ("wall_friction_first_normal", "plane_friction(p, h, nh[k], x + 3 * i", "plane_friction(p, h, nh[0], x + 3 * i",
      "test_oracle_walls.py"),
-    ("wall_energy_dropped", "    for (int k = 0; k < np; ++k) {\n        double d = c[k] - dot3(x + 3 * i, nh[k]);\n        if (d > 0.0) G += 0.5",
-     "    for (int k = 0; k < 0; ++k) {\n        double d = c[k] - dot3(x + 3 * i, nh[k]);\n        if (d > 0.0) G += 0.5",
+    ("wall_energy_dropped",
+     "    for (int k = 0; k < np; ++k) {\n        double d = c[k] - dot3(x + 3 * i, nh[k]);\n"
+     "        if (d > 0.0) G += 0.5",
+     "    for (int k = 0; k < 0; ++k) {\n        double d = c[k] - dot3(x + 3 * i, nh[k]);\n"
+     "        if (d > 0.0) G += 0.5",
      "test_oracle_walls.py"),
     ("subspace_guess_not_projected", "        if (m->sub_dim[i] < 3) {\n            /* a subspace-constrained",
      "        if (0) {\n            /* a subspace-constrained", "test_oracle_subspace.py"),
     ("subspace_rhs_first_axis", "b[a] = dot3(q + 3 * a, f);", "b[a] = dot3(q, f);", "test_oracle_subspace.py"),
-    ("subspace_step_first_axis_only", "    for (int a = 0; a < L; ++a)\n        for (int r = 0; r < 3; ++r) dx[r] +=",
+    ("subspace_step_first_axis_only",
+     "    for (int a = 0; a < L; ++a)\n        for (int r = 0; r < 3; ++r) dx[r] +=",
      "    for (int a = 0; a < 1; ++a)\n        for (int r = 0; r < 3; ++r) dx[r] +=", "test_oracle_subspace.py"),
-    ("subspace_2x2_solve_sign", "dz[1] = (A[0] * b[1] - A[2] * b[0]) / det;", "dz[1] = (A[0] * b[1] + A[2] * b[0]) / det;",
-     "test_oracle_subspace.py"),
+    ("subspace_2x2_solve_sign", "dz[1] = (A[0] * b[1] - A[2] * b[0]) / det;",
+     "dz[1] = (A[0] * b[1] + A[2] * b[0]) / det;", "test_oracle_subspace.py"),
     ("plane_basis_not_orthogonalised", "for (int r = 0; r < 3; ++r) e[r] -= en * d[r];", "",
      "test_oracle_subspace.py"),
     ("ccd_cubic_term_dropped", "cross3(A[1], B[2], tmp); c[1] += dot3(A[0], tmp);", "", "test_oracle_ccd.py"),
     ("ccd_inside_test_two_weights", "if (w[0] >= 0.0 && w[1] >= 0.0 && w[2] >= 0.0) return t;",
      "if (w[0] >= 0.0 && w[1] >= 0.0) return t;", "test_oracle_ccd.py"),
-    ("ccd_latest_impact_wins", "if (t >= 0.0 && t < best - 1e-5) {", "if (t >= 0.0 && (best > 1.5 || t > best + 1e-5)) {",
-     "test_oracle_ccd.py"),
+    ("ccd_latest_impact_wins", "if (t >= 0.0 && t < best - 1e-5) {",
+     "if (t >= 0.0 && (best > 1.5 || t > best + 1e-5)) {", "test_oracle_ccd.py"),
     ("ccd_pair_uses_nearest_point", "    if (m->contact_ccd[a]) {\n        /* CCD pair",
      "    if (0) {\n        /* CCD pair", "test_oracle_ccd.py"),
     ("ee_crossing_parameters_swapped", "double s = dot3(wg, n) / nn, u = dot3(we, n) / nn;",
@@ -83,8 +87,8 @@ MUTANTS = [
      "c[0] = 1.0 - s; c[1] = s; c[2] = -(1.0 - u); c[3] = -u;", "test_oracle_ccd.py"),
     ("ee_pair_not_carried", "if (ee_depth(m, e, x, v, c) > 0.0) m->ee_carried[e] = 1;", "if (0) m->ee_carried[e] = 1;",
      "test_oracle_ccd.py"),
-    ("ee_crossing_test_one_segment", "if (s >= 0.0 && s <= 1.0 && u >= 0.0 && u <= 1.0) {", "if (s >= 0.0 && s <= 1.0) {",
-     "test_oracle_ccd.py"),
+    ("ee_crossing_test_one_segment", "if (s >= 0.0 && s <= 1.0 && u >= 0.0 && u <= 1.0) {",
+     "if (s >= 0.0 && s <= 1.0) {", "test_oracle_ccd.py"),
 ]
 
 
