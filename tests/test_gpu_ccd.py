@@ -192,3 +192,16 @@ def test_crossed_bars_match_oracle(orc):
     err, x, counts = _run_ee(orc, cat, pd, v0, 1 / 60, 20, 10)
     print("crossed bars: err/bbox %.2e, edge-edge pairs %s" % (err, counts))
     assert err <= TOL
+
+
+def test_interpenetrating_slabs_edge_pairs_match_oracle(orc):
+    """The self-collision slab scene (two jittered slabs sunk into each
+    other, 936 boundary edges) with vertex-triangle and edge-edge CCD every 5
+    iterations: about a hundred edge pairs held at once, compared exactly
+    after every step, positions within 1e-5 of the bounding box."""
+    m, cfg, _ = synth.colliding_slabs(n=8, seed=41)
+    pd = params_of(cfg, ccd_interval=5, ccd_edges=True)
+    err, x, counts = _run_ee(orc, m, pd, np.zeros_like(m.rest), cfg.h, cfg.iters, 6)
+    print("slabs with edge pairs: err/bbox %.2e, edge-edge pairs %s" % (err, counts))
+    assert min(counts) >= 50
+    assert err <= TOL
