@@ -194,6 +194,19 @@ def test_crossed_bars_match_oracle(orc):
     assert err <= TOL
 
 
+def test_interpenetrating_slabs_with_vertex_ccd_match_oracle(orc):
+    """The slab scene pushing apart with vertex-triangle CCD every 3
+    iterations beside the step-start DCD: DCD pairs for the vertices inside
+    the other slab, CCD pairs for those that cross a face during a step;
+    every pair compared exactly after every step."""
+    m, cfg, _ = synth.colliding_slabs(n=8, seed=43)
+    pd = params_of(cfg, ccd_interval=3)
+    err, x, v, counts = _run(orc, m, pd, np.zeros_like(m.rest), cfg.h, cfg.iters, 6)
+    print("slabs with vertex CCD: err/bbox %.2e, CCD pairs %s" % (err, counts))
+    assert max(counts) >= 2
+    assert err <= TOL
+
+
 def test_interpenetrating_slabs_edge_pairs_match_oracle(orc):
     """The self-collision slab scene (two jittered slabs sunk into each
     other, 936 boundary edges) with vertex-triangle and edge-edge CCD every 5
