@@ -218,3 +218,43 @@ def test_interpenetrating_slabs_edge_pairs_match_oracle(orc):
     print("slabs with edge pairs: err/bbox %.2e, edge-edge pairs %s" % (err, counts))
     assert min(counts) >= 50
     assert err <= TOL
+
+
+def test_large_slabs_ccd_sampled(orc):
+    """The slab scene at bench size (900,010 vertices, 734,352 boundary
+    triangles) with the upper slab thrown down at 3 m/s (one edge per step)
+    and one CCD per step: after the step-start DCD and the CCD before the
+    first iteration (paths x^t -> initial guess), the pairs of sampled
+    boundary vertices without a step-start pair, each recomputed alone by
+    the oracle (brute force over every triangle)."""
+    m, cfg, u0 = synth.colliding_slabs(n=300, layers=4, seed=31)
+    pd = params_of(cfg, ccd_interval=cfg.iters)
+    x = _f32(m.rest)
+    v0 = np.zeros_like(x)
+    v0[u0:, 2] = -3.0
+    sim = vbd.Sim(m, vbd.make_params(**pd), colors=synth.kuhn_coloring(m.grid_ijk))
+    try:
+        tris = vbd.vbd_get_surface(sim.ctx)
+        sim.set_state(x, v0)
+        vbd.vbd_begin_step(sim.ctx, cfg.h)
+        dcd = vbd.vbd_get_contacts(sim.ctx, m.n_verts)
+        xg, _ = sim.get_state()  # the initial guess
+        x0 = xg.cpu().numpy().astype(np.float64)
+        vbd.vbd_iterate(sim.ctx, 1)  # the CCD runs before iteration 1
+        got = vbd.vbd_get_contacts(sim.ctx, m.n_verts)
+        vbd.vbd_end_step(sim.ctx)
+        sim.sync_status()
+    finally:
+        sim.close()
+    model = orc.Model.from_mesh(m)
+    assert np.array_equal(tris, model.tris())
+    surf = np.unique(tris)
+    free = surf[dcd[surf] < 0]  # swept by the CCD
+    caught = free[got[free] >= 0]
+    print("large slabs: %d step-start pairs, %d CCD pairs" % ((dcd >= 0).sum(), caught.size))
+    assert caught.size > 1000
+    rng = np.random.default_rng(33)
+    sample = np.concatenate([rng.choice(caught, 30, replace=False), rng.choice(free, 30, replace=False)])
+    want = np.array([model.ccd_vertex(x, x0, a)[0] for a in sample])
+    bad = np.nonzero(got[sample] != want)[0]
+    assert bad.size == 0, (sample[bad], got[sample][bad], want[bad])
