@@ -135,6 +135,7 @@ def lib():
             "orc_ccd_vertex": (C.c_int, [vp, _dp, _dp, C.c_int, C.POINTER(C.c_double), _dp]),
             "orc_ccd": (C.c_int, [vp, _dp, _dp]),
             "orc_ccd_edges": (None, [vp, _dp, _dp]),
+            "orc_ee_first_hit": (C.c_int, [vp, _dp, _dp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "orc_cubic_first_root": (C.c_double, [_dp, C.c_double]),
             "orc_model_contact_weights": (None, [vp, _dp, _up]),
             "orc_ee_impact": (C.c_double, [_dp, _dp, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
@@ -439,6 +440,14 @@ class Model:
         w = np.zeros(3)
         T = lib().orc_ccd_vertex(self._h, _d(x0).reshape(-1), _d(x1).reshape(-1), int(a), C.byref(toi), w)
         return int(T), float(toi.value), w
+
+    def ee_first_hit(self, x0, x1, e):
+        """(partner edge or -1, s, u): the edge-edge CCD's search for edge e
+        alone (Sec. 3.5), before the pairing rules."""
+        s, u = C.c_double(-1.0), C.c_double(-1.0)
+        f = lib().orc_ee_first_hit(self._h, _d(x0).reshape(-1), _d(x1).reshape(-1), int(e), C.byref(s),
+                                   C.byref(u))
+        return int(f), float(s.value), float(u.value)
 
     def edges(self) -> np.ndarray:
         e = np.zeros(2 * lib().orc_model_n_edges(self._h), np.int32)

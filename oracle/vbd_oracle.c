@@ -977,27 +977,34 @@ static int shares_tet(const orc_model *m, int a, int q) {
  * parameters; the normal is the edges' unit common perpendicular at x1,
  * oriented along x_b - x_a there and frozen for the pair's life (a pair
  * with x_b - x_a perpendicular to it there is dropped). */
+int orc_ee_first_hit(const orc_model *m, const double *x0, const double *x1, int e, double *s_out,
+                     double *u_out) {
+    const int p0 = m->edges[2 * e], p1 = m->edges[2 * e + 1];
+    double best = 2.0;
+    int found = -1;
+    for (int f = 0; f < m->n_edges; ++f) {
+        const int q0 = m->edges[2 * f], q1 = m->edges[2 * f + 1];
+        if (shares_tet(m, p0, q0) || shares_tet(m, p0, q1) || shares_tet(m, p1, q0) || shares_tet(m, p1, q1))
+            continue;
+        double s, u;
+        double t = orc_ee_impact(x0, x1, p0, p1, q0, q1, &s, &u);
+        if (t >= 0.0 && t < best - 1e-5) {
+            best = t;
+            found = f;
+            *s_out = s;
+            *u_out = u;
+        }
+    }
+    return found;
+}
+
 static void ee_ccd(orc_model *m, const double *x0, const double *x1) {
     int *found = (int *)malloc(sizeof(int) * (size_t)m->n_edges + 1);
     double *su = (double *)malloc(sizeof(double) * 2 * (size_t)m->n_edges + 2);
     for (int e = 0; e < m->n_edges; ++e) {
         found[e] = -1;
         if (m->ee_carried[e]) continue;
-        const int p0 = m->edges[2 * e], p1 = m->edges[2 * e + 1];
-        double best = 2.0;
-        for (int f = 0; f < m->n_edges; ++f) {
-            const int q0 = m->edges[2 * f], q1 = m->edges[2 * f + 1];
-            if (shares_tet(m, p0, q0) || shares_tet(m, p0, q1) || shares_tet(m, p1, q0) || shares_tet(m, p1, q1))
-                continue;
-            double s, u;
-            double t = orc_ee_impact(x0, x1, p0, p1, q0, q1, &s, &u);
-            if (t >= 0.0 && t < best - 1e-5) {
-                best = t;
-                found[e] = f;
-                su[2 * e] = s;
-                su[2 * e + 1] = u;
-            }
-        }
+        found[e] = orc_ee_first_hit(m, x0, x1, e, su + 2 * e, su + 2 * e + 1);
     }
     for (int e = 0; e < m->n_edges; ++e) {
         if (m->ee_carried[e]) continue;

@@ -106,6 +106,13 @@ int orc_ccd_vertex(const orc_model *m, const double *x0, const double *x1, int a
 int orc_ccd(orc_model *m, const double *x0, const double *x1);
 /* the edge-edge part of the CCD alone (pairs held by the edges) */
 void orc_ccd_edges(orc_model *m, const double *x0, const double *x1);
+/* Sec. 3.5, one edge of the edge-edge CCD: the boundary edge that edge e
+ * (an index of orc_model_edges) hits first along the straight paths x0 -> x1
+ * (ties within 1e-5 in time: the lowest index), among the edges none of
+ * whose vertices shares a tet with one of e's; -1 if none, else the impact
+ * parameters on e and on the partner in s_out, u_out. */
+int orc_ee_first_hit(const orc_model *m, const double *x0, const double *x1, int e, double *s_out,
+                     double *u_out);
 /* Earliest root in [0, 1] of c0 + c1 t + c2 t^2 + c3 t^3 at or after t_min
  * whose point passes `accept`; -1 if none (exposed for the pins). */
 double orc_cubic_first_root(const double c[4], double t_min);

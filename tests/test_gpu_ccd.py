@@ -258,3 +258,41 @@ def test_large_slabs_ccd_sampled(orc):
     want = np.array([model.ccd_vertex(x, x0, a)[0] for a in sample])
     bad = np.nonzero(got[sample] != want)[0]
     assert bad.size == 0, (sample[bad], got[sample][bad], want[bad])
+
+
+def test_large_slabs_edge_ccd_sampled(orc):
+    """Edge-edge CCD at bench size (1.1M boundary edges) with the upper slab
+    thrown down at 3 m/s: each sampled edge's first hit, recomputed alone by
+    the oracle (brute force over every edge), is the edge's partner or, for
+    a pair found from both sides, held by the partner (lower index)."""
+    m, cfg, u0 = synth.colliding_slabs(n=300, layers=4, seed=31)
+    pd = params_of(cfg, ccd_interval=cfg.iters, ccd_edges=True)
+    x = _f32(m.rest)
+    v0 = np.zeros_like(x)
+    v0[u0:, 2] = -3.0
+    sim = vbd.Sim(m, vbd.make_params(**pd), colors=synth.kuhn_coloring(m.grid_ijk))
+    try:
+        edges, _ = vbd.vbd_get_edge_pairs(sim.ctx, with_partners=False)
+        sim.set_state(x, v0)
+        vbd.vbd_begin_step(sim.ctx, cfg.h)
+        xg, _ = sim.get_state()  # the initial guess
+        x0 = xg.cpu().numpy().astype(np.float64)
+        vbd.vbd_iterate(sim.ctx, 1)  # the CCD runs before iteration 1
+        _, partner = vbd.vbd_get_edge_pairs(sim.ctx)
+        vbd.vbd_end_step(sim.ctx)
+        sim.sync_status()
+    finally:
+        sim.close()
+    model = orc.Model.from_mesh(m)
+    assert np.array_equal(edges, model.edges())
+    held = np.nonzero(partner >= 0)[0]
+    print("large slabs: %d of %d edges hold an edge-edge pair" % (held.size, partner.size))
+    assert held.size > 1000
+    rng = np.random.default_rng(34)
+    sample = np.concatenate([rng.choice(held, 12, replace=False), rng.choice(partner.size, 12, replace=False)])
+    for e in sample:
+        f, _, _ = model.ee_first_hit(x, x0, e)
+        if partner[e] >= 0:
+            assert f == partner[e], (e, f, partner[e])
+        else:
+            assert f < 0 or (f < e and partner[f] == e), (e, f, partner[f] if f >= 0 else None)
