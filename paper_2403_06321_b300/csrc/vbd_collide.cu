@@ -457,14 +457,16 @@ __device__ __forceinline__ float cubic_first_root(float c0, float c1, float c2, 
         // Illinois false position: the secant point of the bracket, and the
         // value kept at an end that stays twice in a row halved, so that both
         // ends close in; the midpoint where rounding puts the secant point
-        // outside the open bracket, and from step 16 on
+        // outside the open bracket, and from step 16 on.  The sign at lo is
+        // that of the first flo throughout (halving only scales the kept values)
+        const bool neg_lo = flo < 0.f;
         int side = 0;
         for (int it = 0; it < 64 && hi - lo > 1e-7f; ++it) {
             float m = it < 16 ? (lo * fh - hi * flo) / (fh - flo) : 0.5f * (lo + hi);
             if (!(m > lo && m < hi)) m = 0.5f * (lo + hi);
             const float fm = ((c3 * m + c2) * m + c1) * m + c0;
             if (fm == 0.f) return m;
-            if ((fm < 0.f) == (flo < 0.f)) {
+            if ((fm < 0.f) == neg_lo) {
                 lo = m;
                 flo = fm;
                 if (side == -1) fh *= 0.5f;
