@@ -43,7 +43,7 @@ CCD_LAUNCHES = 20      # kernels and memsets of one CCD (two prefix sums)
 EE_LAUNCHES = 17       # the edge-edge part of one CCD (two prefix sums)
 EE_CARRY_LAUNCHES = 9  # carrying edge-edge pairs at the step start (one prefix sum)
 CPU_SAMPLE_N = 32      # the CPU legs run a 32^3-cube crop of the same recipe
-CPU_SAMPLE_ITERS = 10
+CPU_SAMPLE_ITERS = 100  # the workload's own iterations per step
 
 
 def parse_args(argv=None):
@@ -76,9 +76,13 @@ def parse_args(argv=None):
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched, adjoint, self-collision and Chebyshev comparisons")
     ap.add_argument("--batch-meshes", type=int, default=4096)
-    ap.add_argument("--only", choices=["batched", "adjoint", "self_collision", "chebyshev", "small_configs"],
+    ap.add_argument("--only", choices=["batched", "adjoint", "self_collision", "chebyshev", "small_configs",
+                                       "paper_scale", "parity"],
                     default=None,
                     help="run one of the comparisons alone and print it as the JSON line (for profiling)")
+    ap.add_argument("--no-paper-scale", action="store_true", help="skip the 320^3-cube comparison")
+    ap.add_argument("--oracle-child", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--budget", type=float, default=0.0, help=argparse.SUPPRESS)
     args = ap.parse_args(argv)
     if not args.n:
         args.n = 300 if args.scene == "slabs" else 100
@@ -239,8 +243,23 @@ def profiled_traffic(workload_key: str, updates_per_launch: float):
         return None
 
 
-def cpu_sample(n_iters_total_seconds: float = 10.0):
-    """The FP64 oracle on a 32^3-cube crop of the same workload recipe."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def crop_description(n: int = CPU_SAMPLE_N, iters: int = CPU_SAMPLE_ITERS) -> str:
+    return ("large_cube recipe on a %d^3-cube crop (%d verts, %d tets): jitter 10%% (seed 1), E=1e6 nu=0.45, "
+            "0.5 m above ground k_c=1e7, h=1/60, %d iterations/step" % (n, (n + 1) ** 3, 6 * n ** 3, iters))
+
+
+def oracle_child(args) -> int:
+    """Child process of the CPU legs: times the oracle library named by
+    VBD_ORACLE_LIB (the serial build, or the OpenMP build on OMP_NUM_THREADS
+    threads) on the crop, `warmup` untimed steps then steps until `budget`
+    seconds or `steps` steps, and prints one JSON line."""
     import numpy as np
     from oracle import oracle
     from paper_2403_06321_b300 import synth
@@ -251,46 +270,77 @@ def cpu_sample(n_iters_total_seconds: float = 10.0):
     x, v = m.rest.copy(), np.zeros_like(m.rest)
     vp = v.copy()
     n_free = int((m.pinned == 0).sum())
-    return model, p, colors, cfg, x, v, vp, n_free
-
-
-def run_cpu_baseline(budget_s: float = 12.0) -> dict:
-    model, p, colors, cfg, x, v, vp, n_free = cpu_sample()
-    t0 = time.perf_counter()
-    steps = 0
-    while True:
+    for _ in range(args.warmup):
         model.step(p, colors, 4, cfg.h, CPU_SAMPLE_ITERS, x, v, vp)
-        steps += 1
-        if time.perf_counter() - t0 >= budget_s or steps >= 50:
+    t0 = time.perf_counter()
+    times = []
+    while len(times) < args.steps:
+        a = time.perf_counter()
+        model.step(p, colors, 4, cfg.h, CPU_SAMPLE_ITERS, x, v, vp)
+        times.append(time.perf_counter() - a)
+        if args.budget > 0 and time.perf_counter() - t0 >= args.budget:
             break
-    dt = time.perf_counter() - t0
-    return {"value": n_free * CPU_SAMPLE_ITERS * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d step(s) x %d iterations of the serial FP64 oracle on a %d^3-cube crop (%d verts) "
-                      "of the same recipe (jitter, material, ground, h)" % (
-                          steps, CPU_SAMPLE_ITERS, CPU_SAMPLE_N, n_free)}
+    print(json.dumps({"n_free": n_free, "iters": CPU_SAMPLE_ITERS, "step_s": times}), flush=True)
+    return 0
+
+
+def run_oracle_child(threads: int, budget_s: float, steps: int, warmup: int) -> dict:
+    """Runs oracle_child in a fresh interpreter (spawned, so no CUDA state is
+    inherited) with the serial build (threads == 1) or the OpenMP build."""
+    from oracle import oracle
+    lib = oracle.build(openmp=threads > 1)
+    env = dict(os.environ, VBD_ORACLE_LIB=lib, OMP_NUM_THREADS=str(threads), OMP_PROC_BIND="spread",
+               OMP_PLACES="cores" if threads > 1 else "threads")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-child", "--steps", str(steps),
+           "--warmup", str(warmup), "--budget", str(budget_s)]
+    res = subprocess.run(cmd, env=env, capture_output=True, text=True, check=True)
+    out = json.loads(res.stdout.strip().splitlines()[-1])
+    out["threads"] = threads
+    return out
+
+
+def run_cpu_baseline(budget_s: float = 10.0) -> dict:
+    """The FP64 oracle as it stands, on this host: the OpenMP build on every
+    core (the vertices of one colour on all threads) and the serial build on
+    one core, each for about budget_s seconds of steps of the crop."""
+    cores = host_cores()
+    res = {}
+    for threads in sorted({1, cores}):
+        r = run_oracle_child(threads, budget_s, 1000, 0)
+        steps = len(r["step_s"])
+        res[threads] = {"value": r["n_free"] * r["iters"] * steps / sum(r["step_s"]), "unit": UNIT,
+                        "cores": threads, "kind": "oracle",
+                        "sample": "%d step(s) of the %s FP64 oracle on %d thread(s): %s" % (
+                            steps, "OpenMP" if threads > 1 else "serial", threads, crop_description())}
+    out = dict(res[cores])
+    if cores > 1:
+        out["single_core"] = res[1]
+        out["build"] = "oracle/vbd_oracle.c with -fopenmp (vertices of one colour on all threads)"
+    return out
 
 
 # --------------------------------------------------------------- reference ---
 
 def run_reference(args):
+    """The reference arm: the oracle (there is no other implementation of the
+    paper), OpenMP build on every host core, timed step by step on a 32^3-cube
+    crop of the benchmark recipe at the workload's 100 iterations per step."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    model, p, colors, cfg, x, v, vp, n_free = cpu_sample()
-    for _ in range(args.warmup):
-        model.step(p, colors, 4, cfg.h, CPU_SAMPLE_ITERS, x, v, vp)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        model.step(p, colors, 4, cfg.h, CPU_SAMPLE_ITERS, x, v, vp)
-    dt = time.perf_counter() - t0
-    value = n_free * CPU_SAMPLE_ITERS * args.steps / dt
-    sample = ("each step: one time step with %d iterations of the serial FP64 oracle on a %d^3-cube crop "
-              "(%d free verts) of the same recipe" % (CPU_SAMPLE_ITERS, CPU_SAMPLE_N, n_free))
+    cores = host_cores()
+    r = run_oracle_child(cores, 0.0, args.steps, args.warmup)
+    dt = sum(r["step_s"])
+    value = r["n_free"] * r["iters"] * args.steps / dt
+    sample = ("each step: one time step (%d iterations) of the %s FP64 oracle on %d thread(s), %s" % (
+        r["iters"], "OpenMP" if cores > 1 else "serial", cores, crop_description()))
+    cfg = workload_config(args, None)
+    cfg["workload"] = crop_description() + " (a bounded sample of: %s)" % cfg["workload"]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args, None),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -753,6 +803,8 @@ def run_only(args) -> int:
 
 def main(argv=None):
     args = parse_args(argv)
+    if args.oracle_child:
+        return oracle_child(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.only:

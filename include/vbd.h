@@ -71,7 +71,8 @@ typedef struct {
     const float *young;           /* host, T: Young's modulus E > 0 [Pa] */
     const float *poisson;         /* host, T: Poisson ratio in (-1, 0.5) */
     const float *density;         /* host, T: mass density > 0 [kg/m^3] */
-    const uint8_t *pinned;        /* host, N: 1 = fixed vertex (Sec. 3.5), or NULL */
+    const uint8_t *pinned;        /* host, N: 1 = fixed vertex, or NULL (Sec. 3.4: a bilateral
+                                     constraint that fixes a vertex is met by never updating it) */
 } vbd_mesh_desc;
 
 typedef struct {
@@ -257,7 +258,10 @@ vbd_status vbd_set_subspaces(vbd_ctx *ctx, int32_t n, const int32_t *vertex, con
 
 /* Sets x^t, v^t and v^{t-1} (3N floats each, caller order, host or device).
  * v_prev == NULL means v^{t-1} = v^t (zero estimated acceleration, the
- * first-step convention of Sec. 3.7 (d)).  Clears the tape. */
+ * first-step convention of Sec. 3.7 (d)).  v_prev goes beyond the plain
+ * (x, v) state: the adaptive initial guess of Eq. 17 reads the previous
+ * velocity, so a saved (x, v, v_prev) resumes a run bit for bit.  Clears the
+ * tape. */
 vbd_status vbd_set_state(vbd_ctx *ctx, const float *x, const float *v, const float *v_prev);
 
 /* Copies x and v (3N floats each, caller order, host or device; either may
@@ -309,14 +313,16 @@ vbd_status vbd_energy(vbd_ctx *ctx, double *G_out);
  * real-time loop where cudaMalloc's implicit synchronisation is not
  * allowed) and so cannot grant this diagnostic scratch of its own.  Its
  * scratch (per-block partial sums) is a 512 KiB array inside the library,
- * one per device, kept until the process exits; nothing is allocated.
- * G_out: device pointer to one double, written asynchronously on the bound
- * stream (not synchronising).  The first call on a device looks up that
- * array's device address; make it before any stream capture.  Calls that
- * overlap on the GPU (several streams or contexts at once) race on the
- * shared array.  VBD_ERR_INVALID_ARG when ceil(free vertices / 256) +
- * ceil(tets / 256) exceeds 65536 partial sums (about 16.7 million vertices
- * plus tets), or when G_out is not device memory. */
+ * one per CUDA context that loads it, kept until the process exits; nothing
+ * is allocated.  G_out: device pointer to one double, written asynchronously
+ * on the bound stream (not synchronising).  The first call in a context
+ * looks up that context's copy of the array (a context made after a device
+ * reset gets a fresh lookup); make it before any stream capture.  Calls that
+ * overlap on the GPU (several streams at once) race on the shared array.
+ * VBD_ERR_INVALID_ARG when the partial sums needed, ceil(free vertices /
+ * 256) + ceil(tets / 256), plus ceil(boundary triangles / 256) when
+ * self-collision is on, exceed 65536 (about 16.7 million elements in all),
+ * or when G_out is not device memory. */
 vbd_status vbd_energy_static(vbd_ctx *ctx, double *G_out);
 
 /* Self-collision pairs of the current step (found by vbd_begin_step on
@@ -399,20 +405,41 @@ vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, floa
 vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_threads, int32_t variant);
 
 /* Test hook for the time-out report of the TMA-staged sweep (variant 1):
- * while enabled, each CTA's first stage waits for 16 bytes more than its
- * bulk copies deliver, so that wait runs out after about 2 s of SM clock;
- * the CTA records the time-out, drains its own copies (again bounded) and
- * leaves, and the next vbd_sync_status returns VBD_ERR_TIMEOUT.  Nothing
- * faults and the context stays usable.  Other variants ignore it. */
+ * while enabled, each CTA's first chunk, once its bulk copies have landed,
+ * also waits on a spare barrier at which nothing arrives, so that wait runs
+ * out after about 2 s of SM clock; the CTA records the time-out, waits
+ * (bounded) for every copy it has issued and leaves, and the next
+ * vbd_sync_status returns VBD_ERR_TIMEOUT.  Nothing faults, no copy is left
+ * in flight, and the context stays usable.  Other variants ignore it. */
 vbd_status vbd_debug_stall_pipeline(vbd_ctx *ctx, int32_t enable);
 
 /* Enables (1) or disables (0) CUDA-graph replay of vbd_iterate. */
 vbd_status vbd_set_graph(vbd_ctx *ctx, int32_t enable);
 
-/* Times every sweep launch shape on the bound stream with the current state
- * (which it restores) for `iters` iterations at step size h and keeps the
- * fastest.  Synchronising.  best_ms_per_iter may be NULL. */
+/* Times every applicable sweep launch shape of vbd_set_launch on the bound
+ * stream, each for `iters` iterations of a step of size h begun from the
+ * current state, and keeps the fastest (Sec. 3.9's colour passes are what
+ * is timed; the paper fixes one launch shape, this picks it per mesh).
+ * Between steps only (VBD_ERR_STATE inside one).  Everything the timing
+ * steps overwrite is put back: x (from x^t; v and v^{t-1} are never
+ * touched), the inertia target of the last step (so vbd_energy reads the
+ * same G), the device counters of vbd_sync_status, and the host-side step
+ * state.  The shapes differ in rounding (see vbd_set_launch), so the
+ * chosen shape can change the last bits of later results; all of them
+ * meet the same accuracy.  A failing call stops the search, keeps the
+ * previous shape and returns its status.  With self-collision on, the
+ * pass kernel is fixed: returns VBD_OK at once with *best_ms_per_iter = 0.
+ * Synchronising.  best_ms_per_iter (may be NULL) receives the best time
+ * per iteration in ms. */
 vbd_status vbd_autotune(vbd_ctx *ctx, float h, int32_t iters, float *best_ms_per_iter);
+
+/* vbd_autotune with flags: VBD_TUNE_SAME_ARITHMETIC restricts the search to
+ * shapes whose positions equal those of the current shape bit for bit
+ * (variants 0, 2 and 4 with the current lane count, and variant 1 when that
+ * count is 8; variants 3 and 5 only among their own block sizes), so tuning
+ * cannot change any result.  Other bits: VBD_ERR_INVALID_ARG. */
+#define VBD_TUNE_SAME_ARITHMETIC 1
+vbd_status vbd_autotune_ex(vbd_ctx *ctx, float h, int32_t iters, int32_t flags, float *best_ms_per_iter);
 
 /* Message of the last failed call on this context (static storage owned by
  * the context; valid until the next call).  Never NULL. */

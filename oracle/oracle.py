@@ -25,6 +25,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "vbd_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lib = None
 
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -32,17 +33,23 @@ _ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _up = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C99, -O2, no fast-math)."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with gcc (plain C99, -O2, no fast-math).  openmp=True
+    builds liboracle_omp.so from the same source with -fopenmp: the vertices
+    of one colour are then solved on several threads (the timed multi-core
+    baseline; same results bit for bit).  Load it by naming it in
+    VBD_ORACLE_LIB before the first call of lib()."""
+    out = _LIB_OMP if openmp else _LIB
     hdr = os.path.join(_HERE, "vbd_oracle.h")
-    stale = (not os.path.exists(_LIB) or
-             os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(hdr)))
+    stale = (not os.path.exists(out) or
+             os.path.getmtime(out) < max(os.path.getmtime(_SRC), os.path.getmtime(hdr)))
     if force or stale:
-        tmp = _LIB + ".tmp%d" % os.getpid()
+        tmp = out + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-fno-fast-math",
-                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+                               "-ffp-contract=off"] + (["-fopenmp"] if openmp else []) +
+                              ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 class Params(C.Structure):
@@ -58,9 +65,10 @@ class Params(C.Structure):
     def make(cls, gravity=(0.0, 0.0, -9.8), ground_on=False, ground_height=0.0,
              ground_normal=(0.0, 0.0, 1.0), k_c=0.0, cheby_rho=0.0, init_mode=3,
              det_eps=1e-12, k_d=0.0, mu_c=0.0, eps_v=1e-3, line_search=False, jacobi=False,
-             self_collision=False, dcd_radius=0.0, walls=(), ccd_interval=0, ccd_edges=False,
-             **_ignored) -> "Params":
-        """walls: up to 6 world-box half-spaces (nx, ny, nz, offset), the allowed
+             self_collision=False, dcd_radius=0.0, walls=(), ccd_interval=0,
+             ccd_edges=False) -> "Params":
+        """Parameters from keywords; an unknown keyword raises TypeError.
+        walls: up to 6 world-box half-spaces (nx, ny, nz, offset), the allowed
         side being x.n/|n| >= offset (Sec. 3.4)."""
         p = cls()
         p.gravity[:] = [float(g) for g in gravity]

@@ -3,7 +3,11 @@
  *
  * TEST INFRASTRUCTURE ONLY (see vbd_oracle.h).  Plain loops, FP64, no
  * blocking, fusion or reordering beyond what the paper states, so each
- * routine can be read against the paper equation it cites.
+ * routine can be read against the paper equation it cites.  The same file
+ * built with -fopenmp (liboracle_omp.so, used only to time the multi-core
+ * CPU baseline) solves the vertices of one colour on several threads, which
+ * Sec. 3.9 allows because they share no force element; its results equal
+ * the serial build's bit for bit.
  *
  * Readings of points the paper leaves open (each pinned by a test):
  *  - Material: Sec. 5 uses the stable neo-Hookean model of Smith et al.
@@ -1412,18 +1416,30 @@ void orc_sweep_color(const orc_model *m, const orc_params *p, double h, const in
         xs = (double *)malloc(sizeof(double) * n3 + 1);
         memcpy(xs, x, sizeof(double) * n3);
     }
+    /* Sec. 3.9: the vertices of one colour share no force element, so each
+     * solve reads only other colours' positions (or the pass-start copy) and
+     * the order does not matter; the OpenMP build of this file (timed
+     * multi-core baseline) splits this loop over threads and gives the same
+     * numbers bit for bit. */
+    long long solves = 0, skips = 0, contacts = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : solves, skips, contacts)
+#endif
     for (int i = 0; i < m->n_verts; ++i) {
         if (colors[i] != color || m->pinned[i]) continue;
         double dx[3];
         int contact;
         int skipped = orc_vertex_solve(m, p, h, i, xs, y, xt, dx, &contact);
-        if (st) {
-            st->vertex_solves++;
-            st->det_skips += skipped;
-            st->contacts += contact;
-        }
+        solves++;
+        skips += skipped;
+        contacts += contact;
         if (contact && colliding) colliding[i] = 1;
         for (int r = 0; r < 3; ++r) x[3 * i + r] = xs[3 * i + r] + dx[r];
+    }
+    if (st) {
+        st->vertex_solves += solves;
+        st->det_skips += skips;
+        st->contacts += contacts;
     }
     if (xs != x) free(xs);
 }
@@ -1461,18 +1477,25 @@ int orc_step(const orc_model *m, const orc_params *p, const int *colors, int n_c
         if (p->jacobi) {
             /* block Jacobi: solve every free vertex against the previous iterate */
             memcpy(xj, x, sizeof(double) * n3);
+            long long solves = 0, skips = 0, contacts = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : solves, skips, contacts)
+#endif
             for (int i = 0; i < m->n_verts; ++i) {
                 if (m->pinned[i]) continue;
                 double dx[3];
                 int contact;
                 int skipped = orc_vertex_solve(m, p, h, i, x, y, xt, dx, &contact);
-                if (st) {
-                    st->vertex_solves++;
-                    st->det_skips += skipped;
-                    st->contacts += contact;
-                }
+                solves++;
+                skips += skipped;
+                contacts += contact;
                 if (contact) coll[i] = 1;
                 for (int r = 0; r < 3; ++r) xj[3 * i + r] = x[3 * i + r] + dx[r];
+            }
+            if (st) {
+                st->vertex_solves += solves;
+                st->det_skips += skips;
+                st->contacts += contacts;
             }
             memcpy(x, xj, sizeof(double) * n3);
         } else {

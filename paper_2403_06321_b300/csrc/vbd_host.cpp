@@ -1547,47 +1547,108 @@ vbd_status vbd_set_graph(vbd_ctx *ctx, int32_t enable) {
     return VBD_OK;
 }
 
-vbd_status vbd_autotune(vbd_ctx *ctx, float h, int32_t iters, float *best_ms_per_iter) {
+// Shapes whose passes give the same positions bit for bit share a class:
+// variants 0, 2 and 4 with equal lanes, and variant 1 with variant 0 at 8
+// lanes (the same code and reduction order); variants 3 and 5 round
+// differently and form classes of their own (per lane count).
+static int arithmetic_class(int variant, int lanes) {
+    if (variant == 1) return 8;
+    if (variant == 3) return 100 + lanes;
+    if (variant == 5) return 200 + lanes;
+    return lanes;
+}
+
+vbd_status vbd_autotune_ex(vbd_ctx *ctx, float h, int32_t iters, int32_t flags, float *best_ms_per_iter) {
     Range range_("vbd_autotune");
     vbd_status st = check_bound(ctx);
     if (st != VBD_OK) return st;
     if (ctx->in_step) return fail(ctx, VBD_ERR_STATE, "vbd_autotune inside a step");
     if (iters < 1) return fail(ctx, VBD_ERR_INVALID_ARG, "iters must be >= 1");
+    if (!(h > 0.f) || !std::isfinite(h)) return fail(ctx, VBD_ERR_INVALID_ARG, "h must be > 0");
+    if (flags & ~VBD_TUNE_SAME_ARITHMETIC) return fail(ctx, VBD_ERR_INVALID_ARG, "unknown autotune flags");
+    if (best_ms_per_iter) *best_ms_per_iter = 0.f;
+    // self-collision passes always run the plain kernel with contacts
+    if (ctx->params.self_collision) return VBD_OK;
     struct Shape { int pipe, lanes, block; };
     const Shape shapes[] = {{0, 4, 64}, {0, 4, 128}, {0, 4, 256}, {0, 8, 64}, {0, 8, 128}, {0, 8, 256},
                             {0, 16, 64}, {0, 16, 256}, {1, 8, 128}, {1, 8, 256}, {2, 4, 128}, {2, 4, 256},
                             {2, 8, 256}, {3, 4, 128}, {4, 4, 0}, {4, 8, 0}, {4, 16, 0}, {5, 4, 128},
                             {5, 4, 256}};
-    cudaEvent_t e0, e1;
-    CU(cudaEventCreate(&e0), "event");
-    CU(cudaEventCreate(&e1), "event");
+    const Shape cur = {ctx->variant, ctx->lanes, ctx->variant == 1 ? ctx->pipe_block : ctx->block};
+    const int cls = arithmetic_class(cur.pipe, cur.lanes);
+    // what the timing steps overwrite and a later call could still read: the
+    // positions (restored from x^t), the inertia target of the last step
+    // (read by vbd_energy), the device counters (read by vbd_sync_status),
+    // and the host-side step state
+    const int N = ctx->N;
+    std::vector<float4> ym_saved(N);
+    unsigned long long counters_saved[8];
+    CU(cudaStreamSynchronize(ctx->stream), "autotune");
+    CU(cudaMemcpy(ym_saved.data(), ctx->d.ym, 16 * (size_t)N, cudaMemcpyDeviceToHost), "autotune save");
+    CU(cudaMemcpy(counters_saved, ctx->d.counters, sizeof(counters_saved), cudaMemcpyDeviceToHost),
+       "autotune save");
+    const float h_saved = ctx->h;
+    const int iter_saved = ctx->iter_in_step;
     const bool graph_saved = ctx->use_graph;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CU(cudaEventCreate(&e0), "event");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(ctx, VBD_ERR_CUDA, "event");
+    }
     ctx->use_graph = false;
     float best = 1e30f;
-    Shape bs = {ctx->variant, ctx->lanes, ctx->variant == 1 ? ctx->pipe_block : ctx->block};
+    Shape bs = cur;
+    vbd_status bad = VBD_OK;
+    std::string bad_msg;
     for (const Shape &sh : shapes) {
-        if (vbd_set_launch(ctx, sh.lanes, sh.block, sh.pipe) != VBD_OK) continue;
+        if ((flags & VBD_TUNE_SAME_ARITHMETIC) && arithmetic_class(sh.pipe, sh.lanes) != cls) continue;
+        if (vbd_set_launch(ctx, sh.lanes, sh.block, sh.pipe) != VBD_OK) continue;  // not applicable here
         float ms = 0.f;
-        for (int rep = 0; rep < 2; ++rep) {  // first repetition warms up
-            vbd_begin_step(ctx, h);
-            cudaEventRecord(e0, ctx->stream);
-            vbd_iterate(ctx, iters);
-            cudaEventRecord(e1, ctx->stream);
+        for (int rep = 0; rep < 2 && bad == VBD_OK; ++rep) {  // the first repetition warms up
+            st = vbd_begin_step(ctx, h);
+            if (st == VBD_OK) {
+                cudaEventRecord(e0, ctx->stream);
+                st = vbd_iterate(ctx, iters);
+                cudaEventRecord(e1, ctx->stream);
+            }
             ctx->in_step = false;
-            vbd::launch_restore_x(ctx->d, ctx->N, ctx->stream);
-            cudaEventSynchronize(e1);
-            cudaEventElapsedTime(&ms, e0, e1);
+            vbd::launch_restore_x(ctx->d, N, ctx->stream);
+            if (st != VBD_OK) {
+                bad = st;
+                bad_msg = ctx->err;
+                break;
+            }
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                bad = VBD_ERR_CUDA;
+                bad_msg = "autotune timing";
+            }
         }
+        if (bad != VBD_OK) break;
         if (ms < best) { best = ms; bs = sh; }
     }
-    ctx->use_graph = graph_saved;
-    vbd_set_launch(ctx, bs.lanes, bs.block, bs.pipe);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    ctx->use_graph = graph_saved;
+    ctx->h = h_saved;
+    ctx->iter_in_step = iter_saved;
+    ctx->in_step = false;
+    const Shape keep = bad == VBD_OK ? bs : cur;
+    vbd_status ls = vbd_set_launch(ctx, keep.lanes, keep.block, keep.pipe);
+    CU(cudaMemcpyAsync(ctx->d.ym, ym_saved.data(), 16 * (size_t)N, cudaMemcpyHostToDevice, ctx->stream),
+       "autotune restore");
+    CU(cudaMemcpyAsync(ctx->d.counters, counters_saved, sizeof(counters_saved), cudaMemcpyHostToDevice,
+                       ctx->stream), "autotune restore");
     CU(cudaStreamSynchronize(ctx->stream), "autotune");
     CU(cudaGetLastError(), "autotune");
-    if (best_ms_per_iter) *best_ms_per_iter = best / iters;
+    if (bad != VBD_OK) return fail(ctx, bad, "autotune: " + bad_msg);
+    if (ls != VBD_OK) return ls;
+    if (best_ms_per_iter) *best_ms_per_iter = best < 1e30f ? best / iters : 0.f;
     return VBD_OK;
+}
+
+vbd_status vbd_autotune(vbd_ctx *ctx, float h, int32_t iters, float *best_ms_per_iter) {
+    return vbd_autotune_ex(ctx, h, iters, 0, best_ms_per_iter);
 }
 
 const char *vbd_last_error(const vbd_ctx *ctx) {

@@ -24,6 +24,8 @@
 #include <mutex>
 
 #include <cooperative_groups.h>
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "vbd_geom.cuh"
 
@@ -601,7 +603,14 @@ __global__ void __launch_bounds__(256) k_scatter_reduce(Dev d, SweepParams p, in
 // mbarrier), two chunks ahead of the consumers.  The stream is then in flight
 // without occupying registers, which is what limits k_sweep.  Every wait is
 // bounded: on time-out the CTA records an error (counters[2]), waits (again
-// bounded) for its own copies and returns; the host reports it.
+// bounded) on the barriers of every chunk it has issued and returns; the host
+// reports it.  Each stage barrier expects exactly the bytes of the copies
+// issued to it, so that drain returns as soon as those copies have landed.
+// Only if a copy itself never completes (a fault of the copy engine, which
+// nothing here provokes) does the drain give up too, and the CTA then exits
+// with that copy outstanding.  The time-out test hook therefore does not
+// touch the stage barriers: it makes the first chunk also wait on a spare
+// barrier that nothing ever arrives at.
 constexpr int kPipeLanes = 8;
 constexpr int kPipeStages = 2;
 constexpr long long kWaitSpins = 1ll << 22;        // try_wait calls before giving up
@@ -664,8 +673,7 @@ __host__ __device__ inline size_t pipe_smem_bytes(int maxs) {
 
 // issued by one thread: chunk q of the colour range into stage st
 __device__ __forceinline__ void pipe_issue(const Dev &d, const SweepParams &p, int q, int cv, int maxs,
-                                           char *stages, StageMeta *meta, unsigned long long *bar, int st,
-                                           bool stall = false) {
+                                           char *stages, StageMeta *meta, unsigned long long *bar, int st) {
     const int v0 = p.vbegin + q * cv;
     const int v1 = min(p.vend, v0 + cv);
     const int a = d.slot_off[v0], b = d.slot_off[v1];
@@ -681,7 +689,7 @@ __device__ __forceinline__ void pipe_issue(const Dev &d, const SweepParams &p, i
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(ab) : "memory");
         return;
     }
-    const unsigned tx = 48u * (unsigned)n + (stall ? 16u : 0u);  // stall: 16 bytes never come
+    const unsigned tx = 48u * (unsigned)n;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(ab), "r"(tx) : "memory");
     StageView v = stage_view(stages + st * pipe_stage_bytes(maxs), maxs);
     bulk_g2s(v.s0, d.s0 + a, 16u * n, bar + st);
@@ -694,14 +702,15 @@ __global__ void __launch_bounds__(TT) k_sweep_pipe(Dev d, SweepParams p, int max
     constexpr int L = kPipeLanes;
     constexpr int CV = TT / L;  // vertices per chunk
     extern __shared__ __align__(128) char smem[];
-    unsigned long long *bar = (unsigned long long *)smem;     // kPipeStages barriers
+    unsigned long long *bar = (unsigned long long *)smem;     // kPipeStages barriers + the spare
     StageMeta *meta = (StageMeta *)(smem + 64);               // kPipeStages records
+    unsigned long long *never = bar + kPipeStages;            // spare: no arrival (time-out test)
     char *stages = smem + 128;
     const int n = p.vend - p.vbegin;
     const int nchunks = (n + CV - 1) / CV;
     const int first = blockIdx.x, stride = gridDim.x;
     if (threadIdx.x == 0) {
-        for (int st = 0; st < kPipeStages; ++st)
+        for (int st = 0; st <= kPipeStages; ++st)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(bar + st)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -709,14 +718,14 @@ __global__ void __launch_bounds__(TT) k_sweep_pipe(Dev d, SweepParams p, int max
     if (threadIdx.x == 0)
         for (int st = 0; st < kPipeStages; ++st)
             if (first + st * stride < nchunks)
-                pipe_issue(d, p, first + st * stride, CV, maxs, stages, meta, bar, st,
-                           p.stall_test != 0 && st == 0);
+                pipe_issue(d, p, first + st * stride, CV, maxs, stages, meta, bar, st);
     const int lane = threadIdx.x & (L - 1);
     for (int k = 0;; ++k) {
         const int q = first + k * stride;
         if (q >= nchunks) break;
         const int st = k % kPipeStages;
-        const bool ok = mbar_wait(bar + st, (unsigned)((k / kPipeStages) & 1));
+        bool ok = mbar_wait(bar + st, (unsigned)((k / kPipeStages) & 1));
+        if (ok && k == 0 && p.stall_test) ok = mbar_wait(never, 0u);  // runs out after ~2 s
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) {
                 atomicAdd(d.counters + 2, 1ull);
@@ -1305,7 +1314,38 @@ constexpr int kStaticPartials = 65536;
 static __device__ __align__(256) double g_static_partials[kStaticPartials];
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
-double *g_static_ptr[kMaxDevices] = {};
+// per device: the CUDA context whose module the cached address belongs to
+struct StaticScratch {
+    unsigned long long ctx_id;
+    double *ptr;
+};
+StaticScratch g_static[kMaxDevices] = {};
+
+// Unique id of the calling thread's current CUDA context (0 if none).  Taken
+// from the driver through the runtime's entry-point query, so the library
+// needs no link against the driver library.
+cudaError_t current_context_id(unsigned long long *id) {
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    *id = 0;
+    if (!get_current || !get_id) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1);
+        if (e != cudaSuccess) return e;
+        e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess) return e;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return cudaErrorSymbolNotFound;
+        get_current = (PFN_cuCtxGetCurrent_v4000)f1;
+        get_id = (PFN_cuCtxGetId_v12000)f2;
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+    if (!ctx) return cudaSuccess;
+    if (get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+    return cudaSuccess;
+}
 }  // namespace
 
 int energy_static_capacity() { return kStaticPartials; }
@@ -1317,23 +1357,35 @@ int energy_static_partials_needed(int n_free, int n_tets, int n_surf) {
     return (int)std::min<long long>(gv + gt + gc, 0x7fffffffLL);
 }
 
-// Device address of g_static_partials on the current device.  The symbol name
-// is only a host-side handle; kernels must be given this address.  Looked up
-// once per device (the first call on a device does it, so that call should
-// precede any stream capture).
+// Device address of g_static_partials in the current device's current
+// context.  The symbol name is only a host-side handle; kernels must be given
+// this address.  It is looked up once per (device, context): the module, and
+// so the array, is loaded per context, and a context made after a reset of
+// the device (cudaDeviceReset, then new work) may place it elsewhere, so the
+// cached address is keyed by the context's unique id and looked up again
+// when that id changes.  The first call in a context does the lookup, so it
+// should precede any stream capture.
 cudaError_t energy_static_scratch(double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[dev]) {
+    std::lock_guard<std::mutex> lock(g_static_mu);  // also guards the entry points' first lookup
+    unsigned long long id = 0;
+    e = current_context_id(&id);
+    if (e != cudaSuccess) return e;
+    if (id == 0 || !g_static[dev].ptr || g_static[dev].ctx_id != id) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_partials);
+        e = cudaGetSymbolAddress(&p, g_static_partials);  // makes the runtime's context current if none was
         if (e != cudaSuccess) return e;
-        g_static_ptr[dev] = (double *)p;
+        if (id == 0) {
+            e = current_context_id(&id);
+            if (e != cudaSuccess) return e;
+        }
+        g_static[dev].ptr = (double *)p;
+        g_static[dev].ctx_id = id;
     }
-    *out = g_static_ptr[dev];
+    *out = g_static[dev].ptr;
     return cudaSuccess;
 }
 

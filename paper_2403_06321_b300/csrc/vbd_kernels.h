@@ -112,8 +112,8 @@ struct SweepParams {
     int per_tet_mat;  // 1: mu, lambda per tet (via slot_tet); 0: per vertex (vmat)
     int to_unew;      // every vertex writes to d.unew instead of updating d.u in place (block Jacobi)
     int self_collision;  // add the vertex-triangle contact forces of the current pairs
-    int stall_test;   // TMA-staged sweep only: each CTA's first stage expects 16 bytes that never
-                      // arrive, so its bounded wait runs out (tests of the time-out report)
+    int stall_test;   // TMA-staged sweep only: each CTA's first chunk also waits on a barrier that
+                      // nothing arrives at, so its bounded wait runs out (tests of the time-out report)
 };
 
 // the fused iteration loop (one launch of one thread-block cluster per vbd_iterate)

@@ -31,7 +31,8 @@ ENTRY_POINTS = [
     "vbd_accelerate", "vbd_end_step", "vbd_energy", "vbd_energy_static", "vbd_get_contacts", "vbd_get_edge_pairs",
     "vbd_sync_status",
     "vbd_backward",
-    "vbd_set_launch", "vbd_debug_stall_pipeline", "vbd_set_graph", "vbd_autotune", "vbd_last_error",
+    "vbd_set_launch", "vbd_debug_stall_pipeline", "vbd_set_graph", "vbd_autotune", "vbd_autotune_ex",
+    "vbd_last_error",
     "vbd_destroy",
 ]
 
@@ -115,6 +116,7 @@ def load() -> C.CDLL:
         "vbd_debug_stall_pipeline": (C.c_int, [P, I32]),
         "vbd_set_graph": (C.c_int, [P, I32]),
         "vbd_autotune": (C.c_int, [P, F, I32, C.POINTER(F)]),
+        "vbd_autotune_ex": (C.c_int, [P, F, I32, I32, C.POINTER(F)]),
         "vbd_last_error": (C.c_char_p, [P]),
         "vbd_destroy": (None, [P]),
     }
@@ -313,6 +315,15 @@ def vbd_autotune(ctx: int, h: float, iters: int) -> float:
     return ms.value
 
 
+VBD_TUNE_SAME_ARITHMETIC = 1
+
+
+def vbd_autotune_ex(ctx: int, h: float, iters: int, flags: int = 0) -> float:
+    ms = C.c_float()
+    _check("vbd_autotune_ex", ctx, load().vbd_autotune_ex(ctx, h, iters, flags, C.byref(ms)))
+    return ms.value
+
+
 def vbd_last_error(ctx: int) -> str:
     return load().vbd_last_error(ctx).decode()
 
@@ -327,10 +338,12 @@ def vbd_destroy(ctx: int) -> None:
 def make_params(gravity=(0.0, 0.0, -9.8), ground_on=False, ground_height=0.0, ground_normal=(0.0, 0.0, 1.0),
                 k_c=1e7, cheby_rho=0.0, init_mode=3, det_eps=1e-12, k_d=0.0, tape_steps=0, mu_c=0.0,
                 eps_v=1e-3, line_search=False, jacobi=False, self_collision=False, dcd_radius=0.01,
-                scatter_sweep=False, xnew_copy_back=False, walls=(), ccd_interval=0, ccd_edges=False,
-                **_ignored) -> vbd_params:
-    """vbd_params from keywords.  walls: up to 6 world-box half-spaces
-    (nx, ny, nz, offset), the allowed side being x.n/|n| >= offset."""
+                scatter_sweep=False, xnew_copy_back=False, walls=(), ccd_interval=0,
+                ccd_edges=False) -> vbd_params:
+    """vbd_params from keywords (an unknown keyword raises TypeError, so a
+    misspelt option cannot silently run the default).  walls: up to 6
+    world-box half-spaces (nx, ny, nz, offset), the allowed side being
+    x.n/|n| >= offset."""
     p = vbd_default_params()
     p.gravity[:] = [float(g) for g in gravity]
     p.ground_on = int(bool(ground_on))

@@ -215,3 +215,15 @@ def test_subspace_constraints_are_validated(lib):
         assert vbd.vbd_workspace_size(ctx) == size0
     finally:
         vbd.vbd_destroy(ctx)
+
+
+def test_unknown_parameter_keywords_are_rejected(lib):
+    """A misspelt option must fail on both sides instead of running the
+    default on both (which would let a parity test pass without testing it)."""
+    from oracle import oracle
+    with pytest.raises(TypeError):
+        vbd.make_params(cheby_roh=0.9)
+    with pytest.raises(TypeError):
+        oracle.Params.make(cheby_roh=0.9)
+    assert vbd.make_params(cheby_rho=0.9).cheby_rho == pytest.approx(0.9)
+    assert oracle.Params.make(cheby_rho=0.9).cheby_rho == pytest.approx(0.9)

@@ -1,7 +1,12 @@
 """GPU adjoint (vbd_backward, via the torch.autograd wrapper) against the
 oracle's FP64 adjoint of the same steps.  The oracle adjoint is itself
 pinned to central finite differences (tests/test_oracle_adjoint.py).
-Gate: gradients within 1e-3 relative (2-norm) of the oracle's."""
+Gate, element by element: every entry of dL/dlog E within 1e-3 of the
+largest |entry| of the oracle's, likewise each component of dL/dv0 against
+that component's largest entry, and the same sign wherever the oracle's
+entry exceeds 1 % of that largest one (a norm could hide a few hundred
+wrong entries among the many small ones).  The relative 2-norm is printed
+as a diagnostic only."""
 import numpy as np
 import pytest
 import torch
@@ -21,6 +26,33 @@ def _built():
 
 def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _elementwise(g, o):
+    """Worst |g - o| / max|o| over the columns (one column for dL/dlog E,
+    x, y, z for dL/dv0), and the number of sign disagreements among entries
+    above 1 % of their column's largest |entry|."""
+    g = g.reshape(len(g), -1)
+    o = o.reshape(len(o), -1)
+    worst, flips = 0.0, 0
+    for c in range(o.shape[1]):
+        scale = float(np.abs(o[:, c]).max())
+        if scale == 0.0:
+            assert np.all(g[:, c] == 0.0)
+            continue
+        worst = max(worst, float(np.abs(g[:, c] - o[:, c]).max()) / scale)
+        big = np.abs(o[:, c]) > 0.01 * scale
+        flips += int((np.sign(g[big, c]) != np.sign(o[big, c])).sum())
+    return worst, flips
+
+
+def _check(label, gE, oE, gv, ov):
+    wE, fE = _elementwise(gE, oE)
+    wv, fv = _elementwise(gv, ov)
+    print("%s: dlogE worst %.2e (2-norm %.2e, sign flips %d)  dv0 worst %.2e (2-norm %.2e, sign flips %d)" % (
+        label, wE, _rel(gE, oE), fE, wv, _rel(gv, ov), fv))
+    assert wE <= 1e-3 and wv <= 1e-3
+    assert fE == 0 and fv == 0
 
 
 def _gpu_grads(m, pd, colors, h, iters, steps, v0, tip, target, adj_iters, logE=None):
@@ -75,10 +107,9 @@ def test_adjoint_converged_small_beam(orc):
     h, steps = 1 / 60, 4
     gE, gv, xg = _gpu_grads(m, pd, colors, h, 400, steps, v0, tip, target, adj_iters=300)
     oE, ov, xo = _oracle_grads(orc, m, pd, colors, h, 0, steps, v0, tip, target, newton=True)
-    print("small beam: |x|err %.2e  dlogE rel %.2e  dv0 rel %.2e" % (
-        np.abs(xg - xo).max(), _rel(gE, oE), _rel(gv, ov)))
+    print("small beam: |x|err %.2e" % np.abs(xg - xo).max())
     assert np.abs(xg - xo).max() < 1e-5
-    assert _rel(gE, oE) <= 1e-3 and _rel(gv, ov) <= 1e-3
+    _check("small beam", gE, oE, gv, ov)
     assert np.all(gv[m.pinned == 1] == 0)
 
 
@@ -93,10 +124,9 @@ def test_adjoint_differentiable_beam_full_size(orc):
     gE, gv, xg = _gpu_grads(m, pd, colors, cfg.h, cfg.iters, cfg.steps, v0, tip, target, adj_iters=150)
     oE, ov, xo = _oracle_grads(orc, m, pd, colors, cfg.h, cfg.iters, cfg.steps, v0, tip, target)
     diag = float(np.linalg.norm(m.rest.max(0) - m.rest.min(0)))
-    print("differentiable beam: x err/bbox %.2e  dlogE rel %.2e  dv0 rel %.2e" % (
-        np.abs(xg - xo).max() / diag, _rel(gE, oE), _rel(gv, ov)))
+    print("differentiable beam: x err/bbox %.2e" % (np.abs(xg - xo).max() / diag))
     assert np.abs(xg - xo).max() <= 1e-5 * diag
-    assert _rel(gE, oE) <= 1e-3 and _rel(gv, ov) <= 1e-3
+    _check("differentiable beam", gE, oE, gv, ov)
 
 
 def test_adjoint_with_ground_contact(orc):
@@ -116,7 +146,6 @@ def test_adjoint_with_ground_contact(orc):
     gE, gv, xg = _gpu_grads(m, pd, colors, h, 600, steps, v0, top, target, adj_iters=400)
     oE, ov, xo = _oracle_grads(orc, m, pd, colors, h, 0, steps, v0, top, target, newton=True)
     assert (xo[:, 2] < 0).sum() >= 4  # vertices in contact at the last step
-    print("ground contact: |x|err %.2e  dlogE rel %.2e  dv0 rel %.2e" % (
-        np.abs(xg - xo).max(), _rel(gE, oE), _rel(gv, ov)))
+    print("ground contact: |x|err %.2e" % np.abs(xg - xo).max())
     assert np.abs(xg - xo).max() < 1e-5
-    assert _rel(gE, oE) <= 1e-3 and _rel(gv, ov) <= 1e-3
+    _check("ground contact", gE, oE, gv, ov)

@@ -230,9 +230,9 @@ def test_block_jacobi(orc):
 
 def test_pipeline_wait_time_out_is_reported_and_recoverable():
     """A bounded wait of the TMA-staged sweep that runs out (the test hook
-    makes each CTA's first stage expect 16 bytes that never arrive) is
-    reported as VBD_ERR_TIMEOUT; the context then runs normally and gives the
-    same result as a context that never timed out."""
+    makes each CTA's first chunk also wait on a barrier at which nothing
+    arrives) is reported as VBD_ERR_TIMEOUT; the context then runs normally
+    and gives the same result as a context that never timed out."""
     m, cfg = synth.cantilever_beam()
     colors = synth.kuhn_coloring(m.grid_ijk)
     pd = params_of(cfg)
