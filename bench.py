@@ -442,10 +442,11 @@ def run_batched(args) -> dict:
             "speedup_vs_plain": v_batched / v_plain, "n_free_verts": int(info.n_free)}
 
 
-def run_adjoint(args) -> dict:
+def run_adjoint(args, reps: int = 5) -> dict:
     """Adjoint block-GS sweeps (vbd_backward) on the benchmark cube against
     the forward sweeps on the same mesh: vertex-block updates per second of
-    each, 2 recorded steps."""
+    each, 2 recorded steps; forward and backward are each timed `reps` times
+    and the medians are reported."""
     import numpy as np
     import torch
     from paper_2403_06321_b300 import synth, vbd
@@ -462,24 +463,275 @@ def run_adjoint(args) -> dict:
     gx[2::3] = 1.0 / m.n_verts
     gE = torch.empty(m.n_tets, dtype=torch.float32, device=dev)
     gv = torch.empty(3 * m.n_verts, dtype=torch.float32, device=dev)
-
-    def fwd():
-        sim.set_state(m.rest, zeros)
-        for _ in range(steps):
-            sim.step(cfg.h, iters)
-    fwd()
-    vbd.vbd_backward(sim.ctx, gx, gE, gv, adj_iters)  # warm-up
     sim.set_state(m.rest, zeros)
-    t_f = _timed(stream, lambda: sim.step(cfg.h, iters), steps)
-    t_a = _timed(stream, lambda: vbd.vbd_backward(sim.ctx, gx, gE, gv, adj_iters), 1)
+    for _ in range(steps):
+        sim.step(cfg.h, iters)
+    vbd.vbd_backward(sim.ctx, gx, gE, gv, adj_iters)  # warm-up
+    t_f, t_a = [], []
+    for _ in range(reps):
+        sim.set_state(m.rest, zeros)
+        t_f.append(_timed(stream, lambda: sim.step(cfg.h, iters), steps))
+        t_a.append(_timed(stream, lambda: vbd.vbd_backward(sim.ctx, gx, gE, gv, adj_iters), 1))
+    # how converged the timed solves are (untimed): the adjoint's relative
+    # residual per recorded step, and the forward's max |dG/dx| after each step
+    adj_res = vbd.vbd_adjoint_residuals(sim.ctx, steps)
+    sim.set_state(m.rest, zeros)
+    fwd_res = []
+    for _ in range(steps):
+        sim.step(cfg.h, iters)
+        fwd_res.append(vbd.vbd_gradient_norm(sim.ctx))
     sim.sync_status()
     sim.close()
-    v_f = n_free * iters * steps / t_f
-    v_a = n_free * adj_iters * steps / t_a
+    tf, ta = statistics.median(t_f), statistics.median(t_a)
+    v_f = n_free * iters * steps / tf
+    v_a = n_free * adj_iters * steps / ta
     return {"workload": "large_cube %d^3, %d recorded steps, %d adjoint block-GS iterations per step" % (
                 args.n, steps, adj_iters),
             "value": v_a, "unit": "adjoint vertex-block updates/s", "forward_value": v_f,
-            "ratio_vs_plain": v_a / v_f, "ms_backward": t_a * 1e3, "ms_forward": t_f * 1e3}
+            "ratio_vs_plain": v_a / v_f, "ms_backward": ta * 1e3, "ms_forward": tf * 1e3,
+            "timing": "median of %d repetitions (backward %s ms)" % (
+                reps, ", ".join("%.2f" % (t * 1e3) for t in t_a)),
+            "convergence": {
+                "adjoint_rel_residual_per_step": [float(r) for r in adj_res],
+                "adjoint_rel_residual": "max |r - H lam| / max |r| after the sweeps (FP64 reduction)",
+                "forward_grad_inf_per_step_N": [g for g, _ in fwd_res],
+                "forward_weight_scale_N": fwd_res[0][1],
+                "forward_grad": "max_i |dG/dx_i| at the end of each step (FP64 reduction); scale = max_i m_i |g|"}}
+
+
+def _gpu_final(mesh, pdict, colors, h, iters, steps, v0, voff=None, toff=None, track_contact=False):
+    """Final positions (float64, caller order) of `steps` steps through the C
+    ABI; with track_contact, also the most vertices below z = 0 after a step."""
+    import numpy as np
+    from paper_2403_06321_b300 import vbd
+    sim = vbd.Sim(mesh, vbd.make_params(**pdict), colors=colors, vert_offset=voff, tet_offset=toff)
+    touched = 0
+    try:
+        sim.set_state(mesh.rest, v0)
+        for _ in range(steps):
+            sim.step(h, iters)
+            if track_contact:
+                x, _ = sim.get_state()
+                touched = max(touched, int((x[:, 2] < 0).sum().item()))
+        sim.sync_status()
+        x, _ = sim.get_state()
+        return x.cpu().numpy().astype(np.float64), touched
+    finally:
+        sim.close()
+
+
+def _oracle_final(oracle, mesh, pdict, colors, h, iters, steps, v0):
+    import numpy as np
+    model = oracle.Model.from_mesh(mesh)
+    p = oracle.Params.make(**pdict)
+    x, v = mesh.rest.copy(), np.array(v0, np.float64)
+    vp = v.copy()
+    for _ in range(steps):
+        model.step(p, colors, int(colors.max()) + 1, h, iters, x, v, vp)
+    return x
+
+
+def _pdict(cfg, **over):
+    d = dict(gravity=cfg.gravity, ground_on=cfg.ground_on, ground_height=cfg.ground_height,
+             ground_normal=cfg.ground_normal, k_c=cfg.k_c, cheby_rho=cfg.cheby_rho, init_mode=cfg.init_mode,
+             det_eps=cfg.det_eps)
+    d.update(over)
+    return d
+
+
+def run_parity() -> dict:
+    """Part of the oracle (CPU) leg: the FP64 oracle runs a sample of every
+    workload and the CUDA path the same sample; the error of each is
+    max |x_gpu - x_oracle| over all vertices after the last step, divided by
+    the bounding-box diagonal (bar 1e-5), and for the adjoint the worst
+    |g_gpu - g_oracle| over max |g_oracle| per gradient column (bar 1e-3).
+    Each line names its sample."""
+    import numpy as np
+    import torch
+    from oracle import oracle
+    from paper_2403_06321_b300 import synth, vbd
+    os.environ.setdefault("VBD_ORACLE_LIB", oracle.build(openmp=True))
+    t0 = time.perf_counter()
+    out = {"bars": {"positions": "max |x_gpu - x_oracle| / bbox diagonal <= 1e-5",
+                    "gradients": "max |g_gpu - g_oracle| / max |g_oracle| per column <= 1e-3"}}
+
+    def diag(x):
+        return float(np.linalg.norm(x.max(0) - x.min(0)))
+
+    # cantilever beam: the whole recipe
+    m, cfg = synth.cantilever_beam()
+    col = synth.kuhn_coloring(m.grid_ijk)
+    pd = _pdict(cfg)
+    z = np.zeros_like(m.rest)
+    xg, _ = _gpu_final(m, pd, col, cfg.h, cfg.iters, cfg.steps, z)
+    xo = _oracle_final(oracle, m, pd, col, cfg.h, cfg.iters, cfg.steps, z)
+    out["cantilever_beam"] = {"sample": "the whole workload (176 verts, 100 steps x 20 iterations)",
+                              "err_over_bbox": float(np.abs(xg - xo).max()) / diag(xo)}
+    # large cube: the benchmark recipe on a 12^3 crop started 5 mm above the ground
+    m, cfg = synth.large_cube(12, drop_height=0.005)
+    col = synth.kuhn_coloring(m.grid_ijk)
+    pd = _pdict(cfg)
+    z = np.zeros_like(m.rest)
+    xg, touched = _gpu_final(m, pd, col, cfg.h, cfg.iters, cfg.steps, z, track_contact=True)
+    xo = _oracle_final(oracle, m, pd, col, cfg.h, cfg.iters, cfg.steps, z)
+    out["large_cube"] = {"sample": "benchmark recipe (jitter seed 1, E=1e6, nu=0.45, k_c=1e7, 20 steps x 100 "
+                                   "iterations) on a 12^3-cube crop (2,197 verts) started 5 mm above the ground",
+                         "err_over_bbox": float(np.abs(xg - xo).max()) / diag(xo),
+                         "vertices_in_ground_contact_max": touched}
+    # beam batch: the three smallest of the first 16 beams of the recipe, as one union
+    meshes, cfg = synth.beam_batch(16)
+    pick = sorted(range(16), key=lambda b: meshes[b].n_verts)[:3]
+    sub = [meshes[b] for b in pick]
+    cat, voff, toff = synth.concat(sub)
+    col = np.concatenate([synth.kuhn_coloring(mm.grid_ijk) for mm in sub])
+    pd = _pdict(cfg)
+    xg, _ = _gpu_final(cat, pd, col, cfg.h, cfg.iters, cfg.steps, np.zeros_like(cat.rest), voff, toff)
+    worst = 0.0
+    for k, mm in enumerate(sub):
+        xo = _oracle_final(oracle, mm, pd, synth.kuhn_coloring(mm.grid_ijk), cfg.h, cfg.iters, cfg.steps,
+                           np.zeros_like(mm.rest))
+        worst = max(worst, float(np.abs(xg[voff[k]:voff[k + 1]] - xo).max()) / diag(mm.rest))
+    out["beam_batch"] = {"sample": "beams %s of the 4096-beam recipe (%d verts) swept as one union, 50 steps x 30 "
+                                   "iterations" % (pick, cat.n_verts), "err_over_bbox": worst}
+    # differentiable beam: its loss and 30 x 50 schedule on the cantilever mesh, adjoint gradients
+    m, _ = synth.cantilever_beam()
+    col = synth.kuhn_coloring(m.grid_ijk)
+    h, iters, steps, adj_iters = 1 / 60, 50, 30, 150
+    tip = np.nonzero(synth.face_mask(m.grid_ijk, (10, 3, 3), "x+"))[0]
+    target = m.rest[tip] + np.random.default_rng(3).uniform(-0.1, 0.1, size=3)
+    pd = _pdict(synth.SimConfig())
+    sim = vbd.Sim(m, vbd.make_params(tape_steps=steps, **pd), colors=col)
+    try:
+        sim.set_state(m.rest, np.zeros_like(m.rest))
+        for _ in range(steps):
+            sim.step(h, iters)
+        x, _ = sim.get_state()
+        xg = x.cpu().numpy().astype(np.float64)
+        g = np.zeros_like(xg)
+        g[tip] = 2.0 / len(tip) * (xg[tip] - target)
+        dev = sim.workspace.device
+        gE = torch.empty(m.n_tets, dtype=torch.float32, device=dev)
+        gv = torch.empty(3 * m.n_verts, dtype=torch.float32, device=dev)
+        vbd.vbd_backward(sim.ctx, torch.tensor(g.reshape(-1), dtype=torch.float32, device=dev), gE, gv, adj_iters)
+        sim.sync_status()
+        gE = gE.cpu().numpy().astype(np.float64)
+        gv = gv.cpu().numpy().astype(np.float64).reshape(-1, 3)
+    finally:
+        sim.close()
+    model = oracle.Model.from_mesh(m)
+    p = oracle.Params.make(**pd)
+    x, v = m.rest.copy(), np.zeros_like(m.rest)
+    vp = v.copy()
+    xs = [x.copy()]
+    for _ in range(steps):
+        model.step(p, col, 4, h, iters, x, v, vp)
+        xs.append(x.copy())
+    go = np.zeros_like(x)
+    go[tip] = 2.0 / len(tip) * (x[tip] - target)
+    oE, ov, _ = oracle.dense_adjoint(model, p, h, xs, go)
+
+    def worst_col(gg, oo):
+        gg, oo = gg.reshape(len(gg), -1), oo.reshape(len(oo), -1)
+        return max(float(np.abs(gg[:, c] - oo[:, c]).max()) / float(np.abs(oo[:, c]).max())
+                   for c in range(oo.shape[1]) if np.abs(oo[:, c]).max() > 0)
+    out["differentiable_beam"] = {
+        "sample": "its loss (tip face to a seeded target) and schedule (30 steps x 50 iterations, %d adjoint "
+                  "iterations) on the cantilever mesh (176 verts, 540 tets)" % adj_iters,
+        "x_err_over_bbox": float(np.abs(xg - x).max()) / diag(x),
+        "dlogE_worst": worst_col(gE, oE), "dv0_worst": worst_col(gv, ov)}
+    # paper scale: the 33M-vertex recipe on a 12^3 crop
+    m, cfg, v0 = synth.paper_scale_cube(12)
+    v0 = v0.astype(np.float32).astype(np.float64)
+    col = synth.kuhn_coloring(m.grid_ijk)
+    pd = _pdict(cfg)
+    xg, _ = _gpu_final(m, pd, col, cfg.h, cfg.iters, cfg.steps, v0)
+    xo = _oracle_final(oracle, m, pd, col, cfg.h, cfg.iters, cfg.steps, v0)
+    out["paper_scale"] = {"sample": "paper-scale recipe (seed 4, N(0, 0.5 m/s) velocities, 5 steps x 20 "
+                                    "iterations) on a 12^3-cube crop", "err_over_bbox": float(np.abs(xg - xo).max())
+                          / diag(xo)}
+    out["seconds"] = time.perf_counter() - t0
+    return out
+
+
+def timed_steps(sim, h: float, iters: int, K: int, stream):
+    """K steps with CUDA events on the sim's stream: (total ms, iteration
+    phase ms, per-step ms)."""
+    import torch
+    from paper_2403_06321_b300 import vbd
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    torch.cuda.synchronize()
+    for k in range(K):
+        ev[k].record(stream)
+        vbd.vbd_begin_step(sim.ctx, h)
+        ev_a[k].record(stream)
+        vbd.vbd_iterate(sim.ctx, iters)
+        ev_b[k].record(stream)
+        vbd.vbd_end_step(sim.ctx)
+    ev[K].record(stream)
+    torch.cuda.synchronize()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(K)]
+    return ev[0].elapsed_time(ev[K]), sum(a.elapsed_time(b) for a, b in zip(ev_a, ev_b)), per
+
+
+def run_paper_scale(args) -> dict:
+    """The paper-scale recipe at full size: 320^3 cubes (33,076,161 verts,
+    196,608,000 tets, about 1e8 DoFs), N(0, 0.5 m/s) velocities (seed 4),
+    h = 1/60, 20 iterations per step, 5 timed steps after 1 warm-up step,
+    HBM resident (a 67 GB workspace).  Skipped, with the reason, when the host
+    or the GPU lacks the memory."""
+    import numpy as np
+    import torch
+    from paper_2403_06321_b300 import synth, vbd
+    try:
+        import psutil
+        host_free = psutil.virtual_memory().available
+    except ImportError:
+        host_free = 0
+    dev_free, _ = torch.cuda.mem_get_info()
+    if host_free < 80e9 or dev_free < 80e9:
+        return {"skipped": "needs 80 GB of free host and device memory (host %.0f GB, device %.0f GB free)" % (
+            host_free / 1e9, dev_free / 1e9)}
+    t0 = time.perf_counter()
+    m, cfg, v0 = synth.paper_scale_cube(320)
+    colors = synth.kuhn_coloring(m.grid_ijk)
+    stream = torch.cuda.Stream()
+    sim = vbd.Sim(m, vbd.make_params(**_pdict(cfg)), colors=colors, stream=stream)
+    setup_s = time.perf_counter() - t0
+    try:
+        info = sim.info
+        sim.set_state(m.rest, v0)
+        vbd.vbd_autotune(sim.ctx, cfg.h, 2)
+        info = vbd.vbd_get_info(sim.ctx)
+        sim.set_state(m.rest, v0)
+        sim.step(cfg.h, cfg.iters)  # warm-up (graph capture)
+        sim.set_state(m.rest, v0)
+        clocks = ClockSampler(gpu_id_of(torch.cuda.current_device()))
+        time.sleep(0.3)
+        t_ms, sweep_ms, per = timed_steps(sim, cfg.h, cfg.iters, cfg.steps, stream)
+        clk = clocks.stop()
+        sim.sync_status()
+    finally:
+        sim.close()
+    n_upd = float(info.n_free) * cfg.iters * cfg.steps
+    C = info.n_colors
+    b_upd = 4.0 * m.n_tets / m.n_verts * B_INC + B_VTX + B_X * C
+    launches = cfg.steps * cfg.iters * C
+    avg_launch_s = sweep_ms / 1e3 / launches
+    achieved = info.n_free / C * b_upd / avg_launch_s / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    return {"workload": "paper_scale: 320^3 cubes x 6 tets (%d verts, %d tets), N(0, 0.5 m/s) velocities, ground "
+                        "k_c=1e7, h=1/60, %d iterations/step, %d steps" % (m.n_verts, m.n_tets, cfg.iters,
+                                                                         cfg.steps),
+            "value": n_upd / (t_ms / 1e3), "unit": UNIT, "ms_per_step": t_ms / cfg.steps,
+            "ms_per_step_each": per, "setup_s": setup_s,
+            "launch": {"sweep_variant": VARIANTS[info.pipeline], "lanes_per_vertex": info.lanes_per_vertex,
+                       "block_threads": info.block_threads},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind, "alg_bytes_per_update": b_upd,
+                         "avg_launch_us": avg_launch_s * 1e6},
+            "clocks": clk}
 
 
 def run_chebyshev(args) -> dict:
@@ -685,36 +937,23 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     def timed_region():
-        ev_start = torch.cuda.Event(enable_timing=True)
-        ev_end = torch.cuda.Event(enable_timing=True)
-        ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-        ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
         clocks = ClockSampler(gpu_id_of(local))
         time.sleep(0.3)
         barrier(world)
-        torch.cuda.synchronize()
-        ev_start.record(stream)
-        for k in range(K):
-            vbd.vbd_begin_step(sim.ctx, h)
-            ev_a[k].record(stream)
-            vbd.vbd_iterate(sim.ctx, iters)
-            ev_b[k].record(stream)
-            vbd.vbd_end_step(sim.ctx)
-        ev_end.record(stream)
-        torch.cuda.synchronize()
+        t_ms, sweep_ms, per_step = timed_steps(sim, h, iters, K, stream)
         barrier(world)
         clk = clocks.stop()
         sim.sync_status()  # raises on non-finite updates
-        return (ev_start.elapsed_time(ev_end), sum(a.elapsed_time(b) for a, b in zip(ev_a, ev_b)), clk)
+        return t_ms, sweep_ms, per_step, clk
 
-    t_ms, sweep_ms, clk = timed_region()
+    t_ms, sweep_ms, per_step, clk = timed_region()
     if any_rank(clocks_rejected(clk), world):  # throttled or clock-locked: measure once more
         first = clk
         sim.set_state(m.rest, zeros)
         for _ in range(args.warmup):
             sim.step(h, iters)
         sim.set_state(m.rest, zeros)
-        t_ms, sweep_ms, clk = timed_region()
+        t_ms, sweep_ms, per_step, clk = timed_region()
         clk = dict(clk, remeasured_after=first)
     units = float(info.n_free) * iters * K
     t_job, units_job = reduce_job(t_ms / 1e3, units, world)
@@ -778,14 +1017,26 @@ def run_ours(args):
         "gpu_launches": K * launches_per_step(args, info, iters, C),
         "clocks": clk,
     }
+    groups = [g for g in (per_step[k * K // 5:(k + 1) * K // 5] for k in range(5)) if g]
+    if len(groups) == 5:
+        rates = [info.n_free * iters * len(g) / (sum(g) / 1e3) for g in groups]
+        line["median_of_5"] = {"value": statistics.median(rates), "unit": UNIT,
+                               "groups": rates, "how": "the K timed steps split into 5 consecutive groups, "
+                                                       "rate of each group, median (this rank)"}
     if not args.no_extras and world == 1 and args.scene == "cube":
         line["batched"] = run_batched(args)
         line["adjoint"] = run_adjoint(args)
         line["self_collision"] = run_self_collision(args)
         line["chebyshev"] = run_chebyshev(args)
         line["small_configs"] = run_small_configs(args)
+        if not args.no_paper_scale:
+            line["paper_scale"] = run_paper_scale(args)
     if not args.no_cpu_baseline and world == 1:
+        # the oracle leg: timed on this host's cores, and compared with the
+        # CUDA path on a sample of every workload
         line["cpu_baseline"] = run_cpu_baseline()
+        if args.scene == "cube":
+            line["parity"] = run_parity()
     print(json.dumps(line), flush=True)
     return 0
 
@@ -796,7 +1047,8 @@ def run_only(args) -> int:
     build()
     torch.cuda.set_device(0)
     fn = {"batched": run_batched, "adjoint": run_adjoint, "self_collision": run_self_collision,
-          "chebyshev": run_chebyshev, "small_configs": run_small_configs}[args.only]
+          "chebyshev": run_chebyshev, "small_configs": run_small_configs, "paper_scale": run_paper_scale,
+          "parity": lambda _a: run_parity()}[args.only]
     print(json.dumps({"only": args.only, args.only: fn(args)}), flush=True)
     return 0
 

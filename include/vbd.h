@@ -367,6 +367,30 @@ vbd_status vbd_sync_status(vbd_ctx *ctx, int64_t *det_skips, int64_t *contacts);
 vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, float *dL_dv0,
                         int32_t adj_iters);
 
+/* Convergence of the last vbd_backward (no paper counterpart): the adjoint
+ * treats every recorded step as converged and solves H lam = r by a fixed
+ * number of block Gauss-Seidel sweeps, so it reports how far each solve got.
+ * After the sweeps of each step one more pass over all free vertices takes
+ * max_i |r_i - (H lam)_i| and max_i |r_i| (per vertex in FP32, reduced in
+ * FP64; for a subspace-constrained vertex the part within its subspace).
+ * rel_out (host, n >= the number of recorded steps, else
+ * VBD_ERR_INVALID_ARG) receives, per recorded step t in forward order,
+ * max |r - H lam| / max |r| (0 when r = 0).  VBD_ERR_NO_TAPE before any
+ * vbd_backward.  Synchronising. */
+vbd_status vbd_adjoint_residuals(vbd_ctx *ctx, double *rel_out, int32_t n);
+
+/* Convergence of the current step's iterate (no paper counterpart; a report
+ * on how far the fixed iteration count of Algorithm 1 left the minimiser of
+ * G, Eqs. 1-2): *grad_inf_out = max over free vertices of |dG/dx_i|, the
+ * force residual of Eq. 8 with the ground and wall penalties of Eq. 12 at
+ * the current x and the inertia target y of the current (or last) step, in
+ * newtons; self-contact, damping and friction terms are not included (the
+ * last two are not part of G).  Per vertex in FP32 like the sweep, reduced
+ * in FP64.  force_scale_out (may be NULL) receives max_i m_i |a_ext|, the
+ * largest weight, as a scale.  VBD_ERR_STATE before the first step.
+ * Synchronising. */
+vbd_status vbd_gradient_norm(vbd_ctx *ctx, double *grad_inf_out, double *force_scale_out);
+
 /* Sweep launch shape and kernel variant.  variant:
  *  0  plain: one thread group of lanes_per_vertex in {4, 8, 16, 32} per
  *     vertex, loading its slot records from global memory, block_threads in

@@ -16,7 +16,7 @@ HEADERS = [os.path.join(CSRC, "vbd_kernels.h"), os.path.join(CSRC, "vbd_geom.cuh
 NVCC_FLAGS = [
     "-O3", "-std=c++17", "-lineinfo",
     "-gencode", "arch=compute_103a,code=sm_103a",
-    "-Xcompiler", "-fPIC,-O2",
+    "-Xcompiler", "-fPIC,-O2,-fopenmp",
     "-Xptxas", "-v",
 ]
 
@@ -28,14 +28,16 @@ def _nvcc() -> str:
     return "nvcc"
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, defines=()) -> str:
+    """Compiles libvbd.so when a source is newer than it (or force).  defines:
+    extra -D macros (tuning experiments)."""
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     newest = max(os.path.getmtime(p) for p in srcs + HEADERS + [__file__])
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [_nvcc(), *NVCC_FLAGS, "-shared", "-cudart", "static",
-           "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-o", tmp, *srcs]
+    cmd = [_nvcc(), *NVCC_FLAGS, *["-D" + d for d in defines], "-shared", "-cudart", "static",
+           "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-o", tmp, *srcs, "-lgomp"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     log = os.path.join(CSRC, "..", "build_ptxas.log")
     with open(log, "w") as f:

@@ -3,8 +3,9 @@
 // implicit function theorem to dG/dx = 0 of Eq. 2, with y from Eq. 3 and the
 // velocity update of Eq. 6).
 //
-// Positions are displacements u = x - X (tape rows included), and the element
-// is evaluated from F = I + D as in the forward sweep.
+// Positions are displacements u = x - X (tape rows included).  The sweep
+// evaluates the tet through its current edge vectors (see k_adj_sweep), the
+// parameter gradient from F = I + D as in the forward sweep.
 // For a recorded step t with end positions x_{t+1} and H = M/h^2 + d2E/dx2
 // (+ the ground and wall penalty Hessians), going backwards:
 //   r = xbar_{t+1} + vbar_{t+1} / h,   H lam = r   (colour-ordered block GS),
@@ -84,10 +85,34 @@ __device__ __forceinline__ DForm make_dform(const float3 d[3], const float3 g[3]
     return f;
 }
 
+// Per slot the sweep needs only products of H with lam, never P(F) itself, so
+// it works with the tet's current edge vectors y_k = x_k - x_i (k = a, b, c,
+// the slot's three other vertices) instead of F = I + D.  With B the inverse
+// rest edge matrix (rows g_a, g_b, g_c), det_g = det B, and the rest edges
+// e_k = (g_{k+1} x g_{k+2}) / det_g (cyclic; the columns of B^-1):
+//   J          = det_g  y_a . (y_b x y_c)
+//   cof(F) g_a = det_g (y_b x y_c), cyclic, so c_i = cof(F) g_i
+//              = -det_g (y_b - y_a) x (y_c - y_a)
+//   cof F : dF = det_g sum_k lam_k . (y_{k+1} x y_{k+2})        (dF = sum_k lam_k g_k^T)
+//   dcof(F)[dF] g_i = -det_g [(lam_b - lam_a) x (y_c - y_a) + (y_b - y_a) x (lam_c - lam_a)]
+//   dF g_i     = sum_k lam_k (g_k . g_i)
+// and sum_k H_ik lam_k = V [mu dF g_i + lam (cof F : dF) c_i + lam (J - alpha) dcof(F)[dF] g_i].
+// J - 1 now comes from a determinant near 1, but only J - alpha = (J - 1) -
+// mu/lam enters, whose size is set by mu/lam, so its rounding stays at the
+// FP32 level; no step takes a difference of nearly equal O(1) numbers.
+// MODE 0: one Gauss-Seidel update of lam_i; MODE 1: r - (H lam)_i of the
+// subspace-constrained vertices into rhs (lam unchanged); MODE 2: over all
+// free vertices at once, max_i |r_i - (H lam)_i| (projected onto the
+// subspace of a constrained vertex) and max_i |r_i| into res_out[0], [1]
+// (FP64, atomic max of the non-negative doubles' bit patterns).
+// launched with 128 threads, VBD_ADJ_MIN_BLOCKS resident CTAs per SM (8:
+// held to 64 registers)
+#ifndef VBD_ADJ_MIN_BLOCKS
+#define VBD_ADJ_MIN_BLOCKS 8
+#endif
 template <int L>
-// launched with 128 threads and held to 64 registers (8 CTAs per SM; a 12-byte
-// spill), measured 1.7 % faster than 70 registers at 7 CTAs
-__global__ void __launch_bounds__(128, 8) k_adj_sweep(Dev d, const float4 *__restrict__ xs, SweepParams p) {
+__global__ void __launch_bounds__(128, VBD_ADJ_MIN_BLOCKS) k_adj_sweep(Dev d, const float4 *__restrict__ xs, SweepParams p,
+                                                      double *res_out) {
     const int lane = threadIdx.x & (L - 1);
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int vi = p.vbegin + (int)(gt / L);
@@ -105,59 +130,43 @@ __global__ void __launch_bounds__(128, 8) k_adj_sweep(Dev d, const float4 *__res
         const int4 r0 = __ldcs(d.s0 + s);
         const float4 r1 = __ldcs(d.s1 + s);
         const float4 r2 = __ldcs(d.s2 + s);
-        const int nb[3] = {r0.x, r0.y, r0.z};
-        float3 g[3];
-        g[0] = make_float3(__int_as_float(r0.w), r1.x, r1.y);
-        g[1] = make_float3(r1.z, r1.w, r2.x);
-        g[2] = make_float3(r2.y, r2.z, r2.w);
-        // tet volume from the gradients; mu, lambda of the vertex, or of the
-        // tet when materials differ around vertices (after vbd_set_log_young)
-        const float V = __frcp_rn(6.0f * fabsf(dot(g[0], cross(g[1], g[2]))));
+        const float3 ga = make_float3(__int_as_float(r0.w), r1.x, r1.y);
+        const float3 gb = make_float3(r1.z, r1.w, r2.x);
+        const float3 gc = make_float3(r2.y, r2.z, r2.w);
+        const float3 la = f3(d.lam[r0.x]), lb = f3(d.lam[r0.y]), lc = f3(d.lam[r0.z]);  // other colours only
+        const float3 da = sub(f3(__ldg(xs + r0.x)), ui), db = sub(f3(__ldg(xs + r0.y)), ui),
+                     dc = sub(f3(__ldg(xs + r0.z)), ui);
+        const float3 gbc = cross(gb, gc);
+        const float detg = dot(ga, gbc);
+        const float inv = __frcp_rn(detg);
+        // current edges y_k = e_k + (u_k - u_i)
+        const float3 ea = gbc, eb = cross(gc, ga), ec = cross(ga, gb);
+        const float3 ya = make_float3(fmaf(ea.x, inv, da.x), fmaf(ea.y, inv, da.y), fmaf(ea.z, inv, da.z));
+        const float3 yb = make_float3(fmaf(eb.x, inv, db.x), fmaf(eb.y, inv, db.y), fmaf(eb.z, inv, db.z));
+        const float3 yc = make_float3(fmaf(ec.x, inv, dc.x), fmaf(ec.y, inv, dc.y), fmaf(ec.z, inv, dc.z));
+        const float3 Xa = cross(yb, yc), Xb = cross(yc, ya), Xc = cross(ya, yb);
+        const float V = __frcp_rn(6.0f * fabsf(detg));
         float2 mat = vm;
         if (p.per_tet_mat) {
             const int j = __ldcs(d.slot_tet + s);
             mat = make_float2(__ldg(d.tet_mu + j), __ldg(d.tet_lam + j));
         }
         const float Vmu = V * mat.x, Vlam = V * mat.y;
-        const float3 gi = make_float3(-(g[0].x + g[1].x + g[2].x), -(g[0].y + g[1].y + g[2].y),
-                                      -(g[0].z + g[1].z + g[2].z));
-        float3 e[3], lk[3];
-        for (int k = 0; k < 3; ++k) {
-            e[k] = sub(f3(__ldg(xs + nb[k])), ui);
-            lk[k] = f3(d.lam[nb[k]]);  // written by other colours' launches only
-        }
-        const DForm F = make_dform(e, g);
-        const float3 ci = F.cof(gi);
-        const float kJ = Vlam * F.jm1 - Vmu;  // V lam (J - alpha)
-        // sum_k H_ik lam_k = V [mu dF g_i + lam (cof F : dF) c_i + lam (J - alpha) dcof(F)[dF] g_i]
-        // with the direction dF = sum_k lam_k g_k^T (columns dF0..dF2); the last
-        // term equals sum_k (F (g_k x g_i)) x lam_k, the skew part of the blocks.
-        float3 dF0 = make_float3(0.f, 0.f, 0.f), dF1 = dF0, dF2 = dF0;
-        for (int k = 0; k < 3; ++k) {
-            dF0.x += lk[k].x * g[k].x; dF0.y += lk[k].y * g[k].x; dF0.z += lk[k].z * g[k].x;
-            dF1.x += lk[k].x * g[k].y; dF1.y += lk[k].y * g[k].y; dF1.z += lk[k].z * g[k].y;
-            dF2.x += lk[k].x * g[k].z; dF2.y += lk[k].y * g[k].z; dF2.z += lk[k].z * g[k].z;
-        }
-        const float3 dFg = mulF(dF0, dF1, dF2, gi);
-        // cof F : dF, with cof(F) e_c = (1 + tr D) e_c - D^T e_c + cof(D) e_c
-        const float trdF = dF0.x + dF1.y + dF2.z;
-        const float trdFD = dF0.x * F.D0.x + dF0.y * F.D1.x + dF0.z * F.D2.x +
-                            dF1.x * F.D0.y + dF1.y * F.D1.y + dF1.z * F.D2.y +
-                            dF2.x * F.D0.z + dF2.y * F.D1.z + dF2.z * F.D2.z;
-        const float sc = (1.f + F.tr) * trdF - trdFD + dot(dF0, F.q0) + dot(dF1, F.q1) + dot(dF2, F.q2);
-        // dcof(F)[dF] g_i: cof F has columns f1 x f2, f2 x f0, f0 x f1 (f_c = e_c + D_c)
-        const float3 f0 = make_float3(1.f + F.D0.x, F.D0.y, F.D0.z);
-        const float3 f1 = make_float3(F.D1.x, 1.f + F.D1.y, F.D1.z);
-        const float3 f2 = make_float3(F.D2.x, F.D2.y, 1.f + F.D2.z);
-        const float3 c0 = cross(dF1, f2), c0b = cross(f1, dF2);
-        const float3 c1 = cross(dF2, f0), c1b = cross(f2, dF0);
-        const float3 c2 = cross(dF0, f1), c2b = cross(f0, dF1);
-        const float3 w = make_float3(gi.x * (c0.x + c0b.x) + gi.y * (c1.x + c1b.x) + gi.z * (c2.x + c2b.x),
-                                     gi.x * (c0.y + c0b.y) + gi.y * (c1.y + c1b.y) + gi.z * (c2.y + c2b.y),
-                                     gi.x * (c0.z + c0b.z) + gi.y * (c1.z + c1b.z) + gi.z * (c2.z + c2b.z));
-        float3 q = make_float3(Vmu * dFg.x + kJ * w.x, Vmu * dFg.y + kJ * w.y, Vmu * dFg.z + kJ * w.z);
-        q.x += Vlam * ci.x * sc; q.y += Vlam * ci.y * sc; q.z += Vlam * ci.z * sc;
-        a.q0 += q.x; a.q1 += q.y; a.q2 += q.z;
+        const float J = detg * dot(ya, Xa);
+        const float3 ci = make_float3(-detg * (Xa.x + Xb.x + Xc.x), -detg * (Xa.y + Xb.y + Xc.y),
+                                      -detg * (Xa.z + Xb.z + Xc.z));
+        const float sc = detg * (dot(la, Xa) + dot(lb, Xb) + dot(lc, Xc));
+        const float3 lba = sub(lb, la), lca = sub(lc, la), yba = sub(yb, ya), yca = sub(yc, ya);
+        const float3 w1 = cross(lba, yca), w2 = cross(yba, lca);
+        const float3 gi = make_float3(-(ga.x + gb.x + gc.x), -(ga.y + gb.y + gc.y), -(ga.z + gb.z + gc.z));
+        const float pa = dot(ga, gi), pb = dot(gb, gi), pc = dot(gc, gi);
+        const float3 dFg = make_float3(la.x * pa + lb.x * pb + lc.x * pc, la.y * pa + lb.y * pb + lc.y * pc,
+                                       la.z * pa + lb.z * pb + lc.z * pc);
+        const float kJ = -(Vlam * (J - 1.0f) - Vmu) * detg;  // V lam (J - alpha) times -det_g of w
+        const float ks = Vlam * sc;
+        a.q0 += Vmu * dFg.x + ks * ci.x + kJ * (w1.x + w2.x);
+        a.q1 += Vmu * dFg.y + ks * ci.y + kJ * (w1.y + w2.y);
+        a.q2 += Vmu * dFg.z + ks * ci.z + kJ * (w1.z + w2.z);
         const float dd = Vmu * dot(gi, gi);
         a.h00 += dd + Vlam * ci.x * ci.x;
         a.h11 += dd + Vlam * ci.y * ci.y;
@@ -169,72 +178,98 @@ __global__ void __launch_bounds__(128, 8) k_adj_sweep(Dev d, const float4 *__res
     a.q0 = sub_reduce<L>(a.q0); a.q1 = sub_reduce<L>(a.q1); a.q2 = sub_reduce<L>(a.q2);
     a.h00 = sub_reduce<L>(a.h00); a.h01 = sub_reduce<L>(a.h01); a.h02 = sub_reduce<L>(a.h02);
     a.h11 = sub_reduce<L>(a.h11); a.h12 = sub_reduce<L>(a.h12); a.h22 = sub_reduce<L>(a.h22);
-    if (!(active && lane == 0)) return;
-    const float mh2 = d.mass[vi] * p.inv_h2;
-    const float4 r = d.rhs[vi];
-    const float b0 = r.x - a.q0, b1 = r.y - a.q1, b2 = r.z - a.q2;
-    float h00 = a.h00 + mh2, h11 = a.h11 + mh2, h22 = a.h22 + mh2, h01 = a.h01, h02 = a.h02, h12 = a.h12;
-    if (p.n_planes > 0) {  // ground and wall penalty Hessians (Eq. 12, Sec. 3.4)
-        const float4 X = d.rest[vi];
-        for (int k = 0; k < p.n_planes; ++k) {
-            const float4 pl = p.planes[k];
-            const float pen = pl.w - (pl.x * (X.x + ui.x) + pl.y * (X.y + ui.y) + pl.z * (X.z + ui.z));
-            if (pen > 0.f) {
-                h00 += p.kc * pl.x * pl.x; h11 += p.kc * pl.y * pl.y; h22 += p.kc * pl.z * pl.z;
-                h01 += p.kc * pl.x * pl.y; h02 += p.kc * pl.x * pl.z; h12 += p.kc * pl.y * pl.z;
+    const bool owner = active && lane == 0;
+    float res_max = 0.f, r_max = 0.f;
+    if (owner) {
+        const float mh2 = d.mass[vi] * p.inv_h2;
+        const float4 r = d.rhs[vi];
+        const float b0 = r.x - a.q0, b1 = r.y - a.q1, b2 = r.z - a.q2;
+        float h00 = a.h00 + mh2, h11 = a.h11 + mh2, h22 = a.h22 + mh2, h01 = a.h01, h02 = a.h02, h12 = a.h12;
+        if (p.n_planes > 0) {  // ground and wall penalty Hessians (Eq. 12, Sec. 3.4)
+            const float4 X = d.rest[vi];
+            for (int k = 0; k < p.n_planes; ++k) {
+                const float4 pl = p.planes[k];
+                const float pen = pl.w - (pl.x * (X.x + ui.x) + pl.y * (X.y + ui.y) + pl.z * (X.z + ui.z));
+                if (pen > 0.f) {
+                    h00 += p.kc * pl.x * pl.x; h11 += p.kc * pl.y * pl.y; h22 += p.kc * pl.z * pl.z;
+                    h01 += p.kc * pl.x * pl.y; h02 += p.kc * pl.x * pl.z; h12 += p.kc * pl.y * pl.z;
+                }
             }
         }
-    }
-    const int sub = p.n_sub > 0 ? d.sub_id[vi] : -1;
-    if (p.adj_residual) {
-        // after the sweeps: r - (H lam)_i = b - H_ii lam_i of a constrained vertex,
-        // the part of xbar that follows x_t across its constrained directions
-        if (sub >= 0) {
+        const int sub = p.n_sub > 0 ? d.sub_id[vi] : -1;
+        if (p.adj_residual != 0) {
+            // r - (H lam)_i = b - H_ii lam_i
             const float4 l = d.lam[vi];
-            d.rhs[vi] = make_float4(b0 - (h00 * l.x + h01 * l.y + h02 * l.z), b1 - (h01 * l.x + h11 * l.y + h12 * l.z),
-                                    b2 - (h02 * l.x + h12 * l.y + h22 * l.z), 0.f);
-        }
-        return;
-    }
-    float l0, l1, l2;
-    if (sub >= 0) {
-        // reduced block (Sec. 3.4): lam_i = Q (Q^T H_ii Q)^-1 Q^T b
-        const float4 qa = d.sub_q[2 * sub], qb = d.sub_q[2 * sub + 1];
-        const float ha0 = h00 * qa.x + h01 * qa.y + h02 * qa.z;
-        const float ha1 = h01 * qa.x + h11 * qa.y + h12 * qa.z;
-        const float ha2 = h02 * qa.x + h12 * qa.y + h22 * qa.z;
-        const float A00 = qa.x * ha0 + qa.y * ha1 + qa.z * ha2;
-        const float c0 = qa.x * b0 + qa.y * b1 + qa.z * b2;
-        float z0, z1 = 0.f;
-        if (qa.w < 1.5f) {
-            z0 = c0 / A00;
+            float e0 = b0 - (h00 * l.x + h01 * l.y + h02 * l.z), e1 = b1 - (h01 * l.x + h11 * l.y + h12 * l.z),
+                  e2 = b2 - (h02 * l.x + h12 * l.y + h22 * l.z);
+            if (p.adj_residual == 1) {
+                // the part of xbar that follows x_t across a constrained vertex's fixed directions
+                if (sub >= 0) d.rhs[vi] = make_float4(e0, e1, e2, 0.f);
+            } else {
+                if (sub >= 0) {  // only Q^T (r - H lam) is solved for: project onto span(Q)
+                    const float4 qa = d.sub_q[2 * sub], qb = d.sub_q[2 * sub + 1];
+                    const float z0 = qa.x * e0 + qa.y * e1 + qa.z * e2;
+                    const float z1 = qa.w < 1.5f ? 0.f : qb.x * e0 + qb.y * e1 + qb.z * e2;
+                    e0 = qa.x * z0 + qb.x * z1;
+                    e1 = qa.y * z0 + qb.y * z1;
+                    e2 = qa.z * z0 + qb.z * z1;
+                }
+                res_max = fmaxf(fabsf(e0), fmaxf(fabsf(e1), fabsf(e2)));
+                r_max = fmaxf(fabsf(r.x), fmaxf(fabsf(r.y), fabsf(r.z)));
+            }
         } else {
-            const float A01 = qb.x * ha0 + qb.y * ha1 + qb.z * ha2;
-            const float A11 = qb.x * (h00 * qb.x + h01 * qb.y + h02 * qb.z) +
-                              qb.y * (h01 * qb.x + h11 * qb.y + h12 * qb.z) +
-                              qb.z * (h02 * qb.x + h12 * qb.y + h22 * qb.z);
-            const float c1 = qb.x * b0 + qb.y * b1 + qb.z * b2;
-            const float inv2 = 1.f / (A00 * A11 - A01 * A01);
-            z0 = (A11 * c0 - A01 * c1) * inv2;
-            z1 = (A00 * c1 - A01 * c0) * inv2;
+            float l0, l1, l2;
+            if (sub >= 0) {
+                // reduced block (Sec. 3.4): lam_i = Q (Q^T H_ii Q)^-1 Q^T b
+                const float4 qa = d.sub_q[2 * sub], qb = d.sub_q[2 * sub + 1];
+                const float ha0 = h00 * qa.x + h01 * qa.y + h02 * qa.z;
+                const float ha1 = h01 * qa.x + h11 * qa.y + h12 * qa.z;
+                const float ha2 = h02 * qa.x + h12 * qa.y + h22 * qa.z;
+                const float A00 = qa.x * ha0 + qa.y * ha1 + qa.z * ha2;
+                const float c0 = qa.x * b0 + qa.y * b1 + qa.z * b2;
+                float z0, z1 = 0.f;
+                if (qa.w < 1.5f) {
+                    z0 = c0 / A00;
+                } else {
+                    const float A01 = qb.x * ha0 + qb.y * ha1 + qb.z * ha2;
+                    const float A11 = qb.x * (h00 * qb.x + h01 * qb.y + h02 * qb.z) +
+                                      qb.y * (h01 * qb.x + h11 * qb.y + h12 * qb.z) +
+                                      qb.z * (h02 * qb.x + h12 * qb.y + h22 * qb.z);
+                    const float c1 = qb.x * b0 + qb.y * b1 + qb.z * b2;
+                    const float inv2 = 1.f / (A00 * A11 - A01 * A01);
+                    z0 = (A11 * c0 - A01 * c1) * inv2;
+                    z1 = (A00 * c1 - A01 * c0) * inv2;
+                }
+                l0 = qa.x * z0 + qb.x * z1;
+                l1 = qa.y * z0 + qb.y * z1;
+                l2 = qa.z * z0 + qb.z * z1;
+            } else {
+                const float a00 = h11 * h22 - h12 * h12, a01 = h02 * h12 - h01 * h22, a02 = h01 * h12 - h02 * h11;
+                const float a11 = h00 * h22 - h02 * h02, a12 = h01 * h02 - h00 * h12, a22 = h00 * h11 - h01 * h01;
+                const float det = h00 * a00 + h01 * a01 + h02 * a02;
+                const float invd = 1.f / det;
+                l0 = (a00 * b0 + a01 * b1 + a02 * b2) * invd;
+                l1 = (a01 * b0 + a11 * b1 + a12 * b2) * invd;
+                l2 = (a02 * b0 + a12 * b1 + a22 * b2) * invd;
+            }
+            if (!(isfinite(l0) && isfinite(l1) && isfinite(l2)))
+                atomicAdd(d.counters + 0, 1ull);
+            else
+                d.lam[vi] = make_float4(l0, l1, l2, 0.f);
         }
-        l0 = qa.x * z0 + qb.x * z1;
-        l1 = qa.y * z0 + qb.y * z1;
-        l2 = qa.z * z0 + qb.z * z1;
-    } else {
-        const float a00 = h11 * h22 - h12 * h12, a01 = h02 * h12 - h01 * h22, a02 = h01 * h12 - h02 * h11;
-        const float a11 = h00 * h22 - h02 * h02, a12 = h01 * h02 - h00 * h12, a22 = h00 * h11 - h01 * h01;
-        const float det = h00 * a00 + h01 * a01 + h02 * a02;
-        const float inv = 1.f / det;
-        l0 = (a00 * b0 + a01 * b1 + a02 * b2) * inv;
-        l1 = (a01 * b0 + a11 * b1 + a12 * b2) * inv;
-        l2 = (a02 * b0 + a12 * b1 + a22 * b2) * inv;
     }
-    if (!(isfinite(l0) && isfinite(l1) && isfinite(l2))) {
-        atomicAdd(d.counters + 0, 1ull);
-        return;
+    if (p.adj_residual == 2) {
+        // the mode is uniform over the grid, so every lane of the warp is here
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            res_max = fmaxf(res_max, __shfl_xor_sync(FULL, res_max, off));
+            r_max = fmaxf(r_max, __shfl_xor_sync(FULL, r_max, off));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMax((unsigned long long *)res_out, (unsigned long long)__double_as_longlong((double)res_max));
+            atomicMax((unsigned long long *)res_out + 1, (unsigned long long)__double_as_longlong((double)r_max));
+        }
     }
-    d.lam[vi] = make_float4(l0, l1, l2, 0.f);
 }
 
 // xbar, vbar <- seed; lam <- 0; gtheta <- 0 is done by the host (memset).
@@ -331,15 +366,15 @@ void launch_adj_rhs(const Dev &d, int n, int n_free, float inv_h, cudaStream_t s
 }
 
 void launch_adj_sweep(const Dev &d, const float4 *xs, const SweepParams &p, int lanes, int block,
-                      cudaStream_t s) {
+                      cudaStream_t s, double *res_out) {
     const long long threads = (long long)(p.vend - p.vbegin) * lanes;
     if (threads <= 0) return;
     const unsigned grid = blocks_for(threads, block);
     switch (lanes) {
-    case 4: k_adj_sweep<4><<<grid, block, 0, s>>>(d, xs, p); break;
-    case 8: k_adj_sweep<8><<<grid, block, 0, s>>>(d, xs, p); break;
-    case 16: k_adj_sweep<16><<<grid, block, 0, s>>>(d, xs, p); break;
-    default: k_adj_sweep<32><<<grid, block, 0, s>>>(d, xs, p); break;
+    case 4: k_adj_sweep<4><<<grid, block, 0, s>>>(d, xs, p, res_out); break;
+    case 8: k_adj_sweep<8><<<grid, block, 0, s>>>(d, xs, p, res_out); break;
+    case 16: k_adj_sweep<16><<<grid, block, 0, s>>>(d, xs, p, res_out); break;
+    default: k_adj_sweep<32><<<grid, block, 0, s>>>(d, xs, p, res_out); break;
     }
 }
 

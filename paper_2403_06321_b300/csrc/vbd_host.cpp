@@ -37,7 +37,10 @@ struct Range {
 
 constexpr int kMaxColors = 4096;
 // adjoint sweep launch shape (measured best on B300; independent of the forward's)
-constexpr int kAdjLanes = 4, kAdjBlock = 128;
+#ifndef VBD_ADJ_LANES
+#define VBD_ADJ_LANES 4
+#endif
+constexpr int kAdjLanes = VBD_ADJ_LANES, kAdjBlock = 128;
 
 struct GraphEntry {
     int first_n, iters;
@@ -98,6 +101,7 @@ struct vbd_ctx {
     float h = 0.f;
     int iter_in_step = 0;
     int tape_len = 0;
+    int adj_res_len = 0;        // steps with adjoint residuals from the last vbd_backward
     std::vector<float> tape_h;
     // launch shape / graphs
     int lanes = 4, block = 256;
@@ -337,6 +341,8 @@ size_t carve(const vbd_ctx *c, char *base, Dev *d) {
     t.counters = (unsigned long long *)take(8 * 8);
     t.partials = (double *)take(8 * (size_t)vbd::energy_partials_needed(c->n_free, c->T, surf_count(c)));
     t.energy_out = (double *)take(8);
+    t.gnorm = (double *)take(16);
+    t.adj_res = (double *)take(16 * (size_t)std::max(c->params.tape_steps, 1));
     t.tape = (float4 *)take(16 * N * (size_t)std::max(c->params.tape_steps, 0));
     t.lam = (float4 *)take(16 * N);
     t.rhs = (float4 *)take(16 * N);
@@ -579,9 +585,10 @@ void enqueue_iterations(vbd_ctx *c, int first_n, int iters, cudaStream_t s) {
 // the other three vertices' ids and shape gradients (volume and material are
 // not stored per slot).
 void build_slots(const vbd_ctx *c, int k0, int k1, int4 *s0, float4 *s1, float4 *s2, int *stet, int *sloc) {
-    size_t w = 0;
+#pragma omp parallel for schedule(static, 4096)
     for (int k = k0; k < k1; ++k) {
         const int i = c->orig_of_new[k];
+        size_t w = (size_t)c->slot_off[k] - (size_t)c->slot_off[k0];
         for (int q = c->inc_off[i]; q < c->inc_off[i + 1]; ++q, ++w) {
             const int j = c->inc_tet[q], a = c->inc_loc[q];
             const double *Bj = &c->B[9 * (size_t)j];
@@ -811,43 +818,61 @@ vbd_status vbd_create_mesh(const vbd_mesh_desc *desc, const vbd_params *params, 
     ctx->pinned.assign(N, 0);
     if (desc->pinned)
         for (int i = 0; i < N; ++i) ctx->pinned[i] = desc->pinned[i] ? 1 : 0;
-    for (size_t k = 0; k < ctx->rest.size(); ++k)
-        if (!std::isfinite(ctx->rest[k])) { delete ctx; return VBD_ERR_BAD_MESH; }
+    // The loops below write disjoint entries and are split over host threads
+    // (OpenMP); their results do not depend on the split.
+    const long long n3 = (long long)ctx->rest.size();
+    int bad = 0;
+#pragma omp parallel for reduction(| : bad)
+    for (long long k = 0; k < n3; ++k)
+        if (!std::isfinite(ctx->rest[k])) bad |= 1;
     // every tet must stay inside its own mesh
-    for (int b = 0; b < ctx->n_meshes; ++b)
-        for (int j = ctx->tet_off[b]; j < ctx->tet_off[b + 1]; ++j)
+    for (int b = 0; b < ctx->n_meshes && !bad; ++b) {
+        const int t0 = ctx->tet_off[b], t1 = ctx->tet_off[b + 1], v0 = ctx->vert_off[b], v1 = ctx->vert_off[b + 1];
+#pragma omp parallel for reduction(| : bad)
+        for (int j = t0; j < t1; ++j)
             for (int a = 0; a < 4; ++a) {
-                const int v = ctx->tets[4 * j + a];
-                if (v < ctx->vert_off[b] || v >= ctx->vert_off[b + 1]) { delete ctx; return VBD_ERR_BAD_MESH; }
+                const int v = ctx->tets[4 * (size_t)j + a];
+                if (v < v0 || v >= v1) bad |= 1;
             }
-    for (int j = 0; j < T; ++j) {
-        const int *t = &ctx->tets[4 * j];
-        if (t[0] == t[1] || t[0] == t[2] || t[0] == t[3] || t[1] == t[2] || t[1] == t[3] || t[2] == t[3]) {
-            delete ctx;
-            return VBD_ERR_BAD_MESH;
+    }
+    if (!bad) {
+#pragma omp parallel for reduction(| : bad)
+        for (int j = 0; j < T; ++j) {
+            const int *t = &ctx->tets[4 * (size_t)j];
+            if (t[0] == t[1] || t[0] == t[2] || t[0] == t[3] || t[1] == t[2] || t[1] == t[3] || t[2] == t[3])
+                bad |= 1;
+            if (!(ctx->young[j] > 0.f) || !(ctx->poisson[j] > -1.f && ctx->poisson[j] < 0.5f) ||
+                !(ctx->density[j] > 0.f) || !std::isfinite(ctx->young[j]) || !std::isfinite(ctx->density[j]))
+                bad |= 1;
         }
-        if (!(ctx->young[j] > 0.f) || !(ctx->poisson[j] > -1.f && ctx->poisson[j] < 0.5f) ||
-            !(ctx->density[j] > 0.f) || !std::isfinite(ctx->young[j]) || !std::isfinite(ctx->density[j])) {
-            delete ctx;
-            return VBD_ERR_BAD_MESH;
-        }
+    }
+    if (bad) {
+        delete ctx;
+        return VBD_ERR_BAD_MESH;
     }
     ctx->B.resize(9 * (size_t)T);
     ctx->V.resize(T);
     ctx->mu.resize(T);
     ctx->lam.resize(T);
-    ctx->mass.assign(N, 0.0);
+    const double *R = ctx->rest.data();
+#pragma omp parallel for reduction(| : bad)
     for (int j = 0; j < T; ++j) {
-        const int *t = &ctx->tets[4 * j];
-        const double *R = ctx->rest.data();
+        const int *t = &ctx->tets[4 * (size_t)j];
         if (!rest_inverse(R + 3 * (size_t)t[0], R + 3 * (size_t)t[1], R + 3 * (size_t)t[2], R + 3 * (size_t)t[3],
-                          &ctx->B[9 * (size_t)j], &ctx->V[j])) {
-            delete ctx;
-            return VBD_ERR_BAD_MESH;
-        }
+                          &ctx->B[9 * (size_t)j], &ctx->V[j]))
+            bad |= 1;
         const double E = ctx->young[j], nu = ctx->poisson[j];
         ctx->mu[j] = E / (2.0 * (1.0 + nu));
         ctx->lam[j] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)) + ctx->mu[j];
+    }
+    if (bad) {
+        delete ctx;
+        return VBD_ERR_BAD_MESH;
+    }
+    // lumped masses, summed in tet order (serial, so every bit is the same)
+    ctx->mass.assign(N, 0.0);
+    for (int j = 0; j < T; ++j) {
+        const int *t = &ctx->tets[4 * (size_t)j];
         for (int a = 0; a < 4; ++a) ctx->mass[t[a]] += ctx->density[j] * ctx->V[j] / 4.0;
     }
     *out = ctx;
@@ -867,14 +892,22 @@ vbd_status vbd_color(vbd_ctx *ctx, const int32_t *colors, int32_t *n_colors_out)
             col[i] = colors[i];
             nc = std::max(nc, col[i] + 1);
         }
+        int first_bad = T;  // lowest offending tet, whatever the thread split
+#pragma omp parallel for reduction(min : first_bad)
         for (int j = 0; j < T; ++j) {
-            const int *t = &ctx->tets[4 * j];
+            const int *t = &ctx->tets[4 * (size_t)j];
             for (int a = 0; a < 4; ++a)
                 for (int b = a + 1; b < 4; ++b)
-                    if (col[t[a]] == col[t[b]])
-                        return fail(ctx, VBD_ERR_BAD_COLORING,
-                                    "tet " + std::to_string(j) + " has two vertices of colour " +
-                                        std::to_string(col[t[a]]));
+                    if (col[t[a]] == col[t[b]] && j < first_bad) first_bad = j;
+        }
+        if (first_bad < T) {
+            const int *t = &ctx->tets[4 * (size_t)first_bad];
+            int cc = col[t[0]];
+            for (int a = 0; a < 4; ++a)
+                for (int b = a + 1; b < 4; ++b)
+                    if (col[t[a]] == col[t[b]]) cc = col[t[a]];
+            return fail(ctx, VBD_ERR_BAD_COLORING,
+                        "tet " + std::to_string(first_bad) + " has two vertices of colour " + std::to_string(cc));
         }
     } else {
         nc = greedy_coloring(N, T, ctx->tets, col);
@@ -979,6 +1012,7 @@ vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *st
     // entries so that host staging stays bounded at any mesh size
     constexpr long long kChunk = 1 << 24;
     std::vector<float> massf(N);
+#pragma omp parallel for
     for (int k = 0; k < N; ++k) massf[k] = (float)ctx->mass[ctx->orig_of_new[k]];
     CU(cudaMemcpyAsync(d.mass, massf.data(), 4 * (size_t)N, cudaMemcpyHostToDevice, s), "upload mass");
     CU(cudaMemcpyAsync(d.slot_off, ctx->slot_off.data(), 4 * ((size_t)ctx->n_free + 1), cudaMemcpyHostToDevice, s),
@@ -1056,6 +1090,7 @@ vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *st
         for (long long j0 = 0; j0 < T; j0 += kChunk) {
             const long long n = std::min<long long>(kChunk, T - j0);
             tv.resize(n); tB.resize(9 * n); tV.resize(n); tnu.resize(n); tmu.resize(n); tlam.resize(n);
+#pragma omp parallel for
             for (long long q = 0; q < n; ++q) {
                 const size_t j = (size_t)(j0 + q);
                 const int *t = &ctx->tets[4 * j];
@@ -1081,6 +1116,7 @@ vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *st
     CU(cudaMemsetAsync(d.counters, 0, 64, s), "clear counters");
     // rest positions (FP32, internal order); state x = rest (u = 0), v = v_prev = 0
     std::vector<float4> restf(N);
+#pragma omp parallel for
     for (int k = 0; k < N; ++k) {
         const double *X = &ctx->rest[3 * (size_t)ctx->orig_of_new[k]];
         restf[k] = make_float4((float)X[0], (float)X[1], (float)X[2], 0.f);
@@ -1462,6 +1498,7 @@ vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, floa
     cudaStream_t s = ctx->stream;
     const int N = ctx->N;
     CU(cudaMemsetAsync(d.gtheta, 0, 4 * (size_t)ctx->T, s), "clear gtheta");
+    CU(cudaMemsetAsync(d.adj_res, 0, 16 * (size_t)ctx->tape_len, s), "clear adjoint residuals");
     vbd::launch_adj_seed(d, dL_dxT, N, s);
     const float h_saved = ctx->h;
     for (int t = ctx->tape_len - 1; t >= 0; --t) {
@@ -1479,11 +1516,57 @@ vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, floa
                 rp.adj_residual = 1;
                 vbd::launch_adj_sweep(d, xs, rp, kAdjLanes, kAdjBlock, s);
             }
+        {  // how far the sweeps left lam from H lam = r: max |r - H lam| and max |r|
+            vbd::SweepParams rp = sweep_params(ctx, -1);
+            rp.vbegin = 0;
+            rp.vend = ctx->n_free;
+            rp.adj_residual = 2;
+            vbd::launch_adj_sweep(d, xs, rp, kAdjLanes, kAdjBlock, s, d.adj_res + 2 * (size_t)t);
+        }
         vbd::launch_adj_post(d, xs, N, ctx->n_free, ctx->T, h, has_sub, s);
     }
     ctx->h = h_saved;
     vbd::launch_adj_out(d, dL_dlogE, dL_dv0, N, ctx->T, s);
     CU(cudaGetLastError(), "backward");
+    ctx->adj_res_len = ctx->tape_len;
+    return VBD_OK;
+}
+
+vbd_status vbd_adjoint_residuals(vbd_ctx *ctx, double *rel_out, int32_t n) {
+    vbd_status st = check_bound(ctx);
+    if (st != VBD_OK) return st;
+    if (!rel_out || n < 0) return fail(ctx, VBD_ERR_INVALID_ARG, "rel_out is NULL or n < 0");
+    if (ctx->adj_res_len < 1) return fail(ctx, VBD_ERR_NO_TAPE, "no vbd_backward has run");
+    if (n < ctx->adj_res_len)
+        return fail(ctx, VBD_ERR_INVALID_ARG, "rel_out holds " + std::to_string(n) + " entries, " +
+                                                  std::to_string(ctx->adj_res_len) + " needed");
+    std::vector<double> r(2 * (size_t)ctx->adj_res_len);
+    CU(cudaMemcpyAsync(r.data(), ctx->d.adj_res, 8 * r.size(), cudaMemcpyDeviceToHost, ctx->stream),
+       "adjoint residuals");
+    CU(cudaStreamSynchronize(ctx->stream), "adjoint residuals");
+    for (int t = 0; t < ctx->adj_res_len; ++t) rel_out[t] = r[2 * t + 1] > 0.0 ? r[2 * t] / r[2 * t + 1] : 0.0;
+    return VBD_OK;
+}
+
+vbd_status vbd_gradient_norm(vbd_ctx *ctx, double *grad_inf_out, double *force_scale_out) {
+    Range range_("vbd_gradient_norm");
+    vbd_status st = check_bound(ctx);
+    if (st != VBD_OK) return st;
+    if (!grad_inf_out) return fail(ctx, VBD_ERR_INVALID_ARG, "grad_inf_out is NULL");
+    if (!(ctx->h > 0.f)) return fail(ctx, VBD_ERR_STATE, "no step has begun (y undefined)");
+    CU(vbd::launch_grad_norm(ctx->d, sweep_params(ctx, -1), ctx->n_free, ctx->d.gnorm, ctx->stream), "gradient norm");
+    double g = 0.0;
+    CU(cudaMemcpyAsync(&g, ctx->d.gnorm, 8, cudaMemcpyDeviceToHost, ctx->stream), "gradient norm");
+    CU(cudaStreamSynchronize(ctx->stream), "gradient norm");
+    *grad_inf_out = g;
+    if (force_scale_out) {
+        const float *a = ctx->params.gravity;
+        const double an = std::sqrt((double)a[0] * a[0] + (double)a[1] * a[1] + (double)a[2] * a[2]);
+        double mmax = 0.0;
+        for (int i = 0; i < ctx->N; ++i)
+            if (!ctx->pinned[i]) mmax = std::max(mmax, ctx->mass[i]);
+        *force_scale_out = mmax * an;
+    }
     return VBD_OK;
 }
 

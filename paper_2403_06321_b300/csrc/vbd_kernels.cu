@@ -931,6 +931,59 @@ __global__ void k_copy_back(Dev d, int vbegin, int vend, int involved_only, int 
     d.u[i] = d.unew[i];
 }
 
+// Convergence report: max over free vertices of |dG/dx_i| (Eq. 2 with the
+// plane penalties of Eq. 12), i.e. of the local force f_i of Eq. 8 at the
+// current x and the current step's y, without moving anything.  Per vertex in
+// FP32 like the sweep, reduced in FP64 by an atomic max on the bits of the
+// non-negative doubles.  All free vertices in one launch (nothing is written
+// but the maximum).
+template <int L>
+__global__ void __launch_bounds__(256) k_grad_norm(Dev d, SweepParams p, int n_free, double *out) {
+    const int lane = threadIdx.x & (L - 1);
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int vi = (int)(gt / L);
+    const bool active = vi < n_free;
+    float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
+    int s0 = 0, s1 = 0;
+    if (active) {
+        xi = d.u[vi];
+        s0 = d.slot_off[vi];
+        s1 = d.slot_off[vi + 1];
+    }
+    const float3 x3 = f3(xi);
+    const float2 vm = (active && !p.per_tet_mat) ? __ldg(d.vmat + vi) : make_float2(0.f, 0.f);
+    Acc acc = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int s = s0 + lane; s < s1; s += L)
+        accumulate_slot(d, p, s, vm, __ldcs(d.s0 + s), __ldcs(d.s1 + s), __ldcs(d.s2 + s), x3, acc);
+    acc.f0 = sub_reduce<L>(acc.f0);
+    acc.f1 = sub_reduce<L>(acc.f1);
+    acc.f2 = sub_reduce<L>(acc.f2);
+    float g = 0.f;
+    if (active && lane == 0) {
+        const float4 yv = d.ym[vi];
+        float f0 = yv.w * (yv.x - xi.x) + acc.f0, f1 = yv.w * (yv.y - xi.y) + acc.f1,
+              f2 = yv.w * (yv.z - xi.z) + acc.f2;
+        if (p.n_planes > 0) {
+            const float4 X = d.rest[vi];
+            const float3 P = make_float3(X.x + xi.x, X.y + xi.y, X.z + xi.z);
+            for (int k = 0; k < p.n_planes; ++k) {
+                const float4 pl = p.planes[k];
+                const float pen = pl.w - (pl.x * P.x + pl.y * P.y + pl.z * P.z);
+                if (pen > 0.f) {
+                    f0 += p.kc * pen * pl.x;
+                    f1 += p.kc * pen * pl.y;
+                    f2 += p.kc * pen * pl.z;
+                }
+            }
+        }
+        g = fmaxf(fabsf(f0), fmaxf(fabsf(f1), fabsf(f2)));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) g = fmaxf(g, __shfl_xor_sync(FULL, g, off));
+    if ((threadIdx.x & 31) == 0 && g > 0.f)
+        atomicMax((unsigned long long *)out, (unsigned long long)__double_as_longlong((double)g));
+}
+
 __global__ void k_restore_x(Dev d, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) d.u[i] = d.ut[i];
@@ -1268,6 +1321,13 @@ void launch_copy_back(const Dev &d, int vbegin, int vend, bool involved_only, bo
     if (vend > vbegin)
         k_copy_back<<<blocks_for(vend - vbegin, 256), 256, 0, s>>>(d, vbegin, vend, involved_only ? 1 : 0,
                                                                    ee_on ? 1 : 0);
+}
+
+cudaError_t launch_grad_norm(const Dev &d, const SweepParams &p, int n_free, double *out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
+    if (e != cudaSuccess || n_free <= 0) return e;
+    k_grad_norm<4><<<blocks_for(4LL * n_free, 256), 256, 0, s>>>(d, p, n_free, out);
+    return cudaGetLastError();
 }
 
 void launch_restore_x(const Dev &d, int n, cudaStream_t s) {

@@ -47,6 +47,8 @@ struct Dev {
                                    // [3] self-collision pairs found, [4] positions beyond the collision grid
     double *partials; // energy partial sums
     double *energy_out;
+    double *gnorm;    // 2: max |dG/dx_i| (bits of a non-negative double, atomic max) and spare
+    double *adj_res;  // 2 per tape step: max |r - H lam| and max |r| after the step's adjoint sweeps
     float4 *tape;     // tape_steps * N displacements
     // adjoint
     float4 *lam, *rhs, *xbar, *vbar;
@@ -99,7 +101,8 @@ struct SweepParams {
     float4 planes[kMaxPlanes];  // xyz unit normal, w offset: the allowed side is x.n >= w
     int n_planes;     // planes in use (ground first when on, then the walls)
     int n_sub;        // subspace-constrained vertices (Sec. 3.4); > 0 reads Dev::sub_id
-    int adj_residual; // adjoint only: store r - (H lam)_i of constrained vertices in Dev::rhs, lam unchanged
+    int adj_residual; // adjoint only: 1 store r - (H lam)_i of constrained vertices in Dev::rhs, 2 max-reduce
+                      // |r - H lam| and |r| over all free vertices; lam unchanged in both
     int ee_on;        // edge-edge pairs exist (CCD on): the sweep reads Dev::ee_off
     int n_edges;      // boundary edges (energy of the edge-edge pairs)
     float kc;         // collision stiffness (Eq. 12)
@@ -167,6 +170,8 @@ void launch_gather(const float4 *src, float *dst, const int *new_of_orig, const 
 void launch_restore_x(const Dev &d, int n, cudaStream_t s);
 void launch_copy_back(const Dev &d, int vbegin, int vend, bool involved_only, bool ee_on, cudaStream_t s);
 // n_surf > 0 adds the self-contact energy of the current pairs
+// max_i |dG/dx_i| over the free vertices into *out (device double), asynchronous
+cudaError_t launch_grad_norm(const Dev &d, const SweepParams &p, int n_free, double *out, cudaStream_t s);
 void launch_energy(const Dev &d, int n_free, int n_tets, int n_surf, double h, const SweepParams &p,
                    cudaStream_t s);
 int energy_partials_needed(int n_free, int n_tets, int n_surf);
@@ -187,7 +192,7 @@ void launch_set_log_young(const Dev &d, const float *log_young, int n_tets, cuda
 // adjoint
 void launch_adj_rhs(const Dev &d, int n, int n_free, float inv_h, cudaStream_t s);
 void launch_adj_sweep(const Dev &d, const float4 *xs, const SweepParams &p, int lanes, int block,
-                      cudaStream_t s);
+                      cudaStream_t s, double *res_out = nullptr);
 void launch_adj_post(const Dev &d, const float4 *xs, int n, int n_free, int n_tets, float h, bool has_sub,
                      cudaStream_t s);
 void launch_adj_seed(const Dev &d, const float *dL_dx, int n, cudaStream_t s);

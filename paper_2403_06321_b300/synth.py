@@ -103,11 +103,14 @@ def kuhn_grid(nx: int, ny: int, nz: int, edge: float,
     del i, j, k
     rest = np.asarray(origin, dtype=np.float64) + edge * ijk.astype(np.float64)
 
-    # id of each cube's (0,0,0) corner, cubes in x-fastest order
-    ck, cj, ci = np.meshgrid(np.arange(nz, dtype=np.int64), np.arange(ny, dtype=np.int64),
-                             np.arange(nx, dtype=np.int64), indexing="ij")
-    base = (ci + nxv * (cj + nyv * ck)).ravel()
-    del ci, cj, ck
+    # id of each cube's (0,0,0) corner, cubes in x-fastest order (vertex ids
+    # fit in int32, so the tables are built in int32 directly)
+    if nxv * nyv * nzv >= 2 ** 31:
+        raise ValueError("grid too large for int32 vertex ids")
+    it = np.int32
+    base = (np.arange(nx, dtype=it)[None, None, :] +
+            it(nxv) * (np.arange(ny, dtype=it)[None, :, None] +
+                       it(nyv) * np.arange(nz, dtype=it)[:, None, None])).ravel()
 
     def off(e):
         return int(e[0] + nxv * (e[1] + nyv * e[2]))
@@ -118,9 +121,9 @@ def kuhn_grid(nx: int, ny: int, nz: int, edge: float,
         e0 = unit[perm[0]]
         e01 = unit[perm[0]] + unit[perm[1]]
         table.append([0, off(e0), off(e01), off((1, 1, 1))])
-    table = np.asarray(table, dtype=np.int64)  # (6, 4)
+    table = np.asarray(table, dtype=it)  # (6, 4)
     # cube-major order: the 6 tets of one cube are adjacent
-    tets = (base[:, None, None] + table[None, :, :]).reshape(-1, 4).astype(np.int32)
+    tets = (base[:, None, None] + table[None, :, :]).reshape(-1, 4)
     return rest, tets, ijk
 
 

@@ -30,7 +30,7 @@ ENTRY_POINTS = [
     "vbd_set_log_young", "vbd_step", "vbd_begin_step", "vbd_iterate", "vbd_sweep_color",
     "vbd_accelerate", "vbd_end_step", "vbd_energy", "vbd_energy_static", "vbd_get_contacts", "vbd_get_edge_pairs",
     "vbd_sync_status",
-    "vbd_backward",
+    "vbd_backward", "vbd_adjoint_residuals", "vbd_gradient_norm",
     "vbd_set_launch", "vbd_debug_stall_pipeline", "vbd_set_graph", "vbd_autotune", "vbd_autotune_ex",
     "vbd_last_error",
     "vbd_destroy",
@@ -112,6 +112,8 @@ def load() -> C.CDLL:
         "vbd_get_contacts": (C.c_int, [P, P]),
         "vbd_sync_status": (C.c_int, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "vbd_backward": (C.c_int, [P, P, P, P, I32]),
+        "vbd_adjoint_residuals": (C.c_int, [P, P, I32]),
+        "vbd_gradient_norm": (C.c_int, [P, C.POINTER(D), C.POINTER(D)]),
         "vbd_set_launch": (C.c_int, [P, I32, I32, I32]),
         "vbd_debug_stall_pipeline": (C.c_int, [P, I32]),
         "vbd_set_graph": (C.c_int, [P, I32]),
@@ -293,6 +295,20 @@ def vbd_sync_status(ctx: int, with_contacts: bool = False):
 
 def vbd_backward(ctx: int, dL_dxT, dL_dlogE, dL_dv0, adj_iters: int) -> None:
     _check("vbd_backward", ctx, load().vbd_backward(ctx, _ptr(dL_dxT), _ptr(dL_dlogE), _ptr(dL_dv0), adj_iters))
+
+
+def vbd_adjoint_residuals(ctx: int, n_steps: int) -> np.ndarray:
+    """max |r - H lam| / max |r| of each recorded step after the last vbd_backward."""
+    out = np.zeros(max(n_steps, 1), np.float64)
+    _check("vbd_adjoint_residuals", ctx, load().vbd_adjoint_residuals(ctx, out.ctypes.data, len(out)))
+    return out[:n_steps]
+
+
+def vbd_gradient_norm(ctx: int):
+    """(max_i |dG/dx_i| at the current iterate, max_i m_i |a_ext|) in newtons."""
+    g, w = C.c_double(), C.c_double()
+    _check("vbd_gradient_norm", ctx, load().vbd_gradient_norm(ctx, C.byref(g), C.byref(w)))
+    return g.value, w.value
 
 
 def vbd_set_launch(ctx: int, lanes_per_vertex: int = 0, block_threads: int = 0, variant: int = -1) -> None:
