@@ -34,9 +34,9 @@ UNIT = "vertex-block updates/s"
 B_INC, B_VTX, B_X = 52, 44, 12
 B_SC = 24  # with self-collision: contact[i] and rev_off[i], rev_off[i+1], in the sweep and the copy-back
 VARIANTS = {0: "plain", 1: "tma_staged", 2: "persistent", 3: "two_phase_scatter", 4: "fused_cluster_loop",
-            5: "compact_rest_slots"}
+            5: "compact_rest_slots", 6: "compact_rest_slots_packed_pairs"}
 KERNELS = {0: "k_sweep", 1: "k_sweep_pipe", 2: "k_sweep_persist", 3: "k_scatter_slots + k_scatter_reduce",
-           4: "k_iterate_fused", 5: "k_sweep_rest"}
+           4: "k_iterate_fused", 5: "k_sweep_rest", 6: "k_sweep_pair"}
 NOMINAL_HBM_GBS = 7700.0  # B300 HBM3e nominal bandwidth, for context beside the measured peak
 DETECT_LAUNCHES = 20   # kernels and memsets of one self-collision detection (three prefix sums)
 CCD_LAUNCHES = 20      # kernels and memsets of one CCD (two prefix sums)
@@ -410,10 +410,28 @@ def run_batched(args) -> dict:
     h, iters = cfg.h, cfg.iters
     for _ in range(2):
         sim.step(h, iters)
-    t_b = _timed(stream, lambda: sim.step(h, iters), steps)
+    t_ms, sweep_ms, _ = timed_steps(sim, h, iters, steps, stream)
+    t_b = t_ms / 1e3
     sim.sync_status()
     v_batched = info.n_free * iters * steps / t_b
     sim.close()
+    # roofline of the colour passes: the survey's byte model per update
+    # (rest data 52 B per incidence, own vertex 44 B, neighbour re-reads
+    # 12 B per colour) and, for the compact-slot kernels, their own (16 B of
+    # ids per incidence, 60 B own vertex and rest position, 24 B per colour)
+    C = info.n_colors
+    inc = 4.0 * cat.n_tets / cat.n_verts
+    avg_launch_s = sweep_ms / 1e3 / (steps * iters * C)
+    peak, peak_kind = measured_peak_hbm()
+    b_model = inc * B_INC + B_VTX + B_X * C
+    roof = {"bound": "hbm", "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+            "alg_bytes_per_update": b_model, "avg_launch_us": avg_launch_s * 1e6,
+            "achieved": info.n_free / C * b_model / avg_launch_s / 1e9}
+    roof["frac"] = roof["achieved"] / peak
+    if info.pipeline in (5, 6):
+        b_own = inc * 16 + 60 + 24 * C
+        roof["own_model_bytes_per_update"] = b_own
+        roof["own_model_frac"] = info.n_free / C * b_own / avg_launch_s / 1e9 / peak
     # per-mesh contexts
     sims = []
     for m in meshes:
@@ -439,7 +457,7 @@ def run_batched(args) -> dict:
                        "block_threads": info.block_threads},
             "value": v_batched, "unit": UNIT, "ms_per_step": t_b * 1e3 / steps,
             "per_mesh_value": v_plain, "per_mesh_ms_per_step": t_p * 1e3 / psteps,
-            "speedup_vs_plain": v_batched / v_plain, "n_free_verts": int(info.n_free)}
+            "speedup_vs_plain": v_batched / v_plain, "n_free_verts": int(info.n_free), "roofline": roof}
 
 
 def run_adjoint(args, reps: int = 5) -> dict:
@@ -684,10 +702,13 @@ def run_paper_scale(args) -> dict:
     import numpy as np
     import torch
     from paper_2403_06321_b300 import synth, vbd
+    host_free = 0
     try:
-        import psutil
-        host_free = psutil.virtual_memory().available
-    except ImportError:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    host_free = int(ln.split()[1]) * 1024
+    except (OSError, ValueError, IndexError):
         host_free = 0
     dev_free, _ = torch.cuda.mem_get_info()
     if host_free < 80e9 or dev_free < 80e9:

@@ -188,7 +188,8 @@ typedef struct {
     int64_t n_slots;         /* (free vertex, incident tet) pairs streamed per iteration */
     int32_t lanes_per_vertex, block_threads;   /* current sweep launch shape */
     int32_t pipeline;        /* sweep variant of vbd_set_launch (0 plain, 1 TMA-staged, 2 persistent,
-                                3 two-phase scatter, 4 fused loop, 5 compact slots) */
+                                3 two-phase scatter, 4 fused loop, 5 compact slots, 6 compact slots
+                                two per lane in packed FP32) */
     int32_t pipe_stage_slots; /* slot capacity of one pipeline stage */
     int32_t pipe_ctas_per_sm; /* resident CTAs per SM of the pipelined sweep */
     int32_t use_graph;       /* vbd_iterate replays a CUDA graph */
@@ -417,12 +418,18 @@ vbd_status vbd_gradient_norm(vbd_ctx *ctx, double *grad_inf_out, double *force_s
  *     and volume from the FP32 rest positions (three more gathered
  *     positions per slot, a third of the streamed bytes; on B300 as fast as
  *     2 on a 1M-vertex cube and 7 % faster on a 33M-vertex one, where it
- *     stays below the power cap that throttles 2).
+ *     stays below the power cap that throttles 2);
+ *  6  compact slots, two per lane: variant 5's data and persistent grid,
+ *     each lane evaluating two of its slots at once in packed FP32
+ *     (sm_100+ pair instructions: half the FP32 instructions, both slots'
+ *     gathers in flight together).
  * All variants give the same positions: 0, 2 and 4 bit for bit with equal
  * lanes, 1 equals 0 with 8 lanes, and 3 agrees to FP32 rounding (each
  * incidence's terms are rounded before they are summed); 5 differs from 0
  * by the rounding of the rest positions to FP32 (about 2e-7 of the
- * bounding-box diagonal after one iteration of a 1M-vertex cube).  Self-collision passes always use the
+ * bounding-box diagonal after one iteration of a 1M-vertex cube), and 6
+ * from 5 by its explicit fused multiply-adds and the order of its sums
+ * (each lane adds its even and odd slots separately).  Self-collision passes always use the
  * plain form with contacts, and block Jacobi the plain form.  0 keeps a
  * shape value, a negative variant keeps the variant.  Must not be called
  * during stream capture. */
@@ -460,7 +467,7 @@ vbd_status vbd_autotune(vbd_ctx *ctx, float h, int32_t iters, float *best_ms_per
 /* vbd_autotune with flags: VBD_TUNE_SAME_ARITHMETIC restricts the search to
  * shapes whose positions equal those of the current shape bit for bit
  * (variants 0, 2 and 4 with the current lane count, and variant 1 when that
- * count is 8; variants 3 and 5 only among their own block sizes), so tuning
+ * count is 8; variants 3, 5 and 6 only among their own block sizes), so tuning
  * cannot change any result.  Other bits: VBD_ERR_INVALID_ARG. */
 #define VBD_TUNE_SAME_ARITHMETIC 1
 vbd_status vbd_autotune_ex(vbd_ctx *ctx, float h, int32_t iters, int32_t flags, float *best_ms_per_iter);

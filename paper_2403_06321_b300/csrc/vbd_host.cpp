@@ -523,6 +523,8 @@ void launch_colour(vbd_ctx *c, int col, cudaStream_t s) {
         vbd::launch_sweep_persist(c->d, p, c->lanes, c->block, s);
     } else if (c->variant == 5) {
         vbd::launch_sweep_rest(c->d, p, c->lanes, c->block, s);
+    } else if (c->variant == 6) {
+        vbd::launch_sweep_pair(c->d, p, c->lanes, c->block, s);
     } else if (c->variant == 3) {
         vbd::launch_sweep_scatter(c->d, p, c->slot_off[p.vbegin], c->slot_off[p.vend], c->lanes, c->block, s);
     } else {
@@ -1572,7 +1574,7 @@ vbd_status vbd_gradient_norm(vbd_ctx *ctx, double *grad_inf_out, double *force_s
 
 vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_threads, int32_t variant) {
     if (!ctx) return VBD_ERR_INVALID_ARG;
-    if (variant > 5) return fail(ctx, VBD_ERR_INVALID_ARG, "sweep variant must be 0..5 (or < 0 to keep it)");
+    if (variant > 6) return fail(ctx, VBD_ERR_INVALID_ARG, "sweep variant must be 0..6 (or < 0 to keep it)");
     const int var = variant < 0 ? ctx->variant : variant;
     const bool pipe = var == 1;
     if (var == 3 && !ctx->params.scatter_sweep)
@@ -1638,6 +1640,7 @@ static int arithmetic_class(int variant, int lanes) {
     if (variant == 1) return 8;
     if (variant == 3) return 100 + lanes;
     if (variant == 5) return 200 + lanes;
+    if (variant == 6) return 300 + lanes;
     return lanes;
 }
 
@@ -1656,7 +1659,7 @@ vbd_status vbd_autotune_ex(vbd_ctx *ctx, float h, int32_t iters, int32_t flags, 
     const Shape shapes[] = {{0, 4, 64}, {0, 4, 128}, {0, 4, 256}, {0, 8, 64}, {0, 8, 128}, {0, 8, 256},
                             {0, 16, 64}, {0, 16, 256}, {1, 8, 128}, {1, 8, 256}, {2, 4, 128}, {2, 4, 256},
                             {2, 8, 256}, {3, 4, 128}, {4, 4, 0}, {4, 8, 0}, {4, 16, 0}, {5, 4, 128},
-                            {5, 4, 256}};
+                            {5, 4, 256}, {6, 4, 128}, {6, 4, 256}, {6, 8, 256}};
     const Shape cur = {ctx->variant, ctx->lanes, ctx->variant == 1 ? ctx->pipe_block : ctx->block};
     const int cls = arithmetic_class(cur.pipe, cur.lanes);
     // what the timing steps overwrite and a later call could still read: the

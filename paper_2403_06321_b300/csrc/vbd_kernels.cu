@@ -163,6 +163,117 @@ __device__ __forceinline__ void accumulate_slot_rest(const Dev &d, const SweepPa
     tet_contrib(da, db, dc, ga, gb, gc, V * vm.x, V * vm.y, acc);
 }
 
+// ---- two slots per lane in packed FP32 (variant 6) -------------------------
+// sm_100+ issues FP32 add, multiply and fused multiply-add on register pairs
+// (one instruction, two IEEE single-precision results, each rounded as the
+// scalar operation would be).  The element arithmetic is the same for every
+// slot, so a lane evaluates two of its slots at once: the x half of each pair
+// belongs to slot s, the y half to slot s + L.  This halves the FP32
+// instructions of the compact-slot pass (about three quarters of its
+// instructions) and keeps the two slots' gathers in flight together.
+__device__ __forceinline__ float2 p2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a b - c
+__device__ __forceinline__ float2 fms2(float2 a, float2 b, float2 c) {
+    return __ffma2_rn(a, b, make_float2(-c.x, -c.y));
+}
+
+struct V2 {
+    float2 x, y, z;
+};
+__device__ __forceinline__ V2 cross2(const V2 &a, const V2 &b) {
+    return {fms2(a.y, b.z, mul2(a.z, b.y)), fms2(a.z, b.x, mul2(a.x, b.z)), fms2(a.x, b.y, mul2(a.y, b.x))};
+}
+__device__ __forceinline__ float2 dot2(const V2 &a, const V2 &b) {
+    return fma2(a.x, b.x, fma2(a.y, b.y, mul2(a.z, b.z)));
+}
+// (positions of slot a) - (a position common to both), per component
+__device__ __forceinline__ V2 diff2(float4 a, float4 b, float3 o) {
+    return {sub2(p2(a.x, b.x), bc2(o.x)), sub2(p2(a.y, b.y), bc2(o.y)), sub2(p2(a.z, b.z), bc2(o.z))};
+}
+
+struct Acc2 {
+    float2 f0, f1, f2, h00, h01, h02, h11, h12, h22;
+};
+
+// tet_contrib for two slots, with sg = g_a + g_b + g_c = -g_i so that no
+// result needs a separate negation:
+//   D = sum_k d_k g_k^T,  J - 1 = tr D + tr cof(D) + det D,
+//   cq = (tr D) sg - D^T sg + cof(D) sg = -(cof(F) g_i - g_i),
+//   cn = sg + cq = -cof(F) g_i,  Dsg = D sg = -D g_i,
+//   f_i += V mu (Dsg - cq) + V lam (J - 1) cn,
+//   H_i += V mu |sg|^2 I + V lam cn cn^T.
+__device__ __forceinline__ void tet_contrib2(const V2 &da, const V2 &db, const V2 &dc, const V2 &ga,
+                                             const V2 &gb, const V2 &gc, float2 Vmu, float2 Vlam, Acc2 &acc) {
+    const V2 sg = {add2(add2(ga.x, gb.x), gc.x), add2(add2(ga.y, gb.y), gc.y), add2(add2(ga.z, gb.z), gc.z)};
+    const V2 D0 = {fma2(da.x, ga.x, fma2(db.x, gb.x, mul2(dc.x, gc.x))),
+                   fma2(da.y, ga.x, fma2(db.y, gb.x, mul2(dc.y, gc.x))),
+                   fma2(da.z, ga.x, fma2(db.z, gb.x, mul2(dc.z, gc.x)))};
+    const V2 D1 = {fma2(da.x, ga.y, fma2(db.x, gb.y, mul2(dc.x, gc.y))),
+                   fma2(da.y, ga.y, fma2(db.y, gb.y, mul2(dc.y, gc.y))),
+                   fma2(da.z, ga.y, fma2(db.z, gb.y, mul2(dc.z, gc.y)))};
+    const V2 D2 = {fma2(da.x, ga.z, fma2(db.x, gb.z, mul2(dc.x, gc.z))),
+                   fma2(da.y, ga.z, fma2(db.y, gb.z, mul2(dc.y, gc.z))),
+                   fma2(da.z, ga.z, fma2(db.z, gb.z, mul2(dc.z, gc.z)))};
+    const float2 tr = add2(add2(D0.x, D1.y), D2.z);
+    const V2 q0 = cross2(D1, D2), q1 = cross2(D2, D0), q2 = cross2(D0, D1);  // columns of cof(D)
+    const float2 jm1 = add2(add2(tr, add2(add2(q0.x, q1.y), q2.z)), dot2(D0, q0));
+    const V2 cq = {fma2(tr, sg.x, fma2(sg.x, q0.x, fma2(sg.y, q1.x, fms2(sg.z, q2.x, dot2(D0, sg))))),
+                   fma2(tr, sg.y, fma2(sg.x, q0.y, fma2(sg.y, q1.y, fms2(sg.z, q2.y, dot2(D1, sg))))),
+                   fma2(tr, sg.z, fma2(sg.x, q0.z, fma2(sg.y, q1.z, fms2(sg.z, q2.z, dot2(D2, sg)))))};
+    const V2 cn = {add2(sg.x, cq.x), add2(sg.y, cq.y), add2(sg.z, cq.z)};
+    const V2 Dsg = {fma2(sg.x, D0.x, fma2(sg.y, D1.x, mul2(sg.z, D2.x))),
+                    fma2(sg.x, D0.y, fma2(sg.y, D1.y, mul2(sg.z, D2.y))),
+                    fma2(sg.x, D0.z, fma2(sg.y, D1.z, mul2(sg.z, D2.z)))};
+    const float2 k = mul2(Vlam, jm1);
+    acc.f0 = fma2(Vmu, sub2(Dsg.x, cq.x), fma2(k, cn.x, acc.f0));
+    acc.f1 = fma2(Vmu, sub2(Dsg.y, cq.y), fma2(k, cn.y, acc.f1));
+    acc.f2 = fma2(Vmu, sub2(Dsg.z, cq.z), fma2(k, cn.z, acc.f2));
+    const float2 dg = mul2(Vmu, dot2(sg, sg));
+    const V2 vc = {mul2(Vlam, cn.x), mul2(Vlam, cn.y), mul2(Vlam, cn.z)};
+    acc.h00 = add2(acc.h00, fma2(vc.x, cn.x, dg));
+    acc.h11 = add2(acc.h11, fma2(vc.y, cn.y, dg));
+    acc.h22 = add2(acc.h22, fma2(vc.z, cn.z, dg));
+    acc.h01 = fma2(vc.x, cn.y, acc.h01);
+    acc.h02 = fma2(vc.x, cn.z, acc.h02);
+    acc.h12 = fma2(vc.y, cn.z, acc.h12);
+}
+
+// Compact slots s (x half) and s + L (y half, or a repeat of s with zero
+// weight when the lane has an odd number of slots): shape gradients and
+// volume from the FP32 rest positions, as in accumulate_slot_rest.
+__device__ __forceinline__ void accumulate_pair_rest(const Dev &d, const SweepParams &p, int sa, int sb, bool hasb,
+                                                     float2 vm, int4 ra, int4 rb, float3 ui, float3 Xi,
+                                                     Acc2 &acc) {
+    const float4 *__restrict__ u = d.u;
+    const float4 *__restrict__ X = d.rest;
+    const float4 ua0 = __ldg(u + ra.x), ua1 = __ldg(u + ra.y), ua2 = __ldg(u + ra.z);
+    const float4 ub0 = __ldg(u + rb.x), ub1 = __ldg(u + rb.y), ub2 = __ldg(u + rb.z);
+    const float4 Xa0 = __ldg(X + ra.x), Xa1 = __ldg(X + ra.y), Xa2 = __ldg(X + ra.z);
+    const float4 Xb0 = __ldg(X + rb.x), Xb1 = __ldg(X + rb.y), Xb2 = __ldg(X + rb.z);
+    float2 mu2 = bc2(vm.x), lam2 = bc2(vm.y);
+    if (p.per_tet_mat) {
+        const int ja = __ldcs(d.slot_tet + sa), jb = hasb ? __ldcs(d.slot_tet + sb) : ja;
+        mu2 = p2(__ldg(d.tet_mu + ja), __ldg(d.tet_mu + jb));
+        lam2 = p2(__ldg(d.tet_lam + ja), __ldg(d.tet_lam + jb));
+    }
+    const V2 da = diff2(ua0, ub0, ui), db = diff2(ua1, ub1, ui), dc = diff2(ua2, ub2, ui);
+    const V2 ea = diff2(Xa0, Xb0, Xi), eb = diff2(Xa1, Xb1, Xi), ec = diff2(Xa2, Xb2, Xi);
+    V2 ga = cross2(eb, ec), gb = cross2(ec, ea), gc = cross2(ea, eb);
+    const float2 det = dot2(ea, ga);
+    const float2 inv = p2(__frcp_rn(det.x), __frcp_rn(det.y));
+    ga = {mul2(ga.x, inv), mul2(ga.y, inv), mul2(ga.z, inv)};
+    gb = {mul2(gb.x, inv), mul2(gb.y, inv), mul2(gb.z, inv)};
+    gc = {mul2(gc.x, inv), mul2(gc.y, inv), mul2(gc.z, inv)};
+    // V = |det| / 6; the repeated slot of an odd count weighs nothing
+    const float2 V = mul2(p2(fabsf(det.x), hasb ? fabsf(det.y) : 0.f), bc2(1.0f / 6.0f));
+    tet_contrib2(da, db, dc, ga, gb, gc, mul2(V, mu2), mul2(V, lam2), acc);
+}
+
 // Edge-edge pair item j = 4 (holding edge) + role (Sec. 3.5): with the
 // contact points x_a = (1 - s) p0 + s p1, x_b = (1 - u) q0 + u q1 and the
 // frozen normal n, d = (x_b - x_a).n = sum_v c_v x_v . n with
@@ -506,6 +617,48 @@ __device__ __forceinline__ void sweep_body(const Dev &d, const SweepParams &p, l
     if (active && lane == 0) solve_and_store<SC, EXT>(d, p, vi, xi, acc, ca, sc);
 }
 
+// Variant 6: the compact-slot pass with two slots per lane in packed FP32
+// (accumulate_pair_rest); the solve is the one of sweep_body.
+template <int L, bool EXT>
+__device__ __forceinline__ void sweep_body_pair(const Dev &d, const SweepParams &p, long long gt, int vbegin,
+                                                int vend) {
+    const int lane = threadIdx.x & (L - 1);
+    const int vi = vbegin + (int)(gt / L);
+    const bool active = vi < vend;
+    float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
+    int s0 = 0, s1 = 0;
+    if (active) {
+        xi = d.u[vi];
+        s0 = d.slot_off[vi];
+        s1 = d.slot_off[vi + 1];
+    }
+    const float3 x3 = f3(xi);
+    const float3 X3 = active ? f3(__ldg(d.rest + vi)) : make_float3(0.f, 0.f, 0.f);
+    const float2 vm = (active && !p.per_tet_mat) ? __ldg(d.vmat + vi) : make_float2(0.f, 0.f);
+    Acc2 a2;
+    a2.f0 = a2.f1 = a2.f2 = a2.h00 = a2.h01 = a2.h02 = a2.h11 = a2.h12 = a2.h22 = make_float2(0.f, 0.f);
+    for (int s = s0 + lane; s < s1; s += 2 * L) {
+        const int sb = s + L;
+        const bool hasb = sb < s1;
+        const int4 ra = __ldcs(d.s0 + s);
+        const int4 rb = hasb ? __ldcs(d.s0 + sb) : ra;
+        accumulate_pair_rest(d, p, s, sb, hasb, vm, ra, rb, x3, X3, a2);
+    }
+    Acc acc = {a2.f0.x + a2.f0.y, a2.f1.x + a2.f1.y, a2.f2.x + a2.f2.y, a2.h00.x + a2.h00.y,
+               a2.h01.x + a2.h01.y, a2.h02.x + a2.h02.y, a2.h11.x + a2.h11.y, a2.h12.x + a2.h12.y,
+               a2.h22.x + a2.h22.y};
+    acc.f0 = sub_reduce<L>(acc.f0);
+    acc.f1 = sub_reduce<L>(acc.f1);
+    acc.f2 = sub_reduce<L>(acc.f2);
+    acc.h00 = sub_reduce<L>(acc.h00);
+    acc.h01 = sub_reduce<L>(acc.h01);
+    acc.h02 = sub_reduce<L>(acc.h02);
+    acc.h11 = sub_reduce<L>(acc.h11);
+    acc.h12 = sub_reduce<L>(acc.h12);
+    acc.h22 = sub_reduce<L>(acc.h22);
+    if (active && lane == 0) solve_and_store<false, EXT>(d, p, vi, xi, acc, acc, 0);
+}
+
 // Both gather kernels are held to 48 registers (5 CTAs of 256 threads per
 // SM, no spills without the line search): 40 resident warps hide the gather
 // latency better than 32 at 56 registers (measured 62.1 vs 64.0 us per
@@ -532,6 +685,17 @@ __global__ void __launch_bounds__(256, 4) k_sweep_rest(Dev d, SweepParams p, lon
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < threads; base += stride)
         sweep_body<L, false, false, EXT, true>(d, p, base + threadIdx.x, p.vbegin, p.vend);
+}
+
+// persistent form of the packed two-slot compact pass (variant 6)
+#ifndef VBD_PAIR_MIN_BLOCKS
+#define VBD_PAIR_MIN_BLOCKS 3
+#endif
+template <int L, bool EXT>
+__global__ void __launch_bounds__(256, VBD_PAIR_MIN_BLOCKS) k_sweep_pair(Dev d, SweepParams p, long long threads) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < threads; base += stride)
+        sweep_body_pair<L, EXT>(d, p, base + threadIdx.x, p.vbegin, p.vend);
 }
 
 // with self-contact forces; capped at 64 registers so that enough warps stay
@@ -1180,6 +1344,35 @@ void launch_sweep_rest(const Dev &d, const SweepParams &p, int lanes, int block,
         launch_rest_ext<true>(d, p, lanes, block, threads, s);
     else
         launch_rest_ext<false>(d, p, lanes, block, threads, s);
+}
+
+template <int L, bool EXT>
+static unsigned pair_grid(int block) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_pair<L, EXT>, block, 0) != cudaSuccess || occ < 1)
+        occ = 1;
+    return (unsigned)(num_sms() * occ);
+}
+
+template <bool EXT>
+static void launch_pair_ext(const Dev &d, const SweepParams &p, int lanes, int block, long long threads,
+                            cudaStream_t s) {
+    const unsigned need = blocks_for(threads, block);
+    switch (lanes) {
+    case 4: k_sweep_pair<4, EXT><<<std::min(need, pair_grid<4, EXT>(block)), block, 0, s>>>(d, p, threads); break;
+    case 8: k_sweep_pair<8, EXT><<<std::min(need, pair_grid<8, EXT>(block)), block, 0, s>>>(d, p, threads); break;
+    case 16: k_sweep_pair<16, EXT><<<std::min(need, pair_grid<16, EXT>(block)), block, 0, s>>>(d, p, threads); break;
+    default: k_sweep_pair<32, EXT><<<std::min(need, pair_grid<32, EXT>(block)), block, 0, s>>>(d, p, threads); break;
+    }
+}
+
+void launch_sweep_pair(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s) {
+    const long long threads = (long long)(p.vend - p.vbegin) * lanes;
+    if (threads <= 0) return;
+    if (needs_ext(p))
+        launch_pair_ext<true>(d, p, lanes, block, threads, s);
+    else
+        launch_pair_ext<false>(d, p, lanes, block, threads, s);
 }
 
 void launch_sweep_scatter(const Dev &d, const SweepParams &p, int sbegin, int send, int lanes, int block,

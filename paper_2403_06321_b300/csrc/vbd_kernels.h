@@ -147,6 +147,8 @@ void launch_sweep(const Dev &d, const SweepParams &p, int lanes, int block, cuda
 void launch_sweep_persist(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s);
 // persistent sweep over compact slots (shape gradients from the rest positions)
 void launch_sweep_rest(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s);
+// variant 6: compact slots, two slots per lane in packed FP32
+void launch_sweep_pair(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s);
 // two-phase tet-scatter-into-slots form; slots [sbegin, send) are the colour's
 void launch_sweep_scatter(const Dev &d, const SweepParams &p, int sbegin, int send, int lanes, int block,
                           cudaStream_t s);

@@ -124,3 +124,31 @@ def test_adjoint_residuals_one_sweep_matches_oracle_and_more_sweeps_converge(orc
     lasts = [rel[k][-1] for k in (1, 4, 16, 64, 256)]
     assert all(b < a for a, b in zip(lasts, lasts[1:]))
     assert max(rel[256]) < 1e-4
+
+
+def test_report_calls_refuse_what_they_cannot_answer():
+    m = synth.beam(3, 2, 2, jitter_frac=0.05, seed=63)
+    sim = vbd.Sim(m, vbd.make_params(tape_steps=2), colors=synth.kuhn_coloring(m.grid_ijk))
+    try:
+        with pytest.raises(vbd.VbdError) as e:
+            vbd.vbd_gradient_norm(sim.ctx)  # no step yet: y is undefined
+        assert e.value.status == "VBD_ERR_STATE"
+        with pytest.raises(vbd.VbdError) as e:
+            vbd.vbd_adjoint_residuals(sim.ctx, 2)  # no vbd_backward yet
+        assert e.value.status == "VBD_ERR_NO_TAPE"
+        sim.set_state(m.rest, np.zeros_like(m.rest))
+        for _ in range(2):
+            sim.step(1 / 60, 5)
+        g, w = vbd.vbd_gradient_norm(sim.ctx)
+        assert np.isfinite(g) and g >= 0.0 and w > 0.0
+        dev = sim.workspace.device
+        gx = torch.ones(3 * m.n_verts, dtype=torch.float32, device=dev)
+        vbd.vbd_backward(sim.ctx, gx, None, None, 3)
+        with pytest.raises(vbd.VbdError) as e:
+            vbd.vbd_adjoint_residuals(sim.ctx, 1)  # two recorded steps need two entries
+        assert e.value.status == "VBD_ERR_INVALID_ARG"
+        r = vbd.vbd_adjoint_residuals(sim.ctx, 2)
+        assert r.shape == (2,) and np.all(np.isfinite(r)) and np.all(r >= 0.0)
+        sim.sync_status()
+    finally:
+        sim.close()

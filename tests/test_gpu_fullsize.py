@@ -87,7 +87,8 @@ def test_sweep_variants_agree_at_full_size(big):
     kernel: the persistent grid equals the plain grid bit for bit at equal
     lanes, the TMA-staged kernel equals the plain 8-lane sweep bit for bit,
     the two-phase scatter agrees to FP32 rounding, the compact slots (shape
-    gradients from the rest positions) to 1e-6 of the bbox, and the fused cluster
+    gradients from the rest positions) to 1e-6 of the bbox, as do the packed
+    two-slot compact pass and the compact pass, and the fused cluster
     loop refuses a mesh this large."""
     m, cfg, x0, v0 = big
     colors = synth.kuhn_coloring(m.grid_ijk)
@@ -97,7 +98,8 @@ def test_sweep_variants_agree_at_full_size(big):
     try:
         for key, (lanes, block, variant) in {"plain4": (4, 256, 0), "persist4": (4, 256, 2),
                                              "plain8": (8, 256, 0), "tma8": (8, 256, 1),
-                                             "scatter4": (4, 256, 3), "rest4": (4, 256, 5)}.items():
+                                             "scatter4": (4, 256, 3), "rest4": (4, 256, 5),
+                                             "pair4": (4, 256, 6)}.items():
             vbd.vbd_set_launch(sim.ctx, lanes, block if variant != 1 else 256, variant)
             sim.set_state(x0, v0)
             vbd.vbd_begin_step(sim.ctx, cfg.h)
@@ -117,5 +119,8 @@ def test_sweep_variants_agree_at_full_size(big):
     assert float(np.abs(out["plain8"] - out["plain4"]).max()) <= 1e-7 * diag
     # gradients from the FP32 rest positions instead of the FP64-derived ones
     rest_err = float(np.abs(out["rest4"] - out["plain4"]).max()) / diag
-    print("compact rest slots vs stored gradients: %.2e of the bbox" % rest_err)
+    pair_err = float(np.abs(out["pair4"] - out["rest4"]).max()) / diag
+    print("compact rest slots vs stored gradients: %.2e of the bbox; packed pairs vs compact: %.2e" % (
+        rest_err, pair_err))
     assert rest_err <= 1e-6
+    assert pair_err <= 1e-6

@@ -53,7 +53,8 @@ def test_one_iteration_from_perturbed_state_ragged(orc):
              [dict(variant=0, lanes=l) for l in (4, 8, 16, 32)] + \
              [dict(variant=2, lanes=4), dict(variant=2, lanes=8, block=256), dict(variant=3, lanes=4),
               dict(variant=3, lanes=8), dict(variant=4, lanes=4), dict(variant=4, lanes=8),
-              dict(variant=5, lanes=4), dict(variant=5, lanes=8, block=128)]
+              dict(variant=5, lanes=4), dict(variant=5, lanes=8, block=128),
+              dict(variant=6, lanes=4), dict(variant=6, lanes=8, block=128), dict(variant=6, lanes=16)]
     results = []
     for sh in shapes:
         xg, vg = gpu_run(m, pd, colors, 1 / 60, 1, 1, x0, v0, **sh)

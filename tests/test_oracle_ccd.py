@@ -267,6 +267,29 @@ def test_edge_edge_impact_closed_form(orc):
     assert orc.ee_impact(x0c, x1c, 0, 1, 2, 3)[0] == -1.0
 
 
+@pytest.mark.parametrize("deg, paired", [(5.0, False), (5.70, False), (5.78, True), (6.5, True), (30.0, True)])
+def test_edge_edge_pairs_skip_edges_within_about_6_degrees_of_parallel(orc, deg, paired):
+    """The crossing point of two nearly parallel segments is ill-conditioned,
+    so edges whose directions make an angle theta with sin(theta) <= 0.1
+    (theta <= 5.74 degrees) are not paired (their end points' vertex-triangle
+    pairs take them).  A unit edge at angle theta to a static edge along x,
+    centred above it, falls through it: above the threshold it is paired at
+    t = 0.5 with the crossing at s = 0.65 on the static edge and at the
+    falling edge's midpoint (u = 0.5); below it, never."""
+    th = np.radians(deg)
+    dv = 0.5 * np.array([np.cos(th), np.sin(th), 0.0])
+    c = np.array([0.3, 0.1, 0.5])
+    x0 = np.array([[-1, 0.1, 0], [1, 0.1, 0], c - dv, c + dv], float)
+    x1 = x0.copy()
+    x1[2:, 2] = -0.5
+    t, s, u = orc.ee_impact(x0, x1, 0, 1, 2, 3)
+    if paired:
+        assert t == pytest.approx(0.5, abs=1e-12)
+        assert s == pytest.approx(0.65, abs=1e-9) and u == pytest.approx(0.5, abs=1e-9)
+    else:
+        assert t == -1.0
+
+
 def test_edge_edge_impact_against_dense_sampling(orc):
     """Random rotating, translating, stretching edge pairs: the first time
     the four points become coplanar with the segments crossing, from a

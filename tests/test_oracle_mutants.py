@@ -89,6 +89,8 @@ MUTANTS = [
      "test_oracle_ccd.py"),
     ("ee_crossing_test_one_segment", "if (s >= 0.0 && s <= 1.0 && u >= 0.0 && u <= 1.0) {",
      "if (s >= 0.0 && s <= 1.0) {", "test_oracle_ccd.py"),
+    ("ee_parallel_threshold_loosened", "if (nn > 0.01 * dot3(e, e) * dot3(g, g)) {",
+     "if (nn > 0.0001 * dot3(e, e) * dot3(g, g)) {", "test_oracle_ccd.py"),
 ]
 
 
