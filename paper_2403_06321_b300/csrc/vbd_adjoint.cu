@@ -214,8 +214,11 @@ __global__ void __launch_bounds__(128, VBD_ADJ_MIN_BLOCKS) k_adj_sweep(Dev d, co
                     e1 = qa.y * z0 + qb.y * z1;
                     e2 = qa.z * z0 + qb.z * z1;
                 }
-                res_max = fmaxf(fabsf(e0), fmaxf(fabsf(e1), fabsf(e2)));
-                r_max = fmaxf(fabsf(r.x), fmaxf(fabsf(r.y), fabsf(r.z)));
+                // a non-finite component reports as +inf (fmaxf alone would drop a NaN)
+                res_max = (isfinite(e0) && isfinite(e1) && isfinite(e2))
+                              ? fmaxf(fabsf(e0), fmaxf(fabsf(e1), fabsf(e2))) : INFINITY;
+                r_max = (isfinite(r.x) && isfinite(r.y) && isfinite(r.z))
+                            ? fmaxf(fabsf(r.x), fmaxf(fabsf(r.y), fabsf(r.z))) : INFINITY;
             }
         } else {
             float l0, l1, l2;

@@ -102,6 +102,7 @@ struct vbd_ctx {
     int iter_in_step = 0;
     int tape_len = 0;
     int adj_res_len = 0;        // steps with adjoint residuals from the last vbd_backward
+    double max_free_mass = 0.0; // largest lumped mass of a free vertex (scale of vbd_gradient_norm)
     std::vector<float> tape_h;
     // launch shape / graphs
     int lanes = 4, block = 256;
@@ -877,6 +878,8 @@ vbd_status vbd_create_mesh(const vbd_mesh_desc *desc, const vbd_params *params, 
         const int *t = &ctx->tets[4 * (size_t)j];
         for (int a = 0; a < 4; ++a) ctx->mass[t[a]] += ctx->density[j] * ctx->V[j] / 4.0;
     }
+    for (int i = 0; i < N; ++i)
+        if (!ctx->pinned[i]) ctx->max_free_mass = std::max(ctx->max_free_mass, ctx->mass[i]);
     *out = ctx;
     return VBD_OK;
 }
@@ -1564,10 +1567,7 @@ vbd_status vbd_gradient_norm(vbd_ctx *ctx, double *grad_inf_out, double *force_s
     if (force_scale_out) {
         const float *a = ctx->params.gravity;
         const double an = std::sqrt((double)a[0] * a[0] + (double)a[1] * a[1] + (double)a[2] * a[2]);
-        double mmax = 0.0;
-        for (int i = 0; i < ctx->N; ++i)
-            if (!ctx->pinned[i]) mmax = std::max(mmax, ctx->mass[i]);
-        *force_scale_out = mmax * an;
+        *force_scale_out = ctx->max_free_mass * an;
     }
     return VBD_OK;
 }

@@ -1140,7 +1140,9 @@ __global__ void __launch_bounds__(256) k_grad_norm(Dev d, SweepParams p, int n_f
                 }
             }
         }
-        g = fmaxf(fabsf(f0), fmaxf(fabsf(f1), fabsf(f2)));
+        // a non-finite component reports as +inf (fmaxf alone would drop a NaN)
+        g = (isfinite(f0) && isfinite(f1) && isfinite(f2)) ? fmaxf(fabsf(f0), fmaxf(fabsf(f1), fabsf(f2)))
+                                                             : INFINITY;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) g = fmaxf(g, __shfl_xor_sync(FULL, g, off));
