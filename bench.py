@@ -742,6 +742,12 @@ def run_paper_scale(args) -> dict:
     avg_launch_s = sweep_ms / 1e3 / launches
     achieved = info.n_free / C * b_upd / avg_launch_s / 1e9
     peak, peak_kind = measured_peak_hbm()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": peak_kind, "alg_bytes_per_update": b_upd, "avg_launch_us": avg_launch_s * 1e6}
+    if info.pipeline in (5, 6):  # the compact-slot kernels' own byte model
+        b_own = 4.0 * m.n_tets / m.n_verts * 16 + 60 + 24 * C
+        roof["own_model_bytes_per_update"] = b_own
+        roof["own_model_frac"] = info.n_free / C * b_own / avg_launch_s / 1e9 / peak
     return {"workload": "paper_scale: 320^3 cubes x 6 tets (%d verts, %d tets), N(0, 0.5 m/s) velocities, ground "
                         "k_c=1e7, h=1/60, %d iterations/step, %d steps" % (m.n_verts, m.n_tets, cfg.iters,
                                                                          cfg.steps),
@@ -749,10 +755,7 @@ def run_paper_scale(args) -> dict:
             "ms_per_step_each": per, "setup_s": setup_s,
             "launch": {"sweep_variant": VARIANTS[info.pipeline], "lanes_per_vertex": info.lanes_per_vertex,
                        "block_threads": info.block_threads},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_source": peak_kind, "alg_bytes_per_update": b_upd,
-                         "avg_launch_us": avg_launch_s * 1e6},
-            "clocks": clk}
+            "roofline": roof, "clocks": clk}
 
 
 def run_chebyshev(args) -> dict:
@@ -896,14 +899,28 @@ def run_small_configs(args) -> dict:
     fwd()
     vbd.vbd_backward(sim.ctx, gx, gE, gv, cfg.iters)
     t_f = _timed(stream, fwd, 1)
+    gx.copy_(torch.tensor(np.random.default_rng(3).normal(0.0, 1.0, 3 * m.n_verts), dtype=torch.float32,
+                          device=dev))
     t_b = _timed(stream, lambda: vbd.vbd_backward(sim.ctx, gx, gE, gv, cfg.iters), 1)
+    adj_res = vbd.vbd_adjoint_residuals(sim.ctx, cfg.steps)
+    sim.set_state(m.rest, zeros)
+    fwd_res = []
+    for _ in range(cfg.steps):
+        sim.step(cfg.h, cfg.iters)
+        fwd_res.append(vbd.vbd_gradient_norm(sim.ctx))
     sim.sync_status()
     sim.close()
     out["differentiable_beam"] = {"workload": "40x8x8 cubes (3,321 verts, 15,360 tets), %d steps x %d iterations, "
                                               "adjoint %d block-GS iterations per step" % (
                                                   cfg.steps, cfg.iters, cfg.iters),
                                   "ms_per_step": t_f * 1e3 / cfg.steps, "ms_backward_per_step": t_b * 1e3 / cfg.steps,
-                                  "sweep_variant": chosen}
+                                  "sweep_variant": chosen,
+                                  "convergence": {
+                                      "adjoint_rel_residual_max": float(max(adj_res)),
+                                      "adjoint_rel_residual_last_step": float(adj_res[-1]),
+                                      "forward_grad_inf_max_N": max(g for g, _ in fwd_res),
+                                      "forward_weight_scale_N": fwd_res[0][1],
+                                      "note": "adjoint for a seeded N(0, 1) dL/dx_T; max over the 30 steps"}}
     return out
 
 
