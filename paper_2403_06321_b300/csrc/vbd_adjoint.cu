@@ -47,7 +47,6 @@ __device__ __forceinline__ float sub_reduce(float v) {
 
 struct AdjAcc {
     float q0, q1, q2;                      // sum_k H_ik lam_k (off-diagonal part)
-    float h00, h01, h02, h11, h12, h22;    // elastic diagonal block
 };
 
 // F = I + D restricted to what the adjoint needs: D from the displacements
@@ -83,6 +82,84 @@ __device__ __forceinline__ DForm make_dform(const float3 d[3], const float3 g[3]
     f.q2 = cross(f.D0, f.D1);
     f.jm1 = f.tr + m2 + dot(f.D0, f.q0);
     return f;
+}
+
+// H_ii of every free vertex at the step's recorded positions, once per step:
+// sum over its tets of V (mu |g_i|^2 I + lam c_i c_i^T) with c_i = cof(F) g_i
+// in the edge form of k_adj_sweep (below), plus m_i/h^2 I and the ground and
+// wall penalty Hessians (Eq. 12, Sec. 3.4).  It does not change while the
+// sweeps solve for lam, so they read it from Dev::hdiag (h00 h01 h02 h11 |
+// h12 h22) instead of rebuilding it from every slot at every sweep.
+template <int L>
+__global__ void __launch_bounds__(128, 8) k_adj_diag(Dev d, const float4 *__restrict__ xs, SweepParams p) {
+    const int lane = threadIdx.x & (L - 1);
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int vi = p.vbegin + (int)(gt / L);
+    const bool active = vi < p.vend;
+    float3 ui = make_float3(0.f, 0.f, 0.f);
+    int s0 = 0, s1 = 0;
+    if (active) {
+        ui = f3(xs[vi]);
+        s0 = d.slot_off[vi];
+        s1 = d.slot_off[vi + 1];
+    }
+    const float2 vm = (active && !p.per_tet_mat) ? __ldg(d.vmat + vi) : make_float2(0.f, 0.f);
+    float h00 = 0.f, h01 = 0.f, h02 = 0.f, h11 = 0.f, h12 = 0.f, h22 = 0.f;
+    for (int s = s0 + lane; s < s1; s += L) {
+        const int4 r0 = __ldcs(d.s0 + s);
+        const float4 r1 = __ldcs(d.s1 + s);
+        const float4 r2 = __ldcs(d.s2 + s);
+        const float3 ga = make_float3(__int_as_float(r0.w), r1.x, r1.y);
+        const float3 gb = make_float3(r1.z, r1.w, r2.x);
+        const float3 gc = make_float3(r2.y, r2.z, r2.w);
+        const float3 da = sub(f3(__ldg(xs + r0.x)), ui), db = sub(f3(__ldg(xs + r0.y)), ui),
+                     dc = sub(f3(__ldg(xs + r0.z)), ui);
+        const float3 gbc = cross(gb, gc);
+        const float detg = dot(ga, gbc);
+        const float inv = __frcp_rn(detg);
+        const float3 ea = gbc, eb = cross(gc, ga), ec = cross(ga, gb);
+        const float3 ya = make_float3(fmaf(ea.x, inv, da.x), fmaf(ea.y, inv, da.y), fmaf(ea.z, inv, da.z));
+        const float3 yb = make_float3(fmaf(eb.x, inv, db.x), fmaf(eb.y, inv, db.y), fmaf(eb.z, inv, db.z));
+        const float3 yc = make_float3(fmaf(ec.x, inv, dc.x), fmaf(ec.y, inv, dc.y), fmaf(ec.z, inv, dc.z));
+        const float3 Xa = cross(yb, yc), Xb = cross(yc, ya), Xc = cross(ya, yb);
+        const float V = __frcp_rn(6.0f * fabsf(detg));
+        float2 mat = vm;
+        if (p.per_tet_mat) {
+            const int j = __ldcs(d.slot_tet + s);
+            mat = make_float2(__ldg(d.tet_mu + j), __ldg(d.tet_lam + j));
+        }
+        const float Vmu = V * mat.x, Vlam = V * mat.y;
+        const float3 ci = make_float3(-detg * (Xa.x + Xb.x + Xc.x), -detg * (Xa.y + Xb.y + Xc.y),
+                                      -detg * (Xa.z + Xb.z + Xc.z));
+        const float3 gi = make_float3(-(ga.x + gb.x + gc.x), -(ga.y + gb.y + gc.y), -(ga.z + gb.z + gc.z));
+        const float dd = Vmu * dot(gi, gi);
+        h00 += dd + Vlam * ci.x * ci.x;
+        h11 += dd + Vlam * ci.y * ci.y;
+        h22 += dd + Vlam * ci.z * ci.z;
+        h01 += Vlam * ci.x * ci.y;
+        h02 += Vlam * ci.x * ci.z;
+        h12 += Vlam * ci.y * ci.z;
+    }
+    h00 = sub_reduce<L>(h00); h01 = sub_reduce<L>(h01); h02 = sub_reduce<L>(h02);
+    h11 = sub_reduce<L>(h11); h12 = sub_reduce<L>(h12); h22 = sub_reduce<L>(h22);
+    if (!(active && lane == 0)) return;
+    const float mh2 = d.mass[vi] * p.inv_h2;
+    h00 += mh2;
+    h11 += mh2;
+    h22 += mh2;
+    if (p.n_planes > 0) {  // ground and wall penalty Hessians (Eq. 12, Sec. 3.4)
+        const float4 X = d.rest[vi];
+        for (int k = 0; k < p.n_planes; ++k) {
+            const float4 pl = p.planes[k];
+            const float pen = pl.w - (pl.x * (X.x + ui.x) + pl.y * (X.y + ui.y) + pl.z * (X.z + ui.z));
+            if (pen > 0.f) {
+                h00 += p.kc * pl.x * pl.x; h11 += p.kc * pl.y * pl.y; h22 += p.kc * pl.z * pl.z;
+                h01 += p.kc * pl.x * pl.y; h02 += p.kc * pl.x * pl.z; h12 += p.kc * pl.y * pl.z;
+            }
+        }
+    }
+    d.hdiag[2 * vi] = make_float4(h00, h01, h02, h11);
+    d.hdiag[2 * vi + 1] = make_float4(h12, h22, 0.f, 0.f);
 }
 
 // Per slot the sweep needs only products of H with lam, never P(F) itself, so
@@ -125,7 +202,7 @@ __global__ void __launch_bounds__(128, VBD_ADJ_MIN_BLOCKS) k_adj_sweep(Dev d, co
         s1 = d.slot_off[vi + 1];
     }
     const float2 vm = (active && !p.per_tet_mat) ? __ldg(d.vmat + vi) : make_float2(0.f, 0.f);
-    AdjAcc a = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    AdjAcc a = {0.f, 0.f, 0.f};
     for (int s = s0 + lane; s < s1; s += L) {
         const int4 r0 = __ldcs(d.s0 + s);
         const float4 r1 = __ldcs(d.s1 + s);
@@ -167,35 +244,15 @@ __global__ void __launch_bounds__(128, VBD_ADJ_MIN_BLOCKS) k_adj_sweep(Dev d, co
         a.q0 += Vmu * dFg.x + ks * ci.x + kJ * (w1.x + w2.x);
         a.q1 += Vmu * dFg.y + ks * ci.y + kJ * (w1.y + w2.y);
         a.q2 += Vmu * dFg.z + ks * ci.z + kJ * (w1.z + w2.z);
-        const float dd = Vmu * dot(gi, gi);
-        a.h00 += dd + Vlam * ci.x * ci.x;
-        a.h11 += dd + Vlam * ci.y * ci.y;
-        a.h22 += dd + Vlam * ci.z * ci.z;
-        a.h01 += Vlam * ci.x * ci.y;
-        a.h02 += Vlam * ci.x * ci.z;
-        a.h12 += Vlam * ci.y * ci.z;
     }
     a.q0 = sub_reduce<L>(a.q0); a.q1 = sub_reduce<L>(a.q1); a.q2 = sub_reduce<L>(a.q2);
-    a.h00 = sub_reduce<L>(a.h00); a.h01 = sub_reduce<L>(a.h01); a.h02 = sub_reduce<L>(a.h02);
-    a.h11 = sub_reduce<L>(a.h11); a.h12 = sub_reduce<L>(a.h12); a.h22 = sub_reduce<L>(a.h22);
     const bool owner = active && lane == 0;
     float res_max = 0.f, r_max = 0.f;
     if (owner) {
-        const float mh2 = d.mass[vi] * p.inv_h2;
         const float4 r = d.rhs[vi];
         const float b0 = r.x - a.q0, b1 = r.y - a.q1, b2 = r.z - a.q2;
-        float h00 = a.h00 + mh2, h11 = a.h11 + mh2, h22 = a.h22 + mh2, h01 = a.h01, h02 = a.h02, h12 = a.h12;
-        if (p.n_planes > 0) {  // ground and wall penalty Hessians (Eq. 12, Sec. 3.4)
-            const float4 X = d.rest[vi];
-            for (int k = 0; k < p.n_planes; ++k) {
-                const float4 pl = p.planes[k];
-                const float pen = pl.w - (pl.x * (X.x + ui.x) + pl.y * (X.y + ui.y) + pl.z * (X.z + ui.z));
-                if (pen > 0.f) {
-                    h00 += p.kc * pl.x * pl.x; h11 += p.kc * pl.y * pl.y; h22 += p.kc * pl.z * pl.z;
-                    h01 += p.kc * pl.x * pl.y; h02 += p.kc * pl.x * pl.z; h12 += p.kc * pl.y * pl.z;
-                }
-            }
-        }
+        const float4 hA = d.hdiag[2 * vi], hB = d.hdiag[2 * vi + 1];  // H_ii of k_adj_diag
+        const float h00 = hA.x, h01 = hA.y, h02 = hA.z, h11 = hA.w, h12 = hB.x, h22 = hB.y;
         const int sub = p.n_sub > 0 ? d.sub_id[vi] : -1;
         if (p.adj_residual != 0) {
             // r - (H lam)_i = b - H_ii lam_i
@@ -378,6 +435,18 @@ void launch_adj_sweep(const Dev &d, const float4 *xs, const SweepParams &p, int 
     case 8: k_adj_sweep<8><<<grid, block, 0, s>>>(d, xs, p, res_out); break;
     case 16: k_adj_sweep<16><<<grid, block, 0, s>>>(d, xs, p, res_out); break;
     default: k_adj_sweep<32><<<grid, block, 0, s>>>(d, xs, p, res_out); break;
+    }
+}
+
+void launch_adj_diag(const Dev &d, const float4 *xs, const SweepParams &p, int lanes, int block, cudaStream_t s) {
+    const long long threads = (long long)(p.vend - p.vbegin) * lanes;
+    if (threads <= 0) return;
+    const unsigned grid = blocks_for(threads, block);
+    switch (lanes) {
+    case 4: k_adj_diag<4><<<grid, block, 0, s>>>(d, xs, p); break;
+    case 8: k_adj_diag<8><<<grid, block, 0, s>>>(d, xs, p); break;
+    case 16: k_adj_diag<16><<<grid, block, 0, s>>>(d, xs, p); break;
+    default: k_adj_diag<32><<<grid, block, 0, s>>>(d, xs, p); break;
     }
 }
 

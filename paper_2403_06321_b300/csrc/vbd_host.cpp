@@ -346,6 +346,7 @@ size_t carve(const vbd_ctx *c, char *base, Dev *d) {
     t.adj_res = (double *)take(16 * (size_t)std::max(c->params.tape_steps, 1));
     t.tape = (float4 *)take(16 * N * (size_t)std::max(c->params.tape_steps, 0));
     t.lam = (float4 *)take(16 * N);
+    if (c->params.tape_steps > 0) t.hdiag = (float4 *)take(32 * N);
     t.rhs = (float4 *)take(16 * N);
     t.xbar = (float4 *)take(16 * N);
     t.vbar = (float4 *)take(16 * N);
@@ -1511,6 +1512,12 @@ vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, floa
         ctx->h = h;
         const float4 *xs = d.tape + (size_t)t * N;
         vbd::launch_adj_rhs(d, N, ctx->n_free, 1.f / h, s);
+        {  // the diagonal blocks do not change during this step's sweeps
+            vbd::SweepParams dp = sweep_params(ctx, -1);
+            dp.vbegin = 0;
+            dp.vend = ctx->n_free;
+            vbd::launch_adj_diag(d, xs, dp, kAdjLanes, kAdjBlock, s);
+        }
         for (int it = 0; it < adj_iters; ++it)
             for (int col = 0; col < ctx->n_colors; ++col)
                 vbd::launch_adj_sweep(d, xs, sweep_params(ctx, col), kAdjLanes, kAdjBlock, s);

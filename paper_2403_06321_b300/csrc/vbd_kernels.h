@@ -52,6 +52,8 @@ struct Dev {
     float4 *tape;     // tape_steps * N displacements
     // adjoint
     float4 *lam, *rhs, *xbar, *vbar;
+    float4 *hdiag;    // 2N: each free vertex's diagonal block H_ii of the current adjoint step
+                      // (h00 h01 h02 h11 | h12 h22 . .); carved with a tape
     float *gtheta;    // T
     // self-collision (vertex-triangle pairs, Sec. 3.5); carved only when enabled
     int4 *tri;        // boundary triangles: internal vertex ids, outward at rest (.w unused)
@@ -193,6 +195,8 @@ void launch_set_log_young(const Dev &d, const float *log_young, int n_tets, cuda
 
 // adjoint
 void launch_adj_rhs(const Dev &d, int n, int n_free, float inv_h, cudaStream_t s);
+// H_ii of the free vertices [p.vbegin, p.vend) at the recorded positions xs, into Dev::hdiag
+void launch_adj_diag(const Dev &d, const float4 *xs, const SweepParams &p, int lanes, int block, cudaStream_t s);
 void launch_adj_sweep(const Dev &d, const float4 *xs, const SweepParams &p, int lanes, int block,
                       cudaStream_t s, double *res_out = nullptr);
 void launch_adj_post(const Dev &d, const float4 *xs, int n, int n_free, int n_tets, float h, bool has_sub,
