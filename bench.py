@@ -34,9 +34,9 @@ UNIT = "vertex-block updates/s"
 B_INC, B_VTX, B_X = 52, 44, 12
 B_SC = 24  # with self-collision: contact[i] and rev_off[i], rev_off[i+1], in the sweep and the copy-back
 VARIANTS = {0: "plain", 1: "tma_staged", 2: "persistent", 3: "two_phase_scatter", 4: "fused_cluster_loop",
-            5: "compact_rest_slots", 6: "compact_rest_slots_packed_pairs"}
+            5: "compact_rest_slots", 6: "compact_rest_slots_packed_pairs", 7: "warp_rows_tma_ring"}
 KERNELS = {0: "k_sweep", 1: "k_sweep_pipe", 2: "k_sweep_persist", 3: "k_scatter_slots + k_scatter_reduce",
-           4: "k_iterate_fused", 5: "k_sweep_rest", 6: "k_sweep_pair"}
+           4: "k_iterate_fused", 5: "k_sweep_rest", 6: "k_sweep_pair", 7: "k_sweep_rows"}
 NOMINAL_HBM_GBS = 7700.0  # B300 HBM3e nominal bandwidth, for context beside the measured peak
 DETECT_LAUNCHES = 20   # kernels and memsets of one self-collision detection (three prefix sums)
 CCD_LAUNCHES = 20      # kernels and memsets of one CCD (two prefix sums)
@@ -61,7 +61,8 @@ def parse_args(argv=None):
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--variant", type=int, default=-1,
                     help="sweep kernel: 0 plain, 1 TMA-staged, 2 persistent, 3 two-phase scatter, "
-                         "4 fused loop (small meshes); -1 autotune")
+                         "4 fused loop (small meshes), 5 compact slots, 6 compact slots in packed pairs, "
+                         "7 warp rows; -1 autotune")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shape")
     ap.add_argument("--mu-c", type=float, default=0.0, help="ground friction coefficient (Eqs. 13-16)")
@@ -951,7 +952,7 @@ def run_ours(args):
                              init_mode=cfg.init_mode, det_eps=cfg.det_eps, mu_c=args.mu_c,
                              line_search=args.line_search, jacobi=args.jacobi,
                              self_collision=cfg.self_collision, dcd_radius=cfg.dcd_radius,
-                             scatter_sweep=args.variant == 3,
+                             scatter_sweep=args.variant == 3, warp_rows=args.variant == 7,
                              ccd_interval=args.ccd_interval if args.scene == "slabs" else 0,
                              ccd_edges=bool(args.ccd_edges) and args.scene == "slabs")
     stream = torch.cuda.Stream()

@@ -107,6 +107,9 @@ typedef struct {
     int32_t ccd_edges;       /* 1: that CCD also pairs crossing boundary edges (Sec. 3.5, where
                                 both kinds are used); a separate switch so that the vertex-
                                 triangle CCD can run alone */
+    int32_t warp_rows;       /* 1: carve and fill the warp-row copy of the slot records that sweep
+                                variant 7 of vbd_set_launch streams (about the size of the slot
+                                records again); set before vbd_bind */
 } vbd_params;
 
 #define VBD_MAX_WALLS 6
@@ -189,7 +192,7 @@ typedef struct {
     int32_t lanes_per_vertex, block_threads;   /* current sweep launch shape */
     int32_t pipeline;        /* sweep variant of vbd_set_launch (0 plain, 1 TMA-staged, 2 persistent,
                                 3 two-phase scatter, 4 fused loop, 5 compact slots, 6 compact slots
-                                two per lane in packed FP32) */
+                                two per lane in packed FP32, 7 warp rows) */
     int32_t pipe_stage_slots; /* slot capacity of one pipeline stage */
     int32_t pipe_ctas_per_sm; /* resident CTAs per SM of the pipelined sweep */
     int32_t use_graph;       /* vbd_iterate replays a CUDA graph */
@@ -422,9 +425,17 @@ vbd_status vbd_gradient_norm(vbd_ctx *ctx, double *grad_inf_out, double *force_s
  *  6  compact slots, two per lane: variant 5's data and persistent grid,
  *     each lane evaluating two of its slots at once in packed FP32
  *     (sm_100+ pair instructions: half the FP32 instructions, both slots'
- *     gathers in flight together).
+ *     gathers in flight together);
+ *  7  warp rows: variant 2's arithmetic with 4 lanes (lanes_per_vertex and
+ *     block_threads are ignored: 4 and 256) on a persistent grid whose warps
+ *     each stream their next 64 slot records, copied at bind into one
+ *     3,072-byte row per two iterations, into a ring of two shared-memory
+ *     stages by bulk copies (TMA), every wait bounded (VBD_ERR_TIMEOUT as
+ *     for variant 1); needs warp_rows = 1 at bind time, else VBD_ERR_STATE;
+ *     with per-tet materials (vbd_set_log_young, mixed materials) its passes
+ *     run variant 2.  On B300 slower than 2 (the ring's bookkeeping).
  * All variants give the same positions: 0, 2 and 4 bit for bit with equal
- * lanes, 1 equals 0 with 8 lanes, and 3 agrees to FP32 rounding (each
+ * lanes (7 too, with 4), 1 equals 0 with 8 lanes, and 3 agrees to FP32 rounding (each
  * incidence's terms are rounded before they are summed); 5 differs from 0
  * by the rounding of the rest positions to FP32 (about 2e-7 of the
  * bounding-box diagonal after one iteration of a 1M-vertex cube), and 6
@@ -466,8 +477,9 @@ vbd_status vbd_autotune(vbd_ctx *ctx, float h, int32_t iters, float *best_ms_per
 
 /* vbd_autotune with flags: VBD_TUNE_SAME_ARITHMETIC restricts the search to
  * shapes whose positions equal those of the current shape bit for bit
- * (variants 0, 2 and 4 with the current lane count, and variant 1 when that
- * count is 8; variants 3, 5 and 6 only among their own block sizes), so tuning
+ * (variants 0, 2 and 4 with the current lane count, variant 7 when that
+ * count is 4, and variant 1 when it is 8; variants 3, 5 and 6 only among their
+ * own block sizes), so tuning
  * cannot change any result.  Other bits: VBD_ERR_INVALID_ARG. */
 #define VBD_TUNE_SAME_ARITHMETIC 1
 vbd_status vbd_autotune_ex(vbd_ctx *ctx, float h, int32_t iters, int32_t flags, float *best_ms_per_iter);

@@ -75,6 +75,10 @@ struct vbd_ctx {
     long long n_slots = 0;
     bool per_tet_mat = false;        // some vertex's tets differ in material, or log E was set
     std::vector<int> slot_off;       // n_free + 1
+    // warp rows (variant 7): groups of 8 consecutive free vertices of a colour, each spanning
+    // rows_per_group(max over its vertices of ceil(slots / 4)) rows of slot records
+    std::vector<int> group_begin;    // n_colors + 1: groups of each colour
+    std::vector<int> group_row;      // n_groups + 1: first row of each group
     std::vector<int> inc_off, inc_tet, inc_loc;  // vertex -> incident tets (caller ids)
     // boundary surface for self-collision (internal vertex ids), built on demand
     bool surface_built = false;
@@ -107,7 +111,8 @@ struct vbd_ctx {
     // launch shape / graphs
     int lanes = 4, block = 256;
     int variant = 2;            // sweep kernel: 0 plain, 1 TMA-staged, 2 persistent, 3 two-phase scatter,
-                                // 4 fused iteration loop in one cluster, 5 compact slots
+                                // 4 fused iteration loop in one cluster, 5 compact slots, 6 compact slots
+                                // two per lane in packed FP32, 7 warp rows
     int fused_cluster = 0;      // CTAs of that cluster
     bool stall_test = false;    // vbd_debug_stall_pipeline
     int pipe_block = 128;
@@ -318,6 +323,11 @@ size_t carve(const vbd_ctx *c, char *base, Dev *d) {
     t.s1 = (float4 *)take(16 * S);
     t.s2 = (float4 *)take(16 * S);
     t.vmat = (float2 *)take(8 * N);
+    if (c->params.warp_rows && !c->group_row.empty()) {
+        const size_t rows = (size_t)std::max(c->group_row.back(), 1);
+        t.wrow = (float4 *)take(vbd::row_record_bytes() * rows);
+        t.group_row = (int *)take(4 * c->group_row.size());
+    }
     if (c->params.scatter_sweep) {
         const size_t cs = (size_t)std::max(max_colour_slots(c), 1LL);
         t.slot_vtx = (int *)take(4 * S);
@@ -409,6 +419,8 @@ SweepParams sweep_params(const vbd_ctx *c, int color) {
     SweepParams p{};
     p.vbegin = color >= 0 ? c->color_begin[color] : 0;
     p.vend = color >= 0 ? c->color_begin[color + 1] : 0;
+    p.gbegin = color >= 0 && !c->group_begin.empty() ? c->group_begin[color] : 0;
+    p.gend = color >= 0 && !c->group_begin.empty() ? c->group_begin[color + 1] : 0;
     auto add_plane = [&p](const float *n, float offset) {
         const float nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
         p.planes[p.n_planes++] = make_float4(n[0] / nn, n[1] / nn, n[2] / nn, offset);
@@ -527,6 +539,12 @@ void launch_colour(vbd_ctx *c, int col, cudaStream_t s) {
         vbd::launch_sweep_rest(c->d, p, c->lanes, c->block, s);
     } else if (c->variant == 6) {
         vbd::launch_sweep_pair(c->d, p, c->lanes, c->block, s);
+    } else if (c->variant == 7) {
+        // warp rows hold no per-tet material index: per-tet materials run variant 2
+        if (c->d.wrow && !p.per_tet_mat)
+            vbd::launch_sweep_rows(c->d, p, s);
+        else
+            vbd::launch_sweep_persist(c->d, p, 4, 256, s);
     } else if (c->variant == 3) {
         vbd::launch_sweep_scatter(c->d, p, c->slot_off[p.vbegin], c->slot_off[p.vend], c->lanes, c->block, s);
     } else {
@@ -943,6 +961,19 @@ vbd_status vbd_color(vbd_ctx *ctx, const int32_t *colors, int32_t *n_colors_out)
         ctx->slot_off[k + 1] = ctx->slot_off[k] + (ctx->inc_off[i + 1] - ctx->inc_off[i]);
     }
     ctx->n_slots = ctx->slot_off[ctx->n_free];
+    // warp-row groups (variant 7): 8 consecutive free vertices of one colour each
+    ctx->group_begin.assign(nc + 1, 0);
+    ctx->group_row.assign(1, 0);
+    for (int c = 0; c < nc; ++c) {
+        const int vb = ctx->color_begin[c], ve = ctx->color_begin[c + 1];
+        for (int v0 = vb; v0 < ve; v0 += 8) {
+            int K = 0;
+            for (int v = v0; v < std::min(v0 + 8, ve); ++v)
+                K = std::max(K, (ctx->slot_off[v + 1] - ctx->slot_off[v] + 3) / 4);
+            ctx->group_row.push_back(ctx->group_row.back() + vbd::rows_per_group(K));
+        }
+        ctx->group_begin[c + 1] = (int)ctx->group_row.size() - 1;
+    }
     ctx->colored = true;
     ctx->surface_built = false;  // it holds internal ids of the previous order
     if (ctx->params.self_collision) build_surface(ctx);
@@ -969,8 +1000,9 @@ vbd_status vbd_get_info(const vbd_ctx *ctx, vbd_info *out) {
     out->n_free = ctx->colored ? ctx->n_free : 0;
     out->n_colors = ctx->colored ? ctx->n_colors : 0;
     out->n_slots = ctx->colored ? ctx->n_slots : 0;
-    out->lanes_per_vertex = ctx->variant == 1 ? 8 : ctx->lanes;
-    out->block_threads = ctx->variant == 1 ? ctx->pipe_block : (ctx->variant == 4 ? vbd::kFusedThreads : ctx->block);
+    out->lanes_per_vertex = ctx->variant == 1 ? 8 : (ctx->variant == 7 ? 4 : ctx->lanes);
+    out->block_threads = ctx->variant == 1 ? ctx->pipe_block
+                         : (ctx->variant == 4 ? vbd::kFusedThreads : (ctx->variant == 7 ? 256 : ctx->block));
     out->pipeline = ctx->variant;
     out->pipe_stage_slots = ctx->pipe_maxs;
     out->pipe_ctas_per_sm = ctx->pipe_ctas_per_sm;
@@ -1089,6 +1121,15 @@ vbd_status vbd_bind(vbd_ctx *ctx, void *device_workspace, size_t bytes, void *st
             CU(cudaStreamSynchronize(s), "upload slots");  // the staging vectors are reused
             k0 = k1;
         }
+    }
+    if (d.wrow) {  // warp rows of every colour, from the slot records just uploaded
+        CU(cudaMemcpyAsync(d.group_row, ctx->group_row.data(), 4 * ctx->group_row.size(), cudaMemcpyHostToDevice, s),
+           "upload warp-row groups");
+        for (int c = 0; c < ctx->n_colors; ++c)
+            vbd::launch_build_rows(d, ctx->color_begin[c], ctx->color_begin[c + 1], ctx->group_begin[c],
+                                   ctx->group_begin[c + 1], s);
+        CU(cudaGetLastError(), "build warp rows");
+        CU(cudaStreamSynchronize(s), "build warp rows");
     }
     {
         std::vector<int4> tv;
@@ -1581,13 +1622,17 @@ vbd_status vbd_gradient_norm(vbd_ctx *ctx, double *grad_inf_out, double *force_s
 
 vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_threads, int32_t variant) {
     if (!ctx) return VBD_ERR_INVALID_ARG;
-    if (variant > 6) return fail(ctx, VBD_ERR_INVALID_ARG, "sweep variant must be 0..6 (or < 0 to keep it)");
+    if (variant > 7) return fail(ctx, VBD_ERR_INVALID_ARG, "sweep variant must be 0..7 (or < 0 to keep it)");
     const int var = variant < 0 ? ctx->variant : variant;
     const bool pipe = var == 1;
     if (var == 3 && !ctx->params.scatter_sweep)
         return fail(ctx, VBD_ERR_STATE, "the scatter sweep needs scatter_sweep = 1 in the params at bind time");
     if (var == 3 && ctx->bound && !ctx->d.slot_vtx)
         return fail(ctx, VBD_ERR_STATE, "the bound workspace has no scatter buffers: bind again");
+    if (var == 7 && !ctx->params.warp_rows)
+        return fail(ctx, VBD_ERR_STATE, "the warp-row sweep needs warp_rows = 1 in the params at bind time");
+    if (var == 7 && ctx->bound && !ctx->d.wrow)
+        return fail(ctx, VBD_ERR_STATE, "the bound workspace has no warp rows: bind again");
     if (lanes_per_vertex != 0 && lanes_per_vertex != 4 && lanes_per_vertex != 8 && lanes_per_vertex != 16 &&
         lanes_per_vertex != 32)
         return fail(ctx, VBD_ERR_INVALID_ARG, "lanes_per_vertex must be 4, 8, 16 or 32");
@@ -1648,6 +1693,7 @@ static int arithmetic_class(int variant, int lanes) {
     if (variant == 3) return 100 + lanes;
     if (variant == 5) return 200 + lanes;
     if (variant == 6) return 300 + lanes;
+    if (variant == 7) return 4;  // variant 2's arithmetic with 4 lanes
     return lanes;
 }
 
@@ -1666,7 +1712,7 @@ vbd_status vbd_autotune_ex(vbd_ctx *ctx, float h, int32_t iters, int32_t flags, 
     const Shape shapes[] = {{0, 4, 64}, {0, 4, 128}, {0, 4, 256}, {0, 8, 64}, {0, 8, 128}, {0, 8, 256},
                             {0, 16, 64}, {0, 16, 256}, {1, 8, 128}, {1, 8, 256}, {2, 4, 128}, {2, 4, 256},
                             {2, 8, 256}, {3, 4, 128}, {4, 4, 0}, {4, 8, 0}, {4, 16, 0}, {5, 4, 128},
-                            {5, 4, 256}, {6, 4, 128}, {6, 4, 256}, {6, 8, 256}};
+                            {5, 4, 256}, {6, 4, 128}, {6, 4, 256}, {6, 8, 256}, {7, 4, 256}};
     const Shape cur = {ctx->variant, ctx->lanes, ctx->variant == 1 ? ctx->pipe_block : ctx->block};
     const int cls = arithmetic_class(cur.pipe, cur.lanes);
     // what the timing steps overwrite and a later call could still read: the

@@ -942,6 +942,183 @@ __global__ void __launch_bounds__(TT) k_sweep_pipe(Dev d, SweepParams p, int max
     }
 }
 
+// ---- warp rows: per-warp TMA ring over the slot stream (variant 7) ---------
+// With vbd_params.warp_rows the slot records are also laid out in "warp
+// rows" (Dev::wrow, built at bind by k_build_rows): the free vertices of a
+// colour form groups of 8 consecutive vertices, one group per warp-turn; a
+// group needs K = max over its vertices of ceil(slots / 4) iterations of 4
+// lanes, and takes ceil(K / 2) rows.  Row m of a group holds iterations 2m
+// and 2m + 1: entry 32 h + 4 j + l is slot 4 (2m + h) + l of the group's
+// vertex j (the slot that lane l of the vertex's four lanes takes at
+// iteration 2m + h of k_sweep<4>), or padding (id -1).  A row is one
+// 3,072-byte record (the 64 entries' id words, then the two gradient words
+// of each), so one bulk copy moves a warp's next 64 slots into its own
+// shared-memory ring.  Each warp keeps kRowStages rows in flight, issued by
+// its lane 0 as soon as a stage has been read: the slot stream is in flight
+// without holding registers, and the lanes wait only on the L2 gathers of the
+// neighbour positions.  Per lane the slots and the arithmetic are those of
+// k_sweep<4> in the same order, so the positions equal variant 2's with 4
+// lanes bit for bit.  Every wait is bounded as in k_sweep_pipe; on a time-out
+// the warp records it (counters[2]), waits (bounded) for the rows it has
+// issued and leaves.  Each stage barrier expects exactly the bytes copied to it.
+constexpr int kRowStages = 2;
+constexpr int kRowIters = 2;                     // iterations of 4 lanes per row
+constexpr int kRowEntries = 32 * kRowIters;
+constexpr int kRowBytes = 3 * kRowEntries * 16;  // one row: ids, then the gradient words
+constexpr int kRowWarps = 8;                     // 256-thread CTAs
+constexpr size_t kRowSmem = 256 + (size_t)kRowWarps * kRowStages * kRowBytes;
+
+__device__ __forceinline__ void row_issue(const Dev &d, int row, char *stage, unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(kRowBytes)
+                 : "memory");
+    bulk_g2s(stage, d.wrow + (size_t)row * (3 * kRowEntries), (unsigned)kRowBytes, bar);
+}
+
+// one poll of a stage barrier, then the bounded wait only if the row is late
+__device__ __forceinline__ bool row_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return ok ? true : mbar_wait(bar, parity);
+}
+
+#ifndef VBD_ROWS_MIN_BLOCKS
+#define VBD_ROWS_MIN_BLOCKS 4
+#endif
+template <bool EXT>
+__global__ void __launch_bounds__(256, VBD_ROWS_MIN_BLOCKS) k_sweep_rows(Dev d, SweepParams p) {
+    constexpr int L = 4;
+    extern __shared__ __align__(128) char smem[];
+    const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
+    // per warp: kRowStages stage barriers and a spare (time-out test), then its ring
+    unsigned long long *bar = (unsigned long long *)smem + warp * (kRowStages + 1);
+    char *ring = smem + 256 + (size_t)warp * kRowStages * kRowBytes;
+    const int nwarps = gridDim.x * kRowWarps;
+    const int w = blockIdx.x * kRowWarps + warp;
+    const int ng = p.gend - p.gbegin;
+    const int *__restrict__ grow = d.group_row + p.gbegin;
+    if (wl == 0) {
+        for (int st = 0; st <= kRowStages; ++st)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar + st)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    // the issue cursor (lane 0 only): group ig, its row ik of iK, rows issued so far;
+    // groups without rows (vertices in no tet) are stepped over, as the consumer does
+    int ig = w, ik = 0, iK = 0, issued = 0;
+    auto next_group = [&]() {
+        ik = 0;
+        iK = ig < ng ? grow[ig + 1] - grow[ig] : 0;
+        while (ig < ng && iK == 0) {
+            ig += nwarps;
+            iK = ig < ng ? grow[ig + 1] - grow[ig] : 0;
+        }
+    };
+    if (wl == 0) {
+        next_group();
+        for (int st = 0; st < kRowStages && ig < ng; ++st) {
+            row_issue(d, grow[ig] + ik, ring + st * kRowBytes, bar + st);
+            ++issued;
+            if (++ik == iK) {
+                ig += nwarps;
+                next_group();
+            }
+        }
+    }
+    const int lane = wl & (L - 1);
+    int r = 0, st = 0;
+    unsigned phase = 0;
+    for (int g = w; g < ng; g += nwarps) {
+        const int K = grow[g + 1] - grow[g];
+        const int vi = p.vbegin + 8 * g + (wl >> 2);
+        const bool active = vi < p.vend;
+        const float4 xi = active ? d.u[vi] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float3 x3 = f3(xi);
+        const float2 vm = active ? __ldg(d.vmat + vi) : make_float2(0.f, 0.f);
+        Acc acc = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < K; ++k, ++r) {
+            bool ok = row_wait(bar + st, phase);
+            if (ok && r == 0 && p.stall_test) ok = mbar_wait(bar + kRowStages, 0u);  // runs out after ~2 s
+            if (!__all_sync(FULL, ok)) {
+                if (wl == 0) {
+                    atomicAdd(d.counters + 2, 1ull);
+                    for (int q = r; q < issued; ++q)  // rows issued and not yet consumed
+                        mbar_wait(bar + q % kRowStages, (unsigned)((q / kRowStages) & 1));
+                }
+                __syncwarp();
+                return;
+            }
+            const float4 *row = (const float4 *)(ring + st * kRowBytes);
+            float4 e[3 * kRowIters];
+#pragma unroll
+            for (int h = 0; h < kRowIters; ++h)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) e[3 * h + a] = row[a * kRowEntries + 32 * h + wl];
+            // every lane's reads of this stage are ordered before lane 0 refills it
+            __syncwarp();
+            if (wl == 0 && ig < ng) {
+                row_issue(d, grow[ig] + ik, ring + st * kRowBytes, bar + st);
+                ++issued;
+                if (++ik == iK) {
+                    ig += nwarps;
+                    next_group();
+                }
+            }
+            if (++st == kRowStages) {
+                st = 0;
+                phase ^= 1u;
+            }
+#pragma unroll
+            for (int h = 0; h < kRowIters; ++h) {
+                const int4 r0 = make_int4(__float_as_int(e[3 * h].x), __float_as_int(e[3 * h].y),
+                                          __float_as_int(e[3 * h].z), __float_as_int(e[3 * h].w));
+                if (r0.x >= 0) accumulate_slot(d, p, 0, vm, r0, e[3 * h + 1], e[3 * h + 2], x3, acc);
+            }
+        }
+        acc.f0 = sub_reduce<L>(acc.f0);
+        acc.f1 = sub_reduce<L>(acc.f1);
+        acc.f2 = sub_reduce<L>(acc.f2);
+        acc.h00 = sub_reduce<L>(acc.h00);
+        acc.h01 = sub_reduce<L>(acc.h01);
+        acc.h02 = sub_reduce<L>(acc.h02);
+        acc.h11 = sub_reduce<L>(acc.h11);
+        acc.h12 = sub_reduce<L>(acc.h12);
+        acc.h22 = sub_reduce<L>(acc.h22);
+        if (active && lane == 0) solve_and_store<false, EXT>(d, p, vi, xi, acc, acc, 0);
+    }
+}
+
+// Builds the warp rows of one colour from the slot records (one warp per group).
+__global__ void k_build_rows(Dev d, int vbegin, int vend, int gbegin, int gend) {
+    const int wl = threadIdx.x & 31;
+    const int j = wl >> 2, l = wl & 3;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < gend - gbegin; g += nwarps) {
+        const int R0 = d.group_row[gbegin + g], R = d.group_row[gbegin + g + 1] - R0;
+        const int v = vbegin + 8 * (int)g + j;
+        const int s0 = v < vend ? d.slot_off[v] : 0, nv = v < vend ? d.slot_off[v + 1] - s0 : 0;
+        for (int m = 0; m < R; ++m)
+            for (int h = 0; h < kRowIters; ++h) {
+                const int q = 4 * (kRowIters * m + h) + l;
+                float4 *rw = d.wrow + (size_t)(R0 + m) * (3 * kRowEntries) + 32 * h + wl;
+                if (q < nv) {
+                    const int4 a = d.s0[s0 + q];
+                    rw[0] = make_float4(__int_as_float(a.x), __int_as_float(a.y), __int_as_float(a.z),
+                                        __int_as_float(a.w));
+                    rw[kRowEntries] = d.s1[s0 + q];
+                    rw[2 * kRowEntries] = d.s2[s0 + q];
+                } else {
+                    rw[0] = make_float4(__int_as_float(-1), __int_as_float(-1), __int_as_float(-1), 0.f);
+                    rw[kRowEntries] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    rw[2 * kRowEntries] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+    }
+}
+
 // Eq. 3 and Sec. 3.7 options (a)-(d), Eq. 17.  Pinned vertices (ids >= n_free) keep x^t.
 __global__ void k_predict(Dev d, int n, int n_free, float h, float3 g, float gnorm, int mode,
                           int cheby, int has_sub) {
@@ -1375,6 +1552,40 @@ void launch_sweep_pair(const Dev &d, const SweepParams &p, int lanes, int block,
         launch_pair_ext<true>(d, p, lanes, block, threads, s);
     else
         launch_pair_ext<false>(d, p, lanes, block, threads, s);
+}
+
+template <bool EXT>
+static unsigned rows_grid() {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_rows<EXT>, 256, kRowSmem) != cudaSuccess ||
+        occ < 1)
+        occ = 1;
+    return (unsigned)(num_sms() * occ);
+}
+
+void launch_sweep_rows(const Dev &d, const SweepParams &p, cudaStream_t s) {
+    const int ng = p.gend - p.gbegin;
+    if (ng <= 0) return;
+    static bool attr_set = false;  // above the 48 KB default of dynamic shared memory
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_sweep_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowSmem);
+        cudaFuncSetAttribute(k_sweep_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowSmem);
+        attr_set = true;
+    }
+    const unsigned need = (unsigned)((ng + kRowWarps - 1) / kRowWarps);
+    if (needs_ext(p))
+        k_sweep_rows<true><<<std::min(need, rows_grid<true>()), 256, kRowSmem, s>>>(d, p);
+    else
+        k_sweep_rows<false><<<std::min(need, rows_grid<false>()), 256, kRowSmem, s>>>(d, p);
+}
+
+int rows_per_group(int iterations) { return (iterations + kRowIters - 1) / kRowIters; }
+size_t row_record_bytes() { return (size_t)kRowBytes; }
+
+void launch_build_rows(const Dev &d, int vbegin, int vend, int gbegin, int gend, cudaStream_t s) {
+    if (gend > gbegin)
+        k_build_rows<<<std::min<long long>(blocks_for(32LL * (gend - gbegin), 256), 148 * 16), 256, 0, s>>>(
+            d, vbegin, vend, gbegin, gend);
 }
 
 void launch_sweep_scatter(const Dev &d, const SweepParams &p, int sbegin, int send, int lanes, int block,

@@ -32,6 +32,12 @@ struct Dev {
     int *slot_vtx;    // own vertex of each slot (two-phase scatter sweep only)
     float4 *scr0, *scr1;  // scatter sweep scratch per slot of one colour: f0 f1 f2 h00 | h01 h02 h11 h12
     float *scr2;      //                                               h22
+    // warp rows (variant 7, carved with vbd_params.warp_rows): the slot records again, in rows of
+    // 64 entries (two iterations of 32 lanes) per group of 8 consecutive vertices of a colour
+    // (k_sweep_rows), padding id -1; a row is 192 float4: the entries' s0 words (ids as float
+    // bits), then s1, then s2
+    float4 *wrow;
+    int *group_row;   // n_groups + 1: first row of each group (groups of all colours in colour order)
     int *slot_tet;    // caller tet id of each slot
     int *slot_loc;    // local index (0..3) of the slot's own vertex in that tet
     // subspace constraints (Sec. 3.4), when any vertex has one
@@ -100,6 +106,7 @@ constexpr int kMaxPlanes = 7;
 
 struct SweepParams {
     int vbegin, vend;
+    int gbegin, gend; // warp-row groups of the colour (variant 7)
     float4 planes[kMaxPlanes];  // xyz unit normal, w offset: the allowed side is x.n >= w
     int n_planes;     // planes in use (ground first when on, then the walls)
     int n_sub;        // subspace-constrained vertices (Sec. 3.4); > 0 reads Dev::sub_id
@@ -151,6 +158,13 @@ void launch_sweep_persist(const Dev &d, const SweepParams &p, int lanes, int blo
 void launch_sweep_rest(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s);
 // variant 6: compact slots, two slots per lane in packed FP32
 void launch_sweep_pair(const Dev &d, const SweepParams &p, int lanes, int block, cudaStream_t s);
+// variant 7: warp rows streamed by per-warp bulk copies (4 lanes, 256 threads)
+void launch_sweep_rows(const Dev &d, const SweepParams &p, cudaStream_t s);
+// rows of a warp-row group that needs `iterations` iterations of 4 lanes, and the bytes of a row
+int rows_per_group(int iterations);
+size_t row_record_bytes();
+// fills Dev::wrow for the groups [gbegin, gend) of one colour from the slot records
+void launch_build_rows(const Dev &d, int vbegin, int vend, int gbegin, int gend, cudaStream_t s);
 // two-phase tet-scatter-into-slots form; slots [sbegin, send) are the colour's
 void launch_sweep_scatter(const Dev &d, const SweepParams &p, int sbegin, int send, int lanes, int block,
                           cudaStream_t s);

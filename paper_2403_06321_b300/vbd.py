@@ -62,7 +62,7 @@ class vbd_params(C.Structure):
                 ("line_search", C.c_int32), ("jacobi", C.c_int32), ("self_collision", C.c_int32),
                 ("dcd_radius", C.c_float), ("scatter_sweep", C.c_int32), ("xnew_copy_back", C.c_int32),
                 ("n_walls", C.c_int32), ("walls", (C.c_float * 4) * 6), ("ccd_interval", C.c_int32),
-                ("ccd_edges", C.c_int32)]
+                ("ccd_edges", C.c_int32), ("warp_rows", C.c_int32)]
 
 
 class vbd_info(C.Structure):
@@ -313,7 +313,7 @@ def vbd_gradient_norm(ctx: int):
 
 def vbd_set_launch(ctx: int, lanes_per_vertex: int = 0, block_threads: int = 0, variant: int = -1) -> None:
     """variant: 0 plain, 1 TMA-staged, 2 persistent, 3 two-phase scatter, 4 fused loop,
-    5 compact slots (< 0 keeps it)."""
+    5 compact slots, 6 compact slots in packed pairs, 7 warp rows (< 0 keeps it)."""
     _check("vbd_set_launch", ctx, load().vbd_set_launch(ctx, lanes_per_vertex, block_threads, variant))
 
 
@@ -355,7 +355,7 @@ def make_params(gravity=(0.0, 0.0, -9.8), ground_on=False, ground_height=0.0, gr
                 k_c=1e7, cheby_rho=0.0, init_mode=3, det_eps=1e-12, k_d=0.0, tape_steps=0, mu_c=0.0,
                 eps_v=1e-3, line_search=False, jacobi=False, self_collision=False, dcd_radius=0.01,
                 scatter_sweep=False, xnew_copy_back=False, walls=(), ccd_interval=0,
-                ccd_edges=False) -> vbd_params:
+                ccd_edges=False, warp_rows=False) -> vbd_params:
     """vbd_params from keywords (an unknown keyword raises TypeError, so a
     misspelt option cannot silently run the default).  walls: up to 6
     world-box half-spaces (nx, ny, nz, offset), the allowed side being
@@ -381,6 +381,7 @@ def make_params(gravity=(0.0, 0.0, -9.8), ground_on=False, ground_height=0.0, gr
     p.xnew_copy_back = int(bool(xnew_copy_back))
     p.ccd_interval = int(ccd_interval)
     p.ccd_edges = int(bool(ccd_edges))
+    p.warp_rows = int(bool(warp_rows))
     walls = [tuple(float(v) for v in w) for w in walls]
     if len(walls) > 6 or any(len(w) != 4 for w in walls):
         raise ValueError("walls: at most 6 tuples (nx, ny, nz, offset)")

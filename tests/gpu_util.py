@@ -27,6 +27,8 @@ def gpu_run(mesh, pdict: dict, colors, h, iters, steps, x0=None, v0=None, vprev0
     """Returns (x, v) as float64 numpy arrays in caller order."""
     if variant == 3:
         pdict = dict(pdict, scatter_sweep=True)
+    if variant == 7:
+        pdict = dict(pdict, warp_rows=True)
     sim = vbd.Sim(mesh, vbd.make_params(**pdict), colors=colors,
                   vert_offset=vert_offset, tet_offset=tet_offset)
     try:

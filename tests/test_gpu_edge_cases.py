@@ -130,3 +130,29 @@ def test_in_place_writes_equal_xnew_copy_back(orc):
     xb, vb = gpu_run(m, dict(pd, xnew_copy_back=True), colors, H, 10, 10, v0=v0)
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
     assert xa[:, 2].min() < 0.01  # it reached the ground
+
+
+def test_warp_rows_with_per_tet_materials_run_the_persistent_pass():
+    """The warp-row records carry no per-tet material index, so with
+    per-tet materials (here after vbd_set_log_young) variant 7's passes run
+    variant 2 with 4 lanes: the same positions bit for bit, and the same as
+    variant 7 gives once the materials are uniform again."""
+    m = synth.beam(8, 3, 3, edge=0.05, E=2e5, nu=0.4, jitter_frac=0.1, seed=77)
+    colors = synth.kuhn_coloring(m.grid_ijk)
+    rng = np.random.default_rng(78)
+    logE = (np.log(2e5) + rng.uniform(-0.5, 0.5, m.n_tets)).astype(np.float32)
+    out = {}
+    for variant in (2, 7):
+        sim = vbd.Sim(m, vbd.make_params(warp_rows=True), colors=colors)
+        try:
+            vbd.vbd_set_launch(sim.ctx, 4, 256, variant)
+            vbd.vbd_set_log_young(sim.ctx, logE)
+            sim.set_state(m.rest, np.zeros_like(m.rest))
+            for _ in range(4):
+                sim.step(1 / 60, 10)
+            sim.sync_status()
+            out[variant] = sim.get_state()[0].cpu().numpy()
+        finally:
+            sim.close()
+    assert np.array_equal(out[2], out[7])
+    assert np.abs(out[7] - m.rest).max() > 1e-4  # it moved

@@ -84,8 +84,8 @@ def test_energy_never_rises_per_pass(big):
 
 def test_sweep_variants_agree_at_full_size(big):
     """One full iteration (all colours) of the benchmark cube with each sweep
-    kernel: the persistent grid equals the plain grid bit for bit at equal
-    lanes, the TMA-staged kernel equals the plain 8-lane sweep bit for bit,
+    kernel: the persistent grid and the warp-row stream equal the plain grid
+    bit for bit at equal lanes, the TMA-staged kernel equals the plain 8-lane sweep bit for bit,
     the two-phase scatter agrees to FP32 rounding, the compact slots (shape
     gradients from the rest positions) to 1e-6 of the bbox, as do the packed
     two-slot compact pass and the compact pass, and the fused cluster
@@ -94,12 +94,12 @@ def test_sweep_variants_agree_at_full_size(big):
     colors = synth.kuhn_coloring(m.grid_ijk)
     pd = params_of(cfg)
     out = {}
-    sim = vbd.Sim(m, vbd.make_params(scatter_sweep=True, **pd), colors=colors)
+    sim = vbd.Sim(m, vbd.make_params(scatter_sweep=True, warp_rows=True, **pd), colors=colors)
     try:
         for key, (lanes, block, variant) in {"plain4": (4, 256, 0), "persist4": (4, 256, 2),
                                              "plain8": (8, 256, 0), "tma8": (8, 256, 1),
                                              "scatter4": (4, 256, 3), "rest4": (4, 256, 5),
-                                             "pair4": (4, 256, 6)}.items():
+                                             "pair4": (4, 256, 6), "rows4": (4, 256, 7)}.items():
             vbd.vbd_set_launch(sim.ctx, lanes, block if variant != 1 else 256, variant)
             sim.set_state(x0, v0)
             vbd.vbd_begin_step(sim.ctx, cfg.h)
@@ -113,6 +113,7 @@ def test_sweep_variants_agree_at_full_size(big):
     finally:
         sim.close()
     assert np.array_equal(out["persist4"], out["plain4"])
+    assert np.array_equal(out["rows4"], out["plain4"])
     assert np.array_equal(out["tma8"], out["plain8"])
     diag = bbox_diag(m.rest)
     assert float(np.abs(out["scatter4"] - out["plain4"]).max()) <= 1e-7 * diag

@@ -54,7 +54,8 @@ def test_one_iteration_from_perturbed_state_ragged(orc):
              [dict(variant=2, lanes=4), dict(variant=2, lanes=8, block=256), dict(variant=3, lanes=4),
               dict(variant=3, lanes=8), dict(variant=4, lanes=4), dict(variant=4, lanes=8),
               dict(variant=5, lanes=4), dict(variant=5, lanes=8, block=128),
-              dict(variant=6, lanes=4), dict(variant=6, lanes=8, block=128), dict(variant=6, lanes=16)]
+              dict(variant=6, lanes=4), dict(variant=6, lanes=8, block=128), dict(variant=6, lanes=16),
+              dict(variant=7)]
     results = []
     for sh in shapes:
         xg, vg = gpu_run(m, pd, colors, 1 / 60, 1, 1, x0, v0, **sh)
@@ -70,6 +71,8 @@ def test_one_iteration_from_perturbed_state_ragged(orc):
         assert _err(a, b, m.rest) <= 1e-7
     # the fused cluster loop runs the same passes inside one launch
     assert np.array_equal(results[10], results[2]) and np.array_equal(results[11], results[3])
+    # warp rows: the same slots per lane in the same order as 4 lanes, streamed through shared memory
+    assert np.array_equal(results[17], results[2])
 
 
 def test_ground_contact_and_chebyshev(orc):
@@ -229,7 +232,8 @@ def test_block_jacobi(orc):
     assert np.array_equal(xk, xg)
 
 
-def test_pipeline_wait_time_out_is_reported_and_recoverable():
+@pytest.mark.parametrize("variant", [1, 7])
+def test_pipeline_wait_time_out_is_reported_and_recoverable(variant):
     """A bounded wait of the TMA-staged sweep that runs out (the test hook
     makes each CTA's first chunk also wait on a barrier at which nothing
     arrives) is reported as VBD_ERR_TIMEOUT; the context then runs normally
@@ -237,10 +241,10 @@ def test_pipeline_wait_time_out_is_reported_and_recoverable():
     m, cfg = synth.cantilever_beam()
     colors = synth.kuhn_coloring(m.grid_ijk)
     pd = params_of(cfg)
-    ref, _ = gpu_run(m, pd, colors, cfg.h, 5, 3, variant=1)
-    sim = vbd.Sim(m, vbd.make_params(**pd), colors=colors)
+    ref, _ = gpu_run(m, pd, colors, cfg.h, 5, 3, variant=variant)
+    sim = vbd.Sim(m, vbd.make_params(warp_rows=variant == 7, **pd), colors=colors)
     try:
-        vbd.vbd_set_launch(sim.ctx, 0, 0, 1)
+        vbd.vbd_set_launch(sim.ctx, 0, 0, variant)
         sim.set_state(m.rest, np.zeros_like(m.rest))
         vbd.vbd_debug_stall_pipeline(sim.ctx, True)
         vbd.vbd_begin_step(sim.ctx, cfg.h)

@@ -45,7 +45,7 @@ def _case(seed: int):
     v0[m.pinned == 1] = 0.0
     v0[:, 2] -= float(rng.uniform(0.0, 1.0))
     greedy = bool(rng.random() < 0.5)
-    variant = int(rng.choice([0, 1, 2, 4, 5, 6]))
+    variant = int(rng.choice([0, 1, 2, 4, 5, 6, 7]))
     lanes = int(rng.choice([4, 8, 16]))
     h = float(rng.choice([1 / 60, 1 / 120, 1 / 300]))
     iters, steps = int(rng.integers(3, 15)), int(rng.integers(2, 8))

@@ -48,7 +48,7 @@ def _on_subspaces(m, x, rel, x0=None):
         assert off <= rel * scale, (i, off, scale)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
 def test_rollers_match_oracle_on_every_variant(orc, variant):
     m = _rollers()
     colors = synth.kuhn_coloring(m.grid_ijk)

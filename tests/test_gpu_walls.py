@@ -32,7 +32,7 @@ def _f32(a):
     return np.asarray(a, np.float32).astype(np.float64)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
 def test_block_thrown_about_a_box_matches_oracle(orc, variant):
     """30 steps: the block hits the +x, +y and floor walls with friction on."""
     m = _block()
