@@ -1566,11 +1566,21 @@ static unsigned rows_grid() {
 void launch_sweep_rows(const Dev &d, const SweepParams &p, cudaStream_t s) {
     const int ng = p.gend - p.gbegin;
     if (ng <= 0) return;
-    static bool attr_set = false;  // above the 48 KB default of dynamic shared memory
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_sweep_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowSmem);
-        cudaFuncSetAttribute(k_sweep_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowSmem);
-        attr_set = true;
+    // above the 48 KB default of dynamic shared memory; the attribute is per device
+    static std::mutex mu;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;  // the caller reads the error
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!attr_set[dev]) {
+            if (cudaFuncSetAttribute(k_sweep_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kRowSmem) != cudaSuccess ||
+                cudaFuncSetAttribute(k_sweep_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kRowSmem) != cudaSuccess)
+                return;  // left in cudaGetLastError for the caller
+            attr_set[dev] = true;
+        }
     }
     const unsigned need = (unsigned)((ng + kRowWarps - 1) / kRowWarps);
     if (needs_ext(p))

@@ -125,3 +125,60 @@ def test_sweep_variants_agree_at_full_size(big):
         rest_err, pair_err))
     assert rest_err <= 1e-6
     assert pair_err <= 1e-6
+
+
+_ORACLE_TWO_STEPS = r'''
+import sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from oracle import oracle
+from paper_2403_06321_b300 import synth
+m, cfg = synth.large_cube(100)
+x0, v0 = synth.perturbed_state(m.rest, 0.0005, 0.5, seed=31)
+x = x0.astype(np.float32).astype(np.float64)
+v = v0.astype(np.float32).astype(np.float64)
+vp = v.copy()
+model = oracle.Model.from_mesh(m)
+p = oracle.Params.make(gravity=cfg.gravity, ground_on=cfg.ground_on, ground_height=cfg.ground_height,
+                       ground_normal=cfg.ground_normal, k_c=cfg.k_c, init_mode=cfg.init_mode, det_eps=cfg.det_eps)
+colors = synth.kuhn_coloring(m.grid_ijk)
+for _ in range(int(sys.argv[3])):
+    model.step(p, colors, 4, cfg.h, cfg.iters, x, v, vp)
+np.save(sys.argv[2], x)
+'''
+
+
+def test_two_full_steps_every_vertex(big, tmp_path):
+    """The benchmark workload at full size (1.03M vertices, 100 iterations per
+    step) from a deformed state with 0.5 m/s random velocities: two whole
+    steps on the GPU against two whole steps of the FP64 oracle, every
+    vertex compared.  The oracle runs its OpenMP build (bit-identical to the
+    serial one) in a child process on all host cores."""
+    import os
+    import subprocess
+    import sys
+    from oracle import oracle
+    m, cfg, x0, v0 = big
+    steps = 2
+    colors = synth.kuhn_coloring(m.grid_ijk)
+    sim = vbd.Sim(m, vbd.make_params(**params_of(cfg)), colors=colors)
+    try:
+        sim.set_state(x0, v0)
+        for _ in range(steps):
+            sim.step(cfg.h, cfg.iters)
+        sim.sync_status()
+        xg = sim.get_state()[0].cpu().numpy().astype(np.float64)
+    finally:
+        sim.close()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = str(tmp_path / "x.npy")
+    env = dict(os.environ, VBD_ORACLE_LIB=oracle.build(openmp=True))
+    subprocess.run([sys.executable, "-c", _ORACLE_TWO_STEPS, root, out, str(steps)], check=True, env=env,
+                   timeout=1800)
+    xo = np.load(out)
+    diag = bbox_diag(m.rest)
+    err = float(np.abs(xg - xo).max()) / diag
+    print("large cube, two full steps from a deformed state: max err / bbox = %.3e (moved %.3e)" % (
+        err, float(np.abs(xo - x0).max())))
+    assert float(np.abs(xo - x0).max()) > 1e-3
+    assert err <= 1e-5
