@@ -18,6 +18,8 @@
 // in-place update is an exact Gauss-Seidel sweep.
 #include "vbd_kernels.h"
 
+#include <algorithm>
+
 namespace vbd {
 
 namespace {
@@ -36,6 +38,19 @@ __device__ __forceinline__ float3 cross(float3 a, float3 b) {
 __device__ __forceinline__ float3 mulF(float3 f0, float3 f1, float3 f2, float3 v) {
     return make_float3(v.x * f0.x + v.y * f1.x + v.z * f2.x, v.x * f0.y + v.y * f1.y + v.z * f2.y,
                        v.x * f0.z + v.y * f1.z + v.z * f2.z);
+}
+
+// Dev::lam holds a 32-byte record per vertex: [2i] the recorded displacement
+// of the step being solved, [2i+1] lam_i.  One 256-bit load brings both
+// (non-coherent path: a colour pass reads only other colours' records, and
+// the cache does not outlive the launch), with an L2 evict-last policy so
+// that the records stay in L2 while the slot stream passes.
+__device__ __forceinline__ void ld_xlam(const float4 *rec, float3 &x, float3 &l) {
+    float xw, lw;
+    asm("{\n\t.reg .b64 pol;\n\tcreatepolicy.fractional.L2::evict_last.b64 pol, 1.0;\n\t"
+        "ld.global.nc.L2::cache_hint.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], pol;\n\t}"
+        : "=f"(x.x), "=f"(x.y), "=f"(x.z), "=f"(xw), "=f"(l.x), "=f"(l.y), "=f"(l.z), "=f"(lw)
+        : "l"(rec));
 }
 
 template <int L>
@@ -187,11 +202,10 @@ __global__ void __launch_bounds__(128, 8) k_adj_diag(Dev d, const float4 *__rest
 #ifndef VBD_ADJ_MIN_BLOCKS
 #define VBD_ADJ_MIN_BLOCKS 8
 #endif
-template <int L>
-__global__ void __launch_bounds__(128, VBD_ADJ_MIN_BLOCKS) k_adj_sweep(Dev d, const float4 *__restrict__ xs, SweepParams p,
-                                                      double *res_out) {
+template <int L, int MODE>
+__device__ __forceinline__ void adj_body(const Dev &d, const float4 *__restrict__ xs, const SweepParams &p,
+                                         double *res_out, long long gt) {
     const int lane = threadIdx.x & (L - 1);
-    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int vi = p.vbegin + (int)(gt / L);
     const bool active = vi < p.vend;
     float3 ui = make_float3(0.f, 0.f, 0.f);
@@ -210,9 +224,11 @@ __global__ void __launch_bounds__(128, VBD_ADJ_MIN_BLOCKS) k_adj_sweep(Dev d, co
         const float3 ga = make_float3(__int_as_float(r0.w), r1.x, r1.y);
         const float3 gb = make_float3(r1.z, r1.w, r2.x);
         const float3 gc = make_float3(r2.y, r2.z, r2.w);
-        const float3 la = f3(d.lam[r0.x]), lb = f3(d.lam[r0.y]), lc = f3(d.lam[r0.z]);  // other colours only
-        const float3 da = sub(f3(__ldg(xs + r0.x)), ui), db = sub(f3(__ldg(xs + r0.y)), ui),
-                     dc = sub(f3(__ldg(xs + r0.z)), ui);
+        float3 xa, xb, xc, la, lb, lc;  // other colours only
+        ld_xlam(d.lam + 2 * (size_t)r0.x, xa, la);
+        ld_xlam(d.lam + 2 * (size_t)r0.y, xb, lb);
+        ld_xlam(d.lam + 2 * (size_t)r0.z, xc, lc);
+        const float3 da = sub(xa, ui), db = sub(xb, ui), dc = sub(xc, ui);
         const float3 gbc = cross(gb, gc);
         const float detg = dot(ga, gbc);
         const float inv = __frcp_rn(detg);
@@ -254,12 +270,12 @@ __global__ void __launch_bounds__(128, VBD_ADJ_MIN_BLOCKS) k_adj_sweep(Dev d, co
         const float4 hA = d.hdiag[2 * vi], hB = d.hdiag[2 * vi + 1];  // H_ii of k_adj_diag
         const float h00 = hA.x, h01 = hA.y, h02 = hA.z, h11 = hA.w, h12 = hB.x, h22 = hB.y;
         const int sub = p.n_sub > 0 ? d.sub_id[vi] : -1;
-        if (p.adj_residual != 0) {
+        if (MODE != 0) {
             // r - (H lam)_i = b - H_ii lam_i
-            const float4 l = d.lam[vi];
+            const float4 l = d.lam[2 * (size_t)vi + 1];
             float e0 = b0 - (h00 * l.x + h01 * l.y + h02 * l.z), e1 = b1 - (h01 * l.x + h11 * l.y + h12 * l.z),
                   e2 = b2 - (h02 * l.x + h12 * l.y + h22 * l.z);
-            if (p.adj_residual == 1) {
+            if (MODE == 1) {
                 // the part of xbar that follows x_t across a constrained vertex's fixed directions
                 if (sub >= 0) d.rhs[vi] = make_float4(e0, e1, e2, 0.f);
             } else {
@@ -315,10 +331,10 @@ __global__ void __launch_bounds__(128, VBD_ADJ_MIN_BLOCKS) k_adj_sweep(Dev d, co
             if (!(isfinite(l0) && isfinite(l1) && isfinite(l2)))
                 atomicAdd(d.counters + 0, 1ull);
             else
-                d.lam[vi] = make_float4(l0, l1, l2, 0.f);
+                d.lam[2 * (size_t)vi + 1] = make_float4(l0, l1, l2, 0.f);
         }
     }
-    if (p.adj_residual == 2) {
+    if (MODE == 2) {
         // the mode is uniform over the grid, so every lane of the warp is here
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -332,6 +348,18 @@ __global__ void __launch_bounds__(128, VBD_ADJ_MIN_BLOCKS) k_adj_sweep(Dev d, co
     }
 }
 
+// Persistent grid: 148 x resident CTAs walk the colour's vertices with a
+// grid stride (every thread of a CTA makes the same number of turns, so the
+// warp-wide reduction of mode 2 sees full warps).  MODE = SweepParams::adj_residual,
+// one instance each, so that the sweep (mode 0) carries no residual code.
+template <int L, int MODE>
+__global__ void __launch_bounds__(128, VBD_ADJ_MIN_BLOCKS) k_adj_sweep(Dev d, const float4 *__restrict__ xs, SweepParams p,
+                                                      double *res_out, long long threads) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < threads; base += stride)
+        adj_body<L, MODE>(d, xs, p, res_out, base + threadIdx.x);
+}
+
 // xbar, vbar <- seed; lam <- 0; gtheta <- 0 is done by the host (memset).
 __global__ void k_adj_seed(Dev d, const float *dL_dx, int n) {
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
@@ -341,11 +369,13 @@ __global__ void k_adj_seed(Dev d, const float *dL_dx, int n) {
     d.vbar[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// r = xbar + vbar / h on free vertices; lam = 0 everywhere (pinned stay 0).
-__global__ void k_adj_rhs(Dev d, int n, int n_free, float inv_h) {
+// r = xbar + vbar / h on free vertices; lam = 0 everywhere (pinned stay 0)
+// beside the step's recorded displacement in the vertex's (x, lam) record.
+__global__ void k_adj_rhs(Dev d, const float4 *__restrict__ xs, int n, int n_free, float inv_h) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    d.lam[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    d.lam[2 * (size_t)i] = xs[i];
+    d.lam[2 * (size_t)i + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (i >= n_free) return;
     const float4 xb = d.xbar[i], vb = d.vbar[i];
     d.rhs[i] = make_float4(xb.x + vb.x * inv_h, xb.y + vb.y * inv_h, xb.z + vb.z * inv_h, 0.f);
@@ -362,7 +392,7 @@ __global__ void k_adj_post_verts(Dev d, int n, int n_free, float h, int has_sub)
         return;
     }
     const float m = d.mass[i];
-    const float4 l = d.lam[i], vb = d.vbar[i];
+    const float4 l = d.lam[2 * (size_t)i + 1], vb = d.vbar[i];
     const float a = m / (h * h), b = m / h, c = 1.f / h;
     float4 xb = make_float4(a * l.x - c * vb.x, a * l.y - c * vb.y, a * l.z - c * vb.z, 0.f);
     if (has_sub && d.sub_id[i] >= 0) {
@@ -395,7 +425,7 @@ __global__ void k_adj_post_tets(Dev d, const float4 *__restrict__ xs, int n_tets
     float acc = 0.f;
     for (int k = 0; k < 4; ++k) {
         const float3 gk = k == 0 ? g0 : g[k - 1];
-        const float3 l = f3(d.lam[id[k]]);
+        const float3 l = f3(d.lam[2 * (size_t)id[k] + 1]);
         const float3 c = F.cof(gk);                  // g_k + c'_k
         const float3 Dg = F.dmul(gk);
         const float3 cp = make_float3(c.x - gk.x, c.y - gk.y, c.z - gk.z);
@@ -415,26 +445,57 @@ __global__ void k_adj_out(Dev d, float *dL_dv0, int n) {
 
 inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
+// SMs x resident CTAs of k_adj_sweep<lanes, MODE> at this block size on the
+// current device (0 if the query fails: the launch then covers every vertex at once)
+template <int MODE>
+long long adj_persist_grid(int lanes, int block) {
+    int dev = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    cudaError_t e;
+    switch (lanes) {
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adj_sweep<4, MODE>, block, 0); break;
+    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adj_sweep<8, MODE>, block, 0); break;
+    case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adj_sweep<16, MODE>, block, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adj_sweep<32, MODE>, block, 0); break;
+    }
+    if (e != cudaSuccess || occ < 1) return 0;
+    return (long long)sms * occ;
+}
+
+template <int MODE>
+void launch_adj_sweep_mode(const Dev &d, const float4 *xs, const SweepParams &p, int lanes, int block,
+                           long long threads, cudaStream_t s, double *res_out) {
+    const long long need = (long long)blocks_for(threads, block);
+    const long long cap = adj_persist_grid<MODE>(lanes, block);
+    const unsigned grid = (unsigned)(cap > 0 ? std::min(need, cap) : need);
+    switch (lanes) {
+    case 4: k_adj_sweep<4, MODE><<<grid, block, 0, s>>>(d, xs, p, res_out, threads); break;
+    case 8: k_adj_sweep<8, MODE><<<grid, block, 0, s>>>(d, xs, p, res_out, threads); break;
+    case 16: k_adj_sweep<16, MODE><<<grid, block, 0, s>>>(d, xs, p, res_out, threads); break;
+    default: k_adj_sweep<32, MODE><<<grid, block, 0, s>>>(d, xs, p, res_out, threads); break;
+    }
+}
+
 }  // namespace
 
 void launch_adj_seed(const Dev &d, const float *dL_dx, int n, cudaStream_t s) {
     k_adj_seed<<<blocks_for(n, 256), 256, 0, s>>>(d, dL_dx, n);
 }
 
-void launch_adj_rhs(const Dev &d, int n, int n_free, float inv_h, cudaStream_t s) {
-    k_adj_rhs<<<blocks_for(n, 256), 256, 0, s>>>(d, n, n_free, inv_h);
+void launch_adj_rhs(const Dev &d, const float4 *xs, int n, int n_free, float inv_h, cudaStream_t s) {
+    k_adj_rhs<<<blocks_for(n, 256), 256, 0, s>>>(d, xs, n, n_free, inv_h);
 }
 
 void launch_adj_sweep(const Dev &d, const float4 *xs, const SweepParams &p, int lanes, int block,
                       cudaStream_t s, double *res_out) {
     const long long threads = (long long)(p.vend - p.vbegin) * lanes;
     if (threads <= 0) return;
-    const unsigned grid = blocks_for(threads, block);
-    switch (lanes) {
-    case 4: k_adj_sweep<4><<<grid, block, 0, s>>>(d, xs, p, res_out); break;
-    case 8: k_adj_sweep<8><<<grid, block, 0, s>>>(d, xs, p, res_out); break;
-    case 16: k_adj_sweep<16><<<grid, block, 0, s>>>(d, xs, p, res_out); break;
-    default: k_adj_sweep<32><<<grid, block, 0, s>>>(d, xs, p, res_out); break;
+    switch (p.adj_residual) {
+    case 0: launch_adj_sweep_mode<0>(d, xs, p, lanes, block, threads, s, res_out); break;
+    case 1: launch_adj_sweep_mode<1>(d, xs, p, lanes, block, threads, s, res_out); break;
+    default: launch_adj_sweep_mode<2>(d, xs, p, lanes, block, threads, s, res_out); break;
     }
 }
 

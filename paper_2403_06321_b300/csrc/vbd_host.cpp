@@ -355,7 +355,7 @@ size_t carve(const vbd_ctx *c, char *base, Dev *d) {
     t.gnorm = (double *)take(16);
     t.adj_res = (double *)take(16 * (size_t)std::max(c->params.tape_steps, 1));
     t.tape = (float4 *)take(16 * N * (size_t)std::max(c->params.tape_steps, 0));
-    t.lam = (float4 *)take(16 * N);
+    t.lam = (float4 *)take((c->params.tape_steps > 0 ? 32 : 16) * (size_t)N);
     if (c->params.tape_steps > 0) t.hdiag = (float4 *)take(32 * N);
     t.rhs = (float4 *)take(16 * N);
     t.xbar = (float4 *)take(16 * N);
@@ -1552,7 +1552,7 @@ vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, floa
         const float h = ctx->tape_h[t];
         ctx->h = h;
         const float4 *xs = d.tape + (size_t)t * N;
-        vbd::launch_adj_rhs(d, N, ctx->n_free, 1.f / h, s);
+        vbd::launch_adj_rhs(d, xs, N, ctx->n_free, 1.f / h, s);
         {  // the diagonal blocks do not change during this step's sweeps
             vbd::SweepParams dp = sweep_params(ctx, -1);
             dp.vbegin = 0;

@@ -57,7 +57,9 @@ struct Dev {
     double *adj_res;  // 2 per tape step: max |r - H lam| and max |r| after the step's adjoint sweeps
     float4 *tape;     // tape_steps * N displacements
     // adjoint
-    float4 *lam, *rhs, *xbar, *vbar;
+    float4 *lam;      // 2N with a tape: per vertex a 32-byte record, [2i] the recorded displacement
+                      // of the step being solved, [2i+1] lam_i (one 256-bit gather brings both)
+    float4 *rhs, *xbar, *vbar;
     float4 *hdiag;    // 2N: each free vertex's diagonal block H_ii of the current adjoint step
                       // (h00 h01 h02 h11 | h12 h22 . .); carved with a tape
     float *gtheta;    // T
@@ -208,7 +210,7 @@ void launch_ccd(const Dev &d, const CollideDims &c, int n_free, cudaStream_t s);
 void launch_set_log_young(const Dev &d, const float *log_young, int n_tets, cudaStream_t s);
 
 // adjoint
-void launch_adj_rhs(const Dev &d, int n, int n_free, float inv_h, cudaStream_t s);
+void launch_adj_rhs(const Dev &d, const float4 *xs, int n, int n_free, float inv_h, cudaStream_t s);
 // H_ii of the free vertices [p.vbegin, p.vend) at the recorded positions xs, into Dev::hdiag
 void launch_adj_diag(const Dev &d, const float4 *xs, const SweepParams &p, int lanes, int block, cudaStream_t s);
 void launch_adj_sweep(const Dev &d, const float4 *xs, const SweepParams &p, int lanes, int block,
