@@ -182,3 +182,87 @@ def test_two_full_steps_every_vertex(big, tmp_path):
         err, float(np.abs(xo - x0).max())))
     assert float(np.abs(xo - x0).max()) > 1e-3
     assert err <= 1e-5
+
+
+def test_adjoint_one_sweep_sampled(orc, big):
+    """The adjoint's first block Gauss-Seidel sweep at full size, where each
+    colour pass takes several turns of the persistent grid.  With one recorded
+    step, lam = 0 before the sweep and dL/dv0 = M/h lam after it, and for the
+    first two colours lam after one sweep is an exact function of the recorded
+    state: colour 0: lam_i = H_ii^-1 r_i; colour 1: lam_i = H_ii^-1 (r_i -
+    sum_k H_ik lam_k) over its colour-0 neighbours k (the others are still 0),
+    with r = dL/dx_T and H = M/h^2 + d2E/dx2 (+ ground) at the recorded
+    positions.  Sampled vertices across each colour's whole range are
+    recomputed in FP64 from the oracle's element Hessian blocks."""
+    m, cfg, x0, v0 = big
+    colors = synth.kuhn_coloring(m.grid_ijk)
+    pd = params_of(cfg)
+    sim = vbd.Sim(m, vbd.make_params(tape_steps=1, **pd), colors=colors)
+    rng = np.random.default_rng(41)
+    g = rng.normal(0.0, 1.0, size=m.rest.shape)
+    try:
+        dev = sim.workspace.device
+        sim.set_state(x0, v0)
+        sim.step(cfg.h, cfg.iters)
+        x1 = sim.get_state()[0].cpu().numpy().astype(np.float64)
+        gx = torch.tensor(g.reshape(-1), dtype=torch.float32, device=dev)
+        gE = torch.empty(m.n_tets, dtype=torch.float32, device=dev)
+        gv = torch.empty(3 * m.n_verts, dtype=torch.float32, device=dev)
+        vbd.vbd_backward(sim.ctx, gx, gE, gv, 1)
+        sim.sync_status()
+        gv = gv.cpu().numpy().astype(np.float64).reshape(-1, 3)
+    finally:
+        sim.close()
+    r = g.astype(np.float32).astype(np.float64)  # the seed as the GPU read it
+    model = orc.Model.from_mesh(m)
+    p = orc.Params.make(**pd)
+    h = cfg.h
+    mass = model.mass()
+    B, V, mu, lam = model.tet_data()
+    tets = m.tets
+    order = np.argsort(tets.reshape(-1), kind="stable")
+    start = np.searchsorted(tets.reshape(-1)[order], np.arange(m.n_verts + 1))
+    planes = model._plane_terms(p, x1)
+
+    def incident(i):
+        e = order[start[i]:start[i + 1]]
+        return e // 4, e % 4
+
+    def block(j, a, b):
+        return orc.tet_hess_block(x1[tets[j]].reshape(-1), B[j], V[j], mu[j], lam[j], int(a), int(b))
+
+    def h_ii(i):
+        H = mass[i] / h ** 2 * np.eye(3)
+        for j, a in zip(*incident(i)):
+            H += block(j, a, a)
+        for nrm, _, act in planes:
+            if act[i]:
+                H += p.k_c * np.outer(nrm, nrm)
+        return H
+
+    lam0 = {}
+
+    def lam_colour0(k):
+        if k not in lam0:
+            lam0[k] = np.linalg.solve(h_ii(k), r[k])
+        return lam0[k]
+
+    turn = torch.cuda.get_device_properties(0).multi_processor_count * 8 * 128 // 4
+    for c in (0, 1):
+        ids = np.nonzero(colors == c)[0]
+        sample = ids[np.unique(np.linspace(0, len(ids) - 1, 120).astype(np.int64))]
+        want = np.zeros((len(sample), 3))
+        for s, i in enumerate(sample):
+            b = r[i].copy()
+            if c == 1:
+                for j, a in zip(*incident(i)):
+                    for bl in range(4):
+                        k = tets[j][bl]
+                        if bl != a and colors[k] == 0:
+                            b -= block(j, a, bl) @ lam_colour0(k)
+            want[s] = np.linalg.solve(h_ii(i), b)
+        got = gv[sample] * h / mass[sample][:, None]
+        err = float(np.abs(got - want).max() / np.abs(want).max())
+        print("adjoint one sweep, colour %d (%d vertices, about %.1f turns of the grid): max err / max |lam| = %.2e"
+              % (c, len(ids), len(ids) / turn, err))
+        assert err <= 1e-4
