@@ -74,6 +74,8 @@ def parse_args(argv=None):
     ap.add_argument("--young", type=float, default=0.0, help="override Young's modulus of the workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-per-mesh", action="store_true",
+                    help="batched leg: skip the comparison with one context per mesh")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched, adjoint, self-collision and Chebyshev comparisons")
     ap.add_argument("--batch-meshes", type=int, default=4096)
@@ -404,7 +406,10 @@ def run_batched(args) -> dict:
     stream = torch.cuda.Stream()
     sim = vbd.Sim(cat, params, colors=colors, stream=stream, vert_offset=voff, tet_offset=toff)
     sim.set_state(cat.rest, np.zeros_like(cat.rest))
-    vbd.vbd_autotune(sim.ctx, cfg.h, cfg.iters)  # launch shape for this batch
+    if args.lanes or args.block or args.variant >= 0:  # a given launch shape (profiling)
+        vbd.vbd_set_launch(sim.ctx, args.lanes, args.block, args.variant)
+    elif not args.no_autotune:
+        vbd.vbd_autotune(sim.ctx, cfg.h, cfg.iters)  # launch shape for this batch
     info = vbd.vbd_get_info(sim.ctx)
     sim.set_state(cat.rest, np.zeros_like(cat.rest))
     steps = 5
@@ -433,6 +438,15 @@ def run_batched(args) -> dict:
         b_own = inc * 16 + 60 + 24 * C
         roof["own_model_bytes_per_update"] = b_own
         roof["own_model_frac"] = info.n_free / C * b_own / avg_launch_s / 1e9 / peak
+    out = {"workload": "%d beams, %d verts, %d tets, Kuhn 4-colouring, h=1/60, %d iterations/step, "
+                       "one launch per colour for all meshes, CUDA graph per step" % (
+                           len(meshes), cat.n_verts, cat.n_tets, iters),
+           "launch": {"sweep_variant": VARIANTS[info.pipeline], "lanes_per_vertex": info.lanes_per_vertex,
+                      "block_threads": info.block_threads},
+           "value": v_batched, "unit": UNIT, "ms_per_step": t_b * 1e3 / steps,
+           "n_free_verts": int(info.n_free), "roofline": roof}
+    if args.no_per_mesh:
+        return out
     # per-mesh contexts
     sims = []
     for m in meshes:
@@ -451,14 +465,9 @@ def run_batched(args) -> dict:
     for s_ in sims:
         s_.sync_status()
         s_.close()
-    return {"workload": "%d beams, %d verts, %d tets, Kuhn 4-colouring, h=1/60, %d iterations/step, "
-                        "one launch per colour for all meshes, CUDA graph per step" % (
-                            len(meshes), cat.n_verts, cat.n_tets, iters),
-            "launch": {"sweep_variant": VARIANTS[info.pipeline], "lanes_per_vertex": info.lanes_per_vertex,
-                       "block_threads": info.block_threads},
-            "value": v_batched, "unit": UNIT, "ms_per_step": t_b * 1e3 / steps,
-            "per_mesh_value": v_plain, "per_mesh_ms_per_step": t_p * 1e3 / psteps,
-            "speedup_vs_plain": v_batched / v_plain, "n_free_verts": int(info.n_free), "roofline": roof}
+    out.update({"per_mesh_value": v_plain, "per_mesh_ms_per_step": t_p * 1e3 / psteps,
+                "speedup_vs_plain": v_batched / v_plain})
+    return out
 
 
 def run_adjoint(args, reps: int = 5) -> dict:
