@@ -13,9 +13,11 @@
 //   d L / d log E_j -= sum_{i in tet j} lam_i . dE_j/dx_i.
 // The block Gauss-Seidel sweep reuses the forward's slot layout: per slot it
 // forms the tet's off-diagonal blocks H_ik (k = the three other vertices)
-// applied to lam_k, and the vertex's diagonal block, then one lane solves
-// the 3x3 system for lam_i.  Vertices of one colour share no tet, so the
-// in-place update is an exact Gauss-Seidel sweep.
+// applied to lam_k, then one lane solves the 3x3 system for lam_i with the
+// diagonal block H_ii that k_adj_diag computed once for the step.  Vertices
+// of one colour share no tet, so the in-place update is an exact
+// Gauss-Seidel sweep.  Each vertex's recorded displacement and lam sit in one
+// 32-byte record (Dev::lam), so a neighbour costs one 256-bit gather.
 #include "vbd_kernels.h"
 
 #include <algorithm>
