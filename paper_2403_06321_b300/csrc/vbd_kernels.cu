@@ -903,10 +903,15 @@ __global__ void __launch_bounds__(TT) k_sweep_pipe(Dev d, SweepParams p, int max
             return;
         }
         // all threads are past chunk k-1: its stage takes chunk k-1+kPipeStages
+        // (the block barrier orders every thread's reads of the stage before
+        // thread 0's next accesses; the proxy fence extends that order to the
+        // bulk copies' async-proxy writes)
         if (k >= 1 && threadIdx.x == 0) {
             const int kk = k - 1 + kPipeStages;
-            if (first + kk * stride < nchunks)
+            if (first + kk * stride < nchunks) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 pipe_issue(d, p, first + kk * stride, CV, maxs, stages, meta, bar, kk % kPipeStages);
+            }
         }
         const StageMeta m = meta[st];
         const StageView v = stage_view(stages + st * pipe_stage_bytes(maxs), maxs);
@@ -1057,9 +1062,12 @@ __global__ void __launch_bounds__(256, VBD_ROWS_MIN_BLOCKS) k_sweep_rows(Dev d, 
             for (int h = 0; h < kRowIters; ++h)
 #pragma unroll
                 for (int a = 0; a < 3; ++a) e[3 * h + a] = row[a * kRowEntries + 32 * h + wl];
-            // every lane's reads of this stage are ordered before lane 0 refills it
+            // every lane's reads of this stage are ordered before lane 0 refills it:
+            // the warp barrier orders them before lane 0's next accesses, and the
+            // proxy fence extends that order to the bulk copy's async-proxy writes
             __syncwarp();
             if (wl == 0 && ig < ng) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 row_issue(d, grow[ig] + ik, ring + st * kRowBytes, bar + st);
                 ++issued;
                 if (++ik == iK) {
