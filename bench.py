@@ -421,7 +421,7 @@ def run_batched(args) -> dict:
     sim.sync_status()
     v_batched = info.n_free * iters * steps / t_b
     sim.close()
-    # roofline of the colour passes: the survey's byte model per update
+    # roofline of the colour passes: the algorithmic byte model per update
     # (rest data 52 B per incidence, own vertex 44 B, neighbour re-reads
     # 12 B per colour) and, for the compact-slot kernels, their own (16 B of
     # ids per incidence, 60 B own vertex and rest position, 24 B per colour)
