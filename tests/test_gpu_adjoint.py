@@ -1,6 +1,7 @@
 """GPU adjoint (vbd_backward, via the torch.autograd wrapper) against the
-oracle's FP64 adjoint of the same steps.  The oracle adjoint is itself
-pinned to central finite differences (tests/test_oracle_adjoint.py).
+oracle's FP64 adjoint of the same steps, and on a converged beam straight
+against central finite differences of the FP64 forward.  The oracle adjoint
+is itself pinned to central finite differences (tests/test_oracle_adjoint.py).
 Gate, element by element: every entry of dL/dlog E within 1e-3 of the
 largest |entry| of the oracle's, likewise each component of dL/dv0 against
 that component's largest entry, and the same sign wherever the oracle's
@@ -111,6 +112,60 @@ def test_adjoint_converged_small_beam(orc):
     assert np.abs(xg - xo).max() < 1e-5
     _check("small beam", gE, oE, gv, ov)
     assert np.all(gv[m.pinned == 1] == 0)
+
+
+def test_adjoint_against_central_fd(orc):
+    """The GPU adjoint straight against central finite differences of the
+    loss (no oracle adjoint in between): the 6x2x2 beam of the test above, 4
+    steps, the GPU forward and adjoint run to convergence; the differences
+    are taken on the FP64 forward solved by dense Newton for sampled tets'
+    log E and sampled components of v0.  Gate: every sampled entry within
+    1e-3 of its column's largest |entry|.  Steps: 3e-2 in log E and 1e-2
+    m/s in v0.  The converged forward leaves about 1e-11 of noise in the
+    loss and the dL/dlog E entries here are only ~1e-5, so smaller steps
+    measure the noise (at 1e-4 the quotient is off by 1e-2 of the largest
+    entry); at these steps the central differences agree with the oracle's
+    dense adjoint to 1e-4 (log E) and 1e-5 (v0) of the largest entry."""
+    m = synth.beam(6, 2, 2, E=1e5, nu=0.4, jitter_frac=0.05, seed=51)
+    colors, _ = orc.color_greedy(m.n_verts, m.tets)
+    pd = params_of(synth.SimConfig())
+    rng = np.random.default_rng(52)
+    v0 = rng.normal(0, 0.3, m.rest.shape) * (1 - m.pinned[:, None])
+    tip = np.nonzero(m.grid_ijk[:, 0] == 6)[0]
+    target = m.rest[tip] + np.array([0.05, -0.03, 0.08])
+    h, steps = 1 / 60, 4
+    gE, gv, _ = _gpu_grads(m, pd, colors, h, 400, steps, v0, tip, target, adj_iters=300)
+    model = orc.Model.from_mesh(m)
+    p = orc.Params.make(**pd)
+    logE = np.log(m.young.astype(np.float64))
+
+    def loss(le, vv):
+        model.set_log_young(le)
+        x, v = m.rest.copy(), np.array(vv, np.float64)
+        for _ in range(steps):
+            y = model.inertia_target(p, h, x, v)
+            xn = model.newton_solve(p, h, x + h * v, y, tol=1e-14, max_iter=60)
+            v, x = (xn - x) / h, xn
+        d = x[tip] - target
+        return float((d * d).sum(axis=1).mean())
+
+    eps_E, eps_v = 3e-2, 1e-2
+    worst_E = worst_v = 0.0
+    for j in rng.choice(m.n_tets, 6, replace=False):
+        e = np.zeros_like(logE)
+        e[j] = eps_E
+        fd = (loss(logE + e, v0) - loss(logE - e, v0)) / (2 * eps_E)
+        worst_E = max(worst_E, abs(gE[j] - fd) / np.abs(gE).max())
+    free = np.nonzero(m.pinned == 0)[0]
+    for i in rng.choice(free, 4, replace=False):
+        for r in range(3):
+            dv = np.zeros_like(v0)
+            dv[i, r] = eps_v
+            fd = (loss(logE, v0 + dv) - loss(logE, v0 - dv)) / (2 * eps_v)
+            worst_v = max(worst_v, abs(gv[i, r] - fd) / np.abs(gv[:, r]).max())
+    print("GPU adjoint vs central FD: dlogE worst %.2e, dv0 worst %.2e (of the column's largest entry)" % (
+        worst_E, worst_v))
+    assert worst_E <= 1e-3 and worst_v <= 1e-3
 
 
 def test_adjoint_differentiable_beam_full_size(orc):
