@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(128, 8) k_adj_diag(Dev d, const float4 *__rest
 #endif
 template <int L, int MODE>
 __device__ __forceinline__ void adj_body(const Dev &d, const float4 *__restrict__ xs, const SweepParams &p,
-                                         double *res_out, long long gt) {
+                                         long long gt, float &res_acc, float &r_acc) {
     const int lane = threadIdx.x & (L - 1);
     const int vi = p.vbegin + (int)(gt / L);
     const bool active = vi < p.vend;
@@ -345,17 +345,9 @@ __device__ __forceinline__ void adj_body(const Dev &d, const float4 *__restrict_
                 d.lam[2 * (size_t)vi + 1] = make_float4(l0, l1, l2, 0.f);
         }
     }
-    if (MODE == 2) {
-        // the mode is uniform over the grid, so every lane of the warp is here
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            res_max = fmaxf(res_max, __shfl_xor_sync(FULL, res_max, off));
-            r_max = fmaxf(r_max, __shfl_xor_sync(FULL, r_max, off));
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicMax((unsigned long long *)res_out, (unsigned long long)__double_as_longlong((double)res_max));
-            atomicMax((unsigned long long *)res_out + 1, (unsigned long long)__double_as_longlong((double)r_max));
-        }
+    if (MODE == 2) {  // running maxima of this thread over its grid-stride turns
+        res_acc = fmaxf(res_acc, res_max);
+        r_acc = fmaxf(r_acc, r_max);
     }
 }
 
@@ -367,8 +359,22 @@ template <int L, int MODE>
 __global__ void __launch_bounds__(128, VBD_ADJ_MIN_BLOCKS) k_adj_sweep(Dev d, const float4 *__restrict__ xs, SweepParams p,
                                                       double *res_out, long long threads) {
     const long long stride = (long long)gridDim.x * blockDim.x;
+    float res_acc = 0.f, r_acc = 0.f;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < threads; base += stride)
-        adj_body<L, MODE>(d, xs, p, res_out, base + threadIdx.x);
+        adj_body<L, MODE>(d, xs, p, base + threadIdx.x, res_acc, r_acc);
+    if (MODE == 2) {
+        // every thread of the CTA made the same number of turns, so the whole
+        // warp is here: one warp reduction and two atomics per warp
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            res_acc = fmaxf(res_acc, __shfl_xor_sync(FULL, res_acc, off));
+            r_acc = fmaxf(r_acc, __shfl_xor_sync(FULL, r_acc, off));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMax((unsigned long long *)res_out, (unsigned long long)__double_as_longlong((double)res_acc));
+            atomicMax((unsigned long long *)res_out + 1, (unsigned long long)__double_as_longlong((double)r_acc));
+        }
+    }
 }
 
 // xbar, vbar <- seed; lam <- 0; gtheta <- 0 is done by the host (memset).

@@ -49,6 +49,14 @@ struct GraphEntry {
     cudaGraphExec_t exec;
 };
 
+// a captured backward step loop: keyed on the tape length, the sweeps per
+// step, a hash of the recorded step sizes and the context's version
+struct AdjGraphEntry {
+    int tape_len, adj_iters;
+    uint64_t h_hash, version;
+    cudaGraphExec_t exec;
+};
+
 }  // namespace
 
 struct vbd_ctx {
@@ -122,6 +130,7 @@ struct vbd_ctx {
     bool use_graph = true;
     uint64_t version = 1;
     std::vector<GraphEntry> graphs;
+    std::vector<AdjGraphEntry> adj_graphs;
     cudaStream_t capture_stream = nullptr;
     std::string err = "no error";
 };
@@ -483,6 +492,8 @@ bool params_ok(const vbd_params *p, std::string &why) {
 void clear_graphs(vbd_ctx *c) {
     for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
     c->graphs.clear();
+    for (auto &g : c->adj_graphs) cudaGraphExecDestroy(g.exec);
+    c->adj_graphs.clear();
 }
 
 // Chebyshev omega_n of Eq. 19 (computed in FP64)
@@ -1529,6 +1540,44 @@ vbd_status vbd_sync_status(vbd_ctx *ctx, int64_t *det_skips, int64_t *contacts) 
     return VBD_OK;
 }
 
+// The launches of recorded step t of the backward (Sec. 3.1 Eq. 2 through the
+// implicit-function theorem): right-hand side, the step's diagonal blocks,
+// adj_iters colour-ordered block Gauss-Seidel sweeps, the residual passes and
+// the parameter and state adjoints, all on the workspace; ctx->h is set to
+// the step's h for the sweep parameters (the caller restores it).
+static void enqueue_adjoint_step(vbd_ctx *ctx, int t, int adj_iters, cudaStream_t s) {
+    const vbd::Dev &d = ctx->d;
+    const int N = ctx->N;
+    const float h = ctx->tape_h[t];
+    ctx->h = h;
+    const float4 *xs = d.tape + (size_t)t * N;
+    vbd::launch_adj_rhs(d, xs, N, ctx->n_free, 1.f / h, s);
+    {  // the diagonal blocks do not change during this step's sweeps
+        vbd::SweepParams dp = sweep_params(ctx, -1);
+        dp.vbegin = 0;
+        dp.vend = ctx->n_free;
+        vbd::launch_adj_diag(d, xs, dp, kAdjLanes, kAdjBlock, s);
+    }
+    for (int it = 0; it < adj_iters; ++it)
+        for (int col = 0; col < ctx->n_colors; ++col)
+            vbd::launch_adj_sweep(d, xs, sweep_params(ctx, col), kAdjLanes, kAdjBlock, s);
+    const bool has_sub = !ctx->sub_vertex.empty();
+    if (has_sub)  // r - (H lam)_i of the constrained vertices, for xbar
+        for (int col = 0; col < ctx->n_colors; ++col) {
+            vbd::SweepParams rp = sweep_params(ctx, col);
+            rp.adj_residual = 1;
+            vbd::launch_adj_sweep(d, xs, rp, kAdjLanes, kAdjBlock, s);
+        }
+    {  // how far the sweeps left lam from H lam = r: max |r - H lam| and max |r|
+        vbd::SweepParams rp = sweep_params(ctx, -1);
+        rp.vbegin = 0;
+        rp.vend = ctx->n_free;
+        rp.adj_residual = 2;
+        vbd::launch_adj_sweep(d, xs, rp, kAdjLanes, kAdjBlock, s, d.adj_res + 2 * (size_t)t);
+    }
+    vbd::launch_adj_post(d, xs, N, ctx->n_free, ctx->T, h, has_sub, s);
+}
+
 vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, float *dL_dv0, int32_t adj_iters) {
     Range range_("vbd_backward");
     vbd_status st = check_bound(ctx);
@@ -1548,35 +1597,43 @@ vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, floa
     CU(cudaMemsetAsync(d.adj_res, 0, 16 * (size_t)ctx->tape_len, s), "clear adjoint residuals");
     vbd::launch_adj_seed(d, dL_dxT, N, s);
     const float h_saved = ctx->h;
-    for (int t = ctx->tape_len - 1; t >= 0; --t) {
-        const float h = ctx->tape_h[t];
-        ctx->h = h;
-        const float4 *xs = d.tape + (size_t)t * N;
-        vbd::launch_adj_rhs(d, xs, N, ctx->n_free, 1.f / h, s);
-        {  // the diagonal blocks do not change during this step's sweeps
-            vbd::SweepParams dp = sweep_params(ctx, -1);
-            dp.vbegin = 0;
-            dp.vend = ctx->n_free;
-            vbd::launch_adj_diag(d, xs, dp, kAdjLanes, kAdjBlock, s);
+    if (!ctx->use_graph) {
+        for (int t = ctx->tape_len - 1; t >= 0; --t) enqueue_adjoint_step(ctx, t, adj_iters, s);
+        CU(cudaGetLastError(), "backward");
+    } else {
+        // the whole step loop as one CUDA graph: its launches read and write
+        // only the workspace, so one capture serves every later call with the
+        // same tape length, sweep count and step sizes
+        uint64_t hh = 1469598103934665603ull;
+        for (int t = 0; t < ctx->tape_len; ++t) {
+            uint32_t b;
+            std::memcpy(&b, &ctx->tape_h[t], 4);
+            hh = (hh ^ b) * 1099511628211ull;
         }
-        for (int it = 0; it < adj_iters; ++it)
-            for (int col = 0; col < ctx->n_colors; ++col)
-                vbd::launch_adj_sweep(d, xs, sweep_params(ctx, col), kAdjLanes, kAdjBlock, s);
-        const bool has_sub = !ctx->sub_vertex.empty();
-        if (has_sub)  // r - (H lam)_i of the constrained vertices, for xbar
-            for (int col = 0; col < ctx->n_colors; ++col) {
-                vbd::SweepParams rp = sweep_params(ctx, col);
-                rp.adj_residual = 1;
-                vbd::launch_adj_sweep(d, xs, rp, kAdjLanes, kAdjBlock, s);
+        cudaGraphExec_t exec = nullptr;
+        for (auto &g : ctx->adj_graphs)
+            if (g.tape_len == ctx->tape_len && g.adj_iters == adj_iters && g.h_hash == hh &&
+                g.version == ctx->version)
+                exec = g.exec;
+        if (!exec) {
+            if (!ctx->capture_stream)
+                CU(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking), "capture stream");
+            cudaGraph_t graph = nullptr;
+            CU(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            for (int t = ctx->tape_len - 1; t >= 0; --t) enqueue_adjoint_step(ctx, t, adj_iters, ctx->capture_stream);
+            cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &graph);
+            ctx->h = h_saved;
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture (backward)");
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate (backward)");
+            if (ctx->adj_graphs.size() >= 4) {
+                cudaGraphExecDestroy(ctx->adj_graphs.front().exec);
+                ctx->adj_graphs.erase(ctx->adj_graphs.begin());
             }
-        {  // how far the sweeps left lam from H lam = r: max |r - H lam| and max |r|
-            vbd::SweepParams rp = sweep_params(ctx, -1);
-            rp.vbegin = 0;
-            rp.vend = ctx->n_free;
-            rp.adj_residual = 2;
-            vbd::launch_adj_sweep(d, xs, rp, kAdjLanes, kAdjBlock, s, d.adj_res + 2 * (size_t)t);
+            ctx->adj_graphs.push_back({ctx->tape_len, adj_iters, hh, ctx->version, exec});
         }
-        vbd::launch_adj_post(d, xs, N, ctx->n_free, ctx->T, h, has_sub, s);
+        CU(cudaGraphLaunch(exec, s), "graph launch (backward)");
     }
     ctx->h = h_saved;
     vbd::launch_adj_out(d, dL_dlogE, dL_dv0, N, ctx->T, s);

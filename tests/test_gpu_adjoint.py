@@ -56,9 +56,10 @@ def _check(label, gE, oE, gv, ov):
     assert fE == 0 and fv == 0
 
 
-def _gpu_grads(m, pd, colors, h, iters, steps, v0, tip, target, adj_iters, logE=None):
+def _gpu_grads(m, pd, colors, h, iters, steps, v0, tip, target, adj_iters, logE=None, graph=True):
     sim = vbd.Sim(m, vbd.make_params(tape_steps=steps, **pd), colors=colors)
     try:
+        vbd.vbd_set_graph(sim.ctx, graph)
         dev = sim.workspace.device
         le = torch.tensor(np.log(m.young.astype(np.float64)) if logE is None else logE,
                           dtype=torch.float32, device=dev, requires_grad=True)
@@ -166,6 +167,43 @@ def test_adjoint_against_central_fd(orc):
     print("GPU adjoint vs central FD: dlogE worst %.2e, dv0 worst %.2e (of the column's largest entry)" % (
         worst_E, worst_v))
     assert worst_E <= 1e-3 and worst_v <= 1e-3
+
+
+def test_backward_graph_equals_eager():
+    """The backward's step loop replayed as one CUDA graph gives the same
+    gradients, bit for bit, as its launches issued one by one; a second
+    backward through the same context (the cached graph) repeats them."""
+    m, cfg, tip, target = synth.differentiable_beam()
+    colors = synth.kuhn_coloring(m.grid_ijk)
+    pd = params_of(cfg)
+    v0 = np.zeros_like(m.rest)
+    steps = 6
+    out = {}
+    for graph in (True, False):
+        out[graph] = _gpu_grads(m, pd, colors, cfg.h, cfg.iters, steps, v0, tip, target, adj_iters=40,
+                                graph=graph)
+    for a, b in zip(out[True], out[False]):
+        assert np.array_equal(a, b)
+    sim = vbd.Sim(m, vbd.make_params(tape_steps=steps, **pd), colors=colors)
+    try:
+        dev = sim.workspace.device
+        sim.set_state(m.rest, v0)
+        for _ in range(steps):
+            sim.step(cfg.h, cfg.iters)
+        gx = torch.zeros(3 * m.n_verts, dtype=torch.float32, device=dev)
+        gx[2::3] = 1.0
+        res = []
+        for _ in range(2):
+            gE = torch.empty(m.n_tets, dtype=torch.float32, device=dev)
+            gv = torch.empty(3 * m.n_verts, dtype=torch.float32, device=dev)
+            vbd.vbd_backward(sim.ctx, gx, gE, gv, 40)
+            torch.cuda.synchronize()  # the backward runs on the context's stream
+            res.append((gE.cpu().numpy(), gv.cpu().numpy()))
+        sim.sync_status()
+    finally:
+        sim.close()
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert np.abs(res[0][1]).max() > 0
 
 
 def test_adjoint_differentiable_beam_full_size(orc):
