@@ -366,8 +366,11 @@ vbd_status vbd_sync_status(vbd_ctx *ctx, int64_t *det_skips, int64_t *contacts);
  * device): dL/dx of the final positions.  Outputs (device, overwritten):
  * dL_dlogE (T floats, caller tet order): dL/d log E per tet; dL_dv0 (3N):
  * dL/dv at the first recorded step; either may be NULL.  Needs k_d = 0 and
- * mu_c = 0 (damping and friction are not variational).  Synchronises only
- * to read the tape length. */
+ * mu_c = 0 (damping and friction are not variational).  With graphs on
+ * (vbd_set_graph, the default) the step loop is captured once per tape
+ * length, adj_iters and recorded step sizes and replayed by later calls;
+ * it touches only the workspace, so the three buffers may differ from call
+ * to call.  Synchronises only to read the tape length. */
 vbd_status vbd_backward(vbd_ctx *ctx, const float *dL_dxT, float *dL_dlogE, float *dL_dv0,
                         int32_t adj_iters);
 
@@ -455,7 +458,9 @@ vbd_status vbd_set_launch(vbd_ctx *ctx, int32_t lanes_per_vertex, int32_t block_
  * in flight, and the context stays usable.  Other variants ignore it. */
 vbd_status vbd_debug_stall_pipeline(vbd_ctx *ctx, int32_t enable);
 
-/* Enables (1) or disables (0) CUDA-graph replay of vbd_iterate. */
+/* Enables (1) or disables (0) CUDA-graph replay of vbd_iterate's loop and of
+ * vbd_backward's step loop (on by default; replay equals the eager launches
+ * bit for bit). */
 vbd_status vbd_set_graph(vbd_ctx *ctx, int32_t enable);
 
 /* Times every applicable sweep launch shape of vbd_set_launch on the bound

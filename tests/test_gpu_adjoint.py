@@ -204,6 +204,30 @@ def test_backward_graph_equals_eager():
         sim.close()
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
     assert np.abs(res[0][1]).max() > 0
+    # a new recording with another step size in a context that holds a captured
+    # backward: the cached graph does not match it, a new one is captured, and
+    # the gradients equal those of eager launches
+    h2 = 0.5 * cfg.h
+    out2 = {}
+    for graph in (True, False):
+        sim = vbd.Sim(m, vbd.make_params(tape_steps=steps, **pd), colors=colors)
+        try:
+            vbd.vbd_set_graph(sim.ctx, graph)
+            dev = sim.workspace.device
+            for h in ((cfg.h, h2) if graph else (h2,)):
+                sim.set_state(m.rest, v0)
+                for _ in range(steps):
+                    sim.step(h, cfg.iters)
+                gE = torch.empty(m.n_tets, dtype=torch.float32, device=dev)
+                gv = torch.empty(3 * m.n_verts, dtype=torch.float32, device=dev)
+                vbd.vbd_backward(sim.ctx, gx, gE, gv, 40)
+                torch.cuda.synchronize()
+            out2[graph] = (gE.cpu().numpy(), gv.cpu().numpy())
+            sim.sync_status()
+        finally:
+            sim.close()
+    assert np.array_equal(out2[True][0], out2[False][0]) and np.array_equal(out2[True][1], out2[False][1])
+    assert not np.array_equal(out2[True][1], res[0][1])
 
 
 def test_adjoint_differentiable_beam_full_size(orc):
