@@ -1800,8 +1800,11 @@ vbd_status vbd_autotune_ex(vbd_ctx *ctx, float h, int32_t iters, int32_t flags, 
     for (const Shape &sh : shapes) {
         if ((flags & VBD_TUNE_SAME_ARITHMETIC) && arithmetic_class(sh.pipe, sh.lanes) != cls) continue;
         if (vbd_set_launch(ctx, sh.lanes, sh.block, sh.pipe) != VBD_OK) continue;  // not applicable here
-        float ms = 0.f;
-        for (int rep = 0; rep < 2 && bad == VBD_OK; ++rep) {  // the first repetition warms up
+        // the first repetition warms up; then the best of at least two timed
+        // repetitions, more (up to seven) until 2 ms have been timed, so that
+        // short trials on small meshes are not decided by one noisy sample
+        float ms = 0.f, best_rep = 1e30f, timed = 0.f;
+        for (int rep = 0; rep < 8 && bad == VBD_OK; ++rep) {
             st = vbd_begin_step(ctx, h);
             if (st == VBD_OK) {
                 cudaEventRecord(e0, ctx->stream);
@@ -1818,10 +1821,15 @@ vbd_status vbd_autotune_ex(vbd_ctx *ctx, float h, int32_t iters, int32_t flags, 
             if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
                 bad = VBD_ERR_CUDA;
                 bad_msg = "autotune timing";
+                break;
             }
+            if (rep == 0) continue;
+            best_rep = std::min(best_rep, ms);
+            timed += ms;
+            if (rep >= 2 && timed >= 2.0f) break;
         }
         if (bad != VBD_OK) break;
-        if (ms < best) { best = ms; bs = sh; }
+        if (best_rep < best) { best = best_rep; bs = sh; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
