@@ -75,3 +75,16 @@ def test_clock_records_that_invalidate_a_measurement():
     assert b.clocks_rejected({"sm_mhz": 1100.0, "sm_max_mhz": 2032.0, "reasons": []})  # locked low
     assert not b.clocks_rejected({"sm_mhz": 1100.0, "sm_max_mhz": 2032.0, "reasons": ["sw_power_cap"]})
     assert not b.clocks_rejected({"sm_mhz": None, "sm_max_mhz": None, "reasons": []})
+
+
+def test_committed_dram_profile_matches_the_kernel_source():
+    """The bench's roofline `traffic` comes from the DRAM bytes per update in
+    profiles/sweep_large_cube.md, used only while the hash recorded there
+    matches the current forward kernel source: a kernel change needs a new
+    capture before the bench reports traffic again."""
+    import bench
+    t = bench.profiled_traffic("large_cube", 257575)
+    assert t is not None, "profiles/sweep_large_cube.md was taken on other kernel source (%s)" % (
+        bench.kernel_source_sha())
+    # DRAM bytes per update within the algorithmic model's range (1,303 B at this size)
+    assert 0.8 * 1303 <= t / 257575 <= 1.1 * 1303
