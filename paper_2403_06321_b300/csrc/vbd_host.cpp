@@ -949,12 +949,24 @@ vbd_status vbd_color(vbd_ctx *ctx, const int32_t *colors, int32_t *n_colors_out)
     }
     ctx->colors = col;
     ctx->n_colors = nc;
-    // colour-major order of free vertices (ties by caller id), pinned at the end
+    // colour-major order of free vertices, pinned at the end.  Within a colour
+    // the vertices with more incident tets come first (caller order among
+    // equals), so that the vertices a warp sweeps together have about as many
+    // slots each and no lane waits long on the warp's busiest vertex.  Within a
+    // colour the order changes no vertex's arithmetic (its solve reads only
+    // other colours).
+#ifndef VBD_DEGREE_ORDER
+#define VBD_DEGREE_ORDER 1
+#endif
+    std::vector<int> deg(N, 0);
+    if (VBD_DEGREE_ORDER)
+        for (size_t q = 0; q < ctx->tets.size(); ++q) deg[ctx->tets[q]]++;
     std::vector<int> order;
     order.reserve(N);
     for (int i = 0; i < N; ++i)
         if (!ctx->pinned[i]) order.push_back(i);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return col[a] < col[b]; });
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return col[a] < col[b] || (col[a] == col[b] && deg[a] > deg[b]); });
     ctx->n_free = (int)order.size();
     for (int i = 0; i < N; ++i)
         if (ctx->pinned[i]) order.push_back(i);
