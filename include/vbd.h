@@ -466,7 +466,9 @@ vbd_status vbd_set_graph(vbd_ctx *ctx, int32_t enable);
 /* Times every applicable sweep launch shape of vbd_set_launch on the bound
  * stream, each for `iters` iterations of a step of size h begun from the
  * current state (one warm-up run, then the best of two to seven timed runs,
- * as many as fit in about 2 ms of timing), and keeps the fastest (Sec. 3.9's colour passes are what
+ * as many as fit in about 2 ms of timing; with the context's CUDA-graph
+ * setting, so small meshes are timed as they will run), and keeps the
+ * fastest (Sec. 3.9's colour passes are what
  * is timed; the paper fixes one launch shape, this picks it per mesh).
  * Between steps only (VBD_ERR_STATE inside one).  Everything the timing
  * steps overwrite is put back: x (from x^t; v and v^{t-1} are never

@@ -1804,7 +1804,9 @@ vbd_status vbd_autotune_ex(vbd_ctx *ctx, float h, int32_t iters, int32_t flags, 
         cudaEventDestroy(e0);
         return fail(ctx, VBD_ERR_CUDA, "event");
     }
-    ctx->use_graph = false;
+    // the trials run as the context will (with its CUDA-graph setting): on a
+    // small mesh the eager launches would be host bound and hide the
+    // differences between shapes that the graph replays show
     float best = 1e30f;
     Shape bs = cur;
     vbd_status bad = VBD_OK;
