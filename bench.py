@@ -733,7 +733,7 @@ def run_paper_scale(args) -> dict:
     try:
         info = sim.info
         sim.set_state(m.rest, v0)
-        vbd.vbd_autotune(sim.ctx, cfg.h, 2)
+        vbd.vbd_autotune(sim.ctx, cfg.h, cfg.iters)  # trials of a whole step: long enough to show the power cap
         info = vbd.vbd_get_info(sim.ctx)
         sim.set_state(m.rest, v0)
         sim.step(cfg.h, cfg.iters)  # warm-up (graph capture)
